@@ -1,0 +1,306 @@
+"""ctypes wrapper of the FP64 CPU oracle (liboracle.so, built from oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and bench.py's CPU
+baseline. The product package never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (OpenMP over voxels, no FP contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-o", _LIB, src, "-lm"])
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [(k, C.c_double) for k in (
+        "C11", "C12", "C44", "gdot0", "n", "tau0", "alpha", "b", "k1", "k2", "rho0", "zeta",
+        "kc", "q", "s_nucl", "s_soften", "omega_gb", "dx", "l_gb", "L_dt", "eta_drop")]
+
+
+class Config(C.Structure):
+    _fields_ = [("n", C.c_int), ("grains", C.c_int), ("kmax", C.c_int), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("allow_unconverged", C.c_int), ("newton_tol", C.c_double),
+                ("newton_max", C.c_int), ("predictor", C.c_int), ("nthreads", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("newton_max_iters", C.c_int), ("status", C.c_int),
+                ("err_eq", C.c_double), ("err_bc", C.c_double), ("sig_mean", C.c_double * 6),
+                ("E", C.c_double * 6)]
+
+
+class PFStats(C.Structure):
+    _fields_ = [("F_tot", C.c_double), ("X_rex", C.c_double), ("n_grains", C.c_int), ("overflow", C.c_int)]
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_cp = np.ctypeslib.ndpointer(dtype=np.complex128, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_mix64.restype = C.c_uint64
+        L.orc_mix64.argtypes = [C.c_uint64]
+        L.orc_u01.restype = C.c_double
+        L.orc_u01.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+        L.orc_weibull.restype = C.c_double
+        L.orc_weibull.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_voronoi.argtypes = [C.c_int, C.c_int, _lp, _ip]
+        L.orc_quat_to_R.argtypes = [_dp, _dp]
+        L.orc_slip_systems.argtypes = [_dp, _dp]
+        L.orc_grain_tables.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_fft1d.argtypes = [_cp, C.c_int, C.c_long, C.c_int]
+        L.orc_fft3d.argtypes = [C.c_int, _cp, C.c_int]
+        L.orc_dft3d_brute.argtypes = [C.c_int, _cp, _cp, C.c_int]
+        L.orc_gamma0.argtypes = [_dp, C.c_double, C.c_double, _dp]
+        L.orc_newton.restype = C.c_int
+        L.orc_newton.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_int,
+                                 _dp, _dp, C.POINTER(C.c_int)]
+        L.orc_residual.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp, _dp]
+        L.orc_km_update.argtypes = [C.POINTER(Params), _dp, _dp, C.c_double]
+        L.orc_point_model.restype = C.c_int
+        L.orc_point_model.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                      C.c_int, _dp]
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(Config), C.POINTER(Params), _ip, _dp, C.c_uint64]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_field.restype = C.POINTER(C.c_double)
+        L.orc_field.argtypes = [C.c_void_p, C.c_char_p]
+        L.orc_ifield.restype = C.POINTER(C.c_int32)
+        L.orc_ifield.argtypes = [C.c_void_p, C.c_char_p]
+        L.orc_increment.restype = C.c_int
+        L.orc_increment.argtypes = [C.c_void_p, C.c_double, C.c_double, C.POINTER(Stats)]
+        L.orc_nucleate.restype = C.c_int
+        L.orc_nucleate.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)]
+        L.orc_pf_step.restype = C.c_int
+        L.orc_pf_step.argtypes = [C.c_void_p, C.c_int, C.POINTER(PFStats)]
+        L.orc_pf_step_dense.restype = C.c_int
+        L.orc_pf_step_dense.argtypes = [C.c_void_p, C.c_int]
+        L.orc_pf_energy.restype = C.c_double
+        L.orc_pf_energy.argtypes = [C.c_void_p]
+        L.orc_stats_now.argtypes = [C.c_void_p, C.POINTER(PFStats)]
+        L.orc_next_id.restype = C.c_int
+        L.orc_next_id.argtypes = [C.c_void_p]
+        L.orc_set_next_id.argtypes = [C.c_void_p, C.c_int]
+        L.orc_refresh_derived.argtypes = [C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def make_params(mat) -> Params:
+    p = Params()
+    for k, _ in Params._fields_:
+        setattr(p, k, float(getattr(mat, k)))
+    return p
+
+
+# ---------------------------------------------------------------------------------------------
+# thin numpy-facing helpers
+# ---------------------------------------------------------------------------------------------
+def u01(seed, idx, draw):
+    return lib().orc_u01(seed, idx, draw)
+
+
+def weibull(u, kc, q):
+    return lib().orc_weibull(u, kc, q)
+
+
+def voronoi(n, seeds):
+    seeds = np.ascontiguousarray(seeds, dtype=np.int64)
+    out = np.zeros(n ** 3, dtype=np.int32)
+    lib().orc_voronoi(n, seeds.shape[0], seeds.reshape(-1), out)
+    return out
+
+
+def quat_to_R(q):
+    R = np.zeros(9)
+    lib().orc_quat_to_R(np.ascontiguousarray(q, dtype=np.float64), R)
+    return R.reshape(3, 3)
+
+
+def slip_systems():
+    d = np.zeros(36)
+    nr = np.zeros(36)
+    lib().orc_slip_systems(d, nr)
+    return d.reshape(12, 3), nr.reshape(12, 3)
+
+
+def grain_tables(mat, quat):
+    quat = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1, 4)
+    G = quat.shape[0]
+    Cm = np.zeros(G * 36)
+    Sm = np.zeros(G * 36)
+    Mm = np.zeros(G * 72)
+    p = make_params(mat)
+    lib().orc_grain_tables(C.byref(p), G, quat.reshape(-1), Cm, Sm, Mm)
+    return Cm.reshape(G, 6, 6), Sm.reshape(G, 6, 6), Mm.reshape(G, 12, 6)
+
+
+def fft3d(a, sign=-1):
+    a = np.ascontiguousarray(a, dtype=np.complex128).copy()
+    n = a.shape[0]
+    lib().orc_fft3d(n, a.reshape(-1), sign)
+    return a
+
+
+def fft1d(a, sign=-1):
+    a = np.ascontiguousarray(a, dtype=np.complex128).copy()
+    lib().orc_fft1d(a, a.shape[0], 1, sign)
+    return a
+
+
+def dft3d_brute(a, sign=-1):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    out = np.zeros_like(a)
+    lib().orc_dft3d_brute(a.shape[0], a.reshape(-1), out.reshape(-1), sign)
+    return out
+
+
+def gamma0(xi, lam0, mu0):
+    G = np.zeros(36)
+    lib().orc_gamma0(np.ascontiguousarray(xi, dtype=np.float64), lam0, mu0, G)
+    return G.reshape(6, 6)
+
+
+def newton(mat, S, M, eps_tr, tauc, dt, sig0, tol=1e-12, maxit=50):
+    p = make_params(mat)
+    sig = np.ascontiguousarray(sig0, dtype=np.float64).copy()
+    gd = np.zeros(12)
+    its = C.c_int(0)
+    rc = lib().orc_newton(C.byref(p), np.ascontiguousarray(S, dtype=np.float64).reshape(-1),
+                          np.ascontiguousarray(M, dtype=np.float64).reshape(-1),
+                          np.ascontiguousarray(eps_tr, dtype=np.float64), tauc, dt, tol, maxit, sig, gd,
+                          C.byref(its))
+    return rc, sig, gd, its.value
+
+
+def residual(mat, S, M, eps_tr, tauc, dt, sig):
+    p = make_params(mat)
+    r = np.zeros(6)
+    K = np.zeros(36)
+    lib().orc_residual(C.byref(p), np.ascontiguousarray(S, dtype=np.float64).reshape(-1),
+                       np.ascontiguousarray(M, dtype=np.float64).reshape(-1),
+                       np.ascontiguousarray(eps_tr, dtype=np.float64), tauc, dt,
+                       np.ascontiguousarray(sig, dtype=np.float64), r, K)
+    return r, K.reshape(6, 6)
+
+
+def km_update(mat, rho, gdot, dt):
+    p = make_params(mat)
+    rho = np.ascontiguousarray(rho, dtype=np.float64).copy()
+    lib().orc_km_update(C.byref(p), rho, np.ascontiguousarray(gdot, dtype=np.float64), dt)
+    return rho
+
+
+def point_model(mat, S, M, dE33, dt, nsteps, rho0=None):
+    p = make_params(mat)
+    sig = np.zeros(6)
+    epsp = np.zeros(6)
+    rho = np.full(12, mat.rho0 if rho0 is None else rho0, dtype=np.float64)
+    E = np.zeros(6)
+    hist = np.zeros(max(nsteps, 1))
+    rc = lib().orc_point_model(C.byref(p), np.ascontiguousarray(S, dtype=np.float64).reshape(-1),
+                               np.ascontiguousarray(M, dtype=np.float64).reshape(-1), sig, epsp, rho, E,
+                               dE33, dt, nsteps, hist)
+    return rc, hist[:nsteps], dict(sig=sig, epsp=epsp, rho=rho, E=E)
+
+
+class State:
+    """The oracle's full simulation state (FP64, host memory)."""
+
+    def __init__(self, n, grains, g0, quat, mat, seed, kmax=8, tol=1e-10, max_iter=1000,
+                 allow_unconverged=0, newton_tol=1e-12, newton_max=50, predictor=1, nthreads=0):
+        self.n, self.G, self.K = n, grains, kmax
+        self.N3 = n ** 3
+        self.mat = mat
+        self._cfg = Config(n, grains, kmax, tol, max_iter, allow_unconverged, newton_tol, newton_max,
+                           predictor, nthreads)
+        self._p = make_params(mat)
+        self._g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)
+        self._q = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1)
+        self.h = lib().orc_create(C.byref(self._cfg), C.byref(self._p), self._g0, self._q, seed)
+
+    def close(self):
+        if self.h:
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    _SIZES = {"eps": 6, "epsp": 6, "sig": 6, "deps_prev": 6, "rho": 12, "k": 1, "kappa": 1}
+
+    def field(self, name):
+        """A view (not a copy) of a double field, shaped (components, N^3)."""
+        ptr = lib().orc_field(self.h, name.encode())
+        if name in ("E", "dE_prev"):
+            return np.ctypeslib.as_array(ptr, shape=(6,))
+        if name == "eta":
+            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3))
+        return np.ctypeslib.as_array(ptr, shape=(self._SIZES[name], self.N3))
+
+    def ifield(self, name):
+        ptr = lib().orc_ifield(self.h, name.encode())
+        if name == "ids":
+            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3))
+        return np.ctypeslib.as_array(ptr, shape=(self.N3,))
+
+    def increment(self, dE33, dt):
+        st = Stats()
+        rc = lib().orc_increment(self.h, dE33, dt, C.byref(st))
+        return rc, st
+
+    def nucleate(self, step=0):
+        nn = C.c_int32(0)
+        rc = lib().orc_nucleate(self.h, step, C.byref(nn))
+        return rc, nn.value
+
+    def pf_step(self, nsteps):
+        st = PFStats()
+        rc = lib().orc_pf_step(self.h, nsteps, C.byref(st))
+        return rc, st
+
+    def pf_step_dense(self, nsteps):
+        return lib().orc_pf_step_dense(self.h, nsteps)
+
+    def pf_energy(self):
+        return lib().orc_pf_energy(self.h)
+
+    def stats(self):
+        st = PFStats()
+        lib().orc_stats_now(self.h, C.byref(st))
+        return st
+
+    @property
+    def next_id(self):
+        return lib().orc_next_id(self.h)
+
+    @next_id.setter
+    def next_id(self, v):
+        lib().orc_set_next_id(self.h, int(v))
+
+    def refresh_derived(self):
+        lib().orc_refresh_derived(self.h)

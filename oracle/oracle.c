@@ -1,0 +1,1044 @@
+/*
+ * FP64 CPU oracle of the coupled FFT-EVP / phase-field DRX hot path
+ * (Zhao, Low, Wang, Niezgoda, arXiv:1509.04953).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the CPU baseline
+ * leg of bench.py. It is plain, slow and written to be checked against the paper by eye:
+ * plain loops, a textbook radix-2 FFT, full 4th-order tensors, no fusion and no blocking.
+ * It shares no code with the CUDA library.
+ *
+ * Every function names the passage of the paper (or the textbook closed form) it follows.
+ * Readings of passages the paper leaves open are listed where they are used.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* complex.h defines I as the imaginary unit; the oracle uses I as a Mandel index instead */
+#undef I
+#define IU _Complex_I
+#define SQ2 1.41421356237309504880
+#define PI 3.14159265358979323846
+
+/* Mandel index -> tensor index pair, and the Mandel weight of each slot. */
+static const int MI[6] = {0, 1, 2, 1, 0, 0};
+static const int MJ[6] = {0, 1, 2, 2, 2, 1};
+static double mw(int I) { return I < 3 ? 1.0 : SQ2; }
+
+/* ------------------------------------------------------------------------------------------
+ * Counter-based generator: SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA 2014), applied
+ * to (seed, voxel index, draw number). u lies strictly inside (0,1).
+ * ---------------------------------------------------------------------------------------- */
+uint64_t orc_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+double orc_u01(uint64_t seed, uint64_t idx, uint64_t draw) {
+    const uint64_t golden = 0x9E3779B97F4A7C15ULL;
+    uint64_t h = orc_mix64(seed ^ 0xD1B54A32D192ED03ULL);
+    h = orc_mix64(h + golden * (idx + 1));
+    h = orc_mix64(h + golden * (draw + 1));
+    return ((double)(h >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+/* Inverse of the Weibull CDF P(kappa < k) = 1 - exp(-(k/kc)^q)  (Eqs. NumCrt, NuclStrengthProb). */
+double orc_weibull(double u, double kc, double q) {
+    return kc * pow(-log(1.0 - u), 1.0 / q);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Microstructure: periodic Voronoi tessellation. Voxel centres sit at (i*2^16 + 2^15) on the
+ * integer sub-grid; a voxel joins the seed at the smallest squared periodic distance, ties
+ * going to the smaller seed index. Exact integer arithmetic.
+ * ---------------------------------------------------------------------------------------- */
+void orc_voronoi(int n, int G, const int64_t *seeds, int32_t *ids) {
+    const int64_t L = (int64_t)n << 16;
+    for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x) {
+                int64_t c[3] = {((int64_t)x << 16) + 32768, ((int64_t)y << 16) + 32768,
+                                ((int64_t)z << 16) + 32768};
+                int64_t best = -1;
+                int arg = 0;
+                for (int g = 0; g < G; ++g) {
+                    int64_t d2 = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        int64_t d = c[a] - seeds[3 * g + a];
+                        if (d < 0) d = -d;
+                        d %= L;
+                        if (L - d < d) d = L - d;
+                        d2 += d * d;
+                    }
+                    if (best < 0 || d2 < best) { best = d2; arg = g; }
+                }
+                ids[x + (size_t)n * (y + (size_t)n * z)] = arg;
+            }
+}
+
+/* Rotation matrix of a unit quaternion (w,x,y,z); R maps crystal coordinates to sample ones. */
+void orc_quat_to_R(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double s = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+    w *= s; x *= s; y *= s; z *= s;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* The 12 FCC {111}<110> slip systems (crystal frame, unit vectors): "single-phase FCC",
+ * Sec. 2.2. Slip plane normals (111), (-111), (1-11), (11-1), three <110> directions each. */
+void orc_slip_systems(double d[12][3], double nrm[12][3]) {
+    static const double N4[4][3] = {{1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {1, 1, -1}};
+    static const double D4[4][3][3] = {
+        {{0, 1, -1}, {1, 0, -1}, {1, -1, 0}},
+        {{0, 1, -1}, {1, 0, 1}, {1, 1, 0}},
+        {{0, 1, 1}, {1, 0, -1}, {1, 1, 0}},
+        {{0, 1, 1}, {1, 0, 1}, {1, -1, 0}}};
+    for (int p = 0; p < 4; ++p)
+        for (int j = 0; j < 3; ++j) {
+            int a = 3 * p + j;
+            for (int c = 0; c < 3; ++c) {
+                nrm[a][c] = N4[p][c] / sqrt(3.0);
+                d[a][c] = D4[p][j][c] / sqrt(2.0);
+            }
+        }
+}
+
+/* Plain Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix. */
+static int inv_gj(int n, const double *A, double *Ainv) {
+    double W[6][12];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < 2 * n; ++j) W[i][j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(W[r][c]) > fabs(W[p][c])) p = r;
+        if (W[p][c] == 0.0) return -1;
+        if (p != c)
+            for (int j = 0; j < 2 * n; ++j) { double t = W[c][j]; W[c][j] = W[p][j]; W[p][j] = t; }
+        double piv = W[c][c];
+        for (int j = 0; j < 2 * n; ++j) W[c][j] /= piv;
+        for (int r = 0; r < n; ++r)
+            if (r != c) {
+                double f = W[r][c];
+                for (int j = 0; j < 2 * n; ++j) W[r][j] -= f * W[c][j];
+            }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Ainv[i * n + j] = W[i][j + n];
+    return 0;
+}
+
+/* Per-grain tables in the sample frame: stiffness C (Mandel 6x6), compliance S = C^-1 and
+ * Schmid tensors m^a = sym(d^a x n^a) as Mandel 6-vectors (Eqs. HookeLaw, PlasticRate).
+ * The cubic stiffness is rotated index by index: C'_ijkl = R_ia R_jb R_kc R_ld C_abcd. */
+void orc_grain_tables(const orc_params *p, int G, const double *quat, double *C, double *S, double *M) {
+    double d[12][3], nr[12][3];
+    orc_slip_systems(d, nr);
+    double Cc[3][3][3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    double v = p->C12 * (i == j) * (k == l) + p->C44 * ((i == k) * (j == l) + (i == l) * (j == k));
+                    if (i == j && j == k && k == l) v += p->C11 - p->C12 - 2.0 * p->C44;
+                    Cc[i][j][k][l] = v;
+                }
+    for (int g = 0; g < G; ++g) {
+        double R[9];
+        orc_quat_to_R(quat + 4 * g, R);
+        double Cs[3][3][3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) {
+                        double acc = 0.0;
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b)
+                                for (int c = 0; c < 3; ++c)
+                                    for (int e = 0; e < 3; ++e)
+                                        acc += R[3 * i + a] * R[3 * j + b] * R[3 * k + c] * R[3 * l + e] * Cc[a][b][c][e];
+                        Cs[i][j][k][l] = acc;
+                    }
+        double *Cg = C + 36 * g;
+        for (int I = 0; I < 6; ++I)
+            for (int J = 0; J < 6; ++J) Cg[6 * I + J] = mw(I) * mw(J) * Cs[MI[I]][MJ[I]][MI[J]][MJ[J]];
+        inv_gj(6, Cg, S + 36 * g);
+        for (int a = 0; a < 12; ++a) {
+            double ds[3], ns[3];
+            for (int i = 0; i < 3; ++i) {
+                ds[i] = R[3 * i] * d[a][0] + R[3 * i + 1] * d[a][1] + R[3 * i + 2] * d[a][2];
+                ns[i] = R[3 * i] * nr[a][0] + R[3 * i + 1] * nr[a][1] + R[3 * i + 2] * nr[a][2];
+            }
+            for (int I = 0; I < 6; ++I) {
+                int i = MI[I], j = MJ[I];
+                M[72 * g + 6 * a + I] = mw(I) * 0.5 * (ds[i] * ns[j] + ds[j] * ns[i]);
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Textbook iterative radix-2 Cooley-Tukey FFT (bit reversal, then butterflies), unnormalised,
+ * a[j] <- sum_k a[k] exp(sign*2*pi*i*j*k/n). n must be a power of two.
+ * ---------------------------------------------------------------------------------------- */
+void orc_fft1d(double complex *a, int n, long stride, int sign) {
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { double complex t = a[i * stride]; a[i * stride] = a[j * stride]; a[j * stride] = t; }
+    }
+    for (int len = 2; len <= n; len <<= 1)
+        for (int i = 0; i < n; i += len)
+            for (int k = 0; k < len / 2; ++k) {
+                double complex w = cexp(sign * 2.0 * PI * IU * (double)k / (double)len);
+                double complex u = a[(i + k) * stride], v = w * a[(i + k + len / 2) * stride];
+                a[(i + k) * stride] = u + v;
+                a[(i + k + len / 2) * stride] = u - v;
+            }
+}
+
+void orc_fft3d(int n, double complex *a, int sign) {
+    const long n2 = (long)n * n;
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < n2; ++l) orc_fft1d(a + l * n, n, 1, sign);                 /* x lines */
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < n2; ++l) orc_fft1d(a + (l / n) * n2 + (l % n), n, n, sign); /* y lines */
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < n2; ++l) orc_fft1d(a + l, n, n2, sign);                    /* z lines */
+}
+
+/* Brute-force O(N^6) DFT, the definition written out (pins the FFT). */
+void orc_dft3d_brute(int n, const double complex *in, double complex *out, int sign) {
+    for (int kz = 0; kz < n; ++kz)
+        for (int ky = 0; ky < n; ++ky)
+            for (int kx = 0; kx < n; ++kx) {
+                double complex acc = 0;
+                for (int z = 0; z < n; ++z)
+                    for (int y = 0; y < n; ++y)
+                        for (int x = 0; x < n; ++x) {
+                            long ph = ((long)kx * x + (long)ky * y + (long)kz * z) % n;
+                            acc += in[x + n * (y + n * z)] * cexp(sign * 2.0 * PI * IU * (double)ph / (double)n);
+                        }
+                out[kx + n * (ky + n * kz)] = acc;
+            }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Green operator of an isotropic reference medium (lambda0, mu0) in Fourier space
+ * (Moulinec-Suquet form, cited by the paper in Sec. 2.1):
+ *   G_khij = [d_ki x_h x_j + d_hi x_k x_j + d_kj x_h x_i + d_hj x_k x_i] / (4 mu0 |x|^2)
+ *          - (lambda0+mu0)/(mu0 (lambda0+2 mu0)) x_i x_j x_k x_h / |x|^4,
+ * assembled as a full 4th-order tensor and then written in Mandel form. xi != 0.
+ * ---------------------------------------------------------------------------------------- */
+void orc_gamma0(const double xi[3], double lam0, double mu0, double Gm[36]) {
+    double x2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    double c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+    double Gt[3][3][3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int h = 0; h < 3; ++h)
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    Gt[k][h][i][j] = ((k == i) * xi[h] * xi[j] + (h == i) * xi[k] * xi[j] + (k == j) * xi[h] * xi[i] +
+                                      (h == j) * xi[k] * xi[i]) / (4.0 * mu0 * x2) -
+                                     c2 * xi[i] * xi[j] * xi[k] * xi[h] / (x2 * x2);
+    /* Mandel form of the map sigma -> eps: eps_kh = sum_ij G_khij sigma_ij, where the
+     * symmetric sum over (i,j) counts both off-diagonal slots. */
+    for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) {
+            int k = MI[I], h = MJ[I], i = MI[J], j = MJ[J];
+            double v = (i == j) ? Gt[k][h][i][j] : (Gt[k][h][i][j] + Gt[k][h][j][i]);
+            Gm[6 * I + J] = mw(I) * v / mw(J);
+        }
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Constitutive law (readings of Sec. 2.2 for the power-law / Kocks-Mecking form):
+ *   gdot^a = gdot0 |tau^a/tau_c|^n sign(tau^a),  tau^a = m^a : sigma.
+ * Implicit Euler stress update (Eq. HookeLaw with Eq. PlasticRate), written as the strain
+ * residual  r(sigma) = S:sigma + dt * sum_a m^a gdot^a(sigma) - (eps - eps_p^t) = 0.
+ * r is the gradient of the convex potential
+ *   Phi(sigma) = 1/2 sigma:S:sigma - sigma:eps_tr + dt sum_a gdot0 tau_c |tau^a/tau_c|^(n+1)/(n+1),
+ * whose Hessian K = S + dt sum_a (n gdot0 |x^a|^(n-1)/tau_c) m^a (x) m^a is symmetric positive
+ * definite. Newton steps on r with Armijo backtracking on Phi converge from any start.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct { double r[6], K[36], phi, gdot[12]; } nt_eval;
+
+static void nt_evaluate(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+                        double tauc, double dt, const double sig[6], nt_eval *e) {
+    for (int I = 0; I < 6; ++I) {
+        double acc = 0.0;
+        for (int J = 0; J < 6; ++J) acc += S[6 * I + J] * sig[J];
+        e->r[I] = acc - eps_tr[I];
+        for (int J = 0; J < 6; ++J) e->K[6 * I + J] = S[6 * I + J];
+    }
+    double phi = 0.0;
+    for (int I = 0; I < 6; ++I) {
+        double Ss = 0.0;
+        for (int J = 0; J < 6; ++J) Ss += S[6 * I + J] * sig[J];
+        phi += 0.5 * sig[I] * Ss - sig[I] * eps_tr[I];
+    }
+    for (int a = 0; a < 12; ++a) {
+        const double *m = M + 6 * a;
+        double tau = 0.0;
+        for (int I = 0; I < 6; ++I) tau += m[I] * sig[I];
+        double x = tau / tauc, ax = fabs(x);
+        double pw = ax > 0.0 ? pow(ax, p->n) : 0.0;
+        double gd = p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0);
+        if (ax == 0.0) gd = 0.0;
+        e->gdot[a] = gd;
+        double slope = ax > 0.0 ? dt * p->n * p->gdot0 * (pw / ax) / tauc : 0.0;
+        for (int I = 0; I < 6; ++I) {
+            e->r[I] += dt * m[I] * gd;
+            for (int J = 0; J < 6; ++J) e->K[6 * I + J] += slope * m[I] * m[J];
+        }
+        phi += dt * p->gdot0 * tauc * pw * ax / (p->n + 1.0);
+    }
+    e->phi = phi;
+}
+
+void orc_residual(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+                  double tauc, double dt, const double sig[6], double r[6], double K[36]) {
+    nt_eval e;
+    nt_evaluate(p, S, M, eps_tr, tauc, dt, sig, &e);
+    memcpy(r, e.r, sizeof e.r);
+    memcpy(K, e.K, sizeof e.K);
+}
+
+int orc_newton(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+               double tauc, double dt, double tol, int maxit, double sig[6], double gdot[12], int *iters) {
+    nt_eval e, t;
+    nt_evaluate(p, S, M, eps_tr, tauc, dt, sig, &e);
+    for (int it = 1; it <= maxit; ++it) {
+        double Ki[36], d[6];
+        if (inv_gj(6, e.K, Ki) != 0) { *iters = it; return -1; }
+        for (int I = 0; I < 6; ++I) {
+            d[I] = 0.0;
+            for (int J = 0; J < 6; ++J) d[I] += Ki[6 * I + J] * e.r[J];
+        }
+        double rd = 0.0, dn = 0.0, sn = 0.0;
+        for (int I = 0; I < 6; ++I) { rd += e.r[I] * d[I]; dn += d[I] * d[I]; sn += sig[I] * sig[I]; }
+        dn = sqrt(dn);
+        double scale = sqrt(sn) + tauc;
+        double s = 1.0, trial[6];
+        int ok = 0;
+        for (int h = 0; h < 60; ++h) {
+            for (int I = 0; I < 6; ++I) trial[I] = sig[I] - s * d[I];
+            nt_evaluate(p, S, M, eps_tr, tauc, dt, trial, &t);
+            if (t.phi <= e.phi - 1e-4 * s * rd || s * dn <= 1e-6 * scale) { ok = 1; break; }
+            s *= 0.5;
+        }
+        if (!ok) { *iters = it; return -1; }
+        memcpy(sig, trial, sizeof trial);
+        e = t;
+        if (s * dn <= tol * scale) {
+            memcpy(gdot, e.gdot, sizeof e.gdot);
+            *iters = it;
+            return 0;
+        }
+    }
+    *iters = maxit;
+    return -1;
+}
+
+/* Kocks-Mecking update with explicit densities and the converged shear rates (reading of the
+ * paper's first and third SSD terms, Eq. SSDEvolution, with rho_F the summed density):
+ *   rho^a <- rho^a + dt (k1 sqrt(rho_F) - k2 rho^a) |gdot^a|. */
+void orc_km_update(const orc_params *p, double *rho, const double *gdot, double dt) {
+    double rf = 0.0;
+    for (int a = 0; a < 12; ++a) rf += rho[a];
+    double srf = sqrt(rf);
+    for (int a = 0; a < 12; ++a) rho[a] = rho[a] + dt * (p->k1 * srf - p->k2 * rho[a]) * fabs(gdot[a]);
+}
+
+static double mu_voigt(const orc_params *p) { return (p->C11 - p->C12 + 3.0 * p->C44) / 5.0; }
+static double lam_voigt(const orc_params *p) { return (p->C11 + 4.0 * p->C12 - 2.0 * p->C44) / 5.0; }
+static double tauc_of(const orc_params *p, const double *rho, long N3, long v) {
+    double rf = 0.0;
+    for (int a = 0; a < 12; ++a) rf += rho[a * N3 + v];
+    return p->tau0 + p->alpha * mu_voigt(p) * p->b * sqrt(rf);
+}
+
+/* Uniaxial-stress point model of one crystal, solved by bisection on sigma33 (all other
+ * stress components zero, E33 prescribed): a different algorithm from the FFT mixed-BC loop. */
+int orc_point_model(const orc_params *p, const double *S, const double *M, double *sig, double *epsp,
+                    double *rho, double *E, double dE33, double dt, int nsteps, double *sig33_hist) {
+    for (int st = 0; st < nsteps; ++st) {
+        double rf = 0.0;
+        for (int a = 0; a < 12; ++a) rf += rho[a];
+        double tauc = p->tau0 + p->alpha * mu_voigt(p) * p->b * sqrt(rf);
+        double target = E[2] + dE33;
+        nt_eval e;
+        double zero6[6] = {0, 0, 0, 0, 0, 0};
+#define F33(s33, out)                                                                  \
+    do {                                                                               \
+        double sg[6] = {0, 0, (s33), 0, 0, 0};                                         \
+        nt_evaluate(p, S, M, zero6, tauc, dt, sg, &e);                                 \
+        (out) = e.r[2] + epsp[2] - target;                                             \
+    } while (0)
+        double lo = -1.0, hi = 1.0, flo, fhi;
+        F33(lo, flo);
+        F33(hi, fhi);
+        for (int k = 0; k < 200 && flo > 0.0; ++k) { lo *= 2.0; F33(lo, flo); }
+        for (int k = 0; k < 200 && fhi < 0.0; ++k) { hi *= 2.0; F33(hi, fhi); }
+        if (flo > 0.0 || fhi < 0.0) return -1;
+        for (int k = 0; k < 400 && hi - lo > 0.0; ++k) {
+            double mid = 0.5 * (lo + hi), fm;
+            if (mid == lo || mid == hi) break;
+            F33(mid, fm);
+            if (fm > 0.0) hi = mid; else lo = mid;
+        }
+        double s33 = 0.5 * (lo + hi);
+        double sg[6] = {0, 0, s33, 0, 0, 0};
+        nt_evaluate(p, S, M, zero6, tauc, dt, sg, &e);
+        /* e.r = S sigma + dt eps_p_dot; total strain E = that + eps_p^t */
+        for (int I = 0; I < 6; ++I) E[I] = e.r[I] + epsp[I];
+        E[2] = target;
+        for (int I = 0; I < 6; ++I) {
+            double ep = 0.0;
+            for (int a = 0; a < 12; ++a) ep += M[6 * a + I] * e.gdot[a];
+            epsp[I] += dt * ep;
+        }
+        orc_km_update(p, rho, e.gdot, dt);
+        memcpy(sig, sg, sizeof sg);
+        if (sig33_hist) sig33_hist[st] = s33;
+#undef F33
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Full state.
+ * ---------------------------------------------------------------------------------------- */
+struct orc_state {
+    orc_config cfg;
+    orc_params p;
+    int n, G, K;
+    long N3;
+    uint64_t seed;
+    int next_id, have_prev;
+    double E[6], dE_prev[6];
+    double *C, *S, *M;
+    int32_t *g0, *g, *draws, *ids, *ids2;
+    double *eps, *epsp, *sig, *deps_prev, *rho, *k, *kappa, *eta, *eta2;
+    double *work_eps, *work_sig;
+    double complex *spec;
+};
+
+static void *xcalloc(size_t n, size_t sz) {
+    void *p = calloc(n ? n : 1, sz);
+    if (!p) { fprintf(stderr, "oracle: out of memory\n"); abort(); }
+    return p;
+}
+
+orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat,
+                      uint64_t seed) {
+    orc_state *s = (orc_state *)xcalloc(1, sizeof *s);
+    s->cfg = *cfg;
+    s->p = *p;
+    s->n = cfg->n;
+    s->G = cfg->grains;
+    s->K = cfg->kmax;
+    s->N3 = (long)cfg->n * cfg->n * cfg->n;
+    s->seed = seed;
+    s->next_id = s->G;
+#ifdef _OPENMP
+    if (cfg->nthreads > 0) omp_set_num_threads(cfg->nthreads);
+#endif
+    long N3 = s->N3;
+    s->C = xcalloc(36 * (size_t)s->G, sizeof(double));
+    s->S = xcalloc(36 * (size_t)s->G, sizeof(double));
+    s->M = xcalloc(72 * (size_t)s->G, sizeof(double));
+    orc_grain_tables(p, s->G, quat, s->C, s->S, s->M);
+    s->g0 = xcalloc(N3, sizeof(int32_t));
+    s->g = xcalloc(N3, sizeof(int32_t));
+    s->draws = xcalloc(N3, sizeof(int32_t));
+    s->ids = xcalloc((size_t)s->K * N3, sizeof(int32_t));
+    s->ids2 = xcalloc((size_t)s->K * N3, sizeof(int32_t));
+    s->eta = xcalloc((size_t)s->K * N3, sizeof(double));
+    s->eta2 = xcalloc((size_t)s->K * N3, sizeof(double));
+    s->eps = xcalloc(6 * N3, sizeof(double));
+    s->epsp = xcalloc(6 * N3, sizeof(double));
+    s->sig = xcalloc(6 * N3, sizeof(double));
+    s->deps_prev = xcalloc(6 * N3, sizeof(double));
+    s->rho = xcalloc(12 * N3, sizeof(double));
+    s->k = xcalloc(N3, sizeof(double));
+    s->kappa = xcalloc(N3, sizeof(double));
+    s->work_eps = xcalloc(6 * N3, sizeof(double));
+    s->work_sig = xcalloc(6 * N3, sizeof(double));
+    s->spec = xcalloc(6 * N3, sizeof(double complex));
+    for (long v = 0; v < N3; ++v) {
+        s->g0[v] = g0[v];
+        s->g[v] = g0[v];
+        for (int a = 0; a < 12; ++a) s->rho[a * N3 + v] = p->rho0;
+        double kk = 0.0;
+        for (int a = 0; a < 12; ++a) kk += s->rho[a * N3 + v];
+        s->k[v] = kk;
+        /* initial nucleation strength: draw 0 from Weibull(q, kc) (Sec. 2.3, implementation) */
+        s->kappa[v] = orc_weibull(orc_u01(seed, (uint64_t)v, 0), p->kc, p->q);
+        /* initial order parameters: sharp, one grain per voxel */
+        for (int j = 0; j < s->K; ++j) { s->ids[j * N3 + v] = -1; s->eta[j * N3 + v] = 0.0; }
+        s->ids[v] = g0[v];
+        s->eta[v] = 1.0;
+    }
+    return s;
+}
+
+void orc_destroy(orc_state *s) {
+    if (!s) return;
+    free(s->C); free(s->S); free(s->M); free(s->g0); free(s->g); free(s->draws); free(s->ids);
+    free(s->ids2); free(s->eta); free(s->eta2); free(s->eps); free(s->epsp); free(s->sig);
+    free(s->deps_prev); free(s->rho); free(s->k); free(s->kappa); free(s->work_eps);
+    free(s->work_sig); free(s->spec); free(s);
+}
+
+double *orc_field(orc_state *s, const char *name) {
+    if (!strcmp(name, "eps")) return s->eps;
+    if (!strcmp(name, "epsp")) return s->epsp;
+    if (!strcmp(name, "sig")) return s->sig;
+    if (!strcmp(name, "deps_prev")) return s->deps_prev;
+    if (!strcmp(name, "rho")) return s->rho;
+    if (!strcmp(name, "k")) return s->k;
+    if (!strcmp(name, "kappa")) return s->kappa;
+    if (!strcmp(name, "eta")) return s->eta;
+    if (!strcmp(name, "C")) return s->C;
+    if (!strcmp(name, "S")) return s->S;
+    if (!strcmp(name, "M")) return s->M;
+    if (!strcmp(name, "E")) return s->E;
+    if (!strcmp(name, "dE_prev")) return s->dE_prev;
+    return NULL;
+}
+
+int32_t *orc_ifield(orc_state *s, const char *name) {
+    if (!strcmp(name, "g0")) return s->g0;
+    if (!strcmp(name, "g")) return s->g;
+    if (!strcmp(name, "draws")) return s->draws;
+    if (!strcmp(name, "ids")) return s->ids;
+    return NULL;
+}
+
+int orc_next_id(orc_state *s) { return s->next_id; }
+void orc_set_next_id(orc_state *s, int next_id) { s->next_id = next_id; }
+
+/* Recompute k = rho_tot from rho (after a caller overwrote rho). */
+void orc_refresh_derived(orc_state *s) {
+    for (long v = 0; v < s->N3; ++v) {
+        double kk = 0.0;
+        for (int a = 0; a < 12; ++a) kk += s->rho[a * s->N3 + v];
+        s->k[v] = kk;
+    }
+}
+
+/* Signed frequency of index k on an n-point axis; the Nyquist index n/2 is taken as +n/2. */
+static int freq(int k, int n) { return k <= n / 2 ? k : k - n; }
+
+/* ------------------------------------------------------------------------------------------
+ * One mechanical increment (Sec. 2.1): the basic Green-operator fixed point with a
+ * strain-driven local Newton, under mixed macroscopic conditions (E33 prescribed, the other
+ * mean stresses zero). Steps, in order, per iteration k:
+ *   1. sigma^k(x) = local implicit update at eps^{k-1}(x)              (Eqs. HookeLaw, PlasticRate)
+ *   2. sigma_hat = FFT(sigma^k)
+ *   3. err_eq = sqrt(sum_xi |xi . sigma_hat|^2) / |sigma_hat(0)|, xi = 2 pi k / N;
+ *      err_bc = |<sigma>_u| / |<sigma>|  (u = stress-controlled components)
+ *   4. stop if both <= tol, or if k = max_iter
+ *   5. E_u += (C0_uu)^-1 (0 - <sigma>_u)
+ *   6. eps^k = eps^{k-1} - iFFT(Gamma0_hat : sigma_hat) + dE, with Gamma0_hat replaced by
+ *      C0^-1 at frequencies that have a Nyquist component (Moulinec-Suquet treatment of even N)
+ * After convergence the state is advanced with the converged shear rates (a7).
+ * ---------------------------------------------------------------------------------------- */
+int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
+    const orc_params *p = &s->p;
+    const int n = s->n;
+    const long N3 = s->N3;
+    const double lam0 = lam_voigt(p), mu0 = mu_voigt(p);
+    int status = 0;
+    memset(out, 0, sizeof *out);
+
+    /* reference-medium compliance (for Nyquist frequencies) and the mixed-BC correction */
+    double C0[36], S0[36];
+    for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) C0[6 * I + J] = (I < 3 && J < 3 ? lam0 : 0.0) + (I == J ? 2.0 * mu0 : 0.0);
+    inv_gj(6, C0, S0);
+    const int U[5] = {0, 1, 3, 4, 5};
+    double C0uu[25], C0uu_inv[25];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) C0uu[5 * a + b] = C0[6 * U[a] + U[b]];
+    inv_gj(5, C0uu, C0uu_inv);
+
+    /* hardening frozen over the increment (explicit in rho) */
+    double *tauc = (double *)xcalloc(N3, sizeof(double));
+    for (long v = 0; v < N3; ++v) tauc[v] = tauc_of(p, s->rho, N3, v);
+
+    /* predictor: extrapolate the previous strain-increment field, else a uniform guess that is
+     * the reference medium's response to dE33 under zero lateral stress */
+    double dE[6];
+    double *epsk = s->work_eps, *sigk = s->work_sig;
+    if (s->cfg.predictor && s->have_prev && s->dE_prev[2] != 0.0) {
+        double r = dE33 / s->dE_prev[2];
+        for (int I = 0; I < 6; ++I) dE[I] = r * s->dE_prev[I];
+        dE[2] = dE33;
+        for (long i = 0; i < 6 * N3; ++i) epsk[i] = s->eps[i] + r * s->deps_prev[i];
+    } else {
+        double nu0 = lam0 / (2.0 * (lam0 + mu0));
+        double g[6] = {-nu0 * dE33, -nu0 * dE33, dE33, 0, 0, 0};
+        memcpy(dE, g, sizeof g);
+        for (int I = 0; I < 6; ++I)
+            for (long v = 0; v < N3; ++v) epsk[I * N3 + v] = s->eps[I * N3 + v] + dE[I];
+    }
+    memcpy(sigk, s->sig, 6 * N3 * sizeof(double));
+
+    int k, conv = 0, newton_max = 0, newton_fail = 0;
+    double err_eq = 0, err_bc = 0, mean[6] = {0};
+    for (k = 1; k <= s->cfg.max_iter; ++k) {
+        /* 1. local stress update */
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : newton_max) reduction(| : newton_fail)
+        for (long v = 0; v < N3; ++v) {
+            int gr = s->g0[v];
+            double etr[6], sg[6], gd[12];
+            for (int I = 0; I < 6; ++I) {
+                etr[I] = epsk[I * N3 + v] - s->epsp[I * N3 + v];
+                sg[I] = sigk[I * N3 + v];
+            }
+            int its = 0;
+            int rc = orc_newton(p, s->S + 36 * gr, s->M + 72 * gr, etr, tauc[v], dt, s->cfg.newton_tol,
+                                s->cfg.newton_max, sg, gd, &its);
+            if (rc) newton_fail |= 1;
+            if (its > newton_max) newton_max = its;
+            for (int I = 0; I < 6; ++I) sigk[I * N3 + v] = sg[I];
+        }
+        if (newton_fail) { status = -3; break; }
+        /* 2. forward transform of the six stress components */
+        for (int I = 0; I < 6; ++I) {
+            for (long v = 0; v < N3; ++v) s->spec[I * N3 + v] = sigk[I * N3 + v];
+            orc_fft3d(n, s->spec + I * N3, -1);
+        }
+        /* 3. residuals */
+        double acc = 0.0, mn = 0.0, mu_n = 0.0;
+        for (int I = 0; I < 6; ++I) mean[I] = creal(s->spec[I * N3]) / (double)N3;
+        for (int kz = 0; kz < n; ++kz)
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx < n; ++kx) {
+                    long v = kx + (long)n * (ky + (long)n * kz);
+                    double xi[3] = {2.0 * PI * freq(kx, n) / n, 2.0 * PI * freq(ky, n) / n, 2.0 * PI * freq(kz, n) / n};
+                    double complex T[3][3];
+                    for (int I = 0; I < 6; ++I) {
+                        T[MI[I]][MJ[I]] = s->spec[I * N3 + v] / mw(I);
+                        T[MJ[I]][MI[I]] = s->spec[I * N3 + v] / mw(I);
+                    }
+                    for (int i = 0; i < 3; ++i) {
+                        double complex dv = 0;
+                        for (int j = 0; j < 3; ++j) dv += xi[j] * T[i][j];
+                        acc += creal(dv) * creal(dv) + cimag(dv) * cimag(dv);
+                    }
+                }
+        for (int I = 0; I < 6; ++I) mn += mean[I] * mean[I];
+        for (int a = 0; a < 5; ++a) mu_n += mean[U[a]] * mean[U[a]];
+        double den = fmax(sqrt(mn), p->tau0);
+        err_eq = sqrt(acc) / ((double)N3 * den);
+        err_bc = sqrt(mu_n) / den;
+        if (!isfinite(err_eq) || !isfinite(err_bc)) { status = -5; break; }
+        if (err_eq <= s->cfg.tol && err_bc <= s->cfg.tol) { conv = 1; break; }
+        if (k == s->cfg.max_iter) break;
+        /* 5. macroscopic strain on the stress-controlled components */
+        double dEk[6] = {0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < 5; ++a) {
+            double v = 0.0;
+            for (int b = 0; b < 5; ++b) v += C0uu_inv[5 * a + b] * (0.0 - mean[U[b]]);
+            dEk[U[a]] = v;
+        }
+        for (int I = 0; I < 6; ++I) dE[I] += dEk[I];
+        /* 6. Green-operator correction */
+        for (int kz = 0; kz < n; ++kz)
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx < n; ++kx) {
+                    long v = kx + (long)n * (ky + (long)n * kz);
+                    double complex sh[6], eh[6];
+                    for (int I = 0; I < 6; ++I) sh[I] = s->spec[I * N3 + v];
+                    if (kx == 0 && ky == 0 && kz == 0) {
+                        for (int I = 0; I < 6; ++I) eh[I] = 0;
+                    } else {
+                        double Gm[36];
+                        int nyq = (n > 1) && (kx == n / 2 || ky == n / 2 || kz == n / 2);
+                        if (nyq) memcpy(Gm, S0, sizeof Gm);
+                        else {
+                            double xi[3] = {freq(kx, n), freq(ky, n), freq(kz, n)};
+                            orc_gamma0(xi, lam0, mu0, Gm);
+                        }
+                        for (int I = 0; I < 6; ++I) {
+                            double complex a = 0;
+                            for (int J = 0; J < 6; ++J) a += Gm[6 * I + J] * sh[J];
+                            eh[I] = -a;
+                        }
+                    }
+                    for (int I = 0; I < 6; ++I) s->spec[I * N3 + v] = eh[I];
+                }
+        for (int I = 0; I < 6; ++I) {
+            orc_fft3d(n, s->spec + I * N3, +1);
+            for (long v = 0; v < N3; ++v) epsk[I * N3 + v] += creal(s->spec[I * N3 + v]) / (double)N3 + dEk[I];
+        }
+    }
+    out->iterations = k > s->cfg.max_iter ? s->cfg.max_iter : k;
+    out->newton_max_iters = newton_max;
+    out->err_eq = err_eq;
+    out->err_bc = err_bc;
+    memcpy(out->sig_mean, mean, sizeof mean);
+    if (status == 0 && !conv) status = s->cfg.allow_unconverged ? 1 : -4;
+    if (status < 0) {
+        for (int I = 0; I < 6; ++I) out->E[I] = s->E[I] + dE[I];
+        out->status = status;
+        free(tauc);
+        return status;
+    }
+    /* a7: state update with the converged stress */
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < N3; ++v) {
+        int gr = s->g0[v];
+        const double *M = s->M + 72 * gr;
+        double gd[12], rho[12];
+        for (int a = 0; a < 12; ++a) {
+            double tau = 0.0;
+            for (int I = 0; I < 6; ++I) tau += M[6 * a + I] * sigk[I * N3 + v];
+            double x = tau / tauc[v], ax = fabs(x);
+            gd[a] = ax > 0.0 ? p->gdot0 * pow(ax, p->n) * (x < 0.0 ? -1.0 : 1.0) : 0.0;
+        }
+        for (int I = 0; I < 6; ++I) {
+            double ep = 0.0;
+            for (int a = 0; a < 12; ++a) ep += M[6 * a + I] * gd[a];
+            s->epsp[I * N3 + v] += dt * ep;
+        }
+        for (int a = 0; a < 12; ++a) rho[a] = s->rho[a * N3 + v];
+        orc_km_update(p, rho, gd, dt);
+        double kk = 0.0;
+        for (int a = 0; a < 12; ++a) { s->rho[a * N3 + v] = rho[a]; kk += rho[a]; }
+        s->k[v] = kk;
+        for (int I = 0; I < 6; ++I) {
+            s->deps_prev[I * N3 + v] = epsk[I * N3 + v] - s->eps[I * N3 + v];
+            s->eps[I * N3 + v] = epsk[I * N3 + v];
+            s->sig[I * N3 + v] = sigk[I * N3 + v];
+        }
+    }
+    for (int I = 0; I < 6; ++I) { s->E[I] += dE[I]; s->dE_prev[I] = dE[I]; }
+    s->have_prev = 1;
+    memcpy(out->E, s->E, sizeof s->E);
+    out->status = status;
+    free(tauc);
+    return status;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * a8: stochastic DRX nucleation (Sec. 2.3 and Appendix). A grain-boundary voxel (a face
+ * neighbour carries another grain id) nucleates iff k(x) = rho_tot(x) > kappa(x)
+ * (Eq. TotDislocationDensity). Nuclei get fresh ids in ascending voxel order; the voxel's
+ * order parameters become {(new id, 1)}, its densities are softened by s_soften (Eq. UpdateGND
+ * read for a single density family) and kappa is redrawn with k_c' = s_nucl k_c.
+ * ---------------------------------------------------------------------------------------- */
+static long nbr(int n, long v, int dir) {
+    int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
+    switch (dir) {
+        case 0: x = (x + n - 1) % n; break;
+        case 1: x = (x + 1) % n; break;
+        case 2: y = (y + n - 1) % n; break;
+        case 3: y = (y + 1) % n; break;
+        case 4: z = (z + n - 1) % n; break;
+        default: z = (z + 1) % n; break;
+    }
+    return x + (long)n * (y + (long)n * z);
+}
+
+int orc_nucleate(orc_state *s, uint64_t step, int32_t *n_new) {
+    (void)step;
+    const long N3 = s->N3;
+    const orc_params *p = &s->p;
+    unsigned char *mark = (unsigned char *)xcalloc(N3, 1);
+    for (long v = 0; v < N3; ++v) {
+        int gb = 0;
+        for (int d = 0; d < 6; ++d)
+            if (s->g[nbr(s->n, v, d)] != s->g[v]) gb = 1;
+        mark[v] = (unsigned char)(gb && s->k[v] > s->kappa[v]);
+    }
+    int cnt = 0;
+    for (long v = 0; v < N3; ++v) {
+        if (!mark[v]) continue;
+        int id = s->next_id + cnt++;
+        for (int j = 0; j < s->K; ++j) { s->ids[j * N3 + v] = -1; s->eta[j * N3 + v] = 0.0; }
+        s->ids[v] = id;
+        s->eta[v] = 1.0;
+        s->g[v] = id;
+        double kk = 0.0;
+        for (int a = 0; a < 12; ++a) {
+            s->rho[a * N3 + v] = p->s_soften * s->rho[a * N3 + v];
+            kk += s->rho[a * N3 + v];
+        }
+        s->k[v] = kk;
+        s->draws[v] += 1;
+        s->kappa[v] = orc_weibull(orc_u01(s->seed, (uint64_t)v, (uint64_t)s->draws[v]), p->s_nucl * p->kc, p->q);
+    }
+    s->next_id += cnt;
+    *n_new = cnt;
+    free(mark);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * a9: phase field (Sec. 2.4), grid-nondimensional (lengths in dx, energies in omega_gb/dx,
+ * time in dx^2/(M omega_gb)). One order parameter per grain id; ids < G are deformed grains,
+ * ids >= G recrystallised. Quantitative Moelans coefficients (interface width l, energy 1):
+ *   m = 6/l, kappa = 3l/4, gamma = 3/2  (Eq. GBEnergyDensity with the relations below it)
+ *   f0 = sum_i (eta_i^4/4 - eta_i^2/2) + gamma sum_{i<j} eta_i^2 eta_j^2 + 1/4
+ *   f_def = E' D/S, D = sum_def eta^2, R = sum_rex eta^2, S = D + R  (Eq. StoredEnergyDensity)
+ *   deta_i = -L dt [ m (eta_i^3 - eta_i + 2 gamma eta_i (S2 - eta_i^2)) - kappa lap(eta_i)
+ *                    + (def: 2E' eta_i R/S^2 | rex: -2E' eta_i D/S^2) ]       (Eq. PFGoverning)
+ * with a periodic 7-point Laplacian and explicit Euler. E' = zeta mu b^2 rho_tot dx / omega_gb.
+ * ---------------------------------------------------------------------------------------- */
+static double pf_E_scale(const orc_params *p) {
+    return p->zeta * (mu_voigt(p) * 1e6) * p->b * p->b * p->dx / p->omega_gb;
+}
+
+/* New value of one order parameter from its value at x, its six neighbours, the local sums
+ * and the local driving force; the order of operations is fixed (documented above). */
+static double pf_update_one(const orc_params *p, int is_def, double e0, const double nb[6], double S2,
+                            double D, double R, double Ep) {
+    const double l = p->l_gb, m = 6.0 / l, kap = 0.75 * l, gam = 1.5;
+    double lap = nb[0] + nb[1] + nb[2] + nb[3] + nb[4] + nb[5] - 6.0 * e0;
+    double df0 = m * (e0 * e0 * e0 - e0 + 2.0 * gam * e0 * (S2 - e0 * e0));
+    double S = D + R, ddef = 0.0;
+    if (S > 1e-12) ddef = is_def ? 2.0 * Ep * e0 * R / (S * S) : -2.0 * Ep * e0 * D / (S * S);
+    return e0 - p->L_dt * (df0 - kap * lap + ddef);
+}
+
+static double eta_at(const orc_state *s, const int32_t *ids, const double *eta, long v, int id) {
+    for (int j = 0; j < s->K; ++j)
+        if (ids[j * s->N3 + v] == id) return eta[j * s->N3 + v];
+    return 0.0;
+}
+
+static int cmp_int(const void *a, const void *b) {
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+typedef struct { int id; double e; } cand_t;
+static int cmp_keep(const void *a, const void *b) { /* eta descending, then id ascending */
+    const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+    if (x->e > y->e) return -1;
+    if (x->e < y->e) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+static int cmp_id(const void *a, const void *b) {
+    const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+static void pf_one_step(orc_state *s, int *overflow) {
+    const long N3 = s->N3;
+    const int K = s->K, G = s->G;
+    const double Esc = pf_E_scale(&s->p);
+    int ovf = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : ovf)
+    for (long v = 0; v < N3; ++v) {
+        long nv[6];
+        for (int d = 0; d < 6; ++d) nv[d] = nbr(s->n, v, d);
+        int cand[7 * 64];
+        int nc = 0;
+        long src[7] = {v, nv[0], nv[1], nv[2], nv[3], nv[4], nv[5]};
+        for (int q = 0; q < 7; ++q)
+            for (int j = 0; j < K; ++j) {
+                int id = s->ids[j * N3 + src[q]];
+                if (id >= 0) cand[nc++] = id;
+            }
+        qsort(cand, nc, sizeof(int), cmp_int);
+        int nu = 0;
+        for (int i = 0; i < nc; ++i)
+            if (nu == 0 || cand[nu - 1] != cand[i]) cand[nu++] = cand[i];
+        /* local sums in ascending id order */
+        double S2 = 0.0, D = 0.0, R = 0.0;
+        double e0s[7 * 64];
+        for (int i = 0; i < nu; ++i) {
+            double e0 = eta_at(s, s->ids, s->eta, v, cand[i]);
+            e0s[i] = e0;
+            S2 += e0 * e0;
+            if (cand[i] < G) D += e0 * e0; else R += e0 * e0;
+        }
+        double Ep = Esc * s->k[v];
+        cand_t out[7 * 64];
+        int no = 0;
+        double best = -1e300;
+        int best_i = -1;
+        for (int i = 0; i < nu; ++i) {
+            double nb[6];
+            for (int d = 0; d < 6; ++d) nb[d] = eta_at(s, s->ids, s->eta, nv[d], cand[i]);
+            double en = pf_update_one(&s->p, cand[i] < G, e0s[i], nb, S2, D, R, Ep);
+            if (en > best) { best = en; best_i = i; }
+            if (en >= s->p.eta_drop) { out[no].id = cand[i]; out[no].e = en; ++no; }
+        }
+        if (no == 0 && best_i >= 0) { out[0].id = cand[best_i]; out[0].e = best; no = 1; }
+        qsort(out, no, sizeof(cand_t), cmp_keep);
+        if (no > K) { ovf += 1; no = K; }
+        qsort(out, no, sizeof(cand_t), cmp_id);
+        for (int j = 0; j < K; ++j) {
+            s->ids2[j * N3 + v] = j < no ? out[j].id : -1;
+            s->eta2[j * N3 + v] = j < no ? out[j].e : 0.0;
+        }
+    }
+    int32_t *ti = s->ids; s->ids = s->ids2; s->ids2 = ti;
+    double *te = s->eta; s->eta = s->eta2; s->eta2 = te;
+    *overflow += ovf;
+}
+
+/* grain id = argmax over the order parameters, ties to the smaller id (Sec. 2.4, last paragraph) */
+static void pf_argmax(orc_state *s) {
+    const long N3 = s->N3;
+    for (long v = 0; v < N3; ++v) {
+        int bi = -1;
+        double be = 0.0;
+        for (int j = 0; j < s->K; ++j) {
+            int id = s->ids[j * N3 + v];
+            if (id < 0) continue;
+            double e = s->eta[j * N3 + v];
+            if (bi < 0 || e > be || (e == be && id < bi)) { bi = id; be = e; }
+        }
+        s->g[v] = bi;
+    }
+}
+
+/* Discrete free energy whose gradient is the update above: bulk + forward-difference gradient
+ * energy over the periodic grid + stored energy (Eqs. TotalFreeEnergy, GBEnergyDensity,
+ * StoredEnergyDensity, nondimensional). */
+double orc_pf_energy(orc_state *s) {
+    const long N3 = s->N3;
+    const int K = s->K, G = s->G;
+    const double l = s->p.l_gb, m = 6.0 / l, kap = 0.75 * l, gam = 1.5, Esc = pf_E_scale(&s->p);
+    double F = 0.0;
+    for (long v = 0; v < N3; ++v) {
+        double f0 = 0.25, S2 = 0.0, D = 0.0;
+        for (int j = 0; j < K; ++j) {
+            int id = s->ids[j * N3 + v];
+            if (id < 0) continue;
+            double e = s->eta[j * N3 + v];
+            f0 += e * e * e * e / 4.0 - e * e / 2.0;
+            S2 += e * e;
+            if (id < G) D += e * e;
+            for (int i2 = j + 1; i2 < K; ++i2) {
+                if (s->ids[i2 * N3 + v] < 0) continue;
+                double e2 = s->eta[i2 * N3 + v];
+                f0 += gam * e * e * e2 * e2;
+            }
+        }
+        double fdef = S2 > 1e-12 ? Esc * s->k[v] * D / S2 : 0.0;
+        double grad = 0.0;
+        for (int d = 1; d < 6; d += 2) {
+            long w = nbr(s->n, v, d);
+            /* union of ids at v and w */
+            int u[128], nu = 0;
+            for (int j = 0; j < K; ++j) {
+                if (s->ids[j * N3 + v] >= 0) u[nu++] = s->ids[j * N3 + v];
+                if (s->ids[j * N3 + w] >= 0) u[nu++] = s->ids[j * N3 + w];
+            }
+            qsort(u, nu, sizeof(int), cmp_int);
+            for (int i = 0; i < nu; ++i) {
+                if (i > 0 && u[i] == u[i - 1]) continue;
+                double dv = eta_at(s, s->ids, s->eta, w, u[i]) - eta_at(s, s->ids, s->eta, v, u[i]);
+                grad += dv * dv;
+            }
+        }
+        F += m * f0 + 0.5 * kap * grad + fdef;
+    }
+    return F;
+}
+
+void orc_stats_now(orc_state *s, orc_pf_stats *out) {
+    const long N3 = s->N3;
+    long rex = 0;
+    unsigned char *seen = (unsigned char *)xcalloc((size_t)s->next_id + 1, 1);
+    int ng = 0;
+    for (long v = 0; v < N3; ++v) {
+        int g = s->g[v];
+        if (g >= s->G) ++rex;
+        if (g >= 0 && g <= s->next_id && !seen[g]) { seen[g] = 1; ++ng; }
+    }
+    free(seen);
+    out->X_rex = (double)rex / (double)N3;
+    out->n_grains = ng;
+    out->F_tot = orc_pf_energy(s);
+}
+
+int orc_pf_step(orc_state *s, int nsteps, orc_pf_stats *out) {
+    const long N3 = s->N3;
+    int32_t *gprev = (int32_t *)xcalloc(N3, sizeof(int32_t));
+    memcpy(gprev, s->g, N3 * sizeof(int32_t));
+    int ovf = 0;
+    for (int t = 0; t < nsteps; ++t) pf_one_step(s, &ovf);
+    if (nsteps > 0) pf_argmax(s);
+    /* sweep softening: a voxel whose grain changes from a deformed to a recrystallised one
+     * over this call has its densities scaled by s_soften (reading of Eq. UpdateGND) */
+    for (long v = 0; v < N3; ++v) {
+        if (gprev[v] < s->G && s->g[v] >= s->G) {
+            double kk = 0.0;
+            for (int a = 0; a < 12; ++a) {
+                s->rho[a * N3 + v] = s->p.s_soften * s->rho[a * N3 + v];
+                kk += s->rho[a * N3 + v];
+            }
+            s->k[v] = kk;
+        }
+    }
+    free(gprev);
+    if (out) {
+        orc_stats_now(s, out);
+        out->overflow = ovf;
+    }
+    return ovf > 0 ? 2 : 0;
+}
+
+/* Dense multi-order-parameter update (every id at every voxel, no active set): the same
+ * equations with the sums over all ids in ascending order. Used to pin the sparse update. */
+int orc_pf_step_dense(orc_state *s, int nsteps) {
+    const long N3 = s->N3;
+    const int NG = s->next_id, K = s->K, G = s->G;
+    const double Esc = pf_E_scale(&s->p);
+    double *eta = (double *)xcalloc((size_t)NG * N3, sizeof(double));
+    double *eta2 = (double *)xcalloc((size_t)NG * N3, sizeof(double));
+    for (long v = 0; v < N3; ++v)
+        for (int j = 0; j < K; ++j) {
+            int id = s->ids[j * N3 + v];
+            if (id >= 0) eta[(long)id * N3 + v] = s->eta[j * N3 + v];
+        }
+    for (int t = 0; t < nsteps; ++t) {
+        for (long v = 0; v < N3; ++v) {
+            double S2 = 0.0, D = 0.0, R = 0.0;
+            for (int i = 0; i < NG; ++i) {
+                double e = eta[(long)i * N3 + v];
+                S2 += e * e;
+                if (i < G) D += e * e; else R += e * e;
+            }
+            double Ep = Esc * s->k[v];
+            for (int i = 0; i < NG; ++i) {
+                double nb[6];
+                for (int d = 0; d < 6; ++d) nb[d] = eta[(long)i * N3 + nbr(s->n, v, d)];
+                eta2[(long)i * N3 + v] = pf_update_one(&s->p, i < G, eta[(long)i * N3 + v], nb, S2, D, R, Ep);
+            }
+        }
+        double *tt = eta; eta = eta2; eta2 = tt;
+    }
+    /* write back into the slot arrays: ids whose value is not exactly zero, ascending id */
+    for (long v = 0; v < N3; ++v) {
+        int j = 0;
+        for (int i = 0; i < NG && j < K; ++i) {
+            double e = eta[(long)i * N3 + v];
+            if (e != 0.0) { s->ids[j * N3 + v] = i; s->eta[j * N3 + v] = e; ++j; }
+        }
+        for (; j < K; ++j) { s->ids[j * N3 + v] = -1; s->eta[j * N3 + v] = 0.0; }
+    }
+    pf_argmax(s);
+    free(eta);
+    free(eta2);
+    return 0;
+}
