@@ -1,0 +1,408 @@
+"""Benchmark of the coupled FFT-EVP / phase-field DRX hot path on GB300.
+
+One step = one DRX increment of the 128^3 / 256-grain polycrystal: the converged Green-operator
+fixed point with per-voxel Newton (evp_increment), nucleation (drx_nucleate) and five phase-field
+steps (pf_step). Headline: FFT-EVP voxel-iterations/s in the FP32-mixed path; the FP64 path runs
+on the same seeded input for the precision comparison (macro stress error, voxel stress error,
+recrystallised fraction) and its own throughput.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl native|reference]
+
+Multi-GPU: the path has no exchange step in this build (replicas only), so each rank runs an
+independent replica; the value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1509_04953_gb300 import synth  # noqa: E402
+
+METRIC = "FFT-EVP voxel-iters/s + DRX increments/s at 128^3, FP32-mixed vs FP64 at <=1e-4"
+UNIT = "voxel-iterations/s"
+# per-kernel algorithmic bytes per voxel for one launch (FP32 / FP64 field words)
+NEWTON_FLOPS_EVAL = 1140      # FP operations of one residual+tangent+potential evaluation
+NEWTON_FLOPS_SOLVE = 160      # FP operations of one 6x6 Cholesky factorisation + two solves
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="cu128")
+    ap.add_argument("--fp64-steps", type=int, default=-1, help="FP64 comparison increments (-1 = warmup+steps)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
+    ap.add_argument("--tol64", type=float, default=1e-8, help="fixed-point tolerance of the FP64 path")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def workload_inputs(wl):
+    seeds = synth.voronoi_seeds(wl.n, wl.grains, wl.seed)
+    quat = synth.orientations(wl.grains, wl.seed)
+    return seeds, quat
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------------------------
+def run_steps(solver, steps, dE33, dt, pf_steps, torch, record=None):
+    """Run `steps` DRX increments; returns per-step (evp_ms, step_ms, iterations, stats)."""
+    out = []
+    st = solver.stream
+    for s in range(steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        rc, es = solver.increment(dE33, dt)
+        e1.record(st)
+        _, nn = solver.nucleate(s)
+        _, ps = solver.pf_step(pf_steps)
+        e2.record(st)
+        e2.synchronize()
+        out.append(dict(evp_ms=e0.elapsed_time(e1), step_ms=e0.elapsed_time(e2), it=es.iterations,
+                        sig33=es.sig_mean[2], nuclei=nn, X_rex=ps.X_rex, F=ps.F_tot, n_grains=ps.n_grains,
+                        rc=rc))
+    return out
+
+
+def native(args, ws, rank, local):
+    import torch
+    from paper_1509_04953_gb300 import build, evp
+    build.build()
+    torch.cuda.set_device(local)
+    wl = synth.WORKLOADS[args.workload]
+    mat = synth.Material()
+    seeds, quat = workload_inputs(wl)
+    g0 = evp.voronoi(wl.n, seeds).cpu().numpy()
+    N3 = wl.n ** 3
+    mixed = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="mixed", tol=args.tol, max_iter=5000)
+    # warm-up (untimed)
+    warm = run_steps(mixed, args.warmup, wl.dE33, wl.dt, wl.pf_steps, torch)
+    mixed.set_profiling(True)
+    mixed.kernel_times(reset=True)
+    l0 = mixed.launch_count()
+    n0 = mixed.newton_counts()
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    timed = run_steps(mixed, args.steps, wl.dE33, wl.dt, wl.pf_steps, torch)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(ws)
+    clk = clocks.stop()
+    ktimes = mixed.kernel_times(reset=True)
+    mixed.set_profiling(False)
+    launches = mixed.launch_count() - l0
+    n1 = mixed.newton_counts()
+    evp_s = sum(r["evp_ms"] for r in timed) / 1e3
+    step_s = sum(r["step_ms"] for r in timed) / 1e3
+    iters = sum(r["it"] for r in timed)
+    step_s_max = allreduce_max(step_s, ws)
+    evp_s_max = allreduce_max(evp_s, ws)
+    tot_iters = allreduce_sum(iters, ws)
+    value = N3 * tot_iters / evp_s_max
+    incs_per_s = ws * args.steps / step_s_max
+
+    res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+               ms_per_step=1e3 * step_s_max / args.steps, higher_is_better=True, scaling="weak",
+               vs_baseline=None, dtype="f32 fields/FFT/PF + f64 Newton solve and reductions", data="synthetic",
+               config={"workload": wl.name, "n": wl.n, "grains": wl.grains, "precision": "mixed",
+                       "tol": args.tol, "dE33": wl.dE33, "pf_steps": wl.pf_steps,
+                       "l2": "inputs larger than L2 (about 0.8 GB of fields per replica, no flush needed)",
+                       "parallelism": f"replicas x{ws}"},
+               drx_increments_per_s=incs_per_s,
+               fixed_point_iterations=[r["it"] for r in timed],
+               gpu_launches=int(launches), clocks=clk)
+    # roofline of the dominant kernel class
+    pk, pk_kind = peaks()
+    res["kernel_ms"] = {k: round(v[0], 3) for k, v in ktimes.items() if v[1]}
+    res["kernel_launches"] = {k: v[1] for k, v in ktimes.items() if v[1]}
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    solves, evals = n1[0] - n0[0], n1[1] - n0[1]
+    res["newton"] = {"solves": solves, "evals": evals, "solves_per_voxel_iter": solves / (N3 * iters),
+                     "evals_per_voxel_iter": evals / (N3 * iters)}
+    res["roofline"] = roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision="mixed")
+    # FP64 companion run on the same seeded input
+    n64 = args.warmup + args.steps if args.fp64_steps < 0 else args.fp64_steps
+    if n64 > 0:
+        res["fp64"] = fp64_companion(args, wl, g0, quat, mat, n64, warm + timed, torch, evp)
+    if not args.no_e2e:
+        res["e2e"] = e2e(mixed, wl, torch, evp)
+    del mixed
+    return res
+
+
+def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision):
+    ms, n = ktimes[dom]
+    avg_s = ms / 1e3 / max(n, 1)
+    T = 4 if precision != "fp64" else 8
+    Hw = (wl.n // 2 + 1) / wl.n    # half-spectrum words per real word
+    bytes_per_voxel = {
+        "fft_x_r2c": (6 + 6 * Hw * 2) * T, "fft_y_fwd": 2 * 6 * Hw * 2 * T, "fft_z_gamma": 2 * 6 * Hw * 2 * T,
+        "fft_y_inv": 2 * 6 * Hw * 2 * T, "fft_x_c2r_update": (6 * Hw * 2 + 12) * T,
+        "predictor": (12 + 18 + 7) * T, "state_update": (6 + 1 + 1 + 6 + 6 * 4 + 24) * T + 8,
+        "pf_step": 2 * 8 * (4 + T) + 8,
+    }
+    if dom == "newton":
+        flops = NEWTON_FLOPS_EVAL * evals + NEWTON_FLOPS_SOLVE * solves
+        achieved = flops / (ms / 1e3) / 1e12
+        # FP32 vector peak: 152 SMs x 128 lanes x 2 flop x max clock (2070 MHz)
+        peak = 152 * 128 * 2 * 2.070e9 / 1e12 if precision != "fp64" else 1.25
+        return {"bound": "alu", "kernel": "newton", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": "algorithmic flops = 1140 x evaluations + 160 x 6x6 solves; peak derived from unit counts"
+                        " and max clock (FP32 when mixed, FP64 nominal when fp64)"}
+    b = bytes_per_voxel.get(dom, 0.0) * N3
+    achieved = b / avg_s / 1e9
+    peak = pk.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": pk_kind}
+
+
+def fp64_companion(args, wl, g0, quat, mat, nsteps, mixed_hist, torch, evp):
+    s64 = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="fp64", tol=args.tol64, max_iter=5000)
+    h = run_steps(s64, nsteps, wl.dE33, wl.dt, wl.pf_steps, torch)
+    N3 = wl.n ** 3
+    m = mixed_hist[:nsteps]
+    errs = [abs(a["sig33"] - b["sig33"]) / abs(b["sig33"]) for a, b in zip(m, h)]
+    evp_s = sum(r["evp_ms"] for r in h) / 1e3
+    step_s = sum(r["step_ms"] for r in h) / 1e3
+    out = {"voxel_iters_per_s": N3 * sum(r["it"] for r in h) / evp_s, "drx_increments_per_s": nsteps / step_s,
+           "ms_per_step": 1e3 * step_s / nsteps, "increments": nsteps,
+           "fixed_point_iterations": [r["it"] for r in h], "tol": args.tol64,
+           "mixed_vs_fp64_macro_stress_rel_err_max": max(errs),
+           "X_rex_abs_diff_max": max(abs(a["X_rex"] - b["X_rex"]) for a, b in zip(m, h))}
+    return out
+
+
+def e2e(solver, wl, torch, evp):
+    """Same metric through the public C ABI with the state in pinned host memory: every step
+    uploads the state fields, runs the increment, nucleation and PF, and downloads them again."""
+    names = ["sig", "epse", "epsp", "deps", "rho", "kappa", "g", "draws", "ids", "eta"]
+    host = {k: torch.from_numpy(solver.get(k)).pin_memory() for k in names}
+    L = evp.load()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    steps = 2
+    st = solver.stream
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters = 0
+    e0.record(st)
+    for s in range(steps):
+        for k in names:
+            t = host[k]
+            L.set_fields(solver.h, evp.FIELDS[k], t.data_ptr(), t.numel() * t.element_size(), 0)
+        _, es = solver.increment(wl.dE33, wl.dt)
+        iters += es.iterations
+        solver.nucleate(100 + s)
+        solver.pf_step(wl.pf_steps)
+        for k in names:
+            t = host[k]
+            L.get_fields(solver.h, evp.FIELDS[k], t.data_ptr(), t.numel() * t.element_size(), 0)
+    e1.record(st)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    return {"value": wl.n ** 3 * iters / secs, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+            "steps": steps, "drx_increments_per_s": steps / secs,
+            "note": "state round-trips through pinned host memory every step via set_fields/get_fields"}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(wl, iters_cap, nthreads=0):
+    """Time the FP64 oracle on the workload: one increment capped at `iters_cap` fixed-point
+    iterations (a bounded sample), then nucleation and the phase-field steps."""
+    import oracle as O
+    mat = synth.Material()
+    seeds, quat = workload_inputs(wl)
+    g0 = O.voronoi(wl.n, seeds)
+    st = O.State(wl.n, wl.grains, g0, quat, mat, seed=wl.seed, tol=0.0, max_iter=iters_cap, allow_unconverged=1,
+                 nthreads=nthreads)
+    t0 = time.perf_counter()
+    rc, s = st.increment(wl.dE33, wl.dt)
+    t1 = time.perf_counter()
+    st.nucleate(0)
+    st.pf_step(wl.pf_steps)
+    t2 = time.perf_counter()
+    st.close()
+    return dict(evp_s=t1 - t0, step_s=t2 - t0, iters=s.iterations)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline(wl):
+    cores = cpu_cores()
+    r = oracle_sample(wl, 2)
+    return {"value": wl.n ** 3 * r["iters"] / r["evp_s"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one {wl.n}^3 increment capped at {r['iters']} fixed-point iterations (FP64, OpenMP over"
+                      f" voxels), {r['evp_s']:.1f} s"}
+
+
+def reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    wl = synth.WORKLOADS[args.workload]
+    cores = cpu_cores()
+    for _ in range(args.warmup):
+        oracle_sample(wl, 1)
+    evp_s = step_s = 0.0
+    iters = 0
+    for _ in range(args.steps):
+        r = oracle_sample(wl, 1)
+        evp_s += r["evp_s"]
+        step_s += r["step_s"]
+        iters += r["iters"]
+    value = wl.n ** 3 * iters / evp_s
+    return dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * step_s / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config={"workload": wl.name, "n": wl.n, "grains": wl.grains, "precision": "fp64 (CPU oracle)"},
+                cpu_baseline={"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
+                              "sample": f"each step: one {wl.n}^3 increment capped at 1 fixed-point iteration,"
+                                        f" nucleation and {wl.pf_steps} phase-field steps"},
+                e2e={"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                drx_increments_per_s=None)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        res = reference(args, ws, rank)
+    else:
+        res = native(args, ws, rank, local)
+        if rank == 0 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(synth.WORKLOADS[args.workload])
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

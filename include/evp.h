@@ -1,0 +1,192 @@
+/*
+ * evp.h -- C ABI of the GB300 (sm_103a) coupled FFT-EVP / phase-field DRX hot path.
+ *
+ * Method: Zhao, Low, Wang, Niezgoda, "Integrated full-field dislocation-based modeling of
+ * dynamic recrystallization" (arXiv:1509.04953). Section references below are to that paper.
+ *
+ * Conventions
+ *  - Every call returns an int status: 0 = OK, > 0 = warning, < 0 = error (EVP_ERR_*).
+ *    No call aborts, traps or prints. evp_last_error() gives a one-line reason.
+ *  - The library never allocates device memory. The caller sizes one device workspace with
+ *    evp_workspace_bytes() and passes it to evp_init(); it stays owned by the caller and must
+ *    outlive the handle. The handle itself is a small host object freed by evp_destroy().
+ *  - All device work is enqueued on the stream given to evp_init (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream). Calls that return host values synchronise that
+ *    stream before returning.
+ *  - Units: stress MPa, lengths m, densities 1/m^2, time s. Symmetric tensors are Mandel
+ *    6-vectors (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12).
+ *  - Fields are structure-of-arrays over the N^3 grid with linear index v = x + N*(y + N*z),
+ *    component-major: component c of voxel v sits at c*N^3 + v.
+ *  - N must be a power of two, 4 <= N <= 256.
+ */
+#ifndef EVP_GB300_H
+#define EVP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define EVP_OK 0
+#define EVP_WARN_UNCONVERGED 1   /* fixed point stopped at max_iter (allow_unconverged = 1) */
+#define EVP_WARN_OVERFLOW 2      /* an active set had more than kmax members; smallest dropped */
+#define EVP_ERR_ARG (-1)         /* bad argument, size or pointer */
+#define EVP_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define EVP_ERR_NEWTON (-3)      /* a voxel's local Newton did not converge */
+#define EVP_ERR_FIXEDPOINT (-4)  /* the Green-operator fixed point did not converge */
+#define EVP_ERR_NONFINITE (-5)   /* NaN or Inf in the residual reduction */
+#define EVP_ERR_OOM (-6)         /* workspace smaller than evp_workspace_bytes() / id space full */
+
+/* precision of the field arithmetic */
+#define EVP_FP64 0   /* every field, FFT and solve in FP64 */
+#define EVP_MIXED 1  /* FP32 fields, FFTs and phase field; FP64 local Newton solve and FP64 macro
+                        reductions (norms, mean stress, residuals, nucleation decision) */
+#define EVP_MIXED_FAST 2  /* as EVP_MIXED, but the 6x6 Newton solve runs in FP32 too */
+
+typedef struct {
+    int n;                 /* grid points per edge */
+    int grains;            /* number of initial (deformed) grains G; ids 0..G-1 */
+    int kmax;              /* order parameters kept per voxel, 1..8 (active set, Sec. 2.4) */
+    int precision;         /* EVP_FP64 / EVP_MIXED / EVP_MIXED_FAST */
+    double tol;            /* fixed-point tolerance on err_eq and err_bc */
+    int max_iter;          /* fixed-point iteration cap per increment */
+    int allow_unconverged; /* 1: finish an increment at max_iter with EVP_WARN_UNCONVERGED */
+    double newton_tol;     /* local Newton: stop when |d sigma| <= newton_tol (|sigma| + tau_c) */
+    int newton_max;        /* local Newton iteration cap */
+    int predictor;         /* 1: start each increment from the previous strain-increment field */
+    int max_ids;           /* capacity of the grain-id space (>= grains); 0 = grains + 8 N^3 */
+} evp_config;
+
+typedef struct {
+    double C11, C12, C44;        /* cubic elastic constants, MPa */
+    double gdot0, n;             /* power-law flow rule gdot = gdot0 |tau/tau_c|^n sign(tau) */
+    double tau0, alpha, b;       /* tau_c = tau0 + alpha mu b sqrt(sum_a rho^a), mu = Voigt average */
+    double k1, k2, rho0;         /* Kocks-Mecking storage / recovery, initial density per system */
+    double zeta;                 /* stored energy E = zeta mu b^2 rho_tot (Sec. 2.4) */
+    double kc, q, s_nucl, s_soften; /* Weibull nucleation strength and DRX updates (Table 2) */
+    double omega_gb, dx, l_gb, L_dt, eta_drop; /* phase field: energy, spacing, width (in dx),
+                                                  mobility x time step, active-set drop level */
+} evp_params;
+
+typedef struct {
+    int iterations;        /* fixed-point iterations of the increment */
+    int newton_max_iters;  /* largest local Newton count seen */
+    int status;
+    double err_eq;         /* sqrt(sum_xi |xi.sigma_hat|^2)/|sigma_hat(0)|, xi = 2 pi k/N */
+    double err_bc;         /* |<sigma>_u|/|<sigma>| over the stress-controlled components */
+    double sig_mean[6];    /* volume-average stress (Mandel) */
+    double E[6];           /* macroscopic strain after the increment (Mandel) */
+} evp_stats;
+
+typedef struct {
+    double F_tot;          /* discrete phase-field free energy (nondimensional) */
+    double X_rex;          /* fraction of voxels whose grain id is recrystallised (id >= G) */
+    int n_grains;          /* number of distinct grain ids present */
+    int overflow;          /* voxel-steps whose active set was truncated to kmax */
+} pf_stats;
+
+typedef struct evp_handle evp_handle;
+
+/* field masks for get_fields / set_fields; fields are packed in this bit order, each as
+ * (components x N^3) of the type given ("T" = double in EVP_FP64, float otherwise) */
+#define EVP_F_SIG   (1u << 0)   /* stress, 6 x T */
+#define EVP_F_EPS   (1u << 1)   /* total strain eps = eps_e + eps_p, 6 x T (get only) */
+#define EVP_F_EPSP  (1u << 2)   /* plastic strain, 6 x T */
+#define EVP_F_EPSE  (1u << 3)   /* elastic strain eps - eps_p, 6 x T */
+#define EVP_F_DEPS  (1u << 4)   /* strain increment of the last increment, 6 x T */
+#define EVP_F_RHO   (1u << 5)   /* dislocation density per slip system, 12 x T */
+#define EVP_F_K     (1u << 6)   /* rho_tot = nucleation propensity k, 1 x double */
+#define EVP_F_KAPPA (1u << 7)   /* nucleation strength kappa, 1 x double */
+#define EVP_F_GRAIN (1u << 8)   /* current grain id (argmax order parameter), 1 x int32 */
+#define EVP_F_G0    (1u << 9)   /* initial grain id (orientation index), 1 x int32 (get only) */
+#define EVP_F_DRAWS (1u << 10)  /* kappa draws so far, 1 x int32 */
+#define EVP_F_IDS   (1u << 11)  /* active-set ids, kmax x int32 (slot-major, -1 = empty) */
+#define EVP_F_ETA   (1u << 12)  /* active-set order parameters, kmax x T */
+
+/* Bytes of device workspace evp_init needs for this configuration. */
+int evp_workspace_bytes(const evp_config *cfg, size_t *bytes);
+
+/* a1 + set-up (Sec. 2.1 and 3): copies the caller's host grain-id field (N^3 int32, ids in
+ * 0..G-1) and G unit quaternions (w,x,y,z; rotation crystal -> sample) to the device, builds
+ * the per-grain compliance and Schmid tables of the 12 FCC {111}<110> systems, sets
+ * rho^a = rho0, draws kappa ~ Weibull(q, kc) per voxel from a counter-based hash of
+ * (seed, voxel, draw) (Eqs. NumCrt, NuclStrengthProb) and sets one order parameter per voxel.
+ * The caller keeps ownership of its host arrays and of the workspace. */
+int evp_init(evp_handle **h, const evp_config *cfg, const evp_params *p, const int32_t *grain_id,
+             const double *quat, uint64_t seed, void *workspace, size_t workspace_bytes,
+             void *cuda_stream);
+
+/* a2-a7 (Sec. 2.1, Eqs. HookeLaw, PlasticRate; hardening and densities Sec. 2.2): one
+ * mechanical increment under mixed conditions -- E33 advances by dE33, the other mean stresses
+ * are driven to zero -- solved by the Green-operator fixed point with a per-voxel implicit
+ * Newton stress update, then the plastic strain, densities, tau_c and k = rho_tot are advanced.
+ * out may be NULL. Returns EVP_ERR_NEWTON / EVP_ERR_FIXEDPOINT / EVP_ERR_NONFINITE without
+ * advancing the state. */
+int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out);
+
+/* a8 (Sec. 2.3 with its Appendix, Eq. UpdateGND): stochastic nucleation. A voxel with a face
+ * neighbour of another grain nucleates iff k > kappa; nuclei receive fresh ids in ascending
+ * voxel order, a single order parameter 1, densities scaled by s_soften and a new kappa drawn
+ * with kc' = s_nucl kc. *n_new = nuclei created. step is recorded only (draws are counted per
+ * voxel), so results depend on the seed and the call history alone. */
+int drx_nucleate(evp_handle *h, uint64_t step, int32_t *n_new);
+
+/* a9-a10 (Sec. 2.4, Eqs. TotalFreeEnergy .. PFGoverning; sparse storage as cited there):
+ * nsteps explicit Allen-Cahn steps of the active-set multi-grain model, grain id = argmax,
+ * then densities of voxels swept from a deformed to a recrystallised grain are scaled by
+ * s_soften. out may be NULL (then F_tot and the statistics are not computed). */
+int pf_step(evp_handle *h, int nsteps, pf_stats *out);
+
+/* Copy the fields in field_mask, packed in bit order, to dst (host or device memory of
+ * exactly `bytes` bytes, see evp_fields_bytes). Synchronises the stream. */
+int get_fields(evp_handle *h, uint32_t field_mask, void *dst, size_t bytes, int dst_is_device);
+/* Overwrite state fields from src (same packing). EVP_F_EPS and EVP_F_G0 cannot be set.
+ * Setting EVP_F_RHO refreshes k = rho_tot. */
+int set_fields(evp_handle *h, uint32_t field_mask, const void *src, size_t bytes, int src_is_device);
+/* Bytes that get_fields / set_fields expect for field_mask. */
+int evp_fields_bytes(const evp_handle *h, uint32_t field_mask, size_t *bytes);
+
+/* Macroscopic scalars of the state, for checkpointing: E[6], dE_prev[6], have_prev, next_id. */
+int evp_get_scalars(const evp_handle *h, double *E6, double *dE_prev6, int *have_prev, int *next_id);
+int evp_set_scalars(evp_handle *h, const double *E6, const double *dE_prev6, int have_prev, int next_id);
+/* Change the fixed-point controls after init. */
+int evp_set_solver(evp_handle *h, double tol, int max_iter, int allow_unconverged);
+
+/* Instrumentation. Kernel launches are always counted. With profiling on (evp_set_profiling
+ * (h, 1)) every kernel launch is bracketed by CUDA events on the handle's stream and its device
+ * time is accumulated per kernel class. Classes: 0 newton, 1 fft_x_r2c, 2 fft_y_fwd,
+ * 3 fft_z_gamma, 4 fft_y_inv, 5 fft_x_c2r_update, 6 reduce, 7 predictor, 8 state_update,
+ * 9 nucleate, 10 pf_step, 11 pf_soften, 12 pf_stats. ms and launches hold EVP_NCLASS entries. */
+#define EVP_NCLASS 13
+int evp_set_profiling(evp_handle *h, int on);
+int evp_kernel_times(evp_handle *h, double *ms, int64_t *launches, int reset);
+int evp_launch_count(const evp_handle *h, int64_t *launches);
+/* Running totals over all increments: local Newton iterations (one 6x6 solve each) and
+ * evaluations of the residual, tangent and potential (including backtracking trials). */
+int evp_newton_counts(const evp_handle *h, int64_t *solves, int64_t *evals);
+
+void evp_destroy(evp_handle *h);
+const char *evp_last_error(const evp_handle *h);
+
+/* ---- stand-alone primitives (same kernels as the increment; used for parity tests) ---- */
+
+/* a1: periodic Voronoi grain ids. seeds: G x 3 int64 on the sub-grid [0, N*2^16)^3 (device);
+ * voxel centres sit at i*2^16 + 2^15; nearest seed by exact integer squared periodic distance,
+ * ties to the smaller index. ids: N^3 int32 (device). */
+int evp_voronoi(int n, int grains, const int64_t *seeds_dev, int32_t *ids_dev, void *cuda_stream);
+
+/* a3: forward 3D real-to-complex transform of `nfields` real N^3 fields (double if precision
+ * == EVP_FP64, else float; device) into half spectra [field][kz][ky][kx], kx = 0..N/2
+ * (interleaved complex of the same type; device). Unnormalised, exp(-2 pi i k.x/N).
+ * Needs no scratch: the y and z passes run in place in out. */
+int evp_rfft3d(int n, int precision, int nfields, const void *in_dev, void *out_dev, void *cuda_stream);
+/* inverse (complex-to-real) of evp_rfft3d, unnormalised: out = N^3 * field. in is overwritten. */
+int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

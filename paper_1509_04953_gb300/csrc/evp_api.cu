@@ -1,0 +1,779 @@
+// C ABI of libevp_gb300 (declared in include/evp.h): handle, workspace layout, increment driver,
+// nucleation and phase-field entry points, field I/O. All device work is enqueued on the
+// handle's stream; the library never allocates device memory.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/evp.h"
+#include "kernels.h"
+
+using namespace evp;
+
+struct evp_handle {
+    evp_config cfg;
+    evp_params p;
+    int n, G, K, prec;
+    long N3;
+    long H;          // half-spectrum points per field
+    int dbl;         // 1: fields are double
+    size_t tsz;      // sizeof(field type)
+    cudaStream_t st;
+    char *ws;
+    size_t ws_bytes;
+    // fields
+    void *sig, *sigk, *epse, *epst, *epsp, *deps, *rho, *tauc, *eta, *eta2, *spec, *Stab, *Mtab;
+    double *k, *kappa, *partials, *scal;
+    int32_t *g0, *g, *gprev, *draws, *ids, *ids2, *flags, *blk_counts, *blk_off, *count;
+    uint32_t *bitmap;
+    int bitmap_words, max_ids, npartials;
+    // macroscopic state (host)
+    double E[6], dE_prev[6];
+    int have_prev, next_id;
+    uint64_t seed;
+    MatConst mc;
+    PFConst pc;
+    // instrumentation
+    int64_t launches;
+    int64_t newton_solves, newton_evals;
+    int prof;
+    double prof_ms[EVP_NCLASS];
+    int64_t prof_n[EVP_NCLASS];
+    struct Pend { int cls; cudaEvent_t a, b; };
+    Pend pend[64];
+    int npend;
+    cudaEvent_t pool[128];
+    int npool;
+    char err[512];
+    ~evp_handle() {
+        for (int i = 0; i < npend; ++i) { cudaEventDestroy(pend[i].a); cudaEventDestroy(pend[i].b); }
+        for (int i = 0; i < npool; ++i) cudaEventDestroy(pool[i]);
+    }
+};
+
+namespace {
+
+int fail(evp_handle *h, int code, const char *fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof h->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(h, EVP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+cudaEvent_t ev_get(evp_handle *h) {
+    if (h->npool > 0) return h->pool[--h->npool];
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+void ev_put(evp_handle *h, cudaEvent_t e) {
+    if (!e) return;
+    if (h->npool < 128) h->pool[h->npool++] = e;
+    else cudaEventDestroy(e);
+}
+// Accumulate the device time of every bracketed launch whose events have completed.
+void prof_collect(evp_handle *h) {
+    int keep = 0;
+    for (int i = 0; i < h->npend; ++i) {
+        auto &q = h->pend[i];
+        float ms = 0.f;
+        if (cudaEventQuery(q.b) == cudaSuccess && cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+            h->prof_ms[q.cls] += ms;
+            h->prof_n[q.cls] += 1;
+            ev_put(h, q.a);
+            ev_put(h, q.b);
+        } else {
+            h->pend[keep++] = q;
+        }
+    }
+    h->npend = keep;
+}
+struct ProfScope {
+    evp_handle *h;
+    int cls;
+    cudaEvent_t a = nullptr;
+    ProfScope(evp_handle *h_, int c, int nk) : h(h_), cls(c) {
+        h->launches += nk;
+        if (h->prof) {
+            if (h->npend >= 64) {
+                cudaStreamSynchronize(h->st);
+                prof_collect(h);
+            }
+            a = ev_get(h);
+            if (a) cudaEventRecord(a, h->st);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = ev_get(h);
+        if (!b) { ev_put(h, a); return; }
+        cudaEventRecord(b, h->st);
+        h->pend[h->npend++] = {cls, a, b};
+    }
+};
+#define PROF(cls, nk) ProfScope prof_scope(h, (cls), (nk))
+
+bool pow2(int n) { return n >= 4 && n <= 256 && (n & (n - 1)) == 0; }
+
+int check_cfg(const evp_config *c, char *why, size_t wl) {
+    if (!c) return snprintf(why, wl, "config is NULL"), EVP_ERR_ARG;
+    if (!pow2(c->n)) return snprintf(why, wl, "n=%d must be a power of two in [4,256]", c->n), EVP_ERR_ARG;
+    if (c->grains < 1) return snprintf(why, wl, "grains=%d must be >= 1", c->grains), EVP_ERR_ARG;
+    if (c->kmax < 1 || c->kmax > 8) return snprintf(why, wl, "kmax=%d must be in [1,8]", c->kmax), EVP_ERR_ARG;
+    if (c->precision < EVP_FP64 || c->precision > EVP_MIXED_FAST)
+        return snprintf(why, wl, "unknown precision %d", c->precision), EVP_ERR_ARG;
+    if (c->max_iter < 1 || c->newton_max < 1) return snprintf(why, wl, "iteration caps must be >= 1"), EVP_ERR_ARG;
+    if (!(c->tol >= 0.0) || !(c->newton_tol > 0.0)) return snprintf(why, wl, "tolerances must be >= 0"), EVP_ERR_ARG;
+    if (c->max_ids != 0 && c->max_ids < c->grains) return snprintf(why, wl, "max_ids < grains"), EVP_ERR_ARG;
+    return EVP_OK;
+}
+
+// Walk the workspace in a fixed order; assigns pointers when h != nullptr. 256-byte aligned.
+size_t layout(const evp_config *c, evp_handle *h, char *base) {
+    const long n = c->n, N3 = n * n * n, H = n * n * (n / 2 + 1);
+    const size_t T = c->precision == EVP_FP64 ? 8 : 4;
+    const int K = c->kmax, G = c->grains;
+    const long max_ids = c->max_ids ? c->max_ids : (long)G + 8 * N3;
+    const int nb = nucleate_blocks(N3);
+    const int npart = std::max(fft_z_blocks((int)n, T == 8), 2 * pf_stat_blocks(N3) + 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        off = (off + 255) & ~(size_t)255;
+        char *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    char *sig = take(6 * N3 * T), *sigk = take(6 * N3 * T), *epse = take(6 * N3 * T), *epst = take(6 * N3 * T);
+    char *epsp = take(6 * N3 * T), *deps = take(6 * N3 * T), *rho = take(12 * N3 * T), *tauc = take(N3 * T);
+    char *eta = take(K * N3 * T), *eta2 = take(K * N3 * T), *spec = take(6 * H * 2 * T);
+    char *Stab = take(36 * (size_t)G * T), *Mtab = take(72 * (size_t)G * T);
+    char *k = take(N3 * 8), *kappa = take(N3 * 8);
+    char *g0 = take(N3 * 4), *g = take(N3 * 4), *gprev = take(N3 * 4), *draws = take(N3 * 4);
+    char *ids = take(K * N3 * 4), *ids2 = take(K * N3 * 4);
+    char *partials = take(sizeof(double) * npart), *scal = take(sizeof(double) * 64);
+    char *flags = take(sizeof(int32_t) * 16);
+    char *blk_counts = take(sizeof(int32_t) * nb);
+    char *blk_off = take(sizeof(int32_t) * nb + N3);   // offsets, then one mark byte per voxel
+    char *count = take(sizeof(int32_t) * 4);
+    const long words = (max_ids + 31) / 32;
+    char *bitmap = take(sizeof(uint32_t) * words);
+    if (h) {
+        h->sig = sig; h->sigk = sigk; h->epse = epse; h->epst = epst; h->epsp = epsp; h->deps = deps;
+        h->rho = rho; h->tauc = tauc; h->eta = eta; h->eta2 = eta2; h->spec = spec; h->Stab = Stab; h->Mtab = Mtab;
+        h->k = (double *)k; h->kappa = (double *)kappa; h->g0 = (int32_t *)g0; h->g = (int32_t *)g;
+        h->gprev = (int32_t *)gprev; h->draws = (int32_t *)draws; h->ids = (int32_t *)ids; h->ids2 = (int32_t *)ids2;
+        h->partials = (double *)partials; h->scal = (double *)scal; h->flags = (int32_t *)flags;
+        h->blk_counts = (int32_t *)blk_counts; h->blk_off = (int32_t *)blk_off; h->count = (int32_t *)count;
+        h->bitmap = (uint32_t *)bitmap; h->bitmap_words = (int)words; h->max_ids = (int)max_ids;
+        h->npartials = npart;
+    }
+    return (off + 255) & ~(size_t)255;
+}
+
+// ---- per-grain tables (sample frame), built on the host in the field precision ----
+const double kN4[4][3] = {{1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {1, 1, -1}};
+const double kD4[4][3][3] = {{{0, 1, -1}, {1, 0, -1}, {1, -1, 0}},
+                             {{0, 1, -1}, {1, 0, 1}, {1, 1, 0}},
+                             {{0, 1, 1}, {1, 0, -1}, {1, 1, 0}},
+                             {{0, 1, 1}, {1, 0, 1}, {1, -1, 0}}};
+const int kMi[6] = {0, 1, 2, 1, 0, 0}, kMj[6] = {0, 1, 2, 2, 2, 1};
+
+void tensor_to_mandel(const double T[3][3], double v[6]) {
+    const double r2 = std::sqrt(2.0);
+    for (int I = 0; I < 6; ++I) v[I] = (I < 3 ? 1.0 : r2) * T[kMi[I]][kMj[I]];
+}
+
+// 6x6 matrix Q with mandel(R A R^T) = Q mandel(A) for symmetric A.
+void mandel_rotation(const double R[3][3], double Q[6][6]) {
+    const double r2 = std::sqrt(2.0);
+    for (int J = 0; J < 6; ++J) {
+        double B[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const int i = kMi[J], j = kMj[J];
+        if (J < 3) B[i][j] = 1.0;
+        else { B[i][j] = 1.0 / r2; B[j][i] = 1.0 / r2; }
+        double RB[3][3], RBR[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                RB[a][b] = 0;
+                for (int c = 0; c < 3; ++c) RB[a][b] += R[a][c] * B[c][b];
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                RBR[a][b] = 0;
+                for (int c = 0; c < 3; ++c) RBR[a][b] += RB[a][c] * R[b][c];
+            }
+        double col[6];
+        tensor_to_mandel(RBR, col);
+        for (int I = 0; I < 6; ++I) Q[I][J] = col[I];
+    }
+}
+
+template <typename T> void build_tables(const evp_params *p, int G, const double *quat, T *S, T *M) {
+    const double den = (p->C11 - p->C12) * (p->C11 + 2.0 * p->C12);
+    double Sc[6][6] = {};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Sc[i][j] = i == j ? (p->C11 + p->C12) / den : -p->C12 / den;
+    for (int i = 3; i < 6; ++i) Sc[i][i] = 1.0 / (2.0 * p->C44);
+    double mc[12][6];
+    for (int pl = 0; pl < 4; ++pl)
+        for (int d = 0; d < 3; ++d) {
+            double nn[3], dd[3], Tm[3][3];
+            for (int c = 0; c < 3; ++c) {
+                nn[c] = kN4[pl][c] / std::sqrt(3.0);
+                dd[c] = kD4[pl][d][c] / std::sqrt(2.0);
+            }
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) Tm[a][b] = 0.5 * (dd[a] * nn[b] + dd[b] * nn[a]);
+            tensor_to_mandel(Tm, mc[3 * pl + d]);
+        }
+    for (int g = 0; g < G; ++g) {
+        const double *q = quat + 4 * g;
+        const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        const double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                                {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                                {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+        double Q[6][6];
+        mandel_rotation(R, Q);
+        double QS[6][6];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                QS[i][j] = 0;
+                for (int k = 0; k < 6; ++k) QS[i][j] += Q[i][k] * Sc[k][j];
+            }
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                double a = 0;
+                for (int k = 0; k < 6; ++k) a += QS[i][k] * Q[j][k];
+                S[36 * (size_t)g + 6 * i + j] = (T)a;
+            }
+        for (int a = 0; a < 12; ++a)
+            for (int i = 0; i < 6; ++i) {
+                double v = 0;
+                for (int k = 0; k < 6; ++k) v += Q[i][k] * mc[a][k];
+                M[72 * (size_t)g + 6 * a + i] = (T)v;
+            }
+    }
+}
+
+double voigt_mu(const evp_params *p) { return (p->C11 - p->C12 + 3.0 * p->C44) / 5.0; }
+double voigt_lam(const evp_params *p) { return (p->C11 + 4.0 * p->C12 - 2.0 * p->C44) / 5.0; }
+
+size_t field_bytes(const evp_handle *h, uint32_t bit) {
+    const size_t N3 = (size_t)h->N3, T = h->tsz, K = (size_t)h->K;
+    switch (bit) {
+        case EVP_F_SIG: case EVP_F_EPS: case EVP_F_EPSP: case EVP_F_EPSE: case EVP_F_DEPS: return 6 * N3 * T;
+        case EVP_F_RHO: return 12 * N3 * T;
+        case EVP_F_K: case EVP_F_KAPPA: return N3 * 8;
+        case EVP_F_GRAIN: case EVP_F_G0: case EVP_F_DRAWS: return N3 * 4;
+        case EVP_F_IDS: return K * N3 * 4;
+        case EVP_F_ETA: return K * N3 * T;
+        default: return 0;
+    }
+}
+
+void *field_ptr(evp_handle *h, uint32_t bit) {
+    switch (bit) {
+        case EVP_F_SIG: return h->sig;
+        case EVP_F_EPSP: return h->epsp;
+        case EVP_F_EPSE: return h->epse;
+        case EVP_F_DEPS: return h->deps;
+        case EVP_F_RHO: return h->rho;
+        case EVP_F_K: return h->k;
+        case EVP_F_KAPPA: return h->kappa;
+        case EVP_F_GRAIN: return h->g;
+        case EVP_F_G0: return h->g0;
+        case EVP_F_DRAWS: return h->draws;
+        case EVP_F_IDS: return h->ids;
+        case EVP_F_ETA: return h->eta;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int evp_workspace_bytes(const evp_config *cfg, size_t *bytes) {
+    char why[256];
+    const int rc = check_cfg(cfg, why, sizeof why);
+    if (rc) return rc;
+    if (!bytes) return EVP_ERR_ARG;
+    *bytes = layout(cfg, nullptr, nullptr);
+    return EVP_OK;
+}
+
+const char *evp_last_error(const evp_handle *h) { return h ? h->err : "no handle"; }
+
+void evp_destroy(evp_handle *h) { delete h; }
+
+int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const int32_t *grain_id, const double *quat,
+             uint64_t seed, void *workspace, size_t workspace_bytes, void *cuda_stream) {
+    if (!out) return EVP_ERR_ARG;
+    *out = nullptr;
+    evp_handle *h = new (std::nothrow) evp_handle();
+    if (!h) return EVP_ERR_OOM;
+    *out = h;
+    const int rc = check_cfg(cfg, h->err, sizeof h->err);
+    if (rc) return rc;
+    if (!p || !grain_id || !quat || !workspace) return fail(h, EVP_ERR_ARG, "NULL argument to evp_init");
+    if (((uintptr_t)workspace & 255) != 0) return fail(h, EVP_ERR_ARG, "workspace must be 256-byte aligned");
+    h->cfg = *cfg;
+    h->p = *p;
+    h->n = cfg->n;
+    h->G = cfg->grains;
+    h->K = cfg->kmax;
+    h->prec = cfg->precision;
+    h->N3 = (long)h->n * h->n * h->n;
+    h->H = (long)h->n * h->n * (h->n / 2 + 1);
+    h->dbl = h->prec == EVP_FP64;
+    h->tsz = h->dbl ? 8 : 4;
+    h->st = (cudaStream_t)cuda_stream;
+    const size_t need = layout(cfg, nullptr, nullptr);
+    if (workspace_bytes < need)
+        return fail(h, EVP_ERR_OOM, "workspace has %zu bytes, needs %zu", workspace_bytes, need);
+    h->ws = (char *)workspace;
+    h->ws_bytes = workspace_bytes;
+    layout(cfg, h, h->ws);
+    for (long v = 0; v < h->N3; ++v)
+        if (grain_id[v] < 0 || grain_id[v] >= h->G)
+            return fail(h, EVP_ERR_ARG, "grain_id[%ld]=%d outside [0,%d)", v, grain_id[v], h->G);
+    h->seed = seed;
+    h->next_id = h->G;
+    h->have_prev = 0;
+    for (int i = 0; i < 6; ++i) h->E[i] = h->dE_prev[i] = 0.0;
+    const double mu = voigt_mu(p), lam = voigt_lam(p);
+    h->mc.gdot0 = p->gdot0;
+    h->mc.n = p->n;
+    h->mc.dt = 1.0;
+    h->mc.tau0 = p->tau0;
+    h->mc.alpha_mu_b = p->alpha * mu * p->b;
+    h->mc.k1 = p->k1;
+    h->mc.k2 = p->k2;
+    h->mc.lam0 = lam;
+    h->mc.mu0 = mu;
+    h->mc.n_int = (p->n >= 1.0 && p->n <= 64.0 && p->n == std::floor(p->n)) ? (int)p->n : 0;
+    h->pc.m = 6.0 / p->l_gb;
+    h->pc.kappa = 0.75 * p->l_gb;
+    h->pc.gam = 1.5;
+    h->pc.L_dt = p->L_dt;
+    h->pc.Escale = p->zeta * (mu * 1e6) * p->b * p->b * p->dx / p->omega_gb;
+    h->pc.drop = p->eta_drop;
+    h->pc.G = h->G;
+    h->pc.K = h->K;
+    // tables
+    {
+        const size_t G = (size_t)h->G;
+        void *hS = std::malloc(36 * G * h->tsz), *hM = std::malloc(72 * G * h->tsz);
+        if (!hS || !hM) { std::free(hS); std::free(hM); return fail(h, EVP_ERR_OOM, "host allocation"); }
+        if (h->dbl) build_tables<double>(p, h->G, quat, (double *)hS, (double *)hM);
+        else build_tables<float>(p, h->G, quat, (float *)hS, (float *)hM);
+        cudaError_t e1 = cudaMemcpyAsync(h->Stab, hS, 36 * G * h->tsz, cudaMemcpyHostToDevice, h->st);
+        cudaError_t e2 = cudaMemcpyAsync(h->Mtab, hM, 72 * G * h->tsz, cudaMemcpyHostToDevice, h->st);
+        cudaError_t e3 = cudaStreamSynchronize(h->st);
+        std::free(hS);
+        std::free(hM);
+        CK(e1);
+        CK(e2);
+        CK(e3);
+    }
+    CK(cudaMemcpyAsync(h->g0, grain_id, sizeof(int32_t) * h->N3, cudaMemcpyHostToDevice, h->st));
+    const size_t fb = 6 * (size_t)h->N3 * h->tsz;
+    CK(cudaMemsetAsync(h->sig, 0, fb, h->st));
+    CK(cudaMemsetAsync(h->epse, 0, fb, h->st));
+    CK(cudaMemsetAsync(h->epsp, 0, fb, h->st));
+    CK(cudaMemsetAsync(h->deps, 0, fb, h->st));
+    if (h->dbl)
+        CK(drx_init<double>(h->N3, h->g0, (double *)h->rho, h->k, h->kappa, h->g, h->draws, h->ids, (double *)h->eta,
+                            h->K, p->rho0, p->kc, p->q, seed, h->st));
+    else
+        CK(drx_init<float>(h->N3, h->g0, (float *)h->rho, h->k, h->kappa, h->g, h->draws, h->ids, (float *)h->eta, h->K,
+                           p->rho0, p->kc, p->q, seed, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return EVP_OK;
+}
+
+int evp_set_profiling(evp_handle *h, int on) {
+    if (!h) return EVP_ERR_ARG;
+    h->prof = on ? 1 : 0;
+    return EVP_OK;
+}
+
+int evp_kernel_times(evp_handle *h, double *ms, int64_t *launches, int reset) {
+    if (!h) return EVP_ERR_ARG;
+    CK(cudaStreamSynchronize(h->st));
+    prof_collect(h);
+    for (int i = 0; i < EVP_NCLASS; ++i) {
+        if (ms) ms[i] = h->prof_ms[i];
+        if (launches) launches[i] = h->prof_n[i];
+        if (reset) { h->prof_ms[i] = 0.0; h->prof_n[i] = 0; }
+    }
+    return EVP_OK;
+}
+
+int evp_launch_count(const evp_handle *h, int64_t *launches) {
+    if (!h || !launches) return EVP_ERR_ARG;
+    *launches = h->launches;
+    return EVP_OK;
+}
+
+int evp_newton_counts(const evp_handle *h, int64_t *solves, int64_t *evals) {
+    if (!h) return EVP_ERR_ARG;
+    if (solves) *solves = h->newton_solves;
+    if (evals) *evals = h->newton_evals;
+    return EVP_OK;
+}
+
+int evp_set_solver(evp_handle *h, double tol, int max_iter, int allow_unconverged) {
+    if (!h || max_iter < 1 || !(tol >= 0.0)) return fail(h, EVP_ERR_ARG, "bad solver controls");
+    h->cfg.tol = tol;
+    h->cfg.max_iter = max_iter;
+    h->cfg.allow_unconverged = allow_unconverged;
+    return EVP_OK;
+}
+
+int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
+    if (!h) return EVP_ERR_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dE33)) return fail(h, EVP_ERR_ARG, "dt must be > 0 and dE33 finite");
+    const long N3 = h->N3;
+    const int n = h->n;
+    MatConst mc = h->mc;
+    mc.dt = dt;
+    const double lam0 = mc.lam0, mu0 = mc.mu0;
+    // predictor
+    double dE[6];
+    int use_field = 0;
+    double r = 0.0;
+    if (h->cfg.predictor && h->have_prev && h->dE_prev[2] != 0.0) {
+        r = dE33 / h->dE_prev[2];
+        for (int i = 0; i < 6; ++i) dE[i] = r * h->dE_prev[i];
+        dE[2] = dE33;
+        use_field = 1;
+    } else {
+        const double nu0 = lam0 / (2.0 * (lam0 + mu0));
+        const double g[6] = {-nu0 * dE33, -nu0 * dE33, dE33, 0, 0, 0};
+        for (int i = 0; i < 6; ++i) dE[i] = g[i];
+    }
+    const size_t fb = 6 * (size_t)N3 * h->tsz;
+    CK(cudaMemcpyAsync(h->sigk, h->sig, fb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemsetAsync(h->flags, 0, sizeof(int32_t) * 16, h->st));
+    {
+        PROF(7, 1);
+        if (h->dbl)
+            CK(predictor<double>(N3, (double *)h->epse, (double *)h->deps, (double *)h->rho, (double *)h->epst,
+                                 (double *)h->tauc, mc, r, dE, use_field, h->st));
+        else
+            CK(predictor<float>(N3, (float *)h->epse, (float *)h->deps, (float *)h->rho, (float *)h->epst,
+                                (float *)h->tauc, mc, r, dE, use_field, h->st));
+    }
+    // mixed-BC correction: (C0_uu)^-1 on u = {11, 22, 23, 13, 12}
+    const double a = lam0 + 2.0 * mu0, b = lam0, det = a * a - b * b;
+    const int solve64 = h->prec != EVP_MIXED_FAST;
+    const double ntol = h->cfg.newton_tol;
+    int status = EVP_OK, it = 0, conv = 0, nmax = 0;
+    double err_eq = 0, err_bc = 0, mean[6] = {0, 0, 0, 0, 0, 0};
+    const int zb = fft_z_blocks(n, h->dbl);
+    double hs[8];
+    int32_t hf[2];
+    int64_t hcount[2] = {0, 0};
+    for (it = 1; it <= h->cfg.max_iter; ++it) {
+        if (h->dbl) {
+          { PROF(0, 1);
+            CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
+                                    (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1, h->flags,
+                                    h->st)); }
+          { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st)); }
+          { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st)); }
+          { PROF(3, 1); CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st)); }
+        } else {
+          { PROF(0, 1);
+            CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk, (float *)h->Stab,
+                                   (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64, h->flags, h->st)); }
+          { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st)); }
+          { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st)); }
+          { PROF(3, 1); CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st)); }
+        }
+        { PROF(6, 1); CK(reduce_partials(h->partials, zb, 1, h->scal + 6, h->st)); }
+        CK(cudaMemcpyAsync(hs, h->scal, sizeof(double) * 7, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(hf, h->flags, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (h->prof) prof_collect(h);
+        nmax = hf[1] > nmax ? hf[1] : nmax;
+        if (hf[0] != 0) {
+            status = fail(h, EVP_ERR_NEWTON, "local Newton failed in %d voxels at iteration %d", hf[0], it);
+            break;
+        }
+        for (int i = 0; i < 6; ++i) mean[i] = hs[i];
+        double mn = 0, mu_n = 0;
+        for (int i = 0; i < 6; ++i) mn += mean[i] * mean[i];
+        mu_n = mn - mean[2] * mean[2];
+        const double den = std::fmax(std::sqrt(mn), h->p.tau0);
+        err_eq = std::sqrt(hs[6]) / ((double)N3 * den);
+        err_bc = std::sqrt(std::fmax(mu_n, 0.0)) / den;
+        if (!std::isfinite(err_eq) || !std::isfinite(err_bc)) {
+            status = fail(h, EVP_ERR_NONFINITE, "non-finite residual at iteration %d", it);
+            break;
+        }
+        if (err_eq <= h->cfg.tol && err_bc <= h->cfg.tol) { conv = 1; break; }
+        if (it == h->cfg.max_iter) break;
+        double dEk[6] = {0, 0, 0, 0, 0, 0};
+        dEk[0] = (a * (-mean[0]) - b * (-mean[1])) / det;
+        dEk[1] = (-b * (-mean[0]) + a * (-mean[1])) / det;
+        for (int i = 3; i < 6; ++i) dEk[i] = -mean[i] / (2.0 * mu0);
+        for (int i = 0; i < 6; ++i) dE[i] += dEk[i];
+        const double inv = 1.0 / (double)N3;
+        if (h->dbl) {
+            { PROF(4, 1); CK(fft_y<double>(h->spec, n, 6, 1, h->st)); }
+            { PROF(5, 1); CK(fft_x_c2r<double>(h->spec, (double *)h->epst, n, 6, inv, dEk, h->st)); }
+        } else {
+            { PROF(4, 1); CK(fft_y<float>(h->spec, n, 6, 1, h->st)); }
+            { PROF(5, 1); CK(fft_x_c2r<float>(h->spec, (float *)h->epst, n, 6, (float)inv, dEk, h->st)); }
+        }
+    }
+    if (it > h->cfg.max_iter) it = h->cfg.max_iter;
+    CK(cudaMemcpyAsync(hcount, h->flags + 4, sizeof hcount, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->newton_solves += hcount[0];
+    h->newton_evals += hcount[1];
+    if (status == EVP_OK && !conv) {
+        if (h->cfg.allow_unconverged) status = EVP_WARN_UNCONVERGED;
+        else status = fail(h, EVP_ERR_FIXEDPOINT, "fixed point not converged in %d iterations (err_eq %.3e, err_bc %.3e)",
+                           it, err_eq, err_bc);
+    }
+    if (out) {
+        out->iterations = it;
+        out->newton_max_iters = nmax;
+        out->status = status;
+        out->err_eq = err_eq;
+        out->err_bc = err_bc;
+        for (int i = 0; i < 6; ++i) {
+            out->sig_mean[i] = mean[i];
+            out->E[i] = h->E[i] + dE[i];
+        }
+    }
+    if (status < 0) return status;
+    { PROF(8, 1);
+    if (h->dbl)
+        CK(state_update<double>(N3, (double *)h->sigk, (double *)h->tauc, h->g0, (double *)h->Mtab, (double *)h->epst,
+                                (double *)h->epse, (double *)h->epsp, (double *)h->deps, (double *)h->rho, h->k, mc,
+                                h->st));
+    else
+        CK(state_update<float>(N3, (float *)h->sigk, (float *)h->tauc, h->g0, (float *)h->Mtab, (float *)h->epst,
+                               (float *)h->epse, (float *)h->epsp, (float *)h->deps, (float *)h->rho, h->k, mc, h->st));
+    }
+    void *t = h->sig;
+    h->sig = h->sigk;
+    h->sigk = t;
+    for (int i = 0; i < 6; ++i) {
+        h->E[i] += dE[i];
+        h->dE_prev[i] = dE[i];
+    }
+    h->have_prev = 1;
+    CK(cudaStreamSynchronize(h->st));
+    if (h->prof) prof_collect(h);
+    return status;
+}
+
+int drx_nucleate(evp_handle *h, uint64_t step, int32_t *n_new) {
+    (void)step;
+    if (!h || !n_new) return fail(h, EVP_ERR_ARG, "NULL argument to drx_nucleate");
+    const double kc_new = h->p.s_nucl * h->p.kc;
+    { PROF(9, 3);
+    if (h->dbl)
+        CK(nucleate<double>(h->n, h->K, h->g, h->g, h->k, h->kappa, (double *)h->rho, h->draws, h->ids,
+                            (double *)h->eta, h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften, kc_new,
+                            h->p.q, h->seed, h->st));
+    else
+        CK(nucleate<float>(h->n, h->K, h->g, h->g, h->k, h->kappa, (float *)h->rho, h->draws, h->ids, (float *)h->eta,
+                           h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften, kc_new, h->p.q, h->seed,
+                           h->st));
+    }
+    int32_t c = 0;
+    CK(cudaMemcpyAsync(&c, h->count, sizeof c, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (h->prof) prof_collect(h);
+    *n_new = c;
+    if ((long)h->next_id + c > (long)h->max_ids)
+        return fail(h, EVP_ERR_OOM, "grain-id space of %d exhausted", h->max_ids);
+    h->next_id += c;
+    return EVP_OK;
+}
+
+int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
+    if (!h || nsteps < 0) return fail(h, EVP_ERR_ARG, "bad pf_step arguments");
+    const long N3 = h->N3;
+    CK(cudaMemcpyAsync(h->gprev, h->g, sizeof(int32_t) * N3, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemsetAsync(h->flags + 2, 0, sizeof(int32_t), h->st));
+    for (int s = 0; s < nsteps; ++s) {
+        PROF(10, 1);
+        if (h->dbl)
+            CK(pf_one_step<double>(h->n, h->ids, (double *)h->eta, h->ids2, (double *)h->eta2, h->g, h->k, h->pc,
+                                   h->flags + 2, h->st));
+        else
+            CK(pf_one_step<float>(h->n, h->ids, (float *)h->eta, h->ids2, (float *)h->eta2, h->g, h->k, h->pc,
+                                  h->flags + 2, h->st));
+        int32_t *ti = h->ids; h->ids = h->ids2; h->ids2 = ti;
+        void *te = h->eta; h->eta = h->eta2; h->eta2 = te;
+    }
+    { PROF(11, 1);
+    if (h->dbl) CK(pf_soften<double>(N3, h->gprev, h->g, (double *)h->rho, h->k, h->G, h->p.s_soften, h->st));
+    else CK(pf_soften<float>(N3, h->gprev, h->g, (float *)h->rho, h->k, h->G, h->p.s_soften, h->st));
+    }
+    int32_t ovf = 0;
+    if (out) {
+        const int nb = pf_stat_blocks(N3);
+        { PROF(12, 3);
+        if (h->dbl)
+            CK(pf_stats_launch<double>(h->n, h->ids, (double *)h->eta, h->g, h->k, h->pc, h->bitmap, h->bitmap_words,
+                                h->partials, h->st));
+        else
+            CK(pf_stats_launch<float>(h->n, h->ids, (float *)h->eta, h->g, h->k, h->pc, h->bitmap, h->bitmap_words,
+                               h->partials, h->st));
+        CK(reduce_partials(h->partials, nb, 2, h->scal + 8, h->st));
+        }
+        double hs[2], ng = 0;
+        CK(cudaMemcpyAsync(hs, h->scal + 8, sizeof hs, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(&ng, h->partials + 2 * (long)nb, sizeof ng, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(&ovf, h->flags + 2, sizeof ovf, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (h->prof) prof_collect(h);
+        out->F_tot = hs[0];
+        out->X_rex = hs[1] / (double)N3;
+        out->n_grains = (int)ng;
+        out->overflow = ovf;
+    } else {
+        CK(cudaMemcpyAsync(&ovf, h->flags + 2, sizeof ovf, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (h->prof) prof_collect(h);
+    }
+    return ovf > 0 ? EVP_WARN_OVERFLOW : EVP_OK;
+}
+
+int evp_fields_bytes(const evp_handle *h, uint32_t mask, size_t *bytes) {
+    if (!h || !bytes) return EVP_ERR_ARG;
+    if (mask == 0 || (mask >> 13) != 0) return EVP_ERR_ARG;
+    size_t tot = 0;
+    for (uint32_t bit = 1; bit <= EVP_F_ETA; bit <<= 1)
+        if (mask & bit) tot += field_bytes(h, bit);
+    *bytes = tot;
+    return EVP_OK;
+}
+
+int get_fields(evp_handle *h, uint32_t mask, void *dst, size_t bytes, int dst_is_device) {
+    size_t need = 0;
+    if (!h || !dst) return fail(h, EVP_ERR_ARG, "NULL argument to get_fields");
+    if (evp_fields_bytes(h, mask, &need) != EVP_OK) return fail(h, EVP_ERR_ARG, "bad field mask 0x%x", mask);
+    if (bytes != need) return fail(h, EVP_ERR_ARG, "get_fields: %zu bytes given, %zu expected", bytes, need);
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t off = 0;
+    for (uint32_t bit = 1; bit <= EVP_F_ETA; bit <<= 1) {
+        if (!(mask & bit)) continue;
+        const size_t fb = field_bytes(h, bit);
+        const void *src = field_ptr(h, bit);
+        if (bit == EVP_F_EPS) {
+            if (h->dbl) CK(total_strain<double>(h->N3, (double *)h->epse, (double *)h->epsp, (double *)h->spec, h->st));
+            else CK(total_strain<float>(h->N3, (float *)h->epse, (float *)h->epsp, (float *)h->spec, h->st));
+            src = h->spec;
+        }
+        CK(cudaMemcpyAsync((char *)dst + off, src, fb, kind, h->st));
+        off += fb;
+    }
+    CK(cudaStreamSynchronize(h->st));
+    return EVP_OK;
+}
+
+int set_fields(evp_handle *h, uint32_t mask, const void *src, size_t bytes, int src_is_device) {
+    size_t need = 0;
+    if (!h || !src) return fail(h, EVP_ERR_ARG, "NULL argument to set_fields");
+    if (mask & (EVP_F_EPS | EVP_F_G0)) return fail(h, EVP_ERR_ARG, "EVP_F_EPS and EVP_F_G0 cannot be set");
+    if (evp_fields_bytes(h, mask, &need) != EVP_OK) return fail(h, EVP_ERR_ARG, "bad field mask 0x%x", mask);
+    if (bytes != need) return fail(h, EVP_ERR_ARG, "set_fields: %zu bytes given, %zu expected", bytes, need);
+    const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t off = 0;
+    for (uint32_t bit = 1; bit <= EVP_F_ETA; bit <<= 1) {
+        if (!(mask & bit)) continue;
+        const size_t fb = field_bytes(h, bit);
+        CK(cudaMemcpyAsync(field_ptr(h, bit), (const char *)src + off, fb, kind, h->st));
+        off += fb;
+    }
+    if (mask & EVP_F_RHO) {
+        if (h->dbl) CK(refresh_k<double>(h->N3, (double *)h->rho, h->k, h->st));
+        else CK(refresh_k<float>(h->N3, (float *)h->rho, h->k, h->st));
+    }
+    CK(cudaStreamSynchronize(h->st));
+    return EVP_OK;
+}
+
+int evp_get_scalars(const evp_handle *h, double *E6, double *dE_prev6, int *have_prev, int *next_id) {
+    if (!h) return EVP_ERR_ARG;
+    for (int i = 0; i < 6; ++i) {
+        if (E6) E6[i] = h->E[i];
+        if (dE_prev6) dE_prev6[i] = h->dE_prev[i];
+    }
+    if (have_prev) *have_prev = h->have_prev;
+    if (next_id) *next_id = h->next_id;
+    return EVP_OK;
+}
+
+int evp_set_scalars(evp_handle *h, const double *E6, const double *dE_prev6, int have_prev, int next_id) {
+    if (!h || next_id < h->G || next_id > h->max_ids) return fail(h, EVP_ERR_ARG, "bad scalars");
+    for (int i = 0; i < 6; ++i) {
+        if (E6) h->E[i] = E6[i];
+        if (dE_prev6) h->dE_prev[i] = dE_prev6[i];
+    }
+    h->have_prev = have_prev;
+    h->next_id = next_id;
+    return EVP_OK;
+}
+
+int evp_voronoi(int n, int grains, const int64_t *seeds_dev, int32_t *ids_dev, void *cuda_stream) {
+    if (!pow2(n) || grains < 1 || !seeds_dev || !ids_dev) return EVP_ERR_ARG;
+    const cudaError_t e = voronoi(n, grains, seeds_dev, ids_dev, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+int evp_rfft3d(int n, int precision, int nfields, const void *in_dev, void *out_dev, void *cuda_stream) {
+    if (!pow2(n) || nfields < 1 || nfields > 6 || !in_dev || !out_dev) return EVP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    if (precision == EVP_FP64) {
+        e = fft_x_r2c<double>((const double *)in_dev, out_dev, n, nfields, s);
+        if (e == cudaSuccess) e = fft_y<double>(out_dev, n, nfields, 0, s);
+        if (e == cudaSuccess) e = fft_z<double>(out_dev, n, nfields, Z_FWD, 0, 0, nullptr, nullptr, s);
+    } else {
+        e = fft_x_r2c<float>((const float *)in_dev, out_dev, n, nfields, s);
+        if (e == cudaSuccess) e = fft_y<float>(out_dev, n, nfields, 0, s);
+        if (e == cudaSuccess) e = fft_z<float>(out_dev, n, nfields, Z_FWD, 0, 0, nullptr, nullptr, s);
+    }
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, void *cuda_stream) {
+    if (!pow2(n) || nfields < 1 || nfields > 6 || !in_dev || !out_dev) return EVP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    if (precision == EVP_FP64) {
+        e = fft_z<double>(in_dev, n, nfields, Z_INV, 0, 0, nullptr, nullptr, s);
+        if (e == cudaSuccess) e = fft_y<double>(in_dev, n, nfields, 1, s);
+        if (e == cudaSuccess) e = fft_x_c2r<double>(in_dev, (double *)out_dev, n, nfields, 1.0, nullptr, s);
+    } else {
+        e = fft_z<float>(in_dev, n, nfields, Z_INV, 0, 0, nullptr, nullptr, s);
+        if (e == cudaSuccess) e = fft_y<float>(in_dev, n, nfields, 1, s);
+        if (e == cudaSuccess) e = fft_x_c2r<float>(in_dev, (float *)out_dev, n, nfields, 1.0f, nullptr, s);
+    }
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+}  // extern "C"

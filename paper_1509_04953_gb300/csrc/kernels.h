@@ -1,0 +1,72 @@
+// Host-side launchers of the device kernels (internal to libevp_gb300; not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace evp {
+
+// ---- material / solver constants passed by value to the kernels ----
+struct MatConst {
+    double gdot0, n, dt, tau0, alpha_mu_b, k1, k2;
+    double lam0, mu0;       // reference medium (Voigt isotropic average)
+    int n_int;              // n if it is a small positive integer (fast power), else 0
+};
+
+// ---- fft.cu ----
+enum ZMode { Z_FWD = 0, Z_INV = 1, Z_FWD_GAMMA_INV = 2 };
+template <typename T> cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s);
+template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s);
+template <typename T>
+cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials,
+                  double *mean6, cudaStream_t s);
+// x-pass complex-to-real. If add != nullptr: out[c] += scale * field + add[c]; else out = field.
+template <typename T>
+cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6,
+                      cudaStream_t s);
+int fft_z_blocks(int n, int is_double);
+
+// ---- newton.cu ----
+// solve_fp64: 1 -> the 6x6 Newton system is solved in FP64 even when TA = float.
+template <typename TA>
+cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
+                         const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
+                         cudaStream_t s);
+template <typename TA>
+cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
+                      double r, const double *dE6, int use_field, cudaStream_t s);
+template <typename TA>
+cudaError_t state_update(long N3, const TA *sig, const TA *tauc, const int32_t *g0, const TA *Mtab, TA *epst,
+                         TA *epse, TA *epsp, TA *deps, TA *rho, double *k, MatConst mc, cudaStream_t s);
+template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const TA *epsp, TA *eps, cudaStream_t s);
+
+// ---- drx.cu ----
+cudaError_t voronoi(int n, int G, const int64_t *seeds, int32_t *ids, cudaStream_t s);
+template <typename T>
+cudaError_t drx_init(long N3, const int32_t *g0, T *rho, double *k, double *kappa, int32_t *g, int32_t *draws,
+                     int32_t *ids, T *eta, int K, double rho0, double kc, double q, uint64_t seed, cudaStream_t s);
+template <typename T> cudaError_t refresh_k(long N3, const T *rho, double *k, cudaStream_t s);
+int nucleate_blocks(long N3);
+template <typename T>
+cudaError_t nucleate(int n, int K, const int32_t *g_in, int32_t *g, double *k, double *kappa, T *rho,
+                     int32_t *draws, int32_t *ids, T *eta, int32_t *blk_counts, int32_t *blk_offsets,
+                     int32_t *count_out, int next_id, double s_soften, double kc_new, double q, uint64_t seed,
+                     cudaStream_t s);
+
+// ---- pf.cu ----
+struct PFConst {
+    double m, kappa, gam, L_dt, Escale, drop;
+    int G, K;
+};
+template <typename T>
+cudaError_t pf_one_step(int n, const int32_t *ids, const T *eta, int32_t *ids2, T *eta2, int32_t *g,
+                        const double *k, PFConst pc, int32_t *overflow, cudaStream_t s);
+template <typename T>
+cudaError_t pf_soften(long N3, const int32_t *gprev, const int32_t *g, T *rho, double *k, int G, double s_soften,
+                      cudaStream_t s);
+int pf_stat_blocks(long N3);
+template <typename T>
+cudaError_t pf_stats_launch(int n, const int32_t *ids, const T *eta, const int32_t *g, const double *k, PFConst pc,
+                     uint32_t *bitmap, int bitmap_words, double *partials, cudaStream_t s);
+cudaError_t reduce_partials(const double *partials, int nparts, int nvals, double *out, cudaStream_t s);
+
+}  // namespace evp

@@ -1,0 +1,368 @@
+// Per-voxel crystal-plasticity kernels (Sec. 2.1 Eqs. HookeLaw / PlasticRate, Sec. 2.2 flow rule
+// and density evolution read as a power law with Kocks-Mecking hardening).
+//
+// Local problem: find sigma with r(sigma) = S:sigma + dt sum_a m^a gdot^a(sigma) - eps_tr = 0,
+// gdot^a = gdot0 |tau^a/tau_c|^n sign(tau^a), tau^a = m^a:sigma. This is the implicit Euler
+// stress update of Eq. HookeLaw multiplied by the compliance S = C^-1; its Jacobian
+// K = S + dt sum_a (n gdot0 |x^a|^(n-1)/tau_c) m^a (x) m^a is symmetric positive definite, so the
+// 6x6 Newton system is solved by Cholesky, and r is the gradient of a convex potential Phi used
+// for Armijo backtracking. eps_tr = eps^{t+dt} - eps_p^t is carried directly (the "trial" elastic
+// strain), which keeps FP32 fields accurate when the total strain is large.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace evp {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x) { return sqrt(x); }
+__device__ __forceinline__ double dsqrt(double x) { return __dsqrt_rn(x); }
+template <typename T> __device__ __forceinline__ T drcp(T x) { return (T)1 / x; }
+__device__ __forceinline__ double drcp(double x) { return __drcp_rn(x); }
+
+// |x|^(n-1) for the power law; fast path for small integer n (exponentiation by squaring).
+template <typename T> __device__ __forceinline__ T pow_nm1(T ax, const MatConst &mc) {
+    if (mc.n_int > 0) {
+        int e = mc.n_int - 1;
+        T r = (T)1, b = ax;
+        while (e) {
+            if (e & 1) r *= b;
+            b *= b;
+            e >>= 1;
+        }
+        return r;
+    }
+    return ax > (T)0 ? (T)pow((double)ax, mc.n - 1.0) : (T)0;
+}
+
+// Packed lower-triangular index of (i, j), j <= i.
+__host__ __device__ constexpr int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+template <typename TA> struct Eval {
+    TA r[6];
+    TA K[21];
+    TA phi;
+};
+
+template <typename TA>
+__device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA inv_tc,
+                                         const TA sg[6], const MatConst &mc, Eval<TA> &e) {
+    const TA dt = (TA)mc.dt, g0 = (TA)mc.gdot0, nn = (TA)mc.n;
+    TA phi = (TA)0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        TA acc = (TA)0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += Sp[i >= j ? pk(i, j) : pk(j, i)] * sg[j];
+        e.r[i] = acc - etr[i];
+        phi += sg[i] * ((TA)0.5 * acc - etr[i]);
+    }
+#pragma unroll
+    for (int q = 0; q < 21; ++q) e.K[q] = Sp[q];
+    const TA cphi = dt * g0 * tauc / (nn + (TA)1);
+    const TA cslope = dt * nn * g0 * inv_tc;
+#pragma unroll 1
+    for (int a = 0; a < 12; ++a) {
+        TA m[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) m[i] = __ldg(M + 6 * a + i);
+        TA tau = (TA)0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
+        const TA x = tau * inv_tc;
+        const TA ax = fabs(x);
+        const TA p9 = pow_nm1(ax, mc);       // |x|^(n-1)
+        const TA p10 = p9 * ax;              // |x|^n
+        const TA gd = x < (TA)0 ? -g0 * p10 : g0 * p10;
+        const TA slope = cslope * p9;
+        TA sm[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            e.r[i] += dt * gd * m[i];
+            sm[i] = slope * m[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) e.K[pk(i, j)] += sm[i] * m[j];
+        phi += cphi * p10 * ax;
+    }
+    e.phi = phi;
+}
+
+// Cholesky solve of K d = r (K packed lower, SPD). Returns false if K is not positive definite.
+template <typename TS, typename TA> __device__ __forceinline__ bool chol_solve(const TA Kin[21], const TA rin[6], TA dout[6]) {
+    TS L[21], y[6];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) L[q] = (TS)Kin[q];
+    TS inv_d[6];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        TS s = L[pk(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= L[pk(j, k)] * L[pk(j, k)];
+        ok = ok && (s > (TS)0);
+        s = s > (TS)0 ? s : (TS)1;
+        const TS dj = dsqrt(s);
+        inv_d[j] = drcp(dj);
+        L[pk(j, j)] = dj;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            TS t = L[pk(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[pk(i, k)] * L[pk(j, k)];
+            L[pk(i, j)] = t * inv_d[j];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        TS t = (TS)rin[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= L[pk(i, k)] * y[k];
+        y[i] = t * inv_d[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        TS t = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) t -= L[pk(k, i)] * y[k];
+        y[i] = t * inv_d[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dout[i] = (TA)y[i];
+    return ok;
+}
+
+// Damped Newton on one voxel. Returns the iteration count (> 0) or minus it on failure.
+template <typename TA, typename TS>
+__device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA sg[6],
+                            const MatConst &mc, TA tol, int maxit, TA ls_free, int &nevals) {
+    const TA inv_tc = drcp(tauc);
+    Eval<TA> e;
+    evaluate(Sp, M, etr, tauc, inv_tc, sg, mc, e);
+    nevals = 1;
+    for (int it = 1; it <= maxit; ++it) {
+        TA d[6];
+        if (!chol_solve<TS, TA>(e.K, e.r, d)) return -it;
+        TA rd = (TA)0, dn = (TA)0, sn = (TA)0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            rd += e.r[i] * d[i];
+            dn += d[i] * d[i];
+            sn += sg[i] * sg[i];
+        }
+        dn = dsqrt(dn);
+        const TA scale = dsqrt(sn) + tauc;
+        const TA phi0 = e.phi;
+        TA s = (TA)1, st[6];
+        bool ok = false;
+        for (int h = 0; h < 60; ++h) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) st[i] = sg[i] - s * d[i];
+            evaluate(Sp, M, etr, tauc, inv_tc, st, mc, e);
+            ++nevals;
+            if (e.phi <= phi0 - (TA)1e-4 * s * rd || s * dn <= ls_free * scale) {
+                ok = true;
+                break;
+            }
+            s *= (TA)0.5;
+        }
+        if (!ok) return -it;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sg[i] = st[i];
+        if (s * dn <= tol * scale) return it;
+    }
+    return -maxit;
+}
+
+template <typename TA, typename TS>
+__global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc,
+                                                    const int32_t *__restrict__ g0, TA *__restrict__ sig,
+                                                    const TA *__restrict__ Stab, const TA *__restrict__ Mtab, MatConst mc,
+                                                    TA tol, int maxit, TA ls_free, int *__restrict__ flags) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = v < N3;
+    int r = 1, nev = 0;
+    if (valid) {
+        const int g = g0[v];
+        TA Sp[21];
+        const TA *S = Stab + 36 * (long)g;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) Sp[pk(i, j)] = __ldg(S + 6 * i + j);
+        TA etr[6], sg[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            etr[c] = epst[c * N3 + v];
+            sg[c] = sig[c * N3 + v];
+        }
+        r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
+    }
+    // warp-aggregated flag updates (blockDim is a multiple of 32; every lane reaches here)
+    __syncwarp();
+    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
+    int mx = valid ? (r < 0 ? -r : r) : 0;
+    int sit = valid ? mx : 0, sev = nev;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sit += __shfl_xor_sync(0xffffffffu, sit, o);
+        sev += __shfl_xor_sync(0xffffffffu, sev, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fmask) atomicAdd(flags, __popc(fmask));
+        atomicMax(flags + 1, mx);
+        // flags[4..5] and [6..7] hold 64-bit totals of local iterations (= 6x6 solves) and evaluations
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
+    }
+}
+
+// Start of an increment: tau_c from the densities at t (frozen over the increment) and the
+// predictor eps_tr = eps_e^t + (r * deps_prev  |  dE).
+template <typename TA>
+__global__ void __launch_bounds__(256) k_predictor(long N3, const TA *__restrict__ epse, const TA *__restrict__ deps,
+                                                  const TA *__restrict__ rho, TA *__restrict__ epst, TA *__restrict__ tauc,
+                                                  MatConst mc, double r, int use_field, double d0, double d1, double d2,
+                                                  double d3, double d4, double d5) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N3) return;
+    double rf = 0.0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) rf += (double)rho[a * N3 + v];
+    tauc[v] = (TA)(mc.tau0 + mc.alpha_mu_b * sqrt(rf));
+    const double dE[6] = {d0, d1, d2, d3, d4, d5};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const TA add = use_field ? (TA)(r * (double)deps[c * N3 + v]) : (TA)dE[c];
+        epst[c * N3 + v] = epse[c * N3 + v] + add;
+    }
+}
+
+// After convergence (a7): advance eps_p, eps_e, the strain increment and the densities with
+// the converged shear rates; k = rho_tot in FP64.
+template <typename TA>
+__global__ void __launch_bounds__(kThreads) k_state_update(long N3, const TA *__restrict__ sig, const TA *__restrict__ tauc,
+                                                          const int32_t *__restrict__ g0, const TA *__restrict__ Mtab,
+                                                          const TA *__restrict__ epst, TA *__restrict__ epse,
+                                                          TA *__restrict__ epsp, TA *__restrict__ deps, TA *__restrict__ rho,
+                                                          double *__restrict__ kf, MatConst mc) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N3) return;
+    const int g = g0[v];
+    const TA *M = Mtab + 72 * (long)g;
+    TA sg[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sg[c] = sig[c * N3 + v];
+    const TA inv_tc = (TA)1 / tauc[v];
+    const TA g0r = (TA)mc.gdot0, dt = (TA)mc.dt;
+    TA ep[6] = {0, 0, 0, 0, 0, 0};
+    TA agd[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+        TA m[6], tau = (TA)0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            m[i] = __ldg(M + 6 * a + i);
+            tau += m[i] * sg[i];
+        }
+        const TA x = tau * inv_tc, ax = fabs(x);
+        const TA p10 = pow_nm1(ax, mc) * ax;
+        const TA gd = x < (TA)0 ? -g0r * p10 : g0r * p10;
+        agd[a] = fabs(gd);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) ep[i] += m[i] * gd;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const TA tr = epst[c * N3 + v];
+        const TA eo = epse[c * N3 + v];
+        epsp[c * N3 + v] += dt * ep[c];
+        deps[c * N3 + v] = tr - eo;
+        epse[c * N3 + v] = tr - dt * ep[c];
+    }
+    double rf = 0.0;
+    TA r[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+        r[a] = rho[a * N3 + v];
+        rf += (double)r[a];
+    }
+    const double srf = sqrt(rf);
+    double kk = 0.0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+        const TA nr = (TA)((double)r[a] + mc.dt * (mc.k1 * srf - mc.k2 * (double)r[a]) * (double)agd[a]);
+        rho[a * N3 + v] = nr;
+        kk += (double)nr;
+    }
+    kf[v] = kk;
+}
+
+template <typename TA>
+__global__ void k_total_strain(long N3, const TA *__restrict__ epse, const TA *__restrict__ epsp, TA *__restrict__ eps) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 6 * N3) eps[i] = epse[i] + epsp[i];
+}
+
+template <typename TA> TA ls_free_of() { return sizeof(TA) == 4 ? (TA)1e-3 : (TA)1e-6; }
+
+}  // namespace
+
+template <typename TA>
+cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
+                         const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
+                         cudaStream_t s) {
+    const int blocks = (int)((N3 + kThreads - 1) / kThreads);
+    if (solve_fp64)
+        k_newton<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol, maxit,
+                                                         ls_free_of<TA>(), flags);
+    else
+        k_newton<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol, maxit,
+                                                     ls_free_of<TA>(), flags);
+    return cudaGetLastError();
+}
+
+template <typename TA>
+cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
+                      double r, const double *dE6, int use_field, cudaStream_t s) {
+    const int blocks = (int)((N3 + 255) / 256);
+    k_predictor<TA><<<blocks, 256, 0, s>>>(N3, epse, deps, rho, epst, tauc, mc, r, use_field, dE6[0], dE6[1], dE6[2],
+                                           dE6[3], dE6[4], dE6[5]);
+    return cudaGetLastError();
+}
+
+template <typename TA>
+cudaError_t state_update(long N3, const TA *sig, const TA *tauc, const int32_t *g0, const TA *Mtab, TA *epst,
+                         TA *epse, TA *epsp, TA *deps, TA *rho, double *k, MatConst mc, cudaStream_t s) {
+    const int blocks = (int)((N3 + kThreads - 1) / kThreads);
+    k_state_update<TA><<<blocks, kThreads, 0, s>>>(N3, sig, tauc, g0, Mtab, epst, epse, epsp, deps, rho, k, mc);
+    return cudaGetLastError();
+}
+
+template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const TA *epsp, TA *eps, cudaStream_t s) {
+    const long n = 6 * N3;
+    k_total_strain<TA><<<(int)((n + 255) / 256), 256, 0, s>>>(N3, epse, epsp, eps);
+    return cudaGetLastError();
+}
+
+#define EVP_INST(TA)                                                                                              \
+    template cudaError_t newton_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,        \
+                                          const TA *, MatConst, double, int, int, int *, cudaStream_t);          \
+    template cudaError_t predictor<TA>(long, const TA *, const TA *, const TA *, TA *, TA *, MatConst, double,    \
+                                       const double *, int, cudaStream_t);                                        \
+    template cudaError_t state_update<TA>(long, const TA *, const TA *, const int32_t *, const TA *, TA *, TA *,  \
+                                          TA *, TA *, TA *, double *, MatConst, cudaStream_t);                    \
+    template cudaError_t total_strain<TA>(long, const TA *, const TA *, TA *, cudaStream_t);
+EVP_INST(float)
+EVP_INST(double)
+#undef EVP_INST
+
+}  // namespace evp

@@ -1,0 +1,296 @@
+// Active-set multi-grain Allen-Cahn step (Sec. 2.4, Eqs. TotalFreeEnergy, GBEnergyDensity,
+// StoredEnergyDensity, PFGoverning; sparse storage after the cited Gruber / Vedantam technique).
+//
+// Grid-nondimensional form (lengths dx, energies omega_gb/dx, time dx^2/(M omega_gb)):
+//   m = 6/l, kappa = 3l/4, gamma = 3/2,  E' = zeta mu b^2 rho_tot dx / omega_gb
+//   eta_i <- eta_i - L dt [ m (eta_i^3 - eta_i + 2 gamma eta_i (S2 - eta_i^2)) - kappa lap(eta_i)
+//                            + (i deformed: 2E' eta_i R/S^2 | i recrystallised: -2E' eta_i D/S^2) ]
+// with S2 = D + R the local sum of eta^2 over deformed (D, ids < G) and recrystallised (R)
+// grains and a periodic 7-point Laplacian. Each voxel stores up to K (id, eta) pairs sorted by
+// id (-1 = empty). Candidates at a voxel are the ids present there or at its six neighbours;
+// values below `drop` are discarded, the K largest kept (ties to the smaller id) and the grain
+// id is the argmax. This file is compiled without FMA contraction so that, in FP64, each value
+// is rounded exactly as the plain formula above prescribes.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace evp {
+
+namespace {
+
+constexpr int KM = 8;   // compile-time capacity of the active set (runtime K <= KM)
+constexpr int kPF = 128;
+
+struct Nbr {
+    long q[7];   // self, x-, x+, y-, y+, z-, z+
+};
+
+__device__ __forceinline__ Nbr neighbours(int n, long v) {
+    const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
+    const long nn = (long)n * n;
+    Nbr b;
+    b.q[0] = v;
+    b.q[1] = v - x + (x + n - 1) % n;
+    b.q[2] = v - x + (x + 1) % n;
+    b.q[3] = v + (long)(((y + n - 1) % n) - y) * n;
+    b.q[4] = v + (long)(((y + 1) % n) - y) * n;
+    b.q[5] = v + (long)(((z + n - 1) % n) - z) * nn;
+    b.q[6] = v + (long)(((z + 1) % n) - z) * nn;
+    return b;
+}
+
+constexpr int kEmpty = 0x7fffffff;
+
+template <typename T> __device__ __forceinline__ bool better(T ea, int ia, T eb, int ib) {
+    return ea > eb || (ea == eb && ia < ib);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta,
+                                           int32_t *__restrict__ ids2, T *__restrict__ eta2, int32_t *__restrict__ gout,
+                                           const double *__restrict__ kf, PFConst pc, int32_t *__restrict__ overflow) {
+    const long N3 = (long)n * n * n;
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N3) return;
+    const int K = pc.K, G = pc.G;
+    const Nbr nb = neighbours(n, v);
+    const T m = (T)pc.m, kap = (T)pc.kappa, gam = (T)pc.gam, Ldt = (T)pc.L_dt, drop = (T)pc.drop;
+    // local sums over the voxel's own list, ascending id
+    T S2 = (T)0, D = (T)0, R = (T)0;
+    for (int j = 0; j < K; ++j) {
+        const int id = ids[j * N3 + v];
+        if (id < 0) break;
+        const T e = eta[j * N3 + v];
+        S2 += e * e;
+        if (id < G) D += e * e;
+        else R += e * e;
+    }
+    const T Ep = (T)(pc.Escale * kf[v]);
+    const T Ssum = D + R;
+    // merge the seven sorted lists
+    int head[7], pos[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        pos[q] = 0;
+        const int id = ids[nb.q[q]];
+        head[q] = id < 0 ? kEmpty : id;
+    }
+    int kid[KM + 1];
+    T ke[KM + 1];
+#pragma unroll
+    for (int j = 0; j <= KM; ++j) {
+        kid[j] = kEmpty;
+        ke[j] = (T)-INFINITY;
+    }
+    int best_id = kEmpty;
+    T best = (T)-INFINITY;
+    bool ovf = false;
+    for (int guard = 0; guard < 7 * KM; ++guard) {
+        int c = head[0];
+#pragma unroll
+        for (int q = 1; q < 7; ++q) c = min(c, head[q]);
+        if (c == kEmpty) break;
+        T e[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            e[q] = (T)0;
+            if (head[q] == c) {
+                e[q] = eta[pos[q] * N3 + nb.q[q]];
+                ++pos[q];
+                int nx = kEmpty;
+                if (pos[q] < K) {
+                    const int id = ids[pos[q] * N3 + nb.q[q]];
+                    nx = id < 0 ? kEmpty : id;
+                }
+                head[q] = nx;
+            }
+        }
+        const T e0 = e[0];
+        const T lap = e[1] + e[2] + e[3] + e[4] + e[5] + e[6] - (T)6 * e0;
+        const T df0 = m * (e0 * e0 * e0 - e0 + (T)2 * gam * e0 * (S2 - e0 * e0));
+        T ddef = (T)0;
+        if (Ssum > (T)1e-12) ddef = (c < G) ? (T)2 * Ep * e0 * R / (Ssum * Ssum) : -(T)2 * Ep * e0 * D / (Ssum * Ssum);
+        const T en = e0 - Ldt * (df0 - kap * lap + ddef);
+        if (en > best) { best = en; best_id = c; }
+        if (en >= drop) {
+            // insert at the spare slot KM and bubble up (sorted by eta desc, id asc)
+            kid[KM] = c;
+            ke[KM] = en;
+#pragma unroll
+            for (int j = KM - 1; j >= 0; --j) {
+                if (better(ke[j + 1], kid[j + 1], ke[j], kid[j])) {
+                    const int ti = kid[j]; kid[j] = kid[j + 1]; kid[j + 1] = ti;
+                    const T te = ke[j]; ke[j] = ke[j + 1]; ke[j + 1] = te;
+                }
+            }
+            // anything beyond the runtime capacity K is dropped
+#pragma unroll
+            for (int j = 0; j <= KM; ++j)
+                if (j >= K && kid[j] != kEmpty) { ovf = true; kid[j] = kEmpty; ke[j] = (T)-INFINITY; }
+        }
+    }
+    if (kid[0] == kEmpty && best_id != kEmpty) { kid[0] = best_id; ke[0] = best; }
+    gout[v] = kid[0];
+    // sort the kept entries by id (empties last)
+#pragma unroll
+    for (int a = 0; a < KM; ++a)
+#pragma unroll
+        for (int j = 0; j < KM - 1 - a; ++j)
+            if (kid[j] > kid[j + 1]) {
+                const int ti = kid[j]; kid[j] = kid[j + 1]; kid[j + 1] = ti;
+                const T te = ke[j]; ke[j] = ke[j + 1]; ke[j + 1] = te;
+            }
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+        if (j < K) {
+            const bool has = kid[j] != kEmpty;
+            ids2[j * N3 + v] = has ? kid[j] : -1;
+            eta2[j * N3 + v] = has ? ke[j] : (T)0;
+        }
+    }
+    if (ovf) atomicAdd(overflow, 1);
+}
+
+template <typename T>
+__global__ void k_pf_soften(long N3, const int32_t *__restrict__ gprev, const int32_t *__restrict__ g, T *__restrict__ rho,
+                            double *__restrict__ kf, int G, double s) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N3) return;
+    if (!(gprev[v] < G && g[v] >= G)) return;
+    double kk = 0.0;
+    for (int a = 0; a < 12; ++a) {
+        const T r = (T)(s * (double)rho[a * N3 + v]);
+        rho[a * N3 + v] = r;
+        kk += (double)r;
+    }
+    kf[v] = kk;
+}
+
+// Per-voxel discrete free energy (bulk + forward-difference gradient + stored energy) and
+// recrystallised count, summed per block in FP64; distinct grain ids marked in a bitmap.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pf_stats(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta,
+                                                 const int32_t *__restrict__ g, const double *__restrict__ kf, PFConst pc,
+                                                 uint32_t *__restrict__ bitmap, int bitmap_words, double *__restrict__ part) {
+    __shared__ double red[32];
+    const long N3 = (long)n * n * n;
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double F = 0.0, rex = 0.0;
+    if (v < N3) {
+        const int K = pc.K, G = pc.G;
+        const int gi = g[v];
+        if (gi >= G) rex = 1.0;
+        if (gi >= 0 && (gi >> 5) < bitmap_words) atomicOr(bitmap + (gi >> 5), 1u << (gi & 31));
+        double f0 = 0.25, S2 = 0.0, D = 0.0;
+        for (int j = 0; j < K; ++j) {
+            const int id = ids[j * N3 + v];
+            if (id < 0) break;
+            const double e = (double)eta[j * N3 + v];
+            f0 += e * e * e * e / 4.0 - e * e / 2.0;
+            S2 += e * e;
+            if (id < G) D += e * e;
+            for (int i2 = j + 1; i2 < K; ++i2) {
+                if (ids[i2 * N3 + v] < 0) break;
+                const double e2 = (double)eta[i2 * N3 + v];
+                f0 += pc.gam * e * e * e2 * e2;
+            }
+        }
+        const double fdef = S2 > 1e-12 ? pc.Escale * kf[v] * D / S2 : 0.0;
+        const Nbr nb = neighbours(n, v);
+        double grad = 0.0;
+        for (int d = 2; d <= 6; d += 2) {   // x+, y+, z+
+            const long w = nb.q[d];
+            int pa = 0, pb = 0;
+            for (int guard = 0; guard < 2 * KM; ++guard) {
+                const int ia = pa < K ? ids[pa * N3 + v] : -1;
+                const int ib = pb < K ? ids[pb * N3 + w] : -1;
+                const int ca = ia < 0 ? kEmpty : ia, cb = ib < 0 ? kEmpty : ib;
+                if (ca == kEmpty && cb == kEmpty) break;
+                double ea = 0.0, eb = 0.0;
+                if (ca <= cb) { ea = (double)eta[pa * N3 + v]; ++pa; }
+                if (cb <= ca) { eb = (double)eta[pb * N3 + w]; ++pb; }
+                grad += (eb - ea) * (eb - ea);
+            }
+        }
+        F = pc.m * f0 + 0.5 * pc.kappa * grad + fdef;
+    }
+    const double sF = block_sum(F, red);
+    const double sR = block_sum(rex, red);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sF;
+        part[2 * blockIdx.x + 1] = sR;
+    }
+}
+
+__global__ void k_popc(const uint32_t *__restrict__ bitmap, int words, double *__restrict__ out_slot) {
+    __shared__ double red[32];
+    double c = 0.0;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) c += (double)__popc(bitmap[i]);
+    const double s = block_sum(c, red);
+    if (threadIdx.x == 0) *out_slot = s;
+}
+
+// Deterministic sum of partials [nparts][nvals] -> out[nvals] (one block, fixed order).
+__global__ void k_reduce(const double *__restrict__ part, int nparts, int nvals, double *__restrict__ out) {
+    __shared__ double red[32];
+    for (int c = 0; c < nvals; ++c) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[(long)i * nvals + c];
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) out[c] = s;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t pf_one_step(int n, const int32_t *ids, const T *eta, int32_t *ids2, T *eta2, int32_t *g, const double *k,
+                        PFConst pc, int32_t *overflow, cudaStream_t s) {
+    const long N3 = (long)n * n * n;
+    if (pc.K > KM || pc.K < 1) return cudaErrorInvalidValue;
+    k_pf<T><<<(int)((N3 + kPF - 1) / kPF), kPF, 0, s>>>(n, ids, eta, ids2, eta2, g, k, pc, overflow);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pf_soften(long N3, const int32_t *gprev, const int32_t *g, T *rho, double *k, int G, double s_soften,
+                      cudaStream_t s) {
+    k_pf_soften<T><<<(int)((N3 + 255) / 256), 256, 0, s>>>(N3, gprev, g, rho, k, G, s_soften);
+    return cudaGetLastError();
+}
+
+int pf_stat_blocks(long N3) { return (int)((N3 + 255) / 256); }
+
+template <typename T>
+cudaError_t pf_stats_launch(int n, const int32_t *ids, const T *eta, const int32_t *g, const double *k, PFConst pc,
+                     uint32_t *bitmap, int bitmap_words, double *partials, cudaStream_t s) {
+    const long N3 = (long)n * n * n;
+    const int nb = pf_stat_blocks(N3);
+    cudaError_t e = cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)bitmap_words, s);
+    if (e != cudaSuccess) return e;
+    k_pf_stats<T><<<nb, 256, 0, s>>>(n, ids, eta, g, k, pc, bitmap, bitmap_words, partials);
+    // partials layout: [nb][2] energies / rex counts, then one slot for the distinct-id count
+    k_popc<<<1, 1024, 0, s>>>(bitmap, bitmap_words, partials + 2 * (long)nb);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const double *partials, int nparts, int nvals, double *out, cudaStream_t s) {
+    k_reduce<<<1, 1024, 0, s>>>(partials, nparts, nvals, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t pf_one_step<float>(int, const int32_t *, const float *, int32_t *, float *, int32_t *,
+                                        const double *, PFConst, int32_t *, cudaStream_t);
+template cudaError_t pf_one_step<double>(int, const int32_t *, const double *, int32_t *, double *, int32_t *,
+                                         const double *, PFConst, int32_t *, cudaStream_t);
+template cudaError_t pf_soften<float>(long, const int32_t *, const int32_t *, float *, double *, int, double, cudaStream_t);
+template cudaError_t pf_soften<double>(long, const int32_t *, const int32_t *, double *, double *, int, double, cudaStream_t);
+template cudaError_t pf_stats_launch<float>(int, const int32_t *, const float *, const int32_t *, const double *, PFConst,
+                                     uint32_t *, int, double *, cudaStream_t);
+template cudaError_t pf_stats_launch<double>(int, const int32_t *, const double *, const int32_t *, const double *, PFConst,
+                                      uint32_t *, int, double *, cudaStream_t);
+
+}  // namespace evp

@@ -1,0 +1,267 @@
+"""GPU parity: every step of the hot path, called through the C ABI, against the FP64 oracle.
+
+Floating-point fields: FP64 path within 1e-10 relative (normwise per field) of the oracle, mixed
+path within 1e-4 relative macro stress of the FP64 GPU path. Integer / index work (grain ids,
+nucleation sites, fresh ids, active-set ids, draw counters): bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1509_04953_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_04953_gb300 import build
+    build.build()
+    from paper_1509_04953_gb300 import evp
+    return evp
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def make_pair(ev, mat, n, G, seed, precision="fp64", **kw):
+    seeds = synth.voronoi_seeds(n, G, seed)
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, seeds)
+    gpu = ev.Solver(n, G, g0, quat, mat, seed, precision=precision, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("tol", "max_iter", "allow_unconverged", "kmax", "predictor")}
+    ref = O.State(n, G, g0, quat, mat, seed=seed, **okw)
+    return gpu, ref, g0
+
+
+# ------------------------------------------------------------------------------------------
+# a1 Voronoi, a3 FFT
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n,G", [(16, 8), (32, 27), (64, 64), (128, 256)])
+def test_voronoi_bit_exact(ev, n, G):
+    seeds = synth.voronoi_seeds(n, G, 100 + n)
+    got = ev.voronoi(n, seeds).cpu().numpy()
+    assert np.array_equal(got, O.voronoi(n, seeds))
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rfft3d_matches_oracle_fft(ev, n, prec):
+    import torch
+    rng = np.random.default_rng(n)
+    nf = 6 if n <= 16 else 3
+    x = rng.standard_normal((nf, n, n, n))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    spec = ev.rfft3d(torch.tensor(x, dtype=dt, device="cuda")).cpu().numpy()
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    for f in range(nf):
+        full = O.fft3d(x[f].astype(np.complex128), -1)      # [z][y][x] layout, full spectrum
+        assert rel(spec[f], full[:, :, : n // 2 + 1]) < tol
+    back = ev.irfft3d(torch.tensor(spec, device="cuda")).cpu().numpy() / n ** 3
+    assert rel(back, x) < (1e-14 if prec == "fp64" else 2e-6)
+
+
+# ------------------------------------------------------------------------------------------
+# a2-a7 fixed point and state update
+# ------------------------------------------------------------------------------------------
+def test_fixed_iterations_match_oracle_fp64(ev, mat):
+    """Same number of fixed-point iterations on both sides: every field agrees to round-off."""
+    n, G, seed = 16, 8, synth.BASE_SEED
+    kw = dict(tol=0.0, max_iter=6, allow_unconverged=1)
+    gpu, ref, _ = make_pair(ev, mat, n, G, seed, **kw)
+    for inc in range(2):
+        rc, st = gpu.increment(-1e-3, 1.0)
+        rco, sto = ref.increment(-1e-3, 1.0)
+        assert rc == 1 and rco == 1 and st.iterations == sto.iterations == 6
+        assert rel(st.sig_mean, sto.sig_mean) < FP64_TOL
+        assert rel(st.E, sto.E) < FP64_TOL
+        for f in ("sig", "eps", "epsp", "deps", "rho"):
+            assert rel(gpu.get(f), ref.field(f if f != "deps" else "deps_prev")) < FP64_TOL, f
+        assert rel(gpu.get("k")[0], ref.field("k")[0]) < FP64_TOL
+
+
+def test_converged_increments_match_oracle_fp64(ev, mat):
+    n, G, seed = 16, 8, synth.BASE_SEED
+    kw = dict(tol=1e-9, max_iter=3000)
+    gpu, ref, _ = make_pair(ev, mat, n, G, seed, **kw)
+    for inc in range(3):
+        rc, st = gpu.increment(-1e-3, 1.0)
+        rco, sto = ref.increment(-1e-3, 1.0)
+        assert rc == 0 and rco == 0
+        assert abs(st.iterations - sto.iterations) <= 1
+        assert st.err_eq <= 1e-9 and st.err_bc <= 1e-9
+        assert rel(st.sig_mean, sto.sig_mean) < 1e-8
+        assert rel(gpu.get("sig"), ref.field("sig")) < 1e-8
+        assert rel(gpu.get("rho"), ref.field("rho")) < 1e-10
+
+
+def test_single_crystal_gpu_matches_point_model(ev, mat):
+    """Homogeneous crystal (G = 1): the spectral solver reproduces the 0-D point model."""
+    n = 8
+    quat = synth.orientations(1, 21)
+    g0 = np.zeros(n ** 3, dtype=np.int32)
+    gpu = ev.Solver(n, 1, g0, quat, mat, 1, precision="fp64", tol=1e-12, max_iter=20000)
+    _, S, M = O.grain_tables(mat, quat)
+    rc, hist, pm = O.point_model(mat, S[0], M[0], -1e-3, 1.0, 4)
+    for inc in range(4):
+        rc, st = gpu.increment(-1e-3, 1.0)
+        assert rc == 0
+        assert abs(st.sig_mean[2] / hist[inc] - 1) < 1e-9
+    assert rel(st.E, pm["E"]) < 1e-8
+
+
+def test_mixed_precision_macro_stress_within_1e4_of_fp64(ev, mat):
+    n, G, seed = 32, 27, synth.BASE_SEED + 3
+    seeds = synth.voronoi_seeds(n, G, seed)
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, seeds)
+    a = ev.Solver(n, G, g0, quat, mat, seed, precision="fp64", tol=1e-8, max_iter=4000)
+    b = ev.Solver(n, G, g0, quat, mat, seed, precision="mixed", tol=1e-6, max_iter=4000)
+    c = ev.Solver(n, G, g0, quat, mat, seed, precision="mixed_fast", tol=1e-6, max_iter=4000)
+    for inc in range(5):
+        _, sa = a.increment(-1e-3, 1.0)
+        _, sb = b.increment(-1e-3, 1.0)
+        _, sc = c.increment(-1e-3, 1.0)
+        assert abs(sb.sig_mean[2] / sa.sig_mean[2] - 1) < 1e-4
+        assert abs(sc.sig_mean[2] / sa.sig_mean[2] - 1) < 1e-4
+    assert rel(b.get("sig"), a.get("sig")) < 1e-3
+
+
+# ------------------------------------------------------------------------------------------
+# a8 nucleation
+# ------------------------------------------------------------------------------------------
+def test_nucleation_bit_exact(ev, mat):
+    n, G, seed = 32, 27, 77
+    gpu, ref, g0 = make_pair(ev, mat, n, G, seed)
+    # raise the densities so that a sizeable set of boundary voxels nucleates
+    rng = np.random.default_rng(5)
+    rho = np.repeat(rng.uniform(0.5e13, 3.0e13, size=(1, n ** 3)), 12, axis=0)
+    gpu.set("rho", rho)
+    ref.field("rho")[:] = rho
+    ref.refresh_derived()
+    assert rel(gpu.get("k")[0], ref.field("k")[0]) == 0.0
+    assert rel(gpu.get("kappa")[0], ref.field("kappa")[0]) < 1e-15
+    for step in range(2):
+        rc, nn = gpu.nucleate(step)
+        rco, nno = ref.nucleate(step)
+        assert nn == nno and nn > 10
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))
+        assert np.array_equal(gpu.get("ids"), ref.ifield("ids"))
+        assert np.array_equal(gpu.get("draws")[0], ref.ifield("draws"))
+        assert rel(gpu.get("kappa")[0], ref.field("kappa")[0]) < 1e-15
+        assert rel(gpu.get("rho"), ref.field("rho")) == 0.0
+        assert gpu.next_id == ref.next_id
+
+
+# ------------------------------------------------------------------------------------------
+# a9-a10 phase field
+# ------------------------------------------------------------------------------------------
+def pf_setup(ev, mat, n, G, seed, kmax=8, nuclei=(5, 400, 1000, 1500)):
+    gpu, ref, g0 = make_pair(ev, mat, n, G, seed, kmax=kmax)
+    rng = np.random.default_rng(seed)
+    rho = np.repeat(rng.uniform(2e13, 8e13, size=(1, n ** 3)), 12, axis=0)
+    ids = ref.ifield("ids")
+    for j, v in enumerate(nuclei):
+        ids[0, v] = G + j
+    ref.next_id = G + len(nuclei)
+    ref.field("rho")[:] = rho
+    ref.refresh_derived()
+    gpu.set("rho", rho)
+    gpu.set("ids", ids.copy())
+    sc = gpu.scalars()
+    gpu.set_scalars(sc["E"], sc["dE_prev"], sc["have_prev"], G + len(nuclei))
+    return gpu, ref
+
+
+@pytest.mark.parametrize("kmax", [8, 2])
+def test_pf_steps_bit_exact_fp64(ev, mat, kmax):
+    n, G = 16, 8
+    gpu, ref = pf_setup(ev, mat, n, G, 3, kmax=kmax)
+    for call in range(3):
+        rc, st = gpu.pf_step(5)
+        rco, sto = ref.pf_step(5)
+        assert np.array_equal(gpu.get("ids"), ref.ifield("ids"))
+        assert np.array_equal(gpu.get("eta"), ref.field("eta"))          # bitwise (no FMA contraction)
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))
+        assert st.n_grains == sto.n_grains and st.X_rex == sto.X_rex
+        assert st.overflow == sto.overflow
+        assert abs(st.F_tot / sto.F_tot - 1) < 1e-12
+        assert rel(gpu.get("rho"), ref.field("rho")) == 0.0
+
+
+def test_pf_mixed_close_to_fp64(ev, mat):
+    n, G = 16, 8
+    a, _ = pf_setup(ev, mat, n, G, 4)
+    seeds = synth.voronoi_seeds(n, G, 4)
+    b = ev.Solver(n, G, O.voronoi(n, seeds), synth.orientations(G, 4), mat, 4, precision="mixed")
+    b.set("rho", a.get("rho").astype(np.float32))
+    b.set("ids", a.get("ids"))
+    sc = a.scalars()
+    b.set_scalars(sc["E"], sc["dE_prev"], sc["have_prev"], sc["next_id"])
+    _, sa = a.pf_step(10)
+    _, sb = b.pf_step(10)
+    assert abs(sb.F_tot / sa.F_tot - 1) < 1e-5
+    assert np.mean(a.get("g")[0] == b.get("g")[0]) > 0.999
+
+
+# ------------------------------------------------------------------------------------------
+# coupled increments (a2-a10) at the small workload
+# ------------------------------------------------------------------------------------------
+def test_coupled_run_matches_oracle(ev, mat):
+    n, G, seed = 16, 8, synth.BASE_SEED
+    kw = dict(tol=1e-9, max_iter=3000)
+    gpu, ref, _ = make_pair(ev, mat, n, G, seed, **kw)
+    rho = np.repeat(np.random.default_rng(1).uniform(2e13, 6e13, size=(1, n ** 3)), 12, axis=0)
+    gpu.set("rho", rho)
+    ref.field("rho")[:] = rho
+    ref.refresh_derived()
+    flips = 0
+    for inc in range(3):
+        rc, st = gpu.increment(-1e-3, 1.0)
+        rco, sto = ref.increment(-1e-3, 1.0)
+        assert rc == 0 and rco == 0
+        _, nn = gpu.nucleate(inc)
+        _, nno = ref.nucleate(inc)
+        assert nn == nno
+        _, ps = gpu.pf_step(5)
+        _, pso = ref.pf_step(5)
+        flips += int((gpu.get("g")[0] != ref.ifield("g")).sum())
+        assert rel(st.sig_mean, sto.sig_mean) < 1e-8
+        assert abs(ps.F_tot / pso.F_tot - 1) < 1e-9
+    assert flips == 0
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases and errors
+# ------------------------------------------------------------------------------------------
+def test_errors_and_degenerate_cases(ev, mat):
+    import ctypes as C
+    n, G = 8, 1
+    g0 = np.zeros(n ** 3, dtype=np.int32)
+    s = ev.Solver(n, G, g0, synth.orientations(1, 1), mat, 1, kmax=1)
+    rc, st = s.pf_step(0)
+    assert rc == 0 and st.n_grains == 1 and st.X_rex == 0.0
+    rc, nn = s.nucleate(0)                     # a single grain has no boundary voxels
+    assert nn == 0
+    with pytest.raises(ev.EVPError):
+        s.increment(-1e-3, 0.0)                # dt must be > 0
+    out = np.zeros(7, dtype=np.float64)
+    assert ev.load().get_fields(s.h, ev.F_SIG, out.ctypes.data, out.nbytes, 0) == -1
+    assert ev.load().set_fields(s.h, ev.F_EPS, out.ctypes.data, out.nbytes, 0) == -1
+    with pytest.raises(ev.EVPError):
+        ev.Solver(n, 2, np.full(n ** 3, 5, dtype=np.int32), synth.orientations(2, 1), mat, 1)
+    # a non-converging cap reports the fixed-point error without advancing the state
+    t = ev.Solver(16, 8, O.voronoi(16, synth.voronoi_seeds(16, 8, 2)), synth.orientations(8, 2), mat, 2,
+                  tol=1e-14, max_iter=3)
+    sig0 = t.get("sig")
+    rc, st = t.increment(-1e-3, 1.0, check=False)
+    assert rc == -4 and "not converged" in t.last_error()
+    assert np.array_equal(t.get("sig"), sig0)
