@@ -183,6 +183,16 @@ int evp_voronoi(int n, int grains, const int64_t *seeds_dev, int32_t *ids_dev, v
  * (interleaved complex of the same type; device). Unnormalised, exp(-2 pi i k.x/N).
  * Needs no scratch: the y and z passes run in place in out. */
 int evp_rfft3d(int n, int precision, int nfields, const void *in_dev, void *out_dev, void *cuda_stream);
+/* a4 residual of a given stress field (Sec. 2.1, the equilibrium check of the spectral solve):
+ * forward transform of the six Mandel stress components sig_dev (6 x N^3, T, device) into
+ * spec_dev (6 half spectra as evp_rfft3d, device, output), then out_dev (7 doubles, device,
+ * output) = [mean stress (6), sum over all frequencies of |xi . sigma_hat|^2] with
+ * xi = 2 pi k / N. scratch_dev: caller-owned device scratch of evp_residual_scratch_bytes()
+ * bytes for the per-block partial sums. err_eq = sqrt(out[6]) / (N^3 |mean|). */
+int evp_residual_scratch_bytes(int n, int precision, size_t *bytes);
+int evp_stress_residual(int n, int precision, const void *sig_dev, void *spec_dev, void *scratch_dev,
+                        double *out_dev, void *cuda_stream);
+
 /* inverse (complex-to-real) of evp_rfft3d, unnormalised: out = N^3 * field. in is overwritten. */
 int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, void *cuda_stream);
 

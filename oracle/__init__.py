@@ -77,6 +77,7 @@ def lib():
         L.orc_newton.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_int,
                                  _dp, _dp, C.POINTER(C.c_int)]
         L.orc_residual.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp, _dp]
+        L.orc_stress_residual.argtypes = [C.c_int, _dp, _dp]
         L.orc_km_update.argtypes = [C.POINTER(Params), _dp, _dp, C.c_double]
         L.orc_point_model.restype = C.c_int
         L.orc_point_model.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
@@ -203,6 +204,13 @@ def residual(mat, S, M, eps_tr, tauc, dt, sig):
                        np.ascontiguousarray(eps_tr, dtype=np.float64), tauc, dt,
                        np.ascontiguousarray(sig, dtype=np.float64), r, K)
     return r, K.reshape(6, 6)
+
+
+def stress_residual(n, sig):
+    """[mean stress (6), sum_xi |xi.sigma_hat|^2] of a (6, N^3) stress field."""
+    out = np.zeros(7)
+    lib().orc_stress_residual(n, np.ascontiguousarray(sig, dtype=np.float64).reshape(-1), out)
+    return out
 
 
 def km_update(mat, rho, gdot, dt):

@@ -541,6 +541,43 @@ void orc_refresh_derived(orc_state *s) {
 /* Signed frequency of index k on an n-point axis; the Nyquist index n/2 is taken as +n/2. */
 static int freq(int k, int n) { return k <= n / 2 ? k : k - n; }
 
+/* Equilibrium residual of a transformed stress field (six full complex spectra, unnormalised):
+ * returns sum_xi |xi . sigma_hat(xi)|^2 with xi = 2 pi k / N and writes the mean stress. */
+static double spectral_residual(int n, const double complex *spec, double mean[6]) {
+    const long N3 = (long)n * n * n;
+    double acc = 0.0;
+    for (int I = 0; I < 6; ++I) mean[I] = creal(spec[I * N3]) / (double)N3;
+    for (int kz = 0; kz < n; ++kz)
+        for (int ky = 0; ky < n; ++ky)
+            for (int kx = 0; kx < n; ++kx) {
+                long v = kx + (long)n * (ky + (long)n * kz);
+                double xi[3] = {2.0 * PI * freq(kx, n) / n, 2.0 * PI * freq(ky, n) / n, 2.0 * PI * freq(kz, n) / n};
+                double complex T[3][3];
+                for (int I = 0; I < 6; ++I) {
+                    T[MI[I]][MJ[I]] = spec[I * N3 + v] / mw(I);
+                    T[MJ[I]][MI[I]] = spec[I * N3 + v] / mw(I);
+                }
+                for (int i = 0; i < 3; ++i) {
+                    double complex dv = 0;
+                    for (int j = 0; j < 3; ++j) dv += xi[j] * T[i][j];
+                    acc += creal(dv) * creal(dv) + cimag(dv) * cimag(dv);
+                }
+            }
+    return acc;
+}
+
+/* Stand-alone form for tests: sig is 6 x N^3 (Mandel), out = [mean stress (6), residual sum]. */
+void orc_stress_residual(int n, const double *sig, double out[7]) {
+    const long N3 = (long)n * n * n;
+    double complex *spec = (double complex *)xcalloc(6 * N3, sizeof(double complex));
+    for (int I = 0; I < 6; ++I) {
+        for (long v = 0; v < N3; ++v) spec[I * N3 + v] = sig[I * N3 + v];
+        orc_fft3d(n, spec + I * N3, -1);
+    }
+    out[6] = spectral_residual(n, spec, out);
+    free(spec);
+}
+
 /* ------------------------------------------------------------------------------------------
  * One mechanical increment (Sec. 2.1): the basic Green-operator fixed point with a
  * strain-driven local Newton, under mixed macroscopic conditions (E33 prescribed, the other
@@ -623,23 +660,7 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
         }
         /* 3. residuals */
         double acc = 0.0, mn = 0.0, mu_n = 0.0;
-        for (int I = 0; I < 6; ++I) mean[I] = creal(s->spec[I * N3]) / (double)N3;
-        for (int kz = 0; kz < n; ++kz)
-            for (int ky = 0; ky < n; ++ky)
-                for (int kx = 0; kx < n; ++kx) {
-                    long v = kx + (long)n * (ky + (long)n * kz);
-                    double xi[3] = {2.0 * PI * freq(kx, n) / n, 2.0 * PI * freq(ky, n) / n, 2.0 * PI * freq(kz, n) / n};
-                    double complex T[3][3];
-                    for (int I = 0; I < 6; ++I) {
-                        T[MI[I]][MJ[I]] = s->spec[I * N3 + v] / mw(I);
-                        T[MJ[I]][MI[I]] = s->spec[I * N3 + v] / mw(I);
-                    }
-                    for (int i = 0; i < 3; ++i) {
-                        double complex dv = 0;
-                        for (int j = 0; j < 3; ++j) dv += xi[j] * T[i][j];
-                        acc += creal(dv) * creal(dv) + cimag(dv) * cimag(dv);
-                    }
-                }
+        acc = spectral_residual(n, s->spec, mean);
         for (int I = 0; I < 6; ++I) mn += mean[I] * mean[I];
         for (int a = 0; a < 5; ++a) mu_n += mean[U[a]] * mean[U[a]];
         double den = fmax(sqrt(mn), p->tau0);

@@ -72,6 +72,8 @@ void orc_km_update(const orc_params *p, double *rho, const double *gdot, double 
 int orc_point_model(const orc_params *p, const double *S, const double *M, double *sig, double *epsp,
                     double *rho, double *E, double dE33, double dt, int nsteps, double *sig33_hist);
 
+void orc_stress_residual(int n, const double *sig, double out[7]);
+
 /* ---- full state ---- */
 orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat,
                       uint64_t seed);

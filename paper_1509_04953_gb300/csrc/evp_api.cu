@@ -776,4 +776,31 @@ int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, 
     return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
 
+int evp_residual_scratch_bytes(int n, int precision, size_t *bytes) {
+    if (!pow2(n) || !bytes || precision < EVP_FP64 || precision > EVP_MIXED_FAST) return EVP_ERR_ARG;
+    *bytes = sizeof(double) * (size_t)fft_z_blocks(n, precision == EVP_FP64);
+    return EVP_OK;
+}
+
+int evp_stress_residual(int n, int precision, const void *sig_dev, void *spec_dev, void *scratch_dev,
+                        double *out_dev, void *cuda_stream) {
+    if (!pow2(n) || !sig_dev || !spec_dev || !scratch_dev || !out_dev) return EVP_ERR_ARG;
+    if (precision < EVP_FP64 || precision > EVP_MIXED_FAST) return EVP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int dbl = precision == EVP_FP64;
+    double *part = (double *)scratch_dev;
+    cudaError_t e;
+    if (dbl) {
+        e = fft_x_r2c<double>((const double *)sig_dev, spec_dev, n, 6, s);
+        if (e == cudaSuccess) e = fft_y<double>(spec_dev, n, 6, 0, s);
+        if (e == cudaSuccess) e = fft_z<double>(spec_dev, n, 6, Z_FWD_RESID, 0, 0, part, out_dev, s);
+    } else {
+        e = fft_x_r2c<float>((const float *)sig_dev, spec_dev, n, 6, s);
+        if (e == cudaSuccess) e = fft_y<float>(spec_dev, n, 6, 0, s);
+        if (e == cudaSuccess) e = fft_z<float>(spec_dev, n, 6, Z_FWD_RESID, 0, 0, part, out_dev, s);
+    }
+    if (e == cudaSuccess) e = reduce_partials(part, fft_z_blocks(n, dbl), 1, out_dev + 6, s);
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
 }  // extern "C"

@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__rest
 // the reference medium replaces it; the zero frequency is left to the macroscopic update.
 // Returns -Gamma:sigma in s (in place) and accumulates |xi.sigma|^2 (xi = 2 pi k/N).
 template <typename C, typename T>
-__device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int N, T lam0, T mu0, double &acc, double wgt) {
+__device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int N, T lam0, T mu0, double &acc, double wgt,
+                                            bool apply) {
     const int fx = kx;                                   // 0..N/2
     const int fy = ky <= (N >> 1) ? ky : ky - N;
     const int fz = kz <= (N >> 1) ? kz : kz - N;
@@ -216,6 +217,7 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
         acc += wgt * ((double)d1.x * d1.x + (double)d1.y * d1.y + (double)d2.x * d2.x + (double)d2.y * d2.y +
                       (double)d3.x * d3.x + (double)d3.y * d3.y);
     }
+    if (!apply) return;
     if (fx == 0 && fy == 0 && fz == 0) {
         for (int i = 0; i < 6; ++i) s[i] = cmk<C>(0, 0);
         return;
@@ -288,7 +290,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
     }
     __syncthreads();
     if (mode != Z_INV) fft_dit(buf, N, logN, nf * TX, ls, tw, false);
-    if (mode == Z_FWD_GAMMA_INV) {
+    if (mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) {
+        const bool apply = mode == Z_FWD_GAMMA_INV;
         double acc = 0.0;
         for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
             const int kz = t / TX, xl = t - kz * TX;
@@ -301,21 +304,23 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
                 for (int f = 0; f < 6; ++f) mean6[f] = (double)s6[f].x * inv;
             }
             const double wgt = (kx == 0 || kx == (N >> 1)) ? 1.0 : 2.0;
-            gamma_point<C, T>(s6, kx, ky, kz, N, lam0, mu0, acc, wgt);
-            for (int f = 0; f < 6; ++f) buf[(f * TX + xl) * ls + kz] = s6[f];
+            gamma_point<C, T>(s6, kx, ky, kz, N, lam0, mu0, acc, wgt, apply);
+            if (apply)
+                for (int f = 0; f < 6; ++f) buf[(f * TX + xl) * ls + kz] = s6[f];
         }
         __syncthreads();
         const double tot = block_sum(acc, red);
         if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = tot;
     }
-    if (mode != Z_FWD) fft_dif(buf, N, logN, nf * TX, ls, tw, true);
+    const bool fwd_only = mode == Z_FWD || mode == Z_FWD_RESID;
+    if (!fwd_only) fft_dif(buf, N, logN, nf * TX, ls, tw, true);
     for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
         const int f = t / (TX * N);
         const int r = t - f * TX * N;
         const int z = r / TX, xl = r - z * TX;
         const int kx = kx0 + xl;
         if (kx >= Hx) continue;
-        const int zi = (mode == Z_FWD) ? z : bitrev(z, logN);
+        const int zi = fwd_only ? z : bitrev(z, logN);
         spec[f * fstride + z * plane + (long)ky * Hx + kx] = buf[(f * TX + xl) * ls + zi];
     }
 }
@@ -377,7 +382,7 @@ cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double 
                   double *mean6, cudaStream_t s) {
     using C = typename CT<T>::type;
     constexpr int TX = tx_z<T>();
-    if (mode == Z_FWD_GAMMA_INV && nfields != 6) return cudaErrorInvalidValue;
+    if ((mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) && nfields != 6) return cudaErrorInvalidValue;
     const int Hx = n / 2 + 1;
     const int blocks = n * ((Hx + TX - 1) / TX);
     const size_t sm = sizeof(C) * (n / 2 + (size_t)nfields * TX * (n + 1));

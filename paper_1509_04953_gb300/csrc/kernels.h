@@ -13,7 +13,7 @@ struct MatConst {
 };
 
 // ---- fft.cu ----
-enum ZMode { Z_FWD = 0, Z_INV = 1, Z_FWD_GAMMA_INV = 2 };
+enum ZMode { Z_FWD = 0, Z_INV = 1, Z_FWD_GAMMA_INV = 2, Z_FWD_RESID = 3 };
 template <typename T> cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s);
 template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s);
 template <typename T>

@@ -89,10 +89,12 @@ def load():
     L.evp_voronoi.argtypes = [i, i, vp, vp, vp]
     L.evp_rfft3d.argtypes = [i, i, i, vp, vp, vp]
     L.evp_irfft3d.argtypes = [i, i, i, vp, vp, vp]
+    L.evp_residual_scratch_bytes.argtypes = [i, i, C.POINTER(sz)]
+    L.evp_stress_residual.argtypes = [i, i, vp, vp, vp, vp, vp]
     for f in ("evp_workspace_bytes", "evp_init", "evp_increment", "drx_nucleate", "pf_step", "get_fields",
               "set_fields", "evp_fields_bytes", "evp_get_scalars", "evp_set_scalars", "evp_set_solver",
               "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_kernel_times",
-              "evp_launch_count", "evp_newton_counts"):
+              "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -311,3 +313,24 @@ def irfft3d(spec):
     if rc != 0:
         raise EVPError(f"evp_irfft3d: {EVP_ERR.get(rc, rc)}")
     return out
+
+
+def stress_residual(sig):
+    """Equilibrium residual of a (6, N, N, N) stress field on the device (float32 or float64):
+    returns (spectrum, out) with out = [mean stress (6), sum |xi.sigma_hat|^2] as a CUDA tensor."""
+    torch = _torch()
+    n = sig.shape[1]
+    prec = 0 if sig.dtype == torch.float64 else 1
+    cd = torch.complex128 if prec == 0 else torch.complex64
+    L = load()
+    nb = C.c_size_t(0)
+    if L.evp_residual_scratch_bytes(n, prec, C.byref(nb)) != 0:
+        raise EVPError("evp_residual_scratch_bytes: bad size")
+    scratch = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    spec = torch.empty((6, n, n, n // 2 + 1), dtype=cd, device="cuda")
+    out = torch.empty(7, dtype=torch.float64, device="cuda")
+    rc = L.evp_stress_residual(n, prec, sig.contiguous().data_ptr(), spec.data_ptr(), scratch.data_ptr(),
+                               out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise EVPError(f"evp_stress_residual: {EVP_ERR.get(rc, rc)}")
+    return spec, out

@@ -69,6 +69,21 @@ def test_rfft3d_matches_oracle_fft(ev, n, prec):
     assert rel(back, x) < (1e-14 if prec == "fp64" else 2e-6)
 
 
+@pytest.mark.parametrize("n,prec", [(8, "fp64"), (16, "fp64"), (32, "fp64"), (16, "fp32"), (64, "fp32")])
+def test_stress_residual_matches_oracle(ev, n, prec):
+    import torch
+    rng = np.random.default_rng(n)
+    sig = rng.standard_normal((6, n, n, n)) * 50.0 + np.array([1, -2, 30, 0.5, 0, -1.0])[:, None, None, None]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    spec, out = ev.stress_residual(torch.tensor(sig, dtype=dt, device="cuda"))
+    want = O.stress_residual(n, sig.reshape(6, -1))
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert rel(out[:6].cpu().numpy(), want[:6]) < tol
+    assert abs(out[6].item() / want[6] - 1) < tol
+    full = O.fft3d(sig[2].astype(np.complex128), -1)
+    assert rel(spec[2].cpu().numpy(), full[:, :, : n // 2 + 1]) < (1e-13 if prec == "fp64" else 2e-6)
+
+
 # ------------------------------------------------------------------------------------------
 # a2-a7 fixed point and state update
 # ------------------------------------------------------------------------------------------
@@ -100,7 +115,9 @@ def test_converged_increments_match_oracle_fp64(ev, mat):
         assert st.err_eq <= 1e-9 and st.err_bc <= 1e-9
         assert rel(st.sig_mean, sto.sig_mean) < 1e-8
         assert rel(gpu.get("sig"), ref.field("sig")) < 1e-8
-        assert rel(gpu.get("rho"), ref.field("rho")) < 1e-10
+        # converged runs agree to the fixed-point tolerance; the density rate carries |tau|^n,
+        # so its relative difference is about n times that of the stress
+        assert rel(gpu.get("rho"), ref.field("rho")) < 1e-8
 
 
 def test_single_crystal_gpu_matches_point_model(ev, mat):
