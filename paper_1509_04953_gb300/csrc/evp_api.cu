@@ -517,8 +517,10 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         }
         for (int i = 0; i < 6; ++i) mean[i] = hs[i];
         double mn = 0, mu_n = 0;
-        for (int i = 0; i < 6; ++i) mn += mean[i] * mean[i];
-        mu_n = mn - mean[2] * mean[2];
+        for (int i = 0; i < 6; ++i) {
+            mn += mean[i] * mean[i];
+            if (i != 2) mu_n += mean[i] * mean[i];
+        }
         const double den = std::fmax(std::sqrt(mn), h->p.tau0);
         err_eq = std::sqrt(hs[6]) / ((double)N3 * den);
         err_bc = std::sqrt(std::fmax(mu_n, 0.0)) / den;

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__rest
 // the reference medium replaces it; the zero frequency is left to the macroscopic update.
 // Returns -Gamma:sigma in s (in place) and accumulates |xi.sigma|^2 (xi = 2 pi k/N).
 template <typename C, typename T>
-__device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int N, T lam0, T mu0, double &acc, double wgt,
+__device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int N, T lam0, T mu0, T &acc, bool partner,
                                             bool apply) {
     const int fx = kx;                                   // 0..N/2
     const int fy = ky <= (N >> 1) ? ky : ky - N;
@@ -208,14 +208,19 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
     const C t11 = s[0], t22 = s[1], t33 = s[2];
     const C t23 = cmk<C>(s[3].x * r2, s[3].y * r2), t13 = cmk<C>(s[4].x * r2, s[4].y * r2),
             t12 = cmk<C>(s[5].x * r2, s[5].y * r2);
-    {   // equilibrium residual
+    {   // equilibrium residual |xi.sigma_hat|^2 at this frequency and, for 0 < kx < N/2, at its
+        // Hermitian partner -k (whose signed frequency differs from -xi on Nyquist ky / kz planes)
         const T w = (T)(6.283185307179586476925 / N);
-        const T x1 = w * fx, x2 = w * fy, x3 = w * fz;
-        const C d1 = cmk<C>(x1 * t11.x + x2 * t12.x + x3 * t13.x, x1 * t11.y + x2 * t12.y + x3 * t13.y);
-        const C d2 = cmk<C>(x1 * t12.x + x2 * t22.x + x3 * t23.x, x1 * t12.y + x2 * t22.y + x3 * t23.y);
-        const C d3 = cmk<C>(x1 * t13.x + x2 * t23.x + x3 * t33.x, x1 * t13.y + x2 * t23.y + x3 * t33.y);
-        acc += wgt * ((double)d1.x * d1.x + (double)d1.y * d1.y + (double)d2.x * d2.x + (double)d2.y * d2.y +
-                      (double)d3.x * d3.x + (double)d3.y * d3.y);
+        const int nparts = partner ? 2 : 1;
+        for (int pt = 0; pt < nparts; ++pt) {
+            const int gy = pt == 0 ? fy : ((N - ky) % N <= (N >> 1) ? (N - ky) % N : (N - ky) % N - N);
+            const int gz = pt == 0 ? fz : ((N - kz) % N <= (N >> 1) ? (N - kz) % N : (N - kz) % N - N);
+            const T x1 = w * (pt == 0 ? fx : -fx), x2 = w * gy, x3 = w * gz;
+            const C d1 = cmk<C>(x1 * t11.x + x2 * t12.x + x3 * t13.x, x1 * t11.y + x2 * t12.y + x3 * t13.y);
+            const C d2 = cmk<C>(x1 * t12.x + x2 * t22.x + x3 * t23.x, x1 * t12.y + x2 * t22.y + x3 * t23.y);
+            const C d3 = cmk<C>(x1 * t13.x + x2 * t23.x + x3 * t33.x, x1 * t13.y + x2 * t23.y + x3 * t33.y);
+            acc += d1.x * d1.x + d1.y * d1.y + d2.x * d2.x + d2.y * d2.y + d3.x * d3.x + d3.y * d3.y;
+        }
     }
     if (!apply) return;
     if (fx == 0 && fy == 0 && fz == 0) {
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
     if (mode != Z_INV) fft_dit(buf, N, logN, nf * TX, ls, tw, false);
     if (mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) {
         const bool apply = mode == Z_FWD_GAMMA_INV;
-        double acc = 0.0;
+        T acc = (T)0;   // per-thread sum in the field precision; block and global sums in FP64
         for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
             const int kz = t / TX, xl = t - kz * TX;
             const int kx = kx0 + xl;
@@ -303,13 +308,13 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
                 const double inv = 1.0 / ((double)N * N * N);
                 for (int f = 0; f < 6; ++f) mean6[f] = (double)s6[f].x * inv;
             }
-            const double wgt = (kx == 0 || kx == (N >> 1)) ? 1.0 : 2.0;
-            gamma_point<C, T>(s6, kx, ky, kz, N, lam0, mu0, acc, wgt, apply);
+            const bool partner = !(kx == 0 || kx == (N >> 1));
+            gamma_point<C, T>(s6, kx, ky, kz, N, lam0, mu0, acc, partner, apply);
             if (apply)
                 for (int f = 0; f < 6; ++f) buf[(f * TX + xl) * ls + kz] = s6[f];
         }
         __syncthreads();
-        const double tot = block_sum(acc, red);
+        const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = tot;
     }
     const bool fwd_only = mode == Z_FWD || mode == Z_FWD_RESID;

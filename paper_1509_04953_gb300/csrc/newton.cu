@@ -5,7 +5,7 @@
 // gdot^a = gdot0 |tau^a/tau_c|^n sign(tau^a), tau^a = m^a:sigma. This is the implicit Euler
 // stress update of Eq. HookeLaw multiplied by the compliance S = C^-1; its Jacobian
 // K = S + dt sum_a (n gdot0 |x^a|^(n-1)/tau_c) m^a (x) m^a is symmetric positive definite, so the
-// 6x6 Newton system is solved by Cholesky, and r is the gradient of a convex potential Phi used
+// 6x6 Newton system is solved by an LDL^T factorisation, and r is the gradient of a convex potential Phi used
 // for Armijo backtracking. eps_tr = eps^{t+dt} - eps_p^t is carried directly (the "trial" elastic
 // strain), which keeps FP32 fields accurate when the total strain is large.
 #include <cmath>
@@ -94,44 +94,56 @@ __device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__
     e.phi = phi;
 }
 
-// Cholesky solve of K d = r (K packed lower, SPD). Returns false if K is not positive definite.
-template <typename TS, typename TA> __device__ __forceinline__ bool chol_solve(const TA Kin[21], const TA rin[6], TA dout[6]) {
-    TS L[21], y[6];
-#pragma unroll
-    for (int q = 0; q < 21; ++q) L[q] = (TS)Kin[q];
-    TS inv_d[6];
+// Reciprocal: FP32 division for float; for double an FP32 seed refined by two Newton steps
+// r <- r (2 - x r) (each doubles the correct bits: 24 -> 48 -> full precision).
+__device__ __forceinline__ float rcp_s(float x) { return 1.0f / x; }
+__device__ __forceinline__ double rcp_s(double x) {
+    double r = (double)(1.0f / (float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+// LDL^T solve of K d = r (K packed lower, SPD; no square roots). L is unit lower, D diagonal.
+// Returns false if a pivot is not positive.
+template <typename TS, typename TA> __device__ __forceinline__ bool ldl_solve(const TA Kin[21], const TA rin[6], TA dout[6]) {
+    TS L[21], invD[6], w[6];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        TS s = L[pk(j, j)];
+        TS dj = (TS)Kin[pk(j, j)];
 #pragma unroll
-        for (int k = 0; k < j; ++k) s -= L[pk(j, k)] * L[pk(j, k)];
-        ok = ok && (s > (TS)0);
-        s = s > (TS)0 ? s : (TS)1;
-        const TS dj = dsqrt(s);
-        inv_d[j] = drcp(dj);
+        for (int k = 0; k < j; ++k) {
+            w[k] = L[pk(j, k)] * L[pk(k, k)];   // L_jk D_k (L[kk] holds D_k)
+            dj -= w[k] * L[pk(j, k)];
+        }
+        ok = ok && (dj > (TS)0);
+        dj = dj > (TS)0 ? dj : (TS)1;
         L[pk(j, j)] = dj;
+        invD[j] = rcp_s(dj);
 #pragma unroll
         for (int i = j + 1; i < 6; ++i) {
-            TS t = L[pk(i, j)];
+            TS t = (TS)Kin[pk(i, j)];
 #pragma unroll
-            for (int k = 0; k < j; ++k) t -= L[pk(i, k)] * L[pk(j, k)];
-            L[pk(i, j)] = t * inv_d[j];
+            for (int k = 0; k < j; ++k) t -= L[pk(i, k)] * w[k];
+            L[pk(i, j)] = t * invD[j];
         }
     }
+    TS y[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         TS t = (TS)rin[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) t -= L[pk(i, k)] * y[k];
-        y[i] = t * inv_d[i];
+        y[i] = t;
     }
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
-        TS t = y[i];
+        TS t = y[i] * invD[i];
 #pragma unroll
         for (int k = i + 1; k < 6; ++k) t -= L[pk(k, i)] * y[k];
-        y[i] = t * inv_d[i];
+        y[i] = t;
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) dout[i] = (TA)y[i];
@@ -148,7 +160,7 @@ __device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA 
     nevals = 1;
     for (int it = 1; it <= maxit; ++it) {
         TA d[6];
-        if (!chol_solve<TS, TA>(e.K, e.r, d)) return -it;
+        if (!ldl_solve<TS, TA>(e.K, e.r, d)) return -it;
         TA rd = (TA)0, dn = (TA)0, sn = (TA)0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -158,6 +170,13 @@ __device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA 
         }
         dn = dsqrt(dn);
         const TA scale = dsqrt(sn) + tauc;
+        if (dn <= tol * scale) {
+            // The full step is below the stopping tolerance (and far below the line-search
+            // threshold), so it is taken and the iteration ends without evaluating the new point.
+#pragma unroll
+            for (int i = 0; i < 6; ++i) sg[i] -= d[i];
+            return it;
+        }
         const TA phi0 = e.phi;
         TA s = (TA)1, st[6];
         bool ok = false;
