@@ -193,6 +193,23 @@ int evp_residual_scratch_bytes(int n, int precision, size_t *bytes);
 int evp_stress_residual(int n, int precision, const void *sig_dev, void *spec_dev, void *scratch_dev,
                         double *out_dev, void *cuda_stream);
 
+/* Allocation-free form of evp_stress_residual (the paper has no counterpart: it is a service of
+ * this library). Some callers cannot allocate device memory at the point where they need the
+ * residual -- for instance code in a host callback or another context where cudaMalloc is not
+ * allowed, or a plug-in whose host application owns every device allocation -- and so cannot
+ * supply the scratch buffer evp_stress_residual asks for. This entry point takes the same inputs
+ * and outputs (sig_dev, spec_dev, out_dev, all caller-owned) but keeps its scratch in a fixed
+ * array inside the library: 8192 doubles (64 KiB), enough for every n <= 256 in any precision,
+ * held by each GPU that loads the library until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine. The first call on a device looks up that array's device
+ * address (once per device, with that device current), so make the first call on each device
+ * before any stream capture. All calls share the one array: calls that overlap on the GPU race
+ * and must be serialised by the caller (e.g. one stream). Every scratch slot a call reads is
+ * written earlier in the same call, so nothing needs clearing between calls. Sizes whose
+ * partial sums would not fit return EVP_ERR_ARG. */
+int evp_stress_residual_noalloc(int n, int precision, const void *sig_dev, void *spec_dev, double *out_dev,
+                                void *cuda_stream);
+
 /* inverse (complex-to-real) of evp_rfft3d, unnormalised: out = N^3 * field. in is overwritten. */
 int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, void *cuda_stream);
 
