@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cu128")
     ap.add_argument("--fp64-steps", type=int, default=-1, help="FP64 comparison increments (-1 = warmup+steps)")
+    ap.add_argument("--fast-steps", type=int, default=2, help="timed increments of the FP32-solve mixed path")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
@@ -237,6 +238,9 @@ def native(args, ws, rank, local):
     res["newton"] = {"solves": solves, "evals": evals, "solves_per_voxel_iter": solves / (N3 * iters),
                      "evals_per_voxel_iter": evals / (N3 * iters)}
     res["roofline"] = roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision="mixed")
+    res["memory_bound_kernels"] = memory_kernels(ktimes, wl, N3, "mixed", pk)
+    if args.fast_steps > 0:
+        res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
     # FP64 companion run on the same seeded input
     n64 = args.warmup + args.steps if args.fp64_steps < 0 else args.fp64_steps
     if n64 > 0:
@@ -247,31 +251,67 @@ def native(args, ws, rank, local):
     return res
 
 
+ALG_BYTES_WORDS = None   # see hbm_bytes_per_voxel
+
+
+def hbm_bytes_per_voxel(kernel, n, T):
+    """Algorithmic HBM bytes per voxel for one launch of a memory-bound kernel (each field word read
+    and written once; half spectra have (n/2+1)/n complex words per real word)."""
+    Hw = (n // 2 + 1) / n
+    return {"fft_x_r2c": (6 + 12 * Hw) * T, "fft_y_fwd": 24 * Hw * T, "fft_z_gamma": 24 * Hw * T,
+            "fft_y_inv": 24 * Hw * T, "fft_x_c2r_update": (12 * Hw + 12) * T,
+            "predictor": (12 + 6 + 6 + 6 + 1) * T, "state_update": (6 + 1 + 6 + 4 * 6 + 24) * T + 4 + 8,
+            "pf_step": 2 * 8 * (4 + T) + 8}.get(kernel)
+
+
 def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision):
     ms, n = ktimes[dom]
     avg_s = ms / 1e3 / max(n, 1)
     T = 4 if precision != "fp64" else 8
-    Hw = (wl.n // 2 + 1) / wl.n    # half-spectrum words per real word
-    bytes_per_voxel = {
-        "fft_x_r2c": (6 + 6 * Hw * 2) * T, "fft_y_fwd": 2 * 6 * Hw * 2 * T, "fft_z_gamma": 2 * 6 * Hw * 2 * T,
-        "fft_y_inv": 2 * 6 * Hw * 2 * T, "fft_x_c2r_update": (6 * Hw * 2 + 12) * T,
-        "predictor": (12 + 18 + 7) * T, "state_update": (6 + 1 + 1 + 6 + 6 * 4 + 24) * T + 8,
-        "pf_step": 2 * 8 * (4 + T) + 8,
-    }
     if dom == "newton":
-        flops = NEWTON_FLOPS_EVAL * evals + NEWTON_FLOPS_SOLVE * solves
+        # FP64 pipe: the 6x6 LDL^T solve (about 150 algorithmic flops) in the mixed path; everything
+        # in the FP64 path. FP32 pipe for the fast mixed path. Peaks: FP64 1.25 TFLOP/s (nominal;
+        # 1.203 measured with an FMA-chain probe), FP32 152 SMs x 128 lanes x 2 x 2.07 GHz.
+        if precision == "mixed":
+            flops, peak, pipe = NEWTON_FLOPS_SOLVE * solves, 1.25, "fp64"
+        elif precision == "fp64":
+            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + NEWTON_FLOPS_SOLVE * solves, 1.25, "fp64"
+        else:
+            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + NEWTON_FLOPS_SOLVE * solves, 152 * 128 * 2 * 2.070e9 / 1e12, "fp32"
         achieved = flops / (ms / 1e3) / 1e12
-        # FP32 vector peak: 152 SMs x 128 lanes x 2 flop x max clock (2070 MHz)
-        peak = 152 * 128 * 2 * 2.070e9 / 1e12 if precision != "fp64" else 1.25
-        return {"bound": "alu", "kernel": "newton", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "note": "algorithmic flops = 1140 x evaluations + 160 x 6x6 solves; peak derived from unit counts"
-                        " and max clock (FP32 when mixed, FP64 nominal when fp64)"}
-    b = bytes_per_voxel.get(dom, 0.0) * N3
+        return {"bound": "alu", "kernel": "newton", "pipe": pipe, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "note": "algorithmic flops: 150 per 6x6 LDL^T solve, 1140 per residual/tangent evaluation; "
+                        "peak from unit counts and clock (FP64 nominal 1.25 TFLOP/s)"}
+    b = hbm_bytes_per_voxel(dom, wl.n, T) * N3
     achieved = b / avg_s / 1e9
     peak = pk.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None, "peak_source": pk_kind}
+
+
+def memory_kernels(ktimes, wl, N3, precision, pk):
+    T = 4 if precision != "fp64" else 8
+    out = {}
+    for k, (ms, n) in ktimes.items():
+        bpv = hbm_bytes_per_voxel(k, wl.n, T)
+        if bpv is None or n == 0:
+            continue
+        gbs = bpv * N3 / (ms / 1e3 / n) / 1e9
+        out[k] = {"avg_us": round(1e3 * ms / n, 2), "GB/s": round(gbs, 1), "frac": round(gbs / pk.get("hbm_gbs", 6800.0), 3)}
+    return out
+
+
+def fast_companion(args, wl, g0, quat, mat, torch, evp):
+    """The mixed path with the 6x6 Newton solve in FP32 (EVP_MIXED_FAST), same input."""
+    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="mixed_fast", tol=args.tol, max_iter=5000)
+    run_steps(s, 1, wl.dE33, wl.dt, wl.pf_steps, torch)
+    h = run_steps(s, args.fast_steps, wl.dE33, wl.dt, wl.pf_steps, torch)
+    evp_s = sum(r["evp_ms"] for r in h) / 1e3
+    step_s = sum(r["step_ms"] for r in h) / 1e3
+    return {"voxel_iters_per_s": wl.n ** 3 * sum(r["it"] for r in h) / evp_s,
+            "drx_increments_per_s": len(h) / step_s, "increments": len(h),
+            "fixed_point_iterations": [r["it"] for r in h]}
 
 
 def fp64_companion(args, wl, g0, quat, mat, nsteps, mixed_hist, torch, evp):

@@ -93,6 +93,10 @@ def lib():
         L.orc_increment.argtypes = [C.c_void_p, C.c_double, C.c_double, C.POINTER(Stats)]
         L.orc_nucleate.restype = C.c_int
         L.orc_nucleate.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)]
+        L.orc_loss_grad.restype = C.c_int
+        L.orc_loss_grad.argtypes = [C.POINTER(Config), C.POINTER(Params), _ip, _dp, C.c_uint64, C.c_int, C.c_double,
+                                    C.c_double, C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
+                                    C.c_double]
         L.orc_pf_step.restype = C.c_int
         L.orc_pf_step.argtypes = [C.c_void_p, C.c_int, C.POINTER(PFStats)]
         L.orc_pf_step_dense.restype = C.c_int
@@ -231,6 +235,24 @@ def point_model(mat, S, M, dE33, dt, nsteps, rho0=None):
                                np.ascontiguousarray(M, dtype=np.float64).reshape(-1), sig, epsp, rho, E,
                                dE33, dt, nsteps, hist)
     return rc, hist[:nsteps], dict(sig=sig, epsp=epsp, rho=rho, E=E)
+
+
+def loss_grad(n, grains, g0, quat, mat, seed, T, dE33, dt, target=None, want_grad=True, tol=1e-12,
+              max_iter=20000, adj_tol=1e-12, nthreads=0):
+    """FP64 loss L = sum_t (<sigma33>_t - target_t)^2 over T increments, its adjoint gradient with
+    respect to (k1, k2, tau0, n) and the stress-strain curve."""
+    cfg = Config(n, grains, 8, tol, max_iter, 0, 1e-13, 60, 1, nthreads)
+    p = make_params(mat)
+    g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)
+    q = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1)
+    tg = None if target is None else np.ascontiguousarray(target, dtype=np.float64)
+    loss = C.c_double(0.0)
+    grad = np.zeros(4)
+    s33 = np.zeros(T)
+    rc = lib().orc_loss_grad(C.byref(cfg), C.byref(p), g0, q, seed, T, dE33, dt,
+                             None if tg is None else tg.ctypes.data, C.byref(loss),
+                             grad.ctypes.data if want_grad else None, s33.ctypes.data, adj_tol)
+    return rc, loss.value, grad, s33
 
 
 class State:

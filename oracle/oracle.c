@@ -755,6 +755,247 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
     return status;
 }
 
+
+/* ------------------------------------------------------------------------------------------
+ * Differentiation (spec direction 3; the paper calibrates by hand, Sec. 3): gradient of
+ * L = sum_t (<sigma33>_t - target_t)^2 over T mechanical increments with respect to
+ * theta = (k1, k2, tau0, n), by the discrete adjoint of the converged increments. Nucleation and
+ * phase-field events are not part of this path (held fixed; none occur in its workloads).
+ *
+ * Increment t maps (eps_p^{t-1}, rho^{t-1}; theta) to sigma^t through the converged equilibrium
+ * problem, then eps_p^t = eps_p^{t-1} + dt sum_a m^a gdot^a(sigma^t) and the KM update of rho.
+ * Linearising the converged problem: d sigma = C_t d eps + p, C_t = K^-1 (the local Newton
+ * Jacobian's inverse), p = -C_t d eps_p + dSigma/dtau_c d tau_c + dSigma/dn dn, with d eps in
+ * V = {compatible fluctuations} + {uniform strains with E33 = 0} and <eta, C_t d eps + p> = 0 for
+ * all eta in V. For a load sigma_bar on sigma^t the adjoint field eps_bar in V solves
+ * <eta, C_t eps_bar + C_t sigma_bar> = 0 for all eta in V (the same kind of heterogeneous
+ * problem, solved here by the same basic Green-operator iteration), and
+ * sum_x sigma_bar . d sigma = sum_x (sigma_bar + eps_bar) . p.
+ * ---------------------------------------------------------------------------------------- */
+
+/* per-voxel local quantities at a converged stress: gdot, dgdot/dtau, C_t = K^-1 */
+static void adj_local(const orc_params *p, const double *S, const double *M, double tauc, double dt,
+                      const double sig[6], double gd[12], double gp[12], double lnx[12], double Ct[36]) {
+    double K[36];
+    for (int i = 0; i < 36; ++i) K[i] = S[i];
+    for (int a = 0; a < 12; ++a) {
+        double tau = 0.0;
+        for (int I = 0; I < 6; ++I) tau += M[6 * a + I] * sig[I];
+        double x = tau / tauc, ax = fabs(x);
+        double pw = ax > 0.0 ? pow(ax, p->n) : 0.0;
+        gd[a] = ax > 0.0 ? p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0) : 0.0;
+        gp[a] = ax > 0.0 ? p->n * p->gdot0 * (pw / ax) / tauc : 0.0;   /* d gdot / d tau */
+        lnx[a] = ax > 0.0 ? log(ax) : 0.0;
+        for (int I = 0; I < 6; ++I)
+            for (int J = 0; J < 6; ++J) K[6 * I + J] += dt * gp[a] * M[6 * a + I] * M[6 * a + J];
+    }
+    inv_gj(6, K, Ct);
+}
+
+static void matvec6(const double *A, const double *x, double *y) {
+    for (int I = 0; I < 6; ++I) {
+        double s = 0.0;
+        for (int J = 0; J < 6; ++J) s += A[6 * I + J] * x[J];
+        y[I] = s;
+    }
+}
+
+/* Solve <eta, Ct eb + a> = 0 for all eta in V by the basic scheme (Gamma0, mixed-BC update). */
+static int adj_solve(int n, double lam0, double mu0, const double *Ct, const double *a, double *eb, double tol,
+                     int maxit, double complex *spec) {
+    const long N3 = (long)n * n * n;
+    double C0[36], S0[36];
+    for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) C0[6 * I + J] = (I < 3 && J < 3 ? lam0 : 0.0) + (I == J ? 2.0 * mu0 : 0.0);
+    inv_gj(6, C0, S0);
+    const int U[5] = {0, 1, 3, 4, 5};
+    double C0uu[25], C0uu_inv[25];
+    for (int x = 0; x < 5; ++x)
+        for (int y = 0; y < 5; ++y) C0uu[5 * x + y] = C0[6 * U[x] + U[y]];
+    inv_gj(5, C0uu, C0uu_inv);
+    double *tau = (double *)xcalloc(6 * N3, sizeof(double));
+    double scale = 0.0;
+    for (long i = 0; i < 6 * N3; ++i) scale = fmax(scale, fabs(a[i]));
+    if (scale == 0.0) { free(tau); return 0; }
+    memset(eb, 0, 6 * N3 * sizeof(double));
+    int it;
+    for (it = 1; it <= maxit; ++it) {
+        for (long v = 0; v < N3; ++v) {
+            double e[6], y[6];
+            for (int I = 0; I < 6; ++I) e[I] = eb[I * N3 + v];
+            matvec6(Ct + 36 * v, e, y);
+            for (int I = 0; I < 6; ++I) tau[I * N3 + v] = y[I] + a[I * N3 + v];
+        }
+        for (int I = 0; I < 6; ++I) {
+            for (long v = 0; v < N3; ++v) spec[I * N3 + v] = tau[I * N3 + v];
+            orc_fft3d(n, spec + I * N3, -1);
+        }
+        double mean[6];
+        double acc = spectral_residual(n, spec, mean);
+        double mu_n = 0.0;
+        for (int x = 0; x < 5; ++x) mu_n += mean[U[x]] * mean[U[x]];
+        double err = sqrt(acc) / ((double)N3 * scale) + sqrt(mu_n) / scale;
+        if (err <= tol) break;
+        double dEk[6] = {0, 0, 0, 0, 0, 0};
+        for (int x = 0; x < 5; ++x) {
+            double v = 0.0;
+            for (int y = 0; y < 5; ++y) v += C0uu_inv[5 * x + y] * (0.0 - mean[U[y]]);
+            dEk[U[x]] = v;
+        }
+        for (int kz = 0; kz < n; ++kz)
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx < n; ++kx) {
+                    long v = kx + (long)n * (ky + (long)n * kz);
+                    double complex sh[6];
+                    for (int I = 0; I < 6; ++I) sh[I] = spec[I * N3 + v];
+                    double Gm[36];
+                    if (kx == 0 && ky == 0 && kz == 0) {
+                        for (int I = 0; I < 6; ++I) spec[I * N3 + v] = 0;
+                        continue;
+                    }
+                    int nyq = (n > 1) && (kx == n / 2 || ky == n / 2 || kz == n / 2);
+                    if (nyq) memcpy(Gm, S0, sizeof Gm);
+                    else {
+                        double xi[3] = {freq(kx, n), freq(ky, n), freq(kz, n)};
+                        orc_gamma0(xi, lam0, mu0, Gm);
+                    }
+                    for (int I = 0; I < 6; ++I) {
+                        double complex acc2 = 0;
+                        for (int J = 0; J < 6; ++J) acc2 += Gm[6 * I + J] * sh[J];
+                        spec[I * N3 + v] = -acc2;
+                    }
+                }
+        for (int I = 0; I < 6; ++I) {
+            orc_fft3d(n, spec + I * N3, +1);
+            for (long v = 0; v < N3; ++v) eb[I * N3 + v] += creal(spec[I * N3 + v]) / (double)N3 + dEk[I];
+        }
+    }
+    free(tau);
+    return it > maxit ? -4 : 0;
+}
+
+int orc_loss_grad(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat, uint64_t seed,
+                  int T, double dE33, double dt, const double *target, double *loss, double grad[4], double *sig33,
+                  double adj_tol) {
+    orc_state *s = orc_create(cfg, p, g0, quat, seed);
+    const long N3 = s->N3;
+    const int n = s->n;
+    const double mu = mu_voigt(p), lam = lam_voigt(p);
+    double *rho_tape = (double *)xcalloc((size_t)T * 12 * N3, sizeof(double));
+    double *sig_tape = (double *)xcalloc((size_t)T * 6 * N3, sizeof(double));
+    double *g = (double *)xcalloc((size_t)T, sizeof(double));
+    int rc = 0;
+    *loss = 0.0;
+    for (int t = 0; t < T; ++t) {
+        memcpy(rho_tape + (size_t)t * 12 * N3, s->rho, 12 * N3 * sizeof(double));
+        orc_stats st;
+        rc = orc_increment(s, dE33, dt, &st);
+        if (rc < 0) goto done;
+        memcpy(sig_tape + (size_t)t * 6 * N3, s->sig, 6 * N3 * sizeof(double));
+        double r = st.sig_mean[2] - (target ? target[t] : 0.0);
+        *loss += r * r;
+        g[t] = 2.0 * r;
+        if (sig33) sig33[t] = st.sig_mean[2];
+    }
+    if (grad) {
+        double *lam_ep = (double *)xcalloc(6 * N3, sizeof(double));
+        double *lam_rho = (double *)xcalloc(12 * N3, sizeof(double));
+        double *sbar = (double *)xcalloc(6 * N3, sizeof(double));
+        double *aa = (double *)xcalloc(6 * N3, sizeof(double));
+        double *eb = (double *)xcalloc(6 * N3, sizeof(double));
+        double *Ct = (double *)xcalloc(36 * N3, sizeof(double));
+        double *taubar = (double *)xcalloc(N3, sizeof(double));
+        double gk1 = 0, gk2 = 0, gt0 = 0, gn = 0;
+        const double amb = p->alpha * mu * p->b;
+        for (int t = T - 1; t >= 0 && rc == 0; --t) {
+            const double *rho = rho_tape + (size_t)t * 12 * N3;
+            const double *sg = sig_tape + (size_t)t * 6 * N3;
+            /* explicit part of the state update at fixed sigma^t, and the adjoint load sigma_bar */
+            for (long v = 0; v < N3; ++v) {
+                const int gr = s->g0[v];
+                const double *M = s->M + 72 * gr;
+                double rf = 0.0;
+                for (int a = 0; a < 12; ++a) rf += rho[a * N3 + v];
+                const double srf = sqrt(rf), tc = p->tau0 + amb * srf;
+                double sgv[6], gd[12], gp[12], lx[12];
+                for (int I = 0; I < 6; ++I) sgv[I] = sg[I * N3 + v];
+                adj_local(p, s->S + 36 * gr, M, tc, dt, sgv, gd, gp, lx, Ct + 36 * v);
+                double le[6], lr[12], lr_new[12], sb[6] = {0, 0, 0, 0, 0, 0};
+                for (int I = 0; I < 6; ++I) le[I] = lam_ep[I * N3 + v];
+                for (int a = 0; a < 12; ++a) lr[a] = lam_rho[a * N3 + v];
+                sb[2] += g[t] / (double)N3;                      /* d<sigma33>/d sigma */
+                double tb = 0.0, sum_lr_gd = 0.0;
+                for (int a = 0; a < 12; ++a) {
+                    const double *m = M + 6 * a;
+                    double mle = 0.0;
+                    for (int I = 0; I < 6; ++I) mle += m[I] * le[I];
+                    const double hr = p->k1 * srf - p->k2 * rho[a * N3 + v];
+                    const double sgn = gd[a] < 0.0 ? -1.0 : 1.0, agd = fabs(gd[a]);
+                    /* through gdot(sigma): eps_p and rho updates */
+                    const double coef = dt * gp[a] * (mle + lr[a] * hr * sgn);
+                    for (int I = 0; I < 6; ++I) sb[I] += coef * m[I];
+                    /* direct tau_c dependence of gdot: d gdot / d tau_c = -n gdot / tau_c */
+                    tb += dt * (mle * (-p->n * gd[a] / tc) + lr[a] * hr * (-p->n * agd / tc));
+                    /* direct n dependence: d gdot / d n = gdot ln|x| */
+                    gn += dt * (mle * gd[a] * lx[a] + lr[a] * hr * agd * lx[a]);
+                    gk1 += lr[a] * dt * srf * agd;
+                    gk2 += lr[a] * dt * (-rho[a * N3 + v]) * agd;
+                    sum_lr_gd += lr[a] * dt * p->k1 * agd;
+                }
+                /* d rho^a_t / d rho^b_{t-1} = delta_ab (1 - dt k2 |gdot_a|) + dt k1 |gdot_a| / (2 sqrt(rho_F)) */
+                for (int b = 0; b < 12; ++b)
+                    lr_new[b] = lr[b] * (1.0 - dt * p->k2 * fabs(gd[b])) + sum_lr_gd / (2.0 * srf);
+                for (int b = 0; b < 12; ++b) lam_rho[b * N3 + v] = lr_new[b];
+                taubar[v] = tb;
+                double av[6];
+                matvec6(Ct + 36 * v, sb, av);
+                for (int I = 0; I < 6; ++I) {
+                    sbar[I * N3 + v] = sb[I];
+                    aa[I * N3 + v] = av[I];
+                }
+            }
+            /* adjoint equilibrium solve */
+            if (adj_solve(n, lam, mu, Ct, aa, eb, adj_tol, 100000, s->spec) != 0) { rc = -4; break; }
+            /* implicit part: p_bar = sigma_bar + eps_bar */
+            for (long v = 0; v < N3; ++v) {
+                const int gr = s->g0[v];
+                const double *M = s->M + 72 * gr;
+                const double *rho = rho_tape + (size_t)t * 12 * N3;
+                double rf = 0.0;
+                for (int a = 0; a < 12; ++a) rf += rho[a * N3 + v];
+                const double srf = sqrt(rf), tc = p->tau0 + amb * srf;
+                double sgv[6], gd[12], gp[12], lx[12], Cl[36];
+                for (int I = 0; I < 6; ++I) sgv[I] = sg[I * N3 + v];
+                adj_local(p, s->S + 36 * gr, M, tc, dt, sgv, gd, gp, lx, Cl);
+                double pb[6], cp[6];
+                for (int I = 0; I < 6; ++I) pb[I] = sbar[I * N3 + v] + eb[I * N3 + v];
+                matvec6(Cl, pb, cp);
+                for (int I = 0; I < 6; ++I) lam_ep[I * N3 + v] -= cp[I];   /* dp/d eps_p = -C_t */
+                double tb = taubar[v];
+                for (int a = 0; a < 12; ++a) {
+                    double mc = 0.0;
+                    for (int I = 0; I < 6; ++I) mc += M[6 * a + I] * cp[I];
+                    tb += mc * dt * p->n * gd[a] / tc;                       /* dSigma/dtau_c */
+                    gn += -mc * dt * gd[a] * lx[a];                          /* dSigma/dn */
+                }
+                gt0 += tb;                                                   /* tau_c = tau0 + ... */
+                for (int b = 0; b < 12; ++b) lam_rho[b * N3 + v] += tb * amb / (2.0 * srf);
+            }
+        }
+        grad[0] = gk1;
+        grad[1] = gk2;
+        grad[2] = gt0;
+        grad[3] = gn;
+        free(lam_ep); free(lam_rho); free(sbar); free(aa); free(eb); free(Ct); free(taubar);
+    }
+done:
+    free(rho_tape);
+    free(sig_tape);
+    free(g);
+    orc_destroy(s);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------------------------
  * a8: stochastic DRX nucleation (Sec. 2.3 and Appendix). A grain-boundary voxel (a face
  * neighbour carries another grain id) nucleates iff k(x) = rho_tot(x) > kappa(x)

@@ -82,6 +82,9 @@ double *orc_field(orc_state *s, const char *name);
 int32_t *orc_ifield(orc_state *s, const char *name);
 int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out);
 int orc_nucleate(orc_state *s, uint64_t step, int32_t *n_new);
+int orc_loss_grad(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat, uint64_t seed,
+                  int T, double dE33, double dt, const double *target, double *loss, double grad[4], double *sig33,
+                  double adj_tol);
 int orc_pf_step(orc_state *s, int nsteps, orc_pf_stats *out);
 int orc_pf_step_dense(orc_state *s, int nsteps);
 double orc_pf_energy(orc_state *s);

@@ -1,5 +1,5 @@
 // Hand-written 3D FFT passes for the Green-operator fixed point (Sec. 2.1: the spectral solve of
-// the implicit stress update). Radix-2 butterflies in shared memory; one HBM round trip per axis:
+// the implicit stress update). One HBM round trip per axis:
 //   x pass : real -> half spectrum, two real rows packed as one complex row
 //   y pass : complex, lines along y loaded as [kx tile][y] (coalesced along kx)
 //   z pass : complex, the six stress components of a [kx tile] x z slab of one ky; the forward
@@ -7,6 +7,11 @@
 //            transform run on the slab while it sits in shared memory
 //   x pass : half spectrum -> real, fused with the strain update eps += field/N^3 + dE
 // Spectra are [field][z|kz][ky][kx] with kx = 0..N/2 (row length N/2+1).
+//
+// Line transforms: Stockham auto-sort with register butterflies. N = R1 * R2 with R1 = min(N, 16)
+// and R2 = N / R1 <= 16: a radix-R1 pass (no twiddles) and a radix-R2 pass (twiddles W_N^{r j}),
+// natural order in and out. Shared-memory lines are padded (one slot per 16) so that the strided
+// pass-1 writes hit distinct banks.
 #include <cmath>
 #include <cstdio>
 
@@ -18,115 +23,190 @@ namespace evp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRowPairs = 8;  // row pairs per CTA in the x passes
 
-// In-place radix-2 decimation-in-time on nlines lines of length N (input bit-reversed, output
-// natural order). Line l, element j lives at buf[l*ls + j]. tw[k] = exp(-2 pi i k/N), k < N/2.
-template <typename C>
-__device__ void fft_dit(C *buf, int N, int logN, int nlines, int ls, const C *tw, bool inverse) {
-    const int half = N >> 1;
-    const int nb = nlines * half;
-    for (int s = 0; s < logN; ++s) {
-        const int h = 1 << s;
-        const int tws = half >> s;
-        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-            const int l = t >> (logN - 1), j = t & (half - 1);
-            const int pos = j & (h - 1), grp = j >> s;
-            const int i0 = l * ls + grp * 2 * h + pos, i1 = i0 + h;
-            C w = tw[pos * tws];
-            if (inverse) w.y = -w.y;
-            const C a = buf[i0], b = cmul(buf[i1], w);
-            buf[i0] = cadd(a, b);
-            buf[i1] = csub(a, b);
+template <int N> struct Shape {
+    static constexpr int R1 = N < 16 ? N : 16;
+    static constexpr int R2 = N / R1;
+    static constexpr int LS = N + N / 16 + 1;   // padded line stride
+};
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+template <int L> struct Log2 { static constexpr int v = 1 + Log2<L / 2>::v; };
+template <> struct Log2<1> { static constexpr int v = 0; };
+
+// cos(pi m / 8), m = 0..15: exact values of the sixteenth roots of unity.
+__host__ __device__ constexpr double cos16(int m) {
+    return m == 0 ? 1.0 : m == 1 ? 0.92387953251128675613 : m == 2 ? 0.70710678118654752440
+         : m == 3 ? 0.38268343236508977173 : m == 4 ? 0.0 : m == 5 ? -0.38268343236508977173
+         : m == 6 ? -0.70710678118654752440 : m == 7 ? -0.92387953251128675613 : m == 8 ? -1.0
+         : m == 9 ? -0.92387953251128675613 : m == 10 ? -0.70710678118654752440
+         : m == 11 ? -0.38268343236508977173 : m == 12 ? 0.0 : m == 13 ? 0.38268343236508977173
+         : m == 14 ? 0.70710678118654752440 : 0.92387953251128675613;
+}
+
+template <int M> __host__ __device__ constexpr int brev_c(int i) {
+    int r = 0;
+    for (int b = 0; b < M; ++b) r |= ((i >> b) & 1) << (M - 1 - b);
+    return r;
+}
+
+// Length-R DFT of x held in registers (radix-2 network with constant twiddles). The forward
+// twiddle W_{2h}^p = exp(-2 pi i p / 2h) = (cos(pi m/8), -sin(pi m/8)), m = 16 p / 2h, with
+// sin(pi m/8) = cos(pi (m + 12)/8). INV uses the conjugate.
+template <int R, bool INV, typename C> __device__ __forceinline__ void dft_reg(C (&x)[R]) {
+    using T = decltype(C::x);
+    constexpr int LR = Log2<R>::v;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int j = brev_c<LR>(i);
+        if (j > i) { const C t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+            for (int p = 0; p < h; ++p) {
+                const int m = p * (16 / (2 * h));
+                const T wc = (T)cos16(m);
+                const T ws = INV ? (T)cos16((m + 12) & 15) : -(T)cos16((m + 12) & 15);
+                const C b0 = x[g + p + h];
+                const C b = cmk<C>(b0.x * wc - b0.y * ws, b0.x * ws + b0.y * wc);
+                const C a = x[g + p];
+                x[g + p] = cadd(a, b);
+                x[g + p + h] = csub(a, b);
+            }
+        }
+    }
+}
+
+// In-place transform of nlines padded lines (line l at buf + l*LS). tw[m] = exp(-2 pi i m / N),
+// m < N. Starts after and ends with a barrier. MAXIT >= ceil(nlines * (N/R1) / blockDim).
+template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *buf, int nlines, const C *tw) {
+    constexpr int R1 = Shape<N>::R1, R2 = Shape<N>::R2, LS = Shape<N>::LS;
+    constexpr int M1 = N / R1;
+    if constexpr (R2 == 1) {   // a single radix-N pass; every line is owned by one thread
+        for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
+            C v[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[r] = buf[l * LS + pad16(r)];
+            dft_reg<R1, INV>(v);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) buf[l * LS + pad16(r)] = v[r];
+        }
+        __syncthreads();
+    } else {
+        // pass 1: radix R1, Ns = 1: item (l, j < M1) reads slots j + M1 r and writes j R1 + r, so
+        // every read completes before any write (held in registers across a barrier)
+        const int items = nlines * M1;
+        C v[MAXIT][R1];
+#pragma unroll
+        for (int it = 0; it < MAXIT; ++it) {
+            const int t = threadIdx.x + it * blockDim.x;
+            if (t < items) {
+                const int l = t / M1, j = t - l * M1;
+#pragma unroll
+                for (int r = 0; r < R1; ++r) v[it][r] = buf[l * LS + pad16(j + r * M1)];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < MAXIT; ++it) {
+            const int t = threadIdx.x + it * blockDim.x;
+            if (t < items) {
+                const int l = t / M1, j = t - l * M1;
+                dft_reg<R1, INV>(v[it]);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) buf[l * LS + pad16(j * R1 + r)] = v[it][r];
+            }
+        }
+        __syncthreads();
+        // pass 2: radix R2, Ns = R1 = 16: item (l, j < 16) reads and writes slots j + 16 r only
+        for (int t = threadIdx.x; t < nlines * 16; t += blockDim.x) {
+            const int l = t >> 4, j = t & 15;
+            C u[R2];
+#pragma unroll
+            for (int r = 0; r < R2; ++r) {
+                C a = buf[l * LS + pad16(j + 16 * r)];
+                if (r > 0) {
+                    C w = tw[r * j];
+                    if (INV) w.y = -w.y;
+                    a = cmul(a, w);
+                }
+                u[r] = a;
+            }
+            dft_reg<R2, INV>(u);
+#pragma unroll
+            for (int r = 0; r < R2; ++r) buf[l * LS + pad16(j + 16 * r)] = u[r];
         }
         __syncthreads();
     }
 }
 
-// Radix-2 decimation-in-frequency (input natural, output bit-reversed).
-template <typename C>
-__device__ void fft_dif(C *buf, int N, int logN, int nlines, int ls, const C *tw, bool inverse) {
-    const int half = N >> 1;
-    const int nb = nlines * half;
-    for (int s = logN - 1; s >= 0; --s) {
-        const int h = 1 << s;
-        const int tws = half >> s;
-        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-            const int l = t >> (logN - 1), j = t & (half - 1);
-            const int pos = j & (h - 1), grp = j >> s;
-            const int i0 = l * ls + grp * 2 * h + pos, i1 = i0 + h;
-            C w = tw[pos * tws];
-            if (inverse) w.y = -w.y;
-            const C a = buf[i0], b = buf[i1];
-            buf[i0] = cadd(a, b);
-            buf[i1] = cmul(csub(a, b), w);
-        }
-        __syncthreads();
-    }
-}
-
-// Twiddles exp(-2 pi i k/N), k < N/2, computed once per CTA into shared memory.
-template <typename C>
-__device__ void load_tw(C *tw_s, int N) {
-    for (int k = threadIdx.x; k < (N >> 1); k += blockDim.x) {
+// Twiddles exp(-2 pi i m/N), m < N, computed once per CTA into shared memory.
+template <typename C> __device__ void load_tw(C *tw_s, int N) {
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
         double sn, cs;
         sincospi(-2.0 * (double)k / (double)N, &sn, &cs);
         tw_s[k] = cmk<C>((decltype(C::x))cs, (decltype(C::x))sn);
     }
 }
 
+template <int N> __host__ __device__ constexpr int rowpairs() { return N >= 64 ? 32 : 4096 / (N * 2); }
+template <int N, typename T> __host__ __device__ constexpr int tx_y() { return sizeof(T) == 4 ? 32 : 16; }
+template <typename T> __host__ __device__ constexpr int tx_z() { return sizeof(T) == 4 ? 8 : 4; }
+template <int N> __host__ __device__ constexpr int maxit(int lines) {
+    return (lines * (N / Shape<N>::R1) + kThreads - 1) / kThreads < 1 ? 1
+                                                                     : (lines * (N / Shape<N>::R1) + kThreads - 1) / kThreads;
+}
+
 // ---------------------------------------------------------------------------------------------
-// x pass, real -> half spectrum. CTA = kRowPairs pairs of rows (y even, y+1) of one (field, z).
+// x pass, real -> half spectrum. CTA = RP pairs of rows (y even, y+1) of one (field, z).
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out,
-                                                       int N, int logN, long npairs) {
+                                                       long npairs) {
     using C = typename CT<T>::type;
+    constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *buf = tw + (N >> 1);
-    const int ls = N;
-    const int Hx = (N >> 1) + 1;
+    C *buf = tw + N;
     load_tw(tw, N);
-    const long p0 = (long)blockIdx.x * kRowPairs;
-    const int np = (int)min((long)kRowPairs, npairs - p0);
+    const long p0 = (long)blockIdx.x * RP;
+    const int np = (int)min((long)RP, npairs - p0);
     for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
         const int pl = t / N, j = t - pl * N;
         const long row0 = 2 * (p0 + pl);            // global row index = (field*N + z)*N + y
-        const T a = in[row0 * N + j], b = in[(row0 + 1) * N + j];
-        buf[pl * ls + bitrev(j, logN)] = cmk<C>(a, b);
+        buf[pl * LS + pad16(j)] = cmk<C>(in[row0 * N + j], in[(row0 + 1) * N + j]);
     }
     __syncthreads();
-    fft_dit(buf, N, logN, np, ls, tw, false);
+    block_fft<N, false, maxit<N>(RP)>(buf, np, tw);
     const T h = (T)0.5;
     for (int t = threadIdx.x; t < np * Hx; t += blockDim.x) {
         const int pl = t / Hx, k = t - pl * Hx;
-        const C zk = buf[pl * ls + (k & (N - 1))];
-        const C zc = cconj(buf[pl * ls + ((N - k) & (N - 1))]);
-        const C A = cmk<C>(h * (zk.x + zc.x), h * (zk.y + zc.y));
-        const C B = cmk<C>(h * (zk.y - zc.y), -h * (zk.x - zc.x));   // (zk - zc) / 2i
+        const C zk = buf[pl * LS + pad16(k & (N - 1))];
+        const C zc = cconj(buf[pl * LS + pad16((N - k) & (N - 1))]);
         const long row0 = 2 * (p0 + pl);
-        out[row0 * Hx + k] = A;
-        out[(row0 + 1) * Hx + k] = B;
+        out[row0 * Hx + k] = cmk<C>(h * (zk.x + zc.x), h * (zk.y + zc.y));
+        out[(row0 + 1) * Hx + k] = cmk<C>(h * (zk.y - zc.y), -h * (zk.x - zc.x));   // (zk - zc) / 2i
     }
 }
 
 // ---------------------------------------------------------------------------------------------
 // x pass, half spectrum -> real (complex-to-real through the same row-pair packing).
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
-                                                       int N, int logN, long npairs, T scale, int has_add, double a0, double a1, double a2, double a3,
-                                                       double a4, double a5) {
+                                                       long npairs, T scale, int has_add, double a0, double a1, double a2,
+                                                       double a3, double a4, double a5) {
     using C = typename CT<T>::type;
+    constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *buf = tw + (N >> 1);
-    const int ls = N;
-    const int Hx = (N >> 1) + 1;
+    C *buf = tw + N;
     load_tw(tw, N);
-    const long p0 = (long)blockIdx.x * kRowPairs;
-    const int np = (int)min((long)kRowPairs, npairs - p0);
+    const long p0 = (long)blockIdx.x * RP;
+    const int np = (int)min((long)RP, npairs - p0);
     for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
         const int pl = t / N, k = t - pl * N;
         const long row0 = 2 * (p0 + pl);
@@ -138,15 +218,15 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
             A = cconj(spec[row0 * Hx + (N - k)]);
             B = cconj(spec[(row0 + 1) * Hx + (N - k)]);
         }
-        buf[pl * ls + bitrev(k, logN)] = cmk<C>(A.x - B.y, A.y + B.x);   // A + iB
+        buf[pl * LS + pad16(k)] = cmk<C>(A.x - B.y, A.y + B.x);   // A + iB
     }
     __syncthreads();
-    fft_dit(buf, N, logN, np, ls, tw, true);
+    block_fft<N, true, maxit<N>(RP)>(buf, np, tw);
     const long rows_per_field = (long)N * N;
     for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
         const int pl = t / N, j = t - pl * N;
         const long row0 = 2 * (p0 + pl);
-        const C z = buf[pl * ls + j];
+        const C z = buf[pl * LS + pad16(j)];
         if (has_add) {
             const int f = (int)(row0 / rows_per_field);
             const double add = f == 0 ? a0 : f == 1 ? a1 : f == 2 ? a2 : f == 3 ? a3 : f == 4 ? a4 : a5;
@@ -162,15 +242,14 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
 // ---------------------------------------------------------------------------------------------
 // y pass: CTA = (field, z, kx tile of TX columns); lines along y.
 // ---------------------------------------------------------------------------------------------
-template <typename T, int TX>
-__global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__restrict__ spec, int N, int logN, int inverse) {
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__restrict__ spec) {
     using C = typename CT<T>::type;
+    constexpr int TX = tx_y<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *buf = tw + (N >> 1);
-    const int ls = N + 1;
-    const int Hx = (N >> 1) + 1;
-    const int ntiles = (Hx + TX - 1) / TX;
+    C *buf = tw + N;
+    constexpr int ntiles = (Hx + TX - 1) / TX;
     const int tile = blockIdx.x % ntiles;
     const long plane = blockIdx.x / ntiles;        // field*N + z
     const int kx0 = tile * TX;
@@ -179,16 +258,14 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__rest
     for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
         const int y = t / TX, xl = t - y * TX;
         const int kx = kx0 + xl;
-        C v = cmk<C>(0, 0);
-        if (kx < Hx) v = base[(long)y * Hx + kx];
-        buf[xl * ls + bitrev(y, logN)] = v;
+        buf[xl * LS + pad16(y)] = kx < Hx ? base[(long)y * Hx + kx] : cmk<C>(0, 0);
     }
     __syncthreads();
-    fft_dit(buf, N, logN, TX, ls, tw, inverse != 0);
+    block_fft<N, INV, maxit<N>(TX)>(buf, TX, tw);
     for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
         const int y = t / TX, xl = t - y * TX;
         const int kx = kx0 + xl;
-        if (kx < Hx) base[(long)y * Hx + kx] = buf[xl * ls + y];
+        if (kx < Hx) base[(long)y * Hx + kx] = buf[xl * LS + pad16(y)];
     }
 }
 
@@ -196,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__rest
 // eps_kh = (n_h v_k + n_k v_h)/(2 mu0) - c n_k n_h (n.v), v = sigma.n, n = xi/|xi|,
 // c = (lam0+mu0)/(mu0 (lam0+2 mu0)). At frequencies with a Nyquist component the compliance of
 // the reference medium replaces it; the zero frequency is left to the macroscopic update.
-// Returns -Gamma:sigma in s (in place) and accumulates |xi.sigma|^2 (xi = 2 pi k/N).
+// Returns -Gamma:sigma in s (in place) if apply, and accumulates |xi.sigma|^2 (xi = 2 pi k/N).
 template <typename C, typename T>
 __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int N, T lam0, T mu0, T &acc, bool partner,
                                             bool apply) {
@@ -204,7 +281,6 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
     const int fy = ky <= (N >> 1) ? ky : ky - N;
     const int fz = kz <= (N >> 1) ? kz : kz - N;
     const T r2 = (T)0.70710678118654752440;
-    // tensor components
     const C t11 = s[0], t22 = s[1], t33 = s[2];
     const C t23 = cmk<C>(s[3].x * r2, s[3].y * r2), t13 = cmk<C>(s[4].x * r2, s[4].y * r2),
             t12 = cmk<C>(s[5].x * r2, s[5].y * r2);
@@ -266,17 +342,16 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
 // ---------------------------------------------------------------------------------------------
 // z pass: CTA = (ky, kx tile); nf fields x TX columns x N planes in shared memory.
 // ---------------------------------------------------------------------------------------------
-template <typename T, int TX>
-__global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__restrict__ spec, int N, int logN, int nf, int mode, T lam0, T mu0,
-                                                   double *__restrict__ partials, double *__restrict__ mean6) {
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
+                                                   T mu0, double *__restrict__ partials, double *__restrict__ mean6) {
     using C = typename CT<T>::type;
+    constexpr int TX = tx_z<T>(), LS = Shape<N>::LS, Hx = N / 2 + 1, MI = maxit<N>(6 * TX);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *buf = tw + (N >> 1);
+    C *buf = tw + N;
     __shared__ double red[32];
-    const int ls = N + 1;
-    const int Hx = (N >> 1) + 1;
-    const int ntiles = (Hx + TX - 1) / TX;
+    constexpr int ntiles = (Hx + TX - 1) / TX;
     const int tile = blockIdx.x % ntiles;
     const int ky = blockIdx.x / ntiles;
     const int kx0 = tile * TX;
@@ -288,13 +363,10 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
         const int r = t - f * TX * N;
         const int z = r / TX, xl = r - z * TX;
         const int kx = kx0 + xl;
-        C v = cmk<C>(0, 0);
-        if (kx < Hx) v = spec[f * fstride + z * plane + (long)ky * Hx + kx];
-        const int zi = (mode == Z_INV) ? z : bitrev(z, logN);
-        buf[(f * TX + xl) * ls + zi] = v;
+        buf[(f * TX + xl) * LS + pad16(z)] = kx < Hx ? spec[f * fstride + z * plane + (long)ky * Hx + kx] : cmk<C>(0, 0);
     }
     __syncthreads();
-    if (mode != Z_INV) fft_dit(buf, N, logN, nf * TX, ls, tw, false);
+    if (mode != Z_INV) block_fft<N, false, MI>(buf, nf * TX, tw);
     if (mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) {
         const bool apply = mode == Z_FWD_GAMMA_INV;
         T acc = (T)0;   // per-thread sum in the field precision; block and global sums in FP64
@@ -303,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
             const int kx = kx0 + xl;
             if (kx >= Hx) continue;
             C s6[6];
-            for (int f = 0; f < 6; ++f) s6[f] = buf[(f * TX + xl) * ls + kz];
+            for (int f = 0; f < 6; ++f) s6[f] = buf[(f * TX + xl) * LS + pad16(kz)];
             if (kx == 0 && ky == 0 && kz == 0 && mean6 != nullptr) {
                 const double inv = 1.0 / ((double)N * N * N);
                 for (int f = 0; f < 6; ++f) mean6[f] = (double)s6[f].x * inv;
@@ -311,33 +383,96 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
             const bool partner = !(kx == 0 || kx == (N >> 1));
             gamma_point<C, T>(s6, kx, ky, kz, N, lam0, mu0, acc, partner, apply);
             if (apply)
-                for (int f = 0; f < 6; ++f) buf[(f * TX + xl) * ls + kz] = s6[f];
+                for (int f = 0; f < 6; ++f) buf[(f * TX + xl) * LS + pad16(kz)] = s6[f];
         }
         __syncthreads();
         const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = tot;
     }
-    const bool fwd_only = mode == Z_FWD || mode == Z_FWD_RESID;
-    if (!fwd_only) fft_dif(buf, N, logN, nf * TX, ls, tw, true);
+    if (mode == Z_INV || mode == Z_FWD_GAMMA_INV) block_fft<N, true, MI>(buf, nf * TX, tw);
     for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
         const int f = t / (TX * N);
         const int r = t - f * TX * N;
         const int z = r / TX, xl = r - z * TX;
         const int kx = kx0 + xl;
-        if (kx >= Hx) continue;
-        const int zi = fwd_only ? z : bitrev(z, logN);
-        spec[f * fstride + z * plane + (long)ky * Hx + kx] = buf[(f * TX + xl) * ls + zi];
+        if (kx < Hx) spec[f * fstride + z * plane + (long)ky * Hx + kx] = buf[(f * TX + xl) * LS + pad16(z)];
     }
 }
 
-template <typename T> constexpr int tx_y() { return sizeof(T) == 4 ? 16 : 8; }
-template <typename T> constexpr int tx_z() { return sizeof(T) == 4 ? 16 : 8; }
-
-int ilog2(int n) {
-    int l = 0;
-    while ((1 << l) < n) ++l;
-    return l;
+template <typename T, int N> size_t smem_x() { return sizeof(typename CT<T>::type) * (N + (size_t)rowpairs<N>() * Shape<N>::LS); }
+template <typename T, int N> size_t smem_y() { return sizeof(typename CT<T>::type) * (N + (size_t)tx_y<N, T>() * Shape<N>::LS); }
+template <typename T, int N> size_t smem_z(int nf) {
+    return sizeof(typename CT<T>::type) * (N + (size_t)nf * tx_z<T>() * Shape<N>::LS);
 }
+
+template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int N> cudaError_t x_r2c_n(const T *in, void *spec, int nfields, cudaStream_t s) {
+    using C = typename CT<T>::type;
+    const long npairs = (long)nfields * N * N / 2;
+    const int blocks = (int)((npairs + rowpairs<N>() - 1) / rowpairs<N>());
+    const size_t sm = smem_x<T, N>();
+    cudaError_t e = allow_smem(k_fft_x_r2c<T, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_fft_x_r2c<T, N><<<blocks, kThreads, sm, s>>>(in, (C *)spec, npairs);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double *add6, cudaStream_t s) {
+    using C = typename CT<T>::type;
+    const long npairs = (long)nfields * N * N / 2;
+    const int blocks = (int)((npairs + rowpairs<N>() - 1) / rowpairs<N>());
+    const size_t sm = smem_x<T, N>();
+    cudaError_t e = allow_smem(k_fft_x_c2r<T, N>, sm);
+    if (e != cudaSuccess) return e;
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    if (add6)
+        for (int i = 0; i < 6; ++i) a[i] = add6[i];
+    k_fft_x_c2r<T, N><<<blocks, kThreads, sm, s>>>((const C *)spec, out, npairs, scale, add6 != nullptr, a[0], a[1],
+                                                   a[2], a[3], a[4], a[5]);
+    return cudaGetLastError();
+}
+
+template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int inverse, cudaStream_t s) {
+    using C = typename CT<T>::type;
+    constexpr int TX = tx_y<N, T>(), Hx = N / 2 + 1;
+    const int blocks = nfields * N * ((Hx + TX - 1) / TX);
+    const size_t sm = smem_y<T, N>();
+    cudaError_t e = inverse ? allow_smem(k_fft_y<T, N, true>, sm) : allow_smem(k_fft_y<T, N, false>, sm);
+    if (e != cudaSuccess) return e;
+    if (inverse) k_fft_y<T, N, true><<<blocks, kThreads, sm, s>>>((C *)spec);
+    else k_fft_y<T, N, false><<<blocks, kThreads, sm, s>>>((C *)spec);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t z_n(void *spec, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
+                cudaStream_t s) {
+    using C = typename CT<T>::type;
+    constexpr int TX = tx_z<T>(), Hx = N / 2 + 1;
+    const int blocks = N * ((Hx + TX - 1) / TX);
+    const size_t sm = smem_z<T, N>(nfields);
+    cudaError_t e = allow_smem(k_fft_z<T, N>, smem_z<T, N>(6));
+    if (e != cudaSuccess) return e;
+    k_fft_z<T, N><<<blocks, kThreads, sm, s>>>((C *)spec, nfields, mode, (T)lam0, (T)mu0, partials, mean6);
+    return cudaGetLastError();
+}
+
+#define EVP_DISPATCH(N_, CALL)                             \
+    switch (N_) {                                          \
+        case 4: { constexpr int NN = 4; return CALL; }     \
+        case 8: { constexpr int NN = 8; return CALL; }     \
+        case 16: { constexpr int NN = 16; return CALL; }   \
+        case 32: { constexpr int NN = 32; return CALL; }   \
+        case 64: { constexpr int NN = 64; return CALL; }   \
+        case 128: { constexpr int NN = 128; return CALL; } \
+        case 256: { constexpr int NN = 256; return CALL; } \
+        default: return cudaErrorInvalidValue;             \
+    }
 
 }  // namespace
 
@@ -347,61 +482,24 @@ int fft_z_blocks(int n, int is_double) {
     return n * ((Hx + TX - 1) / TX);
 }
 
-template <typename T>
-cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s) {
-    using C = typename CT<T>::type;
-    const long npairs = (long)nfields * n * n / 2;
-    const int blocks = (int)((npairs + kRowPairs - 1) / kRowPairs);
-    const size_t sm = sizeof(C) * (n / 2 + (size_t)kRowPairs * n);
-    k_fft_x_r2c<T><<<blocks, kThreads, sm, s>>>(in, (C *)spec, n, ilog2(n), npairs);
-    return cudaGetLastError();
+template <typename T> cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s) {
+    EVP_DISPATCH(n, (x_r2c_n<T, NN>(in, spec, nfields, s)))
 }
 
 template <typename T>
-cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6,
-                      cudaStream_t s) {
-    using C = typename CT<T>::type;
-    const long npairs = (long)nfields * n * n / 2;
-    const int blocks = (int)((npairs + kRowPairs - 1) / kRowPairs);
-    const size_t sm = sizeof(C) * (n / 2 + (size_t)kRowPairs * n);
-    double a[6] = {0, 0, 0, 0, 0, 0};
-    if (add6)
-        for (int i = 0; i < 6; ++i) a[i] = add6[i];
-    k_fft_x_c2r<T><<<blocks, kThreads, sm, s>>>((const C *)spec, out, n, ilog2(n), npairs, scale,
-                                                add6 != nullptr, a[0], a[1], a[2], a[3], a[4], a[5]);
-    return cudaGetLastError();
+cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6, cudaStream_t s) {
+    EVP_DISPATCH(n, (x_c2r_n<T, NN>(spec, out, nfields, scale, add6, s)))
 }
 
 template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s) {
-    using C = typename CT<T>::type;
-    constexpr int TX = tx_y<T>();
-    const int Hx = n / 2 + 1;
-    const int blocks = nfields * n * ((Hx + TX - 1) / TX);
-    const size_t sm = sizeof(C) * (n / 2 + (size_t)TX * (n + 1));
-    k_fft_y<T, TX><<<blocks, kThreads, sm, s>>>((C *)spec, n, ilog2(n), inverse);
-    return cudaGetLastError();
+    EVP_DISPATCH(n, (y_n<T, NN>(spec, nfields, inverse, s)))
 }
 
 template <typename T>
-cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials,
-                  double *mean6, cudaStream_t s) {
-    using C = typename CT<T>::type;
-    constexpr int TX = tx_z<T>();
+cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
+                  cudaStream_t s) {
     if ((mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) && nfields != 6) return cudaErrorInvalidValue;
-    const int Hx = n / 2 + 1;
-    const int blocks = n * ((Hx + TX - 1) / TX);
-    const size_t sm = sizeof(C) * (n / 2 + (size_t)nfields * TX * (n + 1));
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
-        cudaError_t e = cudaFuncSetAttribute(k_fft_z<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set[sizeof(T) == 8] = true;
-    }
-    if (sm > 220 * 1024) return cudaErrorInvalidValue;
-    // one launch per group of fields that fits (nfields = 6 always fits for n <= 256)
-    k_fft_z<T, TX><<<blocks, kThreads, sm, s>>>((C *)spec, n, ilog2(n), nfields, mode, (T)lam0,
-                                                (T)mu0, partials, mean6);
-    return cudaGetLastError();
+    EVP_DISPATCH(n, (z_n<T, NN>(spec, nfields, mode, lam0, mu0, partials, mean6, s)))
 }
 
 template cudaError_t fft_x_r2c<float>(const float *, void *, int, int, cudaStream_t);

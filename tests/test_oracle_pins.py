@@ -434,3 +434,30 @@ def test_sparse_active_set_equals_dense_bitwise(mat):
         da = {int(i): ea[j, v] for j, i in enumerate(ia[:, v]) if i >= 0 and ea[j, v] != 0.0}
         db = {int(i): eb[j, v] for j, i in enumerate(ib[:, v]) if i >= 0}
         assert da == db
+
+
+# ------------------------------------------------------------------------------------------
+# P13 gradient of the stress-strain misfit (differentiation direction)
+# ------------------------------------------------------------------------------------------
+def test_oracle_adjoint_gradient_matches_central_differences(mat):
+    """dL/d(k1, k2, tau0, n) from the discrete adjoint equals central finite differences of the
+    loss (h = 1e-6 relative) to 1e-5 relative, on a target curve the oracle makes at known
+    parameters and a gradient taken at perturbed ones."""
+    import dataclasses
+    n, G, T, seed = 8, 4, 4, 7
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, seed))
+    q = synth.orientations(G, seed)
+    rc, _, _, target = O.loss_grad(n, G, g0, q, mat, seed, T, -1e-3, 1.0, want_grad=False)
+    assert rc == 0
+    m1 = dataclasses.replace(mat, k1=mat.k1 * 1.1, k2=mat.k2 * 0.9, tau0=mat.tau0 * 1.2, n=mat.n * 1.05)
+    rc, L, g, _ = O.loss_grad(n, G, g0, q, m1, seed, T, -1e-3, 1.0, target=target)
+    assert rc == 0 and L > 0
+    for i, k in enumerate(("k1", "k2", "tau0", "n")):
+        v = getattr(m1, k)
+        h = 1e-6 * v
+        Lp = O.loss_grad(n, G, g0, q, dataclasses.replace(m1, **{k: v + h}), seed, T, -1e-3, 1.0, target=target,
+                         want_grad=False)[1]
+        Lm = O.loss_grad(n, G, g0, q, dataclasses.replace(m1, **{k: v - h}), seed, T, -1e-3, 1.0, target=target,
+                         want_grad=False)[1]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(g[i] / fd - 1) < 1e-5, (k, g[i], fd)
