@@ -155,6 +155,28 @@ int evp_set_scalars(evp_handle *h, const double *E6, const double *dE_prev6, int
 /* Change the fixed-point controls after init. */
 int evp_set_solver(evp_handle *h, double tol, int max_iter, int allow_unconverged);
 
+/* ---- differentiation (the paper calibrates k1, k2, tau0, n against stress-strain curves by hand,
+ * Sec. 3; this is the gradient such a calibration needs) ----
+ * Discrete adjoint of recorded mechanical increments (a2-a7): for L depending on the mean stresses
+ * <sigma>_t of T increments, evp_adjoint_end returns dL/d(k1, k2, tau0, n) given gbar_t = dL/d<sigma>_t.
+ * The converged increments are differentiated exactly (implicit function theorem); the adjoint
+ * equilibrium problem of each increment -- stiffness C_t = inverse local Newton Jacobian, the same
+ * mixed macroscopic conditions -- is solved by the same Green-operator iteration. Nucleation and
+ * phase-field events in between are held fixed (they must not occur between recorded increments).
+ * Checkpointing: the state is stored every `checkpoint_every` increments in the caller-owned
+ * adjoint workspace; the reverse sweep recomputes each segment from its checkpoint (bitwise the same
+ * forward) and keeps that segment's stresses and densities. */
+int evp_adjoint_workspace_bytes(const evp_config *cfg, int n_increments, int checkpoint_every, size_t *bytes);
+/* Start recording from the current state: adj_ws (device, >= evp_adjoint_workspace_bytes bytes,
+ * 256-byte aligned) holds checkpoints, the segment tape and the adjoint fields. */
+int evp_adjoint_begin(evp_handle *h, void *adj_ws, size_t bytes, int n_increments, int checkpoint_every);
+/* One recorded increment: evp_increment plus checkpointing. At most n_increments calls. */
+int evp_adjoint_step(evp_handle *h, double dE33, double dt, evp_stats *out);
+/* Reverse sweep over the recorded increments. gbar: host, T x 6 doubles (dL/d<sigma>_t, Mandel).
+ * grad: host, 4 doubles (dL/dk1, dL/dk2, dL/dtau0, dL/dn). tol / max_iter: adjoint fixed-point
+ * controls (relative residual). Restores the state of the last recorded increment on return. */
+int evp_adjoint_end(evp_handle *h, const double *gbar, double *grad, double tol, int max_iter);
+
 /* Instrumentation. Kernel launches are always counted. With profiling on (evp_set_profiling
  * (h, 1)) every kernel launch is bracketed by CUDA events on the handle's stream and its device
  * time is accumulated per kernel class. Classes: 0 newton, 1 fft_x_r2c, 2 fft_y_fwd,

@@ -36,6 +36,12 @@ struct evp_handle {
     uint64_t seed;
     MatConst mc;
     PFConst pc;
+    // adjoint recording
+    char *adj;
+    size_t adj_bytes;
+    int adj_T, adj_c, adj_t;
+    double *adj_dE33, *adj_dt, *adj_E, *adj_dEp;
+    int *adj_hp;
     // instrumentation
     int64_t launches;
     int64_t newton_solves, newton_evals;
@@ -49,6 +55,7 @@ struct evp_handle {
     int npool;
     char err[512];
     ~evp_handle() {
+        std::free(adj_dE33); std::free(adj_dt); std::free(adj_E); std::free(adj_dEp); std::free(adj_hp);
         for (int i = 0; i < npend; ++i) { cudaEventDestroy(pend[i].a); cudaEventDestroy(pend[i].b); }
         for (int i = 0; i < npool; ++i) cudaEventDestroy(pool[i]);
     }
@@ -778,6 +785,235 @@ int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, 
     return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
 
+}  // extern "C"
+
+// ---- differentiation: checkpointed discrete adjoint ----
+namespace {
+
+struct AdjLayout {
+    size_t slot, tape_rho, tape_sig, lam_ep, lam_rho, Ct, sbar, a, eb, taub, part, total;
+    int nseg;
+};
+
+AdjLayout adj_layout(const evp_config *c, int T, int ck) {
+    const size_t N3 = (size_t)c->n * c->n * c->n;
+    const size_t ts = c->precision == EVP_FP64 ? 8 : 4;
+    AdjLayout L{};
+    L.nseg = (T + ck - 1) / ck;
+    size_t off = 0;
+    auto take = [&](size_t b) { off = (off + 255) & ~(size_t)255; size_t o = off; off += b; return o; };
+    L.slot = take((size_t)(L.nseg + 1) * 36 * N3 * ts);
+    L.tape_rho = take((size_t)ck * 12 * N3 * ts);
+    L.tape_sig = take((size_t)ck * 6 * N3 * ts);
+    L.lam_ep = take(6 * N3 * ts);
+    L.lam_rho = take(12 * N3 * ts);
+    L.Ct = take(21 * N3 * ts);
+    L.sbar = take(6 * N3 * ts);
+    L.a = take(6 * N3 * ts);
+    L.eb = take(6 * N3 * ts);
+    L.taub = take(N3 * ts);
+    L.part = take(sizeof(double) * 4 * (size_t)adj_blocks((long)N3));
+    L.total = (off + 255) & ~(size_t)255;
+    return L;
+}
+
+// state slot: sig, epse, epsp, deps (6 each), rho (12) -- everything an increment reads
+int save_slot(evp_handle *h, char *slot, int k) {
+    const size_t f6 = 6 * (size_t)h->N3 * h->tsz;
+    CK(cudaMemcpyAsync(slot, h->sig, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(slot + f6, h->epse, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(slot + 2 * f6, h->epsp, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(slot + 3 * f6, h->deps, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(slot + 4 * f6, h->rho, 2 * f6, cudaMemcpyDeviceToDevice, h->st));
+    for (int i = 0; i < 6; ++i) {
+        h->adj_E[6 * k + i] = h->E[i];
+        h->adj_dEp[6 * k + i] = h->dE_prev[i];
+    }
+    h->adj_hp[k] = h->have_prev;
+    return EVP_OK;
+}
+
+int load_slot(evp_handle *h, const char *slot, int k) {
+    const size_t f6 = 6 * (size_t)h->N3 * h->tsz;
+    CK(cudaMemcpyAsync(h->sig, slot, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->epse, slot + f6, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->epsp, slot + 2 * f6, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->deps, slot + 3 * f6, f6, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->rho, slot + 4 * f6, 2 * f6, cudaMemcpyDeviceToDevice, h->st));
+    if (h->dbl) CK(refresh_k<double>(h->N3, (double *)h->rho, h->k, h->st));
+    else CK(refresh_k<float>(h->N3, (float *)h->rho, h->k, h->st));
+    for (int i = 0; i < 6; ++i) {
+        h->E[i] = h->adj_E[6 * k + i];
+        h->dE_prev[i] = h->adj_dEp[6 * k + i];
+    }
+    h->have_prev = h->adj_hp[k];
+    return EVP_OK;
+}
+
+template <typename TA>
+int adjoint_sweep(evp_handle *h, const AdjLayout &L, const double *gbar, double *grad, double tol, int max_iter) {
+    const long N3 = h->N3;
+    const int n = h->n, T = h->adj_t, ck = h->adj_c;
+    const size_t ts = h->tsz;
+    char *base = h->adj;
+    const size_t slot_b = 36 * (size_t)N3 * ts;
+    TA *tape_rho = (TA *)(base + L.tape_rho), *tape_sig = (TA *)(base + L.tape_sig);
+    TA *lam_ep = (TA *)(base + L.lam_ep), *lam_rho = (TA *)(base + L.lam_rho), *Ct = (TA *)(base + L.Ct);
+    TA *sbar = (TA *)(base + L.sbar), *aa = (TA *)(base + L.a), *eb = (TA *)(base + L.eb), *taub = (TA *)(base + L.taub);
+    double *part = (double *)(base + L.part);
+    const int nb = adj_blocks(N3);
+    const int nseg = (T + ck - 1) / ck;
+    const double lam0 = h->mc.lam0, mu0 = h->mc.mu0;
+    const double aa_ = lam0 + 2.0 * mu0, bb_ = lam0, det = aa_ * aa_ - bb_ * bb_;
+    const int zb = fft_z_blocks(n, h->dbl);
+    double gk1 = 0, gk2 = 0, gt0 = 0, gn = 0;
+    int rc = save_slot(h, base + L.slot + (size_t)nseg * slot_b, nseg);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(lam_ep, 0, 6 * (size_t)N3 * ts, h->st));
+    CK(cudaMemsetAsync(lam_rho, 0, 12 * (size_t)N3 * ts, h->st));
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int s0 = seg * ck, s1 = std::min(s0 + ck, T);
+        rc = load_slot(h, base + L.slot + (size_t)seg * slot_b, seg);
+        if (rc) return rc;
+        for (int t = s0; t < s1; ++t) {   // recompute the segment, keeping rho^{t-1} and sigma^t
+            CK(cudaMemcpyAsync(tape_rho + (size_t)(t - s0) * 12 * N3, h->rho, 12 * (size_t)N3 * ts,
+                               cudaMemcpyDeviceToDevice, h->st));
+            rc = evp_increment(h, h->adj_dE33[t], h->adj_dt[t], nullptr);
+            if (rc < 0) return rc;
+            CK(cudaMemcpyAsync(tape_sig + (size_t)(t - s0) * 6 * N3, h->sig, 6 * (size_t)N3 * ts,
+                               cudaMemcpyDeviceToDevice, h->st));
+        }
+        for (int t = s1 - 1; t >= s0; --t) {
+            MatConst mc = h->mc;
+            mc.dt = h->adj_dt[t];
+            const TA *rp = tape_rho + (size_t)(t - s0) * 12 * N3, *sg = tape_sig + (size_t)(t - s0) * 6 * N3;
+            CK(adj_prep<TA>(N3, h->g0, (const TA *)h->Stab, (const TA *)h->Mtab, rp, sg, lam_ep, lam_rho, Ct, sbar, aa,
+                            taub, mc, gbar + 6 * (size_t)t, part, h->st));
+            CK(reduce_partials(part, nb, 4, h->scal + 16, h->st));
+            double r4[4];
+            CK(cudaMemcpyAsync(r4, h->scal + 16, sizeof r4, cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            gk1 += r4[0];
+            gk2 += r4[1];
+            gn += r4[2];
+            const double rms = std::sqrt(r4[3] / (double)N3);
+            CK(cudaMemsetAsync(eb, 0, 6 * (size_t)N3 * ts, h->st));
+            if (rms > 0.0) {
+                int it;
+                double err = 0.0;
+                for (it = 1; it <= max_iter; ++it) {
+                    CK(adj_tau<TA>(N3, Ct, eb, aa, (TA *)h->sigk, h->st));
+                    CK(fft_x_r2c<TA>((const TA *)h->sigk, h->spec, n, 6, h->st));
+                    CK(fft_y<TA>(h->spec, n, 6, 0, h->st));
+                    CK(fft_z<TA>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st));
+                    CK(reduce_partials(h->partials, zb, 1, h->scal + 6, h->st));
+                    double hs[7];
+                    CK(cudaMemcpyAsync(hs, h->scal, sizeof hs, cudaMemcpyDeviceToHost, h->st));
+                    CK(cudaStreamSynchronize(h->st));
+                    h->launches += 5;
+                    double mu_n = 0.0;
+                    for (int i = 0; i < 6; ++i)
+                        if (i != 2) mu_n += hs[i] * hs[i];
+                    err = std::sqrt(hs[6]) / ((double)N3 * rms) + std::sqrt(mu_n) / rms;
+                    if (!std::isfinite(err)) return fail(h, EVP_ERR_NONFINITE, "non-finite adjoint residual");
+                    if (err <= tol) break;
+                    double dEk[6] = {0, 0, 0, 0, 0, 0};
+                    dEk[0] = (aa_ * (-hs[0]) - bb_ * (-hs[1])) / det;
+                    dEk[1] = (-bb_ * (-hs[0]) + aa_ * (-hs[1])) / det;
+                    for (int i = 3; i < 6; ++i) dEk[i] = -hs[i] / (2.0 * mu0);
+                    CK(fft_y<TA>(h->spec, n, 6, 1, h->st));
+                    CK(fft_x_c2r<TA>(h->spec, eb, n, 6, (TA)(1.0 / (double)N3), dEk, h->st));
+                    h->launches += 2;
+                }
+                if (it > max_iter)
+                    return fail(h, EVP_ERR_FIXEDPOINT, "adjoint fixed point not converged at increment %d (err %.3e)", t,
+                                err);
+            }
+            CK(adj_finish<TA>(N3, h->g0, (const TA *)h->Mtab, rp, sg, Ct, sbar, eb, taub, lam_ep, lam_rho, mc, part,
+                              h->st));
+            CK(reduce_partials(part, nb, 2, h->scal + 16, h->st));
+            double r2[2];
+            CK(cudaMemcpyAsync(r2, h->scal + 16, sizeof r2, cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            h->launches += 4;
+            gt0 += r2[0];
+            gn += r2[1];
+        }
+    }
+    rc = load_slot(h, base + L.slot + (size_t)nseg * slot_b, nseg);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->st));
+    grad[0] = gk1;
+    grad[1] = gk2;
+    grad[2] = gt0;
+    grad[3] = gn;
+    return EVP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int evp_adjoint_workspace_bytes(const evp_config *cfg, int n_increments, int checkpoint_every, size_t *bytes) {
+    char why[256];
+    if (check_cfg(cfg, why, sizeof why) != EVP_OK || n_increments < 1 || checkpoint_every < 1 || !bytes)
+        return EVP_ERR_ARG;
+    *bytes = adj_layout(cfg, n_increments, checkpoint_every).total;
+    return EVP_OK;
+}
+
+int evp_adjoint_begin(evp_handle *h, void *adj_ws, size_t bytes, int n_increments, int checkpoint_every) {
+    if (!h || !adj_ws || n_increments < 1 || checkpoint_every < 1) return fail(h, EVP_ERR_ARG, "bad adjoint arguments");
+    if (((uintptr_t)adj_ws & 255) != 0) return fail(h, EVP_ERR_ARG, "adjoint workspace must be 256-byte aligned");
+    const AdjLayout L = adj_layout(&h->cfg, n_increments, checkpoint_every);
+    if (bytes < L.total) return fail(h, EVP_ERR_OOM, "adjoint workspace has %zu bytes, needs %zu", bytes, L.total);
+    std::free(h->adj_dE33); std::free(h->adj_dt); std::free(h->adj_E); std::free(h->adj_dEp); std::free(h->adj_hp);
+    h->adj_dE33 = (double *)std::malloc(sizeof(double) * n_increments);
+    h->adj_dt = (double *)std::malloc(sizeof(double) * n_increments);
+    h->adj_E = (double *)std::malloc(sizeof(double) * 6 * (L.nseg + 1));
+    h->adj_dEp = (double *)std::malloc(sizeof(double) * 6 * (L.nseg + 1));
+    h->adj_hp = (int *)std::malloc(sizeof(int) * (L.nseg + 1));
+    if (!h->adj_dE33 || !h->adj_dt || !h->adj_E || !h->adj_dEp || !h->adj_hp) return fail(h, EVP_ERR_OOM, "host allocation");
+    h->adj = (char *)adj_ws;
+    h->adj_bytes = bytes;
+    h->adj_T = n_increments;
+    h->adj_c = checkpoint_every;
+    h->adj_t = 0;
+    const int rc = save_slot(h, h->adj + L.slot, 0);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->st));
+    return EVP_OK;
+}
+
+int evp_adjoint_step(evp_handle *h, double dE33, double dt, evp_stats *out) {
+    if (!h || !h->adj) return fail(h, EVP_ERR_ARG, "evp_adjoint_begin was not called");
+    if (h->adj_t >= h->adj_T) return fail(h, EVP_ERR_ARG, "more than %d recorded increments", h->adj_T);
+    const int rc = evp_increment(h, dE33, dt, out);
+    if (rc < 0) return rc;
+    h->adj_dE33[h->adj_t] = dE33;
+    h->adj_dt[h->adj_t] = dt;
+    h->adj_t += 1;
+    if (h->adj_t % h->adj_c == 0 && h->adj_t < h->adj_T) {
+        const AdjLayout L = adj_layout(&h->cfg, h->adj_T, h->adj_c);
+        const int k = h->adj_t / h->adj_c;
+        const int r2 = save_slot(h, h->adj + L.slot + (size_t)k * 36 * h->N3 * h->tsz, k);
+        if (r2) return r2;
+    }
+    return rc;
+}
+
+int evp_adjoint_end(evp_handle *h, const double *gbar, double *grad, double tol, int max_iter) {
+    if (!h || !h->adj || !gbar || !grad || max_iter < 1 || !(tol > 0.0))
+        return fail(h, EVP_ERR_ARG, "bad evp_adjoint_end arguments");
+    if (h->adj_t < 1) return fail(h, EVP_ERR_ARG, "no recorded increments");
+    const AdjLayout L = adj_layout(&h->cfg, h->adj_T, h->adj_c);
+    return h->dbl ? adjoint_sweep<double>(h, L, gbar, grad, tol, max_iter)
+                  : adjoint_sweep<float>(h, L, gbar, grad, tol, max_iter);
+}
+
+}  // extern "C"
+
+extern "C" {
 int evp_residual_scratch_bytes(int n, int precision, size_t *bytes) {
     if (!pow2(n) || !bytes || precision < EVP_FP64 || precision > EVP_MIXED_FAST) return EVP_ERR_ARG;
     *bytes = sizeof(double) * (size_t)fft_z_blocks(n, precision == EVP_FP64);

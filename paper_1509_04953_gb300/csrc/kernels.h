@@ -39,6 +39,18 @@ cudaError_t state_update(long N3, const TA *sig, const TA *tauc, const int32_t *
                          TA *epse, TA *epsp, TA *deps, TA *rho, double *k, MatConst mc, cudaStream_t s);
 template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const TA *epsp, TA *eps, cudaStream_t s);
 
+// ---- adjoint.cu ----
+int adj_blocks(long N3);
+template <typename TA>
+cudaError_t adj_prep(long N3, const int32_t *g0, const TA *Stab, const TA *Mtab, const TA *rho_prev, const TA *sig,
+                     const TA *lam_ep, TA *lam_rho, TA *Ct, TA *sbar, TA *a, TA *taub, MatConst mc, const double *gb6,
+                     double *part, cudaStream_t s);
+template <typename TA> cudaError_t adj_tau(long N3, const TA *Ct, const TA *eb, const TA *a, TA *tau, cudaStream_t s);
+template <typename TA>
+cudaError_t adj_finish(long N3, const int32_t *g0, const TA *Mtab, const TA *rho_prev, const TA *sig, const TA *Ct,
+                       const TA *sbar, const TA *eb, const TA *taub, TA *lam_ep, TA *lam_rho, MatConst mc, double *part,
+                       cudaStream_t s);
+
 // ---- drx.cu ----
 cudaError_t voronoi(int n, int G, const int64_t *seeds, int32_t *ids, cudaStream_t s);
 template <typename T>

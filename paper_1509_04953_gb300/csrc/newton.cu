@@ -12,143 +12,13 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "local.cuh"
 
 namespace evp {
 
 namespace {
 
 constexpr int kThreads = 128;
-
-template <typename T> __device__ __forceinline__ T dsqrt(T x) { return sqrt(x); }
-__device__ __forceinline__ double dsqrt(double x) { return __dsqrt_rn(x); }
-template <typename T> __device__ __forceinline__ T drcp(T x) { return (T)1 / x; }
-__device__ __forceinline__ double drcp(double x) { return __drcp_rn(x); }
-
-// |x|^(n-1) for the power law; fast path for small integer n (exponentiation by squaring).
-template <typename T> __device__ __forceinline__ T pow_nm1(T ax, const MatConst &mc) {
-    if (mc.n_int > 0) {
-        int e = mc.n_int - 1;
-        T r = (T)1, b = ax;
-        while (e) {
-            if (e & 1) r *= b;
-            b *= b;
-            e >>= 1;
-        }
-        return r;
-    }
-    return ax > (T)0 ? (T)pow((double)ax, mc.n - 1.0) : (T)0;
-}
-
-// Packed lower-triangular index of (i, j), j <= i.
-__host__ __device__ constexpr int pk(int i, int j) { return i * (i + 1) / 2 + j; }
-
-template <typename TA> struct Eval {
-    TA r[6];
-    TA K[21];
-    TA phi;
-};
-
-template <typename TA>
-__device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA inv_tc,
-                                         const TA sg[6], const MatConst &mc, Eval<TA> &e) {
-    const TA dt = (TA)mc.dt, g0 = (TA)mc.gdot0, nn = (TA)mc.n;
-    TA phi = (TA)0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        TA acc = (TA)0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) acc += Sp[i >= j ? pk(i, j) : pk(j, i)] * sg[j];
-        e.r[i] = acc - etr[i];
-        phi += sg[i] * ((TA)0.5 * acc - etr[i]);
-    }
-#pragma unroll
-    for (int q = 0; q < 21; ++q) e.K[q] = Sp[q];
-    const TA cphi = dt * g0 * tauc / (nn + (TA)1);
-    const TA cslope = dt * nn * g0 * inv_tc;
-#pragma unroll 1
-    for (int a = 0; a < 12; ++a) {
-        TA m[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) m[i] = __ldg(M + 6 * a + i);
-        TA tau = (TA)0;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
-        const TA x = tau * inv_tc;
-        const TA ax = fabs(x);
-        const TA p9 = pow_nm1(ax, mc);       // |x|^(n-1)
-        const TA p10 = p9 * ax;              // |x|^n
-        const TA gd = x < (TA)0 ? -g0 * p10 : g0 * p10;
-        const TA slope = cslope * p9;
-        TA sm[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            e.r[i] += dt * gd * m[i];
-            sm[i] = slope * m[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) e.K[pk(i, j)] += sm[i] * m[j];
-        phi += cphi * p10 * ax;
-    }
-    e.phi = phi;
-}
-
-// Reciprocal: FP32 division for float; for double an FP32 seed refined by two Newton steps
-// r <- r (2 - x r) (each doubles the correct bits: 24 -> 48 -> full precision).
-__device__ __forceinline__ float rcp_s(float x) { return 1.0f / x; }
-__device__ __forceinline__ double rcp_s(double x) {
-    double r = (double)(1.0f / (float)x);
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
-}
-
-// LDL^T solve of K d = r (K packed lower, SPD; no square roots). L is unit lower, D diagonal.
-// Returns false if a pivot is not positive.
-template <typename TS, typename TA> __device__ __forceinline__ bool ldl_solve(const TA Kin[21], const TA rin[6], TA dout[6]) {
-    TS L[21], invD[6], w[6];
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        TS dj = (TS)Kin[pk(j, j)];
-#pragma unroll
-        for (int k = 0; k < j; ++k) {
-            w[k] = L[pk(j, k)] * L[pk(k, k)];   // L_jk D_k (L[kk] holds D_k)
-            dj -= w[k] * L[pk(j, k)];
-        }
-        ok = ok && (dj > (TS)0);
-        dj = dj > (TS)0 ? dj : (TS)1;
-        L[pk(j, j)] = dj;
-        invD[j] = rcp_s(dj);
-#pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-            TS t = (TS)Kin[pk(i, j)];
-#pragma unroll
-            for (int k = 0; k < j; ++k) t -= L[pk(i, k)] * w[k];
-            L[pk(i, j)] = t * invD[j];
-        }
-    }
-    TS y[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        TS t = (TS)rin[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) t -= L[pk(i, k)] * y[k];
-        y[i] = t;
-    }
-#pragma unroll
-    for (int i = 5; i >= 0; --i) {
-        TS t = y[i] * invD[i];
-#pragma unroll
-        for (int k = i + 1; k < 6; ++k) t -= L[pk(k, i)] * y[k];
-        y[i] = t;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) dout[i] = (TA)y[i];
-    return ok;
-}
 
 // Damped Newton on one voxel. Returns the iteration count (> 0) or minus it on failure.
 template <typename TA, typename TS>

@@ -82,6 +82,10 @@ def load():
     L.evp_destroy.restype = None
     L.evp_last_error.argtypes = [vp]
     L.evp_last_error.restype = C.c_char_p
+    L.evp_adjoint_workspace_bytes.argtypes = [C.POINTER(Config), i, i, C.POINTER(sz)]
+    L.evp_adjoint_begin.argtypes = [vp, vp, sz, i, i]
+    L.evp_adjoint_step.argtypes = [vp, d, d, C.POINTER(Stats)]
+    L.evp_adjoint_end.argtypes = [vp, vp, vp, d, i]
     L.evp_set_profiling.argtypes = [vp, i]
     L.evp_kernel_times.argtypes = [vp, vp, vp, i]
     L.evp_launch_count.argtypes = [vp, vp]
@@ -94,7 +98,8 @@ def load():
     for f in ("evp_workspace_bytes", "evp_init", "evp_increment", "drx_nucleate", "pf_step", "get_fields",
               "set_fields", "evp_fields_bytes", "evp_get_scalars", "evp_set_scalars", "evp_set_solver",
               "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_kernel_times",
-              "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual"):
+              "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual",
+              "evp_adjoint_workspace_bytes", "evp_adjoint_begin", "evp_adjoint_step", "evp_adjoint_end"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -245,6 +250,32 @@ class Solver:
         Ea = (C.c_double * 6)(*E)
         dA = (C.c_double * 6)(*dE_prev)
         self._check("evp_set_scalars", load().evp_set_scalars(self.h, Ea, dA, int(have_prev), int(next_id)))
+
+    # ---- differentiation ----
+    def adjoint_begin(self, n_increments, checkpoint_every):
+        """Start recording increments for a reverse sweep (workspace from PyTorch)."""
+        torch = _torch()
+        nb = C.c_size_t(0)
+        rc = load().evp_adjoint_workspace_bytes(C.byref(self.cfg), n_increments, checkpoint_every, C.byref(nb))
+        if rc != 0:
+            raise EVPError(f"evp_adjoint_workspace_bytes: {EVP_ERR.get(rc, rc)}")
+        self.adj_ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        ptr = (self.adj_ws.data_ptr() + 255) & ~255
+        self._check("evp_adjoint_begin", load().evp_adjoint_begin(self.h, ptr, nb.value, n_increments,
+                                                                  checkpoint_every))
+        self.adj_T = n_increments
+
+    def adjoint_step(self, dE33, dt):
+        st = Stats()
+        self._check("evp_adjoint_step", load().evp_adjoint_step(self.h, dE33, dt, C.byref(st)))
+        return st
+
+    def adjoint_end(self, gbar, tol=1e-10, max_iter=20000):
+        """gbar: (T, 6) dL/d<sigma>_t. Returns dL/d(k1, k2, tau0, n)."""
+        g = np.ascontiguousarray(np.asarray(gbar, dtype=np.float64).reshape(-1, 6))
+        grad = np.zeros(4)
+        self._check("evp_adjoint_end", load().evp_adjoint_end(self.h, g.ctypes.data, grad.ctypes.data, tol, max_iter))
+        return grad
 
     # ---- instrumentation ----
     KERNEL_CLASSES = ("newton", "fft_x_r2c", "fft_y_fwd", "fft_z_gamma", "fft_y_inv", "fft_x_c2r_update", "reduce",
