@@ -33,7 +33,8 @@ METRIC = "FFT-EVP voxel-iters/s + DRX increments/s at 128^3, FP32-mixed vs FP64 
 UNIT = "voxel-iterations/s"
 # per-kernel algorithmic bytes per voxel for one launch (FP32 / FP64 field words)
 NEWTON_FLOPS_EVAL = 1140      # FP operations of one residual+tangent+potential evaluation
-NEWTON_FLOPS_SOLVE = 160      # FP operations of one 6x6 Cholesky factorisation + two solves
+NEWTON_FLOPS_FACTOR = 80      # FP operations of one 6x6 LDL^T factorisation
+NEWTON_FLOPS_SOLVE = 72       # FP operations of the two triangular solves of one Newton step
 
 
 def parse():
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cu128")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_fast", "fp64"],
+                    help="precision of the timed solver (the headline is the mixed path)")
     ap.add_argument("--fp64-steps", type=int, default=-1, help="FP64 comparison increments (-1 = warmup+steps)")
     ap.add_argument("--fast-steps", type=int, default=2, help="timed increments of the FP32-solve mixed path")
     ap.add_argument("--no-e2e", action="store_true")
@@ -189,7 +192,8 @@ def native(args, ws, rank, local):
     seeds, quat = workload_inputs(wl)
     g0 = evp.voronoi(wl.n, seeds).cpu().numpy()
     N3 = wl.n ** 3
-    mixed = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="mixed", tol=args.tol, max_iter=5000)
+    tol_main = args.tol64 if args.precision == "fp64" else args.tol
+    mixed = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision, tol=tol_main, max_iter=5000)
     # warm-up (untimed)
     warm = run_steps(mixed, args.warmup, wl.dE33, wl.dt, wl.pf_steps, torch)
     mixed.set_profiling(True)
@@ -221,9 +225,11 @@ def native(args, ws, rank, local):
 
     res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
                ms_per_step=1e3 * step_s_max / args.steps, higher_is_better=True, scaling="weak",
-               vs_baseline=None, dtype="f32 fields/FFT/PF + f64 Newton solve and reductions", data="synthetic",
-               config={"workload": wl.name, "n": wl.n, "grains": wl.grains, "precision": "mixed",
-                       "tol": args.tol, "dE33": wl.dE33, "pf_steps": wl.pf_steps,
+               vs_baseline=None, dtype={"mixed": "f32 fields/FFT/PF + f64 Newton solve and reductions",
+                                        "mixed_fast": "f32 (f64 reductions)", "fp64": "f64"}[args.precision],
+               data="synthetic",
+               config={"workload": wl.name, "n": wl.n, "grains": wl.grains, "precision": args.precision,
+                       "tol": tol_main, "dE33": wl.dE33, "pf_steps": wl.pf_steps,
                        "l2": "inputs larger than L2 (about 0.8 GB of fields per replica, no flush needed)",
                        "parallelism": f"replicas x{ws}"},
                drx_increments_per_s=incs_per_s,
@@ -235,10 +241,12 @@ def native(args, ws, rank, local):
     res["kernel_launches"] = {k: v[1] for k, v in ktimes.items() if v[1]}
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     solves, evals = n1[0] - n0[0], n1[1] - n0[1]
-    res["newton"] = {"solves": solves, "evals": evals, "solves_per_voxel_iter": solves / (N3 * iters),
-                     "evals_per_voxel_iter": evals / (N3 * iters)}
-    res["roofline"] = roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision="mixed")
-    res["memory_bound_kernels"] = memory_kernels(ktimes, wl, N3, "mixed", pk)
+    res["newton"] = {"mode": "reuse" if mixed.cfg.newton_mode == 1 else "exact", "solves": solves, "evals": evals, "factorisations": n1[2] - n0[2],
+                     "solves_per_voxel_iter": solves / (N3 * iters), "evals_per_voxel_iter": evals / (N3 * iters),
+                     "factorisations_per_voxel_iter": (n1[2] - n0[2]) / (N3 * iters)}
+    res["roofline"] = roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision=args.precision,
+                               facs=n1[2] - n0[2])
+    res["memory_bound_kernels"] = memory_kernels(ktimes, wl, N3, args.precision, pk)
     if args.fast_steps > 0:
         res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
     # FP64 companion run on the same seeded input
@@ -264,7 +272,7 @@ def hbm_bytes_per_voxel(kernel, n, T):
             "pf_step": 2 * 8 * (4 + T) + 8}.get(kernel)
 
 
-def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision):
+def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, facs=0):
     ms, n = ktimes[dom]
     avg_s = ms / 1e3 / max(n, 1)
     T = 4 if precision != "fp64" else 8
@@ -272,16 +280,18 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision):
         # FP64 pipe: the 6x6 LDL^T solve (about 150 algorithmic flops) in the mixed path; everything
         # in the FP64 path. FP32 pipe for the fast mixed path. Peaks: FP64 1.25 TFLOP/s (nominal;
         # 1.203 measured with an FMA-chain probe), FP32 152 SMs x 128 lanes x 2 x 2.07 GHz.
+        lin = NEWTON_FLOPS_FACTOR * facs + NEWTON_FLOPS_SOLVE * solves
         if precision == "mixed":
-            flops, peak, pipe = NEWTON_FLOPS_SOLVE * solves, 1.25, "fp64"
+            flops, peak, pipe = lin, 1.25, "fp64"
         elif precision == "fp64":
-            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + NEWTON_FLOPS_SOLVE * solves, 1.25, "fp64"
+            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + lin, 1.25, "fp64"
         else:
-            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + NEWTON_FLOPS_SOLVE * solves, 152 * 128 * 2 * 2.070e9 / 1e12, "fp32"
+            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + lin, 152 * 128 * 2 * 2.070e9 / 1e12, "fp32"
         achieved = flops / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": "newton", "pipe": pipe, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "note": "algorithmic flops: 150 per 6x6 LDL^T solve, 1140 per residual/tangent evaluation; "
+                "note": "algorithmic flops: 80 per 6x6 LDL^T factorisation, 72 per pair of triangular solves, "
+                        "1140 per residual/tangent evaluation (FP64 path only); "
                         "peak from unit counts and clock (FP64 nominal 1.25 TFLOP/s)"}
     b = hbm_bytes_per_voxel(dom, wl.n, T) * N3
     achieved = b / avg_s / 1e9

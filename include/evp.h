@@ -58,7 +58,12 @@ typedef struct {
     int newton_max;        /* local Newton iteration cap */
     int predictor;         /* 1: start each increment from the previous strain-increment field */
     int max_ids;           /* capacity of the grain-id space (>= grains); 0 = grains + 8 N^3 */
+    int newton_mode;       /* 0: exact Newton every fixed-point iteration; 1: keep each voxel's factored
+                              tangent across iterations and refactor only when a step stalls (same
+                              local tolerance, same result); EVP_NEWTON_* */
 } evp_config;
+#define EVP_NEWTON_EXACT 0
+#define EVP_NEWTON_REUSE 1
 
 typedef struct {
     double C11, C12, C44;        /* cubic elastic constants, MPa */
@@ -189,6 +194,8 @@ int evp_launch_count(const evp_handle *h, int64_t *launches);
 /* Running totals over all increments: local Newton iterations (one 6x6 solve each) and
  * evaluations of the residual, tangent and potential (including backtracking trials). */
 int evp_newton_counts(const evp_handle *h, int64_t *solves, int64_t *evals);
+/* Running total of tangent factorisations (EVP_NEWTON_REUSE; equals solves with EVP_NEWTON_EXACT). */
+int evp_newton_refreshes(const evp_handle *h, int64_t *refreshes);
 
 void evp_destroy(evp_handle *h);
 const char *evp_last_error(const evp_handle *h);

@@ -25,7 +25,7 @@ struct evp_handle {
     char *ws;
     size_t ws_bytes;
     // fields
-    void *sig, *sigk, *epse, *epst, *epsp, *deps, *rho, *tauc, *eta, *eta2, *spec, *Stab, *Mtab;
+    void *sig, *sigk, *epse, *epst, *epsp, *deps, *rho, *tauc, *eta, *eta2, *spec, *Stab, *Mtab, *fac;
     double *k, *kappa, *partials, *scal;
     int32_t *g0, *g, *gprev, *draws, *ids, *ids2, *flags, *blk_counts, *blk_off, *count;
     uint32_t *bitmap;
@@ -44,7 +44,7 @@ struct evp_handle {
     int *adj_hp;
     // instrumentation
     int64_t launches;
-    int64_t newton_solves, newton_evals;
+    int64_t newton_solves, newton_evals, newton_refreshes;
     int prof;
     double prof_ms[EVP_NCLASS];
     int64_t prof_n[EVP_NCLASS];
@@ -144,6 +144,8 @@ int check_cfg(const evp_config *c, char *why, size_t wl) {
     if (c->max_iter < 1 || c->newton_max < 1) return snprintf(why, wl, "iteration caps must be >= 1"), EVP_ERR_ARG;
     if (!(c->tol >= 0.0) || !(c->newton_tol > 0.0)) return snprintf(why, wl, "tolerances must be >= 0"), EVP_ERR_ARG;
     if (c->max_ids != 0 && c->max_ids < c->grains) return snprintf(why, wl, "max_ids < grains"), EVP_ERR_ARG;
+    if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE)
+        return snprintf(why, wl, "unknown newton_mode %d", c->newton_mode), EVP_ERR_ARG;
     return EVP_OK;
 }
 
@@ -166,6 +168,8 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *epsp = take(6 * N3 * T), *deps = take(6 * N3 * T), *rho = take(12 * N3 * T), *tauc = take(N3 * T);
     char *eta = take(K * N3 * T), *eta2 = take(K * N3 * T), *spec = take(6 * H * 2 * T);
     char *Stab = take(36 * (size_t)G * T), *Mtab = take(72 * (size_t)G * T);
+    const size_t TSf = c->precision == EVP_MIXED_FAST ? 4 : 8;   // stored tangent factors
+    char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? 21 * N3 * TSf : 0);
     char *k = take(N3 * 8), *kappa = take(N3 * 8);
     char *g0 = take(N3 * 4), *g = take(N3 * 4), *gprev = take(N3 * 4), *draws = take(N3 * 4);
     char *ids = take(K * N3 * 4), *ids2 = take(K * N3 * 4);
@@ -179,6 +183,7 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     if (h) {
         h->sig = sig; h->sigk = sigk; h->epse = epse; h->epst = epst; h->epsp = epsp; h->deps = deps;
         h->rho = rho; h->tauc = tauc; h->eta = eta; h->eta2 = eta2; h->spec = spec; h->Stab = Stab; h->Mtab = Mtab;
+        h->fac = fac;
         h->k = (double *)k; h->kappa = (double *)kappa; h->g0 = (int32_t *)g0; h->g = (int32_t *)g;
         h->gprev = (int32_t *)gprev; h->draws = (int32_t *)draws; h->ids = (int32_t *)ids; h->ids2 = (int32_t *)ids2;
         h->partials = (double *)partials; h->scal = (double *)scal; h->flags = (int32_t *)flags;
@@ -436,6 +441,12 @@ int evp_launch_count(const evp_handle *h, int64_t *launches) {
     return EVP_OK;
 }
 
+int evp_newton_refreshes(const evp_handle *h, int64_t *refreshes) {
+    if (!h || !refreshes) return EVP_ERR_ARG;
+    *refreshes = h->newton_refreshes;
+    return EVP_OK;
+}
+
 int evp_newton_counts(const evp_handle *h, int64_t *solves, int64_t *evals) {
     if (!h) return EVP_ERR_ARG;
     if (solves) *solves = h->newton_solves;
@@ -494,20 +505,32 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
     const int zb = fft_z_blocks(n, h->dbl);
     double hs[8];
     int32_t hf[2];
-    int64_t hcount[2] = {0, 0};
+    int64_t hcount[3] = {0, 0, 0};
+    const int reuse = h->cfg.newton_mode == EVP_NEWTON_REUSE;
     for (it = 1; it <= h->cfg.max_iter; ++it) {
         if (h->dbl) {
           { PROF(0, 1);
-            CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
-                                    (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1, h->flags,
-                                    h->st)); }
+            if (reuse)
+                CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
+                                              (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
+                                              h->cfg.newton_max, 1, it == 1, h->flags, h->st));
+            else
+                CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
+                                        (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
+                                        h->flags, h->st)); }
           { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st)); }
           { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st)); }
           { PROF(3, 1); CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st)); }
         } else {
           { PROF(0, 1);
-            CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk, (float *)h->Stab,
-                                   (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64, h->flags, h->st)); }
+            if (reuse)
+                CK(newton_chord_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
+                                             (float *)h->Stab, (float *)h->Mtab, h->fac, mc, ntol, h->cfg.newton_max,
+                                             solve64, it == 1, h->flags, h->st));
+            else
+                CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
+                                       (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,
+                                       h->flags, h->st)); }
           { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st)); }
           { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st)); }
           { PROF(3, 1); CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st)); }
@@ -556,6 +579,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
     CK(cudaStreamSynchronize(h->st));
     h->newton_solves += hcount[0];
     h->newton_evals += hcount[1];
+    h->newton_refreshes += reuse ? hcount[2] : hcount[0];
     if (status == EVP_OK && !conv) {
         if (h->cfg.allow_unconverged) status = EVP_WARN_UNCONVERGED;
         else status = fail(h, EVP_ERR_FIXEDPOINT, "fixed point not converged in %d iterations (err_eq %.3e, err_bc %.3e)",

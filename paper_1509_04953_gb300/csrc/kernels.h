@@ -31,6 +31,11 @@ template <typename TA>
 cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                          const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
                          cudaStream_t s);
+// Jacobian-reuse variant: fac holds 21 factor words per voxel (double if solve_fp64, else TA).
+template <typename TA>
+cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
+                               const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
+                               int force_refresh, int *flags, cudaStream_t s);
 template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s);

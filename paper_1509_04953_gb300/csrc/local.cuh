@@ -140,4 +140,98 @@ template <typename TS, typename TA> __device__ __forceinline__ bool ldl_solve(co
 }
 
 
+// Residual and potential only (no tangent): the cost of a chord step.
+template <typename TA> struct EvalR {
+    TA r[6];
+    TA phi;
+};
+template <typename TA>
+__device__ __forceinline__ void evaluate_r(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA inv_tc,
+                                           const TA sg[6], const MatConst &mc, EvalR<TA> &e) {
+    const TA dt = (TA)mc.dt, g0 = (TA)mc.gdot0, nn = (TA)mc.n;
+    TA phi = (TA)0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        TA acc = (TA)0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += Sp[i >= j ? pk(i, j) : pk(j, i)] * sg[j];
+        e.r[i] = acc - etr[i];
+        phi += sg[i] * ((TA)0.5 * acc - etr[i]);
+    }
+    const TA cphi = dt * g0 * tauc / (nn + (TA)1);
+#pragma unroll 1
+    for (int a = 0; a < 12; ++a) {
+        TA m[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) m[i] = __ldg(M + 6 * a + i);
+        TA tau = (TA)0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
+        const TA x = tau * inv_tc, ax = fabs(x);
+        const TA p10 = pow_nm1(ax, mc) * ax;
+        const TA gd = x < (TA)0 ? -g0 * p10 : g0 * p10;
+        const TA dg = dt * gd;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) e.r[i] += dg * m[i];
+        phi += cphi * p10 * ax;
+    }
+    e.phi = phi;
+}
+
+// LDL^T factorisation kept for reuse: F[0..14] = strict lower L (row-major by packed index, diagonal
+// slots skipped), F[15..20] = 1/D. Returns false if a pivot is not positive.
+template <typename TS, typename TA> __device__ __forceinline__ bool ldl_factor(const TA Kin[21], TS F[21]) {
+    TS L[21], invD[6], w[6];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        TS dj = (TS)Kin[pk(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) {
+            w[k] = L[pk(j, k)] * L[pk(k, k)];
+            dj -= w[k] * L[pk(j, k)];
+        }
+        ok = ok && (dj > (TS)0);
+        dj = dj > (TS)0 ? dj : (TS)1;
+        L[pk(j, j)] = dj;
+        invD[j] = rcp_s(dj);
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            TS t = (TS)Kin[pk(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[pk(i, k)] * w[k];
+            L[pk(i, j)] = t * invD[j];
+        }
+    }
+    int q = 0;
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) F[q++] = L[pk(i, j)];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) F[15 + j] = invD[j];
+    return ok;
+}
+
+template <typename TS, typename TA> __device__ __forceinline__ void ldl_apply(const TS F[21], const TA rin[6], TA dout[6]) {
+    // strict-lower index of (i, j), j < i: i(i-1)/2 + j
+    TS y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        TS t = (TS)rin[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= F[i * (i - 1) / 2 + k] * y[k];
+        y[i] = t;
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        TS t = y[i] * F[15 + i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) t -= F[k * (k - 1) / 2 + i] * y[k];
+        y[i] = t;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dout[i] = (TA)y[i];
+}
+
 }  // namespace evp

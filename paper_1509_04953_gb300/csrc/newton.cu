@@ -114,6 +114,134 @@ __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restri
     }
 }
 
+// Local solve with Jacobian reuse (chord Newton): the LDL^T factors of the tangent are stored per
+// voxel and reused across fixed-point iterations; a step costs one residual evaluation and two
+// triangular solves. The factors are refreshed (full tangent + factorisation at the current point)
+// on request (first fixed-point iteration of an increment), when a step contracts by less than
+// 4x, or after a backtracking line search. The local problem is still solved to the same
+// tolerance, so the result matches the exact-Newton one to that tolerance.
+template <typename TA, typename TS>
+__device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA sg[6],
+                           const MatConst &mc, TA tol, int maxit, TA ls_free, TS F[21], bool refresh, int &nevals,
+                           int &nref) {
+    const TA inv_tc = drcp(tauc);
+    EvalR<TA> e;
+    evaluate_r(Sp, M, etr, tauc, inv_tc, sg, mc, e);
+    nevals = 1;
+    nref = 0;
+    TA prev_step = (TA)-1;
+    bool fresh = false;
+    for (int it = 1; it <= maxit; ++it) {
+        if (refresh) {
+            Eval<TA> full;
+            evaluate(Sp, M, etr, tauc, inv_tc, sg, mc, full);
+            ++nevals;
+            if (!ldl_factor<TS, TA>(full.K, F)) return -it;
+            ++nref;
+            refresh = false;
+            fresh = true;
+        }
+        TA d[6];
+        ldl_apply<TS, TA>(F, e.r, d);
+        TA rd = (TA)0, dn = (TA)0, sn = (TA)0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            rd += e.r[i] * d[i];
+            dn += d[i] * d[i];
+            sn += sg[i] * sg[i];
+        }
+        dn = dsqrt(dn);
+        const TA scale = dsqrt(sn) + tauc;
+        if (dn <= tol * scale && rd >= (TA)0) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) sg[i] -= d[i];
+            return it;
+        }
+        if (!fresh && (rd <= (TA)0 || (prev_step > (TA)0 && dn > (TA)0.25 * prev_step))) {
+            refresh = true;   // stale tangent: refactor at this point and redo the step
+            continue;
+        }
+        const TA phi0 = e.phi;
+        TA s = (TA)1, st[6];
+        bool ok = false;
+        for (int h = 0; h < 60; ++h) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) st[i] = sg[i] - s * d[i];
+            evaluate_r(Sp, M, etr, tauc, inv_tc, st, mc, e);
+            ++nevals;
+            if (e.phi <= phi0 - (TA)1e-4 * s * rd || s * dn <= ls_free * scale) {
+                ok = true;
+                break;
+            }
+            s *= (TA)0.5;
+        }
+        if (!ok) return -it;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sg[i] = st[i];
+        if (s * dn <= tol * scale) return it;
+        if (s < (TA)1) refresh = true;
+        prev_step = s * dn;
+        fresh = false;
+    }
+    return -maxit;
+}
+
+template <typename TA, typename TS>
+__global__ void __launch_bounds__(kThreads) k_newton_chord(long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc,
+                                                          const int32_t *__restrict__ g0, TA *__restrict__ sig,
+                                                          const TA *__restrict__ Stab, const TA *__restrict__ Mtab,
+                                                          TS *__restrict__ fac, MatConst mc, TA tol, int maxit,
+                                                          TA ls_free, int force_refresh, int *__restrict__ flags) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = v < N3;
+    int r = 1, nev = 0, nref = 0;
+    if (valid) {
+        const int g = g0[v];
+        TA Sp[21];
+        const TA *S = Stab + 36 * (long)g;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) Sp[pk(i, j)] = __ldg(S + 6 * i + j);
+        TA etr[6], sg[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            etr[c] = epst[c * N3 + v];
+            sg[c] = sig[c * N3 + v];
+        }
+        TS F[21];
+        if (!force_refresh) {
+#pragma unroll
+            for (int q = 0; q < 21; ++q) F[q] = fac[q * N3 + v];
+        }
+        r = chord_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
+                                force_refresh != 0, nev, nref);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
+        if (nref) {
+#pragma unroll
+            for (int q = 0; q < 21; ++q) fac[q * N3 + v] = F[q];
+        }
+    }
+    __syncwarp();
+    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
+    int mx = valid ? (r < 0 ? -r : r) : 0;
+    int sit = valid ? mx : 0, sev = nev, srf = nref;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sit += __shfl_xor_sync(0xffffffffu, sit, o);
+        sev += __shfl_xor_sync(0xffffffffu, sev, o);
+        srf += __shfl_xor_sync(0xffffffffu, srf, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fmask) atomicAdd(flags, __popc(fmask));
+        atomicMax(flags + 1, mx);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 8), (unsigned long long)srf);
+    }
+}
+
 // Start of an increment: tau_c from the densities at t (frozen over the increment) and the
 // predictor eps_tr = eps_e^t + (r * deps_prev  |  dE).
 template <typename TA>
@@ -220,6 +348,20 @@ cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t 
 }
 
 template <typename TA>
+cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
+                               const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
+                               int force_refresh, int *flags, cudaStream_t s) {
+    const int blocks = (int)((N3 + kThreads - 1) / kThreads);
+    if (solve_fp64)
+        k_newton_chord<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (double *)fac, mc,
+                                                               (TA)tol, maxit, ls_free_of<TA>(), force_refresh, flags);
+    else
+        k_newton_chord<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc, (TA)tol,
+                                                           maxit, ls_free_of<TA>(), force_refresh, flags);
+    return cudaGetLastError();
+}
+
+template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s) {
     const int blocks = (int)((N3 + 255) / 256);
@@ -245,6 +387,9 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
 #define EVP_INST(TA)                                                                                              \
     template cudaError_t newton_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,        \
                                           const TA *, MatConst, double, int, int, int *, cudaStream_t);          \
+    template cudaError_t newton_chord_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,  \
+                                                const TA *, void *, MatConst, double, int, int, int, int *,       \
+                                                cudaStream_t);                                                    \
     template cudaError_t predictor<TA>(long, const TA *, const TA *, const TA *, TA *, TA *, MatConst, double,    \
                                        const double *, int, cudaStream_t);                                        \
     template cudaError_t state_update<TA>(long, const TA *, const TA *, const int32_t *, const TA *, TA *, TA *,  \

@@ -36,7 +36,8 @@ class EVPError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("n", C.c_int), ("grains", C.c_int), ("kmax", C.c_int), ("precision", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("allow_unconverged", C.c_int),
-                ("newton_tol", C.c_double), ("newton_max", C.c_int), ("predictor", C.c_int), ("max_ids", C.c_int)]
+                ("newton_tol", C.c_double), ("newton_max", C.c_int), ("predictor", C.c_int), ("max_ids", C.c_int),
+                ("newton_mode", C.c_int)]
 
 
 class Params(C.Structure):
@@ -90,6 +91,7 @@ def load():
     L.evp_kernel_times.argtypes = [vp, vp, vp, i]
     L.evp_launch_count.argtypes = [vp, vp]
     L.evp_newton_counts.argtypes = [vp, vp, vp]
+    L.evp_newton_refreshes.argtypes = [vp, vp]
     L.evp_voronoi.argtypes = [i, i, vp, vp, vp]
     L.evp_rfft3d.argtypes = [i, i, i, vp, vp, vp]
     L.evp_irfft3d.argtypes = [i, i, i, vp, vp, vp]
@@ -99,7 +101,8 @@ def load():
               "set_fields", "evp_fields_bytes", "evp_get_scalars", "evp_set_scalars", "evp_set_solver",
               "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_kernel_times",
               "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual",
-              "evp_adjoint_workspace_bytes", "evp_adjoint_begin", "evp_adjoint_step", "evp_adjoint_end"):
+              "evp_adjoint_workspace_bytes", "evp_adjoint_begin", "evp_adjoint_step", "evp_adjoint_end",
+              "evp_newton_refreshes"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -112,12 +115,19 @@ def _torch():
     return torch
 
 
+NEWTON_MODES = {"exact": 0, "reuse": 1}
+
+
 def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, allow_unconverged=0,
-                newton_tol=None, newton_max=50, predictor=1, max_ids=0) -> Config:
+                newton_tol=None, newton_max=50, predictor=1, max_ids=0, newton=None) -> Config:
     if newton_tol is None:
         newton_tol = 1e-12 if precision == "fp64" else 1e-5
+    if newton is None:
+        # tangent reuse pays where the 6x6 solve is FP64 next to an FP32 residual (EVP_MIXED);
+        # with an all-FP64 or all-FP32 local problem the exact Newton is faster on GB300
+        newton = "reuse" if precision == "mixed" else "exact"
     return Config(n, grains, kmax, PRECISION[precision], tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                  predictor, max_ids)
+                  predictor, max_ids, NEWTON_MODES[newton])
 
 
 def make_params(mat) -> Params:
@@ -296,10 +306,13 @@ class Solver:
         return n.value
 
     def newton_counts(self):
+        """(6x6 solves, residual evaluations, tangent factorisations) so far."""
         a = C.c_int64(0)
         b = C.c_int64(0)
+        c = C.c_int64(0)
         self._check("evp_newton_counts", load().evp_newton_counts(self.h, C.byref(a), C.byref(b)))
-        return a.value, b.value
+        self._check("evp_newton_refreshes", load().evp_newton_refreshes(self.h, C.byref(c)))
+        return a.value, b.value, c.value
 
     @property
     def next_id(self):

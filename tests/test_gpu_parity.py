@@ -87,11 +87,13 @@ def test_stress_residual_matches_oracle(ev, n, prec):
 # ------------------------------------------------------------------------------------------
 # a2-a7 fixed point and state update
 # ------------------------------------------------------------------------------------------
-def test_fixed_iterations_match_oracle_fp64(ev, mat):
-    """Same number of fixed-point iterations on both sides: every field agrees to round-off."""
+@pytest.mark.parametrize("newton", ["exact", "reuse"])
+def test_fixed_iterations_match_oracle_fp64(ev, mat, newton):
+    """Same number of fixed-point iterations on both sides: every field agrees to round-off, with the
+    exact local Newton and with tangent reuse (the local problem is solved to the same tolerance)."""
     n, G, seed = 16, 8, synth.BASE_SEED
     kw = dict(tol=0.0, max_iter=6, allow_unconverged=1)
-    gpu, ref, _ = make_pair(ev, mat, n, G, seed, **kw)
+    gpu, ref, _ = make_pair(ev, mat, n, G, seed, newton=newton, **kw)
     for inc in range(2):
         rc, st = gpu.increment(-1e-3, 1.0)
         rco, sto = ref.increment(-1e-3, 1.0)
