@@ -121,3 +121,37 @@ def test_torch_autograd_function(ev, mat, target):
     loss.backward()
     _, g, _, _ = gpu_loss_grad(ev, m1, target)
     assert np.allclose(theta.grad.numpy(), g, rtol=1e-9, atol=0)
+
+
+def test_adjoint_on_the_differentiation_workload(ev, mat):
+    """32^3, 27 grains, 50 increments (about sqrt(50) = 7 increments per checkpoint): the checkpointed
+    FP64 adjoint gradient against central differences of the GPU forward (h = 1e-6 relative)."""
+    wl = synth.WORKLOADS["cu32adj"]
+    g0 = O.voronoi(wl.n, synth.voronoi_seeds(wl.n, wl.grains, wl.seed))
+    q = synth.orientations(wl.grains, wl.seed)
+    T = wl.increments
+
+    def run(m, want_grad, target):
+        s = ev.Solver(wl.n, wl.grains, g0, q, m, wl.seed, precision="fp64", tol=1e-12, max_iter=40000)
+        s.adjoint_begin(T, 7)
+        curve = np.array([s.adjoint_step(wl.dE33, wl.dt).sig_mean[2] for _ in range(T)])
+        L = float(((curve - target) ** 2).sum()) if target is not None else 0.0
+        g = None
+        if want_grad:
+            gb = np.zeros((T, 6))
+            gb[:, 2] = 2 * (curve - target)
+            g = s.adjoint_end(gb, tol=1e-11)
+        s.close()
+        return L, g, curve
+
+    _, _, target = run(mat, False, None)
+    m1 = perturbed(mat)
+    L, g, _ = run(m1, True, target)
+    assert L > 0
+    for i, k in enumerate(("k1", "k2", "tau0", "n")):
+        v = getattr(m1, k)
+        h = 1e-6 * v
+        Lp = run(dataclasses.replace(m1, **{k: v + h}), False, target)[0]
+        Lm = run(dataclasses.replace(m1, **{k: v - h}), False, target)[0]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(g[i] / fd - 1) < 1e-5, (k, g[i], fd)
