@@ -48,6 +48,7 @@ def parse():
                     help="precision of the timed solver (the headline is the mixed path)")
     ap.add_argument("--fp64-steps", type=int, default=-1, help="FP64 comparison increments (-1 = warmup+steps)")
     ap.add_argument("--fast-steps", type=int, default=2, help="timed increments of the FP32-solve mixed path")
+    ap.add_argument("--al-steps", type=int, default=1, help="run the augmented-Lagrangian companion (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
@@ -249,6 +250,8 @@ def native(args, ws, rank, local):
     res["memory_bound_kernels"] = memory_kernels(ktimes, wl, N3, args.precision, pk)
     if args.fast_steps > 0:
         res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
+    if args.al_steps > 0:
+        res["augmented_lagrangian"] = al_companion(args, wl, g0, quat, mat, torch, evp, warm + timed)
     # FP64 companion run on the same seeded input
     n64 = args.warmup + args.steps if args.fp64_steps < 0 else args.fp64_steps
     if n64 > 0:
@@ -322,6 +325,27 @@ def fast_companion(args, wl, g0, quat, mat, torch, evp):
     return {"voxel_iters_per_s": wl.n ** 3 * sum(r["it"] for r in h) / evp_s,
             "drx_increments_per_s": len(h) / step_s, "increments": len(h),
             "fixed_point_iterations": [r["it"] for r in h]}
+
+
+def al_companion(args, wl, g0, quat, mat, torch, evp, basic_hist):
+    """The augmented-Lagrangian solver (the scheme the paper names) on the same input and precision:
+    increments 1..W+K, timed over the last K, macro stress compared with the basic scheme."""
+    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision,
+                   tol=args.tol64 if args.precision == "fp64" else args.tol, max_iter=5000, scheme="al")
+    w = len(basic_hist) - args.steps
+    hw = run_steps(s, w, wl.dE33, wl.dt, wl.pf_steps, torch)
+    s.set_profiling(True)
+    s.kernel_times(reset=True)
+    h = run_steps(s, args.steps, wl.dE33, wl.dt, wl.pf_steps, torch)
+    kt = s.kernel_times(reset=True)
+    evp_s = sum(r["evp_ms"] for r in h) / 1e3
+    step_s = sum(r["step_ms"] for r in h) / 1e3
+    errs = [abs(a["sig33"] - b["sig33"]) / abs(b["sig33"]) for a, b in zip(hw + h, basic_hist)]
+    return {"voxel_iters_per_s": wl.n ** 3 * sum(r["it"] for r in h) / evp_s,
+            "drx_increments_per_s": len(h) / step_s, "ms_per_step": 1e3 * step_s / len(h),
+            "fixed_point_iterations": [r["it"] for r in hw + h], "al_scale": 6.0,
+            "macro_stress_rel_diff_vs_basic_max": max(errs),
+            "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}}
 
 
 def fp64_companion(args, wl, g0, quat, mat, nsteps, mixed_hist, torch, evp):

@@ -61,7 +61,13 @@ typedef struct {
     int newton_mode;       /* 0: exact Newton every fixed-point iteration; 1: keep each voxel's factored
                               tangent across iterations and refactor only when a step stalls (same
                               local tolerance, same result); EVP_NEWTON_* */
+    int scheme;            /* EVP_SCHEME_BASIC: Green-operator fixed point (Moulinec-Suquet);
+                              EVP_SCHEME_AL: augmented Lagrangian (Michel-Moulinec-Suquet), the solver the
+                              paper names (Sec. 2.1); same solution, fewer iterations at high contrast */
+    double al_scale;       /* EVP_SCHEME_AL: reference shear modulus = Voigt mu / al_scale (bulk kept) */
 } evp_config;
+#define EVP_SCHEME_BASIC 0
+#define EVP_SCHEME_AL 1
 #define EVP_NEWTON_EXACT 0
 #define EVP_NEWTON_REUSE 1
 
@@ -128,6 +134,9 @@ int evp_init(evp_handle **h, const evp_config *cfg, const evp_params *p, const i
  * mechanical increment under mixed conditions -- E33 advances by dE33, the other mean stresses
  * are driven to zero -- solved by the Green-operator fixed point with a per-voxel implicit
  * Newton stress update, then the plastic strain, densities, tau_c and k = rho_tot are advanced.
+ * With EVP_SCHEME_AL the same increment is solved by the augmented Lagrangian iteration: err_eq then
+ * reports the RMS multiplier update |C0 (eps - e)| / |<lam>|, and convergence also requires the RMS
+ * compatibility gap |eps - e| / |E| below tol (on-device checks as for the basic scheme).
  * out may be NULL. Returns EVP_ERR_NEWTON / EVP_ERR_FIXEDPOINT / EVP_ERR_NONFINITE without
  * advancing the state. */
 int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out);

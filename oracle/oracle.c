@@ -592,7 +592,241 @@ void orc_stress_residual(int n, const double *sig, double out[7]) {
  *      C0^-1 at frequencies that have a Nyquist component (Moulinec-Suquet treatment of even N)
  * After convergence the state is advanced with the converged shear rates (a7).
  * ---------------------------------------------------------------------------------------- */
+
+/* ------------------------------------------------------------------------------------------
+ * One mechanical increment by the augmented Lagrangian scheme the paper names for its solver
+ * (Sec. 2.1: "augmented Lagrangian scheme adapted from Michel et al. 2000"; Michel, Moulinec,
+ * Suquet 2001). Unknowns: a compatible strain eps (mean E), a local strain e and a stress-like
+ * multiplier lam. With an isotropic reference medium C0 (shear mu_Voigt/al_scale, Voigt bulk):
+ *   (i)   eps = E + Gamma0 * (C0 : e - lam)                      (compatibility, spectral)
+ *   (ii)  sigma(e) + C0 : e = lam + C0 : eps                     (local, per voxel)
+ *   (iii) lam = lam + C0 : (eps - e)
+ * At the fixed point eps = e and lam = sigma(e) with div lam = 0: the same solution as the basic
+ * scheme. Step (ii) is the implicit stress update with the compliance S + C0^-1 and the trial strain
+ * C0^-1 (lam + C0 eps) - eps_p^t, so it reuses orc_newton. Stopping rule: the RMS of eps - e relative
+ * to max(|E|, 1e-6) and of C0 (eps - e) relative to max(|<lam>|, tau0), and the mean stress on the
+ * stress-controlled components, all below tol.
+ * ---------------------------------------------------------------------------------------- */
+static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out) {
+    const orc_params *p = &s->p;
+    const int n = s->n;
+    const long N3 = s->N3;
+    const double lamV = lam_voigt(p), muV = mu_voigt(p);
+    const double K0 = lamV + 2.0 * muV / 3.0;
+    const double mu0 = muV / (s->cfg.al_scale > 0 ? s->cfg.al_scale : 1.0), lam0 = K0 - 2.0 * mu0 / 3.0;
+    int status = 0;
+    memset(out, 0, sizeof *out);
+    double C0[36], S0[36];
+    for (int I = 0; I < 6; ++I)
+        for (int J = 0; J < 6; ++J) C0[6 * I + J] = (I < 3 && J < 3 ? lam0 : 0.0) + (I == J ? 2.0 * mu0 : 0.0);
+    inv_gj(6, C0, S0);
+    const int U[5] = {0, 1, 3, 4, 5};
+    double C0uu[25], C0uu_inv[25];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) C0uu[5 * a + b] = C0[6 * U[a] + U[b]];
+    inv_gj(5, C0uu, C0uu_inv);
+    /* per-grain compliance of the local problem: S + C0^-1 */
+    double *Sal = (double *)xcalloc(36 * (size_t)s->G, sizeof(double));
+    for (int g = 0; g < s->G; ++g)
+        for (int i = 0; i < 36; ++i) Sal[36 * g + i] = s->S[36 * g + i] + S0[i];
+    double *tauc = (double *)xcalloc(N3, sizeof(double));
+    for (long v = 0; v < N3; ++v) tauc[v] = tauc_of(p, s->rho, N3, v);
+    double *eps = s->work_eps, *sig = s->work_sig;
+    double *e = (double *)xcalloc(6 * N3, sizeof(double));
+    double *lam = (double *)xcalloc(6 * N3, sizeof(double));
+    /* predictor (as in the basic scheme) */
+    double dE[6];
+    if (s->cfg.predictor && s->have_prev && s->dE_prev[2] != 0.0) {
+        double r = dE33 / s->dE_prev[2];
+        for (int I = 0; I < 6; ++I) dE[I] = r * s->dE_prev[I];
+        dE[2] = dE33;
+        for (long i = 0; i < 6 * N3; ++i) eps[i] = s->eps[i] + r * s->deps_prev[i];
+    } else {
+        double nu0 = lamV / (2.0 * (lamV + muV));
+        double g[6] = {-nu0 * dE33, -nu0 * dE33, dE33, 0, 0, 0};
+        memcpy(dE, g, sizeof g);
+        for (int I = 0; I < 6; ++I)
+            for (long v = 0; v < N3; ++v) eps[I * N3 + v] = s->eps[I * N3 + v] + dE[I];
+    }
+    /* start: e = eps, lam = sigma(eps) by the local update of the basic scheme */
+    memcpy(sig, s->sig, 6 * N3 * sizeof(double));
+    int newton_max = 0, newton_fail = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : newton_max) reduction(| : newton_fail)
+    for (long v = 0; v < N3; ++v) {
+        int gr = s->g0[v];
+        double etr[6], sg[6], gd[12];
+        for (int I = 0; I < 6; ++I) { etr[I] = eps[I * N3 + v] - s->epsp[I * N3 + v]; sg[I] = sig[I * N3 + v]; }
+        int its = 0;
+        if (orc_newton(p, s->S + 36 * gr, s->M + 72 * gr, etr, tauc[v], dt, s->cfg.newton_tol, s->cfg.newton_max,
+                       sg, gd, &its)) newton_fail |= 1;
+        if (its > newton_max) newton_max = its;
+        for (int I = 0; I < 6; ++I) { sig[I * N3 + v] = sg[I]; lam[I * N3 + v] = sg[I]; e[I * N3 + v] = eps[I * N3 + v]; }
+    }
+    int k, conv = 0;
+    double err_cmp = 0, err_lam = 0, err_bc = 0, mean[6] = {0};
+    for (k = 1; k <= s->cfg.max_iter && !newton_fail; ++k) {
+        /* macroscopic strain on the stress-controlled components, from <lam> */
+        for (int I = 0; I < 6; ++I) {
+            double a = 0.0;
+            for (long v = 0; v < N3; ++v) a += lam[I * N3 + v];
+            mean[I] = a / (double)N3;
+        }
+        double dEk[6] = {0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < 5; ++a) {
+            double v = 0.0;
+            for (int b = 0; b < 5; ++b) v += C0uu_inv[5 * a + b] * (0.0 - mean[U[b]]);
+            dEk[U[a]] = v;
+        }
+        for (int I = 0; I < 6; ++I) dE[I] += dEk[I];
+        /* (i) compatibility: eps = E + Gamma0 * (C0 e - lam) */
+        for (int I = 0; I < 6; ++I) {
+            for (long v = 0; v < N3; ++v) {
+                double ce = 0.0;
+                for (int J = 0; J < 6; ++J) ce += C0[6 * I + J] * e[J * N3 + v];
+                s->spec[I * N3 + v] = ce - lam[I * N3 + v];
+            }
+            orc_fft3d(n, s->spec + I * N3, -1);
+        }
+        for (int kz = 0; kz < n; ++kz)
+            for (int ky = 0; ky < n; ++ky)
+                for (int kx = 0; kx < n; ++kx) {
+                    long v = kx + (long)n * (ky + (long)n * kz);
+                    double complex ph[6], eh[6];
+                    for (int I = 0; I < 6; ++I) ph[I] = s->spec[I * N3 + v];
+                    if (kx == 0 && ky == 0 && kz == 0) {
+                        for (int I = 0; I < 6; ++I) eh[I] = 0;
+                    } else {
+                        double Gm[36];
+                        int nyq = (n > 1) && (kx == n / 2 || ky == n / 2 || kz == n / 2);
+                        if (nyq) memcpy(Gm, S0, sizeof Gm);
+                        else {
+                            double xi[3] = {freq(kx, n), freq(ky, n), freq(kz, n)};
+                            orc_gamma0(xi, lam0, mu0, Gm);
+                        }
+                        for (int I = 0; I < 6; ++I) {
+                            double complex a = 0;
+                            for (int J = 0; J < 6; ++J) a += Gm[6 * I + J] * ph[J];
+                            eh[I] = a;
+                        }
+                    }
+                    for (int I = 0; I < 6; ++I) s->spec[I * N3 + v] = eh[I];
+                }
+        for (int I = 0; I < 6; ++I) {
+            orc_fft3d(n, s->spec + I * N3, +1);
+            for (long v = 0; v < N3; ++v)
+                eps[I * N3 + v] = s->E[I] + dE[I] + creal(s->spec[I * N3 + v]) / (double)N3;
+        }
+        /* (ii) local problem and (iii) multiplier update */
+        double acc_c = 0.0, acc_l = 0.0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : newton_max) reduction(| : newton_fail) reduction(+ : acc_c, acc_l)
+        for (long v = 0; v < N3; ++v) {
+            int gr = s->g0[v];
+            double tau[6], etr[6], sg[6], gd[12];
+            for (int I = 0; I < 6; ++I) {
+                double ce = 0.0;
+                for (int J = 0; J < 6; ++J) ce += C0[6 * I + J] * eps[J * N3 + v];
+                tau[I] = lam[I * N3 + v] + ce;
+            }
+            for (int I = 0; I < 6; ++I) {
+                double st = 0.0;
+                for (int J = 0; J < 6; ++J) st += S0[6 * I + J] * tau[J];
+                etr[I] = st - s->epsp[I * N3 + v];
+                sg[I] = sig[I * N3 + v];
+            }
+            int its = 0;
+            if (orc_newton(p, Sal + 36 * gr, s->M + 72 * gr, etr, tauc[v], dt, s->cfg.newton_tol, s->cfg.newton_max,
+                           sg, gd, &its)) newton_fail |= 1;
+            if (its > newton_max) newton_max = its;
+            double ev[6], d[6];
+            for (int I = 0; I < 6; ++I) {
+                double st = 0.0;
+                for (int J = 0; J < 6; ++J) st += S0[6 * I + J] * (tau[J] - sg[J]);
+                ev[I] = st;                                  /* e = C0^-1 (tau - sigma) */
+                d[I] = eps[I * N3 + v] - ev[I];
+            }
+            for (int I = 0; I < 6; ++I) {
+                double cd = 0.0;
+                for (int J = 0; J < 6; ++J) cd += C0[6 * I + J] * d[J];
+                lam[I * N3 + v] += cd;
+                acc_l += cd * cd;
+                acc_c += d[I] * d[I];
+                e[I * N3 + v] = ev[I];
+                sig[I * N3 + v] = sg[I];
+            }
+        }
+        if (newton_fail) break;
+        double Enorm = 0.0, mn = 0.0, mu_n = 0.0;
+        for (int I = 0; I < 6; ++I) Enorm += (s->E[I] + dE[I]) * (s->E[I] + dE[I]);
+        for (int I = 0; I < 6; ++I) {
+            double a = 0.0;
+            for (long v = 0; v < N3; ++v) a += lam[I * N3 + v];
+            mean[I] = a / (double)N3;
+            mn += mean[I] * mean[I];
+        }
+        for (int a = 0; a < 5; ++a) mu_n += mean[U[a]] * mean[U[a]];
+        const double den = fmax(sqrt(mn), p->tau0);
+        err_cmp = sqrt(acc_c / (double)N3) / fmax(sqrt(Enorm), 1e-6);
+        err_lam = sqrt(acc_l / (double)N3) / den;
+        err_bc = sqrt(mu_n) / den;
+        if (!isfinite(err_cmp) || !isfinite(err_lam)) { status = -5; break; }
+        if (err_cmp <= s->cfg.tol && err_lam <= s->cfg.tol && err_bc <= s->cfg.tol) { conv = 1; break; }
+    }
+    if (newton_fail) status = -3;
+    out->iterations = k > s->cfg.max_iter ? s->cfg.max_iter : k;
+    out->newton_max_iters = newton_max;
+    out->err_eq = err_lam;
+    out->err_bc = err_bc;
+    /* report the mean of the stress field itself */
+    for (int I = 0; I < 6; ++I) {
+        double a = 0.0;
+        for (long v = 0; v < N3; ++v) a += sig[I * N3 + v];
+        out->sig_mean[I] = a / (double)N3;
+    }
+    if (status == 0 && !conv) status = s->cfg.allow_unconverged ? 1 : -4;
+    if (status < 0) {
+        for (int I = 0; I < 6; ++I) out->E[I] = s->E[I] + dE[I];
+        out->status = status;
+        free(Sal); free(tauc); free(e); free(lam);
+        return status;
+    }
+    /* state update with the converged stress; the total strain is the local strain e */
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < N3; ++v) {
+        int gr = s->g0[v];
+        const double *M = s->M + 72 * gr;
+        double gd[12], rho[12];
+        for (int a = 0; a < 12; ++a) {
+            double tau = 0.0;
+            for (int I = 0; I < 6; ++I) tau += M[6 * a + I] * sig[I * N3 + v];
+            double x = tau / tauc[v], ax = fabs(x);
+            gd[a] = ax > 0.0 ? p->gdot0 * pow(ax, p->n) * (x < 0.0 ? -1.0 : 1.0) : 0.0;
+        }
+        for (int I = 0; I < 6; ++I) {
+            double ep = 0.0;
+            for (int a = 0; a < 12; ++a) ep += M[6 * a + I] * gd[a];
+            s->epsp[I * N3 + v] += dt * ep;
+        }
+        for (int a = 0; a < 12; ++a) rho[a] = s->rho[a * N3 + v];
+        orc_km_update(p, rho, gd, dt);
+        double kk = 0.0;
+        for (int a = 0; a < 12; ++a) { s->rho[a * N3 + v] = rho[a]; kk += rho[a]; }
+        s->k[v] = kk;
+        for (int I = 0; I < 6; ++I) {
+            s->deps_prev[I * N3 + v] = e[I * N3 + v] - s->eps[I * N3 + v];
+            s->eps[I * N3 + v] = e[I * N3 + v];
+            s->sig[I * N3 + v] = sig[I * N3 + v];
+        }
+    }
+    for (int I = 0; I < 6; ++I) { s->E[I] += dE[I]; s->dE_prev[I] = dE[I]; }
+    s->have_prev = 1;
+    memcpy(out->E, s->E, sizeof s->E);
+    out->status = status;
+    free(Sal); free(tauc); free(e); free(lam);
+    return status;
+}
+
 int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
+    if (s->cfg.scheme == 1) return orc_increment_al(s, dE33, dt, out);
     const orc_params *p = &s->p;
     const int n = s->n;
     const long N3 = s->N3;

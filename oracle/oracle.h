@@ -37,6 +37,8 @@ typedef struct {
     int newton_max;
     int predictor;             /* 1: extrapolate the previous strain-increment field */
     int nthreads;              /* OpenMP threads for per-voxel loops (0 = default) */
+    int scheme;                /* 0: basic Green-operator iteration, 1: augmented Lagrangian */
+    double al_scale;           /* augmented Lagrangian: reference shear modulus = mu_Voigt / al_scale */
 } orc_config;
 
 typedef struct {

@@ -25,7 +25,7 @@ struct evp_handle {
     char *ws;
     size_t ws_bytes;
     // fields
-    void *sig, *sigk, *epse, *epst, *epsp, *deps, *rho, *tauc, *eta, *eta2, *spec, *Stab, *Mtab, *fac;
+    void *sig, *sigk, *epse, *epst, *epsp, *deps, *rho, *tauc, *eta, *eta2, *spec, *Stab, *Mtab, *fac, *Sal, *lam, *pal;
     double *k, *kappa, *partials, *scal;
     int32_t *g0, *g, *gprev, *draws, *ids, *ids2, *flags, *blk_counts, *blk_off, *count;
     uint32_t *bitmap;
@@ -144,6 +144,10 @@ int check_cfg(const evp_config *c, char *why, size_t wl) {
     if (c->max_iter < 1 || c->newton_max < 1) return snprintf(why, wl, "iteration caps must be >= 1"), EVP_ERR_ARG;
     if (!(c->tol >= 0.0) || !(c->newton_tol > 0.0)) return snprintf(why, wl, "tolerances must be >= 0"), EVP_ERR_ARG;
     if (c->max_ids != 0 && c->max_ids < c->grains) return snprintf(why, wl, "max_ids < grains"), EVP_ERR_ARG;
+    if (c->scheme != EVP_SCHEME_BASIC && c->scheme != EVP_SCHEME_AL)
+        return snprintf(why, wl, "unknown scheme %d", c->scheme), EVP_ERR_ARG;
+    if (c->scheme == EVP_SCHEME_AL && !(c->al_scale >= 1.0))
+        return snprintf(why, wl, "al_scale must be >= 1"), EVP_ERR_ARG;
     if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE)
         return snprintf(why, wl, "unknown newton_mode %d", c->newton_mode), EVP_ERR_ARG;
     return EVP_OK;
@@ -156,7 +160,7 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     const int K = c->kmax, G = c->grains;
     const long max_ids = c->max_ids ? c->max_ids : (long)G + 8 * N3;
     const int nb = nucleate_blocks(N3);
-    const int npart = std::max(fft_z_blocks((int)n, T == 8), 2 * pf_stat_blocks(N3) + 1);
+    const int npart = std::max(std::max(fft_z_blocks((int)n, T == 8), 2 * pf_stat_blocks(N3) + 1), 14 * al_blocks(N3));
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
         off = (off + 255) & ~(size_t)255;
@@ -170,6 +174,8 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *Stab = take(36 * (size_t)G * T), *Mtab = take(72 * (size_t)G * T);
     const size_t TSf = c->precision == EVP_MIXED_FAST ? 4 : 8;   // stored tangent factors
     char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? 21 * N3 * TSf : 0);
+    const bool al = c->scheme == EVP_SCHEME_AL;
+    char *Sal = take(al ? 36 * (size_t)G * T : 0), *lam = take(al ? 6 * N3 * T : 0), *pal = take(al ? 6 * N3 * T : 0);
     char *k = take(N3 * 8), *kappa = take(N3 * 8);
     char *g0 = take(N3 * 4), *g = take(N3 * 4), *gprev = take(N3 * 4), *draws = take(N3 * 4);
     char *ids = take(K * N3 * 4), *ids2 = take(K * N3 * 4);
@@ -184,6 +190,9 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
         h->sig = sig; h->sigk = sigk; h->epse = epse; h->epst = epst; h->epsp = epsp; h->deps = deps;
         h->rho = rho; h->tauc = tauc; h->eta = eta; h->eta2 = eta2; h->spec = spec; h->Stab = Stab; h->Mtab = Mtab;
         h->fac = fac;
+        h->Sal = Sal;
+        h->lam = lam;
+        h->pal = pal;
         h->k = (double *)k; h->kappa = (double *)kappa; h->g0 = (int32_t *)g0; h->g = (int32_t *)g;
         h->gprev = (int32_t *)gprev; h->draws = (int32_t *)draws; h->ids = (int32_t *)ids; h->ids2 = (int32_t *)ids2;
         h->partials = (double *)partials; h->scal = (double *)scal; h->flags = (int32_t *)flags;
@@ -314,6 +323,80 @@ void *field_ptr(evp_handle *h, uint32_t bit) {
     }
 }
 
+
+// Augmented-Lagrangian iterations of one increment (after the predictor): see k_al_local.
+// Returns a status; fills the iteration count, residuals, mean stress and the macro strain increment.
+template <typename TA>
+int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, int *nmax_out, double *err_eq,
+            double *err_bc, double *mean_sig) {
+    const long N3 = h->N3;
+    const int n = h->n;
+    const double muV = h->mc.mu0, lamV = h->mc.lam0;
+    const double mu0 = muV / h->cfg.al_scale, lam0 = (lamV + 2.0 * muV / 3.0) - 2.0 * mu0 / 3.0;
+    const double a = lam0 + 2.0 * mu0, b = lam0, det = a * a - b * b;
+    const int solve64 = h->prec != EVP_MIXED_FAST;
+    const int nb = al_blocks(N3);
+    double hs[14];
+    int32_t hf[2];
+    int nmax = 0, conv = 0, it;
+    double ecmp = 0, elam = 0, ebc = 0;
+    auto local = [&](int init) -> int {
+        { PROF(0, 1);
+          CK(al_local<TA>(N3, (const TA *)h->epst, (const TA *)h->epse, (const TA *)h->tauc, h->g0, (TA *)h->sigk,
+                          (TA *)h->lam, (TA *)h->pal, (const TA *)h->Stab, (const TA *)h->Sal, (const TA *)h->Mtab, mc,
+                          lam0, mu0, h->cfg.newton_tol, h->cfg.newton_max, solve64, init, h->flags, h->partials,
+                          h->st)); }
+        { PROF(6, 1); CK(reduce_partials(h->partials, nb, 14, h->scal + 24, h->st)); }
+        CK(cudaMemcpyAsync(hs, h->scal + 24, sizeof hs, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(hf, h->flags, sizeof hf, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        if (h->prof) prof_collect(h);
+        nmax = hf[1] > nmax ? hf[1] : nmax;
+        if (hf[0] != 0) return fail(h, EVP_ERR_NEWTON, "local Newton failed in %d voxels", hf[0]);
+        return EVP_OK;
+    };
+    int rc = local(1);
+    if (rc) { *it_out = 0; *nmax_out = nmax; return rc; }
+    for (it = 1; it <= h->cfg.max_iter; ++it) {
+        // macroscopic strain on the stress-controlled components from <lam>
+        const double m0 = hs[2] / (double)N3, m1 = hs[3] / (double)N3;
+        double dEk[6] = {0, 0, 0, 0, 0, 0};
+        dEk[0] = (a * (-m0) - b * (-m1)) / det;
+        dEk[1] = (-b * (-m0) + a * (-m1)) / det;
+        for (int i = 3; i < 6; ++i) dEk[i] = -(hs[2 + i] / (double)N3) / (2.0 * mu0);
+        for (int i = 0; i < 6; ++i) dE[i] += dEk[i];
+        // compatibility: eps_tr = eps_e^t + dE + Gamma0 * (C0 de - lam)
+        { PROF(1, 1); CK(fft_x_r2c<TA>((const TA *)h->pal, h->spec, n, 6, h->st)); }
+        { PROF(2, 1); CK(fft_y<TA>(h->spec, n, 6, 0, h->st)); }
+        { PROF(3, 1); CK(fft_z<TA>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, nullptr, nullptr, h->st)); }
+        { PROF(4, 1); CK(fft_y<TA>(h->spec, n, 6, 1, h->st)); }
+        { PROF(5, 1);
+          CK(fft_x_c2r<TA>(h->spec, (TA *)h->epst, n, 6, (TA)(1.0 / (double)N3), dE, h->st, (const TA *)h->epse)); }
+        rc = local(0);
+        if (rc) break;
+        double En = 0.0, mn = 0.0, mu_n = 0.0;
+        for (int i = 0; i < 6; ++i) {
+            const double Ei = h->E[i] + dE[i], mi = hs[2 + i] / (double)N3;
+            En += Ei * Ei;
+            mn += mi * mi;
+            if (i != 2) mu_n += mi * mi;
+        }
+        const double den = std::fmax(std::sqrt(mn), h->p.tau0);
+        ecmp = std::sqrt(hs[0] / (double)N3) / std::fmax(std::sqrt(En), 1e-6);
+        elam = std::sqrt(hs[1] / (double)N3) / den;
+        ebc = std::sqrt(mu_n) / den;
+        if (!std::isfinite(ecmp) || !std::isfinite(elam)) { rc = fail(h, EVP_ERR_NONFINITE, "non-finite AL residual"); break; }
+        if (ecmp <= h->cfg.tol && elam <= h->cfg.tol && ebc <= h->cfg.tol) { conv = 1; break; }
+    }
+    if (it > h->cfg.max_iter) it = h->cfg.max_iter;
+    *it_out = it;
+    *conv_out = conv;
+    *nmax_out = nmax;
+    *err_eq = elam;
+    *err_bc = ebc;
+    for (int i = 0; i < 6; ++i) mean_sig[i] = hs[8 + i] / (double)N3;
+    return rc;
+}
 }  // namespace
 
 extern "C" {
@@ -392,6 +475,25 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
         if (!hS || !hM) { std::free(hS); std::free(hM); return fail(h, EVP_ERR_OOM, "host allocation"); }
         if (h->dbl) build_tables<double>(p, h->G, quat, (double *)hS, (double *)hM);
         else build_tables<float>(p, h->G, quat, (float *)hS, (float *)hM);
+        if (cfg->scheme == EVP_SCHEME_AL) {
+            // S + S0 with S0 the compliance of the AL reference medium (Voigt bulk, shear mu/al_scale)
+            void *hA = std::malloc(36 * G * h->tsz);
+            if (!hA) { std::free(hS); std::free(hM); return fail(h, EVP_ERR_OOM, "host allocation"); }
+            const double mu0 = mu / cfg->al_scale, lam0 = (lam + 2.0 * mu / 3.0) - 2.0 * mu0 / 3.0;
+            const double sa = 1.0 / (2.0 * mu0), sb = lam0 / (2.0 * mu0 * (3.0 * lam0 + 2.0 * mu0));
+            for (size_t gg = 0; gg < G; ++gg)
+                for (int i = 0; i < 6; ++i)
+                    for (int j = 0; j < 6; ++j) {
+                        const double s0 = (i == j ? sa : 0.0) - (i < 3 && j < 3 ? sb : 0.0);
+                        if (h->dbl) ((double *)hA)[36 * gg + 6 * i + j] = ((double *)hS)[36 * gg + 6 * i + j] + s0;
+                        else ((float *)hA)[36 * gg + 6 * i + j] = (float)((double)((float *)hS)[36 * gg + 6 * i + j] + s0);
+                    }
+            cudaError_t ea = cudaMemcpyAsync(h->Sal, hA, 36 * G * h->tsz, cudaMemcpyHostToDevice, h->st);
+            cudaError_t eb = cudaStreamSynchronize(h->st);
+            std::free(hA);
+            CK(ea);
+            CK(eb);
+        }
         cudaError_t e1 = cudaMemcpyAsync(h->Stab, hS, 36 * G * h->tsz, cudaMemcpyHostToDevice, h->st);
         cudaError_t e2 = cudaMemcpyAsync(h->Mtab, hM, 72 * G * h->tsz, cudaMemcpyHostToDevice, h->st);
         cudaError_t e3 = cudaStreamSynchronize(h->st);
@@ -507,6 +609,11 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
     int32_t hf[2];
     int64_t hcount[3] = {0, 0, 0};
     const int reuse = h->cfg.newton_mode == EVP_NEWTON_REUSE;
+    if (h->cfg.scheme == EVP_SCHEME_AL) {
+        status = h->dbl ? al_loop<double>(h, mc, dE, &it, &conv, &nmax, &err_eq, &err_bc, mean)
+                        : al_loop<float>(h, mc, dE, &it, &conv, &nmax, &err_eq, &err_bc, mean);
+        it = it < 1 ? 1 : it;
+    } else
     for (it = 1; it <= h->cfg.max_iter; ++it) {
         if (h->dbl) {
           { PROF(0, 1);

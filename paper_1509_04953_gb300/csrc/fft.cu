@@ -143,12 +143,20 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
     }
 }
 
-// Twiddles exp(-2 pi i m/N), m < N, computed once per CTA into shared memory.
-template <typename C> __device__ void load_tw(C *tw_s, int N) {
+// Twiddles exp(-2 pi i m/N), m < N, computed once per CTA into shared memory, in the precision of
+// the transform (the FP64 pipe is 1/58 of the FP32 rate on this GPU, so FP32 transforms avoid it).
+__device__ __forceinline__ void load_tw(float2 *tw_s, int N) {
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        float sn, cs;
+        sincospif(-2.0f * (float)k / (float)N, &sn, &cs);
+        tw_s[k] = make_float2(cs, sn);
+    }
+}
+__device__ __forceinline__ void load_tw(double2 *tw_s, int N) {
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         double sn, cs;
         sincospi(-2.0 * (double)k / (double)N, &sn, &cs);
-        tw_s[k] = cmk<C>((decltype(C::x))cs, (decltype(C::x))sn);
+        tw_s[k] = make_double2(cs, sn);
     }
 }
 
@@ -198,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
                                                        long npairs, T scale, int has_add, double a0, double a1, double a2,
-                                                       double a3, double a4, double a5) {
+                                                       double a3, double a4, double a5, const T *__restrict__ base) {
     using C = typename CT<T>::type;
     constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -230,8 +238,10 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
         if (has_add) {
             const int f = (int)(row0 / rows_per_field);
             const double add = f == 0 ? a0 : f == 1 ? a1 : f == 2 ? a2 : f == 3 ? a3 : f == 4 ? a4 : a5;
-            out[row0 * N + j] += z.x * scale + (T)add;
-            out[(row0 + 1) * N + j] += z.y * scale + (T)add;
+            const T b0 = base ? base[row0 * N + j] : out[row0 * N + j];
+            const T b1 = base ? base[(row0 + 1) * N + j] : out[(row0 + 1) * N + j];
+            out[row0 * N + j] = b0 + (z.x * scale + (T)add);
+            out[(row0 + 1) * N + j] = b1 + (z.y * scale + (T)add);
         } else {
             out[row0 * N + j] = z.x;
             out[(row0 + 1) * N + j] = z.y;
@@ -422,7 +432,7 @@ template <typename T, int N> cudaError_t x_r2c_n(const T *in, void *spec, int nf
 }
 
 template <typename T, int N>
-cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double *add6, cudaStream_t s) {
+cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double *add6, cudaStream_t s, const T *base) {
     using C = typename CT<T>::type;
     const long npairs = (long)nfields * N * N / 2;
     const int blocks = (int)((npairs + rowpairs<N>() - 1) / rowpairs<N>());
@@ -433,7 +443,7 @@ cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double
     if (add6)
         for (int i = 0; i < 6; ++i) a[i] = add6[i];
     k_fft_x_c2r<T, N><<<blocks, kThreads, sm, s>>>((const C *)spec, out, npairs, scale, add6 != nullptr, a[0], a[1],
-                                                   a[2], a[3], a[4], a[5]);
+                                                   a[2], a[3], a[4], a[5], base);
     return cudaGetLastError();
 }
 
@@ -487,8 +497,9 @@ template <typename T> cudaError_t fft_x_r2c(const T *in, void *spec, int n, int 
 }
 
 template <typename T>
-cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6, cudaStream_t s) {
-    EVP_DISPATCH(n, (x_c2r_n<T, NN>(spec, out, nfields, scale, add6, s)))
+cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6, cudaStream_t s,
+                      const T *base) {
+    EVP_DISPATCH(n, (x_c2r_n<T, NN>(spec, out, nfields, scale, add6, s, base)))
 }
 
 template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s) {
@@ -504,8 +515,10 @@ cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double 
 
 template cudaError_t fft_x_r2c<float>(const float *, void *, int, int, cudaStream_t);
 template cudaError_t fft_x_r2c<double>(const double *, void *, int, int, cudaStream_t);
-template cudaError_t fft_x_c2r<float>(const void *, float *, int, int, float, const double *, cudaStream_t);
-template cudaError_t fft_x_c2r<double>(const void *, double *, int, int, double, const double *, cudaStream_t);
+template cudaError_t fft_x_c2r<float>(const void *, float *, int, int, float, const double *, cudaStream_t,
+                                      const float *);
+template cudaError_t fft_x_c2r<double>(const void *, double *, int, int, double, const double *, cudaStream_t,
+                                       const double *);
 template cudaError_t fft_y<float>(void *, int, int, int, cudaStream_t);
 template cudaError_t fft_y<double>(void *, int, int, int, cudaStream_t);
 template cudaError_t fft_z<float>(void *, int, int, int, double, double, double *, double *, cudaStream_t);

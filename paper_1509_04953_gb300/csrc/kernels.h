@@ -19,10 +19,11 @@ template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inve
 template <typename T>
 cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials,
                   double *mean6, cudaStream_t s);
-// x-pass complex-to-real. If add != nullptr: out[c] += scale * field + add[c]; else out = field.
+// x-pass complex-to-real. If add != nullptr: out[c] = (base ? base[c] : out[c]) + scale * field + add[c];
+// else out = field.
 template <typename T>
 cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6,
-                      cudaStream_t s);
+                      cudaStream_t s, const T *base = nullptr);
 int fft_z_blocks(int n, int is_double);
 
 // ---- newton.cu ----
@@ -36,6 +37,12 @@ template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, cudaStream_t s);
+// Augmented-Lagrangian local step; part: 14 doubles per block (al_blocks blocks).
+int al_blocks(long N3);
+template <typename TA>
+cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
+                     const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
+                     int maxit, int solve_fp64, int init, int *flags, double *part, cudaStream_t s);
 template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s);

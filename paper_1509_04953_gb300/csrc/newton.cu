@@ -242,6 +242,111 @@ __global__ void __launch_bounds__(kThreads) k_newton_chord(long N3, const TA *__
     }
 }
 
+// Augmented-Lagrangian local step (the solver the paper names, Sec. 2.1, after Michel et al.):
+// with C0 the reference stiffness and S0 = C0^-1, per voxel
+//   eps_tr' = S0 lam + eps_tr              (trial strain of the local problem)
+//   solve (S + S0) sigma + dt sum m gdot(sigma) = eps_tr'     -> sigma   (Sal = S + S0 per grain)
+//   e_tr = eps_tr' - S0 sigma              (local strain, minus eps_p^t)
+//   lam  = lam + C0 (eps_tr - e_tr)
+//   p    = lam - C0 (e_tr - eps_e^t)       (minus the polarisation; the z pass returns -Gamma0 p)
+// init = 1 is the start of an increment: sigma from the plain implicit update at eps_tr (S instead of
+// Sal, no lam term), then lam = sigma and e_tr = eps_tr. Partial sums per block: |eps_tr - e_tr|^2,
+// |C0 (eps_tr - e_tr)|^2, the six components of lam and the six of sigma.
+__device__ __forceinline__ double iso_apply_c0(double lam0, double mu0, const double x[6], int i) {
+    const double tr = x[0] + x[1] + x[2];
+    return 2.0 * mu0 * x[i] + (i < 3 ? lam0 * tr : 0.0);
+}
+
+template <typename TA, typename TS>
+__global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__restrict__ epst, const TA *__restrict__ epse,
+                                                      const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
+                                                      TA *__restrict__ sig, TA *__restrict__ lam, TA *__restrict__ pout,
+                                                      const TA *__restrict__ Stab, const TA *__restrict__ Sal,
+                                                      const TA *__restrict__ Mtab, MatConst mc, double lam0, double mu0,
+                                                      TA tol, int maxit, TA ls_free, int init, int *__restrict__ flags,
+                                                      double *__restrict__ part) {
+    __shared__ double red[32];
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = v < N3;
+    int r = 1, nev = 0;
+    double pc = 0.0, pl = 0.0, pm[6] = {0, 0, 0, 0, 0, 0}, ps[6] = {0, 0, 0, 0, 0, 0};
+    if (valid) {
+        const int g = g0[v];
+        TA Sp[21];
+        const TA *S = (init ? Stab : Sal) + 36 * (long)g;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) Sp[pk(i, j)] = __ldg(S + 6 * i + j);
+        // isotropic S0 = (1/2mu0)(I - lam0/(3 lam0 + 2 mu0) J)
+        const double sa = 1.0 / (2.0 * mu0), sb = lam0 / (2.0 * mu0 * (3.0 * lam0 + 2.0 * mu0));
+        double et[6], lm[6], ee[6];
+        TA etr[6], sg[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            et[c] = (double)epst[c * N3 + v];
+            lm[c] = init ? 0.0 : (double)lam[c * N3 + v];
+            ee[c] = (double)epse[c * N3 + v];
+            sg[c] = sig[c * N3 + v];
+        }
+        const double ltr = lm[0] + lm[1] + lm[2];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) etr[c] = (TA)(et[c] + sa * lm[c] - (c < 3 ? sb * ltr : 0.0));
+        r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
+        double s6[6], etr_l[6], d[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            s6[c] = (double)sg[c];
+            sig[c * N3 + v] = sg[c];
+        }
+        const double str = s6[0] + s6[1] + s6[2];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            etr_l[c] = init ? et[c] : (double)etr[c] - (sa * s6[c] - (c < 3 ? sb * str : 0.0));
+            d[c] = et[c] - etr_l[c];
+        }
+        double dl[6], nl[6], de[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) de[c] = etr_l[c] - ee[c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            dl[c] = iso_apply_c0(lam0, mu0, d, c);
+            nl[c] = init ? s6[c] : lm[c] + dl[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            lam[c * N3 + v] = (TA)nl[c];
+            pout[c * N3 + v] = (TA)(nl[c] - iso_apply_c0(lam0, mu0, de, c));
+            pc += d[c] * d[c];
+            pl += dl[c] * dl[c];
+            pm[c] = nl[c];
+            ps[c] = s6[c];
+        }
+    }
+    // flags as in k_newton
+    __syncwarp();
+    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
+    int mx = valid ? (r < 0 ? -r : r) : 0;
+    int sit = valid ? mx : 0, sev = nev;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sit += __shfl_xor_sync(0xffffffffu, sit, o);
+        sev += __shfl_xor_sync(0xffffffffu, sev, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fmask) atomicAdd(flags, __popc(fmask));
+        atomicMax(flags + 1, mx);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
+    }
+    double sums[14] = {pc, pl, pm[0], pm[1], pm[2], pm[3], pm[4], pm[5], ps[0], ps[1], ps[2], ps[3], ps[4], ps[5]};
+#pragma unroll
+    for (int q = 0; q < 14; ++q) {
+        const double t = block_sum(sums[q], red);
+        if (threadIdx.x == 0) part[14 * blockIdx.x + q] = t;
+    }
+}
+
 // Start of an increment: tau_c from the densities at t (frozen over the increment) and the
 // predictor eps_tr = eps_e^t + (r * deps_prev  |  dE).
 template <typename TA>
@@ -361,6 +466,22 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
     return cudaGetLastError();
 }
 
+int al_blocks(long N3) { return (int)((N3 + kThreads - 1) / kThreads); }
+
+template <typename TA>
+cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
+                     const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
+                     int maxit, int solve_fp64, int init, int *flags, double *part, cudaStream_t s) {
+    const int blocks = al_blocks(N3);
+    if (solve_fp64)
+        k_al_local<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc,
+                                                           lam0, mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part);
+    else
+        k_al_local<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc, lam0,
+                                                       mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part);
+    return cudaGetLastError();
+}
+
 template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s) {
@@ -390,6 +511,9 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
     template cudaError_t newton_chord_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,  \
                                                 const TA *, void *, MatConst, double, int, int, int, int *,       \
                                                 cudaStream_t);                                                    \
+    template cudaError_t al_local<TA>(long, const TA *, const TA *, const TA *, const int32_t *, TA *, TA *, TA *, \
+                                      const TA *, const TA *, const TA *, MatConst, double, double, double, int, int, \
+                                      int, int *, double *, cudaStream_t);                                        \
     template cudaError_t predictor<TA>(long, const TA *, const TA *, const TA *, TA *, TA *, MatConst, double,    \
                                        const double *, int, cudaStream_t);                                        \
     template cudaError_t state_update<TA>(long, const TA *, const TA *, const int32_t *, const TA *, TA *, TA *,  \

@@ -37,7 +37,7 @@ class Config(C.Structure):
     _fields_ = [("n", C.c_int), ("grains", C.c_int), ("kmax", C.c_int), ("precision", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("allow_unconverged", C.c_int),
                 ("newton_tol", C.c_double), ("newton_max", C.c_int), ("predictor", C.c_int), ("max_ids", C.c_int),
-                ("newton_mode", C.c_int)]
+                ("newton_mode", C.c_int), ("scheme", C.c_int), ("al_scale", C.c_double)]
 
 
 class Params(C.Structure):
@@ -116,10 +116,12 @@ def _torch():
 
 
 NEWTON_MODES = {"exact": 0, "reuse": 1}
+SCHEMES = {"basic": 0, "al": 1}
 
 
 def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, allow_unconverged=0,
-                newton_tol=None, newton_max=50, predictor=1, max_ids=0, newton=None) -> Config:
+                newton_tol=None, newton_max=50, predictor=1, max_ids=0, newton=None, scheme="basic",
+                al_scale=6.0) -> Config:
     if newton_tol is None:
         newton_tol = 1e-12 if precision == "fp64" else 1e-5
     if newton is None:
@@ -127,7 +129,7 @@ def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, a
         # with an all-FP64 or all-FP32 local problem the exact Newton is faster on GB300
         newton = "reuse" if precision == "mixed" else "exact"
     return Config(n, grains, kmax, PRECISION[precision], tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                  predictor, max_ids, NEWTON_MODES[newton])
+                  predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale)
 
 
 def make_params(mat) -> Params:

@@ -105,6 +105,44 @@ def test_fixed_iterations_match_oracle_fp64(ev, mat, newton):
         assert rel(gpu.get("k")[0], ref.field("k")[0]) < FP64_TOL
 
 
+def test_augmented_lagrangian_fixed_iterations_match_oracle_fp64(ev, mat):
+    """The augmented-Lagrangian iteration on the GPU follows the oracle's iterate for iterate."""
+    n, G, seed = 16, 8, synth.BASE_SEED
+    kw = dict(tol=0.0, max_iter=8, allow_unconverged=1, scheme=1, al_scale=6.0)
+    seeds = synth.voronoi_seeds(n, G, seed)
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, seeds)
+    gpu = ev.Solver(n, G, g0, quat, mat, seed, precision="fp64", tol=0.0, max_iter=8, allow_unconverged=1,
+                    scheme="al", al_scale=6.0)
+    ref = O.State(n, G, g0, quat, mat, seed=seed, **kw)
+    for inc in range(2):
+        rc, st = gpu.increment(-1e-3, 1.0)
+        rco, sto = ref.increment(-1e-3, 1.0)
+        assert rc == 1 and rco == 1 and st.iterations == sto.iterations == 8
+        assert rel(st.sig_mean, sto.sig_mean) < FP64_TOL
+        assert rel(st.E, sto.E) < FP64_TOL
+        assert abs(st.err_eq / sto.err_eq - 1) < 1e-8
+        for f in ("sig", "eps", "epsp", "deps", "rho"):
+            assert rel(gpu.get(f), ref.field(f if f != "deps" else "deps_prev")) < FP64_TOL, f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_augmented_lagrangian_converges_to_the_basic_solution(ev, mat, precision):
+    n, G, seed = 32, 27, synth.BASE_SEED + 3
+    seeds = synth.voronoi_seeds(n, G, seed)
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, seeds)
+    tol = 1e-9 if precision == "fp64" else 1e-6
+    a = ev.Solver(n, G, g0, quat, mat, seed, precision=precision, tol=tol, max_iter=6000)
+    b = ev.Solver(n, G, g0, quat, mat, seed, precision=precision, tol=tol, max_iter=6000, scheme="al")
+    for inc in range(4):
+        _, sa = a.increment(-1e-3, 1.0)
+        _, sb = b.increment(-1e-3, 1.0)
+        assert sb.iterations < sa.iterations / 2
+        assert abs(sb.sig_mean[2] / sa.sig_mean[2] - 1) < (1e-7 if precision == "fp64" else 1e-4)
+    assert rel(b.get("sig"), a.get("sig")) < (1e-6 if precision == "fp64" else 1e-3)
+
+
 def test_converged_increments_match_oracle_fp64(ev, mat):
     n, G, seed = 16, 8, synth.BASE_SEED
     kw = dict(tol=1e-9, max_iter=3000)

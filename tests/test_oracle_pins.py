@@ -461,3 +461,36 @@ def test_oracle_adjoint_gradient_matches_central_differences(mat):
                          want_grad=False)[1]
         fd = (Lp - Lm) / (2 * h)
         assert abs(g[i] / fd - 1) < 1e-5, (k, g[i], fd)
+
+
+# ------------------------------------------------------------------------------------------
+# augmented Lagrangian (the solver the paper names, Sec. 2.1): same fixed point as the basic scheme
+# ------------------------------------------------------------------------------------------
+def test_augmented_lagrangian_reaches_the_basic_scheme_solution(mat):
+    n, G = 8, 5
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, 12))
+    q = synth.orientations(G, 12)
+    a = O.State(n, G, g0, q, mat, seed=1, tol=1e-11, max_iter=20000, scheme=0)
+    b = O.State(n, G, g0, q, mat, seed=1, tol=1e-11, max_iter=20000, scheme=1, al_scale=6.0)
+    for _ in range(3):
+        ra, sa = a.increment(-1e-3, 1.0)
+        rb, sb = b.increment(-1e-3, 1.0)
+        assert ra == 0 and rb == 0
+        assert sb.iterations < sa.iterations
+        assert abs(sb.sig_mean[2] / sa.sig_mean[2] - 1) < 1e-9
+    sig_a, sig_b = a.field("sig"), b.field("sig")
+    assert np.abs(sig_a - sig_b).max() < 1e-7 * np.abs(sig_a).max()
+    assert np.abs(a.field("rho") - b.field("rho")).max() < 1e-7 * a.field("rho").max()
+
+
+def test_augmented_lagrangian_homogeneous_crystal_matches_point_model(mat):
+    n = 4
+    q = synth.orientations(1, 21)
+    st = O.State(n, 1, np.zeros(n ** 3, dtype=np.int32), q, mat, seed=1, tol=1e-12, max_iter=20000, scheme=1,
+                 al_scale=6.0)
+    _, S, M = O.grain_tables(mat, q)
+    _, hist, _ = O.point_model(mat, S[0], M[0], -1e-3, 1.0, 3)
+    for inc in range(3):
+        rc, s = st.increment(-1e-3, 1.0)
+        assert rc == 0
+        assert abs(s.sig_mean[2] / hist[inc] - 1) < 1e-9
