@@ -70,6 +70,8 @@ typedef struct {
 #define EVP_SCHEME_AL 1
 #define EVP_NEWTON_EXACT 0
 #define EVP_NEWTON_REUSE 1
+#define EVP_NEWTON_F32_TANGENT 2  /* EVP_FP64 only: FP64 residual, FP32 tangent and 6x6 solve (the tangent
+                                     only steers the iteration; the result is fixed by the FP64 residual) */
 
 typedef struct {
     double C11, C12, C44;        /* cubic elastic constants, MPa */

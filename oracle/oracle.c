@@ -789,7 +789,8 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
         free(Sal); free(tauc); free(e); free(lam);
         return status;
     }
-    /* state update with the converged stress; the total strain is the local strain e */
+    /* state update with the converged stress; the stored total strain is the compatible field eps
+     * of the last compatibility step (equal to the local strain e to the tolerance) */
 #pragma omp parallel for schedule(static)
     for (long v = 0; v < N3; ++v) {
         int gr = s->g0[v];
@@ -812,8 +813,8 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
         for (int a = 0; a < 12; ++a) { s->rho[a * N3 + v] = rho[a]; kk += rho[a]; }
         s->k[v] = kk;
         for (int I = 0; I < 6; ++I) {
-            s->deps_prev[I * N3 + v] = e[I * N3 + v] - s->eps[I * N3 + v];
-            s->eps[I * N3 + v] = e[I * N3 + v];
+            s->deps_prev[I * N3 + v] = eps[I * N3 + v] - s->eps[I * N3 + v];
+            s->eps[I * N3 + v] = eps[I * N3 + v];
             s->sig[I * N3 + v] = sig[I * N3 + v];
         }
     }

@@ -26,6 +26,7 @@ struct evp_handle {
     size_t ws_bytes;
     // fields
     void *sig, *sigk, *epse, *epst, *epsp, *deps, *rho, *tauc, *eta, *eta2, *spec, *Stab, *Mtab, *fac, *Sal, *lam, *pal;
+    float *Stabf, *Mtabf;
     double *k, *kappa, *partials, *scal;
     int32_t *g0, *g, *gprev, *draws, *ids, *ids2, *flags, *blk_counts, *blk_off, *count;
     uint32_t *bitmap;
@@ -148,8 +149,10 @@ int check_cfg(const evp_config *c, char *why, size_t wl) {
         return snprintf(why, wl, "unknown scheme %d", c->scheme), EVP_ERR_ARG;
     if (c->scheme == EVP_SCHEME_AL && !(c->al_scale >= 1.0))
         return snprintf(why, wl, "al_scale must be >= 1"), EVP_ERR_ARG;
-    if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE)
-        return snprintf(why, wl, "unknown newton_mode %d", c->newton_mode), EVP_ERR_ARG;
+    if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE &&
+        !(c->newton_mode == EVP_NEWTON_F32_TANGENT && c->precision == EVP_FP64))
+        return snprintf(why, wl, "newton_mode %d is not available for precision %d", c->newton_mode, c->precision),
+               EVP_ERR_ARG;
     return EVP_OK;
 }
 
@@ -176,6 +179,8 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? 21 * N3 * TSf : 0);
     const bool al = c->scheme == EVP_SCHEME_AL;
     char *Sal = take(al ? 36 * (size_t)G * T : 0), *lam = take(al ? 6 * N3 * T : 0), *pal = take(al ? 6 * N3 * T : 0);
+    const bool f32t = c->newton_mode == EVP_NEWTON_F32_TANGENT;
+    char *Stabf = take(f32t ? 36 * (size_t)G * 4 : 0), *Mtabf = take(f32t ? 72 * (size_t)G * 4 : 0);
     char *k = take(N3 * 8), *kappa = take(N3 * 8);
     char *g0 = take(N3 * 4), *g = take(N3 * 4), *gprev = take(N3 * 4), *draws = take(N3 * 4);
     char *ids = take(K * N3 * 4), *ids2 = take(K * N3 * 4);
@@ -190,6 +195,8 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
         h->sig = sig; h->sigk = sigk; h->epse = epse; h->epst = epst; h->epsp = epsp; h->deps = deps;
         h->rho = rho; h->tauc = tauc; h->eta = eta; h->eta2 = eta2; h->spec = spec; h->Stab = Stab; h->Mtab = Mtab;
         h->fac = fac;
+        h->Stabf = (float *)Stabf;
+        h->Mtabf = (float *)Mtabf;
         h->Sal = Sal;
         h->lam = lam;
         h->pal = pal;
@@ -340,12 +347,13 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
     int32_t hf[2];
     int nmax = 0, conv = 0, it;
     double ecmp = 0, elam = 0, ebc = 0;
-    auto local = [&](int init) -> int {
+    void *fac = h->cfg.newton_mode == EVP_NEWTON_REUSE ? h->fac : nullptr;
+    auto local = [&](int init, int refresh) -> int {
         { PROF(0, 1);
           CK(al_local<TA>(N3, (const TA *)h->epst, (const TA *)h->epse, (const TA *)h->tauc, h->g0, (TA *)h->sigk,
                           (TA *)h->lam, (TA *)h->pal, (const TA *)h->Stab, (const TA *)h->Sal, (const TA *)h->Mtab, mc,
-                          lam0, mu0, h->cfg.newton_tol, h->cfg.newton_max, solve64, init, h->flags, h->partials,
-                          h->st)); }
+                          lam0, mu0, h->cfg.newton_tol, h->cfg.newton_max, solve64, init, h->flags, h->partials, fac,
+                          refresh, h->st)); }
         { PROF(6, 1); CK(reduce_partials(h->partials, nb, 14, h->scal + 24, h->st)); }
         CK(cudaMemcpyAsync(hs, h->scal + 24, sizeof hs, cudaMemcpyDeviceToHost, h->st));
         CK(cudaMemcpyAsync(hf, h->flags, sizeof hf, cudaMemcpyDeviceToHost, h->st));
@@ -355,7 +363,7 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
         if (hf[0] != 0) return fail(h, EVP_ERR_NEWTON, "local Newton failed in %d voxels", hf[0]);
         return EVP_OK;
     };
-    int rc = local(1);
+    int rc = local(1, 1);
     if (rc) { *it_out = 0; *nmax_out = nmax; return rc; }
     for (it = 1; it <= h->cfg.max_iter; ++it) {
         // macroscopic strain on the stress-controlled components from <lam>
@@ -372,7 +380,7 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
         { PROF(4, 1); CK(fft_y<TA>(h->spec, n, 6, 1, h->st)); }
         { PROF(5, 1);
           CK(fft_x_c2r<TA>(h->spec, (TA *)h->epst, n, 6, (TA)(1.0 / (double)N3), dE, h->st, (const TA *)h->epse)); }
-        rc = local(0);
+        rc = local(0, it == 1);
         if (rc) break;
         double En = 0.0, mn = 0.0, mu_n = 0.0;
         for (int i = 0; i < 6; ++i) {
@@ -493,6 +501,20 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
             std::free(hA);
             CK(ea);
             CK(eb);
+        }
+        if (cfg->newton_mode == EVP_NEWTON_F32_TANGENT) {
+            float *fS = (float *)std::malloc(36 * G * 4), *fM = (float *)std::malloc(72 * G * 4);
+            if (!fS || !fM) { std::free(fS); std::free(fM); std::free(hS); std::free(hM); return fail(h, EVP_ERR_OOM, "host allocation"); }
+            for (size_t i = 0; i < 36 * G; ++i) fS[i] = (float)((double *)hS)[i];
+            for (size_t i = 0; i < 72 * G; ++i) fM[i] = (float)((double *)hM)[i];
+            cudaError_t ea = cudaMemcpyAsync(h->Stabf, fS, 36 * G * 4, cudaMemcpyHostToDevice, h->st);
+            cudaError_t eb = cudaMemcpyAsync(h->Mtabf, fM, 72 * G * 4, cudaMemcpyHostToDevice, h->st);
+            cudaError_t ec = cudaStreamSynchronize(h->st);
+            std::free(fS);
+            std::free(fM);
+            CK(ea);
+            CK(eb);
+            CK(ec);
         }
         cudaError_t e1 = cudaMemcpyAsync(h->Stab, hS, 36 * G * h->tsz, cudaMemcpyHostToDevice, h->st);
         cudaError_t e2 = cudaMemcpyAsync(h->Mtab, hM, 72 * G * h->tsz, cudaMemcpyHostToDevice, h->st);
@@ -617,7 +639,11 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
     for (it = 1; it <= h->cfg.max_iter; ++it) {
         if (h->dbl) {
           { PROF(0, 1);
-            if (reuse)
+            if (h->cfg.newton_mode == EVP_NEWTON_F32_TANGENT)
+                CK(newton_field_df(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
+                                   (double *)h->Stab, (double *)h->Mtab, h->Stabf, h->Mtabf, mc, ntol,
+                                   h->cfg.newton_max, h->flags, h->st));
+            else if (reuse)
                 CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                               (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
                                               h->cfg.newton_max, 1, it == 1, h->flags, h->st));

@@ -37,12 +37,17 @@ template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, cudaStream_t s);
+// FP64 residual / FP32 tangent Newton (FP64 path); Stabf / Mtabf are FP32 copies of the tables.
+cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
+                            const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,
+                            MatConst mc, double tol, int maxit, int *flags, cudaStream_t s);
 // Augmented-Lagrangian local step; part: 14 doubles per block (al_blocks blocks).
 int al_blocks(long N3);
 template <typename TA>
 cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
                      const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
-                     int maxit, int solve_fp64, int init, int *flags, double *part, cudaStream_t s);
+                     int maxit, int solve_fp64, int init, int *flags, double *part, void *fac, int refresh,
+                     cudaStream_t s);
 template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s);

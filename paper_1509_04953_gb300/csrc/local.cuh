@@ -234,4 +234,59 @@ template <typename TS, typename TA> __device__ __forceinline__ void ldl_apply(co
     for (int i = 0; i < 6; ++i) dout[i] = (TA)y[i];
 }
 
+// FP64 residual and potential with the tangent assembled in FP32 (the tangent only steers the
+// iteration; the converged stress is fixed by the FP64 residual). Sf / Mf are FP32 copies of the
+// per-grain compliance and Schmid tables.
+struct EvalDF {
+    double r[6];
+    float K[21];
+    double phi;
+};
+__device__ __forceinline__ void evaluate_df(const double Sp[21], const double *__restrict__ M, const float Spf[21],
+                                            const float *__restrict__ Mf, const double etr[6], double tauc,
+                                            double inv_tc, const double sg[6], const MatConst &mc, EvalDF &e) {
+    const double dt = mc.dt, g0 = mc.gdot0, nn = mc.n;
+    double phi = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += Sp[i >= j ? pk(i, j) : pk(j, i)] * sg[j];
+        e.r[i] = acc - etr[i];
+        phi += sg[i] * (0.5 * acc - etr[i]);
+    }
+#pragma unroll
+    for (int q = 0; q < 21; ++q) e.K[q] = Spf[q];
+    const double cphi = dt * g0 * tauc / (nn + 1.0);
+    const float cslope = (float)(dt * nn * g0 * inv_tc);
+#pragma unroll 1
+    for (int a = 0; a < 12; ++a) {
+        double m[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) m[i] = __ldg(M + 6 * a + i);
+        double tau = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
+        const double x = tau * inv_tc, ax = fabs(x);
+        const double p9 = pow_nm1(ax, mc);
+        const double p10 = p9 * ax;
+        const double dg = x < 0.0 ? -dt * g0 * p10 : dt * g0 * p10;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) e.r[i] += dg * m[i];
+        phi += cphi * p10 * ax;
+        const float slope = cslope * (float)p9;
+        float mf[6], sm[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            mf[i] = __ldg(Mf + 6 * a + i);
+            sm[i] = slope * mf[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) e.K[pk(i, j)] += sm[i] * mf[j];
+    }
+    e.phi = phi;
+}
+
 }  // namespace evp

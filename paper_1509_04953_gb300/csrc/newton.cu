@@ -114,6 +114,109 @@ __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restri
     }
 }
 
+// FP64 path: Newton on the FP64 residual with an FP32 tangent and FP32 6x6 solve. Each step is a
+// slightly inexact Newton step (relative tangent error ~1e-7), so the iteration contracts at least
+// ~1e-6 per step near the solution and stops on the same step-size test; Armijo backtracking on
+// the FP64 potential keeps it globally convergent.
+__device__ int newton_voxel_df(const double Sp[21], const double *__restrict__ M, const float Spf[21],
+                               const float *__restrict__ Mf, const double etr[6], double tauc, double sg[6],
+                               const MatConst &mc, double tol, int maxit, double ls_free, int &nevals) {
+    const double inv_tc = drcp(tauc);
+    EvalDF e;
+    evaluate_df(Sp, M, Spf, Mf, etr, tauc, inv_tc, sg, mc, e);
+    nevals = 1;
+    for (int it = 1; it <= maxit; ++it) {
+        float rf[6], df[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) rf[i] = (float)e.r[i];
+        if (!ldl_solve<float, float>(e.K, rf, df)) return -it;
+        double d[6], rd = 0.0, dn = 0.0, sn = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            d[i] = (double)df[i];
+            rd += e.r[i] * d[i];
+            dn += d[i] * d[i];
+            sn += sg[i] * sg[i];
+        }
+        dn = dsqrt(dn);
+        const double scale = dsqrt(sn) + tauc;
+        if (dn <= tol * scale && rd >= 0.0) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) sg[i] -= d[i];
+            return it;
+        }
+        const double phi0 = e.phi;
+        double s = 1.0, st[6];
+        bool ok = false;
+        for (int h = 0; h < 60; ++h) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) st[i] = sg[i] - s * d[i];
+            evaluate_df(Sp, M, Spf, Mf, etr, tauc, inv_tc, st, mc, e);
+            ++nevals;
+            if (e.phi <= phi0 - 1e-4 * s * rd || s * dn <= ls_free * scale) {
+                ok = true;
+                break;
+            }
+            s *= 0.5;
+        }
+        if (!ok) return -it;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sg[i] = st[i];
+        if (s * dn <= tol * scale) return it;
+    }
+    return -maxit;
+}
+
+__global__ void __launch_bounds__(kThreads) k_newton_df(long N3, const double *__restrict__ epst,
+                                                       const double *__restrict__ tauc, const int32_t *__restrict__ g0,
+                                                       double *__restrict__ sig, const double *__restrict__ Stab,
+                                                       const double *__restrict__ Mtab, const float *__restrict__ Stabf,
+                                                       const float *__restrict__ Mtabf, MatConst mc, double tol,
+                                                       int maxit, int *__restrict__ flags) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = v < N3;
+    int r = 1, nev = 0;
+    if (valid) {
+        const int g = g0[v];
+        double Sp[21];
+        float Spf[21];
+        const double *S = Stab + 36 * (long)g;
+        const float *Sf = Stabf + 36 * (long)g;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                Sp[pk(i, j)] = __ldg(S + 6 * i + j);
+                Spf[pk(i, j)] = __ldg(Sf + 6 * i + j);
+            }
+        double etr[6], sg[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            etr[c] = epst[c * N3 + v];
+            sg[c] = sig[c * N3 + v];
+        }
+        r = newton_voxel_df(Sp, Mtab + 72 * (long)g, Spf, Mtabf + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit,
+                            1e-6, nev);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
+    }
+    __syncwarp();
+    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
+    int mx = valid ? (r < 0 ? -r : r) : 0;
+    int sit = valid ? mx : 0, sev = nev;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sit += __shfl_xor_sync(0xffffffffu, sit, o);
+        sev += __shfl_xor_sync(0xffffffffu, sev, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fmask) atomicAdd(flags, __popc(fmask));
+        atomicMax(flags + 1, mx);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
+    }
+}
+
 // Local solve with Jacobian reuse (chord Newton): the LDL^T factors of the tangent are stored per
 // voxel and reused across fixed-point iterations; a step costs one residual evaluation and two
 // triangular solves. The factors are refreshed (full tangent + factorisation at the current point)
@@ -264,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
                                                       const TA *__restrict__ Stab, const TA *__restrict__ Sal,
                                                       const TA *__restrict__ Mtab, MatConst mc, double lam0, double mu0,
                                                       TA tol, int maxit, TA ls_free, int init, int *__restrict__ flags,
-                                                      double *__restrict__ part) {
+                                                      double *__restrict__ part, TS *__restrict__ fac, int refresh) {
     __shared__ double red[32];
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
@@ -292,7 +395,22 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
         const double ltr = lm[0] + lm[1] + lm[2];
 #pragma unroll
         for (int c = 0; c < 6; ++c) etr[c] = (TA)(et[c] + sa * lm[c] - (c < 3 ? sb * ltr : 0.0));
-        r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
+        if (fac) {   // tangent reuse: factors refreshed on request or when a step stalls
+            TS F[21];
+            if (!refresh) {
+#pragma unroll
+                for (int q = 0; q < 21; ++q) F[q] = fac[q * N3 + v];
+            }
+            int nref = 0;
+            r = chord_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
+                                    refresh != 0, nev, nref);
+            if (nref) {
+#pragma unroll
+                for (int q = 0; q < 21; ++q) fac[q * N3 + v] = F[q];
+            }
+        } else {
+            r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
+        }
         double s6[6], etr_l[6], d[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -468,17 +586,28 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
 
 int al_blocks(long N3) { return (int)((N3 + kThreads - 1) / kThreads); }
 
+cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
+                            const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,
+                            MatConst mc, double tol, int maxit, int *flags, cudaStream_t s) {
+    const int blocks = (int)((N3 + kThreads - 1) / kThreads);
+    k_newton_df<<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, Stabf, Mtabf, mc, tol, maxit, flags);
+    return cudaGetLastError();
+}
+
 template <typename TA>
 cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
                      const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
-                     int maxit, int solve_fp64, int init, int *flags, double *part, cudaStream_t s) {
+                     int maxit, int solve_fp64, int init, int *flags, double *part, void *fac, int refresh,
+                     cudaStream_t s) {
     const int blocks = al_blocks(N3);
     if (solve_fp64)
         k_al_local<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc,
-                                                           lam0, mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part);
+                                                           lam0, mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part,
+                                                           (double *)fac, refresh);
     else
         k_al_local<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc, lam0,
-                                                       mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part);
+                                                       mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part,
+                                                       (TA *)fac, refresh);
     return cudaGetLastError();
 }
 
@@ -513,7 +642,7 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
                                                 cudaStream_t);                                                    \
     template cudaError_t al_local<TA>(long, const TA *, const TA *, const TA *, const int32_t *, TA *, TA *, TA *, \
                                       const TA *, const TA *, const TA *, MatConst, double, double, double, int, int, \
-                                      int, int *, double *, cudaStream_t);                                        \
+                                      int, int *, double *, void *, int, cudaStream_t);                           \
     template cudaError_t predictor<TA>(long, const TA *, const TA *, const TA *, TA *, TA *, MatConst, double,    \
                                        const double *, int, cudaStream_t);                                        \
     template cudaError_t state_update<TA>(long, const TA *, const TA *, const int32_t *, const TA *, TA *, TA *,  \

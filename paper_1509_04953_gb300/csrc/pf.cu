@@ -69,13 +69,18 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
     }
     const T Ep = (T)(pc.Escale * kf[v]);
     const T Ssum = D + R;
-    // merge the seven sorted lists
-    int head[7], pos[7];
+    // merge the seven sorted lists; the first two slots of every list are fetched up front
+    // (independent loads), later slots on demand
+    int head[7], pos[7], id1[7];
+    T e0v[7], e1v[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
         pos[q] = 0;
-        const int id = ids[nb.q[q]];
-        head[q] = id < 0 ? kEmpty : id;
+        const int i0 = ids[nb.q[q]];
+        id1[q] = K > 1 ? ids[N3 + nb.q[q]] : -1;
+        e0v[q] = eta[nb.q[q]];
+        e1v[q] = K > 1 ? eta[N3 + nb.q[q]] : (T)0;
+        head[q] = i0 < 0 ? kEmpty : i0;
     }
     int kid[KM + 1];
     T ke[KM + 1];
@@ -97,11 +102,12 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
         for (int q = 0; q < 7; ++q) {
             e[q] = (T)0;
             if (head[q] == c) {
-                e[q] = eta[pos[q] * N3 + nb.q[q]];
-                ++pos[q];
+                const int pq = pos[q];
+                e[q] = pq == 0 ? e0v[q] : pq == 1 ? e1v[q] : eta[pq * N3 + nb.q[q]];
+                pos[q] = pq + 1;
                 int nx = kEmpty;
-                if (pos[q] < K) {
-                    const int id = ids[pos[q] * N3 + nb.q[q]];
+                if (pq + 1 < K) {
+                    const int id = pq == 0 ? id1[q] : ids[(pq + 1) * N3 + nb.q[q]];
                     nx = id < 0 ? kEmpty : id;
                 }
                 head[q] = nx;
@@ -232,16 +238,14 @@ __global__ void k_popc(const uint32_t *__restrict__ bitmap, int words, double *_
     if (threadIdx.x == 0) *out_slot = s;
 }
 
-// Deterministic sum of partials [nparts][nvals] -> out[nvals] (one block, fixed order).
+// Deterministic sum of partials [nparts][nvals] -> out[nvals]: one block per column, fixed order.
 __global__ void k_reduce(const double *__restrict__ part, int nparts, int nvals, double *__restrict__ out) {
     __shared__ double red[32];
-    for (int c = 0; c < nvals; ++c) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[(long)i * nvals + c];
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) out[c] = s;
-        __syncthreads();
-    }
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[(long)i * nvals + c];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[c] = s;
 }
 
 }  // namespace
@@ -278,7 +282,7 @@ cudaError_t pf_stats_launch(int n, const int32_t *ids, const T *eta, const int32
 }
 
 cudaError_t reduce_partials(const double *partials, int nparts, int nvals, double *out, cudaStream_t s) {
-    k_reduce<<<1, 1024, 0, s>>>(partials, nparts, nvals, out);
+    k_reduce<<<nvals, 1024, 0, s>>>(partials, nparts, nvals, out);
     return cudaGetLastError();
 }
 

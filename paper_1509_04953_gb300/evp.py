@@ -115,7 +115,7 @@ def _torch():
     return torch
 
 
-NEWTON_MODES = {"exact": 0, "reuse": 1}
+NEWTON_MODES = {"exact": 0, "reuse": 1, "f32_tangent": 2}
 SCHEMES = {"basic": 0, "al": 1}
 
 

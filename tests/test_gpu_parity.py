@@ -87,7 +87,7 @@ def test_stress_residual_matches_oracle(ev, n, prec):
 # ------------------------------------------------------------------------------------------
 # a2-a7 fixed point and state update
 # ------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("newton", ["exact", "reuse"])
+@pytest.mark.parametrize("newton", ["exact", "reuse", "f32_tangent"])
 def test_fixed_iterations_match_oracle_fp64(ev, mat, newton):
     """Same number of fixed-point iterations on both sides: every field agrees to round-off, with the
     exact local Newton and with tangent reuse (the local problem is solved to the same tolerance)."""
