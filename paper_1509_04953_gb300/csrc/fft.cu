@@ -24,6 +24,16 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Asynchronous global -> shared copies (cp.async): every thread issues all of its loads before
+// waiting, so many requests are in flight per SM while the pass is latency-bound.
+template <int B> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (B == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else if constexpr (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int N> struct Shape {
     static constexpr int R1 = N < 16 ? N : 16;
     static constexpr int R2 = N / R1;
@@ -185,8 +195,11 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in
     for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
         const int pl = t / N, j = t - pl * N;
         const long row0 = 2 * (p0 + pl);            // global row index = (field*N + z)*N + y
-        buf[pl * LS + pad16(j)] = cmk<C>(in[row0 * N + j], in[(row0 + 1) * N + j]);
+        T *slot = reinterpret_cast<T *>(buf + pl * LS + pad16(j));
+        cp_async<sizeof(T)>(slot, in + row0 * N + j);
+        cp_async<sizeof(T)>(slot + 1, in + (row0 + 1) * N + j);
     }
+    cp_async_wait_all();
     __syncthreads();
     block_fft<N, false, maxit<N>(RP)>(buf, np, tw);
     const T h = (T)0.5;
@@ -268,8 +281,10 @@ __global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__rest
     for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
         const int y = t / TX, xl = t - y * TX;
         const int kx = kx0 + xl;
-        buf[xl * LS + pad16(y)] = kx < Hx ? base[(long)y * Hx + kx] : cmk<C>(0, 0);
+        if (kx < Hx) cp_async<sizeof(C)>(buf + xl * LS + pad16(y), base + (long)y * Hx + kx);
+        else buf[xl * LS + pad16(y)] = cmk<C>(0, 0);
     }
+    cp_async_wait_all();
     __syncthreads();
     block_fft<N, INV, maxit<N>(TX)>(buf, TX, tw);
     for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
@@ -373,8 +388,10 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
         const int r = t - f * TX * N;
         const int z = r / TX, xl = r - z * TX;
         const int kx = kx0 + xl;
-        buf[(f * TX + xl) * LS + pad16(z)] = kx < Hx ? spec[f * fstride + z * plane + (long)ky * Hx + kx] : cmk<C>(0, 0);
+        if (kx < Hx) cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx);
+        else buf[(f * TX + xl) * LS + pad16(z)] = cmk<C>(0, 0);
     }
+    cp_async_wait_all();
     __syncthreads();
     if (mode != Z_INV) block_fft<N, false, MI>(buf, nf * TX, tw);
     if (mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) {

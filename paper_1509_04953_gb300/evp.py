@@ -125,9 +125,10 @@ def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, a
     if newton_tol is None:
         newton_tol = 1e-12 if precision == "fp64" else 1e-5
     if newton is None:
-        # tangent reuse pays where the 6x6 solve is FP64 next to an FP32 residual (EVP_MIXED);
-        # with an all-FP64 or all-FP32 local problem the exact Newton is faster on GB300
-        newton = "reuse" if precision == "mixed" else "exact"
+        # measured on GB300 at 128^3: tangent reuse pays where the 6x6 solve is FP64 next to an FP32
+        # residual (EVP_MIXED, 1.5x); the FP64 path runs fastest with an FP32 tangent and solve under
+        # its FP64 residual (1.5x, identical iterates); the all-FP32 path with the exact Newton
+        newton = {"mixed": "reuse", "fp64": "f32_tangent", "mixed_fast": "exact"}[precision]
     return Config(n, grains, kmax, PRECISION[precision], tol, max_iter, allow_unconverged, newton_tol, newton_max,
                   predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale)
 
