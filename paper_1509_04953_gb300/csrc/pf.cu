@@ -69,18 +69,13 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
     }
     const T Ep = (T)(pc.Escale * kf[v]);
     const T Ssum = D + R;
-    // merge the seven sorted lists; the first two slots of every list are fetched up front
-    // (independent loads), later slots on demand
-    int head[7], pos[7], id1[7];
-    T e0v[7], e1v[7];
+    // merge the seven sorted lists
+    int head[7], pos[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
         pos[q] = 0;
-        const int i0 = ids[nb.q[q]];
-        id1[q] = K > 1 ? ids[N3 + nb.q[q]] : -1;
-        e0v[q] = eta[nb.q[q]];
-        e1v[q] = K > 1 ? eta[N3 + nb.q[q]] : (T)0;
-        head[q] = i0 < 0 ? kEmpty : i0;
+        const int id = ids[nb.q[q]];
+        head[q] = id < 0 ? kEmpty : id;
     }
     int kid[KM + 1];
     T ke[KM + 1];
@@ -102,12 +97,11 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
         for (int q = 0; q < 7; ++q) {
             e[q] = (T)0;
             if (head[q] == c) {
-                const int pq = pos[q];
-                e[q] = pq == 0 ? e0v[q] : pq == 1 ? e1v[q] : eta[pq * N3 + nb.q[q]];
-                pos[q] = pq + 1;
+                e[q] = eta[pos[q] * N3 + nb.q[q]];
+                ++pos[q];
                 int nx = kEmpty;
-                if (pq + 1 < K) {
-                    const int id = pq == 0 ? id1[q] : ids[(pq + 1) * N3 + nb.q[q]];
+                if (pos[q] < K) {
+                    const int id = ids[pos[q] * N3 + nb.q[q]];
                     nx = id < 0 ? kEmpty : id;
                 }
                 head[q] = nx;
