@@ -31,10 +31,13 @@ from paper_1509_04953_gb300 import synth  # noqa: E402
 
 METRIC = "FFT-EVP voxel-iters/s + DRX increments/s at 128^3, FP32-mixed vs FP64 at <=1e-4"
 UNIT = "voxel-iterations/s"
-# per-kernel algorithmic bytes per voxel for one launch (FP32 / FP64 field words)
-NEWTON_FLOPS_EVAL = 1140      # FP operations of one residual+tangent+potential evaluation
-NEWTON_FLOPS_FACTOR = 80      # FP operations of one 6x6 LDL^T factorisation
-NEWTON_FLOPS_SOLVE = 72       # FP operations of the two triangular solves of one Newton step
+# algorithmic floating-point operations of the per-voxel local solve
+NEWTON_FLOPS_EVAL = 1140      # one residual + tangent + potential evaluation (12 slip systems)
+NEWTON_FLOPS_RESID = 544      # one residual + potential evaluation without the tangent
+NEWTON_FLOPS_FACTOR = 80      # one 6x6 LDL^T factorisation
+NEWTON_FLOPS_SOLVE = 72       # the two triangular solves of one Newton step
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.25                             # nominal (1.203 measured with an FMA-chain probe)
 
 
 def parse():
@@ -246,7 +249,7 @@ def native(args, ws, rank, local):
                      "solves_per_voxel_iter": solves / (N3 * iters), "evals_per_voxel_iter": evals / (N3 * iters),
                      "factorisations_per_voxel_iter": (n1[2] - n0[2]) / (N3 * iters)}
     res["roofline"] = roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision=args.precision,
-                               facs=n1[2] - n0[2])
+                               facs=n1[2] - n0[2], reuse=mixed.cfg.newton_mode == 1)
     res["memory_bound_kernels"] = memory_kernels(ktimes, wl, N3, args.precision, pk)
     if args.fast_steps > 0:
         res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
@@ -275,27 +278,40 @@ def hbm_bytes_per_voxel(kernel, n, T):
             "pf_step": 2 * 8 * (4 + T) + 8}.get(kernel)
 
 
-def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, facs=0):
+def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, facs=0, reuse=False):
     ms, n = ktimes[dom]
     avg_s = ms / 1e3 / max(n, 1)
     T = 4 if precision != "fp64" else 8
     if dom == "newton":
-        # FP64 pipe: the 6x6 LDL^T solve (about 150 algorithmic flops) in the mixed path; everything
-        # in the FP64 path. FP32 pipe for the fast mixed path. Peaks: FP64 1.25 TFLOP/s (nominal;
-        # 1.203 measured with an FMA-chain probe), FP32 152 SMs x 128 lanes x 2 x 2.07 GHz.
-        lin = NEWTON_FLOPS_FACTOR * facs + NEWTON_FLOPS_SOLVE * solves
-        if precision == "mixed":
-            flops, peak, pipe = lin, 1.25, "fp64"
-        elif precision == "fp64":
-            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + lin, 1.25, "fp64"
+        # Count the algorithmic flops by pipe and report the pipe they bind. Tangent reuse (chord)
+        # does one tangent evaluation and one FP64 factorisation per refresh and residual-only
+        # evaluations otherwise; its stored factors are applied in the field precision. The exact
+        # Newton evaluates the tangent every time and factorises and solves in FP64 on the mixed
+        # path, in FP32 on the fast mixed path.
+        if reuse:
+            ev = NEWTON_FLOPS_RESID * (evals - facs) + NEWTON_FLOPS_EVAL * facs
+            f64 = NEWTON_FLOPS_FACTOR * facs + (NEWTON_FLOPS_SOLVE * solves if precision == "fp64" else 0)
+            f32 = (NEWTON_FLOPS_SOLVE * solves if precision != "fp64" else 0)
         else:
-            flops, peak, pipe = NEWTON_FLOPS_EVAL * evals + lin, 152 * 128 * 2 * 2.070e9 / 1e12, "fp32"
+            ev = NEWTON_FLOPS_EVAL * evals
+            lin = (NEWTON_FLOPS_FACTOR + NEWTON_FLOPS_SOLVE) * solves
+            f64, f32 = (lin, 0) if precision in ("mixed", "fp64") else (0, lin)
+        if precision == "fp64":
+            f64 += ev
+        else:
+            f32 += ev
+        t64, t32 = f64 / FP64_PEAK_TFLOPS, f32 / FP32_PEAK_TFLOPS
+        flops, peak, pipe = (f64, FP64_PEAK_TFLOPS, "fp64") if t64 >= t32 else (f32, FP32_PEAK_TFLOPS, "fp32")
         achieved = flops / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": "newton", "pipe": pipe, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "note": "algorithmic flops: 80 per 6x6 LDL^T factorisation, 72 per pair of triangular solves, "
-                        "1140 per residual/tangent evaluation (FP64 path only); "
-                        "peak from unit counts and clock (FP64 nominal 1.25 TFLOP/s)"}
+                "flops_fp32": f32, "flops_fp64": f64,
+                "note": "algorithmic flops: 1140 per residual+tangent evaluation, 544 per residual-only "
+                        "evaluation, 80 per 6x6 LDL^T factorisation, 72 per pair of triangular solves, counted "
+                        "by pipe; peak from unit counts and the maximum SM clock"}
+    if hbm_bytes_per_voxel(dom, wl.n, T) is None:
+        return {"bound": "unknown", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
     b = hbm_bytes_per_voxel(dom, wl.n, T) * N3
     achieved = b / avg_s / 1e9
     peak = pk.get("hbm_gbs", 6800.0)

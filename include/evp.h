@@ -42,9 +42,10 @@ extern "C" {
 
 /* precision of the field arithmetic */
 #define EVP_FP64 0   /* every field, FFT and solve in FP64 */
-#define EVP_MIXED 1  /* FP32 fields, FFTs and phase field; FP64 local Newton solve and FP64 macro
-                        reductions (norms, mean stress, residuals, nucleation decision) */
-#define EVP_MIXED_FAST 2  /* as EVP_MIXED, but the 6x6 Newton solve runs in FP32 too */
+#define EVP_MIXED 1  /* FP32 fields, FFTs and phase field; FP64 factorisation of the 6x6 local Newton
+                        tangent (with EVP_NEWTON_REUSE its factors are then stored and applied in FP32)
+                        and FP64 macro reductions (norms, mean stress, residuals, nucleation decision) */
+#define EVP_MIXED_FAST 2  /* as EVP_MIXED, but the 6x6 tangent is factorised in FP32 too */
 
 typedef struct {
     int n;                 /* grid points per edge */
@@ -59,8 +60,9 @@ typedef struct {
     int predictor;         /* 1: start each increment from the previous strain-increment field */
     int max_ids;           /* capacity of the grain-id space (>= grains); 0 = grains + 8 N^3 */
     int newton_mode;       /* 0: exact Newton every fixed-point iteration; 1: keep each voxel's factored
-                              tangent across iterations and refactor only when a step stalls (same
-                              local tolerance, same result); EVP_NEWTON_* */
+                              tangent across iterations (21 words per voxel in the field precision) and
+                              refactor only when a step stalls (same local tolerance, same result);
+                              EVP_NEWTON_* */
     int scheme;            /* EVP_SCHEME_BASIC: Green-operator fixed point (Moulinec-Suquet);
                               EVP_SCHEME_AL: augmented Lagrangian (Michel-Moulinec-Suquet), the solver the
                               paper names (Sec. 2.1); same solution, fewer iterations at high contrast */

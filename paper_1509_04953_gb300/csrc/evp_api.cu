@@ -175,8 +175,7 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *epsp = take(6 * N3 * T), *deps = take(6 * N3 * T), *rho = take(12 * N3 * T), *tauc = take(N3 * T);
     char *eta = take(K * N3 * T), *eta2 = take(K * N3 * T), *spec = take(6 * H * 2 * T);
     char *Stab = take(36 * (size_t)G * T), *Mtab = take(72 * (size_t)G * T);
-    const size_t TSf = c->precision == EVP_MIXED_FAST ? 4 : 8;   // stored tangent factors
-    char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? 21 * N3 * TSf : 0);
+    char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? 21 * N3 * T : 0);   // stored tangent factors
     const bool al = c->scheme == EVP_SCHEME_AL;
     char *Sal = take(al ? 36 * (size_t)G * T : 0), *lam = take(al ? 6 * N3 * T : 0), *pal = take(al ? 6 * N3 * T : 0);
     const bool f32t = c->newton_mode == EVP_NEWTON_F32_TANGENT;

@@ -171,12 +171,28 @@ __device__ __forceinline__ void load_tw(double2 *tw_s, int N) {
 }
 
 template <int N> __host__ __device__ constexpr int rowpairs() { return N >= 64 ? 32 : 4096 / (N * 2); }
-template <int N, typename T> __host__ __device__ constexpr int tx_y() { return sizeof(T) == 4 ? 32 : 16; }
-template <typename T> __host__ __device__ constexpr int tx_z() { return sizeof(T) == 4 ? 8 : 4; }
-template <int N> __host__ __device__ constexpr int maxit(int lines) {
-    return (lines * (N / Shape<N>::R1) + kThreads - 1) / kThreads < 1 ? 1
-                                                                     : (lines * (N / Shape<N>::R1) + kThreads - 1) / kThreads;
+// Column tiles of the half spectrum (kx = 0..N/2): N/2 columns split into full tiles of TXe, and the
+// Nyquist column kx = N/2 appended to tile 0 as one extra line, so no tile is ragged.
+template <int N, typename T> __host__ __device__ constexpr int tx_y() {
+    return (sizeof(T) == 4 ? 32 : 16) < N / 2 ? (sizeof(T) == 4 ? 32 : 16) : N / 2;
 }
+template <int N, typename T> __host__ __device__ constexpr int tx_z() {
+    return (sizeof(T) == 4 ? 8 : 4) < N / 2 ? (sizeof(T) == 4 ? 8 : 4) : N / 2;
+}
+template <int N> __host__ __device__ constexpr int maxit(int lines, int threads = kThreads) {
+    return (lines * (N / Shape<N>::R1) + threads - 1) / threads < 1 ? 1
+                                                                   : (lines * (N / Shape<N>::R1) + threads - 1) / threads;
+}
+// Threads of a column-tile CTA: enough that a tile with its extra Nyquist lines (lines + extra)
+// needs no more pass-1 register sets than a full tile would at kThreads (the extra set would raise
+// register use, and so cut occupancy, for every tile).
+template <int N> __host__ __device__ constexpr int tile_threads(int lines, int extra) {
+    return ((((lines + extra) * (N / Shape<N>::R1) + maxit<N>(lines) - 1) / maxit<N>(lines) + 31) / 32) * 32 < kThreads
+               ? kThreads
+               : ((((lines + extra) * (N / Shape<N>::R1) + maxit<N>(lines) - 1) / maxit<N>(lines) + 31) / 32) * 32;
+}
+template <int N, typename T> __host__ __device__ constexpr int y_threads() { return tile_threads<N>(tx_y<N, T>(), 1); }
+template <int N, typename T> __host__ __device__ constexpr int z_threads() { return tile_threads<N>(6 * tx_z<N, T>(), 6); }
 
 // ---------------------------------------------------------------------------------------------
 // x pass, real -> half spectrum. CTA = RP pairs of rows (y even, y+1) of one (field, z).
@@ -266,32 +282,35 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
 // y pass: CTA = (field, z, kx tile of TX columns); lines along y.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(kThreads) k_fft_y(typename CT<T>::type *__restrict__ spec) {
+__global__ void __launch_bounds__(y_threads<N, T>()) k_fft_y(typename CT<T>::type *__restrict__ spec) {
     using C = typename CT<T>::type;
     constexpr int TX = tx_y<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *buf = tw + N;
-    constexpr int ntiles = (Hx + TX - 1) / TX;
+    constexpr int ntiles = (N / 2) / TX;
     const int tile = blockIdx.x % ntiles;
     const long plane = blockIdx.x / ntiles;        // field*N + z
-    const int kx0 = tile * TX;
+    const bool nyq = tile == 0;                    // tile 0 also carries the column kx = N/2 as line TX
     C *base = spec + plane * (long)N * Hx;
+    const int kx0 = tile * TX;
     load_tw(tw, N);
-    for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
-        const int y = t / TX, xl = t - y * TX;
-        const int kx = kx0 + xl;
-        if (kx < Hx) cp_async<sizeof(C)>(buf + xl * LS + pad16(y), base + (long)y * Hx + kx);
-        else buf[xl * LS + pad16(y)] = cmk<C>(0, 0);
+    for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {   // TX, N powers of two: shifts, no division
+        const int y = t / TX, xl = t % TX;
+        cp_async<sizeof(C)>(buf + xl * LS + pad16(y), base + (long)y * Hx + kx0 + xl);
     }
+    if (nyq)
+        for (int y = threadIdx.x; y < N; y += blockDim.x)
+            cp_async<sizeof(C)>(buf + TX * LS + pad16(y), base + (long)y * Hx + N / 2);
     cp_async_wait_all();
     __syncthreads();
-    block_fft<N, INV, maxit<N>(TX)>(buf, TX, tw);
+    block_fft<N, INV, maxit<N>(TX + 1, y_threads<N, T>())>(buf, TX + (nyq ? 1 : 0), tw);
     for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
-        const int y = t / TX, xl = t - y * TX;
-        const int kx = kx0 + xl;
-        if (kx < Hx) base[(long)y * Hx + kx] = buf[xl * LS + pad16(y)];
+        const int y = t / TX, xl = t % TX;
+        base[(long)y * Hx + kx0 + xl] = buf[xl * LS + pad16(y)];
     }
+    if (nyq)
+        for (int y = threadIdx.x; y < N; y += blockDim.x) base[(long)y * Hx + N / 2] = buf[TX * LS + pad16(y)];
 }
 
 // Green operator of the isotropic reference medium applied to one spectral stress (Mandel):
@@ -368,41 +387,49 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
 // z pass: CTA = (ky, kx tile); nf fields x TX columns x N planes in shared memory.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
+__global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
                                                    T mu0, double *__restrict__ partials, double *__restrict__ mean6) {
     using C = typename CT<T>::type;
-    constexpr int TX = tx_z<T>(), LS = Shape<N>::LS, Hx = N / 2 + 1, MI = maxit<N>(6 * TX);
+    constexpr int TX = tx_z<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1, MI = maxit<N>(6 * (TX + 1), z_threads<N, T>());
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *buf = tw + N;
     __shared__ double red[32];
-    constexpr int ntiles = (Hx + TX - 1) / TX;
+    constexpr int ntiles = (N / 2) / TX;
     const int tile = blockIdx.x % ntiles;
     const int ky = blockIdx.x / ntiles;
+    // lines: f*TX + xl for the TX regular columns of field f, then (tile 0 only) nf*TX + f for the
+    // Nyquist column kx = N/2 of field f
+    const bool nyq = tile == 0;
     const int kx0 = tile * TX;
+    const int nlines = nf * TX + (nyq ? nf : 0);
     const long plane = (long)N * Hx;            // one z plane of one field
     const long fstride = plane * N;
     load_tw(tw, N);
-    for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
-        const int f = t / (TX * N);
-        const int r = t - f * TX * N;
-        const int z = r / TX, xl = r - z * TX;
-        const int kx = kx0 + xl;
-        if (kx < Hx) cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx);
-        else buf[(f * TX + xl) * LS + pad16(z)] = cmk<C>(0, 0);
+    for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {   // TX, N powers of two: shifts
+        const int f = t / (TX * N), r = t % (TX * N);
+        const int z = r / TX, xl = r % TX;
+        cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx0 + xl);
     }
+    if (nyq)
+        for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
+            const int f = t / N, z = t % N;
+            cp_async<sizeof(C)>(buf + (nf * TX + f) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + N / 2);
+        }
     cp_async_wait_all();
     __syncthreads();
-    if (mode != Z_INV) block_fft<N, false, MI>(buf, nf * TX, tw);
+    if (mode != Z_INV) block_fft<N, false, MI>(buf, nlines, tw);
     if (mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) {
         const bool apply = mode == Z_FWD_GAMMA_INV;
         T acc = (T)0;   // per-thread sum in the field precision; block and global sums in FP64
-        for (int t = threadIdx.x; t < TX * N; t += blockDim.x) {
-            const int kz = t / TX, xl = t - kz * TX;
-            const int kx = kx0 + xl;
-            if (kx >= Hx) continue;
+        const int npts = (TX + (nyq ? 1 : 0)) * N;
+        for (int t = threadIdx.x; t < npts; t += blockDim.x) {
+            const bool reg = t < TX * N;
+            const int kz = reg ? t / TX : t - TX * N;
+            const int kx = reg ? kx0 + t % TX : N / 2;
+            const int l0 = reg ? t % TX : nf * TX, ls = reg ? TX : 1;   // line of field f: l0 + f*ls
             C s6[6];
-            for (int f = 0; f < 6; ++f) s6[f] = buf[(f * TX + xl) * LS + pad16(kz)];
+            for (int f = 0; f < 6; ++f) s6[f] = buf[(l0 + f * ls) * LS + pad16(kz)];
             if (kx == 0 && ky == 0 && kz == 0 && mean6 != nullptr) {
                 const double inv = 1.0 / ((double)N * N * N);
                 for (int f = 0; f < 6; ++f) mean6[f] = (double)s6[f].x * inv;
@@ -410,26 +437,29 @@ __global__ void __launch_bounds__(kThreads) k_fft_z(typename CT<T>::type *__rest
             const bool partner = !(kx == 0 || kx == (N >> 1));
             gamma_point<C, T>(s6, kx, ky, kz, N, lam0, mu0, acc, partner, apply);
             if (apply)
-                for (int f = 0; f < 6; ++f) buf[(f * TX + xl) * LS + pad16(kz)] = s6[f];
+                for (int f = 0; f < 6; ++f) buf[(l0 + f * ls) * LS + pad16(kz)] = s6[f];
         }
         __syncthreads();
         const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = tot;
     }
-    if (mode == Z_INV || mode == Z_FWD_GAMMA_INV) block_fft<N, true, MI>(buf, nf * TX, tw);
+    if (mode == Z_INV || mode == Z_FWD_GAMMA_INV) block_fft<N, true, MI>(buf, nlines, tw);
     for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
-        const int f = t / (TX * N);
-        const int r = t - f * TX * N;
-        const int z = r / TX, xl = r - z * TX;
-        const int kx = kx0 + xl;
-        if (kx < Hx) spec[f * fstride + z * plane + (long)ky * Hx + kx] = buf[(f * TX + xl) * LS + pad16(z)];
+        const int f = t / (TX * N), r = t % (TX * N);
+        const int z = r / TX, xl = r % TX;
+        spec[f * fstride + z * plane + (long)ky * Hx + kx0 + xl] = buf[(f * TX + xl) * LS + pad16(z)];
     }
+    if (nyq)
+        for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
+            const int f = t / N, z = t % N;
+            spec[f * fstride + z * plane + (long)ky * Hx + N / 2] = buf[(nf * TX + f) * LS + pad16(z)];
+        }
 }
 
 template <typename T, int N> size_t smem_x() { return sizeof(typename CT<T>::type) * (N + (size_t)rowpairs<N>() * Shape<N>::LS); }
-template <typename T, int N> size_t smem_y() { return sizeof(typename CT<T>::type) * (N + (size_t)tx_y<N, T>() * Shape<N>::LS); }
+template <typename T, int N> size_t smem_y() { return sizeof(typename CT<T>::type) * (N + (size_t)(tx_y<N, T>() + 1) * Shape<N>::LS); }
 template <typename T, int N> size_t smem_z(int nf) {
-    return sizeof(typename CT<T>::type) * (N + (size_t)nf * tx_z<T>() * Shape<N>::LS);
+    return sizeof(typename CT<T>::type) * (N + (size_t)nf * (tx_z<N, T>() + 1) * Shape<N>::LS);
 }
 
 template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
@@ -466,13 +496,13 @@ cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double
 
 template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int inverse, cudaStream_t s) {
     using C = typename CT<T>::type;
-    constexpr int TX = tx_y<N, T>(), Hx = N / 2 + 1;
-    const int blocks = nfields * N * ((Hx + TX - 1) / TX);
+    constexpr int TX = tx_y<N, T>();
+    const int blocks = nfields * N * ((N / 2) / TX);
     const size_t sm = smem_y<T, N>();
     cudaError_t e = inverse ? allow_smem(k_fft_y<T, N, true>, sm) : allow_smem(k_fft_y<T, N, false>, sm);
     if (e != cudaSuccess) return e;
-    if (inverse) k_fft_y<T, N, true><<<blocks, kThreads, sm, s>>>((C *)spec);
-    else k_fft_y<T, N, false><<<blocks, kThreads, sm, s>>>((C *)spec);
+    if (inverse) k_fft_y<T, N, true><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec);
+    else k_fft_y<T, N, false><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec);
     return cudaGetLastError();
 }
 
@@ -480,12 +510,12 @@ template <typename T, int N>
 cudaError_t z_n(void *spec, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
                 cudaStream_t s) {
     using C = typename CT<T>::type;
-    constexpr int TX = tx_z<T>(), Hx = N / 2 + 1;
-    const int blocks = N * ((Hx + TX - 1) / TX);
+    constexpr int TX = tx_z<N, T>();
+    const int blocks = N * ((N / 2) / TX);
     const size_t sm = smem_z<T, N>(nfields);
     cudaError_t e = allow_smem(k_fft_z<T, N>, smem_z<T, N>(6));
     if (e != cudaSuccess) return e;
-    k_fft_z<T, N><<<blocks, kThreads, sm, s>>>((C *)spec, nfields, mode, (T)lam0, (T)mu0, partials, mean6);
+    k_fft_z<T, N><<<blocks, z_threads<N, T>(), sm, s>>>((C *)spec, nfields, mode, (T)lam0, (T)mu0, partials, mean6);
     return cudaGetLastError();
 }
 
@@ -504,9 +534,9 @@ cudaError_t z_n(void *spec, int nfields, int mode, double lam0, double mu0, doub
 }  // namespace
 
 int fft_z_blocks(int n, int is_double) {
-    const int Hx = n / 2 + 1;
-    const int TX = is_double ? tx_z<double>() : tx_z<float>();
-    return n * ((Hx + TX - 1) / TX);
+    const int TX0 = is_double ? 4 : 8;
+    const int TX = TX0 < n / 2 ? TX0 : n / 2;
+    return n * ((n / 2) / TX);
 }
 
 template <typename T> cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s) {

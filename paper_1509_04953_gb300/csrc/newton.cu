@@ -223,7 +223,13 @@ __global__ void __launch_bounds__(kThreads) k_newton_df(long N3, const double *_
 // on request (first fixed-point iteration of an increment), when a step contracts by less than
 // 4x, or after a backtracking line search. The local problem is still solved to the same
 // tolerance, so the result matches the exact-Newton one to that tolerance.
-template <typename TA, typename TS>
+//
+// The factorisation runs in TF and the factors are stored and applied in TS. On the FP32-field path
+// TF = double and TS = float: an FP32 factorisation of this tangent loses the small (elastic) pivots
+// to cancellation once a few slip systems are far into the power law, while FP64 factors rounded to
+// FP32 afterwards are a componentwise perturbation and keep the Newton direction within about 1e-4
+// relative even there, so the reused step runs on the FP32 pipe and reads half the bytes.
+template <typename TA, typename TS, typename TF>
 __device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA sg[6],
                            const MatConst &mc, TA tol, int maxit, TA ls_free, TS F[21], bool refresh, int &nevals,
                            int &nref) {
@@ -239,7 +245,10 @@ __device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA e
             Eval<TA> full;
             evaluate(Sp, M, etr, tauc, inv_tc, sg, mc, full);
             ++nevals;
-            if (!ldl_factor<TS, TA>(full.K, F)) return -it;
+            TF Ff[21];
+            if (!ldl_factor<TF, TA>(full.K, Ff)) return -it;
+#pragma unroll
+            for (int q = 0; q < 21; ++q) F[q] = (TS)Ff[q];
             ++nref;
             refresh = false;
             fresh = true;
@@ -289,8 +298,8 @@ __device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA e
     return -maxit;
 }
 
-template <typename TA, typename TS>
-__global__ void __launch_bounds__(kThreads) k_newton_chord(long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc,
+template <typename TA, typename TS, typename TF>
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_chord(long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc,
                                                           const int32_t *__restrict__ g0, TA *__restrict__ sig,
                                                           const TA *__restrict__ Stab, const TA *__restrict__ Mtab,
                                                           TS *__restrict__ fac, MatConst mc, TA tol, int maxit,
@@ -317,8 +326,8 @@ __global__ void __launch_bounds__(kThreads) k_newton_chord(long N3, const TA *__
 #pragma unroll
             for (int q = 0; q < 21; ++q) F[q] = fac[q * N3 + v];
         }
-        r = chord_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
-                                force_refresh != 0, nev, nref);
+        r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
+                                    force_refresh != 0, nev, nref);
 #pragma unroll
         for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
         if (nref) {
@@ -355,24 +364,53 @@ __global__ void __launch_bounds__(kThreads) k_newton_chord(long N3, const TA *__
 // init = 1 is the start of an increment: sigma from the plain implicit update at eps_tr (S instead of
 // Sal, no lam term), then lam = sigma and e_tr = eps_tr. Partial sums per block: |eps_tr - e_tr|^2,
 // |C0 (eps_tr - e_tr)|^2, the six components of lam and the six of sigma.
-__device__ __forceinline__ double iso_apply_c0(double lam0, double mu0, const double x[6], int i) {
-    const double tr = x[0] + x[1] + x[2];
-    return 2.0 * mu0 * x[i] + (i < 3 ? lam0 * tr : 0.0);
+// C0 x for the isotropic reference stiffness (Lame constants l0, m0), component i of Mandel x.
+template <typename T> __device__ __forceinline__ T iso_apply_c0(T l0, T m0, const T x[6], int i) {
+    const T tr = x[0] + x[1] + x[2];
+    return (T)2 * m0 * x[i] + (i < 3 ? l0 * tr : (T)0);
 }
 
-template <typename TA, typename TS>
+// NV per-thread values summed over the block into part[0..NV): warp sums in the value type (a
+// five-level pairwise tree), then the warp sums in FP64. On the FP32 path this keeps the FP64 pipe
+// out of the per-voxel work; the result stays within a few FP32 roundings of the exact block sum.
+template <int NV, typename T> __device__ __forceinline__ void block_sums(const T (&v)[NV], double *sh, double *part) {
+    T w[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        w[q] = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[wid * NV + q] = (double)w[q];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int k = 0; k < nw; ++k) t += sh[k * NV + threadIdx.x];
+        part[threadIdx.x] = t;
+    }
+}
+
+template <typename TA, typename TS, typename TF>
 __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__restrict__ epst, const TA *__restrict__ epse,
                                                       const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
                                                       TA *__restrict__ sig, TA *__restrict__ lam, TA *__restrict__ pout,
                                                       const TA *__restrict__ Stab, const TA *__restrict__ Sal,
-                                                      const TA *__restrict__ Mtab, MatConst mc, double lam0, double mu0,
-                                                      TA tol, int maxit, TA ls_free, int init, int *__restrict__ flags,
-                                                      double *__restrict__ part, TS *__restrict__ fac, int refresh) {
-    __shared__ double red[32];
+                                                      const TA *__restrict__ Mtab, MatConst mc, TA l0, TA m0, TA sa,
+                                                      TA sb, double sad, double sbd, TA tol, int maxit, TA ls_free,
+                                                      int init,
+                                                      int *__restrict__ flags, double *__restrict__ part,
+                                                      TS *__restrict__ fac, int refresh) {
+    constexpr int NV = 14;
+    __shared__ double red[(kThreads / 32) * NV];
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
     int r = 1, nev = 0;
-    double pc = 0.0, pl = 0.0, pm[6] = {0, 0, 0, 0, 0, 0}, ps[6] = {0, 0, 0, 0, 0, 0};
+    TA sums[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sums[q] = (TA)0;
     if (valid) {
         const int g = g0[v];
         TA Sp[21];
@@ -381,20 +419,18 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
         for (int i = 0; i < 6; ++i)
 #pragma unroll
             for (int j = 0; j <= i; ++j) Sp[pk(i, j)] = __ldg(S + 6 * i + j);
-        // isotropic S0 = (1/2mu0)(I - lam0/(3 lam0 + 2 mu0) J)
-        const double sa = 1.0 / (2.0 * mu0), sb = lam0 / (2.0 * mu0 * (3.0 * lam0 + 2.0 * mu0));
-        double et[6], lm[6], ee[6];
-        TA etr[6], sg[6];
+        // isotropic S0 = C0^-1 = sa I - sb J (Mandel), sa = 1/(2 m0), sb = l0 / (2 m0 (3 l0 + 2 m0))
+        TA et[6], lm[6], ee[6], etr[6], sg[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            et[c] = (double)epst[c * N3 + v];
-            lm[c] = init ? 0.0 : (double)lam[c * N3 + v];
-            ee[c] = (double)epse[c * N3 + v];
+            et[c] = epst[c * N3 + v];
+            lm[c] = init ? (TA)0 : lam[c * N3 + v];
+            ee[c] = epse[c * N3 + v];
             sg[c] = sig[c * N3 + v];
         }
-        const double ltr = lm[0] + lm[1] + lm[2];
+        const TA ltr = lm[0] + lm[1] + lm[2];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) etr[c] = (TA)(et[c] + sa * lm[c] - (c < 3 ? sb * ltr : 0.0));
+        for (int c = 0; c < 6; ++c) etr[c] = et[c] + sa * lm[c] - (c < 3 ? sb * ltr : (TA)0);
         if (fac) {   // tangent reuse: factors refreshed on request or when a step stalls
             TS F[21];
             if (!refresh) {
@@ -402,43 +438,41 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
                 for (int q = 0; q < 21; ++q) F[q] = fac[q * N3 + v];
             }
             int nref = 0;
-            r = chord_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
-                                    refresh != 0, nev, nref);
+            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
+                                        refresh != 0, nev, nref);
             if (nref) {
 #pragma unroll
                 for (int q = 0; q < 21; ++q) fac[q * N3 + v] = F[q];
             }
         } else {
-            r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
+            r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
         }
-        double s6[6], etr_l[6], d[6];
+        // local strain e_tr = eps_tr' - S0 sigma and the gap d = eps_tr - e_tr in FP64: near convergence
+        // eps_tr and e_tr agree to many digits, and forming them in FP32 leaves rounding noise in d
+        // (hence in the multiplier update) that keeps the iteration from settling
+        TA el[6], d[6], de[6];
+        double s6[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            s6[c] = (double)sg[c];
-            sig[c * N3 + v] = sg[c];
-        }
+        for (int c = 0; c < 6; ++c) s6[c] = (double)sg[c];
         const double str = s6[0] + s6[1] + s6[2];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            etr_l[c] = init ? et[c] : (double)etr[c] - (sa * s6[c] - (c < 3 ? sb * str : 0.0));
-            d[c] = et[c] - etr_l[c];
-        }
-        double dl[6], nl[6], de[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) de[c] = etr_l[c] - ee[c];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            dl[c] = iso_apply_c0(lam0, mu0, d, c);
-            nl[c] = init ? s6[c] : lm[c] + dl[c];
+            sig[c * N3 + v] = sg[c];
+            const double eld = init ? (double)et[c] : (double)etr[c] - (sad * s6[c] - (c < 3 ? sbd * str : 0.0));
+            d[c] = (TA)((double)et[c] - eld);
+            el[c] = (TA)eld;
+            de[c] = el[c] - ee[c];
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            lam[c * N3 + v] = (TA)nl[c];
-            pout[c * N3 + v] = (TA)(nl[c] - iso_apply_c0(lam0, mu0, de, c));
-            pc += d[c] * d[c];
-            pl += dl[c] * dl[c];
-            pm[c] = nl[c];
-            ps[c] = s6[c];
+            const TA dl = iso_apply_c0(l0, m0, d, c);
+            const TA nl = init ? sg[c] : lm[c] + dl;
+            lam[c * N3 + v] = nl;
+            pout[c * N3 + v] = nl - iso_apply_c0(l0, m0, de, c);
+            sums[0] += d[c] * d[c];
+            sums[1] += dl * dl;
+            sums[2 + c] = nl;
+            sums[8 + c] = sg[c];
         }
     }
     // flags as in k_newton
@@ -457,12 +491,7 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
         atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
         atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
     }
-    double sums[14] = {pc, pl, pm[0], pm[1], pm[2], pm[3], pm[4], pm[5], ps[0], ps[1], ps[2], ps[3], ps[4], ps[5]};
-#pragma unroll
-    for (int q = 0; q < 14; ++q) {
-        const double t = block_sum(sums[q], red);
-        if (threadIdx.x == 0) part[14 * blockIdx.x + q] = t;
-    }
+    block_sums<NV>(sums, red, part + NV * (long)blockIdx.x);
 }
 
 // Start of an increment: tau_c from the densities at t (frozen over the increment) and the
@@ -575,12 +604,14 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, cudaStream_t s) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
+    // factors stored in the field precision; factorised in FP64 unless the FP32 solve is asked for
     if (solve_fp64)
-        k_newton_chord<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (double *)fac, mc,
-                                                               (TA)tol, maxit, ls_free_of<TA>(), force_refresh, flags);
+        k_newton_chord<TA, TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
+                                                                   (TA)tol, maxit, ls_free_of<TA>(), force_refresh,
+                                                                   flags);
     else
-        k_newton_chord<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc, (TA)tol,
-                                                           maxit, ls_free_of<TA>(), force_refresh, flags);
+        k_newton_chord<TA, TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
+                                                               (TA)tol, maxit, ls_free_of<TA>(), force_refresh, flags);
     return cudaGetLastError();
 }
 
@@ -600,14 +631,17 @@ cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, co
                      int maxit, int solve_fp64, int init, int *flags, double *part, void *fac, int refresh,
                      cudaStream_t s) {
     const int blocks = al_blocks(N3);
+    const double sad = 1.0 / (2.0 * mu0), sbd = lam0 / (2.0 * mu0 * (3.0 * lam0 + 2.0 * mu0));
+    const TA sa = (TA)sad, sb = (TA)sbd;
     if (solve_fp64)
-        k_al_local<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc,
-                                                           lam0, mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part,
-                                                           (double *)fac, refresh);
+        k_al_local<TA, TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab,
+                                                               mc, (TA)lam0, (TA)mu0, sa, sb, sad, sbd, (TA)tol, maxit,
+                                                               ls_free_of<TA>(), init, flags, part, (TA *)fac, refresh);
     else
-        k_al_local<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc, lam0,
-                                                       mu0, (TA)tol, maxit, ls_free_of<TA>(), init, flags, part,
-                                                       (TA *)fac, refresh);
+        k_al_local<TA, TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc,
+                                                           (TA)lam0, (TA)mu0, sa, sb, sad, sbd, (TA)tol, maxit,
+                                                           ls_free_of<TA>(),
+                                                           init, flags, part, (TA *)fac, refresh);
     return cudaGetLastError();
 }
 

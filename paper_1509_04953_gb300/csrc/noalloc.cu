@@ -11,7 +11,7 @@
 
 namespace {
 
-// Partial sums of the z pass, one double per CTA: fft_z_blocks(n) <= 256 * ceil(129/8) = 4352
+// Partial sums of the z pass, one double per CTA: fft_z_blocks(n) <= 256 * (128/4) = 8192
 // for n <= 256 in any precision. Every GPU that loads the library holds this array until exit.
 constexpr int kMaxPartials = 8192;
 static __device__ __align__(256) double g_resid_partials[kMaxPartials];
