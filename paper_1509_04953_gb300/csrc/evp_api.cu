@@ -28,7 +28,9 @@ struct evp_handle {
     void *sig, *sigk, *epse, *epst, *epsp, *deps, *rho, *tauc, *eta, *eta2, *spec, *Stab, *Mtab, *fac, *Sal, *lam, *pal;
     float *Stabf, *Mtabf;
     double *k, *kappa, *partials, *scal;
-    int32_t *g0, *g, *gprev, *draws, *ids, *ids2, *flags, *blk_counts, *blk_off, *count;
+    int32_t *g0, *g, *gprev, *draws, *ids, *ids2, *flags, *blk_counts, *blk_off, *count, *wlist;
+    int nsm;
+    int fac_valid;   // stored tangent factors hold a factorisation (of some earlier state) for every voxel
     uint32_t *bitmap;
     int bitmap_words, max_ids, npartials;
     // macroscopic state (host)
@@ -175,7 +177,9 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *epsp = take(6 * N3 * T), *deps = take(6 * N3 * T), *rho = take(12 * N3 * T), *tauc = take(N3 * T);
     char *eta = take(K * N3 * T), *eta2 = take(K * N3 * T), *spec = take(6 * H * 2 * T);
     char *Stab = take(36 * (size_t)G * T), *Mtab = take(72 * (size_t)G * T);
-    char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? 21 * N3 * T : 0);   // stored tangent factors
+    // stored tangent factors: 21 words per voxel in planes of 16-byte vectors (24 FP32 / 22 FP64 words)
+    char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? (T == 4 ? 24 : 22) * N3 * T : 0);
+    char *wlist = take(c->newton_mode == EVP_NEWTON_REUSE ? 4 * N3 : 0);      // voxels left for the second pass
     const bool al = c->scheme == EVP_SCHEME_AL;
     char *Sal = take(al ? 36 * (size_t)G * T : 0), *lam = take(al ? 6 * N3 * T : 0), *pal = take(al ? 6 * N3 * T : 0);
     const bool f32t = c->newton_mode == EVP_NEWTON_F32_TANGENT;
@@ -194,6 +198,7 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
         h->sig = sig; h->sigk = sigk; h->epse = epse; h->epst = epst; h->epsp = epsp; h->deps = deps;
         h->rho = rho; h->tauc = tauc; h->eta = eta; h->eta2 = eta2; h->spec = spec; h->Stab = Stab; h->Mtab = Mtab;
         h->fac = fac;
+        h->wlist = (int32_t *)wlist;
         h->Stabf = (float *)Stabf;
         h->Mtabf = (float *)Mtabf;
         h->Sal = Sal;
@@ -452,6 +457,12 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     for (long v = 0; v < h->N3; ++v)
         if (grain_id[v] < 0 || grain_id[v] >= h->G)
             return fail(h, EVP_ERR_ARG, "grain_id[%ld]=%d outside [0,%d)", v, grain_id[v], h->G);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || h->nsm < 1)
+            return fail(h, EVP_ERR_CUDA, "cannot query the device");
+    }
     h->seed = seed;
     h->next_id = h->G;
     h->have_prev = 0;
@@ -467,6 +478,7 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     h->mc.lam0 = lam;
     h->mc.mu0 = mu;
     h->mc.n_int = (p->n >= 1.0 && p->n <= 64.0 && p->n == std::floor(p->n)) ? (int)p->n : 0;
+    h->mc.set_fp32();
     h->pc.m = 6.0 / p->l_gb;
     h->pc.kappa = 0.75 * p->l_gb;
     h->pc.gam = 1.5;
@@ -592,6 +604,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
     const int n = h->n;
     MatConst mc = h->mc;
     mc.dt = dt;
+    mc.set_fp32();
     const double lam0 = mc.lam0, mu0 = mc.mu0;
     // predictor
     double dE[6];
@@ -630,6 +643,9 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
     int32_t hf[2];
     int64_t hcount[3] = {0, 0, 0};
     const int reuse = h->cfg.newton_mode == EVP_NEWTON_REUSE;
+    // refactor every voxel's tangent at the first iteration unless valid factors are stored; always while
+    // an adjoint is recorded or swept, so that a recomputed increment repeats the recorded one exactly
+    const bool fresh = !h->fac_valid || h->adj != nullptr;
     if (h->cfg.scheme == EVP_SCHEME_AL) {
         status = h->dbl ? al_loop<double>(h, mc, dE, &it, &conv, &nmax, &err_eq, &err_bc, mean)
                         : al_loop<float>(h, mc, dE, &it, &conv, &nmax, &err_eq, &err_bc, mean);
@@ -645,7 +661,8 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
             else if (reuse)
                 CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                               (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
-                                              h->cfg.newton_max, 1, it == 1, h->flags, h->st));
+                                              h->cfg.newton_max, 1, it == 1 && fresh, h->flags, h->wlist,
+                                              h->nsm, h->st));
             else
                 CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                         (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
@@ -658,7 +675,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
             if (reuse)
                 CK(newton_chord_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                              (float *)h->Stab, (float *)h->Mtab, h->fac, mc, ntol, h->cfg.newton_max,
-                                             solve64, it == 1, h->flags, h->st));
+                                             solve64, it == 1 && fresh, h->flags, h->wlist, h->nsm, h->st));
             else
                 CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                        (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,
@@ -707,6 +724,10 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         }
     }
     if (it > h->cfg.max_iter) it = h->cfg.max_iter;
+    // after a first increment without a local failure every voxel holds factors of an SPD tangent; later
+    // increments start from them (stale factors only cost chord steps: a step that does not contract
+    // refreshes them)
+    if (reuse && h->cfg.scheme == EVP_SCHEME_BASIC) h->fac_valid = status == EVP_OK ? 1 : 0;
     CK(cudaMemcpyAsync(hcount, h->flags + 4, sizeof hcount, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     h->newton_solves += hcount[0];
@@ -1042,6 +1063,7 @@ int adjoint_sweep(evp_handle *h, const AdjLayout &L, const double *gbar, double 
         for (int t = s1 - 1; t >= s0; --t) {
             MatConst mc = h->mc;
             mc.dt = h->adj_dt[t];
+            mc.set_fp32();
             const TA *rp = tape_rho + (size_t)(t - s0) * 12 * N3, *sg = tape_sig + (size_t)(t - s0) * 6 * N3;
             CK(adj_prep<TA>(N3, h->g0, (const TA *)h->Stab, (const TA *)h->Mtab, rp, sg, lam_ep, lam_rho, Ct, sbar, aa,
                             taub, mc, gbar + 6 * (size_t)t, part, h->st));

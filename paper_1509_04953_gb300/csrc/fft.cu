@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
-                                                       long npairs, T scale, int has_add, double a0, double a1, double a2,
-                                                       double a3, double a4, double a5, const T *__restrict__ base) {
+                                                       long npairs, T scale, int has_add, T a0, T a1, T a2, T a3, T a4,
+                                                       T a5, const T *__restrict__ base) {
     using C = typename CT<T>::type;
     constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -266,11 +266,11 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
         const C z = buf[pl * LS + pad16(j)];
         if (has_add) {
             const int f = (int)(row0 / rows_per_field);
-            const double add = f == 0 ? a0 : f == 1 ? a1 : f == 2 ? a2 : f == 3 ? a3 : f == 4 ? a4 : a5;
+            const T add = f == 0 ? a0 : f == 1 ? a1 : f == 2 ? a2 : f == 3 ? a3 : f == 4 ? a4 : a5;
             const T b0 = base ? base[row0 * N + j] : out[row0 * N + j];
             const T b1 = base ? base[(row0 + 1) * N + j] : out[(row0 + 1) * N + j];
-            out[row0 * N + j] = b0 + (z.x * scale + (T)add);
-            out[(row0 + 1) * N + j] = b1 + (z.y * scale + (T)add);
+            out[row0 * N + j] = b0 + (z.x * scale + add);
+            out[(row0 + 1) * N + j] = b1 + (z.y * scale + add);
         } else {
             out[row0 * N + j] = z.x;
             out[(row0 + 1) * N + j] = z.y;
@@ -486,9 +486,9 @@ cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double
     const size_t sm = smem_x<T, N>();
     cudaError_t e = allow_smem(k_fft_x_c2r<T, N>, sm);
     if (e != cudaSuccess) return e;
-    double a[6] = {0, 0, 0, 0, 0, 0};
+    T a[6] = {0, 0, 0, 0, 0, 0};   // rounded to the field precision here, not once per element on the device
     if (add6)
-        for (int i = 0; i < 6; ++i) a[i] = add6[i];
+        for (int i = 0; i < 6; ++i) a[i] = (T)add6[i];
     k_fft_x_c2r<T, N><<<blocks, kThreads, sm, s>>>((const C *)spec, out, npairs, scale, add6 != nullptr, a[0], a[1],
                                                    a[2], a[3], a[4], a[5], base);
     return cudaGetLastError();

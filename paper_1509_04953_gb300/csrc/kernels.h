@@ -10,6 +10,8 @@ struct MatConst {
     double gdot0, n, dt, tau0, alpha_mu_b, k1, k2;
     double lam0, mu0;       // reference medium (Voigt isotropic average)
     int n_int;              // n if it is a small positive integer (fast power), else 0
+    float gdot0_f, n_f, dt_f;   // FP32 copies for the FP32 path (no FP64 conversions in the kernels)
+    void set_fp32() { gdot0_f = (float)gdot0; n_f = (float)n; dt_f = (float)dt; }
 };
 
 // ---- fft.cu ----
@@ -32,11 +34,13 @@ template <typename TA>
 cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                          const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
                          cudaStream_t s);
-// Jacobian-reuse variant: fac holds 21 factor words per voxel (double if solve_fp64, else TA).
+// Jacobian-reuse variant: fac holds 21 factor words per voxel in TA (factorised in FP64 if solve_fp64).
+// Unless force_refresh, runs in two passes with the work list wl (N3 entries, count in flags[10]);
+// nsm = multiprocessors, for the grid of the second pass.
 template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
-                               int force_refresh, int *flags, cudaStream_t s);
+                               int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s);
 // FP64 residual / FP32 tangent Newton (FP64 path); Stabf / Mtabf are FP32 copies of the tables.
 cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
                             const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,

@@ -28,8 +28,95 @@ template <typename T> __device__ __forceinline__ T pow_nm1(T ax, const MatConst 
     return ax > (T)0 ? (T)pow((double)ax, mc.n - 1.0) : (T)0;
 }
 
+// Flow-rule constants in the arithmetic precision.
+template <typename TA> __device__ __forceinline__ void flow_consts(const MatConst &mc, TA &dt, TA &g0, TA &nn) {
+    if constexpr (sizeof(TA) == 4) { dt = mc.dt_f; g0 = mc.gdot0_f; nn = mc.n_f; }
+    else { dt = mc.dt; g0 = mc.gdot0; nn = mc.n; }
+}
+
 // Packed lower-triangular index of (i, j), j <= i.
 __host__ __device__ constexpr int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Per-grain tables: compliance rows (36 words) and Schmid vectors (12 x 6 words) per grain, each grain
+// starting on a 16-byte boundary (144 g / 288 g bytes in FP32, twice that in FP64). They are read with
+// 16-byte vector loads; the load instructions, not the bytes (the tables sit in L1), are what a
+// per-voxel kernel issuing one load per word runs short of.
+template <typename TA> __device__ __forceinline__ void load_compliance(const TA *__restrict__ S, TA Sp[21]) {
+    TA full[36];
+    if constexpr (sizeof(TA) == 4) {
+        const float4 *S4 = reinterpret_cast<const float4 *>(S);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float4 t = __ldg(S4 + k);
+            full[4 * k] = t.x; full[4 * k + 1] = t.y; full[4 * k + 2] = t.z; full[4 * k + 3] = t.w;
+        }
+    } else {
+        const double2 *S2 = reinterpret_cast<const double2 *>(S);
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const double2 t = __ldg(S2 + k);
+            full[2 * k] = t.x; full[2 * k + 1] = t.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) Sp[i * (i + 1) / 2 + j] = full[6 * i + j];
+}
+// Schmid vectors of slip systems 2p and 2p+1 (12 consecutive words, 16-byte aligned).
+template <typename TA> __device__ __forceinline__ void load_slip_pair(const TA *__restrict__ M, int p, TA m[12]) {
+    if constexpr (sizeof(TA) == 4) {
+        const float4 *M4 = reinterpret_cast<const float4 *>(M + 12 * p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 t = __ldg(M4 + k);
+            m[4 * k] = t.x; m[4 * k + 1] = t.y; m[4 * k + 2] = t.z; m[4 * k + 3] = t.w;
+        }
+    } else {
+        const double2 *M2 = reinterpret_cast<const double2 *>(M + 12 * p);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const double2 t = __ldg(M2 + k);
+            m[2 * k] = t.x; m[2 * k + 1] = t.y;
+        }
+    }
+}
+
+// Stored tangent factors (21 words per voxel) in planes of 16-byte vectors: plane k holds words
+// 4k..4k+3 (FP32, 6 planes) or 2k..2k+1 (FP64, 11 planes) of every voxel, so a voxel's factors come
+// in 6 (11) coalesced vector loads. Plane stride N3 vectors.
+template <typename TS> __host__ __device__ constexpr int factor_words() { return sizeof(TS) == 4 ? 24 : 22; }
+template <typename TS> __device__ __forceinline__ void load_factors(const TS *__restrict__ fac, long N3, long v, TS F[21]) {
+    if constexpr (sizeof(TS) == 4) {
+        const float4 *f4 = reinterpret_cast<const float4 *>(fac);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 t = f4[k * N3 + v];
+            F[4 * k] = t.x; if (4 * k + 1 < 21) F[4 * k + 1] = t.y;
+            if (4 * k + 2 < 21) F[4 * k + 2] = t.z; if (4 * k + 3 < 21) F[4 * k + 3] = t.w;
+        }
+    } else {
+        const double2 *f2 = reinterpret_cast<const double2 *>(fac);
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const double2 t = f2[k * N3 + v];
+            F[2 * k] = t.x; if (2 * k + 1 < 21) F[2 * k + 1] = t.y;
+        }
+    }
+}
+template <typename TS> __device__ __forceinline__ void store_factors(TS *__restrict__ fac, long N3, long v, const TS F[21]) {
+    if constexpr (sizeof(TS) == 4) {
+        float4 *f4 = reinterpret_cast<float4 *>(fac);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            f4[k * N3 + v] = make_float4(F[4 * k], 4 * k + 1 < 21 ? F[4 * k + 1] : 0.f, 4 * k + 2 < 21 ? F[4 * k + 2] : 0.f,
+                                         4 * k + 3 < 21 ? F[4 * k + 3] : 0.f);
+    } else {
+        double2 *f2 = reinterpret_cast<double2 *>(fac);
+#pragma unroll
+        for (int k = 0; k < 11; ++k) f2[k * N3 + v] = make_double2(F[2 * k], 2 * k + 1 < 21 ? F[2 * k + 1] : 0.0);
+    }
+}
 
 template <typename TA> struct Eval {
     TA r[6];
@@ -40,7 +127,8 @@ template <typename TA> struct Eval {
 template <typename TA>
 __device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA inv_tc,
                                          const TA sg[6], const MatConst &mc, Eval<TA> &e) {
-    const TA dt = (TA)mc.dt, g0 = (TA)mc.gdot0, nn = (TA)mc.n;
+    TA dt, g0, nn;
+    flow_consts(mc, dt, g0, nn);
     TA phi = (TA)0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -55,10 +143,12 @@ __device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__
     const TA cphi = dt * g0 * tauc / (nn + (TA)1);
     const TA cslope = dt * nn * g0 * inv_tc;
 #pragma unroll 1
-    for (int a = 0; a < 12; ++a) {
-        TA m[6];
+    for (int p = 0; p < 6; ++p) {
+      TA mm[12];
+      load_slip_pair(M, p, mm);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) m[i] = __ldg(M + 6 * a + i);
+      for (int h = 0; h < 2; ++h) {
+        const TA *m = mm + 6 * h;
         TA tau = (TA)0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
@@ -79,6 +169,7 @@ __device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__
 #pragma unroll
             for (int j = 0; j <= i; ++j) e.K[pk(i, j)] += sm[i] * m[j];
         phi += cphi * p10 * ax;
+      }
     }
     e.phi = phi;
 }
@@ -145,10 +236,13 @@ template <typename TA> struct EvalR {
     TA r[6];
     TA phi;
 };
-template <typename TA>
+// UNROLL: slip-system pairs unrolled per loop trip (6 = fully, letting the table loads run ahead of
+// the arithmetic where registers allow).
+template <typename TA, int UNROLL = 1>
 __device__ __forceinline__ void evaluate_r(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA inv_tc,
                                            const TA sg[6], const MatConst &mc, EvalR<TA> &e) {
-    const TA dt = (TA)mc.dt, g0 = (TA)mc.gdot0, nn = (TA)mc.n;
+    TA dt, g0, nn;
+    flow_consts(mc, dt, g0, nn);
     TA phi = (TA)0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -159,21 +253,24 @@ __device__ __forceinline__ void evaluate_r(const TA Sp[21], const TA *__restrict
         phi += sg[i] * ((TA)0.5 * acc - etr[i]);
     }
     const TA cphi = dt * g0 * tauc / (nn + (TA)1);
-#pragma unroll 1
-    for (int a = 0; a < 12; ++a) {
-        TA m[6];
+#pragma unroll UNROLL
+    for (int p = 0; p < 6; ++p) {
+        TA mm[12];
+        load_slip_pair(M, p, mm);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) m[i] = __ldg(M + 6 * a + i);
-        TA tau = (TA)0;
+        for (int h = 0; h < 2; ++h) {
+            const TA *m = mm + 6 * h;
+            TA tau = (TA)0;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
-        const TA x = tau * inv_tc, ax = fabs(x);
-        const TA p10 = pow_nm1(ax, mc) * ax;
-        const TA gd = x < (TA)0 ? -g0 * p10 : g0 * p10;
-        const TA dg = dt * gd;
+            for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
+            const TA x = tau * inv_tc, ax = fabs(x);
+            const TA p10 = pow_nm1(ax, mc) * ax;
+            const TA gd = x < (TA)0 ? -g0 * p10 : g0 * p10;
+            const TA dg = dt * gd;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) e.r[i] += dg * m[i];
-        phi += cphi * p10 * ax;
+            for (int i = 0; i < 6; ++i) e.r[i] += dg * m[i];
+            phi += cphi * p10 * ax;
+        }
     }
     e.phi = phi;
 }
@@ -260,10 +357,15 @@ __device__ __forceinline__ void evaluate_df(const double Sp[21], const double *_
     const double cphi = dt * g0 * tauc / (nn + 1.0);
     const float cslope = (float)(dt * nn * g0 * inv_tc);
 #pragma unroll 1
-    for (int a = 0; a < 12; ++a) {
-        double m[6];
+    for (int p = 0; p < 6; ++p) {
+      double mm[12];
+      float mmf[12];
+      load_slip_pair(M, p, mm);
+      load_slip_pair(Mf, p, mmf);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) m[i] = __ldg(M + 6 * a + i);
+      for (int h = 0; h < 2; ++h) {
+        const double *m = mm + 6 * h;
+        const float *mf = mmf + 6 * h;
         double tau = 0.0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
@@ -275,16 +377,14 @@ __device__ __forceinline__ void evaluate_df(const double Sp[21], const double *_
         for (int i = 0; i < 6; ++i) e.r[i] += dg * m[i];
         phi += cphi * p10 * ax;
         const float slope = cslope * (float)p9;
-        float mf[6], sm[6];
+        float sm[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            mf[i] = __ldg(Mf + 6 * a + i);
-            sm[i] = slope * mf[i];
-        }
+        for (int i = 0; i < 6; ++i) sm[i] = slope * mf[i];
 #pragma unroll
         for (int i = 0; i < 6; ++i)
 #pragma unroll
             for (int j = 0; j <= i; ++j) e.K[pk(i, j)] += sm[i] * mf[j];
+      }
     }
     e.phi = phi;
 }

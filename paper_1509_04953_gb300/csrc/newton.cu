@@ -80,11 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restri
     if (valid) {
         const int g = g0[v];
         TA Sp[21];
-        const TA *S = Stab + 36 * (long)g;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) Sp[pk(i, j)] = __ldg(S + 6 * i + j);
+        load_compliance(Stab + 36 * (long)g, Sp);
         TA etr[6], sg[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -180,15 +176,8 @@ __global__ void __launch_bounds__(kThreads) k_newton_df(long N3, const double *_
         const int g = g0[v];
         double Sp[21];
         float Spf[21];
-        const double *S = Stab + 36 * (long)g;
-        const float *Sf = Stabf + 36 * (long)g;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) {
-                Sp[pk(i, j)] = __ldg(S + 6 * i + j);
-                Spf[pk(i, j)] = __ldg(Sf + 6 * i + j);
-            }
+        load_compliance(Stab + 36 * (long)g, Sp);
+        load_compliance(Stabf + 36 * (long)g, Spf);
         double etr[6], sg[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -310,11 +299,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
     if (valid) {
         const int g = g0[v];
         TA Sp[21];
-        const TA *S = Stab + 36 * (long)g;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) Sp[pk(i, j)] = __ldg(S + 6 * i + j);
+        load_compliance(Stab + 36 * (long)g, Sp);
         TA etr[6], sg[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -323,16 +308,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
         }
         TS F[21];
         if (!force_refresh) {
-#pragma unroll
-            for (int q = 0; q < 21; ++q) F[q] = fac[q * N3 + v];
+            load_factors(fac, N3, v, F);
         }
         r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
                                     force_refresh != 0, nev, nref);
 #pragma unroll
         for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
         if (nref) {
-#pragma unroll
-            for (int q = 0; q < 21; ++q) fac[q * N3 + v] = F[q];
+            store_factors(fac, N3, v, F);
         }
     }
     __syncwarp();
@@ -351,6 +334,122 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
         atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
         atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
         atomicAdd(reinterpret_cast<unsigned long long *>(flags + 8), (unsigned long long)srf);
+    }
+}
+
+// Tangent reuse in two passes. Most voxels accept the first chord step once the fixed point has
+// settled, while a few need line searches or a refreshed tangent; in one kernel the warps holding
+// those few run their long loops with most lanes idle. Pass 1 takes the first step for every voxel
+// and stores it where it is accepted; the others are appended to a work list (warp-aggregated,
+// order immaterial: each voxel's computation is independent and deterministic). Pass 2 runs the
+// full chord iteration on the listed voxels only, from their unchanged state, so every result is
+// bitwise the one the single-kernel iteration gives.
+template <typename TA, typename TS>
+__global__ void __launch_bounds__(kThreads) k_chord_first(long N3, const TA *__restrict__ epst,
+                                                         const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
+                                                         TA *__restrict__ sig, const TA *__restrict__ Stab,
+                                                         const TA *__restrict__ Mtab, const TS *__restrict__ fac,
+                                                         MatConst mc, TA tol, int *__restrict__ flags,
+                                                         int32_t *__restrict__ wl) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = v < N3;
+    bool done = false;
+    if (valid) {
+        const int g = g0[v];
+        TA Sp[21];
+        load_compliance(Stab + 36 * (long)g, Sp);
+        TA etr[6], sg[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            etr[c] = epst[c * N3 + v];
+            sg[c] = sig[c * N3 + v];
+        }
+        TS F[21];
+        load_factors(fac, N3, v, F);
+        const TA tc = tauc[v];
+        EvalR<TA> e;
+        evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, tc, drcp(tc), sg, mc, e);
+        TA d[6];
+        ldl_apply<TS, TA>(F, e.r, d);
+        TA rd = (TA)0, dn = (TA)0, sn = (TA)0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            rd += e.r[i] * d[i];
+            dn += d[i] * d[i];
+            sn += sg[i] * sg[i];
+        }
+        dn = dsqrt(dn);
+        if (dn <= tol * (dsqrt(sn) + tc) && rd >= (TA)0) {   // the acceptance test of chord_voxel
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c] - d[c];
+            done = true;
+        }
+    }
+    const unsigned todo = __ballot_sync(0xffffffffu, valid && !done);
+    const unsigned ndone = __popc(__ballot_sync(0xffffffffu, done));
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && todo) base = atomicAdd(flags + 10, __popc(todo));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (valid && !done) wl[base + __popc(todo & ((1u << lane) - 1u))] = (int32_t)v;
+    if (lane == 0) {
+        // accepted voxels: one evaluation and one solve each, iteration count 1
+        if (ndone) {
+            atomicMax(flags + 1, 1);
+            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)ndone);
+            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)ndone);
+        }
+    }
+}
+
+template <typename TA, typename TS, typename TF>
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_rest(
+    long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
+    TA *__restrict__ sig, const TA *__restrict__ Stab, const TA *__restrict__ Mtab, TS *__restrict__ fac, MatConst mc,
+    TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int32_t *__restrict__ wl) {
+    const int count = *(volatile const int *)(flags + 10);
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long w0 = (long)blockIdx.x * blockDim.x; w0 < count; w0 += stride) {   // warp-uniform trip count
+        const long w = w0 + threadIdx.x;
+        const bool valid = w < count;
+        int r = 1, nev = 0, nref = 0;
+        if (valid) {
+            const long v = wl[w];
+            const int g = g0[v];
+            TA Sp[21];
+            load_compliance(Stab + 36 * (long)g, Sp);
+            TA etr[6], sg[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                etr[c] = epst[c * N3 + v];
+                sg[c] = sig[c * N3 + v];
+            }
+            TS F[21];
+            load_factors(fac, N3, v, F);
+            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F, false,
+                                        nev, nref);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
+            if (nref) {
+                store_factors(fac, N3, v, F);
+            }
+        }
+        const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
+        int mx = valid ? (r < 0 ? -r : r) : 0;
+        int sit = valid ? mx : 0, sev = nev, srf = nref;
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            sit += __shfl_xor_sync(0xffffffffu, sit, o);
+            sev += __shfl_xor_sync(0xffffffffu, sev, o);
+            srf += __shfl_xor_sync(0xffffffffu, srf, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (fmask) atomicAdd(flags, __popc(fmask));
+            atomicMax(flags + 1, mx);
+            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
+            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
+            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 8), (unsigned long long)srf);
+        }
     }
 }
 
@@ -414,11 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
     if (valid) {
         const int g = g0[v];
         TA Sp[21];
-        const TA *S = (init ? Stab : Sal) + 36 * (long)g;
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) Sp[pk(i, j)] = __ldg(S + 6 * i + j);
+        load_compliance((init ? Stab : Sal) + 36 * (long)g, Sp);
         // isotropic S0 = C0^-1 = sa I - sb J (Mandel), sa = 1/(2 m0), sb = l0 / (2 m0 (3 l0 + 2 m0))
         TA et[6], lm[6], ee[6], etr[6], sg[6];
 #pragma unroll
@@ -434,15 +529,13 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
         if (fac) {   // tangent reuse: factors refreshed on request or when a step stalls
             TS F[21];
             if (!refresh) {
-#pragma unroll
-                for (int q = 0; q < 21; ++q) F[q] = fac[q * N3 + v];
+                load_factors(fac, N3, v, F);
             }
             int nref = 0;
             r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
                                         refresh != 0, nev, nref);
             if (nref) {
-#pragma unroll
-                for (int q = 0; q < 21; ++q) fac[q * N3 + v] = F[q];
+                store_factors(fac, N3, v, F);
             }
         } else {
             r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
@@ -602,8 +695,23 @@ cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t 
 template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
-                               int force_refresh, int *flags, cudaStream_t s) {
+                               int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
+    if (!force_refresh && wl) {
+        // flags[10] counts the listed voxels; pass 2 reads it on the device (no host round trip)
+        cudaError_t e = cudaMemsetAsync(flags + 10, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        k_chord_first<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (const TA *)fac, mc,
+                                                          (TA)tol, flags, wl);
+        const int rb = std::min(blocks, nsm * (sizeof(TA) == 4 ? 3 : 2));
+        if (solve_fp64)
+            k_chord_rest<TA, TA, double><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
+                                                                 (TA)tol, maxit, ls_free_of<TA>(), flags, wl);
+        else
+            k_chord_rest<TA, TA, TA><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
+                                                             (TA)tol, maxit, ls_free_of<TA>(), flags, wl);
+        return cudaGetLastError();
+    }
     // factors stored in the field precision; factorised in FP64 unless the FP32 solve is asked for
     if (solve_fp64)
         k_newton_chord<TA, TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
@@ -673,7 +781,7 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
                                           const TA *, MatConst, double, int, int, int *, cudaStream_t);          \
     template cudaError_t newton_chord_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,  \
                                                 const TA *, void *, MatConst, double, int, int, int, int *,       \
-                                                cudaStream_t);                                                    \
+                                                int32_t *, int, cudaStream_t);                                    \
     template cudaError_t al_local<TA>(long, const TA *, const TA *, const TA *, const int32_t *, TA *, TA *, TA *, \
                                       const TA *, const TA *, const TA *, MatConst, double, double, double, int, int, \
                                       int, int *, double *, void *, int, cudaStream_t);                           \
