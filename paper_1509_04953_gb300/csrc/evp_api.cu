@@ -9,6 +9,7 @@
 #include <new>
 
 #include "../../include/evp.h"
+#include "common.cuh"
 #include "kernels.h"
 
 using namespace evp;
@@ -52,10 +53,12 @@ struct evp_handle {
     double prof_ms[EVP_NCLASS];
     int64_t prof_n[EVP_NCLASS];
     struct Pend { int cls; cudaEvent_t a, b; };
-    Pend pend[64];
+    static constexpr int kMaxPend = 512;   // bracketed launches awaiting collection (several queued iterations)
+    Pend pend[kMaxPend];
     int npend;
-    cudaEvent_t pool[128];
+    cudaEvent_t pool[2 * kMaxPend];
     int npool;
+    void *ctl;   // device fixed-point control block (FpCtl)
     char err[512];
     ~evp_handle() {
         std::free(adj_dE33); std::free(adj_dt); std::free(adj_E); std::free(adj_dEp); std::free(adj_hp);
@@ -90,7 +93,7 @@ cudaEvent_t ev_get(evp_handle *h) {
 }
 void ev_put(evp_handle *h, cudaEvent_t e) {
     if (!e) return;
-    if (h->npool < 128) h->pool[h->npool++] = e;
+    if (h->npool < 2 * evp_handle::kMaxPend) h->pool[h->npool++] = e;
     else cudaEventDestroy(e);
 }
 // Accumulate the device time of every bracketed launch whose events have completed.
@@ -117,7 +120,7 @@ struct ProfScope {
     ProfScope(evp_handle *h_, int c, int nk) : h(h_), cls(c) {
         h->launches += nk;
         if (h->prof) {
-            if (h->npend >= 64) {
+            if (h->npend >= evp_handle::kMaxPend) {
                 cudaStreamSynchronize(h->st);
                 prof_collect(h);
             }
@@ -189,6 +192,7 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *ids = take(K * N3 * 4), *ids2 = take(K * N3 * 4);
     char *partials = take(sizeof(double) * npart), *scal = take(sizeof(double) * 64);
     char *flags = take(sizeof(int32_t) * 16);
+    char *ctl = take(256);   // FpCtl
     char *blk_counts = take(sizeof(int32_t) * nb);
     char *blk_off = take(sizeof(int32_t) * nb + N3);   // offsets, then one mark byte per voxel
     char *count = take(sizeof(int32_t) * 4);
@@ -207,6 +211,7 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
         h->k = (double *)k; h->kappa = (double *)kappa; h->g0 = (int32_t *)g0; h->g = (int32_t *)g;
         h->gprev = (int32_t *)gprev; h->draws = (int32_t *)draws; h->ids = (int32_t *)ids; h->ids2 = (int32_t *)ids2;
         h->partials = (double *)partials; h->scal = (double *)scal; h->flags = (int32_t *)flags;
+        h->ctl = ctl;
         h->blk_counts = (int32_t *)blk_counts; h->blk_off = (int32_t *)blk_off; h->count = (int32_t *)count;
         h->bitmap = (uint32_t *)bitmap; h->bitmap_words = (int)words; h->max_ids = (int)max_ids;
         h->npartials = npart;
@@ -337,6 +342,88 @@ void *field_ptr(evp_handle *h, uint32_t bit) {
 
 // Augmented-Lagrangian iterations of one increment (after the predictor): see k_al_local.
 // Returns a status; fills the iteration count, residuals, mean stress and the macro strain increment.
+// Fixed-point control of the basic scheme, on the device. One block sums the z-pass partials of
+// |xi.sigma_hat|^2 (in the fixed order of reduce_partials); its first thread turns them and the mean stress
+// into err_eq and err_bc, decides convergence and computes the correction dE_k of the macroscopic strain on
+// the stress-controlled components. The correction goes into the zero-frequency term of the
+// Green-operator output, which the z pass leaves at zero; after the z pass's own inverse transform that
+// term is the (ky, kx) = (0, 0) entry of every z plane. The inverse y and x transforms then add it to every
+// voxel's strain. The host queues iterations in batches and reads this block once per batch; once `done`
+// is set, the kernels of the iterations still queued return at once.
+struct FpCtl {
+    int done, it, conv, status, nmax, nfail, pad0, pad1;
+    double err_eq, err_bc;
+    double dE[6];
+};
+static_assert(sizeof(FpCtl) <= 256, "FpCtl must fit its workspace slot");
+constexpr int kFpBatch = 16;   // iterations queued between host reads of the control block
+const double kZero6[6] = {0, 0, 0, 0, 0, 0};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_fp_control(FpCtl *__restrict__ c, const double *__restrict__ part, int nparts,
+                                                     double *__restrict__ scal, const int32_t *__restrict__ flags,
+                                                     typename CT<T>::type *__restrict__ spec, long fstride, int n,
+                                                     double N3, double tau0, double tol, int max_iter, double a,
+                                                     double b, double det, double mu0) {
+    __shared__ double red[32];
+    __shared__ double corr[6];
+    __shared__ int go;
+    if (c->done) return;   // uniform over the block
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        go = 0;
+        scal[6] = s;
+        const int it = c->it + 1;
+        c->it = it;
+        c->nmax = max(c->nmax, (int)flags[1]);
+        double mean[6], mn = 0.0, mu_n = 0.0;
+        for (int i = 0; i < 6; ++i) {
+            mean[i] = scal[i];
+            mn += mean[i] * mean[i];
+            if (i != 2) mu_n += mean[i] * mean[i];
+        }
+        const double den = fmax(sqrt(mn), tau0);
+        const double err_eq = sqrt(s) / (N3 * den);
+        const double err_bc = sqrt(fmax(mu_n, 0.0)) / den;
+        c->err_eq = err_eq;
+        c->err_bc = err_bc;
+        if (flags[0] != 0) {
+            c->nfail = flags[0];
+            c->status = EVP_ERR_NEWTON;
+            c->done = 1;
+        } else if (!isfinite(err_eq) || !isfinite(err_bc)) {
+            c->status = EVP_ERR_NONFINITE;
+            c->done = 1;
+        } else if (err_eq <= tol && err_bc <= tol) {
+            c->conv = 1;
+            c->done = 1;
+        } else if (it >= max_iter) {
+            c->done = 1;
+        } else {
+            double dEk[6] = {0, 0, 0, 0, 0, 0};
+            dEk[0] = (a * (-mean[0]) - b * (-mean[1])) / det;
+            dEk[1] = (-b * (-mean[0]) + a * (-mean[1])) / det;
+            for (int i = 3; i < 6; ++i) dEk[i] = -mean[i] / (2.0 * mu0);
+            for (int i = 0; i < 6; ++i) {
+                c->dE[i] += dEk[i];
+                corr[i] = dEk[i] * N3;   // the inverse transforms are unnormalised; x_c2r scales by 1/N^3
+            }
+            go = 1;
+        }
+    }
+    __syncthreads();
+    if (!go) return;
+    // after the z pass the spectrum is [field][z][ky][kx]: the (ky, kx) = (0, 0) entry of every z plane
+    const long zstride = fstride / n;
+    for (int t = threadIdx.x; t < 6 * n; t += blockDim.x) {
+        const int f = t / n, z = t - f * n;
+        auto &e = spec[f * fstride + z * zstride];
+        e.x += (T)corr[f];
+    }
+}
+
 template <typename TA>
 int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, int *nmax_out, double *err_eq,
             double *err_bc, double *mean_sig) {
@@ -640,7 +727,6 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
     double err_eq = 0, err_bc = 0, mean[6] = {0, 0, 0, 0, 0, 0};
     const int zb = fft_z_blocks(n, h->dbl);
     double hs[8];
-    int32_t hf[2];
     int64_t hcount[3] = {0, 0, 0};
     const int reuse = h->cfg.newton_mode == EVP_NEWTON_REUSE;
     // refactor every voxel's tangent at the first iteration unless valid factors are stored; always while
@@ -650,78 +736,95 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         status = h->dbl ? al_loop<double>(h, mc, dE, &it, &conv, &nmax, &err_eq, &err_bc, mean)
                         : al_loop<float>(h, mc, dE, &it, &conv, &nmax, &err_eq, &err_bc, mean);
         it = it < 1 ? 1 : it;
-    } else
-    for (it = 1; it <= h->cfg.max_iter; ++it) {
-        if (h->dbl) {
-          { PROF(0, 1);
-            if (h->cfg.newton_mode == EVP_NEWTON_F32_TANGENT)
-                CK(newton_field_df(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
-                                   (double *)h->Stab, (double *)h->Mtab, h->Stabf, h->Mtabf, mc, ntol,
-                                   h->cfg.newton_max, h->flags, h->st));
-            else if (reuse)
-                CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
-                                              (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
-                                              h->cfg.newton_max, 1, it == 1 && fresh, h->flags, h->wlist,
-                                              h->nsm, h->st));
-            else
-                CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
-                                        (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
-                                        h->flags, h->st)); }
-          { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st)); }
-          { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st)); }
-          { PROF(3, 1); CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st)); }
-        } else {
-          { PROF(0, 1);
-            if (reuse)
-                CK(newton_chord_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
-                                             (float *)h->Stab, (float *)h->Mtab, h->fac, mc, ntol, h->cfg.newton_max,
-                                             solve64, it == 1 && fresh, h->flags, h->wlist, h->nsm, h->st));
-            else
-                CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
-                                       (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,
-                                       h->flags, h->st)); }
-          { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st)); }
-          { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st)); }
-          { PROF(3, 1); CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st)); }
-        }
-        { PROF(6, 1); CK(reduce_partials(h->partials, zb, 1, h->scal + 6, h->st)); }
-        CK(cudaMemcpyAsync(hs, h->scal, sizeof(double) * 7, cudaMemcpyDeviceToHost, h->st));
-        CK(cudaMemcpyAsync(hf, h->flags, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        if (h->prof) prof_collect(h);
-        nmax = hf[1] > nmax ? hf[1] : nmax;
-        if (hf[0] != 0) {
-            status = fail(h, EVP_ERR_NEWTON, "local Newton failed in %d voxels at iteration %d", hf[0], it);
-            break;
-        }
-        for (int i = 0; i < 6; ++i) mean[i] = hs[i];
-        double mn = 0, mu_n = 0;
-        for (int i = 0; i < 6; ++i) {
-            mn += mean[i] * mean[i];
-            if (i != 2) mu_n += mean[i] * mean[i];
-        }
-        const double den = std::fmax(std::sqrt(mn), h->p.tau0);
-        err_eq = std::sqrt(hs[6]) / ((double)N3 * den);
-        err_bc = std::sqrt(std::fmax(mu_n, 0.0)) / den;
-        if (!std::isfinite(err_eq) || !std::isfinite(err_bc)) {
-            status = fail(h, EVP_ERR_NONFINITE, "non-finite residual at iteration %d", it);
-            break;
-        }
-        if (err_eq <= h->cfg.tol && err_bc <= h->cfg.tol) { conv = 1; break; }
-        if (it == h->cfg.max_iter) break;
-        double dEk[6] = {0, 0, 0, 0, 0, 0};
-        dEk[0] = (a * (-mean[0]) - b * (-mean[1])) / det;
-        dEk[1] = (-b * (-mean[0]) + a * (-mean[1])) / det;
-        for (int i = 3; i < 6; ++i) dEk[i] = -mean[i] / (2.0 * mu0);
-        for (int i = 0; i < 6; ++i) dE[i] += dEk[i];
+    } else {
+        // iterations are queued in batches; the device control decides when to stop (see k_fp_check)
+        FpCtl hc{};
+        for (int i = 0; i < 6; ++i) hc.dE[i] = dE[i];
+        FpCtl *dc = (FpCtl *)h->ctl;
+        const int *skip = &dc->done;
+        CK(cudaMemcpyAsync(dc, &hc, sizeof hc, cudaMemcpyHostToDevice, h->st));
         const double inv = 1.0 / (double)N3;
-        if (h->dbl) {
-            { PROF(4, 1); CK(fft_y<double>(h->spec, n, 6, 1, h->st)); }
-            { PROF(5, 1); CK(fft_x_c2r<double>(h->spec, (double *)h->epst, n, 6, inv, dEk, h->st)); }
-        } else {
-            { PROF(4, 1); CK(fft_y<float>(h->spec, n, 6, 1, h->st)); }
-            { PROF(5, 1); CK(fft_x_c2r<float>(h->spec, (float *)h->epst, n, 6, (float)inv, dEk, h->st)); }
+        int queued = 0;
+        while (true) {
+            const int nb = std::min(kFpBatch, h->cfg.max_iter - queued);
+            for (int q = 0; q < nb; ++q) {
+                const int first = queued + q == 0 && fresh;
+                if (h->dbl) {
+                  { PROF(0, 1);
+                    if (h->cfg.newton_mode == EVP_NEWTON_F32_TANGENT)
+                        CK(newton_field_df(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
+                                           (double *)h->Stab, (double *)h->Mtab, h->Stabf, h->Mtabf, mc, ntol,
+                                           h->cfg.newton_max, h->flags, h->st, skip));
+                    else if (reuse)
+                        CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
+                                                      (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
+                                                      h->cfg.newton_max, 1, first, h->flags, h->wlist, h->nsm, h->st,
+                                                      skip));
+                    else
+                        CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
+                                                (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
+                                                h->flags, h->st, skip)); }
+                  { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st, skip)); }
+                  { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st, skip)); }
+                  { PROF(3, 1);
+                    CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip)); }
+                } else {
+                  { PROF(0, 1);
+                    if (reuse)
+                        CK(newton_chord_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
+                                                     (float *)h->Stab, (float *)h->Mtab, h->fac, mc, ntol,
+                                                     h->cfg.newton_max, solve64, first, h->flags, h->wlist, h->nsm,
+                                                     h->st, skip));
+                    else
+                        CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
+                                               (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,
+                                               h->flags, h->st, skip)); }
+                  { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st, skip)); }
+                  { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st, skip)); }
+                  { PROF(3, 1);
+                    CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip)); }
+                }
+                { PROF(6, 1);
+                  if (h->dbl)
+                      k_fp_control<double><<<1, 1024, 0, h->st>>>(dc, h->partials, zb, h->scal, h->flags,
+                                                                  (double2 *)h->spec, h->H, n, (double)N3, h->p.tau0,
+                                                                  h->cfg.tol, h->cfg.max_iter, a, b, det, mu0);
+                  else
+                      k_fp_control<float><<<1, 1024, 0, h->st>>>(dc, h->partials, zb, h->scal, h->flags,
+                                                                 (float2 *)h->spec, h->H, n, (double)N3, h->p.tau0,
+                                                                 h->cfg.tol, h->cfg.max_iter, a, b, det, mu0);
+                  CK(cudaGetLastError()); }
+                // the strain correction arrives through the zero-frequency term: no offsets here
+                if (h->dbl) {
+                    { PROF(4, 1); CK(fft_y<double>(h->spec, n, 6, 1, h->st, skip)); }
+                    { PROF(5, 1);
+                      CK(fft_x_c2r<double>(h->spec, (double *)h->epst, n, 6, inv, kZero6, h->st, nullptr, skip)); }
+                } else {
+                    { PROF(4, 1); CK(fft_y<float>(h->spec, n, 6, 1, h->st, skip)); }
+                    { PROF(5, 1);
+                      CK(fft_x_c2r<float>(h->spec, (float *)h->epst, n, 6, (float)inv, kZero6, h->st, nullptr, skip)); }
+                }
+            }
+            queued += nb;
+            CK(cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, h->st));
+            CK(cudaMemcpyAsync(hs, h->scal, sizeof(double) * 7, cudaMemcpyDeviceToHost, h->st));
+            CK(cudaStreamSynchronize(h->st));
+            if (h->prof) prof_collect(h);
+            if (hc.done || queued >= h->cfg.max_iter) break;
         }
+        it = hc.it;
+        conv = hc.conv;
+        nmax = hc.nmax;
+        err_eq = hc.err_eq;
+        err_bc = hc.err_bc;
+        for (int i = 0; i < 6; ++i) {
+            dE[i] = hc.dE[i];
+            mean[i] = hs[i];
+        }
+        if (hc.status == EVP_ERR_NEWTON)
+            status = fail(h, EVP_ERR_NEWTON, "local Newton failed in %d voxels at iteration %d", hc.nfail, it);
+        else if (hc.status == EVP_ERR_NONFINITE)
+            status = fail(h, EVP_ERR_NONFINITE, "non-finite residual at iteration %d", it);
     }
     if (it > h->cfg.max_iter) it = h->cfg.max_iter;
     // after a first increment without a local failure every voxel holds factors of an SPD tangent; later

@@ -199,7 +199,8 @@ template <int N, typename T> __host__ __device__ constexpr int z_threads() { ret
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out,
-                                                       long npairs) {
+                                                       long npairs, const int *__restrict__ skip) {
+    if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -235,7 +236,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
                                                        long npairs, T scale, int has_add, T a0, T a1, T a2, T a3, T a4,
-                                                       T a5, const T *__restrict__ base) {
+                                                       T a5, const T *__restrict__ base, const int *__restrict__ skip) {
+    if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -282,7 +284,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
 // y pass: CTA = (field, z, kx tile of TX columns); lines along y.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(y_threads<N, T>()) k_fft_y(typename CT<T>::type *__restrict__ spec) {
+__global__ void __launch_bounds__(y_threads<N, T>()) k_fft_y(typename CT<T>::type *__restrict__ spec, const int *__restrict__ skip) {
+    if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int TX = tx_y<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -388,7 +391,8 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N>
 __global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
-                                                   T mu0, double *__restrict__ partials, double *__restrict__ mean6) {
+                                                   T mu0, double *__restrict__ partials, double *__restrict__ mean6, const int *__restrict__ skip) {
+    if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int TX = tx_z<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1, MI = maxit<N>(6 * (TX + 1), z_threads<N, T>());
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -467,19 +471,20 @@ template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int N> cudaError_t x_r2c_n(const T *in, void *spec, int nfields, cudaStream_t s) {
+template <typename T, int N> cudaError_t x_r2c_n(const T *in, void *spec, int nfields, cudaStream_t s, const int *skip) {
     using C = typename CT<T>::type;
     const long npairs = (long)nfields * N * N / 2;
     const int blocks = (int)((npairs + rowpairs<N>() - 1) / rowpairs<N>());
     const size_t sm = smem_x<T, N>();
     cudaError_t e = allow_smem(k_fft_x_r2c<T, N>, sm);
     if (e != cudaSuccess) return e;
-    k_fft_x_r2c<T, N><<<blocks, kThreads, sm, s>>>(in, (C *)spec, npairs);
+    k_fft_x_r2c<T, N><<<blocks, kThreads, sm, s>>>(in, (C *)spec, npairs, skip);
     return cudaGetLastError();
 }
 
 template <typename T, int N>
-cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double *add6, cudaStream_t s, const T *base) {
+cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double *add6, cudaStream_t s, const T *base,
+                    const int *skip) {
     using C = typename CT<T>::type;
     const long npairs = (long)nfields * N * N / 2;
     const int blocks = (int)((npairs + rowpairs<N>() - 1) / rowpairs<N>());
@@ -489,33 +494,35 @@ cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double
     T a[6] = {0, 0, 0, 0, 0, 0};   // rounded to the field precision here, not once per element on the device
     if (add6)
         for (int i = 0; i < 6; ++i) a[i] = (T)add6[i];
-    k_fft_x_c2r<T, N><<<blocks, kThreads, sm, s>>>((const C *)spec, out, npairs, scale, add6 != nullptr, a[0], a[1],
-                                                   a[2], a[3], a[4], a[5], base);
+    const int has_add = add6 != nullptr;
+    k_fft_x_c2r<T, N><<<blocks, kThreads, sm, s>>>((const C *)spec, out, npairs, scale, has_add, a[0], a[1], a[2], a[3],
+                                                   a[4], a[5], base, skip);
     return cudaGetLastError();
 }
 
-template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int inverse, cudaStream_t s) {
+template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int inverse, cudaStream_t s, const int *skip) {
     using C = typename CT<T>::type;
     constexpr int TX = tx_y<N, T>();
     const int blocks = nfields * N * ((N / 2) / TX);
     const size_t sm = smem_y<T, N>();
     cudaError_t e = inverse ? allow_smem(k_fft_y<T, N, true>, sm) : allow_smem(k_fft_y<T, N, false>, sm);
     if (e != cudaSuccess) return e;
-    if (inverse) k_fft_y<T, N, true><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec);
-    else k_fft_y<T, N, false><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec);
+    if (inverse) k_fft_y<T, N, true><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec, skip);
+    else k_fft_y<T, N, false><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec, skip);
     return cudaGetLastError();
 }
 
 template <typename T, int N>
 cudaError_t z_n(void *spec, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
-                cudaStream_t s) {
+                cudaStream_t s, const int *skip) {
     using C = typename CT<T>::type;
     constexpr int TX = tx_z<N, T>();
     const int blocks = N * ((N / 2) / TX);
     const size_t sm = smem_z<T, N>(nfields);
     cudaError_t e = allow_smem(k_fft_z<T, N>, smem_z<T, N>(6));
     if (e != cudaSuccess) return e;
-    k_fft_z<T, N><<<blocks, z_threads<N, T>(), sm, s>>>((C *)spec, nfields, mode, (T)lam0, (T)mu0, partials, mean6);
+    k_fft_z<T, N><<<blocks, z_threads<N, T>(), sm, s>>>((C *)spec, nfields, mode, (T)lam0, (T)mu0, partials, mean6,
+                                                       skip);
     return cudaGetLastError();
 }
 
@@ -539,36 +546,37 @@ int fft_z_blocks(int n, int is_double) {
     return n * ((n / 2) / TX);
 }
 
-template <typename T> cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s) {
-    EVP_DISPATCH(n, (x_r2c_n<T, NN>(in, spec, nfields, s)))
+template <typename T>
+cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s, const int *skip) {
+    EVP_DISPATCH(n, (x_r2c_n<T, NN>(in, spec, nfields, s, skip)))
 }
 
 template <typename T>
 cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6, cudaStream_t s,
-                      const T *base) {
-    EVP_DISPATCH(n, (x_c2r_n<T, NN>(spec, out, nfields, scale, add6, s, base)))
+                      const T *base, const int *skip) {
+    EVP_DISPATCH(n, (x_c2r_n<T, NN>(spec, out, nfields, scale, add6, s, base, skip)))
 }
 
-template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s) {
-    EVP_DISPATCH(n, (y_n<T, NN>(spec, nfields, inverse, s)))
+template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s, const int *skip) {
+    EVP_DISPATCH(n, (y_n<T, NN>(spec, nfields, inverse, s, skip)))
 }
 
 template <typename T>
 cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
-                  cudaStream_t s) {
+                  cudaStream_t s, const int *skip) {
     if ((mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) && nfields != 6) return cudaErrorInvalidValue;
-    EVP_DISPATCH(n, (z_n<T, NN>(spec, nfields, mode, lam0, mu0, partials, mean6, s)))
+    EVP_DISPATCH(n, (z_n<T, NN>(spec, nfields, mode, lam0, mu0, partials, mean6, s, skip)))
 }
 
-template cudaError_t fft_x_r2c<float>(const float *, void *, int, int, cudaStream_t);
-template cudaError_t fft_x_r2c<double>(const double *, void *, int, int, cudaStream_t);
-template cudaError_t fft_x_c2r<float>(const void *, float *, int, int, float, const double *, cudaStream_t,
-                                      const float *);
-template cudaError_t fft_x_c2r<double>(const void *, double *, int, int, double, const double *, cudaStream_t,
-                                       const double *);
-template cudaError_t fft_y<float>(void *, int, int, int, cudaStream_t);
-template cudaError_t fft_y<double>(void *, int, int, int, cudaStream_t);
-template cudaError_t fft_z<float>(void *, int, int, int, double, double, double *, double *, cudaStream_t);
-template cudaError_t fft_z<double>(void *, int, int, int, double, double, double *, double *, cudaStream_t);
+#define EVP_FFT_INST(T)                                                                                            \
+    template cudaError_t fft_x_r2c<T>(const T *, void *, int, int, cudaStream_t, const int *);                     \
+    template cudaError_t fft_x_c2r<T>(const void *, T *, int, int, T, const double *, cudaStream_t, const T *,     \
+                                      const int *);                                                                \
+    template cudaError_t fft_y<T>(void *, int, int, int, cudaStream_t, const int *);                               \
+    template cudaError_t fft_z<T>(void *, int, int, int, double, double, double *, double *, cudaStream_t,         \
+                                  const int *);
+EVP_FFT_INST(float)
+EVP_FFT_INST(double)
+#undef EVP_FFT_INST
 
 }  // namespace evp

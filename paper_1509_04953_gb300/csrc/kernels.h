@@ -16,16 +16,20 @@ struct MatConst {
 
 // ---- fft.cu ----
 enum ZMode { Z_FWD = 0, Z_INV = 1, Z_FWD_GAMMA_INV = 2, Z_FWD_RESID = 3 };
-template <typename T> cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s);
-template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s);
+// skip (optional, device): when *skip != 0 the launched kernel returns at once (a converged fixed point
+// whose remaining queued iterations are discarded).
+template <typename T>
+cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s, const int *skip = nullptr);
+template <typename T>
+cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s, const int *skip = nullptr);
 template <typename T>
 cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials,
-                  double *mean6, cudaStream_t s);
-// x-pass complex-to-real. If add != nullptr: out[c] = (base ? base[c] : out[c]) + scale * field + add[c];
+                  double *mean6, cudaStream_t s, const int *skip = nullptr);
+// x-pass complex-to-real. If add6 != nullptr: out[c] = (base ? base[c] : out[c]) + scale * field + add6[c];
 // else out = field.
 template <typename T>
 cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6,
-                      cudaStream_t s, const T *base = nullptr);
+                      cudaStream_t s, const T *base = nullptr, const int *skip = nullptr);
 int fft_z_blocks(int n, int is_double);
 
 // ---- newton.cu ----
@@ -33,18 +37,21 @@ int fft_z_blocks(int n, int is_double);
 template <typename TA>
 cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                          const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
-                         cudaStream_t s);
+                         cudaStream_t s,
+                         const int *skip = nullptr);
 // Jacobian-reuse variant: fac holds 21 factor words per voxel in TA (factorised in FP64 if solve_fp64).
 // Unless force_refresh, runs in two passes with the work list wl (N3 entries, count in flags[10]);
 // nsm = multiprocessors, for the grid of the second pass.
 template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
-                               int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s);
+                               int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s,
+                               const int *skip = nullptr);
 // FP64 residual / FP32 tangent Newton (FP64 path); Stabf / Mtabf are FP32 copies of the tables.
 cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
                             const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,
-                            MatConst mc, double tol, int maxit, int *flags, cudaStream_t s);
+                            MatConst mc, double tol, int maxit, int *flags, cudaStream_t s,
+                            const int *skip = nullptr);
 // Augmented-Lagrangian local step; part: 14 doubles per block (al_blocks blocks).
 int al_blocks(long N3);
 template <typename TA>
@@ -100,6 +107,7 @@ int pf_stat_blocks(long N3);
 template <typename T>
 cudaError_t pf_stats_launch(int n, const int32_t *ids, const T *eta, const int32_t *g, const double *k, PFConst pc,
                      uint32_t *bitmap, int bitmap_words, double *partials, cudaStream_t s);
-cudaError_t reduce_partials(const double *partials, int nparts, int nvals, double *out, cudaStream_t s);
+cudaError_t reduce_partials(const double *partials, int nparts, int nvals, double *out, cudaStream_t s,
+                            const int *skip = nullptr);
 
 }  // namespace evp

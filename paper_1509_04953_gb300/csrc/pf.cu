@@ -233,7 +233,9 @@ __global__ void k_popc(const uint32_t *__restrict__ bitmap, int words, double *_
 }
 
 // Deterministic sum of partials [nparts][nvals] -> out[nvals]: one block per column, fixed order.
-__global__ void k_reduce(const double *__restrict__ part, int nparts, int nvals, double *__restrict__ out) {
+__global__ void k_reduce(const double *__restrict__ part, int nparts, int nvals, double *__restrict__ out,
+                         const int *__restrict__ skip) {
+    if (skip != nullptr && *skip) return;
     __shared__ double red[32];
     const int c = blockIdx.x;
     double s = 0.0;
@@ -275,8 +277,9 @@ cudaError_t pf_stats_launch(int n, const int32_t *ids, const T *eta, const int32
     return cudaGetLastError();
 }
 
-cudaError_t reduce_partials(const double *partials, int nparts, int nvals, double *out, cudaStream_t s) {
-    k_reduce<<<nvals, 1024, 0, s>>>(partials, nparts, nvals, out);
+cudaError_t reduce_partials(const double *partials, int nparts, int nvals, double *out, cudaStream_t s,
+                            const int *skip) {
+    k_reduce<<<nvals, 1024, 0, s>>>(partials, nparts, nvals, out, skip);
     return cudaGetLastError();
 }
 
