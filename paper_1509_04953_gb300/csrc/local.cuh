@@ -16,12 +16,14 @@ __device__ __forceinline__ double drcp(double x) { return __drcp_rn(x); }
 // |x|^(n-1) for the power law; fast path for small integer n (exponentiation by squaring).
 template <typename T> __device__ __forceinline__ T pow_nm1(T ax, const MatConst &mc) {
     if (mc.n_int > 0) {
-        int e = mc.n_int - 1;
+        // branch-free: the same products in the same order as the bit loop, over all six bits of
+        // e <= 63 (selects instead of branches, so independent slip systems can be interleaved)
+        const int e = mc.n_int - 1;
         T r = (T)1, b = ax;
-        while (e) {
-            if (e & 1) r *= b;
-            b *= b;
-            e >>= 1;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            r = ((e >> k) & 1) ? r * b : r;
+            b = b * b;
         }
         return r;
     }
