@@ -20,6 +20,40 @@ namespace {
 
 constexpr int kThreads = 128;
 
+// Local-solve statistics, summed over the block before they touch the shared counters (the same-address
+// atomics of every warp of a two-million-voxel launch serialise in L2): flags[0] += failed voxels,
+// flags[1] = max(local iterations); 64-bit flags[4..5] += iterations (6x6 solves), [6..7] += residual
+// evaluations, [8..9] += tangent refreshes. Every thread of the block calls it once.
+__device__ __forceinline__ void block_solve_stats(int fail, int maxit, int it, int ev, int rf, int *flags) {
+    __shared__ int sh[kThreads / 32][5];
+    int f = fail, mx = maxit, sit = it, sev = ev, srf = rf;
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_xor_sync(0xffffffffu, f, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sit += __shfl_xor_sync(0xffffffffu, sit, o);
+        sev += __shfl_xor_sync(0xffffffffu, sev, o);
+        srf += __shfl_xor_sync(0xffffffffu, srf, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[w][0] = f; sh[w][1] = mx; sh[w][2] = sit; sh[w][3] = sev; sh[w][4] = srf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tf = 0, tm = 0;
+        unsigned long long ti = 0, te = 0, tr = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            tf += sh[k][0]; tm = max(tm, sh[k][1]);
+            ti += (unsigned)sh[k][2]; te += (unsigned)sh[k][3]; tr += (unsigned)sh[k][4];
+        }
+        if (tf) atomicAdd(flags, tf);
+        if (tm) atomicMax(flags + 1, tm);
+        if (ti) atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), ti);
+        if (te) atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), te);
+        if (tr) atomicAdd(reinterpret_cast<unsigned long long *>(flags + 8), tr);
+    }
+}
+
 // Damped Newton on one voxel. Returns the iteration count (> 0) or minus it on failure.
 template <typename TA, typename TS>
 __device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA sg[6],
@@ -92,23 +126,8 @@ __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restri
 #pragma unroll
         for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
     }
-    // warp-aggregated flag updates (blockDim is a multiple of 32; every lane reaches here)
-    __syncwarp();
-    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
-    int mx = valid ? (r < 0 ? -r : r) : 0;
-    int sit = valid ? mx : 0, sev = nev;
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        sit += __shfl_xor_sync(0xffffffffu, sit, o);
-        sev += __shfl_xor_sync(0xffffffffu, sev, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (fmask) atomicAdd(flags, __popc(fmask));
-        atomicMax(flags + 1, mx);
-        // flags[4..5] and [6..7] hold 64-bit totals of local iterations (= 6x6 solves) and evaluations
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
-    }
+    const int its = valid ? (r < 0 ? -r : r) : 0;
+    block_solve_stats(valid && r < 0, its, its, nev, 0, flags);
 }
 
 // FP64 path: Newton on the FP64 residual with an FP32 tangent and FP32 6x6 solve. Each step is a
@@ -191,21 +210,8 @@ __global__ void __launch_bounds__(kThreads) k_newton_df(long N3, const double *_
 #pragma unroll
         for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
     }
-    __syncwarp();
-    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
-    int mx = valid ? (r < 0 ? -r : r) : 0;
-    int sit = valid ? mx : 0, sev = nev;
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        sit += __shfl_xor_sync(0xffffffffu, sit, o);
-        sev += __shfl_xor_sync(0xffffffffu, sev, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (fmask) atomicAdd(flags, __popc(fmask));
-        atomicMax(flags + 1, mx);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
-    }
+    const int its = valid ? (r < 0 ? -r : r) : 0;
+    block_solve_stats(valid && r < 0, its, its, nev, 0, flags);
 }
 
 // Local solve with Jacobian reuse (chord Newton): the LDL^T factors of the tangent are stored per
@@ -321,23 +327,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
             store_factors(fac, N3, v, F);
         }
     }
-    __syncwarp();
-    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
-    int mx = valid ? (r < 0 ? -r : r) : 0;
-    int sit = valid ? mx : 0, sev = nev, srf = nref;
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        sit += __shfl_xor_sync(0xffffffffu, sit, o);
-        sev += __shfl_xor_sync(0xffffffffu, sev, o);
-        srf += __shfl_xor_sync(0xffffffffu, srf, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (fmask) atomicAdd(flags, __popc(fmask));
-        atomicMax(flags + 1, mx);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 8), (unsigned long long)srf);
-    }
+    const int its = valid ? (r < 0 ? -r : r) : 0;
+    block_solve_stats(valid && r < 0, its, its, nev, nref, flags);
 }
 
 // Tangent reuse in two passes. Most voxels accept the first chord step once the fixed point has
@@ -390,20 +381,12 @@ __global__ void __launch_bounds__(kThreads) k_chord_first(long N3, const TA *__r
         }
     }
     const unsigned todo = __ballot_sync(0xffffffffu, valid && !done);
-    const unsigned ndone = __popc(__ballot_sync(0xffffffffu, done));
     const int lane = threadIdx.x & 31;
     int base = 0;
     if (lane == 0 && todo) base = atomicAdd(flags + 10, __popc(todo));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (valid && !done) wl[base + __popc(todo & ((1u << lane) - 1u))] = (int32_t)v;
-    if (lane == 0) {
-        // accepted voxels: one evaluation and one solve each, iteration count 1
-        if (ndone) {
-            atomicMax(flags + 1, 1);
-            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)ndone);
-            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)ndone);
-        }
-    }
+    // the accepted voxels (one evaluation and one solve each) are counted by pass 2 as N3 - listed
 }
 
 template <typename TA, typename TS, typename TF>
@@ -413,8 +396,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_res
     TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int32_t *__restrict__ wl, const int *__restrict__ skip) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     const int count = *(volatile const int *)(flags + 10);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && N3 - count > 0) {   // pass 1 accepted the others in one step
+        atomicMax(flags + 1, 1);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)(N3 - count));
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)(N3 - count));
+    }
     const long stride = (long)gridDim.x * blockDim.x;
-    for (long w0 = (long)blockIdx.x * blockDim.x; w0 < count; w0 += stride) {   // warp-uniform trip count
+    int t_fail = 0, t_mx = 0, t_it = 0, t_ev = 0, t_rf = 0;
+    for (long w0 = (long)blockIdx.x * blockDim.x; w0 < count; w0 += stride) {   // block-uniform trip count
         const long w = w0 + threadIdx.x;
         const bool valid = w < count;
         int r = 1, nev = 0, nref = 0;
@@ -439,23 +428,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_res
                 store_factors(fac, N3, v, F);
             }
         }
-        const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
-        int mx = valid ? (r < 0 ? -r : r) : 0;
-        int sit = valid ? mx : 0, sev = nev, srf = nref;
-        for (int o = 16; o > 0; o >>= 1) {
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            sit += __shfl_xor_sync(0xffffffffu, sit, o);
-            sev += __shfl_xor_sync(0xffffffffu, sev, o);
-            srf += __shfl_xor_sync(0xffffffffu, srf, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            if (fmask) atomicAdd(flags, __popc(fmask));
-            atomicMax(flags + 1, mx);
-            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
-            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
-            atomicAdd(reinterpret_cast<unsigned long long *>(flags + 8), (unsigned long long)srf);
+        if (valid) {
+            const int it = r < 0 ? -r : r;
+            t_fail += r < 0;
+            t_mx = max(t_mx, it);
+            t_it += it;
+            t_ev += nev;
+            t_rf += nref;
         }
     }
+    block_solve_stats(t_fail, t_mx, t_it, t_ev, t_rf, flags);
 }
 
 // Augmented-Lagrangian local step (the solver the paper names, Sec. 2.1, after Michel et al.):
@@ -574,21 +556,8 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
         }
     }
     // flags as in k_newton
-    __syncwarp();
-    const unsigned fmask = __ballot_sync(0xffffffffu, valid && r < 0);
-    int mx = valid ? (r < 0 ? -r : r) : 0;
-    int sit = valid ? mx : 0, sev = nev;
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        sit += __shfl_xor_sync(0xffffffffu, sit, o);
-        sev += __shfl_xor_sync(0xffffffffu, sev, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (fmask) atomicAdd(flags, __popc(fmask));
-        atomicMax(flags + 1, mx);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)sit);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)sev);
-    }
+    const int its = valid ? (r < 0 ? -r : r) : 0;
+    block_solve_stats(valid && r < 0, its, its, nev, 0, flags);
     block_sums<NV>(sums, red, part + NV * (long)blockIdx.x);
 }
 
