@@ -252,7 +252,8 @@ int evp_stress_residual(int n, int precision, const void *sig_dev, void *spec_de
 int evp_stress_residual_noalloc(int n, int precision, const void *sig_dev, void *spec_dev, double *out_dev,
                                 void *cuda_stream);
 
-/* inverse (complex-to-real) of evp_rfft3d, unnormalised: out = N^3 * field. in is overwritten. */
+/* inverse (complex-to-real) of evp_rfft3d, unnormalised: out = N^3 * field. in is overwritten.
+ * in_dev and out_dev must be 16-byte aligned (EVP_ERR_ARG otherwise). */
 int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, void *cuda_stream);
 
 #ifdef __cplusplus

@@ -367,20 +367,29 @@ __global__ void __launch_bounds__(1024) k_fp_control(FpCtl *__restrict__ c, cons
                                                      double b, double det, double mu0) {
     __shared__ double red[32];
     __shared__ double corr[6];
+    __shared__ double meanv[6];
+    __shared__ int iv[4];
     __shared__ int go;
     if (c->done) return;   // uniform over the block
+    // operands of the decision fetched by separate threads, alongside the reduction (one thread
+    // fetching them one after another would wait out each load's latency in turn)
+    if (threadIdx.x < 6) meanv[threadIdx.x] = scal[threadIdx.x];
+    else if (threadIdx.x == 32) iv[0] = c->it;
+    else if (threadIdx.x == 33) iv[1] = c->nmax;
+    else if (threadIdx.x == 34) iv[2] = flags[0];
+    else if (threadIdx.x == 35) iv[3] = flags[1];
     double s = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
-    s = block_sum(s, red);
+    s = block_sum(s, red);   // its barriers also publish meanv and iv
     if (threadIdx.x == 0) {
         go = 0;
         scal[6] = s;
-        const int it = c->it + 1;
+        const int it = iv[0] + 1;
         c->it = it;
-        c->nmax = max(c->nmax, (int)flags[1]);
+        c->nmax = max(iv[1], iv[3]);
         double mean[6], mn = 0.0, mu_n = 0.0;
         for (int i = 0; i < 6; ++i) {
-            mean[i] = scal[i];
+            mean[i] = meanv[i];
             mn += mean[i] * mean[i];
             if (i != 2) mu_n += mean[i] * mean[i];
         }
@@ -389,8 +398,8 @@ __global__ void __launch_bounds__(1024) k_fp_control(FpCtl *__restrict__ c, cons
         const double err_bc = sqrt(fmax(mu_n, 0.0)) / den;
         c->err_eq = err_eq;
         c->err_bc = err_bc;
-        if (flags[0] != 0) {
-            c->nfail = flags[0];
+        if (iv[2] != 0) {
+            c->nfail = iv[2];
             c->status = EVP_ERR_NEWTON;
             c->done = 1;
         } else if (!isfinite(err_eq) || !isfinite(err_bc)) {
@@ -1051,6 +1060,7 @@ int evp_rfft3d(int n, int precision, int nfields, const void *in_dev, void *out_
 
 int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, void *cuda_stream) {
     if (!pow2(n) || nfields < 1 || nfields > 6 || !in_dev || !out_dev) return EVP_ERR_ARG;
+    if (((uintptr_t)in_dev | (uintptr_t)out_dev) & 15) return EVP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e;
     if (precision == EVP_FP64) {

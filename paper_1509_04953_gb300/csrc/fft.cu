@@ -13,6 +13,7 @@
 // natural order in and out. Shared-memory lines are padded (one slot per 16) so that the strided
 // pass-1 writes hit distinct banks.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 
 #include "common.cuh"
@@ -231,31 +232,52 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in
 }
 
 // ---------------------------------------------------------------------------------------------
-// x pass, half spectrum -> real (complex-to-real through the same row-pair packing).
+// x pass, half spectrum -> real (complex-to-real through the same row-pair packing). The CTA's rows
+// are contiguous in both the half spectrum and the strain, so both arrive by 16-byte asynchronous
+// copies into shared memory before the transform; every global access is then a wide, coalesced one.
 // ---------------------------------------------------------------------------------------------
+template <int N> __host__ __device__ constexpr int rowpairs_c2r() { return rowpairs<N>() > 16 ? 16 : rowpairs<N>(); }
+
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
                                                        long npairs, T scale, int has_add, T a0, T a1, T a2, T a3, T a4,
                                                        T a5, const T *__restrict__ base, const int *__restrict__ skip) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
-    constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
+    constexpr int RP = rowpairs_c2r<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *buf = tw + N;
-    load_tw(tw, N);
+    C *buf = tw + N;                          // RP packed lines
+    C *hs = buf + RP * LS;                    // 2 RP half-spectrum rows, row-major
+    T *bs = reinterpret_cast<T *>(hs + 2 * RP * Hx);   // 2 RP strain rows (with has_add)
     const long p0 = (long)blockIdx.x * RP;
     const int np = (int)min((long)RP, npairs - p0);
+    {   // rows 2 p0 .. 2 (p0 + np) - 1: contiguous, 16-byte aligned (2 Hx sizeof(C) and 2 N sizeof(T) are)
+        const uint4 *src = reinterpret_cast<const uint4 *>(spec + 2 * p0 * Hx);
+        uint4 *dst = reinterpret_cast<uint4 *>(hs);
+        const int nchunk = (int)(2 * np * Hx * sizeof(C) / 16);
+        for (int t = threadIdx.x; t < nchunk; t += blockDim.x) cp_async<16>(dst + t, src + t);
+        if (has_add) {
+            const T *bsrc = base ? base : out;
+            const uint4 *src2 = reinterpret_cast<const uint4 *>(bsrc + 2 * p0 * N);
+            uint4 *dst2 = reinterpret_cast<uint4 *>(bs);
+            const int nchunk2 = (int)(2 * np * N * sizeof(T) / 16);
+            for (int t = threadIdx.x; t < nchunk2; t += blockDim.x) cp_async<16>(dst2 + t, src2 + t);
+        }
+    }
+    load_tw(tw, N);
+    cp_async_wait_all();
+    __syncthreads();
     for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
         const int pl = t / N, k = t - pl * N;
-        const long row0 = 2 * (p0 + pl);
+        const C *ra = hs + 2 * pl * Hx, *rb = ra + Hx;
         C A, B;
         if (k <= (N >> 1)) {
-            A = spec[row0 * Hx + k];
-            B = spec[(row0 + 1) * Hx + k];
+            A = ra[k];
+            B = rb[k];
         } else {
-            A = cconj(spec[row0 * Hx + (N - k)]);
-            B = cconj(spec[(row0 + 1) * Hx + (N - k)]);
+            A = cconj(ra[N - k]);
+            B = cconj(rb[N - k]);
         }
         buf[pl * LS + pad16(k)] = cmk<C>(A.x - B.y, A.y + B.x);   // A + iB
     }
@@ -269,10 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
         if (has_add) {
             const int f = (int)(row0 / rows_per_field);
             const T add = f == 0 ? a0 : f == 1 ? a1 : f == 2 ? a2 : f == 3 ? a3 : f == 4 ? a4 : a5;
-            const T b0 = base ? base[row0 * N + j] : out[row0 * N + j];
-            const T b1 = base ? base[(row0 + 1) * N + j] : out[(row0 + 1) * N + j];
-            out[row0 * N + j] = b0 + (z.x * scale + add);
-            out[(row0 + 1) * N + j] = b1 + (z.y * scale + add);
+            out[row0 * N + j] = bs[2 * pl * N + j] + (z.x * scale + add);
+            out[(row0 + 1) * N + j] = bs[(2 * pl + 1) * N + j] + (z.y * scale + add);
         } else {
             out[row0 * N + j] = z.x;
             out[(row0 + 1) * N + j] = z.y;
@@ -487,8 +507,10 @@ cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double
                     const int *skip) {
     using C = typename CT<T>::type;
     const long npairs = (long)nfields * N * N / 2;
-    const int blocks = (int)((npairs + rowpairs<N>() - 1) / rowpairs<N>());
-    const size_t sm = smem_x<T, N>();
+    constexpr int RP = rowpairs_c2r<N>();
+    const int blocks = (int)((npairs + RP - 1) / RP);
+    const size_t sm = sizeof(C) * (N + (size_t)RP * Shape<N>::LS + 2 * (size_t)RP * (N / 2 + 1)) +
+                      sizeof(T) * 2 * (size_t)RP * N;
     cudaError_t e = allow_smem(k_fft_x_c2r<T, N>, sm);
     if (e != cudaSuccess) return e;
     T a[6] = {0, 0, 0, 0, 0, 0};   // rounded to the field precision here, not once per element on the device
@@ -554,6 +576,8 @@ cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t 
 template <typename T>
 cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6, cudaStream_t s,
                       const T *base, const int *skip) {
+    // the pass copies whole rows in 16-byte chunks
+    if (((uintptr_t)spec | (uintptr_t)out | (uintptr_t)base) & 15) return cudaErrorInvalidValue;
     EVP_DISPATCH(n, (x_c2r_n<T, NN>(spec, out, nfields, scale, add6, s, base, skip)))
 }
 

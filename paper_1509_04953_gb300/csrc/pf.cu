@@ -182,7 +182,15 @@ __global__ void __launch_bounds__(256) k_pf_stats(int n, const int32_t *__restri
         const int K = pc.K, G = pc.G;
         const int gi = g[v];
         if (gi >= G) rex = 1.0;
-        if (gi >= 0 && (gi >> 5) < bitmap_words) atomicOr(bitmap + (gi >> 5), 1u << (gi & 31));
+        // one atomic per distinct id of the warp, and none once the bit is set: neighbouring voxels share
+        // their ids, and same-address atomics from every voxel serialise
+        const bool ok = gi >= 0 && (gi >> 5) < bitmap_words;
+        const unsigned peers = __match_any_sync(__activemask(), ok ? gi : -1);
+        if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) {
+            uint32_t *word = bitmap + (gi >> 5);
+            const uint32_t bit = 1u << (gi & 31);
+            if (!(*(volatile uint32_t *)word & bit)) atomicOr(word, bit);
+        }
         double f0 = 0.25, S2 = 0.0, D = 0.0;
         for (int j = 0; j < K; ++j) {
             const int id = ids[j * N3 + v];
