@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
     ap.add_argument("--tol64", type=float, default=1e-8, help="fixed-point tolerance of the FP64 path")
+    ap.add_argument("--newton-tol", type=float, default=None,
+                    help="local-solve tolerance (default: the library's per precision)")
+    ap.add_argument("--newton-adapt", type=float, default=None,
+                    help="adaptive local tolerance factor of the basic scheme (default: the library's per precision)")
     return ap.parse_args()
 
 
@@ -197,7 +201,8 @@ def native(args, ws, rank, local):
     g0 = evp.voronoi(wl.n, seeds).cpu().numpy()
     N3 = wl.n ** 3
     tol_main = args.tol64 if args.precision == "fp64" else args.tol
-    mixed = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision, tol=tol_main, max_iter=5000)
+    mixed = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision, tol=tol_main, max_iter=5000,
+                       newton_adapt=args.newton_adapt, newton_tol=args.newton_tol)
     # warm-up (untimed)
     warm = run_steps(mixed, args.warmup, wl.dE33, wl.dt, wl.pf_steps, torch)
     mixed.set_profiling(True)
@@ -233,7 +238,9 @@ def native(args, ws, rank, local):
                                         "mixed_fast": "f32 (f64 reductions)", "fp64": "f64"}[args.precision],
                data="synthetic",
                config={"workload": wl.name, "n": wl.n, "grains": wl.grains, "precision": args.precision,
-                       "tol": tol_main, "dE33": wl.dE33, "pf_steps": wl.pf_steps,
+                       "tol": tol_main, "newton_tol": mixed.cfg.newton_tol, "newton_adapt": mixed.cfg.newton_adapt,
+                       "newton_mode": ["exact", "reuse", "f32_tangent"][mixed.cfg.newton_mode],
+                       "dE33": wl.dE33, "pf_steps": wl.pf_steps,
                        "l2": "inputs larger than L2 (about 0.8 GB of fields per replica, no flush needed)",
                        "parallelism": f"replicas x{ws}"},
                drx_increments_per_s=incs_per_s,
@@ -302,13 +309,27 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
             f32 += ev
         t64, t32 = f64 / FP64_PEAK_TFLOPS, f32 / FP32_PEAK_TFLOPS
         flops, peak, pipe = (f64, FP64_PEAK_TFLOPS, "fp64") if t64 >= t32 else (f32, FP32_PEAK_TFLOPS, "fp32")
-        achieved = flops / (ms / 1e3) / 1e12
-        return {"bound": "alu", "kernel": "newton", "pipe": pipe, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "flops_fp32": f32, "flops_fp64": f64,
-                "note": "algorithmic flops: 1140 per residual+tangent evaluation, 544 per residual-only "
+        alu = flops / (ms / 1e3) / 1e12
+        # algorithmic HBM bytes per launch: every voxel reads its trial strain, stress, tau_c and grain id
+        # (and with tangent reuse its 21 stored factor words) and writes its stress
+        words = 6 + 6 + 1 + (21 if reuse else 0) + 6
+        bytes_launch = (words * T + 4) * N3
+        hbm = bytes_launch / avg_s / 1e9
+        hpk = pk.get("hbm_gbs", 6800.0)
+        alu_frac, hbm_frac = alu / peak, hbm / hpk
+        detail = {"alu": {"pipe": pipe, "achieved": alu, "peak": peak, "unit": "TFLOP/s", "frac": alu_frac,
+                          "flops_fp32": f32, "flops_fp64": f64},
+                  "hbm": {"achieved": hbm, "peak": hpk, "unit": "GB/s", "frac": hbm_frac,
+                          "bytes_per_launch": bytes_launch, "peak_source": pk_kind}}
+        top = detail["hbm"] if hbm_frac >= alu_frac else detail["alu"]
+        return {"bound": "hbm" if hbm_frac >= alu_frac else "alu", "kernel": "newton",
+                "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"], "frac": top["frac"],
+                "traffic": None, "resources": detail,
+                "note": "the local solve is reported against the resource it uses the larger fraction of. "
+                        "Algorithmic flops: 1140 per residual+tangent evaluation, 544 per residual-only "
                         "evaluation, 80 per 6x6 LDL^T factorisation, 72 per pair of triangular solves, counted "
-                        "by pipe; peak from unit counts and the maximum SM clock"}
+                        "by pipe, peak from unit counts and the maximum SM clock; algorithmic bytes: the "
+                        "per-voxel words read and written once per launch"}
     if hbm_bytes_per_voxel(dom, wl.n, T) is None:
         return {"bound": "unknown", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
@@ -333,7 +354,8 @@ def memory_kernels(ktimes, wl, N3, precision, pk):
 
 def fast_companion(args, wl, g0, quat, mat, torch, evp):
     """The mixed path with the 6x6 Newton solve in FP32 (EVP_MIXED_FAST), same input."""
-    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="mixed_fast", tol=args.tol, max_iter=5000)
+    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="mixed_fast", tol=args.tol, max_iter=5000,
+                   newton_adapt=args.newton_adapt)
     run_steps(s, 1, wl.dE33, wl.dt, wl.pf_steps, torch)
     h = run_steps(s, args.fast_steps, wl.dE33, wl.dt, wl.pf_steps, torch)
     evp_s = sum(r["evp_ms"] for r in h) / 1e3

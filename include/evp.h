@@ -67,6 +67,11 @@ typedef struct {
                               EVP_SCHEME_AL: augmented Lagrangian (Michel-Moulinec-Suquet), the solver the
                               paper names (Sec. 2.1); same solution, fewer iterations at high contrast */
     double al_scale;       /* EVP_SCHEME_AL: reference shear modulus = Voigt mu / al_scale (bulk kept) */
+    double newton_adapt;   /* EVP_SCHEME_BASIC: 0 solves every local problem to newton_tol; eta > 0 loosens
+                              the local tolerance while the fixed point is far from converged, to
+                              max(newton_tol, eta * err) with err the fixed-point residual of the previous
+                              iteration (1e-2 before the first); the converged result meets the same
+                              tolerances */
 } evp_config;
 #define EVP_SCHEME_BASIC 0
 #define EVP_SCHEME_AL 1

@@ -154,6 +154,7 @@ int check_cfg(const evp_config *c, char *why, size_t wl) {
         return snprintf(why, wl, "unknown scheme %d", c->scheme), EVP_ERR_ARG;
     if (c->scheme == EVP_SCHEME_AL && !(c->al_scale >= 1.0))
         return snprintf(why, wl, "al_scale must be >= 1"), EVP_ERR_ARG;
+    if (!(c->newton_adapt >= 0.0)) return snprintf(why, wl, "newton_adapt must be >= 0"), EVP_ERR_ARG;
     if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE &&
         !(c->newton_mode == EVP_NEWTON_F32_TANGENT && c->precision == EVP_FP64))
         return snprintf(why, wl, "newton_mode %d is not available for precision %d", c->newton_mode, c->precision),
@@ -354,6 +355,8 @@ struct FpCtl {
     int done, it, conv, status, nmax, nfail, pad0, pad1;
     double err_eq, err_bc;
     double dE[6];
+    double tol_loc;     // local-solve tolerance of the next iteration (see evp_config.newton_adapt)
+    float tol_loc_f;
 };
 static_assert(sizeof(FpCtl) <= 256, "FpCtl must fit its workspace slot");
 constexpr int kFpBatch = 16;   // iterations queued between host reads of the control block
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(1024) k_fp_control(FpCtl *__restrict__ c, cons
                                                      double *__restrict__ scal, const int32_t *__restrict__ flags,
                                                      typename CT<T>::type *__restrict__ spec, long fstride, int n,
                                                      double N3, double tau0, double tol, int max_iter, double a,
-                                                     double b, double det, double mu0) {
+                                                     double b, double det, double mu0, double ntol, double eta) {
     __shared__ double red[32];
     __shared__ double corr[6];
     __shared__ double meanv[6];
@@ -418,6 +421,11 @@ __global__ void __launch_bounds__(1024) k_fp_control(FpCtl *__restrict__ c, cons
             for (int i = 0; i < 6; ++i) {
                 c->dE[i] += dEk[i];
                 corr[i] = dEk[i] * N3;   // the inverse transforms are unnormalised; x_c2r scales by 1/N^3
+            }
+            if (eta > 0.0) {
+                const double tl = fmax(ntol, eta * fmax(err_eq, err_bc));
+                c->tol_loc = tl;
+                c->tol_loc_f = (float)tl;
             }
             go = 1;
         }
@@ -749,8 +757,13 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         // iterations are queued in batches; the device control decides when to stop (see k_fp_check)
         FpCtl hc{};
         for (int i = 0; i < 6; ++i) hc.dE[i] = dE[i];
+        const bool adapt = h->cfg.newton_adapt > 0.0;
+        hc.tol_loc = adapt ? std::fmax(ntol, h->cfg.newton_adapt * 1e-2) : ntol;   // before the first residual
+        hc.tol_loc_f = (float)hc.tol_loc;
         FpCtl *dc = (FpCtl *)h->ctl;
         const int *skip = &dc->done;
+        const double *tl64 = adapt ? &dc->tol_loc : nullptr;
+        const float *tl32 = adapt ? &dc->tol_loc_f : nullptr;
         CK(cudaMemcpyAsync(dc, &hc, sizeof hc, cudaMemcpyHostToDevice, h->st));
         const double inv = 1.0 / (double)N3;
         int queued = 0;
@@ -763,16 +776,16 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                     if (h->cfg.newton_mode == EVP_NEWTON_F32_TANGENT)
                         CK(newton_field_df(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                            (double *)h->Stab, (double *)h->Mtab, h->Stabf, h->Mtabf, mc, ntol,
-                                           h->cfg.newton_max, h->flags, h->st, skip));
+                                           h->cfg.newton_max, h->flags, h->st, skip, tl64));
                     else if (reuse)
                         CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                                       (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
                                                       h->cfg.newton_max, 1, first, h->flags, h->wlist, h->nsm, h->st,
-                                                      skip));
+                                                      skip, tl64));
                     else
                         CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                                 (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
-                                                h->flags, h->st, skip)); }
+                                                h->flags, h->st, skip, tl64)); }
                   { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
@@ -783,11 +796,11 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         CK(newton_chord_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                                      (float *)h->Stab, (float *)h->Mtab, h->fac, mc, ntol,
                                                      h->cfg.newton_max, solve64, first, h->flags, h->wlist, h->nsm,
-                                                     h->st, skip));
+                                                     h->st, skip, tl32));
                     else
                         CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                                (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,
-                                               h->flags, h->st, skip)); }
+                                               h->flags, h->st, skip, tl32)); }
                   { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
@@ -797,11 +810,13 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                   if (h->dbl)
                       k_fp_control<double><<<1, 1024, 0, h->st>>>(dc, h->partials, zb, h->scal, h->flags,
                                                                   (double2 *)h->spec, h->H, n, (double)N3, h->p.tau0,
-                                                                  h->cfg.tol, h->cfg.max_iter, a, b, det, mu0);
+                                                                  h->cfg.tol, h->cfg.max_iter, a, b, det, mu0, ntol,
+                                                                  h->cfg.newton_adapt);
                   else
                       k_fp_control<float><<<1, 1024, 0, h->st>>>(dc, h->partials, zb, h->scal, h->flags,
                                                                  (float2 *)h->spec, h->H, n, (double)N3, h->p.tau0,
-                                                                 h->cfg.tol, h->cfg.max_iter, a, b, det, mu0);
+                                                                 h->cfg.tol, h->cfg.max_iter, a, b, det, mu0, ntol,
+                                                                 h->cfg.newton_adapt);
                   CK(cudaGetLastError()); }
                 // the strain correction arrives through the zero-frequency term: no offsets here
                 if (h->dbl) {

@@ -17,7 +17,8 @@ struct MatConst {
 // ---- fft.cu ----
 enum ZMode { Z_FWD = 0, Z_INV = 1, Z_FWD_GAMMA_INV = 2, Z_FWD_RESID = 3 };
 // skip (optional, device): when *skip != 0 the launched kernel returns at once (a converged fixed point
-// whose remaining queued iterations are discarded).
+// whose remaining queued iterations are discarded). tol_dev (optional, device): the local-solve
+// tolerance to use instead of tol, set on the device between iterations.
 template <typename T>
 cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s, const int *skip = nullptr);
 template <typename T>
@@ -38,7 +39,7 @@ template <typename TA>
 cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                          const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
                          cudaStream_t s,
-                         const int *skip = nullptr);
+                         const int *skip = nullptr, const TA *tol_dev = nullptr);
 // Jacobian-reuse variant: fac holds 21 factor words per voxel in TA (factorised in FP64 if solve_fp64).
 // Unless force_refresh, runs in two passes with the work list wl (N3 entries, count in flags[10]);
 // nsm = multiprocessors, for the grid of the second pass.
@@ -46,12 +47,14 @@ template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s,
-                               const int *skip = nullptr);
+                               const int *skip = nullptr,
+                               const TA *tol_dev = nullptr);
 // FP64 residual / FP32 tangent Newton (FP64 path); Stabf / Mtabf are FP32 copies of the tables.
 cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
                             const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,
                             MatConst mc, double tol, int maxit, int *flags, cudaStream_t s,
-                            const int *skip = nullptr);
+                            const int *skip = nullptr,
+                            const double *tol_dev = nullptr);
 // Augmented-Lagrangian local step; part: 14 doubles per block (al_blocks blocks).
 int al_blocks(long N3);
 template <typename TA>

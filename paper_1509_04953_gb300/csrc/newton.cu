@@ -107,8 +107,10 @@ template <typename TA, typename TS>
 __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc,
                                                     const int32_t *__restrict__ g0, TA *__restrict__ sig,
                                                     const TA *__restrict__ Stab, const TA *__restrict__ Mtab, MatConst mc,
-                                                    TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int *__restrict__ skip) {
+                                                    TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int *__restrict__ skip,
+    const TA *__restrict__ tol_dev) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
+    if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
     int r = 1, nev = 0;
@@ -188,8 +190,10 @@ __global__ void __launch_bounds__(kThreads) k_newton_df(long N3, const double *_
                                                        double *__restrict__ sig, const double *__restrict__ Stab,
                                                        const double *__restrict__ Mtab, const float *__restrict__ Stabf,
                                                        const float *__restrict__ Mtabf, MatConst mc, double tol,
-                                                       int maxit, int *__restrict__ flags, const int *__restrict__ skip) {
+                                                       int maxit, int *__restrict__ flags, const int *__restrict__ skip,
+    const double *__restrict__ tol_dev) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
+    if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
     int r = 1, nev = 0;
@@ -300,8 +304,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
                                                           const int32_t *__restrict__ g0, TA *__restrict__ sig,
                                                           const TA *__restrict__ Stab, const TA *__restrict__ Mtab,
                                                           TS *__restrict__ fac, MatConst mc, TA tol, int maxit,
-                                                          TA ls_free, int force_refresh, int *__restrict__ flags, const int *__restrict__ skip) {
+                                                          TA ls_free, int force_refresh, int *__restrict__ flags, const int *__restrict__ skip,
+    const TA *__restrict__ tol_dev) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
+    if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
     int r = 1, nev = 0, nref = 0;
@@ -344,8 +350,10 @@ __global__ void __launch_bounds__(kThreads) k_chord_first(long N3, const TA *__r
                                                          TA *__restrict__ sig, const TA *__restrict__ Stab,
                                                          const TA *__restrict__ Mtab, const TS *__restrict__ fac,
                                                          MatConst mc, TA tol, int *__restrict__ flags,
-                                                         int32_t *__restrict__ wl, const int *__restrict__ skip) {
+                                                         int32_t *__restrict__ wl, const int *__restrict__ skip,
+    const TA *__restrict__ tol_dev) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
+    if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
     bool done = false;
@@ -393,8 +401,10 @@ template <typename TA, typename TS, typename TF>
 __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_rest(
     long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
     TA *__restrict__ sig, const TA *__restrict__ Stab, const TA *__restrict__ Mtab, TS *__restrict__ fac, MatConst mc,
-    TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int32_t *__restrict__ wl, const int *__restrict__ skip) {
+    TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int32_t *__restrict__ wl, const int *__restrict__ skip,
+    const TA *__restrict__ tol_dev) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
+    if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const int count = *(volatile const int *)(flags + 10);
     if (blockIdx.x == 0 && threadIdx.x == 0 && N3 - count > 0) {   // pass 1 accepted the others in one step
         atomicMax(flags + 1, 1);
@@ -655,46 +665,49 @@ template <typename TA> TA ls_free_of() { return sizeof(TA) == 4 ? (TA)1e-3 : (TA
 template <typename TA>
 cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                          const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
-                         cudaStream_t s, const int *skip) {
+                         cudaStream_t s, const int *skip, const TA *tol_dev) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
     if (solve_fp64)
         k_newton<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol, maxit,
-                                                         ls_free_of<TA>(), flags, skip);
+                                                         ls_free_of<TA>(), flags, skip, tol_dev);
     else
         k_newton<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol, maxit,
-                                                     ls_free_of<TA>(), flags, skip);
+                                                     ls_free_of<TA>(), flags, skip, tol_dev);
     return cudaGetLastError();
 }
 
 template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
-                               int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s, const int *skip) {
+                               int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s, const int *skip,
+                               const TA *tol_dev) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
     if (!force_refresh && wl) {
         // flags[10] counts the listed voxels; pass 2 reads it on the device (no host round trip)
         cudaError_t e = cudaMemsetAsync(flags + 10, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
         k_chord_first<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (const TA *)fac, mc,
-                                                          (TA)tol, flags, wl, skip);
+                                                          (TA)tol, flags, wl, skip, tol_dev);
         const int rb = std::min(blocks, nsm * (sizeof(TA) == 4 ? 3 : 2));
         if (solve_fp64)
             k_chord_rest<TA, TA, double><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
-                                                                 (TA)tol, maxit, ls_free_of<TA>(), flags, wl, skip);
+                                                                 (TA)tol, maxit, ls_free_of<TA>(), flags, wl, skip,
+                                                                 tol_dev);
         else
             k_chord_rest<TA, TA, TA><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
-                                                             (TA)tol, maxit, ls_free_of<TA>(), flags, wl, skip);
+                                                             (TA)tol, maxit, ls_free_of<TA>(), flags, wl, skip,
+                                                             tol_dev);
         return cudaGetLastError();
     }
     // factors stored in the field precision; factorised in FP64 unless the FP32 solve is asked for
     if (solve_fp64)
         k_newton_chord<TA, TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
                                                                    (TA)tol, maxit, ls_free_of<TA>(), force_refresh,
-                                                                   flags, skip);
+                                                                   flags, skip, tol_dev);
     else
         k_newton_chord<TA, TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
                                                                (TA)tol, maxit, ls_free_of<TA>(), force_refresh, flags,
-                                                               skip);
+                                                               skip, tol_dev);
     return cudaGetLastError();
 }
 
@@ -702,10 +715,11 @@ int al_blocks(long N3) { return (int)((N3 + kThreads - 1) / kThreads); }
 
 cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
                             const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,
-                            MatConst mc, double tol, int maxit, int *flags, cudaStream_t s, const int *skip) {
+                            MatConst mc, double tol, int maxit, int *flags, cudaStream_t s, const int *skip,
+                            const double *tol_dev) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
     k_newton_df<<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, Stabf, Mtabf, mc, tol, maxit, flags,
-                                            skip);
+                                            skip, tol_dev);
     return cudaGetLastError();
 }
 
@@ -755,10 +769,10 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
 #define EVP_INST(TA)                                                                                              \
     template cudaError_t newton_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,        \
                                           const TA *, MatConst, double, int, int, int *, cudaStream_t,           \
-                                          const int *);                                                          \
+                                          const int *, const TA *);                                              \
     template cudaError_t newton_chord_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,  \
                                                 const TA *, void *, MatConst, double, int, int, int, int *,       \
-                                                int32_t *, int, cudaStream_t, const int *);                       \
+                                                int32_t *, int, cudaStream_t, const int *, const TA *);           \
     template cudaError_t al_local<TA>(long, const TA *, const TA *, const TA *, const int32_t *, TA *, TA *, TA *, \
                                       const TA *, const TA *, const TA *, MatConst, double, double, double, int, int, \
                                       int, int *, double *, void *, int, cudaStream_t);                           \

@@ -37,7 +37,8 @@ class Config(C.Structure):
     _fields_ = [("n", C.c_int), ("grains", C.c_int), ("kmax", C.c_int), ("precision", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("allow_unconverged", C.c_int),
                 ("newton_tol", C.c_double), ("newton_max", C.c_int), ("predictor", C.c_int), ("max_ids", C.c_int),
-                ("newton_mode", C.c_int), ("scheme", C.c_int), ("al_scale", C.c_double)]
+                ("newton_mode", C.c_int), ("scheme", C.c_int), ("al_scale", C.c_double),
+                ("newton_adapt", C.c_double)]
 
 
 class Params(C.Structure):
@@ -121,7 +122,7 @@ SCHEMES = {"basic": 0, "al": 1}
 
 def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, allow_unconverged=0,
                 newton_tol=None, newton_max=50, predictor=1, max_ids=0, newton=None, scheme="basic",
-                al_scale=6.0) -> Config:
+                al_scale=6.0, newton_adapt=None) -> Config:
     if newton_tol is None:
         newton_tol = 1e-12 if precision == "fp64" else 1e-5
     if newton is None:
@@ -129,8 +130,11 @@ def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, a
         # residual (EVP_MIXED, 1.5x); the FP64 path runs fastest with an FP32 tangent and solve under
         # its FP64 residual (1.5x, identical iterates); the all-FP32 path with the exact Newton
         newton = {"mixed": "reuse", "fp64": "f32_tangent", "mixed_fast": "exact"}[precision]
+    if newton_adapt is None:
+        # the FP64 path stays the reference: every local problem solved to newton_tol
+        newton_adapt = 0.0 if precision == "fp64" else 0.1
     return Config(n, grains, kmax, PRECISION[precision], tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                  predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale)
+                  predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale, newton_adapt)
 
 
 def make_params(mat) -> Params:
