@@ -234,7 +234,7 @@ def native(args, ws, rank, local):
 
     res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
                ms_per_step=1e3 * step_s_max / args.steps, higher_is_better=True, scaling="weak",
-               vs_baseline=None, dtype={"mixed": "f32 fields/FFT/PF + f64 Newton solve and reductions",
+               vs_baseline=None, dtype={"mixed": "f32 fields/FFT/PF/residual + f64 tangent factorisation and reductions",
                                         "mixed_fast": "f32 (f64 reductions)", "fp64": "f64"}[args.precision],
                data="synthetic",
                config={"workload": wl.name, "n": wl.n, "grains": wl.grains, "precision": args.precision,
