@@ -36,7 +36,7 @@ class Config(C.Structure):
     _fields_ = [("n", C.c_int), ("grains", C.c_int), ("kmax", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("allow_unconverged", C.c_int), ("newton_tol", C.c_double),
                 ("newton_max", C.c_int), ("predictor", C.c_int), ("nthreads", C.c_int), ("scheme", C.c_int),
-                ("al_scale", C.c_double)]
+                ("al_scale", C.c_double), ("pf_refine", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -261,12 +261,15 @@ class State:
 
     def __init__(self, n, grains, g0, quat, mat, seed, kmax=8, tol=1e-10, max_iter=1000,
                  allow_unconverged=0, newton_tol=1e-12, newton_max=50, predictor=1, nthreads=0, scheme=0,
-                 al_scale=4.0):
+                 al_scale=4.0, pf_refine=1):
         self.n, self.G, self.K = n, grains, kmax
         self.N3 = n ** 3
+        self.r = 2 if pf_refine == 2 else 1
+        self.npf = self.r * n
+        self.N3pf = self.npf ** 3
         self.mat = mat
         self._cfg = Config(n, grains, kmax, tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                           predictor, nthreads, scheme, al_scale)
+                           predictor, nthreads, scheme, al_scale, self.r)
         self._p = make_params(mat)
         self._g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)
         self._q = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1)
@@ -290,14 +293,18 @@ class State:
         ptr = lib().orc_field(self.h, name.encode())
         if name in ("E", "dE_prev"):
             return np.ctypeslib.as_array(ptr, shape=(6,))
-        if name == "eta":
-            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3))
+        if name == "eta":   # on the phase-field grid
+            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3pf))
+        if name == "kpf":
+            return np.ctypeslib.as_array(ptr, shape=(self.N3pf,))
         return np.ctypeslib.as_array(ptr, shape=(self._SIZES[name], self.N3))
 
     def ifield(self, name):
         ptr = lib().orc_ifield(self.h, name.encode())
-        if name == "ids":
-            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3))
+        if name == "ids":   # on the phase-field grid
+            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3pf))
+        if name == "gpf":
+            return np.ctypeslib.as_array(ptr, shape=(self.N3pf,))
         return np.ctypeslib.as_array(ptr, shape=(self.N3,))
 
     def increment(self, dE33, dt):

@@ -430,6 +430,13 @@ struct orc_state {
     double *C, *S, *M;
     int32_t *g0, *g, *draws, *ids, *ids2;
     double *eps, *epsp, *sig, *deps_prev, *rho, *k, *kappa, *eta, *eta2;
+    /* phase-field grid: r = 1 (the mechanics grid; gpf and kpf are g and k) or 2 (refined, Sec. 2.4):
+     * npf = r n points per edge, the active sets ids/eta live there, gpf = argmax id per PF point,
+     * kpf = rho_tot interpolated onto the PF grid */
+    int r, npf;
+    long N3pf;
+    int32_t *gpf;
+    double *kpf;
     double *work_eps, *work_sig;
     double complex *spec;
 };
@@ -438,6 +445,82 @@ static void *xcalloc(size_t n, size_t sz) {
     void *p = calloc(n ? n : 1, sz);
     if (!p) { fprintf(stderr, "oracle: out of memory\n"); abort(); }
     return p;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * The 2:1 phase-field grid (Sec. 2.4). Both grids are cell-centred and periodic: mechanics cell i
+ * spans [i, i+1) with its centre at i + 1/2; PF cell I spans [I/2, (I+1)/2), centre I/2 + 1/4.
+ *  - orientation: a PF point takes the grain of the nearest mechanics point, its parent cell I/2;
+ *  - smooth fields (here rho_tot, the driving force): linear interpolation along each axis between
+ *    the two nearest mechanics centres, weights 3/4 (the parent) and 1/4 (the neighbour on the side
+ *    of the PF centre), i.e. trilinear in 3D;
+ *  - back to the mechanics grid (reading, the paper is silent): the grain id of a mechanics cell is the
+ *    argmax of the order parameters summed over its eight PF children (ties to the smaller id).
+ * ---------------------------------------------------------------------------------------- */
+static long pf_parent(const orc_state *s, long w) {
+    const int m = s->npf, r = s->r;
+    const int X = (int)(w % m), Y = (int)((w / m) % m), Z = (int)(w / ((long)m * m));
+    return X / r + (long)s->n * (Y / r + (long)s->n * (Z / r));
+}
+
+/* the two mechanics indices bracketing PF index I along one axis, and their weights */
+static void interp_axis(int I, int n, int idx[2], double wt[2]) {
+    const int i = I / 2;
+    if (I % 2 == 0) { idx[0] = (i + n - 1) % n; idx[1] = i; wt[0] = 0.25; wt[1] = 0.75; }
+    else { idx[0] = i; idx[1] = (i + 1) % n; wt[0] = 0.75; wt[1] = 0.25; }
+}
+
+/* kpf = trilinear interpolation of k (r = 2); the eight terms summed in the order (z, y, x) outer to
+ * inner, each weight formed as (wz wy) wx */
+static void pf_interp_k(orc_state *s) {
+    if (s->r == 1) return;
+    const int n = s->n, m = s->npf;
+    for (int Z = 0; Z < m; ++Z)
+        for (int Y = 0; Y < m; ++Y)
+            for (int X = 0; X < m; ++X) {
+                int iz[2], iy[2], ix[2];
+                double wz[2], wy[2], wx[2];
+                interp_axis(Z, n, iz, wz);
+                interp_axis(Y, n, iy, wy);
+                interp_axis(X, n, ix, wx);
+                double acc = 0.0;
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b)
+                        for (int c = 0; c < 2; ++c)
+                            acc += (wz[a] * wy[b]) * wx[c] * s->k[ix[c] + (long)n * (iy[b] + (long)n * iz[a])];
+                s->kpf[X + (long)m * (Y + (long)m * Z)] = acc;
+            }
+}
+
+/* g on the mechanics grid from the PF order parameters (r = 2): per cell, for each id present in any
+ * of its eight children, the sum of that id's order parameter over the children in the order
+ * c = dx + 2 dy + 4 dz; the largest sum wins, ties to the smaller id */
+static void pf_restrict_ids(orc_state *s) {
+    if (s->r == 1) return;
+    const int n = s->n, m = s->npf, K = s->K;
+    const long M3 = s->N3pf;
+    for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y)
+            for (int x = 0; x < n; ++x) {
+                long ch[8];
+                for (int c = 0; c < 8; ++c) {
+                    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+                    ch[c] = (2 * x + dx) + (long)m * ((2 * y + dy) + (long)m * (2 * z + dz));
+                }
+                int best = -1;
+                double bsum = 0.0;
+                for (int c0 = 0; c0 < 8; ++c0)
+                    for (int j0 = 0; j0 < K; ++j0) {
+                        const int id = s->ids[j0 * M3 + ch[c0]];
+                        if (id < 0) continue;
+                        double sum = 0.0;
+                        for (int c = 0; c < 8; ++c)
+                            for (int j = 0; j < K; ++j)
+                                if (s->ids[j * M3 + ch[c]] == id) sum += s->eta[j * M3 + ch[c]];
+                        if (best < 0 || sum > bsum || (sum == bsum && id < best)) { best = id; bsum = sum; }
+                    }
+                s->g[x + (long)n * (y + (long)n * z)] = best;
+            }
 }
 
 orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat,
@@ -462,10 +545,13 @@ orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t 
     s->g0 = xcalloc(N3, sizeof(int32_t));
     s->g = xcalloc(N3, sizeof(int32_t));
     s->draws = xcalloc(N3, sizeof(int32_t));
-    s->ids = xcalloc((size_t)s->K * N3, sizeof(int32_t));
-    s->ids2 = xcalloc((size_t)s->K * N3, sizeof(int32_t));
-    s->eta = xcalloc((size_t)s->K * N3, sizeof(double));
-    s->eta2 = xcalloc((size_t)s->K * N3, sizeof(double));
+    s->r = cfg->pf_refine == 2 ? 2 : 1;
+    s->npf = s->r * s->n;
+    s->N3pf = (long)s->npf * s->npf * s->npf;
+    s->ids = xcalloc((size_t)s->K * s->N3pf, sizeof(int32_t));
+    s->ids2 = xcalloc((size_t)s->K * s->N3pf, sizeof(int32_t));
+    s->eta = xcalloc((size_t)s->K * s->N3pf, sizeof(double));
+    s->eta2 = xcalloc((size_t)s->K * s->N3pf, sizeof(double));
     s->eps = xcalloc(6 * N3, sizeof(double));
     s->epsp = xcalloc(6 * N3, sizeof(double));
     s->sig = xcalloc(6 * N3, sizeof(double));
@@ -485,11 +571,24 @@ orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t 
         s->k[v] = kk;
         /* initial nucleation strength: draw 0 from Weibull(q, kc) (Sec. 2.3, implementation) */
         s->kappa[v] = orc_weibull(orc_u01(seed, (uint64_t)v, 0), p->kc, p->q);
-        /* initial order parameters: sharp, one grain per voxel */
-        for (int j = 0; j < s->K; ++j) { s->ids[j * N3 + v] = -1; s->eta[j * N3 + v] = 0.0; }
-        s->ids[v] = g0[v];
-        s->eta[v] = 1.0;
     }
+    if (s->r == 1) {
+        s->gpf = s->g;
+        s->kpf = s->k;
+    } else {
+        s->gpf = xcalloc(s->N3pf, sizeof(int32_t));
+        s->kpf = xcalloc(s->N3pf, sizeof(double));
+    }
+    /* initial order parameters: sharp, one grain per PF point; on the refined grid every point takes
+     * the orientation (grain) of its nearest mechanics point, its parent cell (Sec. 2.4) */
+    for (long w = 0; w < s->N3pf; ++w) {
+        const long v = pf_parent(s, w);
+        for (int j = 0; j < s->K; ++j) { s->ids[j * s->N3pf + w] = -1; s->eta[j * s->N3pf + w] = 0.0; }
+        s->ids[w] = g0[v];
+        s->eta[w] = 1.0;
+        s->gpf[w] = g0[v];
+    }
+    pf_interp_k(s);
     return s;
 }
 
@@ -498,7 +597,9 @@ void orc_destroy(orc_state *s) {
     free(s->C); free(s->S); free(s->M); free(s->g0); free(s->g); free(s->draws); free(s->ids);
     free(s->ids2); free(s->eta); free(s->eta2); free(s->eps); free(s->epsp); free(s->sig);
     free(s->deps_prev); free(s->rho); free(s->k); free(s->kappa); free(s->work_eps);
-    free(s->work_sig); free(s->spec); free(s);
+    free(s->work_sig); free(s->spec);
+    if (s->r != 1) { free(s->gpf); free(s->kpf); }
+    free(s);
 }
 
 double *orc_field(orc_state *s, const char *name) {
@@ -509,6 +610,7 @@ double *orc_field(orc_state *s, const char *name) {
     if (!strcmp(name, "rho")) return s->rho;
     if (!strcmp(name, "k")) return s->k;
     if (!strcmp(name, "kappa")) return s->kappa;
+    if (!strcmp(name, "kpf")) return s->kpf;
     if (!strcmp(name, "eta")) return s->eta;
     if (!strcmp(name, "C")) return s->C;
     if (!strcmp(name, "S")) return s->S;
@@ -523,6 +625,7 @@ int32_t *orc_ifield(orc_state *s, const char *name) {
     if (!strcmp(name, "g")) return s->g;
     if (!strcmp(name, "draws")) return s->draws;
     if (!strcmp(name, "ids")) return s->ids;
+    if (!strcmp(name, "gpf")) return s->gpf;
     return NULL;
 }
 
@@ -536,6 +639,7 @@ void orc_refresh_derived(orc_state *s) {
         for (int a = 0; a < 12; ++a) kk += s->rho[a * s->N3 + v];
         s->k[v] = kk;
     }
+    pf_interp_k(s);
 }
 
 /* Signed frequency of index k on an n-point axis; the Nyquist index n/2 is taken as +n/2. */
@@ -1266,9 +1370,16 @@ int orc_nucleate(orc_state *s, uint64_t step, int32_t *n_new) {
     for (long v = 0; v < N3; ++v) {
         if (!mark[v]) continue;
         int id = s->next_id + cnt++;
-        for (int j = 0; j < s->K; ++j) { s->ids[j * N3 + v] = -1; s->eta[j * N3 + v] = 0.0; }
-        s->ids[v] = id;
-        s->eta[v] = 1.0;
+        /* the nucleus fills the PF points of this cell: the cell itself, or its r^3 children (Sec. 2.4) */
+        const int x = (int)(v % s->n), y = (int)((v / s->n) % s->n), z = (int)(v / ((long)s->n * s->n));
+        for (int c = 0; c < s->r * s->r * s->r; ++c) {
+            const int dx = c % s->r, dy = (c / s->r) % s->r, dz = c / (s->r * s->r);
+            const long w = (s->r * x + dx) + (long)s->npf * ((s->r * y + dy) + (long)s->npf * (s->r * z + dz));
+            for (int j = 0; j < s->K; ++j) { s->ids[j * s->N3pf + w] = -1; s->eta[j * s->N3pf + w] = 0.0; }
+            s->ids[w] = id;
+            s->eta[w] = 1.0;
+            s->gpf[w] = id;
+        }
         s->g[v] = id;
         double kk = 0.0;
         for (int a = 0; a < 12; ++a) {
@@ -1282,6 +1393,7 @@ int orc_nucleate(orc_state *s, uint64_t step, int32_t *n_new) {
     s->next_id += cnt;
     *n_new = cnt;
     free(mark);
+    pf_interp_k(s);   /* the nuclei softened rho */
     return 0;
 }
 
@@ -1296,8 +1408,9 @@ int orc_nucleate(orc_state *s, uint64_t step, int32_t *n_new) {
  *                    + (def: 2E' eta_i R/S^2 | rex: -2E' eta_i D/S^2) ]       (Eq. PFGoverning)
  * with a periodic 7-point Laplacian and explicit Euler. E' = zeta mu b^2 rho_tot dx / omega_gb.
  * ---------------------------------------------------------------------------------------- */
-static double pf_E_scale(const orc_params *p) {
-    return p->zeta * (mu_voigt(p) * 1e6) * p->b * p->b * p->dx / p->omega_gb;
+static double pf_E_scale(const orc_state *s) {   /* E' per unit rho_tot; lengths in PF grid spacings dx / r */
+    const orc_params *p = &s->p;
+    return p->zeta * (mu_voigt(p) * 1e6) * p->b * p->b * (p->dx / s->r) / p->omega_gb;
 }
 
 /* New value of one order parameter from its value at x, its six neighbours, the local sums
@@ -1314,7 +1427,7 @@ static double pf_update_one(const orc_params *p, int is_def, double e0, const do
 
 static double eta_at(const orc_state *s, const int32_t *ids, const double *eta, long v, int id) {
     for (int j = 0; j < s->K; ++j)
-        if (ids[j * s->N3 + v] == id) return eta[j * s->N3 + v];
+        if (ids[j * s->N3pf + v] == id) return eta[j * s->N3pf + v];
     return 0.0;
 }
 
@@ -1336,14 +1449,14 @@ static int cmp_id(const void *a, const void *b) {
 }
 
 static void pf_one_step(orc_state *s, int *overflow) {
-    const long N3 = s->N3;
+    const long N3 = s->N3pf;
     const int K = s->K, G = s->G;
-    const double Esc = pf_E_scale(&s->p);
+    const double Esc = pf_E_scale(s);
     int ovf = 0;
 #pragma omp parallel for schedule(dynamic, 256) reduction(+ : ovf)
     for (long v = 0; v < N3; ++v) {
         long nv[6];
-        for (int d = 0; d < 6; ++d) nv[d] = nbr(s->n, v, d);
+        for (int d = 0; d < 6; ++d) nv[d] = nbr(s->npf, v, d);
         int cand[7 * 64];
         int nc = 0;
         long src[7] = {v, nv[0], nv[1], nv[2], nv[3], nv[4], nv[5]};
@@ -1365,7 +1478,7 @@ static void pf_one_step(orc_state *s, int *overflow) {
             S2 += e0 * e0;
             if (cand[i] < G) D += e0 * e0; else R += e0 * e0;
         }
-        double Ep = Esc * s->k[v];
+        double Ep = Esc * s->kpf[v];
         cand_t out[7 * 64];
         int no = 0;
         double best = -1e300;
@@ -1393,7 +1506,7 @@ static void pf_one_step(orc_state *s, int *overflow) {
 
 /* grain id = argmax over the order parameters, ties to the smaller id (Sec. 2.4, last paragraph) */
 static void pf_argmax(orc_state *s) {
-    const long N3 = s->N3;
+    const long N3 = s->N3pf;
     for (long v = 0; v < N3; ++v) {
         int bi = -1;
         double be = 0.0;
@@ -1403,17 +1516,18 @@ static void pf_argmax(orc_state *s) {
             double e = s->eta[j * N3 + v];
             if (bi < 0 || e > be || (e == be && id < bi)) { bi = id; be = e; }
         }
-        s->g[v] = bi;
+        s->gpf[v] = bi;
     }
+    pf_restrict_ids(s);
 }
 
 /* Discrete free energy whose gradient is the update above: bulk + forward-difference gradient
  * energy over the periodic grid + stored energy (Eqs. TotalFreeEnergy, GBEnergyDensity,
  * StoredEnergyDensity, nondimensional). */
 double orc_pf_energy(orc_state *s) {
-    const long N3 = s->N3;
+    const long N3 = s->N3pf;
     const int K = s->K, G = s->G;
-    const double l = s->p.l_gb, m = 6.0 / l, kap = 0.75 * l, gam = 1.5, Esc = pf_E_scale(&s->p);
+    const double l = s->p.l_gb, m = 6.0 / l, kap = 0.75 * l, gam = 1.5, Esc = pf_E_scale(s);
     double F = 0.0;
     for (long v = 0; v < N3; ++v) {
         double f0 = 0.25, S2 = 0.0, D = 0.0;
@@ -1430,10 +1544,10 @@ double orc_pf_energy(orc_state *s) {
                 f0 += gam * e * e * e2 * e2;
             }
         }
-        double fdef = S2 > 1e-12 ? Esc * s->k[v] * D / S2 : 0.0;
+        double fdef = S2 > 1e-12 ? Esc * s->kpf[v] * D / S2 : 0.0;
         double grad = 0.0;
         for (int d = 1; d < 6; d += 2) {
-            long w = nbr(s->n, v, d);
+            long w = nbr(s->npf, v, d);
             /* union of ids at v and w */
             int u[128], nu = 0;
             for (int j = 0; j < K; ++j) {
@@ -1452,13 +1566,13 @@ double orc_pf_energy(orc_state *s) {
     return F;
 }
 
-void orc_stats_now(orc_state *s, orc_pf_stats *out) {
-    const long N3 = s->N3;
+void orc_stats_now(orc_state *s, orc_pf_stats *out) {   /* on the PF grid */
+    const long N3 = s->N3pf;
     long rex = 0;
     unsigned char *seen = (unsigned char *)xcalloc((size_t)s->next_id + 1, 1);
     int ng = 0;
     for (long v = 0; v < N3; ++v) {
-        int g = s->g[v];
+        int g = s->gpf[v];
         if (g >= s->G) ++rex;
         if (g >= 0 && g <= s->next_id && !seen[g]) { seen[g] = 1; ++ng; }
     }
@@ -1473,8 +1587,9 @@ int orc_pf_step(orc_state *s, int nsteps, orc_pf_stats *out) {
     int32_t *gprev = (int32_t *)xcalloc(N3, sizeof(int32_t));
     memcpy(gprev, s->g, N3 * sizeof(int32_t));
     int ovf = 0;
+    pf_interp_k(s);
     for (int t = 0; t < nsteps; ++t) pf_one_step(s, &ovf);
-    if (nsteps > 0) pf_argmax(s);
+    if (nsteps > 0) pf_argmax(s);   /* also g on the mechanics grid */
     /* sweep softening: a voxel whose grain changes from a deformed to a recrystallised one
      * over this call has its densities scaled by s_soften (reading of Eq. UpdateGND) */
     for (long v = 0; v < N3; ++v) {
@@ -1488,6 +1603,7 @@ int orc_pf_step(orc_state *s, int nsteps, orc_pf_stats *out) {
         }
     }
     free(gprev);
+    pf_interp_k(s);
     if (out) {
         orc_stats_now(s, out);
         out->overflow = ovf;
@@ -1498,9 +1614,10 @@ int orc_pf_step(orc_state *s, int nsteps, orc_pf_stats *out) {
 /* Dense multi-order-parameter update (every id at every voxel, no active set): the same
  * equations with the sums over all ids in ascending order. Used to pin the sparse update. */
 int orc_pf_step_dense(orc_state *s, int nsteps) {
-    const long N3 = s->N3;
+    const long N3 = s->N3pf;
+    pf_interp_k(s);
     const int NG = s->next_id, K = s->K, G = s->G;
-    const double Esc = pf_E_scale(&s->p);
+    const double Esc = pf_E_scale(s);
     double *eta = (double *)xcalloc((size_t)NG * N3, sizeof(double));
     double *eta2 = (double *)xcalloc((size_t)NG * N3, sizeof(double));
     for (long v = 0; v < N3; ++v)
@@ -1516,10 +1633,10 @@ int orc_pf_step_dense(orc_state *s, int nsteps) {
                 S2 += e * e;
                 if (i < G) D += e * e; else R += e * e;
             }
-            double Ep = Esc * s->k[v];
+            double Ep = Esc * s->kpf[v];
             for (int i = 0; i < NG; ++i) {
                 double nb[6];
-                for (int d = 0; d < 6; ++d) nb[d] = eta[(long)i * N3 + nbr(s->n, v, d)];
+                for (int d = 0; d < 6; ++d) nb[d] = eta[(long)i * N3 + nbr(s->npf, v, d)];
                 eta2[(long)i * N3 + v] = pf_update_one(&s->p, i < G, eta[(long)i * N3 + v], nb, S2, D, R, Ep);
             }
         }

@@ -39,6 +39,7 @@ typedef struct {
     int nthreads;              /* OpenMP threads for per-voxel loops (0 = default) */
     int scheme;                /* 0: basic Green-operator iteration, 1: augmented Lagrangian */
     double al_scale;           /* augmented Lagrangian: reference shear modulus = mu_Voigt / al_scale */
+    int pf_refine;             /* phase-field grid per mechanics grid spacing: 1 (same grid) or 2 (Sec. 2.4) */
 } orc_config;
 
 typedef struct {
