@@ -72,6 +72,9 @@ typedef struct {
                               max(newton_tol, eta * err) with err the fixed-point residual of the previous
                               iteration (1e-2 before the first); the converged result meets the same
                               tolerances */
+    int pf_refine;         /* phase-field grid spacing per mechanics spacing: 0 or 1 = the same grid; 2 = the
+                              2:1 refined PF grid of Sec. 2.4 ((2n)^3 PF points; the active sets, the PF argmax
+                              and the interpolated driving force live there; see pf_step and drx_nucleate) */
 } evp_config;
 #define EVP_SCHEME_BASIC 0
 #define EVP_SCHEME_AL 1
@@ -103,15 +106,16 @@ typedef struct {
 
 typedef struct {
     double F_tot;          /* discrete phase-field free energy (nondimensional) */
-    double X_rex;          /* fraction of voxels whose grain id is recrystallised (id >= G) */
-    int n_grains;          /* number of distinct grain ids present */
+    double X_rex;          /* fraction of PF points whose grain id is recrystallised (id >= G) */
+    int n_grains;          /* number of distinct grain ids present on the PF grid */
     int overflow;          /* voxel-steps whose active set was truncated to kmax */
 } pf_stats;
 
 typedef struct evp_handle evp_handle;
 
 /* field masks for get_fields / set_fields; fields are packed in this bit order, each as
- * (components x N^3) of the type given ("T" = double in EVP_FP64, float otherwise) */
+ * (components x N^3) of the type given ("T" = double in EVP_FP64, float otherwise); the phase-field
+ * fields (EVP_F_IDS, EVP_F_ETA, EVP_F_GRAIN_PF) have (components x (r N)^3), r = pf_refine */
 #define EVP_F_SIG   (1u << 0)   /* stress, 6 x T */
 #define EVP_F_EPS   (1u << 1)   /* total strain eps = eps_e + eps_p, 6 x T (get only) */
 #define EVP_F_EPSP  (1u << 2)   /* plastic strain, 6 x T */
@@ -123,8 +127,11 @@ typedef struct evp_handle evp_handle;
 #define EVP_F_GRAIN (1u << 8)   /* current grain id (argmax order parameter), 1 x int32 */
 #define EVP_F_G0    (1u << 9)   /* initial grain id (orientation index), 1 x int32 (get only) */
 #define EVP_F_DRAWS (1u << 10)  /* kappa draws so far, 1 x int32 */
-#define EVP_F_IDS   (1u << 11)  /* active-set ids, kmax x int32 (slot-major, -1 = empty) */
-#define EVP_F_ETA   (1u << 12)  /* active-set order parameters, kmax x T */
+#define EVP_F_IDS   (1u << 11)  /* active-set ids, kmax x int32 per PF point (slot-major, ascending ids, -1 = empty
+                                   slots last) */
+#define EVP_F_ETA   (1u << 12)  /* active-set order parameters, kmax x T per PF point */
+#define EVP_F_GRAIN_PF (1u << 13)  /* argmax id per PF point, 1 x int32 per PF point (get only; the same as
+                                      EVP_F_GRAIN when pf_refine <= 1) */
 
 /* Bytes of device workspace evp_init needs for this configuration. */
 int evp_workspace_bytes(const evp_config *cfg, size_t *bytes);
@@ -152,15 +159,21 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out);
 
 /* a8 (Sec. 2.3 with its Appendix, Eq. UpdateGND): stochastic nucleation. A voxel with a face
  * neighbour of another grain nucleates iff k > kappa; nuclei receive fresh ids in ascending
- * voxel order, a single order parameter 1, densities scaled by s_soften and a new kappa drawn
- * with kc' = s_nucl kc. *n_new = nuclei created. step is recorded only (draws are counted per
- * voxel), so results depend on the seed and the call history alone. */
+ * voxel order, a single order parameter 1 (on every PF point of the voxel: its 8 children with
+ * pf_refine = 2), densities scaled by s_soften and a new kappa drawn with kc' = s_nucl kc.
+ * *n_new = nuclei created. step is recorded only (draws are counted per voxel), so results depend
+ * on the seed and the call history alone. */
 int drx_nucleate(evp_handle *h, uint64_t step, int32_t *n_new);
 
 /* a9-a10 (Sec. 2.4, Eqs. TotalFreeEnergy .. PFGoverning; sparse storage as cited there):
  * nsteps explicit Allen-Cahn steps of the active-set multi-grain model, grain id = argmax,
  * then densities of voxels swept from a deformed to a recrystallised grain are scaled by
- * s_soften. out may be NULL (then F_tot and the statistics are not computed). */
+ * s_soften. out may be NULL (then F_tot and the statistics are not computed).
+ * With pf_refine = 2 (Sec. 2.4's 2:1 PF grid) the steps run on the (2N)^3 PF grid, lengths in
+ * PF spacings dx/2: the driving force rho_tot is interpolated trilinearly (weights 3/4 and 1/4
+ * between the two nearest voxel centres per axis), and a voxel's grain id is the argmax of the
+ * order parameters summed over its 8 PF children (ties to the smaller id). F_tot, X_rex and
+ * n_grains are taken on the PF grid. */
 int pf_step(evp_handle *h, int nsteps, pf_stats *out);
 
 /* Copy the fields in field_mask, packed in bit order, to dst (host or device memory of

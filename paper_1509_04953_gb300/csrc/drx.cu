@@ -80,10 +80,11 @@ __global__ void k_drx_init(long N3, const int32_t *__restrict__ g0, T *__restric
     const int gi = g0[v];
     g[v] = gi;
     draws[v] = 0;
-    for (int j = 0; j < K; ++j) {
-        ids[j * N3 + v] = j == 0 ? gi : -1;
-        eta[j * N3 + v] = j == 0 ? (T)1 : (T)0;
-    }
+    if (ids != nullptr)   // active sets on the mechanics grid (the phase-field grid is set up by pf_init)
+        for (int j = 0; j < K; ++j) {
+            ids[j * N3 + v] = j == 0 ? gi : -1;
+            eta[j * N3 + v] = j == 0 ? (T)1 : (T)0;
+        }
 }
 
 template <typename T>
@@ -149,12 +150,13 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t *__restrict__ cnt, 
 
 // pass 3: fresh ids in ascending voxel order, order parameter reset, softening, kappa redraw
 template <typename T>
-__global__ void __launch_bounds__(kNB) k_nucl_apply(long N3, int K, const uint8_t *__restrict__ mark,
+__global__ void __launch_bounds__(kNB) k_nucl_apply(int n, int r, int K, const uint8_t *__restrict__ mark,
                                                    const int32_t *__restrict__ off, int32_t *__restrict__ g,
                                                    double *__restrict__ k, double *__restrict__ kappa, T *__restrict__ rho,
                                                    int32_t *__restrict__ draws, int32_t *__restrict__ ids,
-                                                   T *__restrict__ eta, int next_id, double s_soften, double kc_new,
-                                                   double q, uint64_t seed) {
+                                                   T *__restrict__ eta, int32_t *__restrict__ gpf, int next_id,
+                                                   double s_soften, double kc_new, double q, uint64_t seed) {
+    const long N3 = (long)n * n * n;
     __shared__ int wsum[kNB / 32];
     const long v = (long)blockIdx.x * kNB + threadIdx.x;
     const int m = (v < N3) ? mark[v] : 0;
@@ -166,16 +168,24 @@ __global__ void __launch_bounds__(kNB) k_nucl_apply(long N3, int K, const uint8_
     int rank = off[blockIdx.x] + __popc(bal & ((1u << lane) - 1u));
     for (int i = 0; i < w; ++i) rank += wsum[i];
     const int id = next_id + rank;
-    for (int j = 0; j < K; ++j) {
-        ids[j * N3 + v] = j == 0 ? id : -1;
-        eta[j * N3 + v] = j == 0 ? (T)1 : (T)0;
+    // the nucleus fills every PF point of this voxel: itself, or its r^3 children on the refined grid
+    const int pm = r * n;
+    const long M3 = (long)pm * pm * pm;
+    const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
+    for (int c = 0; c < r * r * r; ++c) {
+        const long pw = (r * x + c % r) + (long)pm * ((r * y + (c / r) % r) + (long)pm * (r * z + c / (r * r)));
+        for (int j = 0; j < K; ++j) {
+            ids[j * M3 + pw] = j == 0 ? id : -1;
+            eta[j * M3 + pw] = j == 0 ? (T)1 : (T)0;
+        }
+        gpf[pw] = id;
     }
     g[v] = id;
     double kk = 0.0;
     for (int a = 0; a < 12; ++a) {
-        const T r = (T)(s_soften * (double)rho[a * N3 + v]);
-        rho[a * N3 + v] = r;
-        kk += (double)r;
+        const T ra = (T)(s_soften * (double)rho[a * N3 + v]);
+        rho[a * N3 + v] = ra;
+        kk += (double)ra;
     }
     k[v] = kk;
     const int d = draws[v] + 1;
@@ -207,19 +217,18 @@ template <typename T> cudaError_t refresh_k(long N3, const T *rho, double *k, cu
 int nucleate_blocks(long N3) { return (int)((N3 + kNB - 1) / kNB); }
 
 template <typename T>
-cudaError_t nucleate(int n, int K, const int32_t *g_in, int32_t *g, double *k, double *kappa, T *rho,
-                     int32_t *draws, int32_t *ids, T *eta, int32_t *blk_counts, int32_t *blk_offsets,
+cudaError_t nucleate(int n, int r, int K, int32_t *g, double *k, double *kappa, T *rho, int32_t *draws,
+                     int32_t *ids, T *eta, int32_t *gpf, int32_t *blk_counts, int32_t *blk_offsets,
                      int32_t *count_out, int next_id, double s_soften, double kc_new, double q, uint64_t seed,
                      cudaStream_t s) {
-    (void)g_in;
     const long N3 = (long)n * n * n;
     const int nb = nucleate_blocks(N3);
     // the mark bytes live right after the offsets (sized by the caller)
     uint8_t *mark = reinterpret_cast<uint8_t *>(blk_offsets + nb);
     k_nucl_count<<<nb, kNB, 0, s>>>(n, g, k, kappa, mark, blk_counts);
     k_scan<<<1, 1024, 0, s>>>(blk_counts, blk_offsets, nb, count_out);
-    k_nucl_apply<T><<<nb, kNB, 0, s>>>(N3, K, mark, blk_offsets, g, k, kappa, rho, draws, ids, eta, next_id, s_soften,
-                                       kc_new, q, seed);
+    k_nucl_apply<T><<<nb, kNB, 0, s>>>(n, r, K, mark, blk_offsets, g, k, kappa, rho, draws, ids, eta, gpf, next_id,
+                                       s_soften, kc_new, q, seed);
     return cudaGetLastError();
 }
 
@@ -229,11 +238,11 @@ template cudaError_t drx_init<double>(long, const int32_t *, double *, double *,
                                       int32_t *, double *, int, double, double, double, uint64_t, cudaStream_t);
 template cudaError_t refresh_k<float>(long, const float *, double *, cudaStream_t);
 template cudaError_t refresh_k<double>(long, const double *, double *, cudaStream_t);
-template cudaError_t nucleate<float>(int, int, const int32_t *, int32_t *, double *, double *, float *, int32_t *,
-                                     int32_t *, float *, int32_t *, int32_t *, int32_t *, int, double, double, double,
+template cudaError_t nucleate<float>(int, int, int, int32_t *, double *, double *, float *, int32_t *, int32_t *,
+                                     float *, int32_t *, int32_t *, int32_t *, int32_t *, int, double, double, double,
                                      uint64_t, cudaStream_t);
-template cudaError_t nucleate<double>(int, int, const int32_t *, int32_t *, double *, double *, double *, int32_t *,
-                                      int32_t *, double *, int32_t *, int32_t *, int32_t *, int, double, double, double,
-                                      uint64_t, cudaStream_t);
+template cudaError_t nucleate<double>(int, int, int, int32_t *, double *, double *, double *, int32_t *, int32_t *,
+                                      double *, int32_t *, int32_t *, int32_t *, int32_t *, int, double, double,
+                                      double, uint64_t, cudaStream_t);
 
 }  // namespace evp

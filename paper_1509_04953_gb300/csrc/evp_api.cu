@@ -31,6 +31,10 @@ struct evp_handle {
     double *k, *kappa, *partials, *scal;
     int32_t *g0, *g, *gprev, *draws, *ids, *ids2, *flags, *blk_counts, *blk_off, *count, *wlist;
     int nsm;
+    int r, npf;      // phase-field grid: r = 1 (the mechanics grid) or 2 (refined), npf = r n points per edge
+    long N3pf;
+    int32_t *gpf;    // argmax id per PF point (= g when r = 1)
+    double *kpf;     // rho_tot on the PF grid (= k when r = 1)
     int fac_valid;   // stored tangent factors hold a factorisation (of some earlier state) for every voxel
     uint32_t *bitmap;
     int bitmap_words, max_ids, npartials;
@@ -155,6 +159,7 @@ int check_cfg(const evp_config *c, char *why, size_t wl) {
     if (c->scheme == EVP_SCHEME_AL && !(c->al_scale >= 1.0))
         return snprintf(why, wl, "al_scale must be >= 1"), EVP_ERR_ARG;
     if (!(c->newton_adapt >= 0.0)) return snprintf(why, wl, "newton_adapt must be >= 0"), EVP_ERR_ARG;
+    if (c->pf_refine < 0 || c->pf_refine > 2) return snprintf(why, wl, "pf_refine must be 0, 1 or 2"), EVP_ERR_ARG;
     if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE &&
         !(c->newton_mode == EVP_NEWTON_F32_TANGENT && c->precision == EVP_FP64))
         return snprintf(why, wl, "newton_mode %d is not available for precision %d", c->newton_mode, c->precision),
@@ -169,7 +174,9 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     const int K = c->kmax, G = c->grains;
     const long max_ids = c->max_ids ? c->max_ids : (long)G + 8 * N3;
     const int nb = nucleate_blocks(N3);
-    const int npart = std::max(std::max(fft_z_blocks((int)n, T == 8), 2 * pf_stat_blocks(N3) + 1), 14 * al_blocks(N3));
+    const int r = c->pf_refine == 2 ? 2 : 1;
+    const long M3 = (long)r * n * r * n * r * n;   // phase-field points
+    const int npart = std::max(std::max(fft_z_blocks((int)n, T == 8), 2 * pf_stat_blocks(M3) + 1), 14 * al_blocks(N3));
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
         off = (off + 255) & ~(size_t)255;
@@ -179,7 +186,7 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     };
     char *sig = take(6 * N3 * T), *sigk = take(6 * N3 * T), *epse = take(6 * N3 * T), *epst = take(6 * N3 * T);
     char *epsp = take(6 * N3 * T), *deps = take(6 * N3 * T), *rho = take(12 * N3 * T), *tauc = take(N3 * T);
-    char *eta = take(K * N3 * T), *eta2 = take(K * N3 * T), *spec = take(6 * H * 2 * T);
+    char *eta = take(K * M3 * T), *eta2 = take(K * M3 * T), *spec = take(6 * H * 2 * T);
     char *Stab = take(36 * (size_t)G * T), *Mtab = take(72 * (size_t)G * T);
     // stored tangent factors: 21 words per voxel in planes of 16-byte vectors (24 FP32 / 22 FP64 words)
     char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? (T == 4 ? 24 : 22) * N3 * T : 0);
@@ -190,7 +197,8 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *Stabf = take(f32t ? 36 * (size_t)G * 4 : 0), *Mtabf = take(f32t ? 72 * (size_t)G * 4 : 0);
     char *k = take(N3 * 8), *kappa = take(N3 * 8);
     char *g0 = take(N3 * 4), *g = take(N3 * 4), *gprev = take(N3 * 4), *draws = take(N3 * 4);
-    char *ids = take(K * N3 * 4), *ids2 = take(K * N3 * 4);
+    char *ids = take(K * M3 * 4), *ids2 = take(K * M3 * 4);
+    char *gpf = take(r == 2 ? M3 * 4 : 0), *kpf = take(r == 2 ? M3 * 8 : 0);
     char *partials = take(sizeof(double) * npart), *scal = take(sizeof(double) * 64);
     char *flags = take(sizeof(int32_t) * 16);
     char *ctl = take(256);   // FpCtl
@@ -216,6 +224,11 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
         h->blk_counts = (int32_t *)blk_counts; h->blk_off = (int32_t *)blk_off; h->count = (int32_t *)count;
         h->bitmap = (uint32_t *)bitmap; h->bitmap_words = (int)words; h->max_ids = (int)max_ids;
         h->npartials = npart;
+        h->r = r;
+        h->npf = r * (int)n;
+        h->N3pf = M3;
+        h->gpf = r == 2 ? (int32_t *)gpf : h->g;
+        h->kpf = r == 2 ? (double *)kpf : h->k;
     }
     return (off + 255) & ~(size_t)255;
 }
@@ -316,8 +329,9 @@ size_t field_bytes(const evp_handle *h, uint32_t bit) {
         case EVP_F_RHO: return 12 * N3 * T;
         case EVP_F_K: case EVP_F_KAPPA: return N3 * 8;
         case EVP_F_GRAIN: case EVP_F_G0: case EVP_F_DRAWS: return N3 * 4;
-        case EVP_F_IDS: return K * N3 * 4;
-        case EVP_F_ETA: return K * N3 * T;
+        case EVP_F_IDS: return K * (size_t)h->N3pf * 4;
+        case EVP_F_ETA: return K * (size_t)h->N3pf * T;
+        case EVP_F_GRAIN_PF: return (size_t)h->N3pf * 4;
         default: return 0;
     }
 }
@@ -336,6 +350,7 @@ void *field_ptr(evp_handle *h, uint32_t bit) {
         case EVP_F_DRAWS: return h->draws;
         case EVP_F_IDS: return h->ids;
         case EVP_F_ETA: return h->eta;
+        case EVP_F_GRAIN_PF: return h->gpf;
         default: return nullptr;
     }
 }
@@ -587,7 +602,7 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     h->pc.kappa = 0.75 * p->l_gb;
     h->pc.gam = 1.5;
     h->pc.L_dt = p->L_dt;
-    h->pc.Escale = p->zeta * (mu * 1e6) * p->b * p->b * p->dx / p->omega_gb;
+    h->pc.Escale = p->zeta * (mu * 1e6) * p->b * p->b * (p->dx / h->r) / p->omega_gb;   // lengths in PF spacings
     h->pc.drop = p->eta_drop;
     h->pc.G = h->G;
     h->pc.K = h->K;
@@ -647,11 +662,13 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     CK(cudaMemsetAsync(h->epsp, 0, fb, h->st));
     CK(cudaMemsetAsync(h->deps, 0, fb, h->st));
     if (h->dbl)
-        CK(drx_init<double>(h->N3, h->g0, (double *)h->rho, h->k, h->kappa, h->g, h->draws, h->ids, (double *)h->eta,
-                            h->K, p->rho0, p->kc, p->q, seed, h->st));
+        CK(drx_init<double>(h->N3, h->g0, (double *)h->rho, h->k, h->kappa, h->g, h->draws, nullptr, nullptr, h->K,
+                            p->rho0, p->kc, p->q, seed, h->st));
     else
-        CK(drx_init<float>(h->N3, h->g0, (float *)h->rho, h->k, h->kappa, h->g, h->draws, h->ids, (float *)h->eta, h->K,
+        CK(drx_init<float>(h->N3, h->g0, (float *)h->rho, h->k, h->kappa, h->g, h->draws, nullptr, nullptr, h->K,
                            p->rho0, p->kc, p->q, seed, h->st));
+    CK(pf_init(h->n, h->r, h->K, h->g0, h->ids, h->eta, h->dbl, h->gpf, h->st));
+    if (h->r == 2) CK(pf_interp(h->n, h->k, h->kpf, h->st));
     CK(cudaStreamSynchronize(h->st));
     return EVP_OK;
 }
@@ -905,13 +922,13 @@ int drx_nucleate(evp_handle *h, uint64_t step, int32_t *n_new) {
     const double kc_new = h->p.s_nucl * h->p.kc;
     { PROF(9, 3);
     if (h->dbl)
-        CK(nucleate<double>(h->n, h->K, h->g, h->g, h->k, h->kappa, (double *)h->rho, h->draws, h->ids,
-                            (double *)h->eta, h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften, kc_new,
-                            h->p.q, h->seed, h->st));
+        CK(nucleate<double>(h->n, h->r, h->K, h->g, h->k, h->kappa, (double *)h->rho, h->draws, h->ids,
+                            (double *)h->eta, h->gpf, h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften,
+                            kc_new, h->p.q, h->seed, h->st));
     else
-        CK(nucleate<float>(h->n, h->K, h->g, h->g, h->k, h->kappa, (float *)h->rho, h->draws, h->ids, (float *)h->eta,
-                           h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften, kc_new, h->p.q, h->seed,
-                           h->st));
+        CK(nucleate<float>(h->n, h->r, h->K, h->g, h->k, h->kappa, (float *)h->rho, h->draws, h->ids,
+                           (float *)h->eta, h->gpf, h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften,
+                           kc_new, h->p.q, h->seed, h->st));
     }
     int32_t c = 0;
     CK(cudaMemcpyAsync(&c, h->count, sizeof c, cudaMemcpyDeviceToHost, h->st));
@@ -929,31 +946,38 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
     const long N3 = h->N3;
     CK(cudaMemcpyAsync(h->gprev, h->g, sizeof(int32_t) * N3, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemsetAsync(h->flags + 2, 0, sizeof(int32_t), h->st));
+    if (h->r == 2) { PROF(10, 1); CK(pf_interp(h->n, h->k, h->kpf, h->st)); }   // driving force on the PF grid
     for (int s = 0; s < nsteps; ++s) {
         PROF(10, 1);
         if (h->dbl)
-            CK(pf_one_step<double>(h->n, h->ids, (double *)h->eta, h->ids2, (double *)h->eta2, h->g, h->k, h->pc,
-                                   h->flags + 2, h->st));
+            CK(pf_one_step<double>(h->npf, h->ids, (double *)h->eta, h->ids2, (double *)h->eta2, h->gpf, h->kpf,
+                                   h->pc, h->flags + 2, h->st));
         else
-            CK(pf_one_step<float>(h->n, h->ids, (float *)h->eta, h->ids2, (float *)h->eta2, h->g, h->k, h->pc,
+            CK(pf_one_step<float>(h->npf, h->ids, (float *)h->eta, h->ids2, (float *)h->eta2, h->gpf, h->kpf, h->pc,
                                   h->flags + 2, h->st));
         int32_t *ti = h->ids; h->ids = h->ids2; h->ids2 = ti;
         void *te = h->eta; h->eta = h->eta2; h->eta2 = te;
+    }
+    if (h->r == 2 && nsteps > 0) {   // grain ids of the mechanics grid from the PF children
+        PROF(11, 1);
+        if (h->dbl) CK(pf_restrict<double>(h->n, h->K, h->ids, (const double *)h->eta, h->g, h->st));
+        else CK(pf_restrict<float>(h->n, h->K, h->ids, (const float *)h->eta, h->g, h->st));
     }
     { PROF(11, 1);
     if (h->dbl) CK(pf_soften<double>(N3, h->gprev, h->g, (double *)h->rho, h->k, h->G, h->p.s_soften, h->st));
     else CK(pf_soften<float>(N3, h->gprev, h->g, (float *)h->rho, h->k, h->G, h->p.s_soften, h->st));
     }
+    if (h->r == 2) { PROF(11, 1); CK(pf_interp(h->n, h->k, h->kpf, h->st)); }   // softened densities
     int32_t ovf = 0;
     if (out) {
-        const int nb = pf_stat_blocks(N3);
+        const int nb = pf_stat_blocks(h->N3pf);
         { PROF(12, 3);
         if (h->dbl)
-            CK(pf_stats_launch<double>(h->n, h->ids, (double *)h->eta, h->g, h->k, h->pc, h->bitmap, h->bitmap_words,
-                                h->partials, h->st));
+            CK(pf_stats_launch<double>(h->npf, h->ids, (double *)h->eta, h->gpf, h->kpf, h->pc, h->bitmap,
+                                       h->bitmap_words, h->partials, h->st));
         else
-            CK(pf_stats_launch<float>(h->n, h->ids, (float *)h->eta, h->g, h->k, h->pc, h->bitmap, h->bitmap_words,
-                               h->partials, h->st));
+            CK(pf_stats_launch<float>(h->npf, h->ids, (float *)h->eta, h->gpf, h->kpf, h->pc, h->bitmap,
+                                      h->bitmap_words, h->partials, h->st));
         CK(reduce_partials(h->partials, nb, 2, h->scal + 8, h->st));
         }
         double hs[2], ng = 0;
@@ -963,7 +987,7 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
         CK(cudaStreamSynchronize(h->st));
         if (h->prof) prof_collect(h);
         out->F_tot = hs[0];
-        out->X_rex = hs[1] / (double)N3;
+        out->X_rex = hs[1] / (double)h->N3pf;
         out->n_grains = (int)ng;
         out->overflow = ovf;
     } else {
@@ -976,9 +1000,9 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
 
 int evp_fields_bytes(const evp_handle *h, uint32_t mask, size_t *bytes) {
     if (!h || !bytes) return EVP_ERR_ARG;
-    if (mask == 0 || (mask >> 13) != 0) return EVP_ERR_ARG;
+    if (mask == 0 || (mask >> 14) != 0) return EVP_ERR_ARG;
     size_t tot = 0;
-    for (uint32_t bit = 1; bit <= EVP_F_ETA; bit <<= 1)
+    for (uint32_t bit = 1; bit <= EVP_F_GRAIN_PF; bit <<= 1)
         if (mask & bit) tot += field_bytes(h, bit);
     *bytes = tot;
     return EVP_OK;
@@ -991,7 +1015,7 @@ int get_fields(evp_handle *h, uint32_t mask, void *dst, size_t bytes, int dst_is
     if (bytes != need) return fail(h, EVP_ERR_ARG, "get_fields: %zu bytes given, %zu expected", bytes, need);
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     size_t off = 0;
-    for (uint32_t bit = 1; bit <= EVP_F_ETA; bit <<= 1) {
+    for (uint32_t bit = 1; bit <= EVP_F_GRAIN_PF; bit <<= 1) {
         if (!(mask & bit)) continue;
         const size_t fb = field_bytes(h, bit);
         const void *src = field_ptr(h, bit);
@@ -1010,12 +1034,13 @@ int get_fields(evp_handle *h, uint32_t mask, void *dst, size_t bytes, int dst_is
 int set_fields(evp_handle *h, uint32_t mask, const void *src, size_t bytes, int src_is_device) {
     size_t need = 0;
     if (!h || !src) return fail(h, EVP_ERR_ARG, "NULL argument to set_fields");
-    if (mask & (EVP_F_EPS | EVP_F_G0)) return fail(h, EVP_ERR_ARG, "EVP_F_EPS and EVP_F_G0 cannot be set");
+    if (mask & (EVP_F_EPS | EVP_F_G0 | EVP_F_GRAIN_PF))
+        return fail(h, EVP_ERR_ARG, "EVP_F_EPS, EVP_F_G0 and EVP_F_GRAIN_PF cannot be set");
     if (evp_fields_bytes(h, mask, &need) != EVP_OK) return fail(h, EVP_ERR_ARG, "bad field mask 0x%x", mask);
     if (bytes != need) return fail(h, EVP_ERR_ARG, "set_fields: %zu bytes given, %zu expected", bytes, need);
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     size_t off = 0;
-    for (uint32_t bit = 1; bit <= EVP_F_ETA; bit <<= 1) {
+    for (uint32_t bit = 1; bit <= EVP_F_GRAIN_PF; bit <<= 1) {
         if (!(mask & bit)) continue;
         const size_t fb = field_bytes(h, bit);
         CK(cudaMemcpyAsync(field_ptr(h, bit), (const char *)src + off, fb, kind, h->st));
@@ -1024,6 +1049,7 @@ int set_fields(evp_handle *h, uint32_t mask, const void *src, size_t bytes, int 
     if (mask & EVP_F_RHO) {
         if (h->dbl) CK(refresh_k<double>(h->N3, (double *)h->rho, h->k, h->st));
         else CK(refresh_k<float>(h->N3, (float *)h->rho, h->k, h->st));
+        if (h->r == 2) CK(pf_interp(h->n, h->k, h->kpf, h->st));
     }
     CK(cudaStreamSynchronize(h->st));
     return EVP_OK;

@@ -90,8 +90,8 @@ cudaError_t drx_init(long N3, const int32_t *g0, T *rho, double *k, double *kapp
 template <typename T> cudaError_t refresh_k(long N3, const T *rho, double *k, cudaStream_t s);
 int nucleate_blocks(long N3);
 template <typename T>
-cudaError_t nucleate(int n, int K, const int32_t *g_in, int32_t *g, double *k, double *kappa, T *rho,
-                     int32_t *draws, int32_t *ids, T *eta, int32_t *blk_counts, int32_t *blk_offsets,
+cudaError_t nucleate(int n, int r, int K, int32_t *g, double *k, double *kappa, T *rho, int32_t *draws,
+                     int32_t *ids, T *eta, int32_t *gpf, int32_t *blk_counts, int32_t *blk_offsets,
                      int32_t *count_out, int next_id, double s_soften, double kc_new, double q, uint64_t seed,
                      cudaStream_t s);
 
@@ -107,6 +107,13 @@ template <typename T>
 cudaError_t pf_soften(long N3, const int32_t *gprev, const int32_t *g, T *rho, double *k, int G, double s_soften,
                       cudaStream_t s);
 int pf_stat_blocks(long N3);
+// 2:1 PF grid (Sec. 2.4): kpf[(2n)^3] = trilinear interpolation of k[n^3]; g[n^3] = argmax of the order
+// parameters summed over each voxel's 8 PF children; initial PF active sets from the parent grain.
+cudaError_t pf_interp(int n, const double *k, double *kpf, cudaStream_t s);
+template <typename T>
+cudaError_t pf_restrict(int n, int K, const int32_t *ids, const T *eta, int32_t *g, cudaStream_t s);
+cudaError_t pf_init(int n, int r, int K, const int32_t *g0, int32_t *ids, void *eta, int eta_double, int32_t *gpf,
+                    cudaStream_t s);
 template <typename T>
 cudaError_t pf_stats_launch(int n, const int32_t *ids, const T *eta, const int32_t *g, const double *k, PFConst pc,
                      uint32_t *bitmap, int bitmap_words, double *partials, cudaStream_t s);

@@ -252,6 +252,103 @@ __global__ void k_reduce(const double *__restrict__ part, int nparts, int nvals,
     if (threadIdx.x == 0) out[c] = s;
 }
 
+// ---- 2:1 phase-field grid (Sec. 2.4) ----
+// Both grids are cell-centred and periodic: voxel i spans [i, i+1), PF cell I spans [I/2, (I+1)/2).
+// Along each axis a PF centre lies between its parent voxel's centre (weight 3/4) and the neighbour on
+// its side (weight 1/4). PF point w = X + 2n (Y + 2n Z).
+__device__ __forceinline__ void interp_axis(int I, int n, int (&idx)[2], double (&wt)[2]) {
+    const int i = I >> 1;
+    if ((I & 1) == 0) { idx[0] = (i + n - 1) % n; idx[1] = i; wt[0] = 0.25; wt[1] = 0.75; }
+    else { idx[0] = i; idx[1] = (i + 1) % n; wt[0] = 0.75; wt[1] = 0.25; }
+}
+
+// kpf = trilinear interpolation of k (rho_tot); the eight terms in (z, y, x) order, weights (wz wy) wx
+__global__ void k_interp_k(int n, const double *__restrict__ k, double *__restrict__ kpf) {
+    const int m = 2 * n;
+    const long M3 = (long)m * m * m;
+    const long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= M3) return;
+    const int X = (int)(w % m), Y = (int)((w / m) % m), Z = (int)(w / ((long)m * m));
+    int ix[2], iy[2], iz[2];
+    double wx[2], wy[2], wz[2];
+    interp_axis(X, n, ix, wx);
+    interp_axis(Y, n, iy, wy);
+    interp_axis(Z, n, iz, wz);
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                acc += (wz[a] * wy[b]) * wx[c] * k[ix[c] + (long)n * (iy[b] + (long)n * iz[a])];
+    kpf[w] = acc;
+}
+
+// A voxel's grain id from its eight PF children c = dx + 2 dy + 4 dz: the id with the largest sum of
+// order parameters over the children (summed in c order), ties to the smaller id. The children's
+// lists are sorted by id, so the eight are merged in ascending id order.
+template <typename T>
+__global__ void k_restrict(int n, int K, const int32_t *__restrict__ ids, const T *__restrict__ eta,
+                           int32_t *__restrict__ g) {
+    const long N3 = (long)n * n * n;
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N3) return;
+    const int m = 2 * n;
+    const long M3 = (long)m * m * m;
+    const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
+    long ch[8];
+    int pos[8], head[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        ch[c] = (2 * x + (c & 1)) + (long)m * ((2 * y + ((c >> 1) & 1)) + (long)m * (2 * z + (c >> 2)));
+        pos[c] = 0;
+        const int id = ids[ch[c]];
+        head[c] = id < 0 ? kEmpty : id;
+    }
+    int best = -1;
+    double bsum = 0.0;
+    for (int guard = 0; guard < 8 * KM; ++guard) {
+        int cmin = head[0];
+#pragma unroll
+        for (int c = 1; c < 8; ++c) cmin = min(cmin, head[c]);
+        if (cmin == kEmpty) break;
+        double sum = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (head[c] == cmin) {
+                sum += (double)eta[pos[c] * M3 + ch[c]];
+                ++pos[c];
+                int nx = kEmpty;
+                if (pos[c] < K) {
+                    const int id = ids[pos[c] * M3 + ch[c]];
+                    nx = id < 0 ? kEmpty : id;
+                }
+                head[c] = nx;
+            }
+        }
+        if (best < 0 || sum > bsum) { best = cmin; bsum = sum; }   // ascending ids: a tie keeps the smaller
+    }
+    g[v] = best;
+}
+
+// initial active sets on the PF grid: one order parameter 1 of the parent voxel's grain
+__global__ void k_pf_init(int n, int r, int K, const int32_t *__restrict__ g0, int32_t *__restrict__ ids,
+                          void *__restrict__ eta, int eta_double, int32_t *__restrict__ gpf) {
+    const int m = r * n;
+    const long M3 = (long)m * m * m;
+    const long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= M3) return;
+    const int X = (int)(w % m), Y = (int)((w / m) % m), Z = (int)(w / ((long)m * m));
+    const int gi = g0[X / r + (long)n * (Y / r + (long)n * (Z / r))];
+    for (int j = 0; j < K; ++j) {
+        ids[j * M3 + w] = j == 0 ? gi : -1;
+        if (eta_double) static_cast<double *>(eta)[j * M3 + w] = j == 0 ? 1.0 : 0.0;
+        else static_cast<float *>(eta)[j * M3 + w] = j == 0 ? 1.f : 0.f;
+    }
+    gpf[w] = gi;
+}
+
 }  // namespace
 
 template <typename T>
@@ -291,6 +388,29 @@ cudaError_t reduce_partials(const double *partials, int nparts, int nvals, doubl
     return cudaGetLastError();
 }
 
+cudaError_t pf_interp(int n, const double *k, double *kpf, cudaStream_t s) {
+    const long M3 = 8L * n * n * n;
+    k_interp_k<<<(int)((M3 + 255) / 256), 256, 0, s>>>(n, k, kpf);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pf_restrict(int n, int K, const int32_t *ids, const T *eta, int32_t *g, cudaStream_t s) {
+    if (K > KM || K < 1) return cudaErrorInvalidValue;
+    const long N3 = (long)n * n * n;
+    k_restrict<T><<<(int)((N3 + 127) / 128), 128, 0, s>>>(n, K, ids, eta, g);
+    return cudaGetLastError();
+}
+
+cudaError_t pf_init(int n, int r, int K, const int32_t *g0, int32_t *ids, void *eta, int eta_double, int32_t *gpf,
+                    cudaStream_t s) {
+    const long M3 = (long)r * n * r * n * r * n;
+    k_pf_init<<<(int)((M3 + 255) / 256), 256, 0, s>>>(n, r, K, g0, ids, eta, eta_double, gpf);
+    return cudaGetLastError();
+}
+
+template cudaError_t pf_restrict<float>(int, int, const int32_t *, const float *, int32_t *, cudaStream_t);
+template cudaError_t pf_restrict<double>(int, int, const int32_t *, const double *, int32_t *, cudaStream_t);
 template cudaError_t pf_one_step<float>(int, const int32_t *, const float *, int32_t *, float *, int32_t *,
                                         const double *, PFConst, int32_t *, cudaStream_t);
 template cudaError_t pf_one_step<double>(int, const int32_t *, const double *, int32_t *, double *, int32_t *,

@@ -19,14 +19,16 @@ EVP_ERR = {-1: "EVP_ERR_ARG", -2: "EVP_ERR_CUDA", -3: "EVP_ERR_NEWTON", -4: "EVP
            -5: "EVP_ERR_NONFINITE", -6: "EVP_ERR_OOM"}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_fast": 2}
 
-F_SIG, F_EPS, F_EPSP, F_EPSE, F_DEPS, F_RHO, F_K, F_KAPPA, F_GRAIN, F_G0, F_DRAWS, F_IDS, F_ETA = (
-    1 << i for i in range(13))
+F_SIG, F_EPS, F_EPSP, F_EPSE, F_DEPS, F_RHO, F_K, F_KAPPA, F_GRAIN, F_G0, F_DRAWS, F_IDS, F_ETA, F_GRAIN_PF = (
+    1 << i for i in range(14))
 FIELDS = {"sig": F_SIG, "eps": F_EPS, "epsp": F_EPSP, "epse": F_EPSE, "deps": F_DEPS, "rho": F_RHO, "k": F_K,
-          "kappa": F_KAPPA, "g": F_GRAIN, "g0": F_G0, "draws": F_DRAWS, "ids": F_IDS, "eta": F_ETA}
+          "kappa": F_KAPPA, "g": F_GRAIN, "g0": F_G0, "draws": F_DRAWS, "ids": F_IDS, "eta": F_ETA,
+          "gpf": F_GRAIN_PF}
 # (components, kind) with kind "T" = field precision, "f8" = double, "i4" = int32, "K" = kmax components
 _FIELD_SHAPE = {"sig": (6, "T"), "eps": (6, "T"), "epsp": (6, "T"), "epse": (6, "T"), "deps": (6, "T"),
                 "rho": (12, "T"), "k": (1, "f8"), "kappa": (1, "f8"), "g": (1, "i4"), "g0": (1, "i4"),
-                "draws": (1, "i4"), "ids": ("K", "i4"), "eta": ("K", "T")}
+                "draws": (1, "i4"), "ids": ("K", "i4"), "eta": ("K", "T"), "gpf": (1, "i4")}
+_PF_FIELDS = ("ids", "eta", "gpf")   # on the phase-field grid ((r n)^3 points)
 
 
 class EVPError(RuntimeError):
@@ -38,7 +40,7 @@ class Config(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("allow_unconverged", C.c_int),
                 ("newton_tol", C.c_double), ("newton_max", C.c_int), ("predictor", C.c_int), ("max_ids", C.c_int),
                 ("newton_mode", C.c_int), ("scheme", C.c_int), ("al_scale", C.c_double),
-                ("newton_adapt", C.c_double)]
+                ("newton_adapt", C.c_double), ("pf_refine", C.c_int)]
 
 
 class Params(C.Structure):
@@ -122,7 +124,7 @@ SCHEMES = {"basic": 0, "al": 1}
 
 def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, allow_unconverged=0,
                 newton_tol=None, newton_max=50, predictor=1, max_ids=0, newton=None, scheme="basic",
-                al_scale=6.0, newton_adapt=None) -> Config:
+                al_scale=6.0, newton_adapt=None, pf_refine=1) -> Config:
     if newton_tol is None:
         newton_tol = 1e-12 if precision == "fp64" else 1e-5
     if newton is None:
@@ -134,7 +136,7 @@ def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, a
         # the FP64 path stays the reference: every local problem solved to newton_tol
         newton_adapt = 0.0 if precision == "fp64" else 0.1
     return Config(n, grains, kmax, PRECISION[precision], tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                  predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale, newton_adapt)
+                  predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale, newton_adapt, pf_refine)
 
 
 def make_params(mat) -> Params:
@@ -162,6 +164,9 @@ class Solver:
         self.precision = precision
         self.cfg = make_config(n, grains, precision, **cfg_kw)
         self.K = self.cfg.kmax
+        self.r = 2 if self.cfg.pf_refine == 2 else 1
+        self.npf = self.r * n
+        self.N3pf = self.npf ** 3
         self.dtype = np.float64 if precision == "fp64" else np.float32
         self.params = make_params(mat)
         nbytes = workspace_bytes(self.cfg)
@@ -233,10 +238,14 @@ class Solver:
         dt = {"T": self.dtype, "f8": np.float64, "i4": np.int32}[kind]
         return comp, dt
 
+    def _points(self, name):
+        return self.N3pf if name in _PF_FIELDS else self.N3
+
     def get(self, name):
-        """Copy one field to host memory as a (components, N^3) array."""
+        """Copy one field to host memory as a (components, points) array (N^3 voxels, or (r N)^3 PF points
+        for ids, eta and gpf)."""
         comp, dt = self._shape(name)
-        out = np.empty((comp, self.N3), dtype=dt)
+        out = np.empty((comp, self._points(name)), dtype=dt)
         self._check("get_fields", load().get_fields(self.h, FIELDS[name], out.ctypes.data, out.nbytes, 0))
         return out
 
@@ -245,14 +254,14 @@ class Solver:
         torch = _torch()
         comp, dt = self._shape(name)
         tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32}[dt]
-        out = torch.empty((comp, self.N3), dtype=tdt, device="cuda")
+        out = torch.empty((comp, self._points(name)), dtype=tdt, device="cuda")
         self._check("get_fields", load().get_fields(self.h, FIELDS[name], out.data_ptr(),
                                                      out.numel() * out.element_size(), 1))
         return out
 
     def set(self, name, value):
         comp, dt = self._shape(name)
-        arr = np.ascontiguousarray(np.asarray(value, dtype=dt).reshape(comp, self.N3))
+        arr = np.ascontiguousarray(np.asarray(value, dtype=dt).reshape(comp, self._points(name)))
         self._check("set_fields", load().set_fields(self.h, FIELDS[name], arr.ctypes.data, arr.nbytes, 0))
 
     def scalars(self):

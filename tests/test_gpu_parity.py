@@ -37,7 +37,8 @@ def make_pair(ev, mat, n, G, seed, precision="fp64", **kw):
     quat = synth.orientations(G, seed)
     g0 = O.voronoi(n, seeds)
     gpu = ev.Solver(n, G, g0, quat, mat, seed, precision=precision, **kw)
-    okw = {k: v for k, v in kw.items() if k in ("tol", "max_iter", "allow_unconverged", "kmax", "predictor")}
+    okw = {k: v for k, v in kw.items() if k in ("tol", "max_iter", "allow_unconverged", "kmax", "predictor",
+                                                 "pf_refine")}
     ref = O.State(n, G, g0, quat, mat, seed=seed, **okw)
     return gpu, ref, g0
 
@@ -270,6 +271,84 @@ def test_pf_mixed_close_to_fp64(ev, mat):
 
 
 # ------------------------------------------------------------------------------------------
+# a8-a10 on the 2:1 phase-field grid (Sec. 2.4)
+# ------------------------------------------------------------------------------------------
+def refined_setup(ev, mat, n, G, seed, kmax=8, nuclei=(5, 3000, 9000, 20000)):
+    gpu, ref, g0 = make_pair(ev, mat, n, G, seed, kmax=kmax, pf_refine=2)
+    rng = np.random.default_rng(seed)
+    rho = np.repeat(rng.uniform(2e13, 8e13, size=(1, n ** 3)), 12, axis=0)
+    ids = ref.ifield("ids")                              # (kmax, (2n)^3): PF points
+    for j, w in enumerate(nuclei):
+        ids[0, w] = G + j
+    ref.next_id = G + len(nuclei)
+    ref.field("rho")[:] = rho
+    ref.refresh_derived()
+    gpu.set("rho", rho)
+    gpu.set("ids", ids.copy())
+    sc = gpu.scalars()
+    gpu.set_scalars(sc["E"], sc["dE_prev"], sc["have_prev"], G + len(nuclei))
+    return gpu, ref
+
+
+def test_pf_refined_grid_steps_bit_exact_fp64(ev, mat):
+    n, G = 16, 8
+    gpu, ref = refined_setup(ev, mat, n, G, 3)
+    assert gpu.get("ids").shape == (8, (2 * n) ** 3)
+    assert np.array_equal(gpu.get("gpf")[0], ref.ifield("gpf"))
+    for call in range(3):
+        rc, st = gpu.pf_step(5)
+        rco, sto = ref.pf_step(5)
+        assert np.array_equal(gpu.get("ids"), ref.ifield("ids"))
+        assert np.array_equal(gpu.get("eta"), ref.field("eta"))          # bitwise (no FMA contraction)
+        assert np.array_equal(gpu.get("gpf")[0], ref.ifield("gpf"))
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))          # restriction to the mechanics grid
+        assert st.n_grains == sto.n_grains and st.X_rex == sto.X_rex
+        assert st.overflow == sto.overflow
+        assert abs(st.F_tot / sto.F_tot - 1) < 1e-12
+        assert rel(gpu.get("rho"), ref.field("rho")) == 0.0              # sweep softening on the coarse grid
+
+
+def test_nucleation_on_the_refined_grid_bit_exact(ev, mat):
+    n, G, seed = 16, 8, 77
+    gpu, ref, g0 = make_pair(ev, mat, n, G, seed, pf_refine=2)
+    rng = np.random.default_rng(5)
+    rho = np.repeat(rng.uniform(0.5e13, 3.0e13, size=(1, n ** 3)), 12, axis=0)
+    gpu.set("rho", rho)
+    ref.field("rho")[:] = rho
+    ref.refresh_derived()
+    for step in range(2):
+        rc, nn = gpu.nucleate(step)
+        rco, nno = ref.nucleate(step)
+        assert nn == nno and nn > 5
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))
+        assert np.array_equal(gpu.get("gpf")[0], ref.ifield("gpf"))
+        assert np.array_equal(gpu.get("ids"), ref.ifield("ids"))
+        assert np.array_equal(gpu.get("draws")[0], ref.ifield("draws"))
+        assert rel(gpu.get("rho"), ref.field("rho")) == 0.0
+        assert gpu.next_id == ref.next_id
+        _, ps = gpu.pf_step(3)
+        _, pso = ref.pf_step(3)
+        assert np.array_equal(gpu.get("gpf")[0], ref.ifield("gpf"))
+        assert abs(ps.F_tot / pso.F_tot - 1) < 1e-12
+
+
+def test_pf_refined_mixed_close_to_fp64(ev, mat):
+    n, G = 16, 8
+    a, _ = refined_setup(ev, mat, n, G, 4)
+    seeds = synth.voronoi_seeds(n, G, 4)
+    b = ev.Solver(n, G, O.voronoi(n, seeds), synth.orientations(G, 4), mat, 4, precision="mixed", pf_refine=2)
+    b.set("rho", a.get("rho").astype(np.float32))
+    b.set("ids", a.get("ids"))
+    sc = a.scalars()
+    b.set_scalars(sc["E"], sc["dE_prev"], sc["have_prev"], sc["next_id"])
+    _, sa = a.pf_step(10)
+    _, sb = b.pf_step(10)
+    assert abs(sb.F_tot / sa.F_tot - 1) < 1e-5
+    assert np.mean(a.get("gpf")[0] == b.get("gpf")[0]) > 0.999
+    assert np.mean(a.get("g")[0] == b.get("g")[0]) > 0.999
+
+
+# ------------------------------------------------------------------------------------------
 # coupled increments (a2-a10) at the small workload
 # ------------------------------------------------------------------------------------------
 def test_coupled_run_matches_oracle(ev, mat):
@@ -294,6 +373,29 @@ def test_coupled_run_matches_oracle(ev, mat):
         assert rel(st.sig_mean, sto.sig_mean) < 1e-8
         assert abs(ps.F_tot / pso.F_tot - 1) < 1e-9
     assert flips == 0
+
+
+def test_coupled_run_on_the_refined_pf_grid_matches_oracle(ev, mat):
+    n, G, seed = 8, 4, synth.BASE_SEED
+    kw = dict(tol=1e-9, max_iter=3000, pf_refine=2)
+    gpu, ref, _ = make_pair(ev, mat, n, G, seed, **kw)
+    rho = np.repeat(np.random.default_rng(1).uniform(2e13, 6e13, size=(1, n ** 3)), 12, axis=0)
+    gpu.set("rho", rho)
+    ref.field("rho")[:] = rho
+    ref.refresh_derived()
+    for inc in range(3):
+        rc, st = gpu.increment(-1e-3, 1.0)
+        rco, sto = ref.increment(-1e-3, 1.0)
+        assert rc == 0 and rco == 0
+        _, nn = gpu.nucleate(inc)
+        _, nno = ref.nucleate(inc)
+        assert nn == nno
+        _, ps = gpu.pf_step(5)
+        _, pso = ref.pf_step(5)
+        assert np.array_equal(gpu.get("gpf")[0], ref.ifield("gpf"))
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))
+        assert rel(st.sig_mean, sto.sig_mean) < 1e-8
+        assert abs(ps.F_tot / pso.F_tot - 1) < 1e-9
 
 
 # ------------------------------------------------------------------------------------------
