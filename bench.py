@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=-1, help="FP64 comparison increments (-1 = warmup+steps)")
     ap.add_argument("--fast-steps", type=int, default=2, help="timed increments of the FP32-solve mixed path")
     ap.add_argument("--al-steps", type=int, default=1, help="run the augmented-Lagrangian companion (0 = skip)")
+    ap.add_argument("--pf2-steps", type=int, default=2,
+                    help="timed increments of the companion on the 2:1 phase-field grid (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
@@ -262,6 +264,8 @@ def native(args, ws, rank, local):
         res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
     if args.al_steps > 0:
         res["augmented_lagrangian"] = al_companion(args, wl, g0, quat, mat, torch, evp, warm + timed)
+    if args.pf2_steps > 0:
+        res["pf_grid_2to1"] = pf2_companion(args, wl, g0, quat, mat, torch, evp, pk)
     # FP64 companion run on the same seeded input
     n64 = args.warmup + args.steps if args.fp64_steps < 0 else args.fp64_steps
     if n64 > 0:
@@ -363,6 +367,34 @@ def fast_companion(args, wl, g0, quat, mat, torch, evp):
     return {"voxel_iters_per_s": wl.n ** 3 * sum(r["it"] for r in h) / evp_s,
             "drx_increments_per_s": len(h) / step_s, "increments": len(h),
             "fixed_point_iterations": [r["it"] for r in h]}
+
+
+def pf2_companion(args, wl, g0, quat, mat, torch, evp, pk):
+    """The same increments with the phase field on the paper's 2:1 grid ((2n)^3 PF points): DRX
+    increments/s and the live cost of one PF step there, against its algorithmic bytes."""
+    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision,
+                   tol=args.tol64 if args.precision == "fp64" else args.tol, max_iter=5000,
+                   newton_adapt=args.newton_adapt, pf_refine=2)
+    run_steps(s, 1, wl.dE33, wl.dt, wl.pf_steps, torch)
+    s.set_profiling(True)
+    s.kernel_times(reset=True)
+    h = run_steps(s, args.pf2_steps, wl.dE33, wl.dt, wl.pf_steps, torch)
+    kt = s.kernel_times(reset=True)
+    step_s = sum(r["step_ms"] for r in h) / 1e3
+    T = 4 if args.precision != "fp64" else 8
+    M3 = (2 * wl.n) ** 3
+    ms, nl = kt.get("pf_step", (0.0, 0))
+    out = {"pf_points": M3, "drx_increments_per_s": len(h) / step_s, "ms_per_step": 1e3 * step_s / len(h),
+           "increments": len(h), "X_rex": h[-1]["X_rex"], "n_grains": h[-1]["n_grains"]}
+    if nl:
+        # PF launches include one interpolation of the driving force per call
+        steps = nl - len(h)
+        per = ms / max(steps, 1) / 1e3
+        b = hbm_bytes_per_voxel("pf_step", wl.n, T) * M3
+        out["pf_step_us"] = round(1e6 * per, 1)
+        out["pf_step_GB/s"] = round(b / per / 1e9, 1)
+        out["pf_step_frac"] = round(b / per / 1e9 / pk.get("hbm_gbs", 6800.0), 3)
+    return out
 
 
 def al_companion(args, wl, g0, quat, mat, torch, evp, basic_hist):

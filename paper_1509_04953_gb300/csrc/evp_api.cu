@@ -667,7 +667,7 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     else
         CK(drx_init<float>(h->N3, h->g0, (float *)h->rho, h->k, h->kappa, h->g, h->draws, nullptr, nullptr, h->K,
                            p->rho0, p->kc, p->q, seed, h->st));
-    CK(pf_init(h->n, h->r, h->K, h->g0, h->ids, h->eta, h->dbl, h->gpf, h->st));
+    CK(pf_init(h->n, h->r, h->K, h->g0, h->ids, h->eta, h->ids2, h->eta2, h->dbl, h->gpf, h->st));
     if (h->r == 2) CK(pf_interp(h->n, h->k, h->kpf, h->st));
     CK(cudaStreamSynchronize(h->st));
     return EVP_OK;

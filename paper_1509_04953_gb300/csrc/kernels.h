@@ -112,8 +112,8 @@ int pf_stat_blocks(long N3);
 cudaError_t pf_interp(int n, const double *k, double *kpf, cudaStream_t s);
 template <typename T>
 cudaError_t pf_restrict(int n, int K, const int32_t *ids, const T *eta, int32_t *g, cudaStream_t s);
-cudaError_t pf_init(int n, int r, int K, const int32_t *g0, int32_t *ids, void *eta, int eta_double, int32_t *gpf,
-                    cudaStream_t s);
+cudaError_t pf_init(int n, int r, int K, const int32_t *g0, int32_t *ids, void *eta, int32_t *ids2, void *eta2,
+                    int eta_double, int32_t *gpf, cudaStream_t s);
 template <typename T>
 cudaError_t pf_stats_launch(int n, const int32_t *ids, const T *eta, const int32_t *g, const double *k, PFConst pc,
                      uint32_t *bitmap, int bitmap_words, double *partials, cudaStream_t s);

@@ -43,9 +43,6 @@ __device__ __forceinline__ Nbr neighbours(int n, long v) {
 
 constexpr int kEmpty = 0x7fffffff;
 
-template <typename T> __device__ __forceinline__ bool better(T ea, int ia, T eb, int ib) {
-    return ea > eb || (ea == eb && ia < ib);
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta,
@@ -77,15 +74,19 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
         const int id = ids[nb.q[q]];
         head[q] = id < 0 ? kEmpty : id;
     }
+    // Kept entries in ascending id order (the merge yields candidates in that order): append; past K,
+    // drop the worst (smallest value, the larger id among equal values), which leaves the top K by
+    // (value desc, id asc) -- the same set a full sort would keep -- still in id order.
     int kid[KM + 1];
     T ke[KM + 1];
 #pragma unroll
     for (int j = 0; j <= KM; ++j) {
         kid[j] = kEmpty;
-        ke[j] = (T)-INFINITY;
+        ke[j] = (T)0;
     }
-    int best_id = kEmpty;
-    T best = (T)-INFINITY;
+    int cnt = 0;
+    int best_id = kEmpty, kbest_id = kEmpty;
+    T best = (T)-INFINITY, kbest = (T)-INFINITY;
     bool ovf = false;
     for (int guard = 0; guard < 7 * KM; ++guard) {
         int c = head[0];
@@ -115,40 +116,46 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
         const T en = e0 - Ldt * (df0 - kap * lap + ddef);
         if (en > best) { best = en; best_id = c; }
         if (en >= drop) {
-            // insert at the spare slot KM and bubble up (sorted by eta desc, id asc)
-            kid[KM] = c;
-            ke[KM] = en;
-#pragma unroll
-            for (int j = KM - 1; j >= 0; --j) {
-                if (better(ke[j + 1], kid[j + 1], ke[j], kid[j])) {
-                    const int ti = kid[j]; kid[j] = kid[j + 1]; kid[j + 1] = ti;
-                    const T te = ke[j]; ke[j] = ke[j + 1]; ke[j + 1] = te;
-                }
-            }
-            // anything beyond the runtime capacity K is dropped
+            if (en > kbest) { kbest = en; kbest_id = c; }   // ascending ids: a tie keeps the smaller id
 #pragma unroll
             for (int j = 0; j <= KM; ++j)
-                if (j >= K && kid[j] != kEmpty) { ovf = true; kid[j] = kEmpty; ke[j] = (T)-INFINITY; }
+                if (j == cnt) { kid[j] = c; ke[j] = en; }
+            ++cnt;
+            if (cnt > K) {   // over capacity: remove the worst entry
+                ovf = true;
+                int wj = 0, wid = kid[0];
+                T wv = ke[0];
+#pragma unroll
+                for (int j = 1; j <= KM; ++j)
+                    if (j < cnt && (ke[j] < wv || (ke[j] == wv && kid[j] > wid))) { wj = j; wv = ke[j]; wid = kid[j]; }
+#pragma unroll
+                for (int j = 0; j < KM; ++j)
+                    if (j >= wj) { kid[j] = kid[j + 1]; ke[j] = ke[j + 1]; }
+                kid[KM] = kEmpty;
+                ke[KM] = (T)0;
+                cnt = K;
+            }
         }
     }
-    if (kid[0] == kEmpty && best_id != kEmpty) { kid[0] = best_id; ke[0] = best; }
-    gout[v] = kid[0];
-    // sort the kept entries by id (empties last)
+    if (cnt == 0 && best_id != kEmpty) {   // nothing above the drop threshold: keep the largest
+        kid[0] = best_id;
+        ke[0] = best;
+        cnt = 1;
+        kbest_id = best_id;
+    }
+    gout[v] = kbest_id;
+    // Write the kept entries; then clear the slots the destination still holds from its previous use
+    // (every buffer keeps -1 / 0 beyond its entries, so those are the only stale ones).
 #pragma unroll
-    for (int a = 0; a < KM; ++a)
-#pragma unroll
-        for (int j = 0; j < KM - 1 - a; ++j)
-            if (kid[j] > kid[j + 1]) {
-                const int ti = kid[j]; kid[j] = kid[j + 1]; kid[j + 1] = ti;
-                const T te = ke[j]; ke[j] = ke[j + 1]; ke[j + 1] = te;
-            }
-#pragma unroll
-    for (int j = 0; j < KM; ++j) {
-        if (j < K) {
-            const bool has = kid[j] != kEmpty;
-            ids2[j * N3 + v] = has ? kid[j] : -1;
-            eta2[j * N3 + v] = has ? ke[j] : (T)0;
+    for (int j = 0; j < KM; ++j)
+        if (j < cnt) {
+            ids2[j * N3 + v] = kid[j];
+            eta2[j * N3 + v] = ke[j];
         }
+    for (int j = cnt; j < K; ++j) {
+        if (ids2[j * N3 + v] < 0) break;
+        ids2[j * N3 + v] = -1;
+        eta2[j * N3 + v] = (T)0;
     }
     if (ovf) atomicAdd(overflow, 1);
 }
@@ -334,7 +341,8 @@ __global__ void k_restrict(int n, int K, const int32_t *__restrict__ ids, const 
 
 // initial active sets on the PF grid: one order parameter 1 of the parent voxel's grain
 __global__ void k_pf_init(int n, int r, int K, const int32_t *__restrict__ g0, int32_t *__restrict__ ids,
-                          void *__restrict__ eta, int eta_double, int32_t *__restrict__ gpf) {
+                          void *__restrict__ eta, int32_t *__restrict__ ids2, void *__restrict__ eta2, int eta_double,
+                          int32_t *__restrict__ gpf) {
     const int m = r * n;
     const long M3 = (long)m * m * m;
     const long w = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -343,8 +351,14 @@ __global__ void k_pf_init(int n, int r, int K, const int32_t *__restrict__ g0, i
     const int gi = g0[X / r + (long)n * (Y / r + (long)n * (Z / r))];
     for (int j = 0; j < K; ++j) {
         ids[j * M3 + w] = j == 0 ? gi : -1;
-        if (eta_double) static_cast<double *>(eta)[j * M3 + w] = j == 0 ? 1.0 : 0.0;
-        else static_cast<float *>(eta)[j * M3 + w] = j == 0 ? 1.f : 0.f;
+        ids2[j * M3 + w] = -1;   // the step's destination: empty (it only rewrites slots in use)
+        if (eta_double) {
+            static_cast<double *>(eta)[j * M3 + w] = j == 0 ? 1.0 : 0.0;
+            static_cast<double *>(eta2)[j * M3 + w] = 0.0;
+        } else {
+            static_cast<float *>(eta)[j * M3 + w] = j == 0 ? 1.f : 0.f;
+            static_cast<float *>(eta2)[j * M3 + w] = 0.f;
+        }
     }
     gpf[w] = gi;
 }
@@ -402,10 +416,10 @@ cudaError_t pf_restrict(int n, int K, const int32_t *ids, const T *eta, int32_t 
     return cudaGetLastError();
 }
 
-cudaError_t pf_init(int n, int r, int K, const int32_t *g0, int32_t *ids, void *eta, int eta_double, int32_t *gpf,
-                    cudaStream_t s) {
+cudaError_t pf_init(int n, int r, int K, const int32_t *g0, int32_t *ids, void *eta, int32_t *ids2, void *eta2,
+                    int eta_double, int32_t *gpf, cudaStream_t s) {
     const long M3 = (long)r * n * r * n * r * n;
-    k_pf_init<<<(int)((M3 + 255) / 256), 256, 0, s>>>(n, r, K, g0, ids, eta, eta_double, gpf);
+    k_pf_init<<<(int)((M3 + 255) / 256), 256, 0, s>>>(n, r, K, g0, ids, eta, ids2, eta2, eta_double, gpf);
     return cudaGetLastError();
 }
 
