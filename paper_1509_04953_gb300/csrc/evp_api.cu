@@ -606,6 +606,7 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     h->pc.drop = p->eta_drop;
     h->pc.G = h->G;
     h->pc.K = h->K;
+    h->pc.set_fp32();
     // tables
     {
         const size_t G = (size_t)h->G;

@@ -99,6 +99,8 @@ cudaError_t nucleate(int n, int r, int K, int32_t *g, double *k, double *kappa, 
 struct PFConst {
     double m, kappa, gam, L_dt, Escale, drop;
     int G, K;
+    float m_f, kappa_f, gam_f, L_dt_f, drop_f;   // FP32 copies for the FP32 path
+    void set_fp32() { m_f = (float)m; kappa_f = (float)kappa; gam_f = (float)gam; L_dt_f = (float)L_dt; drop_f = (float)drop; }
 };
 template <typename T>
 cudaError_t pf_one_step(int n, const int32_t *ids, const T *eta, int32_t *ids2, T *eta2, int32_t *g,

@@ -27,17 +27,20 @@ struct Nbr {
     long q[7];   // self, x-, x+, y-, y+, z-, z+
 };
 
+// n is a power of two (checked at init): coordinates and periodic wraps by masks and shifts
 __device__ __forceinline__ Nbr neighbours(int n, long v) {
-    const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
+    const int lg = __ffs(n) - 1;
+    const long msk = n - 1;
+    const int x = (int)(v & msk), y = (int)((v >> lg) & msk), z = (int)(v >> (2 * lg));
     const long nn = (long)n * n;
     Nbr b;
     b.q[0] = v;
-    b.q[1] = v - x + (x + n - 1) % n;
-    b.q[2] = v - x + (x + 1) % n;
-    b.q[3] = v + (long)(((y + n - 1) % n) - y) * n;
-    b.q[4] = v + (long)(((y + 1) % n) - y) * n;
-    b.q[5] = v + (long)(((z + n - 1) % n) - z) * nn;
-    b.q[6] = v + (long)(((z + 1) % n) - z) * nn;
+    b.q[1] = v - x + ((x - 1) & msk);
+    b.q[2] = v - x + ((x + 1) & msk);
+    b.q[3] = v + (long)(((y - 1) & msk) - y) * n;
+    b.q[4] = v + (long)(((y + 1) & msk) - y) * n;
+    b.q[5] = v + (long)(((z - 1) & msk) - z) * nn;
+    b.q[6] = v + (long)(((z + 1) & msk) - z) * nn;
     return b;
 }
 
@@ -53,7 +56,9 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
     if (v >= N3) return;
     const int K = pc.K, G = pc.G;
     const Nbr nb = neighbours(n, v);
-    const T m = (T)pc.m, kap = (T)pc.kappa, gam = (T)pc.gam, Ldt = (T)pc.L_dt, drop = (T)pc.drop;
+    T m, kap, gam, Ldt, drop;   // in the field precision (no FP64 conversions on the FP32 path)
+    if constexpr (sizeof(T) == 4) { m = pc.m_f; kap = pc.kappa_f; gam = pc.gam_f; Ldt = pc.L_dt_f; drop = pc.drop_f; }
+    else { m = pc.m; kap = pc.kappa; gam = pc.gam; Ldt = pc.L_dt; drop = pc.drop; }
     // local sums over the voxel's own list, ascending id
     T S2 = (T)0, D = (T)0, R = (T)0;
     for (int j = 0; j < K; ++j) {
