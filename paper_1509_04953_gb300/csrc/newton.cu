@@ -460,6 +460,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_res
 // init = 1 is the start of an increment: sigma from the plain implicit update at eps_tr (S instead of
 // Sal, no lam term), then lam = sigma and e_tr = eps_tr. Partial sums per block: |eps_tr - e_tr|^2,
 // |C0 (eps_tr - e_tr)|^2, the six components of lam and the six of sigma.
+// Error-free transformations on FP32 (Knuth's two-sum; the rounding error of a product by fma): an
+// FP32 result plus the float that it rounded away, exactly.
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod_f(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+
 // C0 x for the isotropic reference stiffness (Lame constants l0, m0), component i of Mandel x.
 template <typename T> __device__ __forceinline__ T iso_apply_c0(T l0, T m0, const T x[6], int i) {
     const T tr = x[0] + x[1] + x[2];
@@ -495,8 +507,8 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
                                                       TA *__restrict__ sig, TA *__restrict__ lam, TA *__restrict__ pout,
                                                       const TA *__restrict__ Stab, const TA *__restrict__ Sal,
                                                       const TA *__restrict__ Mtab, MatConst mc, TA l0, TA m0, TA sa,
-                                                      TA sb, double sad, double sbd, TA tol, int maxit, TA ls_free,
-                                                      int init,
+                                                      TA sb, TA sa_lo, TA sb_lo, double sad, double sbd, TA tol,
+                                                      int maxit, TA ls_free, int init,
                                                       int *__restrict__ flags, double *__restrict__ part,
                                                       TS *__restrict__ fac, int refresh) {
     constexpr int NV = 14;
@@ -537,21 +549,57 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
         } else {
             r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
         }
-        // local strain e_tr = eps_tr' - S0 sigma and the gap d = eps_tr - e_tr in FP64: near convergence
-        // eps_tr and e_tr agree to many digits, and forming them in FP32 leaves rounding noise in d
-        // (hence in the multiplier update) that keeps the iteration from settling
+        // local strain e_tr = eps_tr' - S0 sigma and the gap d = eps_tr - e_tr to about twice the field
+        // precision: near convergence eps_tr and e_tr agree to many digits, and forming them in plain FP32
+        // leaves rounding noise in d (hence in the multiplier update) that keeps the iteration from
+        // settling. FP64 does it on the FP64 path; the FP32 path uses error-free transformations on the
+        // FP32 pipe (the FP64 pipe issues 1/64 as fast).
         TA el[6], d[6], de[6];
-        double s6[6];
+        if constexpr (sizeof(TA) == 4) {
+            float t1, e1, th, e2;
+            two_sum_f(sg[0], sg[1], t1, e1);
+            two_sum_f(t1, sg[2], th, e2);
+            const float tl = __fadd_rn(e1, e2);   // tr(sigma) = th + tl
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s6[c] = (double)sg[c];
-        const double str = s6[0] + s6[1] + s6[2];
+            for (int c = 0; c < 6; ++c) {
+                sig[c * N3 + v] = sg[c];
+                if (init) {
+                    el[c] = et[c];
+                    d[c] = 0.f;
+                } else {
+                    float p, pe;
+                    two_prod_f(sa, sg[c], p, pe);
+                    pe = fmaf(sa_lo, sg[c], pe);   // S0 sigma (shear part) = p + pe
+                    float sh = p, sl = pe;
+                    if (c < 3) {
+                        float q, qe, se;
+                        two_prod_f(sb, th, q, qe);
+                        qe = fmaf(sb, tl, fmaf(sb_lo, th, qe));   // sb tr = q + qe
+                        two_sum_f(p, -q, sh, se);
+                        sl = __fadd_rn(se, __fsub_rn(pe, qe));
+                    }
+                    float u, ue, w, we;
+                    two_sum_f(etr[c], -sh, u, ue);            // e_tr = u + ul
+                    const float ul = __fsub_rn(ue, sl);
+                    two_sum_f(et[c], -u, w, we);              // d = eps_tr - e_tr
+                    d[c] = __fadd_rn(w, __fsub_rn(we, ul));
+                    el[c] = __fadd_rn(u, ul);
+                }
+                de[c] = el[c] - ee[c];
+            }
+        } else {
+            double s6[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            sig[c * N3 + v] = sg[c];
-            const double eld = init ? (double)et[c] : (double)etr[c] - (sad * s6[c] - (c < 3 ? sbd * str : 0.0));
-            d[c] = (TA)((double)et[c] - eld);
-            el[c] = (TA)eld;
-            de[c] = el[c] - ee[c];
+            for (int c = 0; c < 6; ++c) s6[c] = (double)sg[c];
+            const double str = s6[0] + s6[1] + s6[2];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                sig[c * N3 + v] = sg[c];
+                const double eld = init ? (double)et[c] : (double)etr[c] - (sad * s6[c] - (c < 3 ? sbd * str : 0.0));
+                d[c] = (TA)((double)et[c] - eld);
+                el[c] = (TA)eld;
+                de[c] = el[c] - ee[c];
+            }
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -731,13 +779,16 @@ cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, co
     const int blocks = al_blocks(N3);
     const double sad = 1.0 / (2.0 * mu0), sbd = lam0 / (2.0 * mu0 * (3.0 * lam0 + 2.0 * mu0));
     const TA sa = (TA)sad, sb = (TA)sbd;
+    const TA sa_lo = (TA)(sad - (double)sa), sb_lo = (TA)(sbd - (double)sb);   // S0 = (sa + sa_lo) I - (sb + sb_lo) J
     if (solve_fp64)
         k_al_local<TA, TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab,
-                                                               mc, (TA)lam0, (TA)mu0, sa, sb, sad, sbd, (TA)tol, maxit,
+                                                               mc, (TA)lam0, (TA)mu0, sa, sb, sa_lo, sb_lo, sad, sbd,
+                                                               (TA)tol, maxit,
                                                                ls_free_of<TA>(), init, flags, part, (TA *)fac, refresh);
     else
         k_al_local<TA, TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc,
-                                                           (TA)lam0, (TA)mu0, sa, sb, sad, sbd, (TA)tol, maxit,
+                                                           (TA)lam0, (TA)mu0, sa, sb, sa_lo, sb_lo, sad, sbd, (TA)tol,
+                                                           maxit,
                                                            ls_free_of<TA>(),
                                                            init, flags, part, (TA *)fac, refresh);
     return cudaGetLastError();
