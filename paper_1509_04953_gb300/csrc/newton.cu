@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
 // full chord iteration on the listed voxels only, from their unchanged state, so every result is
 // bitwise the one the single-kernel iteration gives.
 template <typename TA, typename TS>
-__global__ void __launch_bounds__(kThreads) k_chord_first(long N3, const TA *__restrict__ epst,
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_first(long N3, const TA *__restrict__ epst,
                                                          const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
                                                          TA *__restrict__ sig, const TA *__restrict__ Stab,
                                                          const TA *__restrict__ Mtab, const TS *__restrict__ fac,
