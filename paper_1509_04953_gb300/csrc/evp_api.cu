@@ -10,6 +10,7 @@
 
 #include "../../include/evp.h"
 #include "common.cuh"
+#include "fpctl.cuh"
 #include "kernels.h"
 
 using namespace evp;
@@ -358,103 +359,9 @@ void *field_ptr(evp_handle *h, uint32_t bit) {
 
 // Augmented-Lagrangian iterations of one increment (after the predictor): see k_al_local.
 // Returns a status; fills the iteration count, residuals, mean stress and the macro strain increment.
-// Fixed-point control of the basic scheme, on the device. One block sums the z-pass partials of
-// |xi.sigma_hat|^2 (in the fixed order of reduce_partials); its first thread turns them and the mean stress
-// into err_eq and err_bc, decides convergence and computes the correction dE_k of the macroscopic strain on
-// the stress-controlled components. The correction goes into the zero-frequency term of the
-// Green-operator output, which the z pass leaves at zero; after the z pass's own inverse transform that
-// term is the (ky, kx) = (0, 0) entry of every z plane. The inverse y and x transforms then add it to every
-// voxel's strain. The host queues iterations in batches and reads this block once per batch; once `done`
-// is set, the kernels of the iterations still queued return at once.
-struct FpCtl {
-    int done, it, conv, status, nmax, nfail, pad0, pad1;
-    double err_eq, err_bc;
-    double dE[6];
-    double tol_loc;     // local-solve tolerance of the next iteration (see evp_config.newton_adapt)
-    float tol_loc_f;
-};
 static_assert(sizeof(FpCtl) <= 256, "FpCtl must fit its workspace slot");
 constexpr int kFpBatch = 16;   // iterations queued between host reads of the control block
 const double kZero6[6] = {0, 0, 0, 0, 0, 0};
-
-template <typename T>
-__global__ void __launch_bounds__(1024) k_fp_control(FpCtl *__restrict__ c, const double *__restrict__ part, int nparts,
-                                                     double *__restrict__ scal, const int32_t *__restrict__ flags,
-                                                     typename CT<T>::type *__restrict__ spec, long fstride, int n,
-                                                     double N3, double tau0, double tol, int max_iter, double a,
-                                                     double b, double det, double mu0, double ntol, double eta) {
-    __shared__ double red[32];
-    __shared__ double corr[6];
-    __shared__ double meanv[6];
-    __shared__ int iv[4];
-    __shared__ int go;
-    if (c->done) return;   // uniform over the block
-    // operands of the decision fetched by separate threads, alongside the reduction (one thread
-    // fetching them one after another would wait out each load's latency in turn)
-    if (threadIdx.x < 6) meanv[threadIdx.x] = scal[threadIdx.x];
-    else if (threadIdx.x == 32) iv[0] = c->it;
-    else if (threadIdx.x == 33) iv[1] = c->nmax;
-    else if (threadIdx.x == 34) iv[2] = flags[0];
-    else if (threadIdx.x == 35) iv[3] = flags[1];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
-    s = block_sum(s, red);   // its barriers also publish meanv and iv
-    if (threadIdx.x == 0) {
-        go = 0;
-        scal[6] = s;
-        const int it = iv[0] + 1;
-        c->it = it;
-        c->nmax = max(iv[1], iv[3]);
-        double mean[6], mn = 0.0, mu_n = 0.0;
-        for (int i = 0; i < 6; ++i) {
-            mean[i] = meanv[i];
-            mn += mean[i] * mean[i];
-            if (i != 2) mu_n += mean[i] * mean[i];
-        }
-        const double den = fmax(sqrt(mn), tau0);
-        const double err_eq = sqrt(s) / (N3 * den);
-        const double err_bc = sqrt(fmax(mu_n, 0.0)) / den;
-        c->err_eq = err_eq;
-        c->err_bc = err_bc;
-        if (iv[2] != 0) {
-            c->nfail = iv[2];
-            c->status = EVP_ERR_NEWTON;
-            c->done = 1;
-        } else if (!isfinite(err_eq) || !isfinite(err_bc)) {
-            c->status = EVP_ERR_NONFINITE;
-            c->done = 1;
-        } else if (err_eq <= tol && err_bc <= tol) {
-            c->conv = 1;
-            c->done = 1;
-        } else if (it >= max_iter) {
-            c->done = 1;
-        } else {
-            double dEk[6] = {0, 0, 0, 0, 0, 0};
-            dEk[0] = (a * (-mean[0]) - b * (-mean[1])) / det;
-            dEk[1] = (-b * (-mean[0]) + a * (-mean[1])) / det;
-            for (int i = 3; i < 6; ++i) dEk[i] = -mean[i] / (2.0 * mu0);
-            for (int i = 0; i < 6; ++i) {
-                c->dE[i] += dEk[i];
-                corr[i] = dEk[i] * N3;   // the inverse transforms are unnormalised; x_c2r scales by 1/N^3
-            }
-            if (eta > 0.0) {
-                const double tl = fmax(ntol, eta * fmax(err_eq, err_bc));
-                c->tol_loc = tl;
-                c->tol_loc_f = (float)tl;
-            }
-            go = 1;
-        }
-    }
-    __syncthreads();
-    if (!go) return;
-    // after the z pass the spectrum is [field][z][ky][kx]: the (ky, kx) = (0, 0) entry of every z plane
-    const long zstride = fstride / n;
-    for (int t = threadIdx.x; t < 6 * n; t += blockDim.x) {
-        const int f = t / n, z = t - f * n;
-        auto &e = spec[f * fstride + z * zstride];
-        e.x += (T)corr[f];
-    }
-}
 
 template <typename TA>
 int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, int *nmax_out, double *err_eq,
@@ -784,6 +691,12 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         const float *tl32 = adapt ? &dc->tol_loc_f : nullptr;
         CK(cudaMemcpyAsync(dc, &hc, sizeof hc, cudaMemcpyHostToDevice, h->st));
         const double inv = 1.0 / (double)N3;
+        ZCtl zc;   // the z pass's last block runs the control (see fpctl.cuh)
+        zc.ctl = dc;
+        zc.flags = h->flags;
+        zc.scal = h->scal;
+        zc.p.N3 = (double)N3; zc.p.tau0 = h->p.tau0; zc.p.tol = h->cfg.tol; zc.p.a = a; zc.p.b = b; zc.p.det = det;
+        zc.p.mu0 = mu0; zc.p.ntol = ntol; zc.p.eta = h->cfg.newton_adapt; zc.p.max_iter = h->cfg.max_iter;
         int queued = 0;
         while (true) {
             const int nb = std::min(kFpBatch, h->cfg.max_iter - queued);
@@ -807,7 +720,8 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                   { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
-                    CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip)); }
+                    CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip,
+                                     &zc)); }
                 } else {
                   { PROF(0, 1);
                     if (reuse)
@@ -822,20 +736,9 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                   { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
-                    CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip)); }
+                    CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip,
+                                    &zc)); }
                 }
-                { PROF(6, 1);
-                  if (h->dbl)
-                      k_fp_control<double><<<1, 1024, 0, h->st>>>(dc, h->partials, zb, h->scal, h->flags,
-                                                                  (double2 *)h->spec, h->H, n, (double)N3, h->p.tau0,
-                                                                  h->cfg.tol, h->cfg.max_iter, a, b, det, mu0, ntol,
-                                                                  h->cfg.newton_adapt);
-                  else
-                      k_fp_control<float><<<1, 1024, 0, h->st>>>(dc, h->partials, zb, h->scal, h->flags,
-                                                                 (float2 *)h->spec, h->H, n, (double)N3, h->p.tau0,
-                                                                 h->cfg.tol, h->cfg.max_iter, a, b, det, mu0, ntol,
-                                                                 h->cfg.newton_adapt);
-                  CK(cudaGetLastError()); }
                 // the strain correction arrives through the zero-frequency term: no offsets here
                 if (h->dbl) {
                     { PROF(4, 1); CK(fft_y<double>(h->spec, n, 6, 1, h->st, skip)); }

@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "fpctl.cuh"
 #include "kernels.h"
 
 namespace evp {
@@ -411,7 +412,8 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N>
 __global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
-                                                   T mu0, double *__restrict__ partials, double *__restrict__ mean6, const int *__restrict__ skip) {
+                                                   T mu0, double *__restrict__ partials, double *__restrict__ mean6, const int *__restrict__ skip,
+                                                   ZCtl zc) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int TX = tx_z<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1, MI = maxit<N>(6 * (TX + 1), z_threads<N, T>());
@@ -478,6 +480,17 @@ __global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::typ
             const int f = t / N, z = t % N;
             spec[f * fstride + z * plane + (long)ky * Hx + N / 2] = buf[(nf * TX + f) * LS + pad16(z)];
         }
+    if (zc.ctl != nullptr) {   // the last block to finish runs the fixed-point control (fpctl.cuh)
+        __shared__ int last;
+        __threadfence();       // this block's partial sum and spectrum are visible to the others
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&zc.ctl->ticket, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        fp_control_block<T>(zc, partials, gridDim.x, spec, fstride, N);
+        if (threadIdx.x == 0) zc.ctl->ticket = 0u;
+    }
 }
 
 template <typename T, int N> size_t smem_x() { return sizeof(typename CT<T>::type) * (N + (size_t)rowpairs<N>() * Shape<N>::LS); }
@@ -536,15 +549,17 @@ template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int invers
 
 template <typename T, int N>
 cudaError_t z_n(void *spec, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
-                cudaStream_t s, const int *skip) {
+                cudaStream_t s, const int *skip, const ZCtl *zcp) {
     using C = typename CT<T>::type;
     constexpr int TX = tx_z<N, T>();
     const int blocks = N * ((N / 2) / TX);
     const size_t sm = smem_z<T, N>(nfields);
     cudaError_t e = allow_smem(k_fft_z<T, N>, smem_z<T, N>(6));
     if (e != cudaSuccess) return e;
+    ZCtl zc{};
+    if (zcp != nullptr) zc = *zcp;
     k_fft_z<T, N><<<blocks, z_threads<N, T>(), sm, s>>>((C *)spec, nfields, mode, (T)lam0, (T)mu0, partials, mean6,
-                                                       skip);
+                                                       skip, zc);
     return cudaGetLastError();
 }
 
@@ -587,9 +602,10 @@ template <typename T> cudaError_t fft_y(void *spec, int n, int nfields, int inve
 
 template <typename T>
 cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
-                  cudaStream_t s, const int *skip) {
+                  cudaStream_t s, const int *skip, const ZCtl *zc) {
     if ((mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) && nfields != 6) return cudaErrorInvalidValue;
-    EVP_DISPATCH(n, (z_n<T, NN>(spec, nfields, mode, lam0, mu0, partials, mean6, s, skip)))
+    if (zc != nullptr && (mode != Z_FWD_GAMMA_INV || partials == nullptr)) return cudaErrorInvalidValue;
+    EVP_DISPATCH(n, (z_n<T, NN>(spec, nfields, mode, lam0, mu0, partials, mean6, s, skip, zc)))
 }
 
 #define EVP_FFT_INST(T)                                                                                            \
@@ -598,7 +614,7 @@ cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double 
                                       const int *);                                                                \
     template cudaError_t fft_y<T>(void *, int, int, int, cudaStream_t, const int *);                               \
     template cudaError_t fft_z<T>(void *, int, int, int, double, double, double *, double *, cudaStream_t,         \
-                                  const int *);
+                                  const int *, const ZCtl *);
 EVP_FFT_INST(float)
 EVP_FFT_INST(double)
 #undef EVP_FFT_INST

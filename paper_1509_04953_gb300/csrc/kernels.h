@@ -15,6 +15,7 @@ struct MatConst {
 };
 
 // ---- fft.cu ----
+struct ZCtl;   // fpctl.cuh: the fixed-point control that the z pass's last block runs
 enum ZMode { Z_FWD = 0, Z_INV = 1, Z_FWD_GAMMA_INV = 2, Z_FWD_RESID = 3 };
 // skip (optional, device): when *skip != 0 the launched kernel returns at once (a converged fixed point
 // whose remaining queued iterations are discarded). tol_dev (optional, device): the local-solve
@@ -25,7 +26,7 @@ template <typename T>
 cudaError_t fft_y(void *spec, int n, int nfields, int inverse, cudaStream_t s, const int *skip = nullptr);
 template <typename T>
 cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double mu0, double *partials,
-                  double *mean6, cudaStream_t s, const int *skip = nullptr);
+                  double *mean6, cudaStream_t s, const int *skip = nullptr, const ZCtl *zc = nullptr);
 // x-pass complex-to-real. If add6 != nullptr: out[c] = (base ? base[c] : out[c]) + scale * field + add6[c];
 // else out = field.
 template <typename T>
