@@ -29,14 +29,15 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [(k, C.c_double) for k in (
         "C11", "C12", "C44", "gdot0", "n", "tau0", "alpha", "b", "k1", "k2", "rho0", "zeta",
-        "kc", "q", "s_nucl", "s_soften", "omega_gb", "dx", "l_gb", "L_dt", "eta_drop")]
+        "kc", "q", "s_nucl", "s_soften", "omega_gb", "dx", "l_gb", "L_dt", "eta_drop",
+        "T", "Q_slip", "Q_bulk", "nu_D", "poisson", "c1", "c2", "c3", "c4", "c5", "c6", "c7", "c8", "xi")]
 
 
 class Config(C.Structure):
     _fields_ = [("n", C.c_int), ("grains", C.c_int), ("kmax", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("allow_unconverged", C.c_int), ("newton_tol", C.c_double),
                 ("newton_max", C.c_int), ("predictor", C.c_int), ("nthreads", C.c_int), ("scheme", C.c_int),
-                ("al_scale", C.c_double), ("pf_refine", C.c_int)]
+                ("al_scale", C.c_double), ("pf_refine", C.c_int), ("law", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -109,6 +110,32 @@ def lib():
         L.orc_next_id.argtypes = [C.c_void_p]
         L.orc_set_next_id.argtypes = [C.c_void_p, C.c_int]
         L.orc_refresh_derived.argtypes = [C.c_void_p]
+        L.orc_mr_tables.argtypes = [_dp]
+        L.orc_mr_project.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_mr_frozen.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp]
+        L.orc_mr_rho_m.restype = C.c_double
+        L.orc_mr_rho_m.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
+        L.orc_mr_gdot.restype = C.c_double
+        L.orc_mr_gdot.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]
+        L.orc_mr_ssd_rate.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
+        L.orc_vm_stress.restype = C.c_double
+        L.orc_vm_stress.argtypes = [_dp]
+        L.orc_vm_strain.restype = C.c_double
+        L.orc_vm_strain.argtypes = [_dp]
+        L.orc_mr_grain_vectors.argtypes = [C.c_int, _dp, _dp, _dp]
+        L.orc_mr_gnd_rates.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
+        L.orc_mr_leff_next.restype = C.c_double
+        L.orc_mr_leff_next.argtypes = [C.c_double, _dp, C.c_double]
+        L.orc_newton_mr.restype = C.c_int
+        L.orc_newton_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                    C.c_double, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
+        L.orc_residual_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp]
+        L.orc_point_model_mr.restype = C.c_int
+        L.orc_point_model_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                         C.c_int, _dp]
+        L.orc_leff.restype = C.c_double
+        L.orc_leff.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -242,7 +269,7 @@ def loss_grad(n, grains, g0, quat, mat, seed, T, dE33, dt, target=None, want_gra
               max_iter=20000, adj_tol=1e-12, nthreads=0):
     """FP64 loss L = sum_t (<sigma33>_t - target_t)^2 over T increments, its adjoint gradient with
     respect to (k1, k2, tau0, n) and the stress-strain curve."""
-    cfg = Config(n, grains, 8, tol, max_iter, 0, 1e-13, 60, 1, nthreads, 0, 4.0)
+    cfg = Config(n, grains, 8, tol, max_iter, 0, 1e-13, 60, 1, nthreads, 0, 4.0, 1, 0)
     p = make_params(mat)
     g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)
     q = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1)
@@ -261,7 +288,7 @@ class State:
 
     def __init__(self, n, grains, g0, quat, mat, seed, kmax=8, tol=1e-10, max_iter=1000,
                  allow_unconverged=0, newton_tol=1e-12, newton_max=50, predictor=1, nthreads=0, scheme=0,
-                 al_scale=4.0, pf_refine=1):
+                 al_scale=4.0, pf_refine=1, law=0):
         self.n, self.G, self.K = n, grains, kmax
         self.N3 = n ** 3
         self.r = 2 if pf_refine == 2 else 1
@@ -269,7 +296,8 @@ class State:
         self.N3pf = self.npf ** 3
         self.mat = mat
         self._cfg = Config(n, grains, kmax, tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                           predictor, nthreads, scheme, al_scale, self.r)
+                           predictor, nthreads, scheme, al_scale, self.r, law)
+        self.law = law
         self._p = make_params(mat)
         self._g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)
         self._q = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1)
@@ -286,7 +314,8 @@ class State:
         except Exception:
             pass
 
-    _SIZES = {"eps": 6, "epsp": 6, "sig": 6, "deps_prev": 6, "rho": 12, "k": 1, "kappa": 1}
+    _SIZES = {"eps": 6, "epsp": 6, "sig": 6, "deps_prev": 6, "rho": 12, "k": 1, "kappa": 1, "gnds": 12,
+              "gndet": 12, "gnd": 12}
 
     def field(self, name):
         """A view (not a copy) of a double field, shaped (components, N^3)."""
@@ -343,3 +372,115 @@ class State:
 
     def refresh_derived(self):
         lib().orc_refresh_derived(self.h)
+
+    @property
+    def leff(self):
+        """Effective GND length l_eff of the Ma-Roters law (Eq. L0evolution), m."""
+        return lib().orc_leff(self.h)
+
+
+# ---------------------------------------------------------------------------------------------
+# Ma-Roters dislocation law (Sec. 2.2)
+# ---------------------------------------------------------------------------------------------
+def _a(x, n=None):
+    a = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+    if n is not None:
+        assert a.size == n
+    return a
+
+
+def mr_tables():
+    """(|cos(n,t)|, |cos(n,d)|, |sin(n,t)|, |sin(n,d)|), each 12 x 12 [alpha, beta]."""
+    t = np.zeros(576)
+    lib().orc_mr_tables(t)
+    return t.reshape(4, 12, 12)
+
+
+def mr_project(ssd, gs=None, ge=None):
+    z = np.zeros(12)
+    rF, rP = np.zeros(12), np.zeros(12)
+    lib().orc_mr_project(mr_tables().reshape(-1), _a(ssd, 12), _a(z if gs is None else gs, 12),
+                         _a(z if ge is None else ge, 12), rF, rP)
+    return rF, rP
+
+
+def mr_frozen(mat, rF, rP):
+    p = make_params(mat)
+    tp, tcut, A = np.zeros(12), np.zeros(12), np.zeros(12)
+    lib().orc_mr_frozen(C.byref(p), _a(rF, 12), _a(rP, 12), tp, tcut, A)
+    return tp, tcut, A
+
+
+def mr_rho_m(mat, rF, rP):
+    return lib().orc_mr_rho_m(C.byref(make_params(mat)), float(rF), float(rP))
+
+
+def mr_gdot(tau, tp, tcut, A):
+    """(gdot, d gdot / d tau, potential) of one slip system."""
+    dg, psi = C.c_double(0.0), C.c_double(0.0)
+    g = lib().orc_mr_gdot(float(tau), float(tp), float(tcut), float(A), C.byref(dg), C.byref(psi))
+    return g, dg.value, psi.value
+
+
+def mr_ssd_rate(mat, ssd, rF, rP, tau, gd, svm, gvm):
+    out = np.zeros(12)
+    lib().orc_mr_ssd_rate(C.byref(make_params(mat)), _a(ssd, 12), _a(rF, 12), _a(rP, 12), _a(tau, 12),
+                          _a(gd, 12), float(svm), float(gvm), out)
+    return out
+
+
+def vm_stress(sig):
+    return lib().orc_vm_stress(_a(sig, 6))
+
+
+def vm_strain(e):
+    return lib().orc_vm_strain(_a(e, 6))
+
+
+def mr_grain_vectors(quat):
+    q = _a(quat)
+    G = q.size // 4
+    dv, tv = np.zeros(36 * G), np.zeros(36 * G)
+    lib().orc_mr_grain_vectors(G, q, dv, tv)
+    return dv.reshape(G, 12, 3), tv.reshape(G, 12, 3)
+
+
+def mr_gnd_rates(n, g, g0, gd, quat, leff, b):
+    """(rho_dot_GNDs, rho_dot_GNDet), each 12 x N^3, of a shear-rate field gd (12 x N^3)."""
+    dv, tv = mr_grain_vectors(quat)
+    N3 = n ** 3
+    rs, re = np.zeros(12 * N3), np.zeros(12 * N3)
+    lib().orc_mr_gnd_rates(n, np.ascontiguousarray(g, dtype=np.int32).reshape(-1),
+                           np.ascontiguousarray(g0, dtype=np.int32).reshape(-1), _a(gd, 12 * N3),
+                           dv.reshape(-1), tv.reshape(-1), float(leff), float(b), rs, re)
+    return rs.reshape(12, N3), re.reshape(12, N3)
+
+
+def mr_leff_next(leff, E, xi):
+    return lib().orc_mr_leff_next(float(leff), _a(E, 6), float(xi))
+
+
+def newton_mr(mat, S, M, eps_tr, tp, tcut, A, tref, dt, sig0, tol=1e-12, maxit=50):
+    p = make_params(mat)
+    sig = _a(sig0, 6).copy()
+    gd = np.zeros(12)
+    its = C.c_int(0)
+    rc = lib().orc_newton_mr(C.byref(p), _a(S, 36), _a(M, 72), _a(eps_tr, 6), _a(tp, 12), _a(tcut, 12), _a(A, 12),
+                             float(tref), float(dt), tol, maxit, sig, gd, C.byref(its))
+    return rc, sig, gd, its.value
+
+
+def residual_mr(mat, S, M, eps_tr, tp, tcut, A, dt, sig):
+    r = np.zeros(6)
+    lib().orc_residual_mr(C.byref(make_params(mat)), _a(S, 36), _a(M, 72), _a(eps_tr, 6), _a(tp, 12),
+                          _a(tcut, 12), _a(A, 12), float(dt), _a(sig, 6), r)
+    return r
+
+
+def point_model_mr(mat, S, M, dE33, dt, nsteps, ssd0=None):
+    p = make_params(mat)
+    sig, epsp, E = np.zeros(6), np.zeros(6), np.zeros(6)
+    ssd = np.full(12, mat.rho0 if ssd0 is None else ssd0, dtype=np.float64)
+    hist = np.zeros(max(nsteps, 1))
+    rc = lib().orc_point_model_mr(C.byref(p), _a(S, 36), _a(M, 72), sig, epsp, ssd, E, dE33, dt, nsteps, hist)
+    return rc, hist[:nsteps], dict(sig=sig, epsp=epsp, ssd=ssd, E=E)

@@ -273,8 +273,18 @@ void orc_gamma0(const double xi[3], double lam0, double mu0, double Gm[36]) {
  * ---------------------------------------------------------------------------------------- */
 typedef struct { double r[6], K[36], phi, gdot[12]; } nt_eval;
 
+/* Flow-rule data of one voxel, frozen over an increment: the power law's tau_c, or the Ma-Roters
+ * passing stress tp, cutting stress tcut and prefactor A of every slip system (law = 1). tauc is
+ * also the stress added to |sigma| in the Newton stopping scale. */
+typedef struct {
+    int law;
+    double tauc;
+    const double *tp, *tcut, *A;
+} nt_flow;
+
 static void nt_evaluate(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
-                        double tauc, double dt, const double sig[6], nt_eval *e) {
+                        const nt_flow *f, double dt, const double sig[6], nt_eval *e) {
+    const double tauc = f->tauc;
     for (int I = 0; I < 6; ++I) {
         double acc = 0.0;
         for (int J = 0; J < 6; ++J) acc += S[6 * I + J] * sig[J];
@@ -291,17 +301,25 @@ static void nt_evaluate(const orc_params *p, const double *S, const double *M, c
         const double *m = M + 6 * a;
         double tau = 0.0;
         for (int I = 0; I < 6; ++I) tau += m[I] * sig[I];
-        double x = tau / tauc, ax = fabs(x);
-        double pw = ax > 0.0 ? pow(ax, p->n) : 0.0;
-        double gd = p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0);
-        if (ax == 0.0) gd = 0.0;
+        double gd, slope;
+        if (f->law == 1) {
+            double dg, psi;
+            gd = orc_mr_gdot(tau, f->tp[a], f->tcut[a], f->A[a], &dg, &psi);
+            slope = dt * dg;
+            phi += dt * psi;
+        } else {
+            double x = tau / tauc, ax = fabs(x);
+            double pw = ax > 0.0 ? pow(ax, p->n) : 0.0;
+            gd = p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0);
+            if (ax == 0.0) gd = 0.0;
+            slope = ax > 0.0 ? dt * p->n * p->gdot0 * (pw / ax) / tauc : 0.0;
+            phi += dt * p->gdot0 * tauc * pw * ax / (p->n + 1.0);
+        }
         e->gdot[a] = gd;
-        double slope = ax > 0.0 ? dt * p->n * p->gdot0 * (pw / ax) / tauc : 0.0;
         for (int I = 0; I < 6; ++I) {
             e->r[I] += dt * m[I] * gd;
             for (int J = 0; J < 6; ++J) e->K[6 * I + J] += slope * m[I] * m[J];
         }
-        phi += dt * p->gdot0 * tauc * pw * ax / (p->n + 1.0);
     }
     e->phi = phi;
 }
@@ -309,15 +327,19 @@ static void nt_evaluate(const orc_params *p, const double *S, const double *M, c
 void orc_residual(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
                   double tauc, double dt, const double sig[6], double r[6], double K[36]) {
     nt_eval e;
-    nt_evaluate(p, S, M, eps_tr, tauc, dt, sig, &e);
+    nt_flow f = {0, tauc, NULL, NULL, NULL};
+    nt_evaluate(p, S, M, eps_tr, &f, dt, sig, &e);
     memcpy(r, e.r, sizeof e.r);
     memcpy(K, e.K, sizeof e.K);
 }
 
-int orc_newton(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
-               double tauc, double dt, double tol, int maxit, double sig[6], double gdot[12], int *iters) {
+/* Damped Newton on r(sigma) = 0 with Armijo backtracking on the convex potential whose gradient
+ * is r; stops when the step is below tol (|sigma| + tau_c). */
+static int nt_newton(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+                     const nt_flow *f, double dt, double tol, int maxit, double sig[6], double gdot[12], int *iters) {
     nt_eval e, t;
-    nt_evaluate(p, S, M, eps_tr, tauc, dt, sig, &e);
+    const double tauc = f->tauc;
+    nt_evaluate(p, S, M, eps_tr, f, dt, sig, &e);
     for (int it = 1; it <= maxit; ++it) {
         double Ki[36], d[6];
         if (inv_gj(6, e.K, Ki) != 0) { *iters = it; return -1; }
@@ -333,7 +355,7 @@ int orc_newton(const orc_params *p, const double *S, const double *M, const doub
         int ok = 0;
         for (int h = 0; h < 60; ++h) {
             for (int I = 0; I < 6; ++I) trial[I] = sig[I] - s * d[I];
-            nt_evaluate(p, S, M, eps_tr, tauc, dt, trial, &t);
+            nt_evaluate(p, S, M, eps_tr, f, dt, trial, &t);
             if (t.phi <= e.phi - 1e-4 * s * rd || s * dn <= 1e-6 * scale) { ok = 1; break; }
             s *= 0.5;
         }
@@ -348,6 +370,12 @@ int orc_newton(const orc_params *p, const double *S, const double *M, const doub
     }
     *iters = maxit;
     return -1;
+}
+
+int orc_newton(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+               double tauc, double dt, double tol, int maxit, double sig[6], double gdot[12], int *iters) {
+    nt_flow f = {0, tauc, NULL, NULL, NULL};
+    return nt_newton(p, S, M, eps_tr, &f, dt, tol, maxit, sig, gdot, iters);
 }
 
 /* Kocks-Mecking update with explicit densities and the converged shear rates (reading of the
@@ -378,11 +406,12 @@ int orc_point_model(const orc_params *p, const double *S, const double *M, doubl
         double tauc = p->tau0 + p->alpha * mu_voigt(p) * p->b * sqrt(rf);
         double target = E[2] + dE33;
         nt_eval e;
+        nt_flow fl = {0, tauc, NULL, NULL, NULL};
         double zero6[6] = {0, 0, 0, 0, 0, 0};
 #define F33(s33, out)                                                                  \
     do {                                                                               \
         double sg[6] = {0, 0, (s33), 0, 0, 0};                                         \
-        nt_evaluate(p, S, M, zero6, tauc, dt, sg, &e);                                 \
+        nt_evaluate(p, S, M, zero6, &fl, dt, sg, &e);                                  \
         (out) = e.r[2] + epsp[2] - target;                                             \
     } while (0)
         double lo = -1.0, hi = 1.0, flo, fhi;
@@ -399,7 +428,7 @@ int orc_point_model(const orc_params *p, const double *S, const double *M, doubl
         }
         double s33 = 0.5 * (lo + hi);
         double sg[6] = {0, 0, s33, 0, 0, 0};
-        nt_evaluate(p, S, M, zero6, tauc, dt, sg, &e);
+        nt_evaluate(p, S, M, zero6, &fl, dt, sg, &e);
         /* e.r = S sigma + dt eps_p_dot; total strain E = that + eps_p^t */
         for (int I = 0; I < 6; ++I) E[I] = e.r[I] + epsp[I];
         E[2] = target;
@@ -412,6 +441,290 @@ int orc_point_model(const orc_params *p, const double *S, const double *M, doubl
         memcpy(sig, sg, sizeof sg);
         if (sig33_hist) sig33_hist[st] = s33;
 #undef F33
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Ma-Roters dislocation-density law (Sec. 2.2, Eqs. FlowRule, RhoForest, RhoParallel,
+ * SSDEvolution, GNDEvolution, L0evolution, TotDislocationDensity, UpdateGND; constants of
+ * Table 1). Stresses in MPa as everywhere in the oracle; the energies Q and k_B T are in J, so
+ * the shear modulus enters the dimensional groups in Pa (mu_Pa = 1e6 mu).
+ *
+ * Readings of what the paper leaves open (each is listed with the other readings of the build):
+ *  - R1 hardening frozen over an increment: rho_F, rho_P, and with them tau_pass, tau_cut and the
+ *    prefactor, come from the densities at the start of the increment (as tau_c for the power law);
+ *  - R2 the attempt frequency nu_D (order of the Debye frequency) and Poisson's ratio are
+ *    parameters; the paper prints neither;
+ *  - R3 t^a = n^a x d^a (unit line direction of the edge dislocation); |cos| and |sin| of the angle
+ *    between two unit vectors are |u.v| and sqrt(1 - (u.v)^2); these are frame-invariant, so one
+ *    12 x 12 table per pair type serves every grain. rho_GNDen stays 0 (zero rate, zero start), so
+ *    its terms vanish;
+ *  - R4 mobile density: the paper prints none; the closure of Ma and Roters (2004),
+ *    rho_M = 2 k_B T / (c1 c2 c3 mu b^3) sqrt(rho_P rho_F);
+ *  - R5 in the SSD law gdot stands for |gdot| (storage does not depend on the sign of slip),
+ *    d_dipole takes |tau|, sigma_vm is the von Mises stress sqrt(3/2 s:s) of the voxel, gdot_vm the
+ *    von Mises plastic strain rate sqrt(2/3 epsp_dot:epsp_dot); explicit Euler with the converged
+ *    rates, the result clipped at 0; c6 multiplies the dipole term and c7 the climb term, the
+ *    placement in the equation, whose units agree with Table 1's values (its labels are swapped);
+ *  - R6 the gradient of gdot^a is taken per axis on the grid with spacing l_eff: central where both
+ *    neighbours belong to the voxel's grain, one-sided where only one does, 0 where neither; "the
+ *    voxel's grain" = same current grain id and same orientation (initial grain);
+ *  - R7 rho_GND^a grows by dt |rho_dot_GND^a| with |rho_dot_GND|^2 = rho_dot_GNDs^2 + rho_dot_GNDet^2
+ *    (the conservation law on the rates); the signed components are integrated as they are;
+ *  - R8 eps_vm is the von Mises equivalent of the macroscopic strain E at the end of the increment,
+ *    and l_eff is updated after the increment's GND rates are taken (l_eff starts at l0 = dx);
+ *  - R9 softening on nucleation and on a PF sweep scales the GND densities (all three components)
+ *    by s_soften and keeps the SSD density (Eq. UpdateGND);
+ *  - R10 the Newton stopping scale adds tau_ref = min_a tau_pass^a to |sigma|.
+ * ---------------------------------------------------------------------------------------- */
+#define ORC_KB 1.380649e-23   /* Boltzmann constant, J/K (exact SI value) */
+
+/* |cos| and |sin| of the angles between slip-plane normals and the sense vectors t (tables 0 and
+ * 2) and the slip directions d (tables 1 and 3) of every pair of systems: tab[k*144 + 12 a + b]. */
+void orc_mr_tables(double tab[576]) {
+    double d[12][3], nr[12][3], t[12][3];
+    orc_slip_systems(d, nr);
+    for (int a = 0; a < 12; ++a) {
+        t[a][0] = nr[a][1] * d[a][2] - nr[a][2] * d[a][1];
+        t[a][1] = nr[a][2] * d[a][0] - nr[a][0] * d[a][2];
+        t[a][2] = nr[a][0] * d[a][1] - nr[a][1] * d[a][0];
+    }
+    for (int a = 0; a < 12; ++a)
+        for (int b = 0; b < 12; ++b) {
+            double ct = fabs(nr[a][0] * t[b][0] + nr[a][1] * t[b][1] + nr[a][2] * t[b][2]);
+            double cd = fabs(nr[a][0] * d[b][0] + nr[a][1] * d[b][1] + nr[a][2] * d[b][2]);
+            tab[0 * 144 + 12 * a + b] = ct;
+            tab[1 * 144 + 12 * a + b] = cd;
+            tab[2 * 144 + 12 * a + b] = sqrt(fmax(0.0, 1.0 - ct * ct));
+            tab[3 * 144 + 12 * a + b] = sqrt(fmax(0.0, 1.0 - cd * cd));
+        }
+}
+
+/* Eqs. RhoForest / RhoParallel with rho_GNDen = 0. */
+void orc_mr_project(const double tab[576], const double ssd[12], const double gs[12], const double ge[12],
+                    double rF[12], double rP[12]) {
+    for (int a = 0; a < 12; ++a) {
+        double f = 0.0, q = 0.0;
+        for (int b = 0; b < 12; ++b) {
+            f += ssd[b] * tab[12 * a + b] + fabs(gs[b] * tab[144 + 12 * a + b]) + fabs(ge[b] * tab[12 * a + b]);
+            q += ssd[b] * tab[288 + 12 * a + b] + fabs(gs[b] * tab[432 + 12 * a + b]) +
+                 fabs(ge[b] * tab[288 + 12 * a + b]);
+        }
+        rF[a] = f;
+        rP[a] = q;
+    }
+}
+
+/* tau_pass = c1 mu b sqrt(rho_P), tau_cut = Q_slip sqrt(rho_F) / (c2 c3 b^2) and the prefactor
+ * A = gdot_0 exp(-Q_slip / k_B T), gdot_0 = 2 k_B T nu_D sqrt(rho_P) / (c1 c3 mu b^2) (Eq. FlowRule). */
+void orc_mr_frozen(const orc_params *p, const double rF[12], const double rP[12], double tp[12], double tcut[12],
+                   double A[12]) {
+    const double kT = ORC_KB * p->T, mu = mu_voigt(p), muPa = 1e6 * mu, b = p->b;
+    for (int a = 0; a < 12; ++a) {
+        tp[a] = p->c1 * mu * b * sqrt(rP[a]);
+        tcut[a] = 1e-6 * p->Q_slip * sqrt(rF[a]) / (p->c2 * p->c3 * b * b);
+        A[a] = 2.0 * kT * p->nu_D * sqrt(rP[a]) / (p->c1 * p->c3 * muPa * b * b) * exp(-p->Q_slip / kT);
+    }
+}
+
+/* Reading R4. */
+double orc_mr_rho_m(const orc_params *p, double rF, double rP) {
+    const double kT = ORC_KB * p->T, muPa = 1e6 * mu_voigt(p), b = p->b;
+    return 2.0 * kT / (p->c1 * p->c2 * p->c3 * muPa * b * b * b) * sqrt(rP * rF);
+}
+
+/* Eq. FlowRule: gdot = A sinh((|tau| - tp) / tcut) sign(tau) above the passing stress, else 0.
+ * Also d gdot / d tau and the convex potential psi(tau) = A tcut (cosh(.) - 1) whose derivative
+ * is gdot. */
+double orc_mr_gdot(double tau, double tp, double tcut, double A, double *dg, double *psi) {
+    const double at = fabs(tau);
+    if (!(at > tp)) { *dg = 0.0; *psi = 0.0; return 0.0; }
+    const double x = (at - tp) / tcut;
+    *dg = A * cosh(x) / tcut;
+    *psi = A * tcut * (cosh(x) - 1.0);
+    return tau < 0.0 ? -A * sinh(x) : A * sinh(x);
+}
+
+/* von Mises equivalents of a Mandel stress and of a Mandel strain (rate). */
+double orc_vm_stress(const double s[6]) {
+    const double m = (s[0] + s[1] + s[2]) / 3.0;
+    const double ss = (s[0] - m) * (s[0] - m) + (s[1] - m) * (s[1] - m) + (s[2] - m) * (s[2] - m) +
+                      s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
+    return sqrt(1.5 * ss);
+}
+double orc_vm_strain(const double e[6]) {
+    const double m = (e[0] + e[1] + e[2]) / 3.0;
+    const double ee = (e[0] - m) * (e[0] - m) + (e[1] - m) * (e[1] - m) + (e[2] - m) * (e[2] - m) +
+                      e[3] * e[3] + e[4] * e[4] + e[5] * e[5];
+    return sqrt(ee / 1.5);
+}
+
+/* Eq. SSDEvolution (reading R5): lock formation, dipole formation, athermal annihilation and
+ * climb, per slip system, from the densities and projections at the start of the increment and
+ * the converged resolved stresses and shear rates. */
+void orc_mr_ssd_rate(const orc_params *p, const double ssd[12], const double rF[12], const double rP[12],
+                     const double tau[12], const double gd[12], double svm, double gvm, double rate[12]) {
+    const double kT = ORC_KB * p->T, mu = mu_voigt(p), b = p->b;
+    const double climb = p->c7 * exp(-p->Q_bulk / kT) * (1e6 * svm) / kT * pow(gvm, p->c8);
+    for (int a = 0; a < 12; ++a) {
+        const double ag = fabs(gd[a]);
+        double r = p->c4 * sqrt(rF[a]) * ag - p->c5 * ssd[a] * ag;
+        if (ag > 0.0) {
+            const double ddip = sqrt(3.0) * mu * b / (16.0 * PI * (1.0 - p->poisson) * fabs(tau[a]));
+            r += p->c6 * ddip * orc_mr_rho_m(p, rF[a], rP[a]) * ag;
+        }
+        r -= climb * ssd[a] * ssd[a];
+        rate[a] = r;
+    }
+}
+
+/* Sample-frame slip directions d and sense vectors t = n x d of every grain (G x 12 x 3 each). */
+void orc_mr_grain_vectors(int G, const double *quat, double *dv, double *tv) {
+    double d[12][3], nr[12][3];
+    orc_slip_systems(d, nr);
+    for (int g = 0; g < G; ++g) {
+        double R[9];
+        orc_quat_to_R(quat + 4 * g, R);
+        for (int a = 0; a < 12; ++a) {
+            double t[3] = {nr[a][1] * d[a][2] - nr[a][2] * d[a][1], nr[a][2] * d[a][0] - nr[a][0] * d[a][2],
+                           nr[a][0] * d[a][1] - nr[a][1] * d[a][0]};
+            for (int i = 0; i < 3; ++i) {
+                dv[36 * g + 3 * a + i] = R[3 * i] * d[a][0] + R[3 * i + 1] * d[a][1] + R[3 * i + 2] * d[a][2];
+                tv[36 * g + 3 * a + i] = R[3 * i] * t[0] + R[3 * i + 1] * t[1] + R[3 * i + 2] * t[2];
+            }
+        }
+    }
+}
+
+/* Eq. GNDEvolution with the differences of reading R6: rs = rho_dot_GNDs = -(grad gdot . t)/b,
+ * re = rho_dot_GNDet = (grad gdot . d)/b, fields 12 x N^3, gd the shear-rate field 12 x N^3. */
+void orc_mr_gnd_rates(int n, const int32_t *g, const int32_t *g0, const double *gd, const double *dv,
+                      const double *tv, double leff, double b, double *rs, double *re) {
+    const long N3 = (long)n * n * n;
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < N3; ++v) {
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
+        long np[3], nm[3];
+        np[0] = ((x + 1) % n) + (long)n * (y + (long)n * z);
+        nm[0] = ((x + n - 1) % n) + (long)n * (y + (long)n * z);
+        np[1] = x + (long)n * (((y + 1) % n) + (long)n * z);
+        nm[1] = x + (long)n * (((y + n - 1) % n) + (long)n * z);
+        np[2] = x + (long)n * (y + (long)n * ((z + 1) % n));
+        nm[2] = x + (long)n * (y + (long)n * ((z + n - 1) % n));
+        int sp[3], sm[3];
+        for (int i = 0; i < 3; ++i) {
+            sp[i] = g[np[i]] == g[v] && g0[np[i]] == g0[v];
+            sm[i] = g[nm[i]] == g[v] && g0[nm[i]] == g0[v];
+        }
+        const double *D = dv + 36 * (long)g0[v], *T = tv + 36 * (long)g0[v];
+        for (int a = 0; a < 12; ++a) {
+            const double *f = gd + a * N3;
+            double grad[3];
+            for (int i = 0; i < 3; ++i) {
+                if (sp[i] && sm[i]) grad[i] = (f[np[i]] - f[nm[i]]) / (2.0 * leff);
+                else if (sp[i]) grad[i] = (f[np[i]] - f[v]) / leff;
+                else if (sm[i]) grad[i] = (f[v] - f[nm[i]]) / leff;
+                else grad[i] = 0.0;
+            }
+            double gt = 0.0, gdd = 0.0;
+            for (int i = 0; i < 3; ++i) { gt += grad[i] * T[3 * a + i]; gdd += grad[i] * D[3 * a + i]; }
+            rs[a * N3 + v] = -gt / b;
+            re[a * N3 + v] = gdd / b;
+        }
+    }
+}
+
+/* Eq. L0evolution with reading R8. */
+double orc_mr_leff_next(double leff, const double E[6], double xi) { return leff * (1.0 + orc_vm_strain(E) / xi); }
+
+static void mr_hardening(const orc_params *p, const double tab[576], const double ssd[12], const double gs[12],
+                         const double ge[12], double rF[12], double rP[12], double tp[12], double tcut[12],
+                         double A[12], double *tref) {
+    orc_mr_project(tab, ssd, gs, ge, rF, rP);
+    orc_mr_frozen(p, rF, rP, tp, tcut, A);
+    double m = tp[0];
+    for (int a = 1; a < 12; ++a) m = fmin(m, tp[a]);
+    *tref = m;
+}
+
+/* Eq. TotDislocationDensity: k = sum_a rho_M^a + rho_SSD^a + rho_GND^a. */
+static double mr_k(const orc_params *p, const double tab[576], const double ssd[12], const double gs[12],
+                   const double ge[12], const double gnd[12]) {
+    double rF[12], rP[12], k = 0.0;
+    orc_mr_project(tab, ssd, gs, ge, rF, rP);
+    for (int a = 0; a < 12; ++a) k += orc_mr_rho_m(p, rF[a], rP[a]) + ssd[a] + gnd[a];
+    return k;
+}
+
+int orc_newton_mr(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+                  const double tp[12], const double tcut[12], const double A[12], double tref, double dt,
+                  double tol, int maxit, double sig[6], double gdot[12], int *iters) {
+    nt_flow f = {1, tref, tp, tcut, A};
+    return nt_newton(p, S, M, eps_tr, &f, dt, tol, maxit, sig, gdot, iters);
+}
+
+void orc_residual_mr(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+                     const double tp[12], const double tcut[12], const double A[12], double dt,
+                     const double sig[6], double r[6]) {
+    nt_eval e;
+    nt_flow f = {1, 0.0, tp, tcut, A};
+    nt_evaluate(p, S, M, eps_tr, &f, dt, sig, &e);
+    memcpy(r, e.r, sizeof e.r);
+}
+
+/* The uniaxial-stress point model of one crystal (as orc_point_model, bisection on sigma33) with
+ * the Ma-Roters law: SSD densities only (a uniform crystal has no slip gradients, so no GND). */
+int orc_point_model_mr(const orc_params *p, const double *S, const double *M, double *sig, double *epsp,
+                       double *ssd, double *E, double dE33, double dt, int nsteps, double *sig33_hist) {
+    double tab[576];
+    orc_mr_tables(tab);
+    const double zero12[12] = {0};
+    for (int st = 0; st < nsteps; ++st) {
+        double rF[12], rP[12], tp[12], tcut[12], A[12], tref;
+        mr_hardening(p, tab, ssd, zero12, zero12, rF, rP, tp, tcut, A, &tref);
+        nt_flow fl = {1, tref, tp, tcut, A};
+        double target = E[2] + dE33;
+        nt_eval e;
+        double zero6[6] = {0, 0, 0, 0, 0, 0};
+#define F33(s33, out)                                                                  \
+    do {                                                                               \
+        double sg[6] = {0, 0, (s33), 0, 0, 0};                                         \
+        nt_evaluate(p, S, M, zero6, &fl, dt, sg, &e);                                  \
+        (out) = e.r[2] + epsp[2] - target;                                             \
+    } while (0)
+        double lo = -1.0, hi = 1.0, flo, fhi;
+        F33(lo, flo);
+        F33(hi, fhi);
+        for (int k = 0; k < 200 && flo > 0.0; ++k) { lo *= 2.0; F33(lo, flo); }
+        for (int k = 0; k < 200 && fhi < 0.0; ++k) { hi *= 2.0; F33(hi, fhi); }
+        if (flo > 0.0 || fhi < 0.0) return -1;
+        for (int k = 0; k < 400 && hi - lo > 0.0; ++k) {
+            double mid = 0.5 * (lo + hi), fm;
+            if (mid == lo || mid == hi) break;
+            F33(mid, fm);
+            if (fm > 0.0) hi = mid; else lo = mid;
+        }
+#undef F33
+        double s33 = 0.5 * (lo + hi);
+        double sg[6] = {0, 0, s33, 0, 0, 0};
+        nt_evaluate(p, S, M, zero6, &fl, dt, sg, &e);
+        for (int I = 0; I < 6; ++I) E[I] = e.r[I] + epsp[I];
+        E[2] = target;
+        double ep[6], tau[12], rate[12];
+        for (int I = 0; I < 6; ++I) {
+            ep[I] = 0.0;
+            for (int a = 0; a < 12; ++a) ep[I] += M[6 * a + I] * e.gdot[a];
+            epsp[I] += dt * ep[I];
+        }
+        for (int a = 0; a < 12; ++a) {
+            tau[a] = 0.0;
+            for (int I = 0; I < 6; ++I) tau[a] += M[6 * a + I] * sg[I];
+        }
+        orc_mr_ssd_rate(p, ssd, rF, rP, tau, e.gdot, orc_vm_stress(sg), orc_vm_strain(ep), rate);
+        for (int a = 0; a < 12; ++a) ssd[a] = fmax(0.0, ssd[a] + dt * rate[a]);
+        memcpy(sig, sg, sizeof sg);
+        if (sig33_hist) sig33_hist[st] = s33;
     }
     return 0;
 }
@@ -439,6 +752,12 @@ struct orc_state {
     double *kpf;
     double *work_eps, *work_sig;
     double complex *spec;
+    /* Ma-Roters law (cfg.law = 1): rho holds rho_SSD; signed GND components gs = rho_GNDs,
+     * ge = rho_GNDet and the accumulated rho_GND (12 x N^3 each); sample-frame d and t per grain;
+     * the projection tables; the effective GND length */
+    double *gs, *ge, *gnd, *dv, *tv;
+    double tab[576];
+    double leff;
 };
 
 static void *xcalloc(size_t n, size_t sz) {
@@ -523,6 +842,42 @@ static void pf_restrict_ids(orc_state *s) {
             }
 }
 
+/* k at voxel v from its densities: sum of rho for the power law, Eq. TotDislocationDensity for the
+ * Ma-Roters law. */
+static void refresh_k_voxel(orc_state *s, long v) {
+    const long N3 = s->N3;
+    if (s->cfg.law == 1) {
+        double ssd[12], gs[12], ge[12], gnd[12];
+        for (int a = 0; a < 12; ++a) {
+            ssd[a] = s->rho[a * N3 + v]; gs[a] = s->gs[a * N3 + v];
+            ge[a] = s->ge[a * N3 + v]; gnd[a] = s->gnd[a * N3 + v];
+        }
+        s->k[v] = mr_k(&s->p, s->tab, ssd, gs, ge, gnd);
+        return;
+    }
+    double kk = 0.0;
+    for (int a = 0; a < 12; ++a) kk += s->rho[a * N3 + v];
+    s->k[v] = kk;
+}
+
+/* Softening of recrystallised material (Eq. UpdateGND): the power law's single density family is
+ * scaled by s_soften; with the Ma-Roters law the GND densities are, the SSD density is kept
+ * (reading R9). k follows. */
+static void soften_voxel(orc_state *s, long v) {
+    const long N3 = s->N3;
+    const double f = s->p.s_soften;
+    for (int a = 0; a < 12; ++a) {
+        if (s->cfg.law == 1) {
+            s->gs[a * N3 + v] = f * s->gs[a * N3 + v];
+            s->ge[a * N3 + v] = f * s->ge[a * N3 + v];
+            s->gnd[a * N3 + v] = f * s->gnd[a * N3 + v];
+        } else {
+            s->rho[a * N3 + v] = f * s->rho[a * N3 + v];
+        }
+    }
+    refresh_k_voxel(s, v);
+}
+
 orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat,
                       uint64_t seed) {
     orc_state *s = (orc_state *)xcalloc(1, sizeof *s);
@@ -562,13 +917,21 @@ orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t 
     s->work_eps = xcalloc(6 * N3, sizeof(double));
     s->work_sig = xcalloc(6 * N3, sizeof(double));
     s->spec = xcalloc(6 * N3, sizeof(double complex));
+    if (cfg->law == 1) {
+        s->gs = xcalloc(12 * N3, sizeof(double));
+        s->ge = xcalloc(12 * N3, sizeof(double));
+        s->gnd = xcalloc(12 * N3, sizeof(double));
+        s->dv = xcalloc(36 * (size_t)s->G, sizeof(double));
+        s->tv = xcalloc(36 * (size_t)s->G, sizeof(double));
+        orc_mr_grain_vectors(s->G, quat, s->dv, s->tv);
+        orc_mr_tables(s->tab);
+        s->leff = p->dx;
+    }
     for (long v = 0; v < N3; ++v) {
         s->g0[v] = g0[v];
         s->g[v] = g0[v];
         for (int a = 0; a < 12; ++a) s->rho[a * N3 + v] = p->rho0;
-        double kk = 0.0;
-        for (int a = 0; a < 12; ++a) kk += s->rho[a * N3 + v];
-        s->k[v] = kk;
+        refresh_k_voxel(s, v);
         /* initial nucleation strength: draw 0 from Weibull(q, kc) (Sec. 2.3, implementation) */
         s->kappa[v] = orc_weibull(orc_u01(seed, (uint64_t)v, 0), p->kc, p->q);
     }
@@ -599,6 +962,7 @@ void orc_destroy(orc_state *s) {
     free(s->deps_prev); free(s->rho); free(s->k); free(s->kappa); free(s->work_eps);
     free(s->work_sig); free(s->spec);
     if (s->r != 1) { free(s->gpf); free(s->kpf); }
+    free(s->gs); free(s->ge); free(s->gnd); free(s->dv); free(s->tv);
     free(s);
 }
 
@@ -617,6 +981,10 @@ double *orc_field(orc_state *s, const char *name) {
     if (!strcmp(name, "M")) return s->M;
     if (!strcmp(name, "E")) return s->E;
     if (!strcmp(name, "dE_prev")) return s->dE_prev;
+    if (!strcmp(name, "gnds")) return s->gs;
+    if (!strcmp(name, "gndet")) return s->ge;
+    if (!strcmp(name, "gnd")) return s->gnd;
+    if (!strcmp(name, "leff")) return &s->leff;
     return NULL;
 }
 
@@ -632,15 +1000,13 @@ int32_t *orc_ifield(orc_state *s, const char *name) {
 int orc_next_id(orc_state *s) { return s->next_id; }
 void orc_set_next_id(orc_state *s, int next_id) { s->next_id = next_id; }
 
-/* Recompute k = rho_tot from rho (after a caller overwrote rho). */
+/* Recompute k = rho_tot from the densities (after a caller overwrote them). */
 void orc_refresh_derived(orc_state *s) {
-    for (long v = 0; v < s->N3; ++v) {
-        double kk = 0.0;
-        for (int a = 0; a < 12; ++a) kk += s->rho[a * s->N3 + v];
-        s->k[v] = kk;
-    }
+    for (long v = 0; v < s->N3; ++v) refresh_k_voxel(s, v);
     pf_interp_k(s);
 }
+
+double orc_leff(orc_state *s) { return s->leff; }
 
 /* Signed frequency of index k on an n-point axis; the Nyquist index n/2 is taken as +n/2. */
 static int freq(int k, int n) { return k <= n / 2 ? k : k - n; }
@@ -711,6 +1077,107 @@ void orc_stress_residual(int n, const double *sig, double out[7]) {
  * to max(|E|, 1e-6) and of C0 (eps - e) relative to max(|<lam>|, tau0), and the mean stress on the
  * stress-controlled components, all below tol.
  * ---------------------------------------------------------------------------------------- */
+/* Hardening frozen over the increment (explicit in the densities, reading R1): tau_c per voxel for
+ * the power law (returns NULL); for the Ma-Roters law returns hf = rho_F, rho_P, tau_pass, tau_cut,
+ * A (5 x 12 x N^3) and puts the Newton stopping scale tau_ref in tauc (reading R10). */
+static double *frozen_hardening(orc_state *s, double *tauc) {
+    const orc_params *p = &s->p;
+    const long N3 = s->N3;
+    if (s->cfg.law != 1) {
+        for (long v = 0; v < N3; ++v) tauc[v] = tauc_of(p, s->rho, N3, v);
+        return NULL;
+    }
+    double *hf = (double *)xcalloc(60 * (size_t)N3, sizeof(double));
+    for (long v = 0; v < N3; ++v) {
+        double ssd[12], gs[12], ge[12], h[5][12];
+        for (int a = 0; a < 12; ++a) {
+            ssd[a] = s->rho[a * N3 + v]; gs[a] = s->gs[a * N3 + v]; ge[a] = s->ge[a * N3 + v];
+        }
+        mr_hardening(p, s->tab, ssd, gs, ge, h[0], h[1], h[2], h[3], h[4], &tauc[v]);
+        for (int q = 0; q < 5; ++q)
+            for (int a = 0; a < 12; ++a) hf[(12 * q + a) * N3 + v] = h[q][a];
+    }
+    return hf;
+}
+
+/* The local Newton of voxel v with compliance S (the grain's, or S + C0^-1 in the augmented
+ * Lagrangian scheme) and the frozen flow-rule data of either law. */
+static int local_newton(const orc_state *s, const double *S, long v, const double *tauc, const double *hf,
+                        const double etr[6], double dt, double sg[6], double gd[12], int *its) {
+    const long N3 = s->N3;
+    const int gr = s->g0[v];
+    if (hf) {
+        double tp[12], tcut[12], A[12];
+        for (int a = 0; a < 12; ++a) {
+            tp[a] = hf[(24 + a) * N3 + v]; tcut[a] = hf[(36 + a) * N3 + v]; A[a] = hf[(48 + a) * N3 + v];
+        }
+        return orc_newton_mr(&s->p, S, s->M + 72 * gr, etr, tp, tcut, A, tauc[v], dt, s->cfg.newton_tol,
+                             s->cfg.newton_max, sg, gd, its);
+    }
+    return orc_newton(&s->p, S, s->M + 72 * gr, etr, tauc[v], dt, s->cfg.newton_tol, s->cfg.newton_max, sg, gd,
+                      its);
+}
+
+/* a7 with the Ma-Roters law: plastic strain from the converged shear rates, then the densities
+ * by explicit Euler: SSD by Eq. SSDEvolution from the projections at the start of the increment,
+ * GND by Eq. GNDEvolution from the gradient of the converged shear-rate field (readings R5-R7),
+ * and k by Eq. TotDislocationDensity. hf as in orc_increment. */
+static void mr_state_update(orc_state *s, const double *sigk, const double *epsk, const double *hf, double dt) {
+    const orc_params *p = &s->p;
+    const long N3 = s->N3;
+    double *gdf = (double *)xcalloc(12 * (size_t)N3, sizeof(double));
+    double *tauf = (double *)xcalloc(12 * (size_t)N3, sizeof(double));
+    double *svm = (double *)xcalloc(N3, sizeof(double));
+    double *gvm = (double *)xcalloc(N3, sizeof(double));
+    double *rs = (double *)xcalloc(12 * (size_t)N3, sizeof(double));
+    double *re = (double *)xcalloc(12 * (size_t)N3, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < N3; ++v) {
+        const double *M = s->M + 72 * s->g0[v];
+        double sg[6], ep[6] = {0, 0, 0, 0, 0, 0};
+        for (int I = 0; I < 6; ++I) sg[I] = sigk[I * N3 + v];
+        for (int a = 0; a < 12; ++a) {
+            double tau = 0.0, dg, psi;
+            for (int I = 0; I < 6; ++I) tau += M[6 * a + I] * sg[I];
+            const double gd = orc_mr_gdot(tau, hf[(24 + a) * N3 + v], hf[(36 + a) * N3 + v], hf[(48 + a) * N3 + v],
+                                          &dg, &psi);
+            gdf[a * N3 + v] = gd;
+            tauf[a * N3 + v] = tau;
+            for (int I = 0; I < 6; ++I) ep[I] += M[6 * a + I] * gd;
+        }
+        svm[v] = orc_vm_stress(sg);
+        gvm[v] = orc_vm_strain(ep);
+        for (int I = 0; I < 6; ++I) {
+            s->epsp[I * N3 + v] += dt * ep[I];
+            s->deps_prev[I * N3 + v] = epsk[I * N3 + v] - s->eps[I * N3 + v];
+            s->eps[I * N3 + v] = epsk[I * N3 + v];
+            s->sig[I * N3 + v] = sg[I];
+        }
+    }
+    orc_mr_gnd_rates(s->n, s->g, s->g0, gdf, s->dv, s->tv, s->leff, p->b, rs, re);
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < N3; ++v) {
+        double ssd[12], rF[12], rP[12], tau[12], gd[12], rate[12];
+        for (int a = 0; a < 12; ++a) {
+            ssd[a] = s->rho[a * N3 + v];
+            rF[a] = hf[a * N3 + v];
+            rP[a] = hf[(12 + a) * N3 + v];
+            tau[a] = tauf[a * N3 + v];
+            gd[a] = gdf[a * N3 + v];
+        }
+        orc_mr_ssd_rate(p, ssd, rF, rP, tau, gd, svm[v], gvm[v], rate);
+        for (int a = 0; a < 12; ++a) {
+            const long i = a * N3 + v;
+            s->rho[i] = fmax(0.0, ssd[a] + dt * rate[a]);
+            s->gs[i] += dt * rs[i];
+            s->ge[i] += dt * re[i];
+            s->gnd[i] += dt * sqrt(rs[i] * rs[i] + re[i] * re[i]);
+        }
+        refresh_k_voxel(s, v);
+    }
+    free(gdf); free(tauf); free(svm); free(gvm); free(rs); free(re);
+}
+
 static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out) {
     const orc_params *p = &s->p;
     const int n = s->n;
@@ -734,7 +1201,7 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
     for (int g = 0; g < s->G; ++g)
         for (int i = 0; i < 36; ++i) Sal[36 * g + i] = s->S[36 * g + i] + S0[i];
     double *tauc = (double *)xcalloc(N3, sizeof(double));
-    for (long v = 0; v < N3; ++v) tauc[v] = tauc_of(p, s->rho, N3, v);
+    double *hf = frozen_hardening(s, tauc);
     double *eps = s->work_eps, *sig = s->work_sig;
     double *e = (double *)xcalloc(6 * N3, sizeof(double));
     double *lam = (double *)xcalloc(6 * N3, sizeof(double));
@@ -761,8 +1228,7 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
         double etr[6], sg[6], gd[12];
         for (int I = 0; I < 6; ++I) { etr[I] = eps[I * N3 + v] - s->epsp[I * N3 + v]; sg[I] = sig[I * N3 + v]; }
         int its = 0;
-        if (orc_newton(p, s->S + 36 * gr, s->M + 72 * gr, etr, tauc[v], dt, s->cfg.newton_tol, s->cfg.newton_max,
-                       sg, gd, &its)) newton_fail |= 1;
+        if (local_newton(s, s->S + 36 * gr, v, tauc, hf, etr, dt, sg, gd, &its)) newton_fail |= 1;
         if (its > newton_max) newton_max = its;
         for (int I = 0; I < 6; ++I) { sig[I * N3 + v] = sg[I]; lam[I * N3 + v] = sg[I]; e[I * N3 + v] = eps[I * N3 + v]; }
     }
@@ -838,8 +1304,7 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
                 sg[I] = sig[I * N3 + v];
             }
             int its = 0;
-            if (orc_newton(p, Sal + 36 * gr, s->M + 72 * gr, etr, tauc[v], dt, s->cfg.newton_tol, s->cfg.newton_max,
-                           sg, gd, &its)) newton_fail |= 1;
+            if (local_newton(s, Sal + 36 * gr, v, tauc, hf, etr, dt, sg, gd, &its)) newton_fail |= 1;
             if (its > newton_max) newton_max = its;
             double ev[6], d[6];
             for (int I = 0; I < 6; ++I) {
@@ -890,11 +1355,14 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
     if (status < 0) {
         for (int I = 0; I < 6; ++I) out->E[I] = s->E[I] + dE[I];
         out->status = status;
-        free(Sal); free(tauc); free(e); free(lam);
+        free(Sal); free(tauc); free(e); free(lam); free(hf);
         return status;
     }
     /* state update with the converged stress; the stored total strain is the compatible field eps
      * of the last compatibility step (equal to the local strain e to the tolerance) */
+    if (hf) {
+        mr_state_update(s, sig, eps, hf, dt);
+    } else {
 #pragma omp parallel for schedule(static)
     for (long v = 0; v < N3; ++v) {
         int gr = s->g0[v];
@@ -922,11 +1390,13 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
             s->sig[I * N3 + v] = sig[I * N3 + v];
         }
     }
+    }
     for (int I = 0; I < 6; ++I) { s->E[I] += dE[I]; s->dE_prev[I] = dE[I]; }
+    if (hf) s->leff = orc_mr_leff_next(s->leff, s->E, p->xi);
     s->have_prev = 1;
     memcpy(out->E, s->E, sizeof s->E);
     out->status = status;
-    free(Sal); free(tauc); free(e); free(lam);
+    free(Sal); free(tauc); free(e); free(lam); free(hf);
     return status;
 }
 
@@ -950,9 +1420,9 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
         for (int b = 0; b < 5; ++b) C0uu[5 * a + b] = C0[6 * U[a] + U[b]];
     inv_gj(5, C0uu, C0uu_inv);
 
-    /* hardening frozen over the increment (explicit in rho) */
+    /* hardening frozen over the increment */
     double *tauc = (double *)xcalloc(N3, sizeof(double));
-    for (long v = 0; v < N3; ++v) tauc[v] = tauc_of(p, s->rho, N3, v);
+    double *hf = frozen_hardening(s, tauc);
 
     /* predictor: extrapolate the previous strain-increment field, else a uniform guess that is
      * the reference medium's response to dE33 under zero lateral stress */
@@ -985,8 +1455,7 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
                 sg[I] = sigk[I * N3 + v];
             }
             int its = 0;
-            int rc = orc_newton(p, s->S + 36 * gr, s->M + 72 * gr, etr, tauc[v], dt, s->cfg.newton_tol,
-                                s->cfg.newton_max, sg, gd, &its);
+            int rc = local_newton(s, s->S + 36 * gr, v, tauc, hf, etr, dt, sg, gd, &its);
             if (rc) newton_fail |= 1;
             if (its > newton_max) newton_max = its;
             for (int I = 0; I < 6; ++I) sigk[I * N3 + v] = sg[I];
@@ -1056,8 +1525,12 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
         for (int I = 0; I < 6; ++I) out->E[I] = s->E[I] + dE[I];
         out->status = status;
         free(tauc);
+        free(hf);
         return status;
     }
+    if (hf) {
+        mr_state_update(s, sigk, epsk, hf, dt);
+    } else {
     /* a7: state update with the converged stress */
 #pragma omp parallel for schedule(static)
     for (long v = 0; v < N3; ++v) {
@@ -1086,11 +1559,14 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
             s->sig[I * N3 + v] = sigk[I * N3 + v];
         }
     }
+    }
     for (int I = 0; I < 6; ++I) { s->E[I] += dE[I]; s->dE_prev[I] = dE[I]; }
+    if (hf) s->leff = orc_mr_leff_next(s->leff, s->E, p->xi);
     s->have_prev = 1;
     memcpy(out->E, s->E, sizeof s->E);
     out->status = status;
     free(tauc);
+    free(hf);
     return status;
 }
 
@@ -1216,6 +1692,7 @@ static int adj_solve(int n, double lam0, double mu0, const double *Ct, const dou
 int orc_loss_grad(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat, uint64_t seed,
                   int T, double dE33, double dt, const double *target, double *loss, double grad[4], double *sig33,
                   double adj_tol) {
+    if (cfg->law != 0) return -1;   /* the adjoint covers the power law + Kocks-Mecking only */
     orc_state *s = orc_create(cfg, p, g0, quat, seed);
     const long N3 = s->N3;
     const int n = s->n;
@@ -1381,12 +1858,7 @@ int orc_nucleate(orc_state *s, uint64_t step, int32_t *n_new) {
             s->gpf[w] = id;
         }
         s->g[v] = id;
-        double kk = 0.0;
-        for (int a = 0; a < 12; ++a) {
-            s->rho[a * N3 + v] = p->s_soften * s->rho[a * N3 + v];
-            kk += s->rho[a * N3 + v];
-        }
-        s->k[v] = kk;
+        soften_voxel(s, v);
         s->draws[v] += 1;
         s->kappa[v] = orc_weibull(orc_u01(s->seed, (uint64_t)v, (uint64_t)s->draws[v]), p->s_nucl * p->kc, p->q);
     }
@@ -1593,14 +2065,7 @@ int orc_pf_step(orc_state *s, int nsteps, orc_pf_stats *out) {
     /* sweep softening: a voxel whose grain changes from a deformed to a recrystallised one
      * over this call has its densities scaled by s_soften (reading of Eq. UpdateGND) */
     for (long v = 0; v < N3; ++v) {
-        if (gprev[v] < s->G && s->g[v] >= s->G) {
-            double kk = 0.0;
-            for (int a = 0; a < 12; ++a) {
-                s->rho[a * N3 + v] = s->p.s_soften * s->rho[a * N3 + v];
-                kk += s->rho[a * N3 + v];
-            }
-            s->k[v] = kk;
-        }
+        if (gprev[v] < s->G && s->g[v] >= s->G) soften_voxel(s, v);
     }
     free(gprev);
     pf_interp_k(s);

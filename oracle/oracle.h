@@ -26,6 +26,12 @@ typedef struct {
     double zeta;               /* stored energy = zeta*mu*b^2*rho_tot */
     double kc, q, s_nucl, s_soften;
     double omega_gb, dx, l_gb, L_dt, eta_drop;
+    /* Ma-Roters dislocation law (law = 1, Sec. 2.2, Table 1); dx is the grid size l0 */
+    double T;                  /* temperature, K */
+    double Q_slip, Q_bulk;     /* activation energies for glide and for climb, J */
+    double nu_D, poisson;      /* attempt frequency, 1/s; Poisson's ratio (d_dipole) */
+    double c1, c2, c3, c4, c5, c6, c7, c8;
+    double xi;                 /* effective GND length: l_eff <- l_eff (1 + eps_vm / xi) */
 } orc_params;
 
 typedef struct {
@@ -40,6 +46,7 @@ typedef struct {
     int scheme;                /* 0: basic Green-operator iteration, 1: augmented Lagrangian */
     double al_scale;           /* augmented Lagrangian: reference shear modulus = mu_Voigt / al_scale */
     int pf_refine;             /* phase-field grid per mechanics grid spacing: 1 (same grid) or 2 (Sec. 2.4) */
+    int law;                   /* 0: power law + Kocks-Mecking; 1: Ma-Roters dislocation law (Sec. 2.2) */
 } orc_config;
 
 typedef struct {
@@ -76,6 +83,32 @@ int orc_point_model(const orc_params *p, const double *S, const double *M, doubl
                     double *rho, double *E, double dE33, double dt, int nsteps, double *sig33_hist);
 
 void orc_stress_residual(int n, const double *sig, double out[7]);
+
+/* ---- Ma-Roters dislocation law (Sec. 2.2), pinned by tests/test_oracle_mr.py ---- */
+void orc_mr_tables(double tab[576]);
+void orc_mr_project(const double tab[576], const double ssd[12], const double gs[12], const double ge[12],
+                    double rF[12], double rP[12]);
+void orc_mr_frozen(const orc_params *p, const double rF[12], const double rP[12], double tp[12], double tcut[12],
+                   double A[12]);
+double orc_mr_rho_m(const orc_params *p, double rF, double rP);
+double orc_mr_gdot(double tau, double tp, double tcut, double A, double *dg, double *psi);
+void orc_mr_ssd_rate(const orc_params *p, const double ssd[12], const double rF[12], const double rP[12],
+                     const double tau[12], const double gd[12], double svm, double gvm, double rate[12]);
+double orc_vm_stress(const double sig[6]);
+double orc_vm_strain(const double e[6]);
+void orc_mr_grain_vectors(int G, const double *quat, double *dv, double *tv);
+void orc_mr_gnd_rates(int n, const int32_t *g, const int32_t *g0, const double *gd, const double *dv,
+                      const double *tv, double leff, double b, double *rs, double *re);
+double orc_mr_leff_next(double leff, const double E[6], double xi);
+int orc_newton_mr(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+                  const double tp[12], const double tcut[12], const double A[12], double tref, double dt,
+                  double tol, int maxit, double sig[6], double gdot[12], int *iters);
+void orc_residual_mr(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
+                     const double tp[12], const double tcut[12], const double A[12], double dt,
+                     const double sig[6], double r[6]);
+int orc_point_model_mr(const orc_params *p, const double *S, const double *M, double *sig, double *epsp,
+                       double *ssd, double *E, double dE33, double dt, int nsteps, double *sig33_hist);
+double orc_leff(orc_state *s);
 
 /* ---- full state ---- */
 orc_state *orc_create(const orc_config *cfg, const orc_params *p, const int32_t *g0, const double *quat,

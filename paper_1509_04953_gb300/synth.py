@@ -43,6 +43,21 @@ class Material:
     l_gb: float = float(np.sqrt(9.6))  # interface width in grid spacings
     L_dt: float = 0.05             # Allen-Cahn mobility x PF time step (grid units)
     eta_drop: float = 1.0e-5       # active-set drop threshold
+    # Ma-Roters dislocation law (Table 1); the grid size l0 is dx
+    T: float = 723.0               # temperature of the DRX case, K
+    Q_slip: float = 3.3e-19        # activation energy for slip, J
+    Q_bulk: float = 3.51e-19       # activation energy for climb, J
+    nu_D: float = 1.0e13           # attempt frequency, order of the Debye frequency, 1/s (not printed)
+    poisson: float = 0.34          # Poisson's ratio of copper in d_dipole (not printed)
+    c1: float = 0.5
+    c2: float = 3.0
+    c3: float = 3.0
+    c4: float = 8.0e7              # 1/m
+    c5: float = 10.0
+    c6: float = 3.0e10             # 1/m, dipole term (the equation's placement)
+    c7: float = 7.0e-28            # m^5 s^(c8-1), climb term
+    c8: float = 0.24
+    xi: float = 200.0
 
     @property
     def mu(self) -> float:
@@ -75,6 +90,12 @@ WORKLOADS = {
     "cu32adj": Workload("cu32_adjoint_32^3_27grains", 32, 27, 50, -1.0e-3, 1.0, 5, "fp64", BASE_SEED + 3),
     "cu256": Workload("cu256_mixed_256^3_1024grains", 256, 1024, 1000, -6.0e-4, 0.6, 5, "mixed", BASE_SEED + 4),
 }
+
+
+def ma_roters_material(T: float = 723.0) -> Material:
+    """Copper with the Ma-Roters law: initial SSD density per system 2.8e11 /m^2 at 723 K and
+    2.5e12 /m^2 at 473 K (Sec. 3)."""
+    return Material(T=T, rho0=2.8e11 if T >= 600.0 else 2.5e12)
 
 
 def voronoi_seeds(n: int, grains: int, seed: int) -> np.ndarray:
