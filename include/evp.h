@@ -75,7 +75,19 @@ typedef struct {
     int pf_refine;         /* phase-field grid spacing per mechanics spacing: 0 or 1 = the same grid; 2 = the
                               2:1 refined PF grid of Sec. 2.4 ((2n)^3 PF points; the active sets, the PF argmax
                               and the interpolated driving force live there; see pf_step and drx_nucleate) */
+    int law;               /* constitutive law, EVP_LAW_*: the power law with Kocks-Mecking hardening, or the
+                              paper's Ma-Roters dislocation-density law (Sec. 2.2) */
 } evp_config;
+#define EVP_LAW_POWER 0  /* gdot = gdot0 |tau/tau_c|^n sign(tau); rho^a by storage and dynamic recovery */
+#define EVP_LAW_MR 1     /* Sec. 2.2, Eqs. FlowRule, RhoForest, RhoParallel, SSDEvolution, GNDEvolution,
+                            L0evolution, TotDislocationDensity, UpdateGND; constants of Table 1. Frozen per increment:
+                            tau_pass = c1 mu b sqrt(rho_P), tau_cut = Q_slip sqrt(rho_F)/(c2 c3 b^2) and the prefactor
+                            2 k_B T nu_D sqrt(rho_P) exp(-Q_slip/k_B T)/(c1 c3 mu b^2). After convergence the SSD
+                            densities follow the four-term law (mobile density 2 k_B T sqrt(rho_P rho_F)/(c1 c2 c3 mu
+                            b^3)), the GND densities the slip-rate gradients (spacing l_eff; central differences
+                            inside a grain, one-sided at its boundaries), k = sum of mobile, SSD and GND densities;
+                            softening (nucleation, PF sweep) scales the GND densities only. Not available with
+                            EVP_NEWTON_F32_TANGENT nor with the adjoint. */
 #define EVP_SCHEME_BASIC 0
 #define EVP_SCHEME_AL 1
 #define EVP_NEWTON_EXACT 0
@@ -92,6 +104,12 @@ typedef struct {
     double kc, q, s_nucl, s_soften; /* Weibull nucleation strength and DRX updates (Table 2) */
     double omega_gb, dx, l_gb, L_dt, eta_drop; /* phase field: energy, spacing, width (in dx),
                                                   mobility x time step, active-set drop level */
+    /* EVP_LAW_MR only (Table 1; dx is its grid size l0, rho0 the initial SSD density per system) */
+    double T;                    /* temperature, K */
+    double Q_slip, Q_bulk;       /* activation energies of glide and of climb, J */
+    double nu_D, poisson;        /* attempt frequency (1/s) and Poisson's ratio (d_dipole); the paper prints neither */
+    double c1, c2, c3, c4, c5, c6, c7, c8;  /* c4, c6 in 1/m; c7 in m^5 s^(c8-1); c6 multiplies the dipole term */
+    double xi;                   /* l_eff <- l_eff (1 + eps_vm / xi) after every increment */
 } evp_params;
 
 typedef struct {
@@ -132,6 +150,8 @@ typedef struct evp_handle evp_handle;
 #define EVP_F_ETA   (1u << 12)  /* active-set order parameters, kmax x T per PF point */
 #define EVP_F_GRAIN_PF (1u << 13)  /* argmax id per PF point, 1 x int32 per PF point (get only; the same as
                                       EVP_F_GRAIN when pf_refine <= 1) */
+#define EVP_F_GND   (1u << 14)  /* EVP_LAW_MR only: rho_GNDs, rho_GNDet (signed) and the accumulated rho_GND,
+                                   3 x 12 x T (EVP_F_RHO then holds rho_SSD) */
 
 /* Bytes of device workspace evp_init needs for this configuration. */
 int evp_workspace_bytes(const evp_config *cfg, size_t *bytes);
@@ -180,7 +200,7 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out);
  * exactly `bytes` bytes, see evp_fields_bytes). Synchronises the stream. */
 int get_fields(evp_handle *h, uint32_t field_mask, void *dst, size_t bytes, int dst_is_device);
 /* Overwrite state fields from src (same packing). EVP_F_EPS and EVP_F_G0 cannot be set.
- * Setting EVP_F_RHO refreshes k = rho_tot. */
+ * Setting EVP_F_RHO (or EVP_F_GND) refreshes k = rho_tot. */
 int set_fields(evp_handle *h, uint32_t field_mask, const void *src, size_t bytes, int src_is_device);
 /* Bytes that get_fields / set_fields expect for field_mask. */
 int evp_fields_bytes(const evp_handle *h, uint32_t field_mask, size_t *bytes);
@@ -188,6 +208,10 @@ int evp_fields_bytes(const evp_handle *h, uint32_t field_mask, size_t *bytes);
 /* Macroscopic scalars of the state, for checkpointing: E[6], dE_prev[6], have_prev, next_id. */
 int evp_get_scalars(const evp_handle *h, double *E6, double *dE_prev6, int *have_prev, int *next_id);
 int evp_set_scalars(evp_handle *h, const double *E6, const double *dE_prev6, int have_prev, int next_id);
+/* Effective GND length l_eff of EVP_LAW_MR (Eq. L0evolution; m; starts at dx, advanced after every increment):
+ * read it, or set it (> 0, finite; EVP_ERR_ARG otherwise) when restoring a checkpoint. */
+int evp_get_leff(const evp_handle *h, double *leff);
+int evp_set_leff(evp_handle *h, double leff);
 /* Change the fixed-point controls after init. */
 int evp_set_solver(evp_handle *h, double tol, int max_iter, int allow_unconverged);
 

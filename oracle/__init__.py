@@ -125,6 +125,8 @@ def lib():
         L.orc_vm_strain.argtypes = [_dp]
         L.orc_mr_grain_vectors.argtypes = [C.c_int, _dp, _dp, _dp]
         L.orc_mr_gnd_rates.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
+        L.orc_mr_gnd_rates_voxel.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, C.c_long,
+                                             _dp, _dp]
         L.orc_mr_leff_next.restype = C.c_double
         L.orc_mr_leff_next.argtypes = [C.c_double, _dp, C.c_double]
         L.orc_newton_mr.restype = C.c_int
@@ -454,6 +456,16 @@ def mr_gnd_rates(n, g, g0, gd, quat, leff, b):
                            np.ascontiguousarray(g0, dtype=np.int32).reshape(-1), _a(gd, 12 * N3),
                            dv.reshape(-1), tv.reshape(-1), float(leff), float(b), rs, re)
     return rs.reshape(12, N3), re.reshape(12, N3)
+
+
+def mr_gnd_rates_voxel(n, g, g0, gd, quat, leff, b, v):
+    """The GND rates of voxel v alone (reads gd at v and its six face neighbours only)."""
+    dv, tv = mr_grain_vectors(quat)
+    rs, re = np.zeros(12), np.zeros(12)
+    lib().orc_mr_gnd_rates_voxel(n, np.ascontiguousarray(g, dtype=np.int32).reshape(-1),
+                                 np.ascontiguousarray(g0, dtype=np.int32).reshape(-1), _a(gd, 12 * n ** 3),
+                                 dv.reshape(-1), tv.reshape(-1), float(leff), float(b), int(v), rs, re)
+    return rs, re
 
 
 def mr_leff_next(leff, E, xi):

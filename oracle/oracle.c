@@ -597,41 +597,51 @@ void orc_mr_grain_vectors(int G, const double *quat, double *dv, double *tv) {
     }
 }
 
-/* Eq. GNDEvolution with the differences of reading R6: rs = rho_dot_GNDs = -(grad gdot . t)/b,
- * re = rho_dot_GNDet = (grad gdot . d)/b, fields 12 x N^3, gd the shear-rate field 12 x N^3. */
+/* Eq. GNDEvolution with the differences of reading R6 at voxel v: rs = rho_dot_GNDs = -(grad gdot . t)/b,
+ * re = rho_dot_GNDet = (grad gdot . d)/b of its 12 systems, gd the shear-rate field 12 x N^3 (only v and its
+ * six face neighbours are read). */
+void orc_mr_gnd_rates_voxel(int n, const int32_t *g, const int32_t *g0, const double *gd, const double *dv,
+                            const double *tv, double leff, double b, long v, double rs[12], double re[12]) {
+    const long N3 = (long)n * n * n;
+    const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
+    long np[3], nm[3];
+    np[0] = ((x + 1) % n) + (long)n * (y + (long)n * z);
+    nm[0] = ((x + n - 1) % n) + (long)n * (y + (long)n * z);
+    np[1] = x + (long)n * (((y + 1) % n) + (long)n * z);
+    nm[1] = x + (long)n * (((y + n - 1) % n) + (long)n * z);
+    np[2] = x + (long)n * (y + (long)n * ((z + 1) % n));
+    nm[2] = x + (long)n * (y + (long)n * ((z + n - 1) % n));
+    int sp[3], sm[3];
+    for (int i = 0; i < 3; ++i) {
+        sp[i] = g[np[i]] == g[v] && g0[np[i]] == g0[v];
+        sm[i] = g[nm[i]] == g[v] && g0[nm[i]] == g0[v];
+    }
+    const double *D = dv + 36 * (long)g0[v], *T = tv + 36 * (long)g0[v];
+    for (int a = 0; a < 12; ++a) {
+        const double *f = gd + a * N3;
+        double grad[3];
+        for (int i = 0; i < 3; ++i) {
+            if (sp[i] && sm[i]) grad[i] = (f[np[i]] - f[nm[i]]) / (2.0 * leff);
+            else if (sp[i]) grad[i] = (f[np[i]] - f[v]) / leff;
+            else if (sm[i]) grad[i] = (f[v] - f[nm[i]]) / leff;
+            else grad[i] = 0.0;
+        }
+        double gt = 0.0, gdd = 0.0;
+        for (int i = 0; i < 3; ++i) { gt += grad[i] * T[3 * a + i]; gdd += grad[i] * D[3 * a + i]; }
+        rs[a] = -gt / b;
+        re[a] = gdd / b;
+    }
+}
+
+/* The same over the whole grid: rs, re fields 12 x N^3. */
 void orc_mr_gnd_rates(int n, const int32_t *g, const int32_t *g0, const double *gd, const double *dv,
                       const double *tv, double leff, double b, double *rs, double *re) {
     const long N3 = (long)n * n * n;
 #pragma omp parallel for schedule(static)
     for (long v = 0; v < N3; ++v) {
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((long)n * n));
-        long np[3], nm[3];
-        np[0] = ((x + 1) % n) + (long)n * (y + (long)n * z);
-        nm[0] = ((x + n - 1) % n) + (long)n * (y + (long)n * z);
-        np[1] = x + (long)n * (((y + 1) % n) + (long)n * z);
-        nm[1] = x + (long)n * (((y + n - 1) % n) + (long)n * z);
-        np[2] = x + (long)n * (y + (long)n * ((z + 1) % n));
-        nm[2] = x + (long)n * (y + (long)n * ((z + n - 1) % n));
-        int sp[3], sm[3];
-        for (int i = 0; i < 3; ++i) {
-            sp[i] = g[np[i]] == g[v] && g0[np[i]] == g0[v];
-            sm[i] = g[nm[i]] == g[v] && g0[nm[i]] == g0[v];
-        }
-        const double *D = dv + 36 * (long)g0[v], *T = tv + 36 * (long)g0[v];
-        for (int a = 0; a < 12; ++a) {
-            const double *f = gd + a * N3;
-            double grad[3];
-            for (int i = 0; i < 3; ++i) {
-                if (sp[i] && sm[i]) grad[i] = (f[np[i]] - f[nm[i]]) / (2.0 * leff);
-                else if (sp[i]) grad[i] = (f[np[i]] - f[v]) / leff;
-                else if (sm[i]) grad[i] = (f[v] - f[nm[i]]) / leff;
-                else grad[i] = 0.0;
-            }
-            double gt = 0.0, gdd = 0.0;
-            for (int i = 0; i < 3; ++i) { gt += grad[i] * T[3 * a + i]; gdd += grad[i] * D[3 * a + i]; }
-            rs[a * N3 + v] = -gt / b;
-            re[a * N3 + v] = gdd / b;
-        }
+        double r1[12], r2[12];
+        orc_mr_gnd_rates_voxel(n, g, g0, gd, dv, tv, leff, b, v, r1, r2);
+        for (int a = 0; a < 12; ++a) { rs[a * N3 + v] = r1[a]; re[a * N3 + v] = r2[a]; }
     }
 }
 

@@ -99,6 +99,8 @@ double orc_vm_strain(const double e[6]);
 void orc_mr_grain_vectors(int G, const double *quat, double *dv, double *tv);
 void orc_mr_gnd_rates(int n, const int32_t *g, const int32_t *g0, const double *gd, const double *dv,
                       const double *tv, double leff, double b, double *rs, double *re);
+void orc_mr_gnd_rates_voxel(int n, const int32_t *g, const int32_t *g0, const double *gd, const double *dv,
+                            const double *tv, double leff, double b, long v, double rs[12], double re[12]);
 double orc_mr_leff_next(double leff, const double E[6], double xi);
 int orc_newton_mr(const orc_params *p, const double *S, const double *M, const double eps_tr[6],
                   const double tp[12], const double tcut[12], const double A[12], double tref, double dt,

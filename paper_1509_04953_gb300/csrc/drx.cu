@@ -181,13 +181,15 @@ __global__ void __launch_bounds__(kNB) k_nucl_apply(int n, int r, int K, const u
         gpf[pw] = id;
     }
     g[v] = id;
-    double kk = 0.0;
-    for (int a = 0; a < 12; ++a) {
-        const T ra = (T)(s_soften * (double)rho[a * N3 + v]);
-        rho[a * N3 + v] = ra;
-        kk += (double)ra;
+    if (rho != nullptr) {   // nullptr: the caller softens (the Ma-Roters law's GND densities)
+        double kk = 0.0;
+        for (int a = 0; a < 12; ++a) {
+            const T ra = (T)(s_soften * (double)rho[a * N3 + v]);
+            rho[a * N3 + v] = ra;
+            kk += (double)ra;
+        }
+        k[v] = kk;
     }
-    k[v] = kk;
     const int d = draws[v] + 1;
     draws[v] = d;
     kappa[v] = weibull_inv(uniform01(seed, (uint64_t)v, (uint64_t)d), kc_new, q);

@@ -64,6 +64,13 @@ struct evp_handle {
     cudaEvent_t pool[2 * kMaxPend];
     int npool;
     void *ctl;   // device fixed-point control block (FpCtl)
+    // Ma-Roters law (cfg.law == EVP_LAW_MR): rho holds rho_SSD; signed GND components gs, ge and the accumulated
+    // rho_GND (12 x N3 each); frozen tau_pass and 1/tau_cut (12 x N3 each, tauc = min tau_pass); shear rates
+    // and (sigma_vm, gdot_vm) of the last increment; sample-frame d and t per grain; constants; l_eff
+    int mr;
+    void *gs, *ge, *gnd, *tp, *itc, *gdm, *aux, *vec;
+    MRConst mrc;
+    double leff;
     char err[512];
     ~evp_handle() {
         std::free(adj_dE33); std::free(adj_dt); std::free(adj_E); std::free(adj_dEp); std::free(adj_hp);
@@ -161,6 +168,9 @@ int check_cfg(const evp_config *c, char *why, size_t wl) {
         return snprintf(why, wl, "al_scale must be >= 1"), EVP_ERR_ARG;
     if (!(c->newton_adapt >= 0.0)) return snprintf(why, wl, "newton_adapt must be >= 0"), EVP_ERR_ARG;
     if (c->pf_refine < 0 || c->pf_refine > 2) return snprintf(why, wl, "pf_refine must be 0, 1 or 2"), EVP_ERR_ARG;
+    if (c->law != EVP_LAW_POWER && c->law != EVP_LAW_MR) return snprintf(why, wl, "unknown law %d", c->law), EVP_ERR_ARG;
+    if (c->law == EVP_LAW_MR && c->newton_mode == EVP_NEWTON_F32_TANGENT)
+        return snprintf(why, wl, "EVP_NEWTON_F32_TANGENT covers the power law only"), EVP_ERR_ARG;
     if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE &&
         !(c->newton_mode == EVP_NEWTON_F32_TANGENT && c->precision == EVP_FP64))
         return snprintf(why, wl, "newton_mode %d is not available for precision %d", c->newton_mode, c->precision),
@@ -208,7 +218,14 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *count = take(sizeof(int32_t) * 4);
     const long words = (max_ids + 31) / 32;
     char *bitmap = take(sizeof(uint32_t) * words);
+    const bool mr = c->law == EVP_LAW_MR;
+    char *gnd3 = take(mr ? 36 * N3 * T : 0);   // rho_GNDs, rho_GNDet, rho_GND: one block (field EVP_F_GND)
+    char *gs = gnd3, *ge = mr ? gnd3 + 12 * N3 * T : nullptr, *gnd = mr ? gnd3 + 24 * N3 * T : nullptr;
+    char *tp = take(mr ? 12 * N3 * T : 0), *itc = take(mr ? 12 * N3 * T : 0), *gdm = take(mr ? 12 * N3 * T : 0);
+    char *aux = take(mr ? 2 * N3 * T : 0), *vec = take(mr ? 72 * (size_t)G * T : 0);
     if (h) {
+        h->mr = mr ? 1 : 0;
+        h->gs = gs; h->ge = ge; h->gnd = gnd; h->tp = tp; h->itc = itc; h->gdm = gdm; h->aux = aux; h->vec = vec;
         h->sig = sig; h->sigk = sigk; h->epse = epse; h->epst = epst; h->epsp = epsp; h->deps = deps;
         h->rho = rho; h->tauc = tauc; h->eta = eta; h->eta2 = eta2; h->spec = spec; h->Stab = Stab; h->Mtab = Mtab;
         h->fac = fac;
@@ -333,6 +350,7 @@ size_t field_bytes(const evp_handle *h, uint32_t bit) {
         case EVP_F_IDS: return K * (size_t)h->N3pf * 4;
         case EVP_F_ETA: return K * (size_t)h->N3pf * T;
         case EVP_F_GRAIN_PF: return (size_t)h->N3pf * 4;
+        case EVP_F_GND: return h->mr ? 36 * N3 * T : 0;
         default: return 0;
     }
 }
@@ -352,10 +370,98 @@ void *field_ptr(evp_handle *h, uint32_t bit) {
         case EVP_F_IDS: return h->ids;
         case EVP_F_ETA: return h->eta;
         case EVP_F_GRAIN_PF: return h->gpf;
+        case EVP_F_GND: return h->gs;
         default: return nullptr;
     }
 }
 
+
+// ---- Ma-Roters law: host-built constants and thin launch wrappers ----
+constexpr double kBoltzmann = 1.380649e-23;   // J/K (exact SI value)
+
+// |cos| / |sin| tables of the slip geometry (crystal frame; the angles do not depend on the orientation),
+// the scalar groups of the law, and the per-grain sample-frame d and t (72 words per grain).
+template <typename T> void mr_setup(evp_handle *h, const evp_params *p, const double *quat, T *vec) {
+    MRConst &c = h->mrc;
+    double nn[12][3], dd[12][3], tt[12][3];
+    for (int pl = 0; pl < 4; ++pl)
+        for (int d = 0; d < 3; ++d)
+            for (int q = 0; q < 3; ++q) {
+                nn[3 * pl + d][q] = kN4[pl][q] / std::sqrt(3.0);
+                dd[3 * pl + d][q] = kD4[pl][d][q] / std::sqrt(2.0);
+            }
+    for (int a = 0; a < 12; ++a) {
+        tt[a][0] = nn[a][1] * dd[a][2] - nn[a][2] * dd[a][1];
+        tt[a][1] = nn[a][2] * dd[a][0] - nn[a][0] * dd[a][2];
+        tt[a][2] = nn[a][0] * dd[a][1] - nn[a][1] * dd[a][0];
+    }
+    for (int a = 0; a < 12; ++a)
+        for (int b = 0; b < 12; ++b) {
+            const double ct = std::fabs(nn[a][0] * tt[b][0] + nn[a][1] * tt[b][1] + nn[a][2] * tt[b][2]);
+            const double cd = std::fabs(nn[a][0] * dd[b][0] + nn[a][1] * dd[b][1] + nn[a][2] * dd[b][2]);
+            const double v4[4] = {ct, cd, std::sqrt(std::fmax(0.0, 1.0 - ct * ct)), std::sqrt(std::fmax(0.0, 1.0 - cd * cd))};
+            for (int k = 0; k < 4; ++k) {
+                c.tab[k * 144 + 12 * a + b] = v4[k];
+                c.tabf[k * 144 + 12 * a + b] = (float)v4[k];
+            }
+        }
+    const double kT = kBoltzmann * p->T, mu = voigt_mu(p), muPa = 1e6 * mu, b = p->b;
+    MRScal<double> &d = c.d;
+    d.tp_c = p->c1 * mu * b;
+    d.tcut_c = 1e-6 * p->Q_slip / (p->c2 * p->c3 * b * b);
+    d.rm_c = 2.0 * kT / (p->c1 * p->c2 * p->c3 * muPa * b * b * b);
+    d.dd_c = std::sqrt(3.0) * mu * b / (16.0 * M_PI * (1.0 - p->poisson));
+    d.climb_c = p->c7 * std::exp(-p->Q_bulk / kT) * 1e6 / kT;
+    d.c4 = p->c4; d.c5 = p->c5; d.c6 = p->c6; d.c8 = p->c8;
+    d.inv_b = 1.0 / b;
+    d.dt = 1.0;
+    d.soften = p->s_soften;
+    // prefactor A = 2 k_B T nu_D sqrt(rho_P) exp(-Q_slip/k_B T) / (c1 c3 mu b^2) per unit tau_pass = tp_c sqrt(rho_P)
+    h->mc.mr_ga = 2.0 * kT * p->nu_D * std::exp(-p->Q_slip / kT) / (p->c1 * p->c3 * muPa * b * b) / d.tp_c;
+    for (int g = 0; g < h->G; ++g) {
+        const double *q = quat + 4 * g;
+        const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        const double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                                {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                                {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+        for (int a = 0; a < 12; ++a)
+            for (int i = 0; i < 3; ++i) {
+                vec[72 * (size_t)g + 3 * a + i] = (T)(R[i][0] * dd[a][0] + R[i][1] * dd[a][1] + R[i][2] * dd[a][2]);
+                vec[72 * (size_t)g + 36 + 3 * a + i] = (T)(R[i][0] * tt[a][0] + R[i][1] * tt[a][1] + R[i][2] * tt[a][2]);
+            }
+    }
+}
+void mr_set_fp32(MRConst &c) {
+    const MRScal<double> &d = c.d;
+    c.f = MRScal<float>{(float)d.tp_c, (float)d.tcut_c, (float)d.rm_c, (float)d.dd_c, (float)d.climb_c, (float)d.c4,
+                        (float)d.c5, (float)d.c6, (float)d.c8, (float)d.inv_b, (float)d.dt, (float)d.soften};
+}
+
+cudaError_t mr_refresh_k(evp_handle *h) {
+    if (h->dbl)
+        return mr_soften<double>(h->N3, 0, nullptr, nullptr, 0, (const double *)h->rho, (double *)h->gs, (double *)h->ge,
+                                 (double *)h->gnd, h->k, h->mrc, h->st);
+    return mr_soften<float>(h->N3, 0, nullptr, nullptr, 0, (const float *)h->rho, (float *)h->gs, (float *)h->ge,
+                            (float *)h->gnd, h->k, h->mrc, h->st);
+}
+cudaError_t mr_soften_sel(evp_handle *h, int mode, int lo) {
+    if (h->dbl)
+        return mr_soften<double>(h->N3, mode, h->gprev, h->g, lo, (const double *)h->rho, (double *)h->gs,
+                                 (double *)h->ge, (double *)h->gnd, h->k, h->mrc, h->st);
+    return mr_soften<float>(h->N3, mode, h->gprev, h->g, lo, (const float *)h->rho, (float *)h->gs, (float *)h->ge,
+                            (float *)h->gnd, h->k, h->mrc, h->st);
+}
+template <typename TA> MRPtr<TA> mr_ptr(const evp_handle *h) {
+    return h->mr ? MRPtr<TA>{(const TA *)h->tp, (const TA *)h->itc} : MRPtr<TA>{nullptr, nullptr};
+}
+// von Mises equivalent of a Mandel strain, sqrt(2/3 e:e) of its deviator (Eq. L0evolution's eps_vm)
+double vm_strain(const double e[6]) {
+    const double m = (e[0] + e[1] + e[2]) / 3.0;
+    const double ee = (e[0] - m) * (e[0] - m) + (e[1] - m) * (e[1] - m) + (e[2] - m) * (e[2] - m) + e[3] * e[3] +
+                      e[4] * e[4] + e[5] * e[5];
+    return std::sqrt(ee / 1.5);
+}
 
 // Augmented-Lagrangian iterations of one increment (after the predictor): see k_al_local.
 // Returns a status; fills the iteration count, residuals, mean stress and the macro strain increment.
@@ -383,7 +489,7 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
           CK(al_local<TA>(N3, (const TA *)h->epst, (const TA *)h->epse, (const TA *)h->tauc, h->g0, (TA *)h->sigk,
                           (TA *)h->lam, (TA *)h->pal, (const TA *)h->Stab, (const TA *)h->Sal, (const TA *)h->Mtab, mc,
                           lam0, mu0, h->cfg.newton_tol, h->cfg.newton_max, solve64, init, h->flags, h->partials, fac,
-                          refresh, h->st)); }
+                          refresh, h->st, mr_ptr<TA>(h))); }
         { PROF(6, 1); CK(reduce_partials(h->partials, nb, 14, h->scal + 24, h->st)); }
         CK(cudaMemcpyAsync(hs, h->scal + 24, sizeof hs, cudaMemcpyDeviceToHost, h->st));
         CK(cudaMemcpyAsync(hf, h->flags, sizeof hf, cudaMemcpyDeviceToHost, h->st));
@@ -514,6 +620,21 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     h->pc.G = h->G;
     h->pc.K = h->K;
     h->pc.set_fp32();
+    h->leff = p->dx;   // Eq. L0evolution starts from the grid size l0
+    if (h->mr) {
+        const size_t vb = 72 * (size_t)h->G * h->tsz;
+        void *hv = std::malloc(vb);
+        if (!hv) return fail(h, EVP_ERR_OOM, "host allocation");
+        if (h->dbl) mr_setup<double>(h, p, quat, (double *)hv);
+        else mr_setup<float>(h, p, quat, (float *)hv);
+        mr_set_fp32(h->mrc);
+        h->mc.set_fp32();
+        cudaError_t ea = cudaMemcpyAsync(h->vec, hv, vb, cudaMemcpyHostToDevice, h->st);
+        cudaError_t eb = cudaStreamSynchronize(h->st);
+        std::free(hv);
+        CK(ea);
+        CK(eb);
+    }
     // tables
     {
         const size_t G = (size_t)h->G;
@@ -575,6 +696,10 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
     else
         CK(drx_init<float>(h->N3, h->g0, (float *)h->rho, h->k, h->kappa, h->g, h->draws, nullptr, nullptr, h->K,
                            p->rho0, p->kc, p->q, seed, h->st));
+    if (h->mr) {   // rho = rho_SSD(0); no GND yet; k = sum of mobile, SSD and GND densities
+        CK(cudaMemsetAsync(h->gs, 0, 36 * (size_t)h->N3 * h->tsz, h->st));
+        CK(mr_refresh_k(h));
+    }
     CK(pf_init(h->n, h->r, h->K, h->g0, h->ids, h->eta, h->ids2, h->eta2, h->dbl, h->gpf, h->st));
     if (h->r == 2) CK(pf_interp(h->n, h->k, h->kpf, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -661,6 +786,15 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
             CK(predictor<float>(N3, (float *)h->epse, (float *)h->deps, (float *)h->rho, (float *)h->epst,
                                 (float *)h->tauc, mc, r, dE, use_field, h->st));
     }
+    if (h->mr) {   // frozen Ma-Roters hardening of the increment; tauc becomes the stopping scale
+        PROF(7, 1);
+        if (h->dbl)
+            CK(mr_harden<double>(N3, (const double *)h->rho, (const double *)h->gs, (const double *)h->ge,
+                                 (double *)h->tp, (double *)h->itc, (double *)h->tauc, h->mrc, h->st));
+        else
+            CK(mr_harden<float>(N3, (const float *)h->rho, (const float *)h->gs, (const float *)h->ge, (float *)h->tp,
+                                (float *)h->itc, (float *)h->tauc, h->mrc, h->st));
+    }
     // mixed-BC correction: (C0_uu)^-1 on u = {11, 22, 23, 13, 12}
     const double a = lam0 + 2.0 * mu0, b = lam0, det = a * a - b * b;
     const int solve64 = h->prec != EVP_MIXED_FAST;
@@ -712,11 +846,11 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                                       (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
                                                       h->cfg.newton_max, 1, first, h->flags, h->wlist, h->nsm, h->st,
-                                                      skip, tl64));
+                                                      skip, tl64, mr_ptr<double>(h)));
                     else
                         CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                                 (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
-                                                h->flags, h->st, skip, tl64)); }
+                                                h->flags, h->st, skip, tl64, mr_ptr<double>(h))); }
                   { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
@@ -728,11 +862,11 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         CK(newton_chord_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                                      (float *)h->Stab, (float *)h->Mtab, h->fac, mc, ntol,
                                                      h->cfg.newton_max, solve64, first, h->flags, h->wlist, h->nsm,
-                                                     h->st, skip, tl32));
+                                                     h->st, skip, tl32, mr_ptr<float>(h)));
                     else
                         CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                                (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,
-                                               h->flags, h->st, skip, tl32)); }
+                                               h->flags, h->st, skip, tl32, mr_ptr<float>(h))); }
                   { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
@@ -798,7 +932,28 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         }
     }
     if (status < 0) return status;
-    { PROF(8, 1);
+    if (h->mr) {
+        PROF(8, 3);
+        MRConst &c = h->mrc;
+        c.d.dt = dt;
+        c.f.dt = (float)dt;
+        if (h->dbl) {
+            CK(mr_rates<double>(N3, (const double *)h->sigk, (const double *)h->tp, (const double *)h->itc, h->g0,
+                                (const double *)h->Mtab, (const double *)h->epst, (double *)h->epse, (double *)h->epsp,
+                                (double *)h->deps, (double *)h->gdm, (double *)h->aux, mc, h->st));
+            CK(mr_update<double>(n, h->g, h->g0, (const double *)h->gdm, (const double *)h->aux, (const double *)h->sigk,
+                                 (const double *)h->Mtab, (const double *)h->vec, (double *)h->rho, (double *)h->gs,
+                                 (double *)h->ge, (double *)h->gnd, h->k, c, h->leff, h->st));
+        } else {
+            CK(mr_rates<float>(N3, (const float *)h->sigk, (const float *)h->tp, (const float *)h->itc, h->g0,
+                               (const float *)h->Mtab, (const float *)h->epst, (float *)h->epse, (float *)h->epsp,
+                               (float *)h->deps, (float *)h->gdm, (float *)h->aux, mc, h->st));
+            CK(mr_update<float>(n, h->g, h->g0, (const float *)h->gdm, (const float *)h->aux, (const float *)h->sigk,
+                                (const float *)h->Mtab, (const float *)h->vec, (float *)h->rho, (float *)h->gs,
+                                (float *)h->ge, (float *)h->gnd, h->k, c, h->leff, h->st));
+        }
+    } else {
+    PROF(8, 1);
     if (h->dbl)
         CK(state_update<double>(N3, (double *)h->sigk, (double *)h->tauc, h->g0, (double *)h->Mtab, (double *)h->epst,
                                 (double *)h->epse, (double *)h->epsp, (double *)h->deps, (double *)h->rho, h->k, mc,
@@ -814,6 +969,8 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         h->E[i] += dE[i];
         h->dE_prev[i] = dE[i];
     }
+    // Eq. L0evolution after the increment's GND rates, with the von Mises strain of the macroscopic strain
+    if (h->mr) h->leff *= 1.0 + vm_strain(h->E) / h->p.xi;
     h->have_prev = 1;
     CK(cudaStreamSynchronize(h->st));
     if (h->prof) prof_collect(h);
@@ -824,15 +981,18 @@ int drx_nucleate(evp_handle *h, uint64_t step, int32_t *n_new) {
     (void)step;
     if (!h || !n_new) return fail(h, EVP_ERR_ARG, "NULL argument to drx_nucleate");
     const double kc_new = h->p.s_nucl * h->p.kc;
-    { PROF(9, 3);
+    { PROF(9, h->mr ? 4 : 3);
+    // the power law softens its single density family in the nucleation kernel; the Ma-Roters law softens the
+    // GND densities of the fresh nuclei (ids >= next_id) afterwards and keeps rho_SSD (Eq. UpdateGND)
     if (h->dbl)
-        CK(nucleate<double>(h->n, h->r, h->K, h->g, h->k, h->kappa, (double *)h->rho, h->draws, h->ids,
-                            (double *)h->eta, h->gpf, h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften,
-                            kc_new, h->p.q, h->seed, h->st));
+        CK(nucleate<double>(h->n, h->r, h->K, h->g, h->k, h->kappa, h->mr ? nullptr : (double *)h->rho, h->draws,
+                            h->ids, (double *)h->eta, h->gpf, h->blk_counts, h->blk_off, h->count, h->next_id,
+                            h->p.s_soften, kc_new, h->p.q, h->seed, h->st));
     else
-        CK(nucleate<float>(h->n, h->r, h->K, h->g, h->k, h->kappa, (float *)h->rho, h->draws, h->ids,
-                           (float *)h->eta, h->gpf, h->blk_counts, h->blk_off, h->count, h->next_id, h->p.s_soften,
-                           kc_new, h->p.q, h->seed, h->st));
+        CK(nucleate<float>(h->n, h->r, h->K, h->g, h->k, h->kappa, h->mr ? nullptr : (float *)h->rho, h->draws,
+                           h->ids, (float *)h->eta, h->gpf, h->blk_counts, h->blk_off, h->count, h->next_id,
+                           h->p.s_soften, kc_new, h->p.q, h->seed, h->st));
+    if (h->mr) CK(mr_soften_sel(h, 1, h->next_id));
     }
     int32_t c = 0;
     CK(cudaMemcpyAsync(&c, h->count, sizeof c, cudaMemcpyDeviceToHost, h->st));
@@ -868,7 +1028,8 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
         else CK(pf_restrict<float>(h->n, h->K, h->ids, (const float *)h->eta, h->g, h->st));
     }
     { PROF(11, 1);
-    if (h->dbl) CK(pf_soften<double>(N3, h->gprev, h->g, (double *)h->rho, h->k, h->G, h->p.s_soften, h->st));
+    if (h->mr) CK(mr_soften_sel(h, 2, h->G));
+    else if (h->dbl) CK(pf_soften<double>(N3, h->gprev, h->g, (double *)h->rho, h->k, h->G, h->p.s_soften, h->st));
     else CK(pf_soften<float>(N3, h->gprev, h->g, (float *)h->rho, h->k, h->G, h->p.s_soften, h->st));
     }
     if (h->r == 2) { PROF(11, 1); CK(pf_interp(h->n, h->k, h->kpf, h->st)); }   // softened densities
@@ -904,9 +1065,10 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
 
 int evp_fields_bytes(const evp_handle *h, uint32_t mask, size_t *bytes) {
     if (!h || !bytes) return EVP_ERR_ARG;
-    if (mask == 0 || (mask >> 14) != 0) return EVP_ERR_ARG;
+    if (mask == 0 || (mask >> 15) != 0) return EVP_ERR_ARG;
+    if ((mask & EVP_F_GND) && !h->mr) return EVP_ERR_ARG;   // GND densities exist under the Ma-Roters law only
     size_t tot = 0;
-    for (uint32_t bit = 1; bit <= EVP_F_GRAIN_PF; bit <<= 1)
+    for (uint32_t bit = 1; bit <= EVP_F_GND; bit <<= 1)
         if (mask & bit) tot += field_bytes(h, bit);
     *bytes = tot;
     return EVP_OK;
@@ -919,7 +1081,7 @@ int get_fields(evp_handle *h, uint32_t mask, void *dst, size_t bytes, int dst_is
     if (bytes != need) return fail(h, EVP_ERR_ARG, "get_fields: %zu bytes given, %zu expected", bytes, need);
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     size_t off = 0;
-    for (uint32_t bit = 1; bit <= EVP_F_GRAIN_PF; bit <<= 1) {
+    for (uint32_t bit = 1; bit <= EVP_F_GND; bit <<= 1) {
         if (!(mask & bit)) continue;
         const size_t fb = field_bytes(h, bit);
         const void *src = field_ptr(h, bit);
@@ -944,14 +1106,15 @@ int set_fields(evp_handle *h, uint32_t mask, const void *src, size_t bytes, int 
     if (bytes != need) return fail(h, EVP_ERR_ARG, "set_fields: %zu bytes given, %zu expected", bytes, need);
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     size_t off = 0;
-    for (uint32_t bit = 1; bit <= EVP_F_GRAIN_PF; bit <<= 1) {
+    for (uint32_t bit = 1; bit <= EVP_F_GND; bit <<= 1) {
         if (!(mask & bit)) continue;
         const size_t fb = field_bytes(h, bit);
         CK(cudaMemcpyAsync(field_ptr(h, bit), (const char *)src + off, fb, kind, h->st));
         off += fb;
     }
-    if (mask & EVP_F_RHO) {
-        if (h->dbl) CK(refresh_k<double>(h->N3, (double *)h->rho, h->k, h->st));
+    if (mask & (EVP_F_RHO | EVP_F_GND)) {
+        if (h->mr) CK(mr_refresh_k(h));
+        else if (h->dbl) CK(refresh_k<double>(h->N3, (double *)h->rho, h->k, h->st));
         else CK(refresh_k<float>(h->N3, (float *)h->rho, h->k, h->st));
         if (h->r == 2) CK(pf_interp(h->n, h->k, h->kpf, h->st));
     }
@@ -978,6 +1141,18 @@ int evp_set_scalars(evp_handle *h, const double *E6, const double *dE_prev6, int
     }
     h->have_prev = have_prev;
     h->next_id = next_id;
+    return EVP_OK;
+}
+
+int evp_get_leff(const evp_handle *h, double *leff) {
+    if (!h || !leff) return EVP_ERR_ARG;
+    *leff = h->leff;
+    return EVP_OK;
+}
+
+int evp_set_leff(evp_handle *h, double leff) {
+    if (!h || !(leff > 0.0) || !std::isfinite(leff)) return fail(h, EVP_ERR_ARG, "l_eff must be positive and finite");
+    h->leff = leff;
     return EVP_OK;
 }
 
@@ -1201,6 +1376,7 @@ int evp_adjoint_workspace_bytes(const evp_config *cfg, int n_increments, int che
 int evp_adjoint_begin(evp_handle *h, void *adj_ws, size_t bytes, int n_increments, int checkpoint_every) {
     if (!h || !adj_ws || n_increments < 1 || checkpoint_every < 1) return fail(h, EVP_ERR_ARG, "bad adjoint arguments");
     if (((uintptr_t)adj_ws & 255) != 0) return fail(h, EVP_ERR_ARG, "adjoint workspace must be 256-byte aligned");
+    if (h->mr) return fail(h, EVP_ERR_ARG, "the adjoint covers the power law with Kocks-Mecking hardening only");
     const AdjLayout L = adj_layout(&h->cfg, n_increments, checkpoint_every);
     if (bytes < L.total) return fail(h, EVP_ERR_OOM, "adjoint workspace has %zu bytes, needs %zu", bytes, L.total);
     std::free(h->adj_dE33); std::free(h->adj_dt); std::free(h->adj_E); std::free(h->adj_dEp); std::free(h->adj_hp);

@@ -10,8 +10,31 @@ struct MatConst {
     double gdot0, n, dt, tau0, alpha_mu_b, k1, k2;
     double lam0, mu0;       // reference medium (Voigt isotropic average)
     int n_int;              // n if it is a small positive integer (fast power), else 0
-    float gdot0_f, n_f, dt_f;   // FP32 copies for the FP32 path (no FP64 conversions in the kernels)
-    void set_fp32() { gdot0_f = (float)gdot0; n_f = (float)n; dt_f = (float)dt; }
+    double mr_ga;           // Ma-Roters flow rule: prefactor per unit passing stress, A = mr_ga tau_pass
+    float gdot0_f, n_f, dt_f, mr_ga_f;   // FP32 copies for the FP32 path (no FP64 conversions in the kernels)
+    void set_fp32() { gdot0_f = (float)gdot0; n_f = (float)n; dt_f = (float)dt; mr_ga_f = (float)mr_ga; }
+};
+
+// Ma-Roters law (Sec. 2.2): the frozen flow-rule data of every voxel, passing stress tau_pass and inverse
+// cutting stress 1/tau_cut per slip system (12 x N^3 each). tp == nullptr selects the power law.
+template <typename TA> struct MRPtr {
+    const TA *tp;
+    const TA *itc;
+};
+
+// Ma-Roters constants (built on the host in FP64; FP32 copies for the FP32 path). tab: |cos| and |sin| of the
+// angles between slip-plane normals and the sense vectors t = n x d (tables 0, 2) and the slip directions d
+// (tables 1, 3) of every pair of systems, [k * 144 + 12 a + b]. Scalars (stress MPa, lengths m):
+//   tau_pass = tp_c sqrt(rho_P), tau_cut = tcut_c sqrt(rho_F), rho_M = rm_c sqrt(rho_P rho_F),
+//   d_dipole = dd_c / |tau|, climb rate = climb_c sigma_vm gdot_vm^c8 rho^2.
+template <typename T> struct MRScal {
+    T tp_c, tcut_c, rm_c, dd_c, climb_c, c4, c5, c6, c8, inv_b, dt, soften;
+};
+struct MRConst {
+    double tab[576];
+    float tabf[576];
+    MRScal<double> d;
+    MRScal<float> f;
 };
 
 // ---- fft.cu ----
@@ -36,11 +59,12 @@ int fft_z_blocks(int n, int is_double);
 
 // ---- newton.cu ----
 // solve_fp64: 1 -> the 6x6 Newton system is solved in FP64 even when TA = float.
+// mrp (optional): the Ma-Roters flow data; tauc then holds the stopping scale tau_ref = min_a tau_pass^a.
 template <typename TA>
 cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                          const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
                          cudaStream_t s,
-                         const int *skip = nullptr, const TA *tol_dev = nullptr);
+                         const int *skip = nullptr, const TA *tol_dev = nullptr, MRPtr<TA> mrp = MRPtr<TA>{});
 // Jacobian-reuse variant: fac holds 21 factor words per voxel in TA (factorised in FP64 if solve_fp64).
 // Unless force_refresh, runs in two passes with the work list wl (N3 entries, count in flags[10]);
 // nsm = multiprocessors, for the grid of the second pass.
@@ -49,7 +73,7 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s,
                                const int *skip = nullptr,
-                               const TA *tol_dev = nullptr);
+                               const TA *tol_dev = nullptr, MRPtr<TA> mrp = MRPtr<TA>{});
 // FP64 residual / FP32 tangent Newton (FP64 path); Stabf / Mtabf are FP32 copies of the tables.
 cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
                             const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,
@@ -62,7 +86,7 @@ template <typename TA>
 cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
                      const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
                      int maxit, int solve_fp64, int init, int *flags, double *part, void *fac, int refresh,
-                     cudaStream_t s);
+                     cudaStream_t s, MRPtr<TA> mrp = MRPtr<TA>{});
 template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s);
@@ -70,6 +94,30 @@ template <typename TA>
 cudaError_t state_update(long N3, const TA *sig, const TA *tauc, const int32_t *g0, const TA *Mtab, TA *epst,
                          TA *epse, TA *epsp, TA *deps, TA *rho, double *k, MatConst mc, cudaStream_t s);
 template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const TA *epsp, TA *eps, cudaStream_t s);
+
+// ---- mr.cu (Ma-Roters law, Sec. 2.2) ----
+// Frozen hardening of an increment: projections of the densities, tau_pass, 1/tau_cut per system and
+// tref = min_a tau_pass^a (the local Newton's stopping scale).
+template <typename T>
+cudaError_t mr_harden(long N3, const T *ssd, const T *gs, const T *ge, T *tp, T *itc, T *tref, const MRConst &c,
+                      cudaStream_t s);
+// After convergence: eps_p / eps_e / strain increment as state_update, and the shear rates gd (12 x N^3) with
+// aux = (sigma_vm, gdot_vm) (2 x N^3) for the density update.
+template <typename T>
+cudaError_t mr_rates(long N3, const T *sig, const T *tp, const T *itc, const int32_t *g0, const T *Mtab, const T *epst,
+                     T *epse, T *epsp, T *deps, T *gd, T *aux, MatConst mc, cudaStream_t s);
+// Density update: SSD (Eq. SSDEvolution), GND from the shear-rate gradients (Eq. GNDEvolution) with spacing
+// leff, and k (Eq. TotDislocationDensity). vec: per grain the sample-frame d then t of the 12 systems (72 T).
+template <typename T>
+cudaError_t mr_update(int n, const int32_t *g, const int32_t *g0, const T *gd, const T *aux, const T *sig,
+                      const T *Mtab, const T *vec, T *ssd, T *gs, T *ge, T *gnd, double *k, const MRConst &c,
+                      double leff, cudaStream_t s);
+// Softening (Eq. UpdateGND): GND densities of the selected voxels times c.soften, then k. mode 1: voxels with
+// g >= lo (fresh nuclei); mode 2: voxels whose grain went from deformed (gprev < lo) to recrystallised
+// (g >= lo); mode 0: none softened, k recomputed everywhere.
+template <typename T>
+cudaError_t mr_soften(long N3, int mode, const int32_t *gprev, const int32_t *g, int lo, const T *ssd, T *gs, T *ge,
+                      T *gnd, double *k, const MRConst &c, cudaStream_t s);
 
 // ---- adjoint.cu ----
 int adj_blocks(long N3);

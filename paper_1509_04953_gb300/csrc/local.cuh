@@ -1,5 +1,6 @@
 // Per-voxel constitutive routines shared by the forward Newton and the adjoint kernels
-// (Sec. 2.1 Eqs. HookeLaw / PlasticRate with the power-law flow rule).
+// (Sec. 2.1 Eqs. HookeLaw / PlasticRate with the power-law flow rule, and with the Ma-Roters flow rule of
+// Sec. 2.2 Eq. FlowRule).
 #pragma once
 #include <cmath>
 
@@ -176,6 +177,90 @@ __device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__
     e.phi = phi;
 }
 
+
+// ---- Ma-Roters flow rule (Sec. 2.2, Eq. FlowRule) ----
+// gdot = A sinh((|tau| - tau_pass) / tau_cut) sign(tau) above the passing stress, A = ga tau_pass; its
+// derivative A cosh(.) / tau_cut and the convex potential A tau_cut (cosh(.) - 1) (zero below). With
+// u = expm1(x) and w = 1/(1+u) = exp(-x): sinh x = u (1+w)/2 and cosh x - 1 = u (1-w)/2, free of
+// cancellation for small x; an overflowing x gives infinities that the line search rejects.
+template <typename TA> struct FlowMR {
+    const TA *__restrict__ tp;    // tau_pass, 12 x N3
+    const TA *__restrict__ itc;   // 1 / tau_cut, 12 x N3
+    long N3, v;
+    TA tref;                      // stopping scale: min_a tau_pass^a
+};
+template <typename TA> __device__ __forceinline__ TA flow_ref(TA tauc) { return tauc; }
+template <typename TA> __device__ __forceinline__ TA flow_ref(const FlowMR<TA> &f) { return f.tref; }
+__device__ __forceinline__ float dexpm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double dexpm1(double x) { return expm1(x); }
+template <typename TA> __device__ __forceinline__ TA mr_ga(const MatConst &mc) {
+    if constexpr (sizeof(TA) == 4) return mc.mr_ga_f;
+    else return mc.mr_ga;
+}
+template <typename TA>
+__device__ __forceinline__ void mr_flow(TA tau, TA tp, TA itc, TA ga, TA &gd, TA &slope, TA &psi) {
+    const TA x = (fabs(tau) - tp) * itc;
+    if (x > (TA)0) {
+        const TA u = dexpm1(x), w = (TA)1 / (u + (TA)1), A = ga * tp;
+        const TA sh = (TA)0.5 * u * ((TA)1 + w), chm1 = (TA)0.5 * u * ((TA)1 - w);
+        gd = tau < (TA)0 ? -A * sh : A * sh;
+        slope = A * ((TA)1 + chm1) * itc;
+        psi = A * chm1 / itc;
+    } else {
+        gd = (TA)0; slope = (TA)0; psi = (TA)0;
+    }
+}
+template <typename TA> __device__ __forceinline__ void mr_sys(const FlowMR<TA> &f, int a, TA &tp, TA &itc) {
+    tp = __ldg(f.tp + (long)a * f.N3 + f.v);
+    itc = __ldg(f.itc + (long)a * f.N3 + f.v);
+}
+
+template <typename TA>
+__device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], const FlowMR<TA> &f,
+                                         TA, const TA sg[6], const MatConst &mc, Eval<TA> &e) {
+    TA dt, g0, nn;
+    flow_consts(mc, dt, g0, nn);
+    const TA ga = mr_ga<TA>(mc);
+    TA phi = (TA)0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        TA acc = (TA)0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += Sp[i >= j ? pk(i, j) : pk(j, i)] * sg[j];
+        e.r[i] = acc - etr[i];
+        phi += sg[i] * ((TA)0.5 * acc - etr[i]);
+    }
+#pragma unroll
+    for (int q = 0; q < 21; ++q) e.K[q] = Sp[q];
+#pragma unroll 1
+    for (int p = 0; p < 6; ++p) {
+      TA mm[12];
+      load_slip_pair(M, p, mm);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const TA *m = mm + 6 * h;
+        TA tau = (TA)0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
+        TA tp, itc, gd, slope, psi;
+        mr_sys(f, 2 * p + h, tp, itc);
+        mr_flow(tau, tp, itc, ga, gd, slope, psi);
+        TA sm[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            e.r[i] += dt * gd * m[i];
+            sm[i] = dt * slope * m[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) e.K[pk(i, j)] += sm[i] * m[j];
+        phi += dt * psi;
+      }
+    }
+    e.phi = phi;
+}
+
 // Reciprocal: FP32 division for float; for double an FP32 seed refined by two Newton steps
 // r <- r (2 - x r) (each doubles the correct bits: 24 -> 48 -> full precision).
 __device__ __forceinline__ float rcp_s(float x) { return 1.0f / x; }
@@ -272,6 +357,44 @@ __device__ __forceinline__ void evaluate_r(const TA Sp[21], const TA *__restrict
 #pragma unroll
             for (int i = 0; i < 6; ++i) e.r[i] += dg * m[i];
             phi += cphi * p10 * ax;
+        }
+    }
+    e.phi = phi;
+}
+
+
+template <typename TA, int UNROLL = 1>
+__device__ __forceinline__ void evaluate_r(const TA Sp[21], const TA *__restrict__ M, const TA etr[6],
+                                           const FlowMR<TA> &f, TA, const TA sg[6], const MatConst &mc, EvalR<TA> &e) {
+    TA dt, g0, nn;
+    flow_consts(mc, dt, g0, nn);
+    const TA ga = mr_ga<TA>(mc);
+    TA phi = (TA)0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        TA acc = (TA)0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc += Sp[i >= j ? pk(i, j) : pk(j, i)] * sg[j];
+        e.r[i] = acc - etr[i];
+        phi += sg[i] * ((TA)0.5 * acc - etr[i]);
+    }
+#pragma unroll UNROLL
+    for (int p = 0; p < 6; ++p) {
+        TA mm[12];
+        load_slip_pair(M, p, mm);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const TA *m = mm + 6 * h;
+            TA tau = (TA)0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) tau += m[i] * sg[i];
+            TA tp, itc, gd, slope, psi;
+            mr_sys(f, 2 * p + h, tp, itc);
+            mr_flow(tau, tp, itc, ga, gd, slope, psi);
+            const TA dg = dt * gd;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) e.r[i] += dg * m[i];
+            phi += dt * psi;
         }
     }
     e.phi = phi;

@@ -9,6 +9,7 @@
 // for Armijo backtracking. eps_tr = eps^{t+dt} - eps_p^t is carried directly (the "trial" elastic
 // strain), which keeps FP32 fields accurate when the total strain is large.
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -55,12 +56,14 @@ __device__ __forceinline__ void block_solve_stats(int fail, int maxit, int it, i
 }
 
 // Damped Newton on one voxel. Returns the iteration count (> 0) or minus it on failure.
-template <typename TA, typename TS>
-__device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA sg[6],
+// H: the power law's tau_c (TA) or the Ma-Roters flow data (FlowMR<TA>, Sec. 2.2).
+template <typename TA, typename TS, typename H>
+__device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], const H &hf, TA sg[6],
                             const MatConst &mc, TA tol, int maxit, TA ls_free, int &nevals) {
+    const TA tauc = flow_ref(hf);
     const TA inv_tc = drcp(tauc);
     Eval<TA> e;
-    evaluate(Sp, M, etr, tauc, inv_tc, sg, mc, e);
+    evaluate(Sp, M, etr, hf, inv_tc, sg, mc, e);
     nevals = 1;
     for (int it = 1; it <= maxit; ++it) {
         TA d[6];
@@ -87,7 +90,7 @@ __device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA 
         for (int h = 0; h < 60; ++h) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) st[i] = sg[i] - s * d[i];
-            evaluate(Sp, M, etr, tauc, inv_tc, st, mc, e);
+            evaluate(Sp, M, etr, hf, inv_tc, st, mc, e);
             ++nevals;
             if (e.phi <= phi0 - (TA)1e-4 * s * rd || s * dn <= ls_free * scale) {
                 ok = true;
@@ -103,12 +106,12 @@ __device__ int newton_voxel(const TA Sp[21], const TA *__restrict__ M, const TA 
     return -maxit;
 }
 
-template <typename TA, typename TS>
+template <typename TA, typename TS, bool MR = false>
 __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc,
                                                     const int32_t *__restrict__ g0, TA *__restrict__ sig,
                                                     const TA *__restrict__ Stab, const TA *__restrict__ Mtab, MatConst mc,
                                                     TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int *__restrict__ skip,
-    const TA *__restrict__ tol_dev) {
+    const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,7 +127,11 @@ __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restri
             etr[c] = epst[c * N3 + v];
             sg[c] = sig[c * N3 + v];
         }
-        r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
+        if constexpr (MR)
+            r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]}, sg, mc,
+                                     tol, maxit, ls_free, nev);
+        else
+            r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
 #pragma unroll
         for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
     }
@@ -230,13 +237,14 @@ __global__ void __launch_bounds__(kThreads) k_newton_df(long N3, const double *_
 // to cancellation once a few slip systems are far into the power law, while FP64 factors rounded to
 // FP32 afterwards are a componentwise perturbation and keep the Newton direction within about 1e-4
 // relative even there, so the reused step runs on the FP32 pipe and reads half the bytes.
-template <typename TA, typename TS, typename TF>
-__device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], TA tauc, TA sg[6],
+template <typename TA, typename TS, typename TF, typename H>
+__device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA etr[6], const H &hf, TA sg[6],
                            const MatConst &mc, TA tol, int maxit, TA ls_free, TS F[21], bool refresh, int &nevals,
                            int &nref) {
+    const TA tauc = flow_ref(hf);
     const TA inv_tc = drcp(tauc);
     EvalR<TA> e;
-    evaluate_r(Sp, M, etr, tauc, inv_tc, sg, mc, e);
+    evaluate_r(Sp, M, etr, hf, inv_tc, sg, mc, e);
     nevals = 1;
     nref = 0;
     TA prev_step = (TA)-1;
@@ -244,7 +252,7 @@ __device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA e
     for (int it = 1; it <= maxit; ++it) {
         if (refresh) {
             Eval<TA> full;
-            evaluate(Sp, M, etr, tauc, inv_tc, sg, mc, full);
+            evaluate(Sp, M, etr, hf, inv_tc, sg, mc, full);
             ++nevals;
             TF Ff[21];
             if (!ldl_factor<TF, TA>(full.K, Ff)) return -it;
@@ -280,7 +288,7 @@ __device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA e
         for (int h = 0; h < 60; ++h) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) st[i] = sg[i] - s * d[i];
-            evaluate_r(Sp, M, etr, tauc, inv_tc, st, mc, e);
+            evaluate_r(Sp, M, etr, hf, inv_tc, st, mc, e);
             ++nevals;
             if (e.phi <= phi0 - (TA)1e-4 * s * rd || s * dn <= ls_free * scale) {
                 ok = true;
@@ -299,13 +307,13 @@ __device__ int chord_voxel(const TA Sp[21], const TA *__restrict__ M, const TA e
     return -maxit;
 }
 
-template <typename TA, typename TS, typename TF>
+template <typename TA, typename TS, typename TF, bool MR = false>
 __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_chord(long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc,
                                                           const int32_t *__restrict__ g0, TA *__restrict__ sig,
                                                           const TA *__restrict__ Stab, const TA *__restrict__ Mtab,
                                                           TS *__restrict__ fac, MatConst mc, TA tol, int maxit,
                                                           TA ls_free, int force_refresh, int *__restrict__ flags, const int *__restrict__ skip,
-    const TA *__restrict__ tol_dev) {
+    const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -325,8 +333,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
         if (!force_refresh) {
             load_factors(fac, N3, v, F);
         }
-        r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
-                                    force_refresh != 0, nev, nref);
+        if constexpr (MR)
+            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]}, sg,
+                                        mc, tol, maxit, ls_free, F, force_refresh != 0, nev, nref);
+        else
+            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
+                                        force_refresh != 0, nev, nref);
 #pragma unroll
         for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
         if (nref) {
@@ -344,14 +356,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
 // order immaterial: each voxel's computation is independent and deterministic). Pass 2 runs the
 // full chord iteration on the listed voxels only, from their unchanged state, so every result is
 // bitwise the one the single-kernel iteration gives.
-template <typename TA, typename TS>
+template <typename TA, typename TS, bool MR = false>
 __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_first(long N3, const TA *__restrict__ epst,
                                                          const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
                                                          TA *__restrict__ sig, const TA *__restrict__ Stab,
                                                          const TA *__restrict__ Mtab, const TS *__restrict__ fac,
                                                          MatConst mc, TA tol, int *__restrict__ flags,
                                                          int32_t *__restrict__ wl, const int *__restrict__ skip,
-    const TA *__restrict__ tol_dev) {
+    const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,7 +383,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
         load_factors(fac, N3, v, F);
         const TA tc = tauc[v];
         EvalR<TA> e;
-        evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, tc, drcp(tc), sg, mc, e);
+        if constexpr (MR)
+            evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tc}, (TA)0, sg, mc, e);
+        else
+            evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, tc, drcp(tc), sg, mc, e);
         TA d[6];
         ldl_apply<TS, TA>(F, e.r, d);
         TA rd = (TA)0, dn = (TA)0, sn = (TA)0;
@@ -397,12 +412,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
     // the accepted voxels (one evaluation and one solve each) are counted by pass 2 as N3 - listed
 }
 
-template <typename TA, typename TS, typename TF>
+template <typename TA, typename TS, typename TF, bool MR = false>
 __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_rest(
     long N3, const TA *__restrict__ epst, const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
     TA *__restrict__ sig, const TA *__restrict__ Stab, const TA *__restrict__ Mtab, TS *__restrict__ fac, MatConst mc,
     TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int32_t *__restrict__ wl, const int *__restrict__ skip,
-    const TA *__restrict__ tol_dev) {
+    const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const int count = *(volatile const int *)(flags + 10);
@@ -430,8 +445,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_res
             }
             TS F[21];
             load_factors(fac, N3, v, F);
-            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F, false,
-                                        nev, nref);
+            if constexpr (MR)
+                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]},
+                                            sg, mc, tol, maxit, ls_free, F, false, nev, nref);
+            else
+                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F, false,
+                                            nev, nref);
 #pragma unroll
             for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c];
             if (nref) {
@@ -501,7 +520,7 @@ template <int NV, typename T> __device__ __forceinline__ void block_sums(const T
     }
 }
 
-template <typename TA, typename TS, typename TF>
+template <typename TA, typename TS, typename TF, bool MR = false>
 __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__restrict__ epst, const TA *__restrict__ epse,
                                                       const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
                                                       TA *__restrict__ sig, TA *__restrict__ lam, TA *__restrict__ pout,
@@ -510,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
                                                       TA sb, TA sa_lo, TA sb_lo, double sad, double sbd, TA tol,
                                                       int maxit, TA ls_free, int init,
                                                       int *__restrict__ flags, double *__restrict__ part,
-                                                      TS *__restrict__ fac, int refresh) {
+                                                      TS *__restrict__ fac, int refresh, MRPtr<TA> mrp) {
     constexpr int NV = 14;
     __shared__ double red[(kThreads / 32) * NV];
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -541,13 +560,21 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
                 load_factors(fac, N3, v, F);
             }
             int nref = 0;
-            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
-                                        refresh != 0, nev, nref);
+            if constexpr (MR)
+                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]},
+                                            sg, mc, tol, maxit, ls_free, F, refresh != 0, nev, nref);
+            else
+                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
+                                            refresh != 0, nev, nref);
             if (nref) {
                 store_factors(fac, N3, v, F);
             }
         } else {
-            r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
+            if constexpr (MR)
+                r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]}, sg,
+                                         mc, tol, maxit, ls_free, nev);
+            else
+                r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
         }
         // local strain e_tr = eps_tr' - S0 sigma and the gap d = eps_tr - e_tr to about twice the field
         // precision: near convergence eps_tr and e_tr agree to many digits, and forming them in plain FP32
@@ -710,53 +737,68 @@ template <typename TA> TA ls_free_of() { return sizeof(TA) == 4 ? (TA)1e-3 : (TA
 
 }  // namespace
 
+// Each launcher runs the power-law kernels, or their Ma-Roters instantiations when mrp.tp is set.
+template <typename TA, typename F> cudaError_t by_law(MRPtr<TA> mrp, F &&go) {
+    if (mrp.tp) go(std::true_type{});
+    else go(std::false_type{});
+    return cudaGetLastError();
+}
+
 template <typename TA>
 cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                          const TA *Mtab, MatConst mc, double tol, int maxit, int solve_fp64, int *flags,
-                         cudaStream_t s, const int *skip, const TA *tol_dev) {
+                         cudaStream_t s, const int *skip, const TA *tol_dev, MRPtr<TA> mrp) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
-    if (solve_fp64)
-        k_newton<TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol, maxit,
-                                                         ls_free_of<TA>(), flags, skip, tol_dev);
-    else
-        k_newton<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol, maxit,
-                                                     ls_free_of<TA>(), flags, skip, tol_dev);
-    return cudaGetLastError();
+    return by_law(mrp, [&](auto law) {
+        constexpr bool MR = decltype(law)::value;
+        if (solve_fp64)
+            k_newton<TA, double, MR><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol,
+                                                                 maxit, ls_free_of<TA>(), flags, skip, tol_dev, mrp);
+        else
+            k_newton<TA, TA, MR><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, mc, (TA)tol, maxit,
+                                                             ls_free_of<TA>(), flags, skip, tol_dev, mrp);
+    });
 }
 
 template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s, const int *skip,
-                               const TA *tol_dev) {
+                               const TA *tol_dev, MRPtr<TA> mrp) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
     if (!force_refresh && wl) {
         // flags[10] counts the listed voxels; pass 2 reads it on the device (no host round trip)
         cudaError_t e = cudaMemsetAsync(flags + 10, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
-        k_chord_first<TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (const TA *)fac, mc,
-                                                          (TA)tol, flags, wl, skip, tol_dev);
         const int rb = std::min(blocks, nsm * (sizeof(TA) == 4 ? 3 : 2));
-        if (solve_fp64)
-            k_chord_rest<TA, TA, double><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
-                                                                 (TA)tol, maxit, ls_free_of<TA>(), flags, wl, skip,
-                                                                 tol_dev);
-        else
-            k_chord_rest<TA, TA, TA><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
-                                                             (TA)tol, maxit, ls_free_of<TA>(), flags, wl, skip,
-                                                             tol_dev);
-        return cudaGetLastError();
+        return by_law(mrp, [&](auto law) {
+            constexpr bool MR = decltype(law)::value;
+            k_chord_first<TA, TA, MR><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (const TA *)fac,
+                                                                  mc, (TA)tol, flags, wl, skip, tol_dev, mrp);
+            if (solve_fp64)
+                k_chord_rest<TA, TA, double, MR><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab,
+                                                                         (TA *)fac, mc, (TA)tol, maxit,
+                                                                         ls_free_of<TA>(), flags, wl, skip, tol_dev,
+                                                                         mrp);
+            else
+                k_chord_rest<TA, TA, TA, MR><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac,
+                                                                     mc, (TA)tol, maxit, ls_free_of<TA>(), flags, wl,
+                                                                     skip, tol_dev, mrp);
+        });
     }
     // factors stored in the field precision; factorised in FP64 unless the FP32 solve is asked for
-    if (solve_fp64)
-        k_newton_chord<TA, TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
-                                                                   (TA)tol, maxit, ls_free_of<TA>(), force_refresh,
-                                                                   flags, skip, tol_dev);
-    else
-        k_newton_chord<TA, TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac, mc,
-                                                               (TA)tol, maxit, ls_free_of<TA>(), force_refresh, flags,
-                                                               skip, tol_dev);
-    return cudaGetLastError();
+    return by_law(mrp, [&](auto law) {
+        constexpr bool MR = decltype(law)::value;
+        if (solve_fp64)
+            k_newton_chord<TA, TA, double, MR><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab,
+                                                                           (TA *)fac, mc, (TA)tol, maxit,
+                                                                           ls_free_of<TA>(), force_refresh, flags,
+                                                                           skip, tol_dev, mrp);
+        else
+            k_newton_chord<TA, TA, TA, MR><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac,
+                                                                       mc, (TA)tol, maxit, ls_free_of<TA>(),
+                                                                       force_refresh, flags, skip, tol_dev, mrp);
+    });
 }
 
 int al_blocks(long N3) { return (int)((N3 + kThreads - 1) / kThreads); }
@@ -775,23 +817,25 @@ template <typename TA>
 cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
                      const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
                      int maxit, int solve_fp64, int init, int *flags, double *part, void *fac, int refresh,
-                     cudaStream_t s) {
+                     cudaStream_t s, MRPtr<TA> mrp) {
     const int blocks = al_blocks(N3);
     const double sad = 1.0 / (2.0 * mu0), sbd = lam0 / (2.0 * mu0 * (3.0 * lam0 + 2.0 * mu0));
     const TA sa = (TA)sad, sb = (TA)sbd;
     const TA sa_lo = (TA)(sad - (double)sa), sb_lo = (TA)(sbd - (double)sb);   // S0 = (sa + sa_lo) I - (sb + sb_lo) J
-    if (solve_fp64)
-        k_al_local<TA, TA, double><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab,
-                                                               mc, (TA)lam0, (TA)mu0, sa, sb, sa_lo, sb_lo, sad, sbd,
-                                                               (TA)tol, maxit,
-                                                               ls_free_of<TA>(), init, flags, part, (TA *)fac, refresh);
-    else
-        k_al_local<TA, TA, TA><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal, Mtab, mc,
-                                                           (TA)lam0, (TA)mu0, sa, sb, sa_lo, sb_lo, sad, sbd, (TA)tol,
-                                                           maxit,
-                                                           ls_free_of<TA>(),
-                                                           init, flags, part, (TA *)fac, refresh);
-    return cudaGetLastError();
+    return by_law(mrp, [&](auto law) {
+        constexpr bool MR = decltype(law)::value;
+        if (solve_fp64)
+            k_al_local<TA, TA, double, MR><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal,
+                                                                       Mtab, mc, (TA)lam0, (TA)mu0, sa, sb, sa_lo,
+                                                                       sb_lo, sad, sbd, (TA)tol, maxit,
+                                                                       ls_free_of<TA>(), init, flags, part, (TA *)fac,
+                                                                       refresh, mrp);
+        else
+            k_al_local<TA, TA, TA, MR><<<blocks, kThreads, 0, s>>>(N3, epst, epse, tauc, g0, sig, lam, p, Stab, Sal,
+                                                                   Mtab, mc, (TA)lam0, (TA)mu0, sa, sb, sa_lo, sb_lo,
+                                                                   sad, sbd, (TA)tol, maxit, ls_free_of<TA>(), init,
+                                                                   flags, part, (TA *)fac, refresh, mrp);
+    });
 }
 
 template <typename TA>
@@ -820,13 +864,13 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
 #define EVP_INST(TA)                                                                                              \
     template cudaError_t newton_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,        \
                                           const TA *, MatConst, double, int, int, int *, cudaStream_t,           \
-                                          const int *, const TA *);                                              \
+                                          const int *, const TA *, MRPtr<TA>);                                   \
     template cudaError_t newton_chord_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,  \
                                                 const TA *, void *, MatConst, double, int, int, int, int *,       \
-                                                int32_t *, int, cudaStream_t, const int *, const TA *);           \
+                                                int32_t *, int, cudaStream_t, const int *, const TA *, MRPtr<TA>); \
     template cudaError_t al_local<TA>(long, const TA *, const TA *, const TA *, const int32_t *, TA *, TA *, TA *, \
                                       const TA *, const TA *, const TA *, MatConst, double, double, double, int, int, \
-                                      int, int *, double *, void *, int, cudaStream_t);                           \
+                                      int, int *, double *, void *, int, cudaStream_t, MRPtr<TA>);                \
     template cudaError_t predictor<TA>(long, const TA *, const TA *, const TA *, TA *, TA *, MatConst, double,    \
                                        const double *, int, cudaStream_t);                                        \
     template cudaError_t state_update<TA>(long, const TA *, const TA *, const int32_t *, const TA *, TA *, TA *,  \

@@ -19,15 +19,16 @@ EVP_ERR = {-1: "EVP_ERR_ARG", -2: "EVP_ERR_CUDA", -3: "EVP_ERR_NEWTON", -4: "EVP
            -5: "EVP_ERR_NONFINITE", -6: "EVP_ERR_OOM"}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_fast": 2}
 
-F_SIG, F_EPS, F_EPSP, F_EPSE, F_DEPS, F_RHO, F_K, F_KAPPA, F_GRAIN, F_G0, F_DRAWS, F_IDS, F_ETA, F_GRAIN_PF = (
-    1 << i for i in range(14))
+(F_SIG, F_EPS, F_EPSP, F_EPSE, F_DEPS, F_RHO, F_K, F_KAPPA, F_GRAIN, F_G0, F_DRAWS, F_IDS, F_ETA, F_GRAIN_PF,
+ F_GND) = (1 << i for i in range(15))
 FIELDS = {"sig": F_SIG, "eps": F_EPS, "epsp": F_EPSP, "epse": F_EPSE, "deps": F_DEPS, "rho": F_RHO, "k": F_K,
           "kappa": F_KAPPA, "g": F_GRAIN, "g0": F_G0, "draws": F_DRAWS, "ids": F_IDS, "eta": F_ETA,
-          "gpf": F_GRAIN_PF}
+          "gpf": F_GRAIN_PF, "gnd3": F_GND}
 # (components, kind) with kind "T" = field precision, "f8" = double, "i4" = int32, "K" = kmax components
 _FIELD_SHAPE = {"sig": (6, "T"), "eps": (6, "T"), "epsp": (6, "T"), "epse": (6, "T"), "deps": (6, "T"),
                 "rho": (12, "T"), "k": (1, "f8"), "kappa": (1, "f8"), "g": (1, "i4"), "g0": (1, "i4"),
-                "draws": (1, "i4"), "ids": ("K", "i4"), "eta": ("K", "T"), "gpf": (1, "i4")}
+                "draws": (1, "i4"), "ids": ("K", "i4"), "eta": ("K", "T"), "gpf": (1, "i4"), "gnd3": (36, "T")}
+LAWS = {"power": 0, "mr": 1}
 _PF_FIELDS = ("ids", "eta", "gpf")   # on the phase-field grid ((r n)^3 points)
 
 
@@ -40,13 +41,14 @@ class Config(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("allow_unconverged", C.c_int),
                 ("newton_tol", C.c_double), ("newton_max", C.c_int), ("predictor", C.c_int), ("max_ids", C.c_int),
                 ("newton_mode", C.c_int), ("scheme", C.c_int), ("al_scale", C.c_double),
-                ("newton_adapt", C.c_double), ("pf_refine", C.c_int)]
+                ("newton_adapt", C.c_double), ("pf_refine", C.c_int), ("law", C.c_int)]
 
 
 class Params(C.Structure):
     _fields_ = [(k, C.c_double) for k in (
         "C11", "C12", "C44", "gdot0", "n", "tau0", "alpha", "b", "k1", "k2", "rho0", "zeta",
-        "kc", "q", "s_nucl", "s_soften", "omega_gb", "dx", "l_gb", "L_dt", "eta_drop")]
+        "kc", "q", "s_nucl", "s_soften", "omega_gb", "dx", "l_gb", "L_dt", "eta_drop",
+        "T", "Q_slip", "Q_bulk", "nu_D", "poisson", "c1", "c2", "c3", "c4", "c5", "c6", "c7", "c8", "xi")]
 
 
 class Stats(C.Structure):
@@ -82,6 +84,8 @@ def load():
     L.evp_get_scalars.argtypes = [vp, vp, vp, vp, vp]
     L.evp_set_scalars.argtypes = [vp, vp, vp, i, i]
     L.evp_set_solver.argtypes = [vp, d, i, i]
+    L.evp_get_leff.argtypes = [vp, C.POINTER(d)]
+    L.evp_set_leff.argtypes = [vp, d]
     L.evp_destroy.argtypes = [vp]
     L.evp_destroy.restype = None
     L.evp_last_error.argtypes = [vp]
@@ -105,7 +109,7 @@ def load():
               "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_kernel_times",
               "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual",
               "evp_adjoint_workspace_bytes", "evp_adjoint_begin", "evp_adjoint_step", "evp_adjoint_end",
-              "evp_newton_refreshes"):
+              "evp_newton_refreshes", "evp_get_leff", "evp_set_leff"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -124,19 +128,23 @@ SCHEMES = {"basic": 0, "al": 1}
 
 def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, allow_unconverged=0,
                 newton_tol=None, newton_max=50, predictor=1, max_ids=0, newton=None, scheme="basic",
-                al_scale=6.0, newton_adapt=None, pf_refine=1) -> Config:
+                al_scale=6.0, newton_adapt=None, pf_refine=1, law="power") -> Config:
     if newton_tol is None:
         newton_tol = 1e-12 if precision == "fp64" else 1e-5
     if newton is None:
         # measured on GB300 at 128^3: tangent reuse pays where the 6x6 solve is FP64 next to an FP32
         # residual (EVP_MIXED, 1.5x); the FP64 path runs fastest with an FP32 tangent and solve under
-        # its FP64 residual (1.5x, identical iterates); the all-FP32 path with the exact Newton
+        # its FP64 residual (1.5x, identical iterates); the all-FP32 path with the exact Newton. The FP32
+        # tangent under an FP64 residual covers the power law only.
         newton = {"mixed": "reuse", "fp64": "f32_tangent", "mixed_fast": "exact"}[precision]
+        if law == "mr" and newton == "f32_tangent":
+            newton = "reuse"
     if newton_adapt is None:
         # the FP64 path stays the reference: every local problem solved to newton_tol
         newton_adapt = 0.0 if precision == "fp64" else 0.1
     return Config(n, grains, kmax, PRECISION[precision], tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                  predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale, newton_adapt, pf_refine)
+                  predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale, newton_adapt, pf_refine,
+                  LAWS[law])
 
 
 def make_params(mat) -> Params:
@@ -276,6 +284,22 @@ class Solver:
         Ea = (C.c_double * 6)(*E)
         dA = (C.c_double * 6)(*dE_prev)
         self._check("evp_set_scalars", load().evp_set_scalars(self.h, Ea, dA, int(have_prev), int(next_id)))
+
+    @property
+    def leff(self):
+        """Effective GND length l_eff of the Ma-Roters law (Eq. L0evolution), m."""
+        v = C.c_double(0.0)
+        self._check("evp_get_leff", load().evp_get_leff(self.h, C.byref(v)))
+        return v.value
+
+    @leff.setter
+    def leff(self, value):
+        self._check("evp_set_leff", load().evp_set_leff(self.h, float(value)))
+
+    def gnd(self):
+        """Ma-Roters GND densities: (rho_GNDs, rho_GNDet, rho_GND), each (12, N^3)."""
+        a = self.get("gnd3")
+        return a[:12], a[12:24], a[24:]
 
     # ---- differentiation ----
     def adjoint_begin(self, n_increments, checkpoint_every):
