@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--al-steps", type=int, default=1, help="run the augmented-Lagrangian companion (0 = skip)")
     ap.add_argument("--pf2-steps", type=int, default=2,
                     help="timed increments of the companion on the 2:1 phase-field grid (0 = skip)")
+    ap.add_argument("--mr-steps", type=int, default=2,
+                    help="timed increments of the Ma-Roters companion (the paper's dislocation law; 0 = skip)")
+    ap.add_argument("--mr-fp64-steps", type=int, default=2, help="FP64 Ma-Roters comparison increments (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
@@ -266,6 +269,8 @@ def native(args, ws, rank, local):
         res["augmented_lagrangian"] = al_companion(args, wl, g0, quat, mat, torch, evp, warm + timed)
     if args.pf2_steps > 0:
         res["pf_grid_2to1"] = pf2_companion(args, wl, g0, quat, mat, torch, evp, pk)
+    if args.mr_steps > 0:
+        res["ma_roters"] = mr_companion(args, wl, g0, quat, torch, evp, pk)
     # FP64 companion run on the same seeded input
     n64 = args.warmup + args.steps if args.fp64_steps < 0 else args.fp64_steps
     if n64 > 0:
@@ -394,6 +399,78 @@ def pf2_companion(args, wl, g0, quat, mat, torch, evp, pk):
         out["pf_step_us"] = round(1e6 * per, 1)
         out["pf_step_GB/s"] = round(b / per / 1e9, 1)
         out["pf_step_frac"] = round(b / per / 1e9 / pk.get("hbm_gbs", 6800.0), 3)
+    return out
+
+
+MR_DT_PER_STRAIN = 625.0   # s per unit strain: the paper's strain rate 1.6e-3 /s
+
+
+def mr_bytes_per_voxel(T):
+    """Algorithmic HBM bytes per voxel of the Ma-Roters state update (three launches): shear rates and
+    strains (reads sigma 6, tau_pass and 1/tau_cut 24, trial / elastic / plastic strain 18, grain id; writes
+    eps_p, eps_e, strain increment 18, rates 12, (sigma_vm, gdot_vm) 2), the density update (reads the rates
+    12, aux 2, sigma 6, SSD / GND 48, both grain ids; writes SSD / GND 48) and k (reads 48, writes k)."""
+    return (6 + 24 + 18 + 18 + 12 + 2) * T + 4 + (12 + 2 + 6 + 48 + 48) * T + 8 + 48 * T + 8
+
+
+def mr_companion(args, wl, g0, quat, torch, evp, pk):
+    """The paper's own constitutive law (Ma-Roters, Sec. 2.2) on the same grid and grains, with the
+    augmented-Lagrangian solver the paper names, at the paper's strain rate (1e-3 strain per increment in
+    0.625 s): throughput, the live rate of the local solve and of the density update against their
+    algorithmic bytes, and the mixed path's macro stress against the FP64 path's."""
+    mat = synth.ma_roters_material()
+    dt = abs(wl.dE33) * MR_DT_PER_STRAIN
+    prec = args.precision
+    tol = args.tol64 if prec == "fp64" else 5e-6
+    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=prec, law="mr", scheme="al", al_scale=8.0,
+                   tol=tol, max_iter=5000)
+    hw = run_steps(s, 1, wl.dE33, dt, wl.pf_steps, torch)
+    s.set_profiling(True)
+    s.kernel_times(reset=True)
+    n0 = s.newton_counts()
+    h = run_steps(s, args.mr_steps, wl.dE33, dt, wl.pf_steps, torch)
+    kt = s.kernel_times(reset=True)
+    n1 = s.newton_counts()
+    N3 = wl.n ** 3
+    T = 4 if prec != "fp64" else 8
+    evp_s = sum(r["evp_ms"] for r in h) / 1e3
+    step_s = sum(r["step_ms"] for r in h) / 1e3
+    iters = sum(r["it"] for r in h)
+    hpk = pk.get("hbm_gbs", 6800.0)
+    out = {"law": "Ma-Roters (Eqs. FlowRule, RhoForest, RhoParallel, SSDEvolution, GNDEvolution, L0evolution)",
+           "scheme": "augmented Lagrangian, al_scale 8", "precision": prec, "tol": tol, "dt": dt,
+           "voxel_iters_per_s": N3 * iters / evp_s, "drx_increments_per_s": len(h) / step_s,
+           "ms_per_step": 1e3 * step_s / len(h), "increments": len(h),
+           "fixed_point_iterations": [r["it"] for r in hw + h], "sig33": [round(r["sig33"], 4) for r in hw + h],
+           "leff_m": s.leff, "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]},
+           "newton_solves_per_voxel_iter": (n1[0] - n0[0]) / (N3 * max(iters, 1)),
+           "newton_evals_per_voxel_iter": (n1[1] - n0[1]) / (N3 * max(iters, 1))}
+    ms, nl = kt.get("state_update", (0.0, 0))
+    if nl:
+        per = ms / len(h) / 1e3
+        b = mr_bytes_per_voxel(T) * N3
+        out["state_update"] = {"us_per_increment": round(1e6 * per, 1), "GB/s": round(b / per / 1e9, 1),
+                               "frac": round(b / per / 1e9 / hpk, 3), "bytes_per_increment": b}
+    ms, nl = kt.get("newton", (0.0, 0))
+    if nl:
+        per = ms / nl / 1e3
+        # AL local step, per voxel: reads trial and elastic strain, multiplier, stress (24), tau_ref (1), tau_pass
+        # and 1/tau_cut (24), stored factors (24 planes' words) and the grain id; writes stress, multiplier,
+        # polarisation (18) and, on a refresh, the factors
+        b = ((6 + 6 + 6 + 6 + 1 + 24 + 24 + 18) * T + 4) * N3
+        out["local_solve"] = {"us_per_launch": round(1e6 * per, 1), "GB/s": round(b / per / 1e9, 1),
+                              "frac": round(b / per / 1e9 / hpk, 3)}
+    if args.mr_fp64_steps > 0 and prec != "fp64":
+        s64 = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="fp64", law="mr", scheme="al",
+                         al_scale=8.0, tol=args.tol64, max_iter=5000)
+        h64 = run_steps(s64, min(args.mr_fp64_steps, len(hw + h)), wl.dE33, dt, wl.pf_steps, torch)
+        errs = [abs(a["sig33"] - b["sig33"]) / abs(b["sig33"]) for a, b in zip(hw + h, h64)]
+        e64 = sum(r["evp_ms"] for r in h64) / 1e3
+        out["fp64"] = {"voxel_iters_per_s": N3 * sum(r["it"] for r in h64) / e64,
+                       "fixed_point_iterations": [r["it"] for r in h64], "tol": args.tol64,
+                       "mixed_vs_fp64_macro_stress_rel_err_max": max(errs)}
+        del s64
+    del s
     return out
 
 

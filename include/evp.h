@@ -67,11 +67,11 @@ typedef struct {
                               EVP_SCHEME_AL: augmented Lagrangian (Michel-Moulinec-Suquet), the solver the
                               paper names (Sec. 2.1); same solution, fewer iterations at high contrast */
     double al_scale;       /* EVP_SCHEME_AL: reference shear modulus = Voigt mu / al_scale (bulk kept) */
-    double newton_adapt;   /* EVP_SCHEME_BASIC: 0 solves every local problem to newton_tol; eta > 0 loosens
-                              the local tolerance while the fixed point is far from converged, to
-                              max(newton_tol, eta * err) with err the fixed-point residual of the previous
-                              iteration (1e-2 before the first); the converged result meets the same
-                              tolerances */
+    double newton_adapt;   /* 0 solves every local problem to newton_tol; eta > 0 loosens the local tolerance
+                              while the fixed point is far from converged, to max(newton_tol, eta * err) with err
+                              the fixed-point residual of the previous iteration (1e-2 before the first; in
+                              EVP_SCHEME_AL the larger of the compatibility and multiplier residuals); the converged
+                              result meets the same tolerances, with local problems solved to newton_tol */
     int pf_refine;         /* phase-field grid spacing per mechanics spacing: 0 or 1 = the same grid; 2 = the
                               2:1 refined PF grid of Sec. 2.4 ((2n)^3 PF points; the active sets, the PF argmax
                               and the interpolated driving force live there; see pf_step and drx_nucleate) */

@@ -68,7 +68,7 @@ struct evp_handle {
     // rho_GND (12 x N3 each); frozen tau_pass and 1/tau_cut (12 x N3 each, tauc = min tau_pass); shear rates
     // and (sigma_vm, gdot_vm) of the last increment; sample-frame d and t per grain; constants; l_eff
     int mr;
-    void *gs, *ge, *gnd, *tp, *itc, *gdm, *aux, *vec;
+    void *gs, *ge, *gnd, *tpi, *gdm, *aux, *vec;
     MRConst mrc;
     double leff;
     char err[512];
@@ -221,11 +221,11 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     const bool mr = c->law == EVP_LAW_MR;
     char *gnd3 = take(mr ? 36 * N3 * T : 0);   // rho_GNDs, rho_GNDet, rho_GND: one block (field EVP_F_GND)
     char *gs = gnd3, *ge = mr ? gnd3 + 12 * N3 * T : nullptr, *gnd = mr ? gnd3 + 24 * N3 * T : nullptr;
-    char *tp = take(mr ? 12 * N3 * T : 0), *itc = take(mr ? 12 * N3 * T : 0), *gdm = take(mr ? 12 * N3 * T : 0);
+    char *tpi = take(mr ? 24 * N3 * T : 0), *gdm = take(mr ? 12 * N3 * T : 0);
     char *aux = take(mr ? 2 * N3 * T : 0), *vec = take(mr ? 72 * (size_t)G * T : 0);
     if (h) {
         h->mr = mr ? 1 : 0;
-        h->gs = gs; h->ge = ge; h->gnd = gnd; h->tp = tp; h->itc = itc; h->gdm = gdm; h->aux = aux; h->vec = vec;
+        h->gs = gs; h->ge = ge; h->gnd = gnd; h->tpi = tpi; h->gdm = gdm; h->aux = aux; h->vec = vec;
         h->sig = sig; h->sigk = sigk; h->epse = epse; h->epst = epst; h->epsp = epsp; h->deps = deps;
         h->rho = rho; h->tauc = tauc; h->eta = eta; h->eta2 = eta2; h->spec = spec; h->Stab = Stab; h->Mtab = Mtab;
         h->fac = fac;
@@ -453,7 +453,7 @@ cudaError_t mr_soften_sel(evp_handle *h, int mode, int lo) {
                             (float *)h->gnd, h->k, h->mrc, h->st);
 }
 template <typename TA> MRPtr<TA> mr_ptr(const evp_handle *h) {
-    return h->mr ? MRPtr<TA>{(const TA *)h->tp, (const TA *)h->itc} : MRPtr<TA>{nullptr, nullptr};
+    return h->mr ? MRPtr<TA>{(const TA *)h->tpi} : MRPtr<TA>{nullptr};
 }
 // von Mises equivalent of a Mandel strain, sqrt(2/3 e:e) of its deviator (Eq. L0evolution's eps_vm)
 double vm_strain(const double e[6]) {
@@ -484,11 +484,16 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
     int nmax = 0, conv = 0, it;
     double ecmp = 0, elam = 0, ebc = 0;
     void *fac = h->cfg.newton_mode == EVP_NEWTON_REUSE ? h->fac : nullptr;
+    // local tolerance: newton_tol, or with newton_adapt = eta > 0 loosened to max(newton_tol, eta err) while the
+    // iteration is far from converged (err = the larger of the compatibility and multiplier residuals of the
+    // previous iteration, 1e-2 before the first), as in the basic scheme
+    const double ntol = h->cfg.newton_tol, eta = h->cfg.newton_adapt;
+    double tol_loc = eta > 0.0 ? std::fmax(ntol, eta * 1e-2) : ntol;
     auto local = [&](int init, int refresh) -> int {
         { PROF(0, 1);
           CK(al_local<TA>(N3, (const TA *)h->epst, (const TA *)h->epse, (const TA *)h->tauc, h->g0, (TA *)h->sigk,
                           (TA *)h->lam, (TA *)h->pal, (const TA *)h->Stab, (const TA *)h->Sal, (const TA *)h->Mtab, mc,
-                          lam0, mu0, h->cfg.newton_tol, h->cfg.newton_max, solve64, init, h->flags, h->partials, fac,
+                          lam0, mu0, tol_loc, h->cfg.newton_max, solve64, init, h->flags, h->partials, fac,
                           refresh, h->st, mr_ptr<TA>(h))); }
         { PROF(6, 1); CK(reduce_partials(h->partials, nb, 14, h->scal + 24, h->st)); }
         CK(cudaMemcpyAsync(hs, h->scal + 24, sizeof hs, cudaMemcpyDeviceToHost, h->st));
@@ -530,7 +535,8 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
         elam = std::sqrt(hs[1] / (double)N3) / den;
         ebc = std::sqrt(mu_n) / den;
         if (!std::isfinite(ecmp) || !std::isfinite(elam)) { rc = fail(h, EVP_ERR_NONFINITE, "non-finite AL residual"); break; }
-        if (ecmp <= h->cfg.tol && elam <= h->cfg.tol && ebc <= h->cfg.tol) { conv = 1; break; }
+        if (ecmp <= h->cfg.tol && elam <= h->cfg.tol && ebc <= h->cfg.tol && tol_loc <= ntol) { conv = 1; break; }
+        if (eta > 0.0) tol_loc = std::fmax(ntol, eta * std::fmax(ecmp, elam));
     }
     if (it > h->cfg.max_iter) it = h->cfg.max_iter;
     *it_out = it;
@@ -790,10 +796,10 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         PROF(7, 1);
         if (h->dbl)
             CK(mr_harden<double>(N3, (const double *)h->rho, (const double *)h->gs, (const double *)h->ge,
-                                 (double *)h->tp, (double *)h->itc, (double *)h->tauc, h->mrc, h->st));
+                                 (double *)h->tpi, (double *)h->tauc, h->mrc, h->st));
         else
-            CK(mr_harden<float>(N3, (const float *)h->rho, (const float *)h->gs, (const float *)h->ge, (float *)h->tp,
-                                (float *)h->itc, (float *)h->tauc, h->mrc, h->st));
+            CK(mr_harden<float>(N3, (const float *)h->rho, (const float *)h->gs, (const float *)h->ge, (float *)h->tpi,
+                                (float *)h->tauc, h->mrc, h->st));
     }
     // mixed-BC correction: (C0_uu)^-1 on u = {11, 22, 23, 13, 12}
     const double a = lam0 + 2.0 * mu0, b = lam0, det = a * a - b * b;
@@ -938,14 +944,14 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         c.d.dt = dt;
         c.f.dt = (float)dt;
         if (h->dbl) {
-            CK(mr_rates<double>(N3, (const double *)h->sigk, (const double *)h->tp, (const double *)h->itc, h->g0,
+            CK(mr_rates<double>(N3, (const double *)h->sigk, (const double *)h->tpi, h->g0,
                                 (const double *)h->Mtab, (const double *)h->epst, (double *)h->epse, (double *)h->epsp,
                                 (double *)h->deps, (double *)h->gdm, (double *)h->aux, mc, h->st));
             CK(mr_update<double>(n, h->g, h->g0, (const double *)h->gdm, (const double *)h->aux, (const double *)h->sigk,
                                  (const double *)h->Mtab, (const double *)h->vec, (double *)h->rho, (double *)h->gs,
                                  (double *)h->ge, (double *)h->gnd, h->k, c, h->leff, h->st));
         } else {
-            CK(mr_rates<float>(N3, (const float *)h->sigk, (const float *)h->tp, (const float *)h->itc, h->g0,
+            CK(mr_rates<float>(N3, (const float *)h->sigk, (const float *)h->tpi, h->g0,
                                (const float *)h->Mtab, (const float *)h->epst, (float *)h->epse, (float *)h->epsp,
                                (float *)h->deps, (float *)h->gdm, (float *)h->aux, mc, h->st));
             CK(mr_update<float>(n, h->g, h->g0, (const float *)h->gdm, (const float *)h->aux, (const float *)h->sigk,

@@ -15,11 +15,11 @@ struct MatConst {
     void set_fp32() { gdot0_f = (float)gdot0; n_f = (float)n; dt_f = (float)dt; mr_ga_f = (float)mr_ga; }
 };
 
-// Ma-Roters law (Sec. 2.2): the frozen flow-rule data of every voxel, passing stress tau_pass and inverse
-// cutting stress 1/tau_cut per slip system (12 x N^3 each). tp == nullptr selects the power law.
+// Ma-Roters law (Sec. 2.2): the frozen flow-rule data of every voxel, the pair (tau_pass, 1/tau_cut) of each slip
+// system, pair (a, v) at words 2 (a N^3 + v) and 2 (a N^3 + v) + 1 (one 8- or 16-byte load). tpi == nullptr
+// selects the power law.
 template <typename TA> struct MRPtr {
-    const TA *tp;
-    const TA *itc;
+    const TA *tpi;
 };
 
 // Ma-Roters constants (built on the host in FP64; FP32 copies for the FP32 path). tab: |cos| and |sin| of the
@@ -96,15 +96,15 @@ cudaError_t state_update(long N3, const TA *sig, const TA *tauc, const int32_t *
 template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const TA *epsp, TA *eps, cudaStream_t s);
 
 // ---- mr.cu (Ma-Roters law, Sec. 2.2) ----
-// Frozen hardening of an increment: projections of the densities, tau_pass, 1/tau_cut per system and
-// tref = min_a tau_pass^a (the local Newton's stopping scale).
+// Frozen hardening of an increment: projections of the densities, the pairs (tau_pass, 1/tau_cut) per system
+// (layout of MRPtr) and tref = min_a tau_pass^a (the local Newton's stopping scale).
 template <typename T>
-cudaError_t mr_harden(long N3, const T *ssd, const T *gs, const T *ge, T *tp, T *itc, T *tref, const MRConst &c,
+cudaError_t mr_harden(long N3, const T *ssd, const T *gs, const T *ge, T *tpi, T *tref, const MRConst &c,
                       cudaStream_t s);
 // After convergence: eps_p / eps_e / strain increment as state_update, and the shear rates gd (12 x N^3) with
 // aux = (sigma_vm, gdot_vm) (2 x N^3) for the density update.
 template <typename T>
-cudaError_t mr_rates(long N3, const T *sig, const T *tp, const T *itc, const int32_t *g0, const T *Mtab, const T *epst,
+cudaError_t mr_rates(long N3, const T *sig, const T *tpi, const int32_t *g0, const T *Mtab, const T *epst,
                      T *epse, T *epsp, T *deps, T *gd, T *aux, MatConst mc, cudaStream_t s);
 // Density update: SSD (Eq. SSDEvolution), GND from the shear-rate gradients (Eq. GNDEvolution) with spacing
 // leff, and k (Eq. TotDislocationDensity). vec: per grain the sample-frame d then t of the 12 systems (72 T).

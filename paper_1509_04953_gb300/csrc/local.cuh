@@ -184,14 +184,16 @@ __device__ __forceinline__ void evaluate(const TA Sp[21], const TA *__restrict__
 // u = expm1(x) and w = 1/(1+u) = exp(-x): sinh x = u (1+w)/2 and cosh x - 1 = u (1-w)/2, free of
 // cancellation for small x; an overflowing x gives infinities that the line search rejects.
 template <typename TA> struct FlowMR {
-    const TA *__restrict__ tp;    // tau_pass, 12 x N3
-    const TA *__restrict__ itc;   // 1 / tau_cut, 12 x N3
+    const TA *__restrict__ tpi;   // (tau_pass, 1 / tau_cut) pairs, 12 x N3 (layout of MRPtr)
     long N3, v;
     TA tref;                      // stopping scale: min_a tau_pass^a
 };
 template <typename TA> __device__ __forceinline__ TA flow_ref(TA tauc) { return tauc; }
 template <typename TA> __device__ __forceinline__ TA flow_ref(const FlowMR<TA> &f) { return f.tref; }
 __device__ __forceinline__ float dexpm1(float x) { return expm1f(x); }
+// 1/x rounded to nearest (FP32 reciprocal instruction with its IEEE fix-up) / FP64 division
+__device__ __forceinline__ float rcp_fast(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 __device__ __forceinline__ double dexpm1(double x) { return expm1(x); }
 template <typename TA> __device__ __forceinline__ TA mr_ga(const MatConst &mc) {
     if constexpr (sizeof(TA) == 4) return mc.mr_ga_f;
@@ -201,18 +203,23 @@ template <typename TA>
 __device__ __forceinline__ void mr_flow(TA tau, TA tp, TA itc, TA ga, TA &gd, TA &slope, TA &psi) {
     const TA x = (fabs(tau) - tp) * itc;
     if (x > (TA)0) {
-        const TA u = dexpm1(x), w = (TA)1 / (u + (TA)1), A = ga * tp;
+        const TA u = dexpm1(x), w = rcp_fast(u + (TA)1), A = ga * tp;
         const TA sh = (TA)0.5 * u * ((TA)1 + w), chm1 = (TA)0.5 * u * ((TA)1 - w);
         gd = tau < (TA)0 ? -A * sh : A * sh;
         slope = A * ((TA)1 + chm1) * itc;
-        psi = A * chm1 / itc;
+        psi = A * chm1 * rcp_fast(itc);   // the potential only steers the line search
     } else {
         gd = (TA)0; slope = (TA)0; psi = (TA)0;
     }
 }
 template <typename TA> __device__ __forceinline__ void mr_sys(const FlowMR<TA> &f, int a, TA &tp, TA &itc) {
-    tp = __ldg(f.tp + (long)a * f.N3 + f.v);
-    itc = __ldg(f.itc + (long)a * f.N3 + f.v);
+    if constexpr (sizeof(TA) == 4) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(f.tpi) + (long)a * f.N3 + f.v);
+        tp = t.x; itc = t.y;
+    } else {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(f.tpi) + (long)a * f.N3 + f.v);
+        tp = t.x; itc = t.y;
+    }
 }
 
 template <typename TA>

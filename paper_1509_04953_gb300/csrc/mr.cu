@@ -78,8 +78,8 @@ __device__ __forceinline__ double total_density(const MRConst &c, const T ssd[12
 
 template <typename T>
 __global__ void __launch_bounds__(kMR) k_mr_harden(long N3, const T *__restrict__ ssd, const T *__restrict__ gs,
-                                                  const T *__restrict__ ge, T *__restrict__ tp, T *__restrict__ itc,
-                                                  T *__restrict__ tref, MRConst c) {
+                                                  const T *__restrict__ ge, T *__restrict__ tpi, T *__restrict__ tref,
+                                                  MRConst c) {
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N3) return;
     T s[12], a1[12], a2[12], rF[12], rP[12];
@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(kMR) k_mr_harden(long N3, const T *__restrict_
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
         const T t = k.tp_c * sqrt(rP[a]);
-        tp[a * N3 + v] = t;
-        itc[a * N3 + v] = (T)1 / (k.tcut_c * sqrt(rF[a]));
+        tpi[2 * (a * N3 + v)] = t;
+        tpi[2 * (a * N3 + v) + 1] = (T)1 / (k.tcut_c * sqrt(rF[a]));
         m = a == 0 ? t : fmin(m, t);
     }
     tref[v] = m;
@@ -108,8 +108,8 @@ template <typename T> __device__ __forceinline__ T vm_of(const T x[6], T f) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMR) k_mr_rates(long N3, const T *__restrict__ sig, const T *__restrict__ tp,
-                                                 const T *__restrict__ itc, const int32_t *__restrict__ g0,
+__global__ void __launch_bounds__(kMR) k_mr_rates(long N3, const T *__restrict__ sig, const T *__restrict__ tpi,
+                                                 const int32_t *__restrict__ g0,
                                                  const T *__restrict__ Mtab, const T *__restrict__ epst,
                                                  T *__restrict__ epse, T *__restrict__ epsp, T *__restrict__ deps,
                                                  T *__restrict__ gd, T *__restrict__ aux, MatConst mc) {
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kMR) k_mr_rates(long N3, const T *__restrict__
             tau += m[i] * sg[i];
         }
         T g, slope, psi;
-        mr_flow(tau, tp[a * N3 + v], itc[a * N3 + v], ga, g, slope, psi);
+        mr_flow(tau, tpi[2 * (a * N3 + v)], tpi[2 * (a * N3 + v) + 1], ga, g, slope, psi);
         gd[a * N3 + v] = g;
 #pragma unroll
         for (int i = 0; i < 6; ++i) ep[i] += m[i] * g;
@@ -257,16 +257,16 @@ inline int blocks_of(long N3) { return (int)((N3 + kMR - 1) / kMR); }
 }  // namespace
 
 template <typename T>
-cudaError_t mr_harden(long N3, const T *ssd, const T *gs, const T *ge, T *tp, T *itc, T *tref, const MRConst &c,
+cudaError_t mr_harden(long N3, const T *ssd, const T *gs, const T *ge, T *tpi, T *tref, const MRConst &c,
                       cudaStream_t s) {
-    k_mr_harden<T><<<blocks_of(N3), kMR, 0, s>>>(N3, ssd, gs, ge, tp, itc, tref, c);
+    k_mr_harden<T><<<blocks_of(N3), kMR, 0, s>>>(N3, ssd, gs, ge, tpi, tref, c);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t mr_rates(long N3, const T *sig, const T *tp, const T *itc, const int32_t *g0, const T *Mtab, const T *epst,
+cudaError_t mr_rates(long N3, const T *sig, const T *tpi, const int32_t *g0, const T *Mtab, const T *epst,
                      T *epse, T *epsp, T *deps, T *gd, T *aux, MatConst mc, cudaStream_t s) {
-    k_mr_rates<T><<<blocks_of(N3), kMR, 0, s>>>(N3, sig, tp, itc, g0, Mtab, epst, epse, epsp, deps, gd, aux, mc);
+    k_mr_rates<T><<<blocks_of(N3), kMR, 0, s>>>(N3, sig, tpi, g0, Mtab, epst, epse, epsp, deps, gd, aux, mc);
     return cudaGetLastError();
 }
 
@@ -292,10 +292,10 @@ cudaError_t mr_soften(long N3, int mode, const int32_t *gprev, const int32_t *g,
 }
 
 #define EVP_MR_INST(T)                                                                                            \
-    template cudaError_t mr_harden<T>(long, const T *, const T *, const T *, T *, T *, T *, const MRConst &,    \
+    template cudaError_t mr_harden<T>(long, const T *, const T *, const T *, T *, T *, const MRConst &,          \
                                       cudaStream_t);                                                            \
-    template cudaError_t mr_rates<T>(long, const T *, const T *, const T *, const int32_t *, const T *, const T *, \
-                                     T *, T *, T *, T *, T *, MatConst, cudaStream_t);                          \
+    template cudaError_t mr_rates<T>(long, const T *, const T *, const int32_t *, const T *, const T *, T *, T *, \
+                                     T *, T *, T *, MatConst, cudaStream_t);                                    \
     template cudaError_t mr_update<T>(int, const int32_t *, const int32_t *, const T *, const T *, const T *,     \
                                       const T *, const T *, T *, T *, T *, T *, double *, const MRConst &, double, \
                                       cudaStream_t);                                                            \

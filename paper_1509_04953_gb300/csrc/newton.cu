@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restri
             sg[c] = sig[c * N3 + v];
         }
         if constexpr (MR)
-            r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]}, sg, mc,
+            r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tauc[v]}, sg, mc,
                                      tol, maxit, ls_free, nev);
         else
             r = newton_voxel<TA, TS>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
             load_factors(fac, N3, v, F);
         }
         if constexpr (MR)
-            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]}, sg,
+            r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tauc[v]}, sg,
                                         mc, tol, maxit, ls_free, F, force_refresh != 0, nev, nref);
         else
             r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
         const TA tc = tauc[v];
         EvalR<TA> e;
         if constexpr (MR)
-            evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tc}, (TA)0, sg, mc, e);
+            evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tc}, (TA)0, sg, mc, e);
         else
             evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, tc, drcp(tc), sg, mc, e);
         TA d[6];
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_res
             TS F[21];
             load_factors(fac, N3, v, F);
             if constexpr (MR)
-                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]},
+                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tauc[v]},
                                             sg, mc, tol, maxit, ls_free, F, false, nev, nref);
             else
                 r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F, false,
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
             }
             int nref = 0;
             if constexpr (MR)
-                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]},
+                r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tauc[v]},
                                             sg, mc, tol, maxit, ls_free, F, refresh != 0, nev, nref);
             else
                 r = chord_voxel<TA, TS, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, F,
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
             }
         } else {
             if constexpr (MR)
-                r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tp, mrp.itc, N3, v, tauc[v]}, sg,
+                r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tauc[v]}, sg,
                                          mc, tol, maxit, ls_free, nev);
             else
                 r = newton_voxel<TA, TF>(Sp, Mtab + 72 * (long)g, etr, tauc[v], sg, mc, tol, maxit, ls_free, nev);
@@ -737,9 +737,9 @@ template <typename TA> TA ls_free_of() { return sizeof(TA) == 4 ? (TA)1e-3 : (TA
 
 }  // namespace
 
-// Each launcher runs the power-law kernels, or their Ma-Roters instantiations when mrp.tp is set.
+// Each launcher runs the power-law kernels, or their Ma-Roters instantiations when mrp.tpi is set.
 template <typename TA, typename F> cudaError_t by_law(MRPtr<TA> mrp, F &&go) {
-    if (mrp.tp) go(std::true_type{});
+    if (mrp.tpi) go(std::true_type{});
     else go(std::false_type{});
     return cudaGetLastError();
 }
