@@ -33,30 +33,13 @@ template <typename T> __device__ __forceinline__ T tabv(const MRConst &c, int k,
     else return c.tab[k * 144 + i];
 }
 
-// Eqs. RhoForest / RhoParallel (rho_GNDen = 0).
-template <typename T>
-__device__ __forceinline__ void project(const MRConst &c, const T ssd[12], const T gs[12], const T ge[12], T rF[12],
-                                        T rP[12]) {
-#pragma unroll
-    for (int a = 0; a < 12; ++a) {
-        T f = (T)0, q = (T)0;
-#pragma unroll
-        for (int b = 0; b < 12; ++b) {
-            const int i = 12 * a + b;
-            f += ssd[b] * tabv<T>(c, 0, i) + fabs(gs[b]) * tabv<T>(c, 1, i) + fabs(ge[b]) * tabv<T>(c, 0, i);
-            q += ssd[b] * tabv<T>(c, 2, i) + fabs(gs[b]) * tabv<T>(c, 3, i) + fabs(ge[b]) * tabv<T>(c, 2, i);
-        }
-        rF[a] = f;
-        rP[a] = q;
-    }
-}
-
 template <typename T> __device__ __forceinline__ void load12(const T *__restrict__ f, long N3, long v, T x[12]) {
 #pragma unroll
     for (int a = 0; a < 12; ++a) x[a] = f[a * N3 + v];
 }
 
-// Eq. TotDislocationDensity from the densities of one voxel (the projections row by row).
+// Eq. TotDislocationDensity from the densities of one voxel (the projections of Eqs. RhoForest / RhoParallel
+// row by row, rho_GNDen = 0).
 template <typename T>
 __device__ __forceinline__ double total_density(const MRConst &c, const T ssd[12], const T gs[12], const T ge[12],
                                                 const T gnd[12]) {
@@ -82,18 +65,24 @@ __global__ void __launch_bounds__(kMR) k_mr_harden(long N3, const T *__restrict_
                                                   MRConst c) {
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N3) return;
-    T s[12], a1[12], a2[12], rF[12], rP[12];
+    T s[12], a1[12], a2[12];
     load12(ssd, N3, v, s);
     load12(gs, N3, v, a1);
     load12(ge, N3, v, a2);
-    project(c, s, a1, a2, rF, rP);
     const MRScal<T> &k = scal<T>(c);
     T m = (T)0;
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
-        const T t = k.tp_c * sqrt(rP[a]);
+        T f = (T)0, q = (T)0;   // row a of Eqs. RhoForest / RhoParallel
+#pragma unroll
+        for (int b = 0; b < 12; ++b) {
+            const int i = 12 * a + b;
+            f += s[b] * tabv<T>(c, 0, i) + fabs(a1[b]) * tabv<T>(c, 1, i) + fabs(a2[b]) * tabv<T>(c, 0, i);
+            q += s[b] * tabv<T>(c, 2, i) + fabs(a1[b]) * tabv<T>(c, 3, i) + fabs(a2[b]) * tabv<T>(c, 2, i);
+        }
+        const T t = k.tp_c * sqrt(q);
         tpi[2 * (a * N3 + v)] = t;
-        tpi[2 * (a * N3 + v) + 1] = (T)1 / (k.tcut_c * sqrt(rF[a]));
+        tpi[2 * (a * N3 + v) + 1] = (T)1 / (k.tcut_c * sqrt(f));
         m = a == 0 ? t : fmin(m, t);
     }
     tref[v] = m;
@@ -149,7 +138,7 @@ __global__ void __launch_bounds__(kMR) k_mr_rates(long N3, const T *__restrict__
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMR) k_mr_update(int n, int lg, const int32_t *__restrict__ g,
+__global__ void __launch_bounds__(kMR, sizeof(T) == 4 ? 4 : 1) k_mr_update(int n, int lg, const int32_t *__restrict__ g,
                                                   const int32_t *__restrict__ g0, const T *__restrict__ gd,
                                                   const T *__restrict__ aux, const T *__restrict__ sig,
                                                   const T *__restrict__ Mtab, const T *__restrict__ vec,
@@ -224,7 +213,7 @@ __global__ void __launch_bounds__(kMR) k_mr_update(int n, int lg, const int32_t 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMR) k_mr_soften(long N3, int mode, const int32_t *__restrict__ gprev,
+__global__ void __launch_bounds__(kMR, sizeof(T) == 4 ? 4 : 1) k_mr_soften(long N3, int mode, const int32_t *__restrict__ gprev,
                                                   const int32_t *__restrict__ g, int lo, const T *__restrict__ ssd,
                                                   T *__restrict__ gs, T *__restrict__ ge, T *__restrict__ gnd,
                                                   double *__restrict__ kf, MRConst c) {
