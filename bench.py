@@ -471,7 +471,26 @@ def mr_companion(args, wl, g0, quat, torch, evp, pk):
                        "mixed_vs_fp64_macro_stress_rel_err_max": max(errs)}
         del s64
     del s
+    if not args.no_cpu_baseline:
+        out["cpu_oracle"] = mr_oracle_sample(wl, dt, 2)
     return out
+
+
+def mr_oracle_sample(wl, dt, iters_cap):
+    """The FP64 oracle on the same Ma-Roters increment (augmented Lagrangian), capped at `iters_cap` iterations:
+    the CPU rate beside the GPU's, in the same unit."""
+    import oracle as O
+    seeds, quat = workload_inputs(wl)
+    g0 = O.voronoi(wl.n, seeds)
+    st = O.State(wl.n, wl.grains, g0, quat, synth.ma_roters_material(), seed=wl.seed, tol=0.0, max_iter=iters_cap,
+                 allow_unconverged=1, scheme=1, al_scale=8.0, law=1)
+    t0 = time.perf_counter()
+    rc, s = st.increment(wl.dE33, dt)
+    t1 = time.perf_counter()
+    st.close()
+    return {"voxel_iters_per_s": wl.n ** 3 * s.iterations / (t1 - t0), "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"one {wl.n}^3 Ma-Roters increment capped at {s.iterations} augmented-Lagrangian iterations "
+                      f"(FP64, OpenMP over voxels; includes the initial local solve), {t1 - t0:.1f} s"}
 
 
 def al_companion(args, wl, g0, quat, mat, torch, evp, basic_hist):

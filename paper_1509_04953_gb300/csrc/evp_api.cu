@@ -478,7 +478,7 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
     const double mu0 = muV / h->cfg.al_scale, lam0 = (lamV + 2.0 * muV / 3.0) - 2.0 * mu0 / 3.0;
     const double a = lam0 + 2.0 * mu0, b = lam0, det = a * a - b * b;
     const int solve64 = h->prec != EVP_MIXED_FAST;
-    const int nb = al_blocks(N3);
+    const int nb = al_grid(N3, h->nsm, (int)sizeof(TA));
     double hs[14];
     int32_t hf[2];
     int nmax = 0, conv = 0, it;
@@ -494,7 +494,7 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
           CK(al_local<TA>(N3, (const TA *)h->epst, (const TA *)h->epse, (const TA *)h->tauc, h->g0, (TA *)h->sigk,
                           (TA *)h->lam, (TA *)h->pal, (const TA *)h->Stab, (const TA *)h->Sal, (const TA *)h->Mtab, mc,
                           lam0, mu0, tol_loc, h->cfg.newton_max, solve64, init, h->flags, h->partials, fac,
-                          refresh, h->st, mr_ptr<TA>(h))); }
+                          refresh, h->st, h->nsm, mr_ptr<TA>(h))); }
         { PROF(6, 1); CK(reduce_partials(h->partials, nb, 14, h->scal + 24, h->st)); }
         CK(cudaMemcpyAsync(hs, h->scal + 24, sizeof hs, cudaMemcpyDeviceToHost, h->st));
         CK(cudaMemcpyAsync(hf, h->flags, sizeof hf, cudaMemcpyDeviceToHost, h->st));

@@ -80,13 +80,15 @@ cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, con
                             MatConst mc, double tol, int maxit, int *flags, cudaStream_t s,
                             const int *skip = nullptr,
                             const double *tol_dev = nullptr);
-// Augmented-Lagrangian local step; part: 14 doubles per block (al_blocks blocks).
+// Augmented-Lagrangian local step, grid-stride over al_grid(N3, nsm, sizeof(TA)) blocks; part: 14 doubles per
+// block. al_blocks(N3) bounds the block count (for sizing).
 int al_blocks(long N3);
+int al_grid(long N3, int nsm, int tsize);
 template <typename TA>
 cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
                      const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
                      int maxit, int solve_fp64, int init, int *flags, double *part, void *fac, int refresh,
-                     cudaStream_t s, MRPtr<TA> mrp = MRPtr<TA>{});
+                     cudaStream_t s, int nsm, MRPtr<TA> mrp = MRPtr<TA>{});
 template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s);

@@ -520,8 +520,20 @@ template <int NV, typename T> __device__ __forceinline__ void block_sums(const T
     }
 }
 
+// The warp's sums of NV per-thread values (a five-level pairwise tree in the value type), added in FP64 by
+// lane 0 to row[0..NV) (one row per warp: no other warp touches it, so no barrier).
+template <int NV, typename T> __device__ __forceinline__ void warp_accumulate(const T (&v)[NV], double *row) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        T w = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if ((threadIdx.x & 31) == 0) row[q] += (double)w;
+    }
+}
+
 template <typename TA, typename TS, typename TF, bool MR = false>
-__global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__restrict__ epst, const TA *__restrict__ epse,
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_al_local(long N3, const TA *__restrict__ epst, const TA *__restrict__ epse,
                                                       const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
                                                       TA *__restrict__ sig, TA *__restrict__ lam, TA *__restrict__ pout,
                                                       const TA *__restrict__ Stab, const TA *__restrict__ Sal,
@@ -531,8 +543,16 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
                                                       int *__restrict__ flags, double *__restrict__ part,
                                                       TS *__restrict__ fac, int refresh, MRPtr<TA> mrp) {
     constexpr int NV = 14;
-    __shared__ double red[(kThreads / 32) * NV];
-    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    // grid-stride over tiles of blockDim voxels (block-uniform trip count): the block's warps run their tiles
+    // without waiting for one another; each warp sums its tile's values and lane 0 adds them, in FP64, to the
+    // warp's row of acc; the rows are summed once, at the end
+    __shared__ double acc[(kThreads / 32) * NV];
+    for (int i = threadIdx.x; i < (kThreads / 32) * NV; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    int t_fail = 0, t_mx = 0, t_it = 0, t_ev = 0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long v0 = (long)blockIdx.x * blockDim.x; v0 < N3; v0 += stride) {
+    const long v = v0 + threadIdx.x;
     const bool valid = v < N3;
     int r = 1, nev = 0;
     TA sums[NV];
@@ -640,10 +660,23 @@ __global__ void __launch_bounds__(kThreads) k_al_local(long N3, const TA *__rest
             sums[8 + c] = sg[c];
         }
     }
+    if (valid) {
+        const int its = r < 0 ? -r : r;
+        t_fail += r < 0;
+        t_mx = max(t_mx, its);
+        t_it += its;
+        t_ev += nev;
+    }
+    warp_accumulate<NV>(sums, acc + (threadIdx.x >> 5) * NV);
+    }
     // flags as in k_newton
-    const int its = valid ? (r < 0 ? -r : r) : 0;
-    block_solve_stats(valid && r < 0, its, its, nev, 0, flags);
-    block_sums<NV>(sums, red, part + NV * (long)blockIdx.x);
+    // (its barrier follows every warp's last acc update, so acc is complete after it)
+    block_solve_stats(t_fail, t_mx, t_it, t_ev, 0, flags);
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += acc[k * NV + threadIdx.x];
+        part[NV * (long)blockIdx.x + threadIdx.x] = t;
+    }
 }
 
 // Start of an increment: tau_c from the densities at t (frozen over the increment) and the
@@ -802,6 +835,7 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
 }
 
 int al_blocks(long N3) { return (int)((N3 + kThreads - 1) / kThreads); }
+int al_grid(long N3, int nsm, int tsize) { return std::min(al_blocks(N3), std::max(nsm, 1) * (tsize == 4 ? 3 : 2)); }
 
 cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
                             const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,
@@ -817,8 +851,8 @@ template <typename TA>
 cudaError_t al_local(long N3, const TA *epst, const TA *epse, const TA *tauc, const int32_t *g0, TA *sig, TA *lam, TA *p,
                      const TA *Stab, const TA *Sal, const TA *Mtab, MatConst mc, double lam0, double mu0, double tol,
                      int maxit, int solve_fp64, int init, int *flags, double *part, void *fac, int refresh,
-                     cudaStream_t s, MRPtr<TA> mrp) {
-    const int blocks = al_blocks(N3);
+                     cudaStream_t s, int nsm, MRPtr<TA> mrp) {
+    const int blocks = al_grid(N3, nsm, (int)sizeof(TA));
     const double sad = 1.0 / (2.0 * mu0), sbd = lam0 / (2.0 * mu0 * (3.0 * lam0 + 2.0 * mu0));
     const TA sa = (TA)sad, sb = (TA)sbd;
     const TA sa_lo = (TA)(sad - (double)sa), sb_lo = (TA)(sbd - (double)sb);   // S0 = (sa + sa_lo) I - (sb + sb_lo) J
@@ -870,7 +904,7 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
                                                 int32_t *, int, cudaStream_t, const int *, const TA *, MRPtr<TA>); \
     template cudaError_t al_local<TA>(long, const TA *, const TA *, const TA *, const int32_t *, TA *, TA *, TA *, \
                                       const TA *, const TA *, const TA *, MatConst, double, double, double, int, int, \
-                                      int, int *, double *, void *, int, cudaStream_t, MRPtr<TA>);                \
+                                      int, int *, double *, void *, int, cudaStream_t, int, MRPtr<TA>);           \
     template cudaError_t predictor<TA>(long, const TA *, const TA *, const TA *, TA *, TA *, MatConst, double,    \
                                        const double *, int, cudaStream_t);                                        \
     template cudaError_t state_update<TA>(long, const TA *, const TA *, const int32_t *, const TA *, TA *, TA *,  \
