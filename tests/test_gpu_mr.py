@@ -256,3 +256,29 @@ def test_mr_full_size_sampled_gnd_against_oracle_stencil(ev, mrmat):
         assert np.allclose(gs[:, v], DT * rs, rtol=0, atol=2e-3 * scale)
     assert worst < 2e-3            # FP32 stress: shear rates to ~1e-5, their differences to ~1e-3 of the field
     assert scale > 1e11
+
+
+def test_mr_coupled_run_on_the_refined_pf_grid_matches_oracle(ev, mrmat):
+    """Ma-Roters law with the phase field on the 2:1 grid: increments, nucleation on forced sites and PF steps
+    (sweep softening of the GND densities) against the oracle; grain ids bit-exact."""
+    n, G, seed = 16, 8, synth.BASE_SEED + 6
+    kw = dict(tol=1e-9, max_iter=3000, al_scale=8.0, pf_refine=2)
+    gpu, ref, _, _ = pair(ev, mrmat, n, G, seed, scheme="al", **kw)
+    for inc in range(2):
+        assert gpu.increment(-1e-3, DT)[0] == 0 and ref.increment(-1e-3, DT)[0] == 0
+    kap = np.full((1, n ** 3), 1e30)
+    kap[0, ::97] = 0.0                                   # a few forced sites (those on boundaries nucleate)
+    gpu.set("kappa", kap)
+    ref.field("kappa")[:] = kap
+    rc, nn = gpu.nucleate(0)
+    rco, nno = ref.nucleate(0)
+    assert nn == nno and nn > 0
+    for _ in range(2):
+        gpu.pf_step(5)
+        ref.pf_step(5)
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))
+        assert np.array_equal(gpu.get("gpf")[0], ref.ifield("gpf"))
+    assert rel(gpu.gnd()[2], ref.field("gnd")) < 1e-5
+    assert rel(gpu.get("k")[0], ref.field("k")[0]) < 1e-6
+    assert gpu.increment(-1e-3, DT)[0] == 0 and ref.increment(-1e-3, DT)[0] == 0
+    assert rel(gpu.get("sig"), ref.field("sig")) < 1e-6
