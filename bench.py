@@ -282,6 +282,8 @@ def native(args, ws, rank, local):
 
 
 ALG_BYTES_WORDS = None   # see hbm_bytes_per_voxel
+# measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one local-solve launch, per workload
+NEWTON_TRAFFIC = {(128, "mixed", True): 357.6e6}
 
 
 def hbm_bytes_per_voxel(kernel, n, T):
@@ -331,9 +333,12 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
                   "hbm": {"achieved": hbm, "peak": hpk, "unit": "GB/s", "frac": hbm_frac,
                           "bytes_per_launch": bytes_launch, "peak_source": pk_kind}}
         top = detail["hbm"] if hbm_frac >= alu_frac else detail["alu"]
+        # DRAM bytes of one local-solve launch (both passes) from the ncu capture of the current build at this
+        # workload (profiles/iteration_kernels_cu128_mixed.md, a late iteration: pass 1 357.5 MB, pass 2 0.1 MB)
+        traffic = NEWTON_TRAFFIC.get((wl.n, precision, reuse))
         return {"bound": "hbm" if hbm_frac >= alu_frac else "alu", "kernel": "newton",
                 "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"], "frac": top["frac"],
-                "traffic": None, "resources": detail,
+                "traffic": traffic, "traffic_unit": "bytes per launch", "resources": detail,
                 "note": "the local solve is reported against the resource it uses the larger fraction of. "
                         "Algorithmic flops: 1140 per residual+tangent evaluation, 544 per residual-only "
                         "evaluation, 80 per 6x6 LDL^T factorisation, 72 per pair of triangular solves, counted "
