@@ -283,7 +283,7 @@ def native(args, ws, rank, local):
 
 ALG_BYTES_WORDS = None   # see hbm_bytes_per_voxel
 # measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one local-solve launch, per workload
-NEWTON_TRAFFIC = {(128, "mixed", True): 357.6e6}
+NEWTON_TRAFFIC = {}   # re-measure after a change of the local-solve kernels (see profiles/)
 
 
 def hbm_bytes_per_voxel(kernel, n, T):
@@ -333,8 +333,8 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
                   "hbm": {"achieved": hbm, "peak": hpk, "unit": "GB/s", "frac": hbm_frac,
                           "bytes_per_launch": bytes_launch, "peak_source": pk_kind}}
         top = detail["hbm"] if hbm_frac >= alu_frac else detail["alu"]
-        # DRAM bytes of one local-solve launch (both passes) from the ncu capture of the current build at this
-        # workload (profiles/iteration_kernels_cu128_mixed.md, a late iteration: pass 1 357.5 MB, pass 2 0.1 MB)
+        # DRAM bytes of one local-solve launch (both passes) from an ncu capture of the current build at this
+        # workload (profiles/iteration_kernels_cu128_mixed.md), when one has been taken
         traffic = NEWTON_TRAFFIC.get((wl.n, precision, reuse))
         return {"bound": "hbm" if hbm_frac >= alu_frac else "alu", "kernel": "newton",
                 "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"], "frac": top["frac"],

@@ -199,8 +199,8 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *epsp = take(6 * N3 * T), *deps = take(6 * N3 * T), *rho = take(12 * N3 * T), *tauc = take(N3 * T);
     char *eta = take(K * M3 * T), *eta2 = take(K * M3 * T), *spec = take(6 * H * 2 * T);
     char *Stab = take(36 * (size_t)G * T), *Mtab = take(72 * (size_t)G * T);
-    // stored tangent factors: 21 words per voxel in planes of 16-byte vectors (24 FP32 / 22 FP64 words)
-    char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? (T == 4 ? 24 : 22) * N3 * T : 0);
+    // stored tangent factors: 21 words per voxel, in planes of 16-byte vectors and one scalar plane
+    char *fac = take(c->newton_mode == EVP_NEWTON_REUSE ? 21 * N3 * T : 0);
     char *wlist = take(c->newton_mode == EVP_NEWTON_REUSE ? 4 * N3 : 0);      // voxels left for the second pass
     const bool al = c->scheme == EVP_SCHEME_AL;
     char *Sal = take(al ? 36 * (size_t)G * T : 0), *lam = take(al ? 6 * N3 * T : 0), *pal = take(al ? 6 * N3 * T : 0);

@@ -85,40 +85,41 @@ template <typename TA> __device__ __forceinline__ void load_slip_pair(const TA *
     }
 }
 
-// Stored tangent factors (21 words per voxel) in planes of 16-byte vectors: plane k holds words
-// 4k..4k+3 (FP32, 6 planes) or 2k..2k+1 (FP64, 11 planes) of every voxel, so a voxel's factors come
-// in 6 (11) coalesced vector loads. Plane stride N3 vectors.
-template <typename TS> __host__ __device__ constexpr int factor_words() { return sizeof(TS) == 4 ? 24 : 22; }
+// Stored tangent factors (21 words per voxel): 16-byte vector planes, then one scalar plane for the last word.
+// FP32: planes 0-4 are float4 (words 4k..4k+3), plane 5 is float (word 20); FP64: planes 0-9 are double2 (words
+// 2k, 2k+1), plane 10 is double (word 20). Each plane holds N3 voxels, so a voxel's factors come in 5 (10)
+// coalesced vector loads and one scalar load, with no padding words.
+template <typename TS> __host__ __device__ constexpr int factor_words() { return 21; }
 template <typename TS> __device__ __forceinline__ void load_factors(const TS *__restrict__ fac, long N3, long v, TS F[21]) {
     if constexpr (sizeof(TS) == 4) {
         const float4 *f4 = reinterpret_cast<const float4 *>(fac);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 5; ++k) {
             const float4 t = f4[k * N3 + v];
-            F[4 * k] = t.x; if (4 * k + 1 < 21) F[4 * k + 1] = t.y;
-            if (4 * k + 2 < 21) F[4 * k + 2] = t.z; if (4 * k + 3 < 21) F[4 * k + 3] = t.w;
+            F[4 * k] = t.x; F[4 * k + 1] = t.y; F[4 * k + 2] = t.z; F[4 * k + 3] = t.w;
         }
+        F[20] = fac[20 * N3 + v];
     } else {
         const double2 *f2 = reinterpret_cast<const double2 *>(fac);
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
+        for (int k = 0; k < 10; ++k) {
             const double2 t = f2[k * N3 + v];
-            F[2 * k] = t.x; if (2 * k + 1 < 21) F[2 * k + 1] = t.y;
+            F[2 * k] = t.x; F[2 * k + 1] = t.y;
         }
+        F[20] = fac[20 * N3 + v];
     }
 }
 template <typename TS> __device__ __forceinline__ void store_factors(TS *__restrict__ fac, long N3, long v, const TS F[21]) {
     if constexpr (sizeof(TS) == 4) {
         float4 *f4 = reinterpret_cast<float4 *>(fac);
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
-            f4[k * N3 + v] = make_float4(F[4 * k], 4 * k + 1 < 21 ? F[4 * k + 1] : 0.f, 4 * k + 2 < 21 ? F[4 * k + 2] : 0.f,
-                                         4 * k + 3 < 21 ? F[4 * k + 3] : 0.f);
+        for (int k = 0; k < 5; ++k) f4[k * N3 + v] = make_float4(F[4 * k], F[4 * k + 1], F[4 * k + 2], F[4 * k + 3]);
     } else {
         double2 *f2 = reinterpret_cast<double2 *>(fac);
 #pragma unroll
-        for (int k = 0; k < 11; ++k) f2[k * N3 + v] = make_double2(F[2 * k], 2 * k + 1 < 21 ? F[2 * k + 1] : 0.0);
+        for (int k = 0; k < 10; ++k) f2[k * N3 + v] = make_double2(F[2 * k], F[2 * k + 1]);
     }
+    fac[20 * N3 + v] = F[20];
 }
 
 template <typename TA> struct Eval {
