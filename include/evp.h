@@ -244,6 +244,9 @@ int evp_adjoint_end(evp_handle *h, const double *gbar, double *grad, double tol,
  * 9 nucleate, 10 pf_step, 11 pf_soften, 12 pf_stats. ms and launches hold EVP_NCLASS entries. */
 #define EVP_NCLASS 13
 int evp_set_profiling(evp_handle *h, int on);
+/* Profile only the classes whose bits are set in mask (bit c = class c; 0 = off). The events cost a few
+ * microseconds of stream time per bracketed launch, so a timing run brackets only the class it reports. */
+int evp_set_profiling_mask(evp_handle *h, uint32_t mask);
 int evp_kernel_times(evp_handle *h, double *ms, int64_t *launches, int reset);
 int evp_launch_count(const evp_handle *h, int64_t *launches);
 /* Running totals over all increments: local Newton iterations (one 6x6 solve each) and

@@ -54,7 +54,7 @@ struct evp_handle {
     // instrumentation
     int64_t launches;
     int64_t newton_solves, newton_evals, newton_refreshes;
-    int prof;
+    uint32_t prof;   // profiled kernel classes (bit mask)
     double prof_ms[EVP_NCLASS];
     int64_t prof_n[EVP_NCLASS];
     struct Pend { int cls; cudaEvent_t a, b; };
@@ -131,7 +131,7 @@ struct ProfScope {
     cudaEvent_t a = nullptr;
     ProfScope(evp_handle *h_, int c, int nk) : h(h_), cls(c) {
         h->launches += nk;
-        if (h->prof) {
+        if (h->prof & (1u << c)) {
             if (h->npend >= evp_handle::kMaxPend) {
                 cudaStreamSynchronize(h->st);
                 prof_collect(h);
@@ -714,7 +714,13 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
 
 int evp_set_profiling(evp_handle *h, int on) {
     if (!h) return EVP_ERR_ARG;
-    h->prof = on ? 1 : 0;
+    h->prof = on ? (1u << EVP_NCLASS) - 1u : 0u;
+    return EVP_OK;
+}
+
+int evp_set_profiling_mask(evp_handle *h, uint32_t mask) {
+    if (!h) return EVP_ERR_ARG;
+    h->prof = mask & ((1u << EVP_NCLASS) - 1u);
     return EVP_OK;
 }
 

@@ -95,6 +95,7 @@ def load():
     L.evp_adjoint_step.argtypes = [vp, d, d, C.POINTER(Stats)]
     L.evp_adjoint_end.argtypes = [vp, vp, vp, d, i]
     L.evp_set_profiling.argtypes = [vp, i]
+    L.evp_set_profiling_mask.argtypes = [vp, C.c_uint32]
     L.evp_kernel_times.argtypes = [vp, vp, vp, i]
     L.evp_launch_count.argtypes = [vp, vp]
     L.evp_newton_counts.argtypes = [vp, vp, vp]
@@ -106,7 +107,8 @@ def load():
     L.evp_stress_residual.argtypes = [i, i, vp, vp, vp, vp, vp]
     for f in ("evp_workspace_bytes", "evp_init", "evp_increment", "drx_nucleate", "pf_step", "get_fields",
               "set_fields", "evp_fields_bytes", "evp_get_scalars", "evp_set_scalars", "evp_set_solver",
-              "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_kernel_times",
+              "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_set_profiling_mask",
+              "evp_kernel_times",
               "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual",
               "evp_adjoint_workspace_bytes", "evp_adjoint_begin", "evp_adjoint_step", "evp_adjoint_end",
               "evp_newton_refreshes", "evp_get_leff", "evp_set_leff"):
@@ -333,6 +335,13 @@ class Solver:
 
     def set_profiling(self, on=True):
         self._check("evp_set_profiling", load().evp_set_profiling(self.h, 1 if on else 0))
+
+    def set_profiling_classes(self, names):
+        """Bracket only the named kernel classes (see KERNEL_CLASSES) with CUDA events."""
+        mask = 0
+        for nm in names:
+            mask |= 1 << self.KERNEL_CLASSES.index(nm)
+        self._check("evp_set_profiling_mask", load().evp_set_profiling_mask(self.h, mask))
 
     def kernel_times(self, reset=False):
         ms = (C.c_double * 13)()
