@@ -1048,13 +1048,15 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
     int32_t ovf = 0;
     if (out) {
         const int nb = pf_stat_blocks(h->N3pf);
+        // every id in use is below next_id: only those words of the id bitmap are cleared and counted
+        const int words = std::min(h->bitmap_words, (h->next_id + 31) / 32);
         { PROF(12, 3);
         if (h->dbl)
-            CK(pf_stats_launch<double>(h->npf, h->ids, (double *)h->eta, h->gpf, h->kpf, h->pc, h->bitmap,
-                                       h->bitmap_words, h->partials, h->st));
+            CK(pf_stats_launch<double>(h->npf, h->ids, (double *)h->eta, h->gpf, h->kpf, h->pc, h->bitmap, words,
+                                       h->partials, h->st));
         else
-            CK(pf_stats_launch<float>(h->npf, h->ids, (float *)h->eta, h->gpf, h->kpf, h->pc, h->bitmap,
-                                      h->bitmap_words, h->partials, h->st));
+            CK(pf_stats_launch<float>(h->npf, h->ids, (float *)h->eta, h->gpf, h->kpf, h->pc, h->bitmap, words,
+                                      h->partials, h->st));
         CK(reduce_partials(h->partials, nb, 2, h->scal + 8, h->st));
         }
         double hs[2], ng = 0;

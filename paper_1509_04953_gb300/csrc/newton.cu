@@ -688,10 +688,10 @@ __global__ void __launch_bounds__(256) k_predictor(long N3, const TA *__restrict
                                                   double d3, double d4, double d5) {
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N3) return;
-    double rf = 0.0;
+    TA rf = (TA)0;   // in the field precision (the FP32 path keeps the FP64 pipe out)
 #pragma unroll
-    for (int a = 0; a < 12; ++a) rf += (double)rho[a * N3 + v];
-    tauc[v] = (TA)(mc.tau0 + mc.alpha_mu_b * sqrt(rf));
+    for (int a = 0; a < 12; ++a) rf += rho[a * N3 + v];
+    tauc[v] = (TA)mc.tau0 + (TA)mc.alpha_mu_b * sqrt(rf);
     const double dE[6] = {d0, d1, d2, d3, d4, d5};
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -742,18 +742,19 @@ __global__ void __launch_bounds__(kThreads) k_state_update(long N3, const TA *__
         deps[c * N3 + v] = tr - eo;
         epse[c * N3 + v] = tr - dt * ep[c];
     }
-    double rf = 0.0;
+    // Kocks-Mecking update in the field precision; k summed in FP64 (the nucleation decision compares it)
+    TA rf = (TA)0;
     TA r[12];
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
         r[a] = rho[a * N3 + v];
-        rf += (double)r[a];
+        rf += r[a];
     }
-    const double srf = sqrt(rf);
+    const TA srf = sqrt(rf), k1 = (TA)mc.k1, k2 = (TA)mc.k2;
     double kk = 0.0;
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
-        const TA nr = (TA)((double)r[a] + mc.dt * (mc.k1 * srf - mc.k2 * (double)r[a]) * (double)agd[a]);
+        const TA nr = r[a] + dt * (k1 * srf - k2 * r[a]) * agd[a];
         rho[a * N3 + v] = nr;
         kk += (double)nr;
     }

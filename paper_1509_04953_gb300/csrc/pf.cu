@@ -203,23 +203,26 @@ __global__ void __launch_bounds__(256) k_pf_stats(int n, const int32_t *__restri
             const uint32_t bit = 1u << (gi & 31);
             if (!(*(volatile uint32_t *)word & bit)) atomicOr(word, bit);
         }
-        double f0 = 0.25, S2 = 0.0, D = 0.0;
+        // per-voxel terms in the field precision (the FP32 path keeps the FP64 pipe out), sums in FP64
+        using A = T;
+        const A gam = sizeof(T) == 4 ? (A)pc.gam_f : (A)pc.gam;
+        A f0 = (A)0.25, S2 = (A)0, D = (A)0;
         for (int j = 0; j < K; ++j) {
             const int id = ids[j * N3 + v];
             if (id < 0) break;
-            const double e = (double)eta[j * N3 + v];
-            f0 += e * e * e * e / 4.0 - e * e / 2.0;
+            const A e = eta[j * N3 + v];
+            f0 += e * e * e * e / (A)4 - e * e / (A)2;
             S2 += e * e;
             if (id < G) D += e * e;
             for (int i2 = j + 1; i2 < K; ++i2) {
                 if (ids[i2 * N3 + v] < 0) break;
-                const double e2 = (double)eta[i2 * N3 + v];
-                f0 += pc.gam * e * e * e2 * e2;
+                const A e2 = eta[i2 * N3 + v];
+                f0 += gam * e * e * e2 * e2;
             }
         }
-        const double fdef = S2 > 1e-12 ? pc.Escale * kf[v] * D / S2 : 0.0;
+        const A fdef = S2 > (A)1e-12 ? (A)(pc.Escale * kf[v]) * D / S2 : (A)0;
         const Nbr nb = neighbours(n, v);
-        double grad = 0.0;
+        A grad = (A)0;
         for (int d = 2; d <= 6; d += 2) {   // x+, y+, z+
             const long w = nb.q[d];
             int pa = 0, pb = 0;
@@ -228,13 +231,14 @@ __global__ void __launch_bounds__(256) k_pf_stats(int n, const int32_t *__restri
                 const int ib = pb < K ? ids[pb * N3 + w] : -1;
                 const int ca = ia < 0 ? kEmpty : ia, cb = ib < 0 ? kEmpty : ib;
                 if (ca == kEmpty && cb == kEmpty) break;
-                double ea = 0.0, eb = 0.0;
-                if (ca <= cb) { ea = (double)eta[pa * N3 + v]; ++pa; }
-                if (cb <= ca) { eb = (double)eta[pb * N3 + w]; ++pb; }
+                A ea = (A)0, eb = (A)0;
+                if (ca <= cb) { ea = eta[pa * N3 + v]; ++pa; }
+                if (cb <= ca) { eb = eta[pb * N3 + w]; ++pb; }
                 grad += (eb - ea) * (eb - ea);
             }
         }
-        F = pc.m * f0 + 0.5 * pc.kappa * grad + fdef;
+        F = (double)((sizeof(T) == 4 ? (A)pc.m_f : (A)pc.m) * f0 +
+                     (A)0.5 * (sizeof(T) == 4 ? (A)pc.kappa_f : (A)pc.kappa) * grad + fdef);
     }
     const double sF = block_sum(F, red);
     const double sR = block_sum(rex, red);
