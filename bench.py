@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--mr-steps", type=int, default=2,
                     help="timed increments of the Ma-Roters companion (the paper's dislocation law; 0 = skip)")
     ap.add_argument("--mr-fp64-steps", type=int, default=2, help="FP64 Ma-Roters comparison increments (0 = skip)")
+    ap.add_argument("--fft-reps", type=int, default=20,
+                    help="repetitions of the FFT comparison against cuFFT (torch.fft; 0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
@@ -281,6 +283,8 @@ def native(args, ws, rank, local):
         res["pf_grid_2to1"] = pf2_companion(args, wl, g0, quat, mat, torch, evp, pk)
     if args.mr_steps > 0:
         res["ma_roters"] = mr_companion(args, wl, g0, quat, torch, evp, pk)
+    if args.fft_reps > 0:
+        res["fft_vs_cufft"] = fft_comparator(wl, torch, evp, args.fft_reps, pk)
     # FP64 companion run on the same seeded input
     n64 = args.warmup + args.steps if args.fp64_steps < 0 else args.fp64_steps
     if n64 > 0:
@@ -373,6 +377,49 @@ def memory_kernels(ktimes, wl, N3, precision, pk):
             continue
         gbs = bpv * N3 / (ms / 1e3 / n) / 1e9
         out[k] = {"avg_us": round(1e3 * ms / n, 2), "GB/s": round(gbs, 1), "frac": round(gbs / pk.get("hbm_gbs", 6800.0), 3)}
+    return out
+
+
+def fft_comparator(wl, torch, evp, reps, pk):
+    """The library's 3D real-to-complex and complex-to-real FFTs of six FP32 fields (the stress / strain
+    spectra of one fixed-point iteration, without the fused Green operator) against cuFFT through torch.fft,
+    same data, same stream, CUDA events over `reps` repetitions after a warm-up."""
+    n = wl.n
+    g = torch.Generator(device="cuda").manual_seed(wl.seed)
+    x = torch.randn((6, n, n, n), device="cuda", dtype=torch.float32, generator=g)
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        b.synchronize()
+        return 1e3 * a.elapsed_time(b) / reps
+
+    spec = evp.rfft3d(x)
+    ours_f = timed(lambda: evp.rfft3d(x))
+    ours_i = timed(lambda: evp.irfft3d(spec.clone()))
+    clone_us = timed(lambda: spec.clone())
+    cu_f = timed(lambda: torch.fft.rfftn(x, dim=(1, 2, 3)))
+    sc = torch.fft.rfftn(x, dim=(1, 2, 3))
+    # unnormalised inverse on both sides (norm="forward" leaves the inverse unscaled)
+    cu_i = timed(lambda: torch.fft.irfftn(sc, s=(n, n, n), dim=(1, 2, 3), norm="forward"))
+    err = (spec - sc).abs().max().item() / sc.abs().max().item()
+    ours_i -= clone_us   # the inverse consumes its input: a copy per repetition, subtracted
+    H = n // 2 + 1
+    b = 6 * (n ** 3 * 4 + n * n * H * 8) * 3   # three passes, each reading and writing the fields once
+    out = {"fields": 6, "n": n, "reps": reps,
+           "ours_forward_us": round(ours_f, 1), "ours_inverse_us": round(ours_i, 1),
+           "cufft_forward_us": round(cu_f, 1), "cufft_inverse_us": round(cu_i, 1),
+           "speedup_vs_cufft": round((cu_f + cu_i) / (ours_f + ours_i), 3),
+           "spectrum_rel_diff_vs_cufft": err,
+           "ours_forward_GB/s_3_passes": round(b / (ours_f * 1e-6) / 1e9, 1),
+           "note": "forward and inverse of six 128^3 FP32 fields; inside the fixed point the Green operator, the "
+                   "residual and the control ride in the z pass and the strain update in the x pass"}
     return out
 
 
