@@ -77,6 +77,11 @@ typedef struct {
                               and the interpolated driving force live there; see pf_step and drx_nucleate) */
     int law;               /* constitutive law, EVP_LAW_*: the power law with Kocks-Mecking hardening, or the
                               paper's Ma-Roters dislocation-density law (Sec. 2.2) */
+    double ref_scale;      /* EVP_SCHEME_BASIC: reference medium of the Green operator and of the mixed-BC
+                              correction = Voigt bulk modulus and shear modulus mu_Voigt / ref_scale (0 or 1: the
+                              Voigt average). The converged solution does not depend on it; the iteration converges
+                              while the reference is stiffer than half of every local stiffness (for copper up to
+                              ref_scale of about 1.45), faster the softer it is. In [0.5, 4] or 0. */
 } evp_config;
 #define EVP_LAW_POWER 0  /* gdot = gdot0 |tau/tau_c|^n sign(tau); rho^a by storage and dynamic recovery */
 #define EVP_LAW_MR 1     /* Sec. 2.2, Eqs. FlowRule, RhoForest, RhoParallel, SSDEvolution, GNDEvolution,

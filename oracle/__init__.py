@@ -37,7 +37,7 @@ class Config(C.Structure):
     _fields_ = [("n", C.c_int), ("grains", C.c_int), ("kmax", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("allow_unconverged", C.c_int), ("newton_tol", C.c_double),
                 ("newton_max", C.c_int), ("predictor", C.c_int), ("nthreads", C.c_int), ("scheme", C.c_int),
-                ("al_scale", C.c_double), ("pf_refine", C.c_int), ("law", C.c_int)]
+                ("al_scale", C.c_double), ("pf_refine", C.c_int), ("law", C.c_int), ("ref_scale", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -271,7 +271,7 @@ def loss_grad(n, grains, g0, quat, mat, seed, T, dE33, dt, target=None, want_gra
               max_iter=20000, adj_tol=1e-12, nthreads=0):
     """FP64 loss L = sum_t (<sigma33>_t - target_t)^2 over T increments, its adjoint gradient with
     respect to (k1, k2, tau0, n) and the stress-strain curve."""
-    cfg = Config(n, grains, 8, tol, max_iter, 0, 1e-13, 60, 1, nthreads, 0, 4.0, 1, 0)
+    cfg = Config(n, grains, 8, tol, max_iter, 0, 1e-13, 60, 1, nthreads, 0, 4.0, 1, 0, 1.0)
     p = make_params(mat)
     g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)
     q = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1)
@@ -290,7 +290,7 @@ class State:
 
     def __init__(self, n, grains, g0, quat, mat, seed, kmax=8, tol=1e-10, max_iter=1000,
                  allow_unconverged=0, newton_tol=1e-12, newton_max=50, predictor=1, nthreads=0, scheme=0,
-                 al_scale=4.0, pf_refine=1, law=0):
+                 al_scale=4.0, pf_refine=1, law=0, ref_scale=1.0):
         self.n, self.G, self.K = n, grains, kmax
         self.N3 = n ** 3
         self.r = 2 if pf_refine == 2 else 1
@@ -298,7 +298,7 @@ class State:
         self.N3pf = self.npf ** 3
         self.mat = mat
         self._cfg = Config(n, grains, kmax, tol, max_iter, allow_unconverged, newton_tol, newton_max,
-                           predictor, nthreads, scheme, al_scale, self.r, law)
+                           predictor, nthreads, scheme, al_scale, self.r, law, ref_scale)
         self.law = law
         self._p = make_params(mat)
         self._g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)

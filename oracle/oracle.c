@@ -1415,7 +1415,13 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
     const orc_params *p = &s->p;
     const int n = s->n;
     const long N3 = s->N3;
-    const double lam0 = lam_voigt(p), mu0 = mu_voigt(p);
+    /* reference medium of the Green operator and of the mixed-BC correction: the Voigt average, or a softer
+     * shear modulus mu_Voigt / ref_scale with the Voigt bulk modulus (the same converged solution; the scheme
+     * converges while the reference is stiffer than half of every local stiffness) */
+    const double lamV = lam_voigt(p), muV = mu_voigt(p);
+    const double rs = s->cfg.ref_scale > 0.0 ? s->cfg.ref_scale : 1.0;
+    const double mu0 = rs == 1.0 ? muV : muV / rs;
+    const double lam0 = rs == 1.0 ? lamV : lamV + 2.0 * muV / 3.0 - 2.0 * mu0 / 3.0;
     int status = 0;
     memset(out, 0, sizeof *out);
 
@@ -1444,7 +1450,7 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
         dE[2] = dE33;
         for (long i = 0; i < 6 * N3; ++i) epsk[i] = s->eps[i] + r * s->deps_prev[i];
     } else {
-        double nu0 = lam0 / (2.0 * (lam0 + mu0));
+        double nu0 = lamV / (2.0 * (lamV + muV));   /* the Voigt medium's lateral response */
         double g[6] = {-nu0 * dE33, -nu0 * dE33, dE33, 0, 0, 0};
         memcpy(dE, g, sizeof g);
         for (int I = 0; I < 6; ++I)

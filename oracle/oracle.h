@@ -47,6 +47,7 @@ typedef struct {
     double al_scale;           /* augmented Lagrangian: reference shear modulus = mu_Voigt / al_scale */
     int pf_refine;             /* phase-field grid per mechanics grid spacing: 1 (same grid) or 2 (Sec. 2.4) */
     int law;                   /* 0: power law + Kocks-Mecking; 1: Ma-Roters dislocation law (Sec. 2.2) */
+    double ref_scale;          /* basic scheme: reference shear modulus mu_Voigt / ref_scale, bulk kept (0 or 1: Voigt) */
 } orc_config;
 
 typedef struct {

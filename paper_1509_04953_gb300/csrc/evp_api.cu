@@ -169,6 +169,8 @@ int check_cfg(const evp_config *c, char *why, size_t wl) {
     if (!(c->newton_adapt >= 0.0)) return snprintf(why, wl, "newton_adapt must be >= 0"), EVP_ERR_ARG;
     if (c->pf_refine < 0 || c->pf_refine > 2) return snprintf(why, wl, "pf_refine must be 0, 1 or 2"), EVP_ERR_ARG;
     if (c->law != EVP_LAW_POWER && c->law != EVP_LAW_MR) return snprintf(why, wl, "unknown law %d", c->law), EVP_ERR_ARG;
+    if (!(c->ref_scale == 0.0 || (c->ref_scale >= 0.5 && c->ref_scale <= 4.0)))
+        return snprintf(why, wl, "ref_scale must be 0 or in [0.5, 4]"), EVP_ERR_ARG;
     if (c->law == EVP_LAW_MR && c->newton_mode == EVP_NEWTON_F32_TANGENT)
         return snprintf(why, wl, "EVP_NEWTON_F32_TANGENT covers the power law only"), EVP_ERR_ARG;
     if (c->newton_mode != EVP_NEWTON_EXACT && c->newton_mode != EVP_NEWTON_REUSE &&
@@ -807,8 +809,13 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
             CK(mr_harden<float>(N3, (const float *)h->rho, (const float *)h->gs, (const float *)h->ge, (float *)h->tpi,
                                 (float *)h->tauc, h->mrc, h->st));
     }
+    // reference medium of the basic scheme (Green operator, mixed-BC correction): Voigt, or the shear modulus
+    // mu_Voigt / ref_scale with the Voigt bulk modulus (the predictor above keeps the Voigt medium)
+    const double rs = h->cfg.ref_scale > 0.0 ? h->cfg.ref_scale : 1.0;
+    const double mu0r = rs == 1.0 ? mu0 : mu0 / rs;
+    const double lam0r = rs == 1.0 ? lam0 : lam0 + 2.0 * mu0 / 3.0 - 2.0 * mu0r / 3.0;
     // mixed-BC correction: (C0_uu)^-1 on u = {11, 22, 23, 13, 12}
-    const double a = lam0 + 2.0 * mu0, b = lam0, det = a * a - b * b;
+    const double a = lam0r + 2.0 * mu0r, b = lam0r, det = a * a - b * b;
     const int solve64 = h->prec != EVP_MIXED_FAST;
     const double ntol = h->cfg.newton_tol;
     int status = EVP_OK, it = 0, conv = 0, nmax = 0;
@@ -842,7 +849,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
         zc.flags = h->flags;
         zc.scal = h->scal;
         zc.p.N3 = (double)N3; zc.p.tau0 = h->p.tau0; zc.p.tol = h->cfg.tol; zc.p.a = a; zc.p.b = b; zc.p.det = det;
-        zc.p.mu0 = mu0; zc.p.ntol = ntol; zc.p.eta = h->cfg.newton_adapt; zc.p.max_iter = h->cfg.max_iter;
+        zc.p.mu0 = mu0r; zc.p.ntol = ntol; zc.p.eta = h->cfg.newton_adapt; zc.p.max_iter = h->cfg.max_iter;
         int queued = 0;
         while (true) {
             const int nb = std::min(kFpBatch, h->cfg.max_iter - queued);
@@ -866,7 +873,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                   { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
-                    CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip,
+                    CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0r, mu0r, h->partials, h->scal, h->st, skip,
                                      &zc)); }
                 } else {
                   { PROF(0, 1);
@@ -882,7 +889,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                   { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st, skip)); }
                   { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st, skip)); }
                   { PROF(3, 1);
-                    CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st, skip,
+                    CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0r, mu0r, h->partials, h->scal, h->st, skip,
                                     &zc)); }
                 }
                 // the strain correction arrives through the zero-frequency term: no offsets here

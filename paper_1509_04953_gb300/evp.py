@@ -41,7 +41,7 @@ class Config(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("allow_unconverged", C.c_int),
                 ("newton_tol", C.c_double), ("newton_max", C.c_int), ("predictor", C.c_int), ("max_ids", C.c_int),
                 ("newton_mode", C.c_int), ("scheme", C.c_int), ("al_scale", C.c_double),
-                ("newton_adapt", C.c_double), ("pf_refine", C.c_int), ("law", C.c_int)]
+                ("newton_adapt", C.c_double), ("pf_refine", C.c_int), ("law", C.c_int), ("ref_scale", C.c_double)]
 
 
 class Params(C.Structure):
@@ -130,7 +130,7 @@ SCHEMES = {"basic": 0, "al": 1}
 
 def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, allow_unconverged=0,
                 newton_tol=None, newton_max=50, predictor=1, max_ids=0, newton=None, scheme="basic",
-                al_scale=6.0, newton_adapt=None, pf_refine=1, law="power") -> Config:
+                al_scale=6.0, newton_adapt=None, pf_refine=1, law="power", ref_scale=1.0) -> Config:
     if newton_tol is None:
         newton_tol = 1e-12 if precision == "fp64" else 1e-5
     if newton is None:
@@ -146,7 +146,7 @@ def make_config(n, grains, precision="fp64", kmax=8, tol=1e-10, max_iter=1000, a
         newton_adapt = 0.0 if precision == "fp64" else 0.1
     return Config(n, grains, kmax, PRECISION[precision], tol, max_iter, allow_unconverged, newton_tol, newton_max,
                   predictor, max_ids, NEWTON_MODES[newton], SCHEMES[scheme], al_scale, newton_adapt, pf_refine,
-                  LAWS[law])
+                  LAWS[law], ref_scale)
 
 
 def make_params(mat) -> Params:

@@ -424,3 +424,21 @@ def test_errors_and_degenerate_cases(ev, mat):
     rc, st = t.increment(-1e-3, 1.0, check=False)
     assert rc == -4 and "not converged" in t.last_error()
     assert np.array_equal(t.get("sig"), sig0)
+
+
+def test_softer_reference_medium_fixed_iterations_match_oracle_fp64(ev, mat):
+    """The basic scheme with the reference shear modulus mu_Voigt / 1.3 follows the oracle iterate for iterate."""
+    n, G, seed = 16, 8, synth.BASE_SEED + 7
+    kw = dict(tol=0.0, max_iter=6, allow_unconverged=1)
+    seeds = synth.voronoi_seeds(n, G, seed)
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, seeds)
+    gpu = ev.Solver(n, G, g0, quat, mat, seed, precision="fp64", ref_scale=1.3, **kw)
+    ref = O.State(n, G, g0, quat, mat, seed=seed, ref_scale=1.3, **kw)
+    for inc in range(2):
+        rc, st = gpu.increment(-1e-3, 1.0)
+        rco, sto = ref.increment(-1e-3, 1.0)
+        assert rc == 1 and rco == 1
+        assert rel(st.sig_mean, sto.sig_mean) < FP64_TOL
+        for f in ("sig", "eps", "epsp", "rho"):
+            assert rel(gpu.get(f), ref.field(f)) < FP64_TOL, f

@@ -494,3 +494,25 @@ def test_augmented_lagrangian_homogeneous_crystal_matches_point_model(mat):
         rc, s = st.increment(-1e-3, 1.0)
         assert rc == 0
         assert abs(s.sig_mean[2] / hist[inc] - 1) < 1e-9
+
+
+def test_softer_reference_medium_reaches_the_same_solution_in_fewer_iterations(mat):
+    """The basic scheme's fixed point does not depend on the reference medium (Moulinec-Suquet): a softer shear
+    modulus mu_Voigt / 1.3, still stiffer than half of copper's largest shear stiffness C44, reaches the Voigt
+    medium's converged stresses, in fewer iterations."""
+    n, G = 16, 8
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, 8))
+    quat = synth.orientations(G, 8)
+    assert mat.mu / 1.3 > mat.C44 / 2
+    out = {}
+    for rs in (1.0, 1.3):
+        st = O.State(n, G, g0, quat, mat, 3, tol=1e-10, newton_tol=1e-13, max_iter=4000, ref_scale=rs)
+        its = []
+        for _ in range(3):
+            rc, s = st.increment(-1e-3, 1.0)
+            assert rc == 0
+            its.append(s.iterations)
+        out[rs] = (st.field("sig").copy(), st.field("eps").copy(), its)
+    assert np.abs(out[1.3][0] - out[1.0][0]).max() < 1e-7 * np.abs(out[1.0][0]).max()
+    assert np.abs(out[1.3][1] - out[1.0][1]).max() < 1e-7 * np.abs(out[1.0][1]).max()
+    assert sum(out[1.3][2]) < 0.85 * sum(out[1.0][2])
