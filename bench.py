@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
+    ap.add_argument("--ref-scale", type=float, default=1.0,
+                    help="basic scheme: reference shear modulus mu_Voigt / ref_scale (1 = Voigt); same solution")
+    ap.add_argument("--soft-ref-steps", type=int, default=2,
+                    help="timed increments of the companion with the softer reference medium (0 = skip)")
+    ap.add_argument("--soft-ref", type=float, default=1.3, help="its ref_scale")
     ap.add_argument("--tol64", type=float, default=1e-8, help="fixed-point tolerance of the FP64 path")
     ap.add_argument("--newton-tol", type=float, default=None,
                     help="local-solve tolerance (default: the library's per precision)")
@@ -209,7 +214,7 @@ def native(args, ws, rank, local):
     N3 = wl.n ** 3
     tol_main = args.tol64 if args.precision == "fp64" else args.tol
     mixed = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision, tol=tol_main, max_iter=5000,
-                       newton_adapt=args.newton_adapt, newton_tol=args.newton_tol)
+                       newton_adapt=args.newton_adapt, newton_tol=args.newton_tol, ref_scale=args.ref_scale)
     # warm-up (untimed)
     warm = run_steps(mixed, args.warmup, wl.dE33, wl.dt, wl.pf_steps, torch)
     # inside the timed region only the local solve (the roofline's kernel) is bracketed by CUDA events: events
@@ -252,6 +257,7 @@ def native(args, ws, rank, local):
                data="synthetic",
                config={"workload": wl.name, "n": wl.n, "grains": wl.grains, "precision": args.precision,
                        "tol": tol_main, "newton_tol": mixed.cfg.newton_tol, "newton_adapt": mixed.cfg.newton_adapt,
+                       "ref_scale": args.ref_scale,
                        "newton_mode": ["exact", "reuse", "f32_tangent"][mixed.cfg.newton_mode],
                        "dE33": wl.dE33, "pf_steps": wl.pf_steps,
                        "l2": "inputs larger than L2 (about 0.8 GB of fields per replica, no flush needed)",
@@ -277,6 +283,8 @@ def native(args, ws, rank, local):
     res["memory_bound_kernels"] = memory_kernels(ksplit, wl, N3, args.precision, pk)
     if args.fast_steps > 0:
         res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
+    if args.soft_ref_steps > 0:
+        res["softer_reference_medium"] = soft_ref_companion(args, wl, g0, quat, mat, torch, evp, warm + timed)
     if args.al_steps > 0:
         res["augmented_lagrangian"] = al_companion(args, wl, g0, quat, mat, torch, evp, warm + timed)
     if args.pf2_steps > 0:
@@ -297,7 +305,9 @@ def native(args, ws, rank, local):
 
 ALG_BYTES_WORDS = None   # see hbm_bytes_per_voxel
 # measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one local-solve launch, per workload
-NEWTON_TRAFFIC = {}   # re-measure after a change of the local-solve kernels (see profiles/)
+# (ncu, dram__bytes_read.sum + dram__bytes_write.sum; profiles/launches_cu128_mixed.md): pass 1 330.8 MB + pass 2
+# 58.4 MB at one iteration of the second increment; re-measure after a change of the local-solve kernels
+NEWTON_TRAFFIC = {(128, "mixed", True): 389.2e6}
 
 
 def hbm_bytes_per_voxel(kernel, n, T):
@@ -423,10 +433,30 @@ def fft_comparator(wl, torch, evp, reps, pk):
     return out
 
 
+def soft_ref_companion(args, wl, g0, quat, mat, torch, evp, main_hist):
+    """The same increments with the basic scheme's reference shear modulus mu_Voigt / soft_ref (Voigt bulk): the
+    same converged solution (macro stress compared with the main run's, increment by increment) in fewer
+    iterations; timed over the last soft_ref_steps increments."""
+    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision,
+                   tol=args.tol64 if args.precision == "fp64" else args.tol, max_iter=5000,
+                   newton_adapt=args.newton_adapt, newton_tol=args.newton_tol, ref_scale=args.soft_ref)
+    w = max(len(main_hist) - args.soft_ref_steps, 0)
+    hw = run_steps(s, w, wl.dE33, wl.dt, wl.pf_steps, torch)
+    h = run_steps(s, args.soft_ref_steps, wl.dE33, wl.dt, wl.pf_steps, torch)
+    evp_s = sum(r["evp_ms"] for r in h) / 1e3
+    step_s = sum(r["step_ms"] for r in h) / 1e3
+    errs = [abs(a["sig33"] - b["sig33"]) / abs(b["sig33"]) for a, b in zip(hw + h, main_hist)]
+    return {"ref_scale": args.soft_ref, "voxel_iters_per_s": wl.n ** 3 * sum(r["it"] for r in h) / evp_s,
+            "drx_increments_per_s": len(h) / step_s, "ms_per_step": 1e3 * step_s / len(h),
+            "fixed_point_iterations": [r["it"] for r in hw + h],
+            "main_run_iterations": [r["it"] for r in main_hist],
+            "macro_stress_rel_diff_vs_main_max": max(errs)}
+
+
 def fast_companion(args, wl, g0, quat, mat, torch, evp):
     """The mixed path with the 6x6 Newton solve in FP32 (EVP_MIXED_FAST), same input."""
     s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="mixed_fast", tol=args.tol, max_iter=5000,
-                   newton_adapt=args.newton_adapt)
+                   newton_adapt=args.newton_adapt, ref_scale=args.ref_scale)
     run_steps(s, 1, wl.dE33, wl.dt, wl.pf_steps, torch)
     h = run_steps(s, args.fast_steps, wl.dE33, wl.dt, wl.pf_steps, torch)
     evp_s = sum(r["evp_ms"] for r in h) / 1e3
@@ -441,7 +471,7 @@ def pf2_companion(args, wl, g0, quat, mat, torch, evp, pk):
     increments/s and the live cost of one PF step there, against its algorithmic bytes."""
     s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision=args.precision,
                    tol=args.tol64 if args.precision == "fp64" else args.tol, max_iter=5000,
-                   newton_adapt=args.newton_adapt, pf_refine=2)
+                   newton_adapt=args.newton_adapt, pf_refine=2, ref_scale=args.ref_scale)
     run_steps(s, 1, wl.dE33, wl.dt, wl.pf_steps, torch)
     s.set_profiling_classes(["pf_step"])
     s.kernel_times(reset=True)
@@ -577,7 +607,8 @@ def al_companion(args, wl, g0, quat, mat, torch, evp, basic_hist):
 
 
 def fp64_companion(args, wl, g0, quat, mat, nsteps, mixed_hist, torch, evp):
-    s64 = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="fp64", tol=args.tol64, max_iter=5000)
+    s64 = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="fp64", tol=args.tol64, max_iter=5000,
+                     ref_scale=args.ref_scale)
     h = run_steps(s64, nsteps, wl.dE33, wl.dt, wl.pf_steps, torch)
     N3 = wl.n ** 3
     m = mixed_hist[:nsteps]
