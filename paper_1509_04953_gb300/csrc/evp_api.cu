@@ -832,7 +832,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         : al_loop<float>(h, mc, dE, &it, &conv, &nmax, &err_eq, &err_bc, mean);
         it = it < 1 ? 1 : it;
     } else {
-        // iterations are queued in batches; the device control decides when to stop (see k_fp_check)
+        // iterations are queued in batches; the device control (the z pass's last CTA, fpctl.cuh) decides when to stop
         FpCtl hc{};
         for (int i = 0; i < 6; ++i) hc.dE[i] = dE[i];
         const bool adapt = h->cfg.newton_adapt > 0.0;
