@@ -352,7 +352,12 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
     const C t11 = s[0], t22 = s[1], t33 = s[2];
     const C t23 = cmk<C>(s[3].x * r2, s[3].y * r2), t13 = cmk<C>(s[4].x * r2, s[4].y * r2),
             t12 = cmk<C>(s[5].x * r2, s[5].y * r2);
-    {   // equilibrium residual |xi.sigma_hat|^2 at this frequency and, for 0 < kx < N/2, at its
+    const int h = N >> 1;
+    const bool nyq = kx == h || ky == h || kz == h;
+    // Where the Green operator is applied (not on a Nyquist plane, not at zero frequency) the residual comes from
+    // its v = sigma_hat n: |xi.sigma_hat|^2 = w^2 |f|^2 |v|^2, the same at the Hermitian partner -k
+    const bool fused = apply && !nyq && !(fx == 0 && fy == 0 && fz == 0);
+    if (!fused) {   // equilibrium residual |xi.sigma_hat|^2 at this frequency and, for 0 < kx < N/2, at its
         // Hermitian partner -k (whose signed frequency differs from -xi on Nyquist ky / kz planes)
         const T w = (T)(6.283185307179586476925 / N);
         const int nparts = partner ? 2 : 1;
@@ -371,8 +376,7 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
         for (int i = 0; i < 6; ++i) s[i] = cmk<C>(0, 0);
         return;
     }
-    const int h = N >> 1;
-    if (kx == h || ky == h || kz == h) {
+    if (nyq) {
         // -S0:sigma, S0 = (1/2mu0)(I - lam0/(3 lam0 + 2 mu0) J)
         const T a = (T)1 / ((T)2 * mu0), b = lam0 / ((T)2 * mu0 * ((T)3 * lam0 + (T)2 * mu0));
         const C tr = cmk<C>(s[0].x + s[1].x + s[2].x, s[0].y + s[1].y + s[2].y);
@@ -386,6 +390,12 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
     const C v2 = cmk<C>(t12.x * n1 + t22.x * n2 + t23.x * n3, t12.y * n1 + t22.y * n2 + t23.y * n3);
     const C v3 = cmk<C>(t13.x * n1 + t23.x * n2 + t33.x * n3, t13.y * n1 + t23.y * n2 + t33.y * n3);
     const C nv = cmk<C>(n1 * v1.x + n2 * v2.x + n3 * v3.x, n1 * v1.y + n2 * v2.y + n3 * v3.y);
+    {   // the residual of this frequency (and of its partner, counted twice)
+        const T w = (T)(6.283185307179586476925 / N);
+        const T f2 = (T)(fx * fx + fy * fy + fz * fz);
+        const T vv = v1.x * v1.x + v1.y * v1.y + v2.x * v2.x + v2.y * v2.y + v3.x * v3.x + v3.y * v3.y;
+        acc += (partner ? (T)2 : (T)1) * (w * w * f2) * vv;
+    }
     const T im = (T)1 / mu0, ih = (T)0.5 / mu0;
     const T c = (lam0 + mu0) / (mu0 * (lam0 + (T)2 * mu0));
     const T sq2 = (T)1.41421356237309504880;
