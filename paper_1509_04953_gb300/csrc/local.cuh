@@ -122,6 +122,46 @@ template <typename TS> __device__ __forceinline__ void store_factors(TS *__restr
     fac[20 * N3 + v] = F[20];
 }
 
+// The same factors staged through shared memory: prefetch_factors starts asynchronous copies of this thread's 21
+// words into its own slots (plane-major, blockDim.x threads per plane: the vector planes, then the scalar plane),
+// prefetched_factors waits for this thread's copies and reads them. Only the issuing thread reads its slots, so no
+// barrier is needed.
+template <typename TS> __device__ __forceinline__ void prefetch_factors(const TS *__restrict__ fac, long N3, long v, TS *sh) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    constexpr int W = sizeof(TS) == 4 ? 4 : 2, P = 20 / W;   // words per vector, vector planes
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(sh + (k * nt + t) * W);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(fac + (k * N3 + v) * W) : "memory");
+    }
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sh + P * nt * W + t);
+    if constexpr (sizeof(TS) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(fac + 20 * N3 + v) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(fac + 20 * N3 + v) : "memory");
+}
+template <typename TS> __device__ __forceinline__ void prefetched_factors(const TS *sh, TS F[21]) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const int t = threadIdx.x, nt = blockDim.x;
+    constexpr int W = sizeof(TS) == 4 ? 4 : 2, P = 20 / W;
+    if constexpr (sizeof(TS) == 4) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(sh);
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const float4 q = s4[k * nt + t];
+            F[4 * k] = q.x; F[4 * k + 1] = q.y; F[4 * k + 2] = q.z; F[4 * k + 3] = q.w;
+        }
+    } else {
+        const double2 *s2 = reinterpret_cast<const double2 *>(sh);
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const double2 q = s2[k * nt + t];
+            F[2 * k] = q.x; F[2 * k + 1] = q.y;
+        }
+    }
+    F[20] = sh[P * nt * W + t];
+}
+
 template <typename TA> struct Eval {
     TA r[6];
     TA K[21];

@@ -369,6 +369,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
     bool done = false;
+    // the stored factors are needed only after the residual: their copies start first, into this thread's slots
+    // of shared memory, and run under the other loads and the evaluation
+    __shared__ __align__(16) TS fsh[factor_words<TS>() * kThreads];
+    if (valid) prefetch_factors(fac, N3, v, fsh);
     if (valid) {
         const int g = g0[v];
         TA Sp[21];
@@ -379,14 +383,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
             etr[c] = epst[c * N3 + v];
             sg[c] = sig[c * N3 + v];
         }
-        TS F[21];
-        load_factors(fac, N3, v, F);
         const TA tc = tauc[v];
         EvalR<TA> e;
         if constexpr (MR)
             evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tc}, (TA)0, sg, mc, e);
         else
             evaluate_r<TA, 6>(Sp, Mtab + 72 * (long)g, etr, tc, drcp(tc), sg, mc, e);
+        TS F[21];
+        prefetched_factors(fsh, F);
         TA d[6];
         ldl_apply<TS, TA>(F, e.r, d);
         TA rd = (TA)0, dn = (TA)0, sn = (TA)0;
