@@ -575,7 +575,7 @@ def mr_oracle_sample(wl, dt, iters_cap):
     seeds, quat = workload_inputs(wl)
     g0 = O.voronoi(wl.n, seeds)
     st = O.State(wl.n, wl.grains, g0, quat, synth.ma_roters_material(), seed=wl.seed, tol=0.0, max_iter=iters_cap,
-                 allow_unconverged=1, scheme=1, al_scale=8.0, law=1)
+                 allow_unconverged=1, scheme=1, al_scale=8.0, law=1, nthreads=cpu_cores())
     t0 = time.perf_counter()
     rc, s = st.increment(wl.dE33, dt)
     t1 = time.perf_counter()
@@ -687,10 +687,17 @@ def cpu_cores():
 
 def cpu_baseline(wl):
     cores = cpu_cores()
-    r = oracle_sample(wl, 2)
-    return {"value": wl.n ** 3 * r["iters"] / r["evp_s"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one {wl.n}^3 increment capped at {r['iters']} fixed-point iterations (FP64, OpenMP over"
-                      f" voxels), {r['evp_s']:.1f} s"}
+    r = oracle_sample(wl, 2, nthreads=cores)   # every call sets its own OpenMP thread count
+    out = {"value": wl.n ** 3 * r["iters"] / r["evp_s"], "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one {wl.n}^3 increment capped at {r['iters']} fixed-point iterations (FP64, OpenMP over"
+                     f" voxels), {r['evp_s']:.1f} s"}
+    # the same on one thread, on the 64^3 / 64-grain configuration (a smaller bounded sample, same unit)
+    w64 = synth.WORKLOADS["cu64"]
+    r1 = oracle_sample(w64, 1, nthreads=1)
+    out["single_thread"] = {"value": w64.n ** 3 * r1["iters"] / r1["evp_s"], "unit": UNIT, "cores": 1,
+                            "sample": f"one {w64.n}^3 increment capped at {r1['iters']} fixed-point iteration, "
+                                      f"{r1['evp_s']:.1f} s"}
+    return out
 
 
 def reference(args, ws, rank):
