@@ -305,9 +305,9 @@ def native(args, ws, rank, local):
 
 ALG_BYTES_WORDS = None   # see hbm_bytes_per_voxel
 # measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one local-solve launch, per workload
-# (ncu, dram__bytes_read.sum + dram__bytes_write.sum; profiles/launches_cu128_mixed.md): pass 1 330.8 MB + pass 2
-# 58.4 MB at one iteration of the second increment; re-measure after a change of the local-solve kernels
-NEWTON_TRAFFIC = {(128, "mixed", True): 389.2e6}
+# (ncu, dram__bytes_read.sum + dram__bytes_write.sum averaged over 214 iterations of the second and third increments;
+# profiles/launches_cu128_mixed.md): pass 1 326.8 MB + pass 2 15.0 MB; re-measure after a change of these kernels
+NEWTON_TRAFFIC = {(128, "mixed", True): 341.8e6}
 
 
 def hbm_bytes_per_voxel(kernel, n, T):
