@@ -442,3 +442,34 @@ def test_softer_reference_medium_fixed_iterations_match_oracle_fp64(ev, mat):
         assert rel(st.sig_mean, sto.sig_mean) < FP64_TOL
         for f in ("sig", "eps", "epsp", "rho"):
             assert rel(gpu.get(f), ref.field(f)) < FP64_TOL, f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_faults_injected_on_the_host_return_a_status_and_leave_the_handle_usable(ev, mat, precision):
+    """Failure detection without a GPU fault: a NaN stress or negative densities set through the ABI make the
+    increment fail with a status (local Newton or non-finite residual), the state does not advance, and after a
+    good state is restored the same handle runs a normal increment. A NaN time step is rejected before any work."""
+    n, G, seed = 16, 8, synth.BASE_SEED + 8
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, seed))
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    s = ev.Solver(n, G, g0, synth.orientations(G, seed), mat, seed, precision=precision, tol=tol, max_iter=3000)
+    assert s.increment(-1e-3, 1.0)[0] == 0
+    good = {k: s.get(k) for k in ("sig", "rho")}
+    sc = s.scalars()
+    bad = good["sig"].copy()
+    bad[2, 123] = np.nan
+    s.set("sig", bad)
+    rc, st = s.increment(-1e-3, 1.0, check=False)
+    assert rc in (-3, -5)                                    # EVP_ERR_NEWTON or EVP_ERR_NONFINITE
+    assert np.array_equal(s.scalars()["E"], sc["E"])         # the macroscopic state did not advance
+    s.set("sig", good["sig"])
+    rho = good["rho"].copy()
+    rho[:, 77] = -1e12
+    s.set("rho", rho)
+    rc, st = s.increment(-1e-3, 1.0, check=False)
+    assert rc in (-3, -5)
+    s.set("rho", good["rho"])
+    with pytest.raises(ev.EVPError):
+        s.increment(-1e-3, float("nan"))
+    rc, st = s.increment(-1e-3, 1.0)
+    assert rc == 0 and np.isfinite(st.sig_mean[2]) and st.sig_mean[2] < 0
