@@ -1588,7 +1588,7 @@ int orc_increment(orc_state *s, double dE33, double dt, orc_stats *out) {
 
 
 /* ------------------------------------------------------------------------------------------
- * Differentiation (spec direction 3; the paper calibrates by hand, Sec. 3): gradient of
+ * Differentiation (the paper calibrates its constants by hand, Sec. 3): gradient of
  * L = sum_t (<sigma33>_t - target_t)^2 over T mechanical increments with respect to
  * theta = (k1, k2, tau0, n), by the discrete adjoint of the converged increments. Nucleation and
  * phase-field events are not part of this path (held fixed; none occur in its workloads).
