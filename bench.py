@@ -8,7 +8,7 @@ recrystallised fraction) and its own throughput.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl native|reference]
 
-Multi-GPU: the path has no exchange step in this build (replicas only), so each rank runs an
+Multi-GPU: the path has no exchange step (replicas only), so each rank runs an
 independent replica; the value is the sum over ranks divided by the slowest rank's time.
 """
 from __future__ import annotations
