@@ -92,6 +92,24 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft_reg(C
     }
 }
 
+// Item t of the radix-R1 pass -> (line l, j < M1). With M1 = 8 (N = 128) a half-warp spans two lines of 8 items;
+// lines l and l + 1 lie 2 LS = 18 banks apart (mod 32) and share a bank pair, lines l and l + 8 lie 16 apart and
+// share none. So within each group of 16 lines the half-warps take lines (l, l + 8); the lines past the last full
+// group keep the plain order. Any mapping of items to threads gives the same values.
+template <int N> __device__ __forceinline__ void pass1_item(int t, int nlines, int &l, int &j) {
+    constexpr int M1 = N / Shape<N>::R1;
+    if constexpr (M1 == 8 && Shape<N>::LS % 16 == 9) {
+        if (t < (nlines >> 4) * 16 * M1) {
+            const int hw = t >> 4, lane = t & 15;
+            l = ((hw >> 3) << 4) + (hw & 7) + ((lane >> 3) << 3);
+            j = lane & 7;
+            return;
+        }
+    }
+    l = t / M1;
+    j = t - l * M1;
+}
+
 // In-place transform of nlines padded lines (line l at buf + l*LS). tw[m] = exp(-2 pi i m / N),
 // m < N. Starts after and ends with a barrier. MAXIT >= ceil(nlines * (N/R1) / blockDim).
 template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *buf, int nlines, const C *tw) {
@@ -116,7 +134,8 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
         for (int it = 0; it < MAXIT; ++it) {
             const int t = threadIdx.x + it * blockDim.x;
             if (t < items) {
-                const int l = t / M1, j = t - l * M1;
+                int l, j;
+                pass1_item<N>(t, nlines, l, j);
 #pragma unroll
                 for (int r = 0; r < R1; ++r) v[it][r] = buf[l * LS + pad16(j + r * M1)];
             }
@@ -126,7 +145,8 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
         for (int it = 0; it < MAXIT; ++it) {
             const int t = threadIdx.x + it * blockDim.x;
             if (t < items) {
-                const int l = t / M1, j = t - l * M1;
+                int l, j;
+                pass1_item<N>(t, nlines, l, j);
                 dft_reg<R1, INV>(v[it]);
 #pragma unroll
                 for (int r = 0; r < R1; ++r) buf[l * LS + pad16(j * R1 + r)] = v[it][r];
