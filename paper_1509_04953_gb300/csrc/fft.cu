@@ -110,7 +110,8 @@ template <int N> __device__ __forceinline__ void pass1_item(int t, int nlines, i
     j = t - l * M1;
 }
 
-// In-place transform of nlines padded lines (line l at buf + l*LS). tw[m] = exp(-2 pi i m / N),
+// In-place transform of nlines padded lines (line l at buf + l*LS). tw[16 r + j] = exp(-2 pi i r j / N)
+// (see load_tw),
 // m < N. Starts after and ends with a barrier. MAXIT >= ceil(nlines * (N/R1) / blockDim).
 template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *buf, int nlines, const C *tw) {
     constexpr int R1 = Shape<N>::R1, R2 = Shape<N>::R2, LS = Shape<N>::LS;
@@ -161,7 +162,7 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
             for (int r = 0; r < R2; ++r) {
                 C a = buf[l * LS + pad16(j + 16 * r)];
                 if (r > 0) {
-                    C w = tw[r * j];
+                    C w = tw[16 * r + j];   // = exp(-2 pi i r j / N), r-major: a half-warp reads 16 in a row
                     if (INV) w.y = -w.y;
                     a = cmul(a, w);
                 }
@@ -175,19 +176,21 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
     }
 }
 
-// Twiddles exp(-2 pi i m/N), m < N, computed once per CTA into shared memory, in the precision of
-// the transform (the FP64 pipe is 1/58 of the FP32 rate on this GPU, so FP32 transforms avoid it).
+// Twiddles of the radix-R2 pass, computed once per CTA into shared memory in the precision of the transform
+// (the FP64 pipe is 1/58 of the FP32 rate on this GPU, so FP32 transforms avoid it): slot k = 16 r + j holds
+// exp(-2 pi i r j / N) for r < N/16, j < 16 (r j < N), so the 16 lanes of a half-warp, which differ in j, read
+// 16 consecutive slots (indexed by the product r j the stride-r reads hit the same banks).
 __device__ __forceinline__ void load_tw(float2 *tw_s, int N) {
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         float sn, cs;
-        sincospif(-2.0f * (float)k / (float)N, &sn, &cs);
+        sincospif(-2.0f * (float)((k >> 4) * (k & 15)) / (float)N, &sn, &cs);
         tw_s[k] = make_float2(cs, sn);
     }
 }
 __device__ __forceinline__ void load_tw(double2 *tw_s, int N) {
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         double sn, cs;
-        sincospi(-2.0 * (double)k / (double)N, &sn, &cs);
+        sincospi(-2.0 * (double)((k >> 4) * (k & 15)) / (double)N, &sn, &cs);
         tw_s[k] = make_double2(cs, sn);
     }
 }
