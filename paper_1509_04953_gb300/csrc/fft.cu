@@ -110,6 +110,21 @@ template <int N> __device__ __forceinline__ void pass1_item(int t, int nlines, i
     j = t - l * M1;
 }
 
+// Element r of a z-pass slab -> (z, column xl < TX) for the column loads, the Green-operator phase and the
+// stores. With TX = 8 a half-warp spans 8 columns of two planes; planes z and z + 1 put columns 0 and 7 on one bank
+// pair (line stride LS = 9 mod 16), planes z and z + 8 (in one 16-plane block) share none. Global accesses keep
+// 8 consecutive columns of a plane per half-warp row.
+template <int N, int TX> __device__ __forceinline__ void slab_item(int r, int &z, int &xl) {
+    if constexpr (TX == 8 && N % 16 == 0 && Shape<N>::LS % 16 == 9) {
+        const int hw = r >> 4, lane = r & 15;
+        z = ((hw >> 3) << 4) + (hw & 7) + ((lane >> 3) << 3);
+        xl = lane & 7;
+    } else {
+        z = r / TX;
+        xl = r % TX;
+    }
+}
+
 // In-place transform of nlines padded lines (line l at buf + l*LS). tw[16 r + j] = exp(-2 pi i r j / N)
 // (see load_tw),
 // m < N. Starts after and ends with a barrier. MAXIT >= ceil(nlines * (N/R1) / blockDim).
@@ -467,7 +482,8 @@ __global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::typ
     load_tw(tw, N);
     for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {   // TX, N powers of two: shifts
         const int f = t / (TX * N), r = t % (TX * N);
-        const int z = r / TX, xl = r % TX;
+        int z, xl;
+        slab_item<N, TX>(r, z, xl);
         cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx0 + xl);
     }
     if (nyq)
@@ -484,9 +500,11 @@ __global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::typ
         const int npts = (TX + (nyq ? 1 : 0)) * N;
         for (int t = threadIdx.x; t < npts; t += blockDim.x) {
             const bool reg = t < TX * N;
-            const int kz = reg ? t / TX : t - TX * N;
-            const int kx = reg ? kx0 + t % TX : N / 2;
-            const int l0 = reg ? t % TX : nf * TX, ls = reg ? TX : 1;   // line of field f: l0 + f*ls
+            int zr = 0, xr = 0;
+            if (reg) slab_item<N, TX>(t, zr, xr);
+            const int kz = reg ? zr : t - TX * N;
+            const int kx = reg ? kx0 + xr : N / 2;
+            const int l0 = reg ? xr : nf * TX, ls = reg ? TX : 1;   // line of field f: l0 + f*ls
             C s6[6];
             for (int f = 0; f < 6; ++f) s6[f] = buf[(l0 + f * ls) * LS + pad16(kz)];
             if (kx == 0 && ky == 0 && kz == 0 && mean6 != nullptr) {
@@ -505,7 +523,8 @@ __global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::typ
     if (mode == Z_INV || mode == Z_FWD_GAMMA_INV) block_fft<N, true, MI>(buf, nlines, tw);
     for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
         const int f = t / (TX * N), r = t % (TX * N);
-        const int z = r / TX, xl = r % TX;
+        int z, xl;
+        slab_item<N, TX>(r, z, xl);
         spec[f * fstride + z * plane + (long)ky * Hx + kx0 + xl] = buf[(f * TX + xl) * LS + pad16(z)];
     }
     if (nyq)
