@@ -64,7 +64,9 @@ template <int M> __host__ __device__ constexpr int brev_c(int i) {
 
 // Length-R DFT of x held in registers (radix-2 network with constant twiddles). The forward
 // twiddle W_{2h}^p = exp(-2 pi i p / 2h) = (cos(pi m/8), -sin(pi m/8)), m = 16 p / 2h, with
-// sin(pi m/8) = cos(pi (m + 12)/8). INV uses the conjugate.
+// sin(pi m/8) = cos(pi (m + 12)/8). INV uses the conjugate. The twiddles 1 (m = 0) and -i (m = 4; +i inverse)
+// are applied as a copy and a swap with a sign change: without fast-math the compiler keeps the products by
+// the zero component, and these are 22 of the 32 twiddles of a 16-point DFT (10 of 12 at 8 points).
 template <int R, bool INV, typename C> __device__ __forceinline__ void dft_reg(C (&x)[R]) {
     using T = decltype(C::x);
     constexpr int LR = Log2<R>::v;
@@ -80,10 +82,17 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft_reg(C
 #pragma unroll
             for (int p = 0; p < h; ++p) {
                 const int m = p * (16 / (2 * h));
-                const T wc = (T)cos16(m);
-                const T ws = INV ? (T)cos16((m + 12) & 15) : -(T)cos16((m + 12) & 15);
                 const C b0 = x[g + p + h];
-                const C b = cmk<C>(b0.x * wc - b0.y * ws, b0.x * ws + b0.y * wc);
+                C b;
+                if (m == 0) {
+                    b = b0;
+                } else if (m == 4) {
+                    b = INV ? cmk<C>(-b0.y, b0.x) : cmk<C>(b0.y, -b0.x);
+                } else {
+                    const T wc = (T)cos16(m);
+                    const T ws = INV ? (T)cos16((m + 12) & 15) : -(T)cos16((m + 12) & 15);
+                    b = cmk<C>(b0.x * wc - b0.y * ws, b0.x * ws + b0.y * wc);
+                }
                 const C a = x[g + p];
                 x[g + p] = cadd(a, b);
                 x[g + p + h] = csub(a, b);
@@ -238,7 +247,7 @@ template <int N, typename T> __host__ __device__ constexpr int z_threads() { ret
 // x pass, real -> half spectrum. CTA = RP pairs of rows (y even, y+1) of one (field, z).
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k_fft_x_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out,
+__global__ void __launch_bounds__(kThreads, N >= 64 && N <= 128 ? (sizeof(T) == 4 ? 6 : 3) : 1) k_fft_x_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out,
                                                        long npairs, const int *__restrict__ skip) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
@@ -459,7 +468,7 @@ __device__ __forceinline__ void gamma_point(C s[6], int kx, int ky, int kz, int 
 // z pass: CTA = (ky, kx tile); nf fields x TX columns x N planes in shared memory.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(z_threads<N, T>()) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
+__global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 ? 3 : 1) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
                                                    T mu0, double *__restrict__ partials, double *__restrict__ mean6, const int *__restrict__ skip,
                                                    ZCtl zc) {
     if (skip != nullptr && *skip) return;   // the fixed point has converged
