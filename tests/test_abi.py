@@ -60,6 +60,37 @@ def test_workspace_bytes_validates_config(lib):
         assert lib.evp_workspace_bytes(C.byref(c), C.byref(nb)) == -1
 
 
+def test_workspace_bytes_validates_solver_and_law_options(lib):
+    """The scheme, law, reference-medium and Newton-mode fields are checked on the host: out-of-range values
+    and combinations the library does not implement return EVP_ERR_ARG with a reason; valid ones are accepted."""
+    import math
+    from paper_1509_04953_gb300 import evp
+    nb = C.c_size_t(0)
+
+    def rc_of(**kw):
+        fields = {k: kw.pop(k) for k in list(kw) if k in ("law_code", "newton_code", "scheme_code")}
+        c = evp.make_config(16, 8, **kw)
+        if "law_code" in fields:
+            c.law = fields["law_code"]
+        if "newton_code" in fields:
+            c.newton_mode = fields["newton_code"]
+        if "scheme_code" in fields:
+            c.scheme = fields["scheme_code"]
+        return lib.evp_workspace_bytes(C.byref(c), C.byref(nb))
+
+    for ok in (dict(law="mr"), dict(law="mr", scheme="al", al_scale=8.0), dict(ref_scale=0.0), dict(ref_scale=0.5),
+               dict(ref_scale=1.3), dict(ref_scale=4.0), dict(scheme="al", al_scale=1.0), dict(pf_refine=2),
+               dict(precision="mixed", newton="reuse", newton_adapt=0.0)):
+        assert rc_of(**ok) == 0, ok
+    for bad in (dict(law_code=2), dict(law_code=-1), dict(ref_scale=0.49), dict(ref_scale=4.01),
+                dict(ref_scale=-1.0), dict(ref_scale=math.nan), dict(scheme_code=2), dict(scheme="al", al_scale=0.5),
+                dict(scheme="al", al_scale=math.nan), dict(pf_refine=3), dict(pf_refine=-1), dict(newton_adapt=-0.1),
+                dict(newton_code=3),
+                dict(law="mr", precision="fp64", newton="f32_tangent"),      # FP32 tangent: power law only
+                dict(precision="mixed", newton="f32_tangent")):              # FP32 tangent: FP64 path only
+        assert rc_of(**bad) == -1, bad
+
+
 def test_init_rejects_bad_arguments_before_touching_the_device(lib):
     """Argument errors are returned (with a reason) before any CUDA call is made."""
     import numpy as np
