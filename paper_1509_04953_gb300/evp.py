@@ -105,13 +105,14 @@ def load():
     L.evp_irfft3d.argtypes = [i, i, i, vp, vp, vp]
     L.evp_residual_scratch_bytes.argtypes = [i, i, C.POINTER(sz)]
     L.evp_stress_residual.argtypes = [i, i, vp, vp, vp, vp, vp]
+    L.evp_stress_residual_noalloc.argtypes = [i, i, vp, vp, vp, vp]
     for f in ("evp_workspace_bytes", "evp_init", "evp_increment", "drx_nucleate", "pf_step", "get_fields",
               "set_fields", "evp_fields_bytes", "evp_get_scalars", "evp_set_scalars", "evp_set_solver",
               "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_set_profiling_mask",
               "evp_kernel_times",
               "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual",
               "evp_adjoint_workspace_bytes", "evp_adjoint_begin", "evp_adjoint_step", "evp_adjoint_end",
-              "evp_newton_refreshes", "evp_get_leff", "evp_set_leff"):
+              "evp_newton_refreshes", "evp_get_leff", "evp_set_leff", "evp_stress_residual_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L

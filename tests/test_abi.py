@@ -35,6 +35,15 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_binding_declares_argument_types_for_every_symbol(lib):
+    """The Python binding gives every declared function its argument and result types, so that ctypes never
+    passes a device pointer or a size through its default 32-bit int conversion."""
+    for name in header_functions():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert fn.restype is not None or name == "evp_destroy", name
+
+
 def test_workspace_bytes_validates_config(lib):
     from paper_1509_04953_gb300 import evp
     cfg = evp.make_config(16, 8)
