@@ -287,14 +287,19 @@ def test_homogeneous_crystal_matches_point_model(mat):
     assert np.allclose(st.field("rho")[:, 0], pm["rho"], rtol=1e-9)
 
 
-def test_elastic_laminate_closed_form(mat):
+@pytest.mark.parametrize("scheme,ref_scale", [(0, 1.0), (1, 1.0), (0, 1.3)],
+                         ids=["basic", "augmented_lagrangian", "basic_softer_reference"])
+def test_elastic_laminate_closed_form(mat, scheme, ref_scale):
+    """P5 under every fixed-point variant: the basic scheme, the augmented Lagrangian (Sec. 2.1) and a softer
+    isotropic reference medium all reach the laminate's closed-form strain and stress."""
     import dataclasses
     m2 = dataclasses.replace(mat, gdot0=0.0)
     n = 8
     q = synth.orientations(2, 31)
     z = np.arange(n ** 3) // (n * n)
     g0 = (z >= n // 2).astype(np.int32)
-    st = O.State(n, 2, g0, q, m2, seed=1, tol=1e-13, max_iter=5000)
+    st = O.State(n, 2, g0, q, m2, seed=1, tol=1e-13, max_iter=5000, scheme=scheme, al_scale=6.0,
+                 ref_scale=ref_scale)
     E33 = -1e-3
     rc, s = st.increment(E33, 1.0)
     assert rc == 0
