@@ -144,6 +144,28 @@ def test_augmented_lagrangian_converges_to_the_basic_solution(ev, mat, precision
     assert rel(b.get("sig"), a.get("sig")) < (1e-6 if precision == "fp64" else 1e-3)
 
 
+def test_full_size_headline_increment_against_oracle_checks(ev, mat):
+    """The workload the throughput is quoted on: 128^3, 256 grains, mixed precision, the bench's solver settings
+    and launch configuration. After the first converged increment the FP64 oracle confirms, on the GPU's fields,
+    equilibrium (its own FFT of the stress), the mixed boundary conditions and, at 400 sampled voxels, the local
+    implicit update and the state update (tests/increment_checks.py). Tolerances: the local solve stops at a
+    relative 1e-5 in FP32 (stress within 2e-4 of the largest stress); the power law's exponent 10 turns that into
+    about 10x on the shear rates (plastic strain and densities within 2e-3)."""
+    from increment_checks import check_first_increment
+    wl = synth.WORKLOADS["cu128"]
+    n, G, seed, tol = wl.n, wl.grains, wl.seed, 1e-6
+    seeds = synth.voronoi_seeds(n, G, seed)
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, seeds)
+    gpu = ev.Solver(n, G, g0, quat, mat, seed, precision="mixed", tol=tol, max_iter=5000)
+    rc, st = gpu.increment(wl.dE33, wl.dt)
+    assert rc == 0 and st.iterations > 1
+    fields = {f: gpu.get(f) for f in ("sig", "eps", "epsp", "rho")}
+    fields["k"] = gpu.get("k")[0]
+    sample = np.random.default_rng(5).choice(n ** 3, 400, replace=False)
+    check_first_increment(mat, quat, g0, n, wl.dt, tol, fields, st.sig_mean, sample, loc_tol=2e-4, state_tol=2e-3)
+
+
 def test_converged_increments_match_oracle_fp64(ev, mat):
     n, G, seed = 16, 8, synth.BASE_SEED
     kw = dict(tol=1e-9, max_iter=3000)

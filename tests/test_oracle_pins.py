@@ -287,6 +287,28 @@ def test_homogeneous_crystal_matches_point_model(mat):
     assert np.allclose(st.field("rho")[:, 0], pm["rho"], rtol=1e-9)
 
 
+@pytest.mark.parametrize("n,G", [(16, 8), (32, 27)])
+def test_converged_increment_checks_hold_for_the_oracle(mat, n, G):
+    """The any-size checks that the GPU's full-size increment is held to (tests/increment_checks.py) hold for the
+    oracle's own converged first increment to round-off: equilibrium within the tolerance, zero stress-controlled
+    means, and at sampled voxels the local update, plastic strain, densities and k."""
+    from increment_checks import check_first_increment
+    seed = synth.BASE_SEED + 2
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, seed))
+    st = O.State(n, G, g0, quat, mat, seed=seed, tol=1e-6, max_iter=5000)
+    rc, s = st.increment(-1e-3, 1.0)
+    assert rc == 0
+    fields = {f: st.field(f) for f in ("sig", "eps", "epsp", "rho")}
+    fields["k"] = st.field("k")[0]
+    sample = np.random.default_rng(3).choice(n ** 3, 200, replace=False)
+    err = check_first_increment(mat, quat, g0, n, 1.0, 1e-6, fields, s.sig_mean, sample, 1e-9, 1e-9, eq_factor=1.0)
+    assert err > 1e-8      # converged to the tolerance, not far below it
+    # a wrong time step in the state update is caught
+    with pytest.raises(AssertionError):
+        check_first_increment(mat, quat, g0, n, 2.0, 1e-6, fields, s.sig_mean, sample, 1e-9, 1e-9)
+
+
 @pytest.mark.parametrize("scheme,ref_scale", [(0, 1.0), (1, 1.0), (0, 1.3)],
                          ids=["basic", "augmented_lagrangian", "basic_softer_reference"])
 def test_elastic_laminate_closed_form(mat, scheme, ref_scale):
