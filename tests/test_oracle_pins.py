@@ -418,6 +418,47 @@ def test_pf_boundary_velocity_is_mobility_times_driving_force(mat, lfac, tol):
     assert abs(v / Ep - 1.0) < tol
 
 
+def test_pf_sweep_softening_and_recrystallised_fraction(mat):
+    """Reading C14 (Eq. UpdateGND applied to swept material) and the statistics of Sec. 2.4 on a moving flat
+    rex/def slab: X_rex and n_grains of the start are the construction's (width/n, 2 grains); during one call the
+    recrystallised slab grows; exactly the voxels whose grain turned from deformed to recrystallised have their
+    densities scaled by s_soften, once, with k their sum; every other voxel keeps its densities bitwise; X_rex
+    grows by the swept count over N^3; a second call does not soften those voxels again."""
+    n, width = 32, 11
+    st = slab_state(mat, n, width, rex=True)
+    N3 = n ** 3
+    rc, ps = st.pf_step(0)
+    assert ps.n_grains == 2 and ps.X_rex == width / n
+    st.pf_step(60)                                   # relax the sharp start (no stored energy yet)
+    Esc = mat.zeta * mat.mu * 1e6 * mat.b ** 2 * mat.dx / mat.omega_gb
+    v = np.arange(N3)
+    pattern = (1.0 + np.arange(12)[:, None] / 12.0) * (1.0 + (v % 5)[None, :] / 10.0)
+    rho = st.field("rho")
+    rho[:] = pattern * (0.3 / Esc) / pattern.sum(axis=0)[None, :].mean()
+    st.field("k")[0][:] = rho.sum(axis=0)
+    G = 2
+    g0 = st.ifield("g").copy()
+    rho0 = rho.copy()
+    _, ps0 = st.pf_step(0)
+    rc, ps1 = st.pf_step(150)
+    g1 = st.ifield("g").copy()
+    swept = (g0 < G) & (g1 >= G)
+    assert swept.sum() >= 2 * n * n                 # both boundaries moved at least one plane
+    assert not np.any((g0 >= G) & (g1 < G))          # no recrystallised voxel returned to the deformed grain
+    rho1 = st.field("rho").copy()
+    assert np.array_equal(rho1[:, swept], mat.s_soften * rho0[:, swept])
+    assert np.array_equal(rho1[:, ~swept], rho0[:, ~swept])
+    k1 = st.field("k")[0]
+    assert np.allclose(k1[swept], rho1[:, swept].sum(axis=0), rtol=1e-14, atol=0)
+    assert ps1.X_rex == pytest.approx(ps0.X_rex + swept.sum() / N3, abs=1e-15)
+    assert ps1.X_rex == pytest.approx((g1 >= G).mean(), abs=1e-15) and ps1.n_grains == 2
+    st.pf_step(1)                                    # the swept voxels are recrystallised now: no second softening
+    g2 = st.ifield("g")
+    rho2 = st.field("rho")
+    again = swept & (g2 >= G)
+    assert np.array_equal(rho2[:, again], rho1[:, again])
+
+
 def test_pf_energy_nonincreasing(mat):
     n, G = 12, 6
     seeds = synth.voronoi_seeds(n, G, 8)
