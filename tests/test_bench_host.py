@@ -1,0 +1,74 @@
+"""Host logic of bench.py on CPU: the roofline arithmetic of the local solve and the memory-bound passes, and the
+clock sampler's parsing of nvidia-smi output (a stand-in nvidia-smi on PATH prints fixed samples)."""
+import os
+import stat
+import time
+import types
+
+import pytest
+
+
+def test_local_solve_roofline_counts_164_bytes_per_voxel_with_stored_factors():
+    import bench
+    n = 128
+    N3 = n ** 3
+    wl = types.SimpleNamespace(n=n)
+    ms, launches = 10.0, 100                       # 100 launches of 0.1 ms
+    out = bench.roofline("newton", {"newton": (ms, launches)}, wl, N3, iters=100, solves=N3 * 100,
+                         evals=N3 * 100, pk={"hbm_gbs": 6000.0}, pk_kind="measured", precision="mixed",
+                         facs=0, reuse=True)
+    hbm = out["resources"]["hbm"]
+    assert hbm["bytes_per_launch"] == 164 * N3      # eps_tr 6, sigma 6, tau_c 1, factors 21, sigma out 6; g0
+    assert hbm["achieved"] == pytest.approx(164 * N3 / 1e-4 / 1e9)
+    assert hbm["frac"] == pytest.approx(hbm["achieved"] / 6000.0)
+    assert out["bound"] == "hbm" and out["frac"] == pytest.approx(hbm["frac"])
+    assert out["traffic"] == bench.NEWTON_TRAFFIC[(128, "mixed", True)]
+    # FP32 pipe: residual-only evaluations with tangent reuse, FP32 triangular solves
+    alu = out["resources"]["alu"]
+    assert alu["pipe"] == "fp32"
+    assert alu["flops_fp32"] == bench.NEWTON_FLOPS_RESID * N3 * 100 + bench.NEWTON_FLOPS_SOLVE * N3 * 100
+    # without stored factors the exact Newton reads 19 words
+    ex = bench.roofline("newton", {"newton": (ms, launches)}, wl, N3, 100, N3 * 100, N3 * 100, {"hbm_gbs": 6000.0},
+                        "measured", "mixed", reuse=False)
+    assert ex["resources"]["hbm"]["bytes_per_launch"] == (19 * 4 + 4) * N3
+
+
+def test_fft_pass_bytes_follow_the_half_spectrum():
+    import bench
+    n, T = 128, 4
+    H = (n // 2 + 1) / n
+    assert bench.hbm_bytes_per_voxel("fft_x_r2c", n, T) == pytest.approx((6 + 12 * H) * T)
+    for k in ("fft_y_fwd", "fft_z_gamma", "fft_y_inv"):
+        assert bench.hbm_bytes_per_voxel(k, n, T) == pytest.approx(24 * H * T)
+    assert bench.hbm_bytes_per_voxel("fft_x_c2r_update", n, T) == pytest.approx((12 * H + 12) * T)
+    m = bench.memory_kernels({"fft_y_fwd": (2.0, 100)}, types.SimpleNamespace(n=n), n ** 3, "mixed",
+                             {"hbm_gbs": 5000.0})
+    gbs = 24 * H * T * n ** 3 / 20e-6 / 1e9
+    assert m["fft_y_fwd"]["avg_us"] == 20.0 and m["fft_y_fwd"]["GB/s"] == pytest.approx(gbs, abs=0.05)
+
+
+def test_clock_sampler_reads_median_clock_and_throttle_reasons(tmp_path, monkeypatch):
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    lines = ["0, 2070, 2070, 350.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1980, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 410.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage line"]
+    fake.write_text("#!/bin/sh\n" + "".join(f"echo '{ln}'\n" for ln in lines) + "exec sleep 30\n")
+    fake.chmod(fake.stat().st_mode | stat.S_IEXEC)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    cs = bench.ClockSampler(0)
+    cs.start()
+    time.sleep(0.5)
+    out = cs.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["power_w_max"] == 900.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    import bench
+    monkeypatch.setenv("PATH", str(tmp_path))
+    cs = bench.ClockSampler(0)
+    cs.start()
+    assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
