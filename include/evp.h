@@ -252,7 +252,12 @@ int evp_set_profiling(evp_handle *h, int on);
 /* Profile only the classes whose bits are set in mask (bit c = class c; 0 = off). The events cost a few
  * microseconds of stream time per bracketed launch, so a timing run brackets only the class it reports. */
 int evp_set_profiling_mask(evp_handle *h, uint32_t mask);
+/* Synchronises the handle's stream, then copies the accumulated device time (ms, host, EVP_NCLASS doubles)
+ * and bracketed launch counts (launches, host, EVP_NCLASS int64) per class; either pointer may be NULL.
+ * reset != 0 zeroes the totals afterwards. EVP_ERR_ARG for a NULL handle, EVP_ERR_CUDA if the stream failed. */
 int evp_kernel_times(evp_handle *h, double *ms, int64_t *launches, int reset);
+/* Number of the library's kernel launches on this handle since evp_init (host counter, no synchronisation).
+ * EVP_ERR_ARG for a NULL handle or output pointer. */
 int evp_launch_count(const evp_handle *h, int64_t *launches);
 /* Running totals over all increments: local Newton iterations (one 6x6 solve each) and
  * evaluations of the residual, tangent and potential (including backtracking trials). */
@@ -260,7 +265,12 @@ int evp_newton_counts(const evp_handle *h, int64_t *solves, int64_t *evals);
 /* Running total of tangent factorisations (EVP_NEWTON_REUSE; equals solves with EVP_NEWTON_EXACT). */
 int evp_newton_refreshes(const evp_handle *h, int64_t *refreshes);
 
+/* Frees the handle and its CUDA events. The workspace stays the caller's (the library never owns device memory);
+ * work still queued on the stream must finish before the caller frees the workspace. NULL is a no-op. */
 void evp_destroy(evp_handle *h);
+/* Text of the most recent error or warning recorded on this handle (later successful calls do not clear it);
+ * valid until the next call on the handle. For a NULL handle: "no handle". evp_init leaves a handle to read it
+ * from even when it fails (release it with evp_destroy). */
 const char *evp_last_error(const evp_handle *h);
 
 /* ---- stand-alone primitives (same kernels as the increment; used for parity tests) ---- */
