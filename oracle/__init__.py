@@ -1,7 +1,7 @@
 """ctypes wrapper of the FP64 CPU oracle (liboracle.so, built from oracle.c).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and bench.py's CPU
-baseline. The product package never imports this module.
+baseline and reference legs (the oracle timed on the host). The product package never imports this module.
 """
 from __future__ import annotations
 

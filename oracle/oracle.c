@@ -3,7 +3,7 @@
  * (Zhao, Low, Wang, Niezgoda, arXiv:1509.04953).
  *
  * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the CPU baseline
- * leg of bench.py. It is plain, slow and written to be checked against the paper by eye:
+ * and reference legs of bench.py (the oracle timed on the host). It is plain, slow and written to be checked against the paper by eye:
  * plain loops, a textbook radix-2 FFT, full 4th-order tensors, no fusion and no blocking.
  * It shares no code with the CUDA library.
  *

@@ -2,7 +2,7 @@
  * FP64 CPU oracle for the coupled FFT-EVP / phase-field DRX hot path.
  *
  * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's CPU
- * baseline may load this library. The product path (paper_1509_04953_gb300) never
+ * baseline and reference legs (the oracle timed on the host) may load this library. The product path (paper_1509_04953_gb300) never
  * includes, links or calls it, and it shares no code with that path.
  *
  * Units: stress MPa, lengths m, densities 1/m^2, time s. Symmetric tensors are Mandel
