@@ -126,3 +126,21 @@ def test_build_entry_point_compiles_everything():
     ge.build()
     assert os.path.exists(os.path.join(ROOT, "paper_1509_04953_gb300", "libevp_gb300.so"))
     assert os.path.exists(os.path.join(ROOT, "oracle", "liboracle.so"))
+
+
+def test_product_path_fails_loudly_without_a_gpu():
+    """No CPU fallback: without a CUDA device every entry of the binding that would compute raises."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import numpy as np
+    from paper_1509_04953_gb300 import evp, synth
+    n, G = 8, 2
+    g0 = np.zeros(n ** 3, dtype=np.int32)
+    with pytest.raises(evp.EVPError, match="no CUDA device"):
+        evp.Solver(n, G, g0, synth.orientations(G, 0), synth.Material(), 0)
+    x = torch.zeros((1, n, n, n), dtype=torch.float64)
+    for call in (lambda: evp.rfft3d(x), lambda: evp.stress_residual(torch.zeros((6, n, n, n))),
+                 lambda: evp.voronoi(n, synth.voronoi_seeds(n, G, 0))):
+        with pytest.raises(evp.EVPError, match="no CUDA device"):
+            call()
