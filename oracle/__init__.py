@@ -5,6 +5,7 @@ baseline and reference legs (the oracle timed on the host). The product package 
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -60,86 +61,103 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        L.orc_mix64.restype = C.c_uint64
-        L.orc_mix64.argtypes = [C.c_uint64]
-        L.orc_u01.restype = C.c_double
-        L.orc_u01.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
-        L.orc_weibull.restype = C.c_double
-        L.orc_weibull.argtypes = [C.c_double, C.c_double, C.c_double]
-        L.orc_voronoi.argtypes = [C.c_int, C.c_int, _lp, _ip]
-        L.orc_quat_to_R.argtypes = [_dp, _dp]
-        L.orc_slip_systems.argtypes = [_dp, _dp]
-        L.orc_grain_tables.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, _dp, _dp]
-        L.orc_fft1d.argtypes = [_cp, C.c_int, C.c_long, C.c_int]
-        L.orc_fft3d.argtypes = [C.c_int, _cp, C.c_int]
-        L.orc_dft3d_brute.argtypes = [C.c_int, _cp, _cp, C.c_int]
-        L.orc_gamma0.argtypes = [_dp, C.c_double, C.c_double, _dp]
-        L.orc_newton.restype = C.c_int
-        L.orc_newton.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_int,
-                                 _dp, _dp, C.POINTER(C.c_int)]
-        L.orc_residual.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp, _dp]
-        L.orc_stress_residual.argtypes = [C.c_int, _dp, _dp]
-        L.orc_km_update.argtypes = [C.POINTER(Params), _dp, _dp, C.c_double]
-        L.orc_point_model.restype = C.c_int
-        L.orc_point_model.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
-                                      C.c_int, _dp]
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [C.POINTER(Config), C.POINTER(Params), _ip, _dp, C.c_uint64]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_field.restype = C.POINTER(C.c_double)
-        L.orc_field.argtypes = [C.c_void_p, C.c_char_p]
-        L.orc_ifield.restype = C.POINTER(C.c_int32)
-        L.orc_ifield.argtypes = [C.c_void_p, C.c_char_p]
-        L.orc_increment.restype = C.c_int
-        L.orc_increment.argtypes = [C.c_void_p, C.c_double, C.c_double, C.POINTER(Stats)]
-        L.orc_nucleate.restype = C.c_int
-        L.orc_nucleate.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)]
-        L.orc_loss_grad.restype = C.c_int
-        L.orc_loss_grad.argtypes = [C.POINTER(Config), C.POINTER(Params), _ip, _dp, C.c_uint64, C.c_int, C.c_double,
-                                    C.c_double, C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
-                                    C.c_double]
-        L.orc_pf_step.restype = C.c_int
-        L.orc_pf_step.argtypes = [C.c_void_p, C.c_int, C.POINTER(PFStats)]
-        L.orc_pf_step_dense.restype = C.c_int
-        L.orc_pf_step_dense.argtypes = [C.c_void_p, C.c_int]
-        L.orc_pf_energy.restype = C.c_double
-        L.orc_pf_energy.argtypes = [C.c_void_p]
-        L.orc_stats_now.argtypes = [C.c_void_p, C.POINTER(PFStats)]
-        L.orc_next_id.restype = C.c_int
-        L.orc_next_id.argtypes = [C.c_void_p]
-        L.orc_set_next_id.argtypes = [C.c_void_p, C.c_int]
-        L.orc_refresh_derived.argtypes = [C.c_void_p]
-        L.orc_mr_tables.argtypes = [_dp]
-        L.orc_mr_project.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
-        L.orc_mr_frozen.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp]
-        L.orc_mr_rho_m.restype = C.c_double
-        L.orc_mr_rho_m.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
-        L.orc_mr_gdot.restype = C.c_double
-        L.orc_mr_gdot.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
-                                  C.POINTER(C.c_double)]
-        L.orc_mr_ssd_rate.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
-        L.orc_vm_stress.restype = C.c_double
-        L.orc_vm_stress.argtypes = [_dp]
-        L.orc_vm_strain.restype = C.c_double
-        L.orc_vm_strain.argtypes = [_dp]
-        L.orc_mr_grain_vectors.argtypes = [C.c_int, _dp, _dp, _dp]
-        L.orc_mr_gnd_rates.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
-        L.orc_mr_gnd_rates_voxel.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, C.c_long,
-                                             _dp, _dp]
-        L.orc_mr_leff_next.restype = C.c_double
-        L.orc_mr_leff_next.argtypes = [C.c_double, _dp, C.c_double]
-        L.orc_newton_mr.restype = C.c_int
-        L.orc_newton_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
-                                    C.c_double, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
-        L.orc_residual_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp]
-        L.orc_point_model_mr.restype = C.c_int
-        L.orc_point_model_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
-                                         C.c_int, _dp]
-        L.orc_leff.restype = C.c_double
-        L.orc_leff.argtypes = [C.c_void_p]
-        _lib = L
+        _lib = _declare(C.CDLL(_LIB))
     return _lib
+
+
+@contextlib.contextmanager
+def using(path):
+    """Run the wrappers on another build of oracle.c (tests build copies with planted mistakes to show that the
+    pins catch them); the default library is back on exit."""
+    global _lib
+    saved = lib()
+    _lib = _declare(C.CDLL(os.path.abspath(path)))
+    try:
+        yield _lib
+    finally:
+        _lib = saved
+
+
+def _declare(L):
+    """ctypes signatures of every oracle entry point."""
+    L.orc_mix64.restype = C.c_uint64
+    L.orc_mix64.argtypes = [C.c_uint64]
+    L.orc_u01.restype = C.c_double
+    L.orc_u01.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+    L.orc_weibull.restype = C.c_double
+    L.orc_weibull.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.orc_voronoi.argtypes = [C.c_int, C.c_int, _lp, _ip]
+    L.orc_quat_to_R.argtypes = [_dp, _dp]
+    L.orc_slip_systems.argtypes = [_dp, _dp]
+    L.orc_grain_tables.argtypes = [C.POINTER(Params), C.c_int, _dp, _dp, _dp, _dp]
+    L.orc_fft1d.argtypes = [_cp, C.c_int, C.c_long, C.c_int]
+    L.orc_fft3d.argtypes = [C.c_int, _cp, C.c_int]
+    L.orc_dft3d_brute.argtypes = [C.c_int, _cp, _cp, C.c_int]
+    L.orc_gamma0.argtypes = [_dp, C.c_double, C.c_double, _dp]
+    L.orc_newton.restype = C.c_int
+    L.orc_newton.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_int,
+                             _dp, _dp, C.POINTER(C.c_int)]
+    L.orc_residual.argtypes = [C.POINTER(Params), _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp, _dp]
+    L.orc_stress_residual.argtypes = [C.c_int, _dp, _dp]
+    L.orc_km_update.argtypes = [C.POINTER(Params), _dp, _dp, C.c_double]
+    L.orc_point_model.restype = C.c_int
+    L.orc_point_model.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                  C.c_int, _dp]
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(Config), C.POINTER(Params), _ip, _dp, C.c_uint64]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_field.restype = C.POINTER(C.c_double)
+    L.orc_field.argtypes = [C.c_void_p, C.c_char_p]
+    L.orc_ifield.restype = C.POINTER(C.c_int32)
+    L.orc_ifield.argtypes = [C.c_void_p, C.c_char_p]
+    L.orc_increment.restype = C.c_int
+    L.orc_increment.argtypes = [C.c_void_p, C.c_double, C.c_double, C.POINTER(Stats)]
+    L.orc_nucleate.restype = C.c_int
+    L.orc_nucleate.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)]
+    L.orc_loss_grad.restype = C.c_int
+    L.orc_loss_grad.argtypes = [C.POINTER(Config), C.POINTER(Params), _ip, _dp, C.c_uint64, C.c_int, C.c_double,
+                                C.c_double, C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
+                                C.c_double]
+    L.orc_pf_step.restype = C.c_int
+    L.orc_pf_step.argtypes = [C.c_void_p, C.c_int, C.POINTER(PFStats)]
+    L.orc_pf_step_dense.restype = C.c_int
+    L.orc_pf_step_dense.argtypes = [C.c_void_p, C.c_int]
+    L.orc_pf_energy.restype = C.c_double
+    L.orc_pf_energy.argtypes = [C.c_void_p]
+    L.orc_stats_now.argtypes = [C.c_void_p, C.POINTER(PFStats)]
+    L.orc_next_id.restype = C.c_int
+    L.orc_next_id.argtypes = [C.c_void_p]
+    L.orc_set_next_id.argtypes = [C.c_void_p, C.c_int]
+    L.orc_refresh_derived.argtypes = [C.c_void_p]
+    L.orc_mr_tables.argtypes = [_dp]
+    L.orc_mr_project.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_mr_frozen.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp]
+    L.orc_mr_rho_m.restype = C.c_double
+    L.orc_mr_rho_m.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
+    L.orc_mr_gdot.restype = C.c_double
+    L.orc_mr_gdot.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                              C.POINTER(C.c_double)]
+    L.orc_mr_ssd_rate.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
+    L.orc_vm_stress.restype = C.c_double
+    L.orc_vm_stress.argtypes = [_dp]
+    L.orc_vm_strain.restype = C.c_double
+    L.orc_vm_strain.argtypes = [_dp]
+    L.orc_mr_grain_vectors.argtypes = [C.c_int, _dp, _dp, _dp]
+    L.orc_mr_gnd_rates.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
+    L.orc_mr_gnd_rates_voxel.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, C.c_long,
+                                         _dp, _dp]
+    L.orc_mr_leff_next.restype = C.c_double
+    L.orc_mr_leff_next.argtypes = [C.c_double, _dp, C.c_double]
+    L.orc_newton_mr.restype = C.c_int
+    L.orc_newton_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                C.c_double, C.c_int, _dp, _dp, C.POINTER(C.c_int)]
+    L.orc_residual_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp]
+    L.orc_point_model_mr.restype = C.c_int
+    L.orc_point_model_mr.argtypes = [C.POINTER(Params), _dp, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double,
+                                     C.c_int, _dp]
+    L.orc_leff.restype = C.c_double
+    L.orc_leff.argtypes = [C.c_void_p]
+    return L
 
 
 def make_params(mat) -> Params:

@@ -1,0 +1,86 @@
+"""The oracle's pins catch plausible mistakes: each case plants one (a wrong constant, sign, exponent, index or a
+dropped term) in a copy of oracle.c, builds that copy on its own, runs the pin that covers the code under it and
+expects that pin to fail. The committed oracle is untouched; the same pins pass on it (test_oracle_pins.py)."""
+import inspect
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import oracle as O
+import test_oracle_pins as P
+from paper_1509_04953_gb300 import synth
+
+SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
+HDR = os.path.join(os.path.dirname(O.__file__), "oracle.h")
+
+
+def _replace_once(old, new):
+    def f(src):
+        assert src.count(old) == 1, old
+        return src.replace(old, new)
+    return f
+
+
+def _halve_basic_plastic_strain(src):
+    # the basic scheme's state update (a7): the plastic strain takes half the converged shear rates
+    anchor = "for (int I = 0; I < 6; ++I) tau += M[6 * a + I] * sigk[I * N3 + v];"
+    line = "s->epsp[I * N3 + v] += dt * ep;"
+    assert src.count(anchor) == 1
+    j = src.index(line, src.index(anchor))
+    return src[:j] + "s->epsp[I * N3 + v] += 0.5 * dt * ep;" + src[j + len(line):]
+
+
+# (case, mutation, pin, pin arguments besides the material)
+CASES = [
+    ("green_operator_constant",        # Gamma0's second term with lam0 + mu0 for lam0 + 2 mu0
+     _replace_once("double c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));",
+                   "double c2 = (lam0 + mu0) / (mu0 * (lam0 + mu0));"),
+     P.test_gamma0_projection_properties, {}),
+    ("fft_twiddle_sign",
+     _replace_once("cexp(sign * 2.0 * PI * IU * (double)k / (double)len)",
+                   "cexp(-sign * 2.0 * PI * IU * (double)k / (double)len)"),
+     P.test_fft_matches_brute_dft, dict(n=4)),
+    ("km_square_root_dropped",         # k1 rho_F instead of k1 sqrt(rho_F)
+     _replace_once("(p->k1 * srf - p->k2 * rho[a])", "(p->k1 * rf - p->k2 * rho[a])"),
+     P.test_km_single_system_closed_form, {}),
+    ("flow_rule_prefactor",            # the shear rate off by a factor its tangent and potential do not share
+     _replace_once("gd = p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0);", "gd = 0.5 * p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0);"),
+     P.test_newton_tangent_and_residual, {}),
+    ("slip_direction_sign",            # [1 0 -1] on the (1 -1 1) plane written as [1 0 1]
+     _replace_once("{{0, 1, 1}, {1, 0, -1}, {1, 1, 0}},", "{{0, 1, 1}, {1, 0, 1}, {1, 1, 0}},"),
+     P.test_rotation_and_slip_geometry, {}),
+    ("pf_gradient_coefficient",        # kappa = l/2 instead of 3l/4 in the phase-field step
+     _replace_once("kap = 0.75 * l, gam = 1.5, Esc", "kap = 0.5 * l, gam = 1.5, Esc"),
+     P.test_pf_flat_interface_tanh_profile_and_energy, {}),
+    ("weibull_exponent",               # (-ln(1-u))^q instead of ^(1/q)
+     _replace_once("return kc * pow(-log(1.0 - u), 1.0 / q);", "return kc * pow(-log(1.0 - u), q);"),
+     P.test_weibull_sampler_matches_cdf, {}),
+    ("sweep_softened_twice",
+     _replace_once("if (gprev[v] < s->G && s->g[v] >= s->G) soften_voxel(s, v);",
+                   "if (gprev[v] < s->G && s->g[v] >= s->G) { soften_voxel(s, v); soften_voxel(s, v); }"),
+     P.test_pf_sweep_softening_and_recrystallised_fraction, {}),
+    ("green_correction_sign",          # eps += Gamma0 : sigma instead of eps -= Gamma0 : sigma
+     _replace_once("eh[I] = -a;", "eh[I] = a;"),
+     P.test_elastic_laminate_closed_form, dict(scheme=0, ref_scale=1.0)),
+    ("plastic_strain_update_halved",
+     _halve_basic_plastic_strain,
+     P.test_converged_increment_checks_hold_for_the_oracle, dict(n=16, G=8)),
+]
+
+
+@pytest.mark.parametrize("case,mutate,pin,kw", CASES, ids=[c[0] for c in CASES])
+def test_pin_catches_planted_mistake(tmp_path, case, mutate, pin, kw):
+    src = mutate(open(SRC).read())
+    (tmp_path / "oracle.c").write_text(src)
+    shutil.copy(HDR, tmp_path / "oracle.h")
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", str(so),
+                           str(tmp_path / "oracle.c"), "-lm"])
+    args = dict(kw)
+    if "mat" in inspect.signature(pin).parameters:
+        args["mat"] = synth.Material()
+    with O.using(so):
+        with pytest.raises(AssertionError):
+            pin(**args)
