@@ -9,6 +9,7 @@ import subprocess
 import pytest
 
 import oracle as O
+import test_oracle_mr as MR
 import test_oracle_pins as P
 from paper_1509_04953_gb300 import synth
 
@@ -67,6 +68,16 @@ CASES = [
     ("plastic_strain_update_halved",
      _halve_basic_plastic_strain,
      P.test_converged_increment_checks_hold_for_the_oracle, dict(n=16, G=8)),
+    # the Ma-Roters law (Sec. 2.2)
+    ("mr_flow_rule_offset_sign",       # sinh((|tau| + tp)/tcut) instead of sinh((|tau| - tp)/tcut), Eq. FlowRule
+     _replace_once("const double x = (at - tp) / tcut;", "const double x = (at + tp) / tcut;"),
+     MR.test_flow_rule_limits_derivative_and_potential, {}),
+    ("mr_dipole_distance_constant",    # 8 pi instead of 16 pi in the dipole distance, Eq. SSDEvolution
+     _replace_once("(16.0 * PI * (1.0 - p->poisson) * fabs(tau[a]))", "(8.0 * PI * (1.0 - p->poisson) * fabs(tau[a]))"),
+     MR.test_ssd_terms_one_by_one, {}),
+    ("mr_gnd_one_sided_difference_sign",   # backward one-sided difference with its sign flipped, Eq. GNDEvolution
+     _replace_once("else if (sm[i]) grad[i] = (f[v] - f[nm[i]]) / leff;", "else if (sm[i]) grad[i] = (f[nm[i]] - f[v]) / leff;"),
+     MR.test_gnd_stencil_exact_on_linear_fields, dict(axis=0)),
 ]
 
 
@@ -79,8 +90,11 @@ def test_pin_catches_planted_mistake(tmp_path, case, mutate, pin, kw):
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", str(so),
                            str(tmp_path / "oracle.c"), "-lm"])
     args = dict(kw)
-    if "mat" in inspect.signature(pin).parameters:
+    params = inspect.signature(pin).parameters
+    if "mat" in params:
         args["mat"] = synth.Material()
+    if "mrmat" in params:
+        args["mrmat"] = synth.ma_roters_material()
     with O.using(so):
         with pytest.raises(AssertionError):
             pin(**args)
