@@ -11,6 +11,7 @@ import pytest
 import oracle as O
 import test_oracle_mr as MR
 import test_oracle_pins as P
+import test_oracle_refined_pf as RP
 from paper_1509_04953_gb300 import synth
 
 SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
@@ -78,6 +79,14 @@ CASES = [
     ("mr_gnd_one_sided_difference_sign",   # backward one-sided difference with its sign flipped, Eq. GNDEvolution
      _replace_once("else if (sm[i]) grad[i] = (f[v] - f[nm[i]]) / leff;", "else if (sm[i]) grad[i] = (f[nm[i]] - f[v]) / leff;"),
      MR.test_gnd_stencil_exact_on_linear_fields, dict(axis=0)),
+    # the 2:1 phase-field grid (Sec. 2.4)
+    ("refined_interpolation_weights",  # the odd child weighted 1/4, 3/4 instead of 3/4, 1/4
+     _replace_once("else { idx[0] = i; idx[1] = (i + 1) % n; wt[0] = 0.75; wt[1] = 0.25; }",
+                   "else { idx[0] = i; idx[1] = (i + 1) % n; wt[0] = 0.25; wt[1] = 0.75; }"),
+     RP.test_interpolation_constant_mean_and_linear_fields, {}),
+    ("refined_driving_force_spacing",  # E' at the mechanics spacing dx instead of the PF spacing dx / 2
+     _replace_once("p->b * p->b * (p->dx / s->r) / p->omega_gb;", "p->b * p->b * p->dx / p->omega_gb;"),
+     RP.test_refined_boundary_velocity_uses_the_pf_spacing, {}),
 ]
 
 
