@@ -69,6 +69,9 @@ CASES = [
     ("plastic_strain_update_halved",
      _halve_basic_plastic_strain,
      P.test_converged_increment_checks_hold_for_the_oracle, dict(n=16, G=8)),
+    ("adjoint_density_chain_factor",   # d sqrt(rho_F) / d rho taken as 1 / sqrt(rho_F), without the 1/2
+     _replace_once("+ sum_lr_gd / (2.0 * srf);", "+ sum_lr_gd / srf;"),
+     P.test_oracle_adjoint_gradient_matches_central_differences, {}),
     # the Ma-Roters law (Sec. 2.2)
     ("mr_flow_rule_offset_sign",       # sinh((|tau| + tp)/tcut) instead of sinh((|tau| - tp)/tcut), Eq. FlowRule
      _replace_once("const double x = (at - tp) / tcut;", "const double x = (at + tp) / tcut;"),
