@@ -9,6 +9,10 @@
  *
  * Every function names the passage of the paper (or the textbook closed form) it follows.
  * Readings of passages the paper leaves open are listed where they are used.
+ *
+ * Pins: each step is checked against closed forms, brute force, invariants or the paper's
+ * relations by the tests. The coupled trajectory as a whole (increments, nucleation and
+ * phase-field steps in sequence) is parity unpinned beyond the pins of its steps.
  */
 #include "oracle.h"
 
