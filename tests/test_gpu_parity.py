@@ -53,6 +53,17 @@ def test_voronoi_bit_exact(ev, n, G):
     assert np.array_equal(got, O.voronoi(n, seeds))
 
 
+def test_voronoi_ties_go_to_the_smaller_index(ev):
+    """Seeds on voxel centres put whole planes of voxels at equal distance from two or three seeds; both sides
+    give them the smaller seed index (reading C21), bit for bit."""
+    c = lambda i: (i << 16) + 32768
+    for n in (4, 8):
+        tied = np.array([[c(2), c(0), c(0)], [c(0), c(0), c(0)], [c(0), c(2), c(0)], [c(n - 2), c(n - 2), c(1)]],
+                        dtype=np.int64)
+        got = ev.voronoi(n, tied).cpu().numpy()
+        assert np.array_equal(got, O.voronoi(n, tied))
+
+
 @pytest.mark.parametrize("n", [4, 8, 16, 32])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_rfft3d_matches_oracle_fft(ev, n, prec):

@@ -98,11 +98,9 @@ def test_nucleation_fraction_and_bookkeeping(mat):
 # ------------------------------------------------------------------------------------------
 # microstructure
 # ------------------------------------------------------------------------------------------
-def test_voronoi_brute_force():
-    n, G = 8, 11
-    seeds = synth.voronoi_seeds(n, G, 5)
-    got = O.voronoi(n, seeds).reshape(n, n, n)       # [z][y][x]
+def _voronoi_brute(n, seeds):
     L = n << 16
+    out = np.zeros((n, n, n), dtype=np.int64)
     for z in range(n):
         for y in range(n):
             for x in range(n):
@@ -110,7 +108,21 @@ def test_voronoi_brute_force():
                 d = np.abs(seeds - c) % L
                 d = np.minimum(d, L - d)
                 d2 = (d * d).sum(axis=1)
-                assert got[z, y, x] == int(np.argmin(d2))   # argmin takes the first (smallest) index
+                out[z, y, x] = int(np.argmin(d2))     # argmin takes the first (smallest) index on a tie
+    return out
+
+
+def test_voronoi_brute_force():
+    """Periodic Voronoi ids against brute force: random seeds, and seeds on voxel centres, where whole planes of
+    voxels lie at equal distance from two or three seeds and reading C21 gives them the smaller seed index."""
+    n, G = 8, 11
+    seeds = synth.voronoi_seeds(n, G, 5)
+    assert np.array_equal(O.voronoi(n, seeds).reshape(n, n, n), _voronoi_brute(n, seeds))
+    c = lambda i: (i << 16) + 32768
+    tied = np.array([[c(2), c(0), c(0)], [c(0), c(0), c(0)], [c(0), c(2), c(0)]], dtype=np.int64)
+    want = _voronoi_brute(4, tied)
+    assert want[0, 0, 1] == 0 and want[0, 0, 3] == 0 and want[0, 1, 1] == 0   # ties to seeds 0 and 1, and 0, 1, 2
+    assert np.array_equal(O.voronoi(4, tied).reshape(4, 4, 4), want)
 
 
 def test_rotation_and_slip_geometry():
