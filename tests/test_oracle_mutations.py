@@ -72,6 +72,19 @@ CASES = [
     ("voronoi_tie_to_larger_index",    # reading C21 gives ties to the smaller seed index
      _replace_once("if (best < 0 || d2 < best) { best = d2; arg = g; }", "if (best < 0 || d2 <= best) { best = d2; arg = g; }"),
      P.test_voronoi_brute_force, {}),
+    ("pf_argmax_tie_to_larger_id",     # reading C21
+     _replace_once("(e == be && id < bi)", "(e == be && id > bi)"),
+     P.test_pf_argmax_ties_go_to_the_smaller_id, {}),
+    ("pf_keep_tie_to_larger_id",       # reading C11: the K largest, ties to the smaller id
+     _replace_once("    if (x->e < y->e) return 1;\n    return (x->id > y->id) - (x->id < y->id);",
+                   "    if (x->e < y->e) return 1;\n    return (x->id < y->id) - (x->id > y->id);"),
+     P.test_pf_active_set_keeps_the_largest_ties_to_smaller_id_and_counts_overflow, {}),
+    ("pf_overflow_not_counted",        # reading C11: overflow counted
+     _replace_once("if (no > K) { ovf += 1; no = K; }", "if (no > K) { no = K; }"),
+     P.test_pf_active_set_keeps_the_largest_ties_to_smaller_id_and_counts_overflow, {}),
+    ("pf_drop_threshold_times_ten",    # reading C11: drop below 1e-5
+     _replace_once("if (en >= s->p.eta_drop) {", "if (en >= 10.0 * s->p.eta_drop) {"),
+     P.test_pf_drop_threshold, {}),
     ("adjoint_density_chain_factor",   # d sqrt(rho_F) / d rho taken as 1 / sqrt(rho_F), without the 1/2
      _replace_once("+ sum_lr_gd / (2.0 * srf);", "+ sum_lr_gd / srf;"),
      P.test_oracle_adjoint_gradient_matches_central_differences, {}),

@@ -471,6 +471,70 @@ def test_pf_sweep_softening_and_recrystallised_fraction(mat):
     assert np.array_equal(rho2[:, again], rho1[:, again])
 
 
+def _pf_state(mat, n, G, kmax):
+    g0 = np.zeros(n ** 3, dtype=np.int32)
+    st = O.State(n, G, g0, synth.orientations(G, 0), mat, seed=0, kmax=kmax)
+    st.field("k")[:] = 0.0
+    st.ifield("ids")[:] = -1
+    st.field("eta")[:] = 0.0
+    st.next_id = G
+    return st
+
+
+def test_pf_argmax_ties_go_to_the_smaller_id(mat):
+    """Reading C21: two order parameters of equal value at every point (a uniform 1/2, 1/2 mixture, which the
+    step keeps exactly symmetric) give the grain id of the smaller id everywhere."""
+    n = 8
+    st = _pf_state(mat, n, 2, 2)
+    ids, eta = st.ifield("ids"), st.field("eta")
+    ids[0], ids[1] = 0, 1
+    eta[0], eta[1] = 0.5, 0.5
+    st.pf_step(1)
+    assert np.array_equal(eta[0], eta[1])            # the tie is exact
+    assert np.all(st.ifield("g") == 0)
+
+
+def test_pf_active_set_keeps_the_largest_ties_to_smaller_id_and_counts_overflow(mat):
+    """Reading C11 at K = 2: on the plane x = 0 of a grain-0 crystal, flanked by a plane of grain 1 (x = n-1) and
+    one of grain 2 (x = 1), ids 1 and 2 arrive with exactly equal values; the point keeps its own id and the
+    smaller of the tied pair, and each of those n^2 points counts once as an overflow."""
+    n = 8
+    st = _pf_state(mat, n, 3, 2)
+    ids, eta = st.ifield("ids"), st.field("eta")
+    x = np.arange(n ** 3) % n
+    ids[0] = np.where(x == n - 1, 1, np.where(x == 1, 2, 0))
+    eta[0] = 1.0
+    rc, ps = st.pf_step(1)
+    ids, eta = st.ifield("ids"), st.field("eta")
+    p0 = x == 0
+    assert ps.overflow == n * n and rc == 2
+    assert np.all(ids[0, p0] == 0) and np.all(ids[1, p0] == 1)
+    assert np.all(eta[1, p0] > mat.eta_drop)
+
+
+def test_pf_drop_threshold(mat):
+    """Reading C11: an order parameter leaves a point's active set when its new value falls below eta_drop
+    (1e-5) and stays when it does not. A grain-0 crystal holds grain 1 at small values on two planes; the
+    points next to them receive values on either side of the threshold."""
+    n = 8
+    st = _pf_state(mat, n, 2, 2)
+    ids, eta = st.ifield("ids"), st.field("eta")
+    x = np.arange(n ** 3) % n
+    ids[0] = 0
+    eta[0] = 1.0
+    for plane, val in ((2, 3e-4), (6, 5e-5)):        # about 0.116 x val arrives next door: 3.5e-5 and 5.8e-6
+        ids[1, x == plane] = 1
+        eta[1, x == plane] = val
+    st.pf_step(1)
+    ids, eta = st.ifield("ids"), st.field("eta")
+    has1 = (ids == 1).any(axis=0)
+    e1 = np.where(ids == 1, eta, 0.0).sum(axis=0)
+    kept = e1[has1]
+    assert np.all(kept >= mat.eta_drop)              # nothing below the threshold is kept
+    assert np.any((kept >= mat.eta_drop) & (kept < 10 * mat.eta_drop))   # values just above it are kept
+    assert np.all(has1[(x == 1) | (x == 3)]) and not np.any(has1[(x == 5) | (x == 7)])
+
+
 def test_pf_energy_nonincreasing(mat):
     n, G = 12, 6
     seeds = synth.voronoi_seeds(n, G, 8)
