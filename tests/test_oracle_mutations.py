@@ -46,7 +46,11 @@ CASES = [
      P.test_fft_matches_brute_dft, dict(n=4)),
     ("km_square_root_dropped",         # k1 rho_F instead of k1 sqrt(rho_F)
      _replace_once("(p->k1 * srf - p->k2 * rho[a])", "(p->k1 * rf - p->k2 * rho[a])"),
-     P.test_km_single_system_closed_form, {}),
+     P.test_km_single_system_closed_form, dict(sense=1.0)),
+    ("km_absolute_shear_dropped",      # (k1 sqrt(rho_F) - k2 rho) gdot instead of ... |gdot|
+     _replace_once("rho[a] = rho[a] + dt * (p->k1 * srf - p->k2 * rho[a]) * fabs(gdot[a]);",
+                   "rho[a] = rho[a] + dt * (p->k1 * srf - p->k2 * rho[a]) * gdot[a];"),
+     P.test_km_single_system_closed_form, dict(sense=-1.0)),
     ("flow_rule_prefactor",            # the shear rate off by a factor its tangent and potential do not share
      _replace_once("gd = p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0);", "gd = 0.5 * p->gdot0 * pw * (x < 0.0 ? -1.0 : 1.0);"),
      P.test_newton_tangent_and_residual, {}),
@@ -72,6 +76,10 @@ CASES = [
     ("voronoi_tie_to_larger_index",    # reading C21 gives ties to the smaller seed index
      _replace_once("if (best < 0 || d2 < best) { best = d2; arg = g; }", "if (best < 0 || d2 <= best) { best = d2; arg = g; }"),
      P.test_voronoi_brute_force, {}),
+    ("nucleation_eligibility_four_neighbours",   # reading C13: six face neighbours, not four
+     _replace_once("        for (int d = 0; d < 6; ++d)\n            if (s->g[nbr(s->n, v, d)] != s->g[v]) gb = 1;",
+                   "        for (int d = 0; d < 4; ++d)\n            if (s->g[nbr(s->n, v, d)] != s->g[v]) gb = 1;"),
+     P.test_nucleation_eligibility_is_the_six_face_neighbours, {}),
     ("pf_argmax_tie_to_larger_id",     # reading C21
      _replace_once("(e == be && id < bi)", "(e == be && id > bi)"),
      P.test_pf_argmax_ties_go_to_the_smaller_id, {}),

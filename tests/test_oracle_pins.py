@@ -260,9 +260,11 @@ def test_newton_tangent_and_residual(mat):
         assert np.allclose(s, Cg @ (eps_tr - dt * (M[g].T @ gd)), rtol=1e-9, atol=1e-9)
 
 
-def test_km_single_system_closed_form(mat):
+@pytest.mark.parametrize("sense", [1.0, -1.0])
+def test_km_single_system_closed_form(mat, sense):
+    """The densities grow with the accumulated |shear|: the same closed form for either sense of slip."""
     gd = np.zeros(12)
-    gd[0] = 1.0
+    gd[0] = sense
     errs = []
     for steps in (2000, 4000):
         gam = 0.2
@@ -469,6 +471,28 @@ def test_pf_sweep_softening_and_recrystallised_fraction(mat):
     rho2 = st.field("rho")
     again = swept & (g2 >= G)
     assert np.array_equal(rho2[:, again], rho1[:, again])
+
+
+def test_nucleation_eligibility_is_the_six_face_neighbours(mat):
+    """Reading C13: a voxel is eligible when one of its six face neighbours belongs to another grain. Three
+    slab bicrystals, with boundaries normal to x, y and z, nucleate wherever k > kappa is forced (kappa = 0):
+    exactly the voxels on either side of each boundary, and no voxel inside a grain."""
+    n = 8
+    for axis in range(3):
+        coord = (np.arange(n ** 3) // n ** axis) % n
+        g0 = (coord >= n // 2).astype(np.int32)
+        st = O.State(n, 2, g0, synth.orientations(2, 0), mat, seed=3)
+        st.field("kappa")[:] = 0.0
+        rc, nn = st.nucleate(0)
+        grid = g0.reshape(n, n, n)                       # [z][y][x]
+        gb = np.zeros_like(grid, dtype=bool)
+        for ax in range(3):
+            for sh in (1, -1):
+                gb |= np.roll(grid, sh, axis=ax) != grid
+        gb = gb.reshape(-1)
+        nucleated = st.ifield("ids")[0] >= 2
+        assert nn == gb.sum() == 4 * n * n
+        assert np.array_equal(nucleated, gb)
 
 
 def _pf_state(mat, n, G, kmax):
