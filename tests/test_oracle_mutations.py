@@ -106,6 +106,19 @@ CASES = [
     ("mr_gnd_one_sided_difference_sign",   # backward one-sided difference with its sign flipped, Eq. GNDEvolution
      _replace_once("else if (sm[i]) grad[i] = (f[v] - f[nm[i]]) / leff;", "else if (sm[i]) grad[i] = (f[nm[i]] - f[v]) / leff;"),
      MR.test_gnd_stencil_exact_on_linear_fields, dict(axis=0)),
+    ("mr_projection_table_swapped",    # GNDs projected with the forest table in place of its own (Eq. RhoForest)
+     _replace_once("fabs(gs[b] * tab[144 + 12 * a + b])", "fabs(gs[b] * tab[12 * a + b])"),
+     MR.test_projection_closed_forms, {}),
+    ("mr_leff_update_inverted",        # l_eff (1 + xi eps) instead of l_eff (1 + eps / xi), Eq. L0evolution
+     _replace_once("return leff * (1.0 + orc_vm_strain(E) / xi);", "return leff * (1.0 + orc_vm_strain(E) * xi);"),
+     MR.test_von_mises_measures, {}),
+    ("mr_gnd_total_sum_not_norm",      # |rs| + |re| instead of sqrt(rs^2 + re^2) (reading R7)
+     _replace_once("s->gnd[i] += dt * sqrt(rs[i] * rs[i] + re[i] * re[i]);", "s->gnd[i] += dt * (fabs(rs[i]) + fabs(re[i]));"),
+     MR.test_state_update_wires_the_gnd_and_ssd_laws, {}),
+    ("mr_softening_reaches_ssd",       # reading R9 keeps rho_SSD at a nucleus
+     _replace_once("            s->gnd[a * N3 + v] = f * s->gnd[a * N3 + v];\n",
+                   "            s->gnd[a * N3 + v] = f * s->gnd[a * N3 + v];\n            s->rho[a * N3 + v] = f * s->rho[a * N3 + v];\n"),
+     MR.test_nucleation_softens_gnd_and_keeps_ssd, {}),
     # the 2:1 phase-field grid (Sec. 2.4)
     ("refined_interpolation_weights",  # the odd child weighted 1/4, 3/4 instead of 3/4, 1/4
      _replace_once("else { idx[0] = i; idx[1] = (i + 1) % n; wt[0] = 0.75; wt[1] = 0.25; }",
