@@ -70,6 +70,10 @@ CASES = [
     ("green_correction_sign",          # eps += Gamma0 : sigma instead of eps -= Gamma0 : sigma
      _replace_once("eh[I] = -a;", "eh[I] = a;"),
      P.test_elastic_laminate_closed_form, dict(scheme=0, ref_scale=1.0)),
+    ("al_local_strain_sign",           # augmented Lagrangian, Sec. 2.1: e = C0^-1 (tau + sigma) for C0^-1 (tau - sigma)
+     _replace_once("for (int J = 0; J < 6; ++J) st += S0[6 * I + J] * (tau[J] - sg[J]);",
+                   "for (int J = 0; J < 6; ++J) st += S0[6 * I + J] * (tau[J] + sg[J]);"),
+     P.test_elastic_laminate_closed_form, dict(scheme=1, ref_scale=1.0)),
     ("plastic_strain_update_halved",
      _halve_basic_plastic_strain,
      P.test_converged_increment_checks_hold_for_the_oracle, dict(n=16, G=8)),
