@@ -128,6 +128,9 @@ CASES = [
      _replace_once("else { idx[0] = i; idx[1] = (i + 1) % n; wt[0] = 0.75; wt[1] = 0.25; }",
                    "else { idx[0] = i; idx[1] = (i + 1) % n; wt[0] = 0.25; wt[1] = 0.75; }"),
      RP.test_interpolation_constant_mean_and_linear_fields, {}),
+    ("refined_restriction_tie_to_larger_id",   # equal summed order parameters go to the smaller id
+     _replace_once("(sum == bsum && id < best)", "(sum == bsum && id > best)"),
+     RP.test_restriction_recovers_grains_and_takes_the_larger_sum, {}),
     ("refined_driving_force_spacing",  # E' at the mechanics spacing dx instead of the PF spacing dx / 2
      _replace_once("p->b * p->b * (p->dx / s->r) / p->omega_gb;", "p->b * p->b * p->dx / p->omega_gb;"),
      RP.test_refined_boundary_velocity_uses_the_pf_spacing, {}),
