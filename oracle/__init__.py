@@ -303,6 +303,28 @@ def loss_grad(n, grains, g0, quat, mat, seed, T, dE33, dt, target=None, want_gra
     return rc, loss.value, grad, s33
 
 
+class _Handle:
+    """Owns one native oracle state and frees it through the library that created it, once nothing refers to it
+    any more: neither its State nor any array view of its fields. A view can therefore never outlive the memory it
+    shows, and a state made under one build (see using()) is never freed through another."""
+
+    def __init__(self, L, h):
+        self.L, self.h = L, h
+
+    def __del__(self):
+        h, self.h = self.h, None
+        if h:
+            self.L.orc_destroy(h)
+
+
+class _View:
+    """An array interface over native memory that holds its _Handle alive."""
+
+    def __init__(self, owner, addr, shape, typestr):
+        self._owner = owner
+        self.__array_interface__ = {"data": (addr, False), "shape": tuple(shape), "typestr": typestr, "version": 3}
+
+
 class State:
     """The oracle's full simulation state (FP64, host memory)."""
 
@@ -321,82 +343,92 @@ class State:
         self._p = make_params(mat)
         self._g0 = np.ascontiguousarray(g0, dtype=np.int32).reshape(-1)
         self._q = np.ascontiguousarray(quat, dtype=np.float64).reshape(-1)
-        self.h = lib().orc_create(C.byref(self._cfg), C.byref(self._p), self._g0, self._q, seed)
+        self._L = lib()      # every call on this state goes to the build that created it
+        self._hd = _Handle(self._L, self._L.orc_create(C.byref(self._cfg), C.byref(self._p), self._g0, self._q,
+                                                     seed))
+
+    @property
+    def h(self):
+        if self._hd is None:
+            raise ValueError("oracle state is closed")
+        return self._hd.h
 
     def close(self):
-        if self.h:
-            lib().orc_destroy(self.h)
-            self.h = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+        """Release the state. The native memory is freed now, or when the last field view of it goes away."""
+        self._hd = None
 
     _SIZES = {"eps": 6, "epsp": 6, "sig": 6, "deps_prev": 6, "rho": 12, "k": 1, "kappa": 1, "gnds": 12,
               "gndet": 12, "gnd": 12}
 
+    def _view(self, ptr, shape, typestr):
+        if not ptr:
+            raise ValueError("no such oracle field")
+        return np.asarray(_View(self._hd, C.cast(ptr, C.c_void_p).value, shape, typestr))
+
     def field(self, name):
-        """A view (not a copy) of a double field, shaped (components, N^3)."""
-        ptr = lib().orc_field(self.h, name.encode())
+        """A view (not a copy) of a double field, shaped (components, N^3); it keeps the state alive."""
+        ptr = self._L.orc_field(self.h, name.encode())
         if name in ("E", "dE_prev"):
-            return np.ctypeslib.as_array(ptr, shape=(6,))
-        if name == "eta":   # on the phase-field grid
-            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3pf))
-        if name == "kpf":
-            return np.ctypeslib.as_array(ptr, shape=(self.N3pf,))
-        return np.ctypeslib.as_array(ptr, shape=(self._SIZES[name], self.N3))
+            shape = (6,)
+        elif name == "eta":   # on the phase-field grid
+            shape = (self.K, self.N3pf)
+        elif name == "kpf":
+            shape = (self.N3pf,)
+        else:
+            shape = (self._SIZES[name], self.N3)
+        return self._view(ptr, shape, "<f8")
 
     def ifield(self, name):
-        ptr = lib().orc_ifield(self.h, name.encode())
+        ptr = self._L.orc_ifield(self.h, name.encode())
         if name == "ids":   # on the phase-field grid
-            return np.ctypeslib.as_array(ptr, shape=(self.K, self.N3pf))
-        if name == "gpf":
-            return np.ctypeslib.as_array(ptr, shape=(self.N3pf,))
-        return np.ctypeslib.as_array(ptr, shape=(self.N3,))
+            shape = (self.K, self.N3pf)
+        elif name == "gpf":
+            shape = (self.N3pf,)
+        else:
+            shape = (self.N3,)
+        return self._view(ptr, shape, "<i4")
 
     def increment(self, dE33, dt):
         st = Stats()
-        rc = lib().orc_increment(self.h, dE33, dt, C.byref(st))
+        rc = self._L.orc_increment(self.h, dE33, dt, C.byref(st))
         return rc, st
 
     def nucleate(self, step=0):
         nn = C.c_int32(0)
-        rc = lib().orc_nucleate(self.h, step, C.byref(nn))
+        rc = self._L.orc_nucleate(self.h, step, C.byref(nn))
         return rc, nn.value
 
     def pf_step(self, nsteps):
         st = PFStats()
-        rc = lib().orc_pf_step(self.h, nsteps, C.byref(st))
+        rc = self._L.orc_pf_step(self.h, nsteps, C.byref(st))
         return rc, st
 
     def pf_step_dense(self, nsteps):
-        return lib().orc_pf_step_dense(self.h, nsteps)
+        return self._L.orc_pf_step_dense(self.h, nsteps)
 
     def pf_energy(self):
-        return lib().orc_pf_energy(self.h)
+        return self._L.orc_pf_energy(self.h)
 
     def stats(self):
         st = PFStats()
-        lib().orc_stats_now(self.h, C.byref(st))
+        self._L.orc_stats_now(self.h, C.byref(st))
         return st
 
     @property
     def next_id(self):
-        return lib().orc_next_id(self.h)
+        return self._L.orc_next_id(self.h)
 
     @next_id.setter
     def next_id(self, v):
-        lib().orc_set_next_id(self.h, int(v))
+        self._L.orc_set_next_id(self.h, int(v))
 
     def refresh_derived(self):
-        lib().orc_refresh_derived(self.h)
+        self._L.orc_refresh_derived(self.h)
 
     @property
     def leff(self):
         """Effective GND length l_eff of the Ma-Roters law (Eq. L0evolution), m."""
-        return lib().orc_leff(self.h)
+        return self._L.orc_leff(self.h)
 
 
 # ---------------------------------------------------------------------------------------------

@@ -1219,6 +1219,9 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
     double *eps = s->work_eps, *sig = s->work_sig;
     double *e = (double *)xcalloc(6 * N3, sizeof(double));
     double *lam = (double *)xcalloc(6 * N3, sizeof(double));
+    /* per-voxel squared gaps |eps - e|^2 and |C0 (eps - e)|^2, summed in voxel order after the
+     * parallel loop so that the stopping rule does not depend on the number of threads */
+    double *gap = (double *)xcalloc(2 * N3, sizeof(double));
     /* predictor (as in the basic scheme) */
     double dE[6];
     if (s->cfg.predictor && s->have_prev && s->dE_prev[2] != 0.0) {
@@ -1302,7 +1305,7 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
         }
         /* (ii) local problem and (iii) multiplier update */
         double acc_c = 0.0, acc_l = 0.0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(max : newton_max) reduction(| : newton_fail) reduction(+ : acc_c, acc_l)
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : newton_max) reduction(| : newton_fail)
         for (long v = 0; v < N3; ++v) {
             int gr = s->g0[v];
             double tau[6], etr[6], sg[6], gd[12];
@@ -1327,17 +1330,24 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
                 ev[I] = st;                                  /* e = C0^-1 (tau - sigma) */
                 d[I] = eps[I * N3 + v] - ev[I];
             }
+            double gc = 0.0, gl = 0.0;
             for (int I = 0; I < 6; ++I) {
                 double cd = 0.0;
                 for (int J = 0; J < 6; ++J) cd += C0[6 * I + J] * d[J];
                 lam[I * N3 + v] += cd;
-                acc_l += cd * cd;
-                acc_c += d[I] * d[I];
+                gl += cd * cd;
+                gc += d[I] * d[I];
                 e[I * N3 + v] = ev[I];
                 sig[I * N3 + v] = sg[I];
             }
+            gap[v] = gc;
+            gap[N3 + v] = gl;
         }
         if (newton_fail) break;
+        for (long v = 0; v < N3; ++v) {
+            acc_c += gap[v];
+            acc_l += gap[N3 + v];
+        }
         double Enorm = 0.0, mn = 0.0, mu_n = 0.0;
         for (int I = 0; I < 6; ++I) Enorm += (s->E[I] + dE[I]) * (s->E[I] + dE[I]);
         for (int I = 0; I < 6; ++I) {
@@ -1369,7 +1379,7 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
     if (status < 0) {
         for (int I = 0; I < 6; ++I) out->E[I] = s->E[I] + dE[I];
         out->status = status;
-        free(Sal); free(tauc); free(e); free(lam); free(hf);
+        free(Sal); free(tauc); free(e); free(lam); free(hf); free(gap);
         return status;
     }
     /* state update with the converged stress; the stored total strain is the compatible field eps
@@ -1410,7 +1420,7 @@ static int orc_increment_al(orc_state *s, double dE33, double dt, orc_stats *out
     s->have_prev = 1;
     memcpy(out->E, s->E, sizeof s->E);
     out->status = status;
-    free(Sal); free(tauc); free(e); free(lam); free(hf);
+    free(Sal); free(tauc); free(e); free(lam); free(hf); free(gap);
     return status;
 }
 

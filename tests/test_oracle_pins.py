@@ -8,6 +8,7 @@ non-hardening steady state, the layered laminate, the tanh interface profile), a
 statistical law (Weibull CDF of the nucleation strength, Eqs. NumCrt / NuclStrengthProb).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -684,3 +685,45 @@ def test_softer_reference_medium_reaches_the_same_solution_in_fewer_iterations(m
     assert np.abs(out[1.3][0] - out[1.0][0]).max() < 1e-7 * np.abs(out[1.0][0]).max()
     assert np.abs(out[1.3][1] - out[1.0][1]).max() < 1e-7 * np.abs(out[1.0][1]).max()
     assert sum(out[1.3][2]) < 0.85 * sum(out[1.0][2])
+
+
+def test_oracle_state_views_outlive_their_state_and_close_safely(mat):
+    """Field views keep the native oracle state alive (a view never shows freed memory), a closed state refuses
+    further calls, and a state made under another build of the oracle is freed through that build."""
+    import gc
+    n, G = 8, 2
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, 1))
+    st = O.State(n, G, g0, synth.orientations(G, 1), mat, seed=1)
+    rho = st.field("rho")
+    rho[0, 0] = 7.0
+    del st
+    gc.collect()
+    for _ in range(4):      # fresh allocations that would reuse freed memory
+        O.State(n, G, g0, synth.orientations(G, 1), mat, seed=2).field("rho")[:] = -1.0
+    assert rho[0, 0] == 7.0 and np.all(rho[:, 1:] == mat.rho0)
+    st = O.State(n, G, g0, synth.orientations(G, 1), mat, seed=1)
+    st.close()
+    with pytest.raises(ValueError):
+        st.increment(-1e-3, 1.0)
+    with O.using(O.lib()._name):
+        other = O.State(n, G, g0, synth.orientations(G, 1), mat, seed=1)
+    assert other._L is not O.lib()
+    assert other.increment(-1e-3, 1.0)[0] == 0
+    del other
+    gc.collect()
+
+
+def test_oracle_augmented_lagrangian_is_independent_of_the_thread_count(mat):
+    """The augmented Lagrangian's stopping sums run in voxel order, so the converged state does not depend on the
+    number of OpenMP threads (bitwise)."""
+    n, G = 8, 4
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, 5))
+    q = synth.orientations(G, 5)
+    out = []
+    for nt in (1, 3, os.cpu_count() or 1):
+        st = O.State(n, G, g0, q, mat, seed=1, tol=1e-10, max_iter=2000, scheme=1, al_scale=6.0, nthreads=nt)
+        rc, s = st.increment(-1e-3, 1.0)
+        assert rc == 0
+        out.append((s.iterations, st.field("sig").copy(), st.field("rho").copy()))
+    for it, sig, rho in out[1:]:
+        assert it == out[0][0] and np.array_equal(sig, out[0][1]) and np.array_equal(rho, out[0][2])
