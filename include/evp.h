@@ -7,9 +7,11 @@
  * Conventions
  *  - Every call returns an int status: 0 = OK, > 0 = warning, < 0 = error (EVP_ERR_*).
  *    No call aborts, traps or prints. evp_last_error() gives a one-line reason.
- *  - The library never allocates device memory. The caller sizes one device workspace with
+ *  - No call allocates device memory at run time. The caller sizes one device workspace with
  *    evp_workspace_bytes() and passes it to evp_init(); it stays owned by the caller and must
- *    outlive the handle. The handle itself is a small host object freed by evp_destroy().
+ *    outlive the handle. The handle itself is a small host object freed by evp_destroy(). The
+ *    only device storage the library owns is the fixed 64 KiB scratch array of
+ *    evp_stress_residual_noalloc.
  *  - All device work is enqueued on the stream given to evp_init (a cudaStream_t passed as
  *    void*; NULL = legacy default stream). Calls that return host values synchronise that
  *    stream before returning.
@@ -296,19 +298,20 @@ int evp_stress_residual(int n, int precision, const void *sig_dev, void *spec_de
                         double *out_dev, void *cuda_stream);
 
 /* Allocation-free form of evp_stress_residual (the paper has no counterpart: it is a service of
- * this library). Some callers cannot allocate device memory at the point where they need the
- * residual -- for instance code in a host callback or another context where cudaMalloc is not
- * allowed, or a plug-in whose host application owns every device allocation -- and so cannot
- * supply the scratch buffer evp_stress_residual asks for. This entry point takes the same inputs
- * and outputs (sig_dev, spec_dev, out_dev, all caller-owned) but keeps its scratch in a fixed
- * array inside the library: 8192 doubles (64 KiB), enough for every n <= 256 in any precision,
- * held by each GPU that loads the library until the process exits. It calls no cudaMalloc,
- * cudaFree or other allocating routine. The first call on a device looks up that array's device
- * address (once per device, with that device current), so make the first call on each device
- * before any stream capture. All calls share the one array: calls that overlap on the GPU race
- * and must be serialised by the caller (e.g. one stream). Every scratch slot a call reads is
- * written earlier in the same call, so nothing needs clearing between calls. Sizes whose
- * partial sums would not fit return EVP_ERR_ARG. */
+ * this library). Some callers cannot allocate device memory themselves -- typically a plug-in or
+ * library component whose host application owns every device allocation and does not let its
+ * components call cudaMalloc -- and so cannot supply the scratch buffer evp_stress_residual asks
+ * for. This entry point takes the same inputs and outputs (sig_dev, spec_dev, out_dev, all
+ * caller-owned) but keeps its scratch in a fixed array inside the library: 8192 doubles (64 KiB),
+ * enough for every n <= 256 in any precision, held by each GPU that loads the library until the
+ * process exits. It calls no cudaMalloc, cudaFree or other allocating routine. The first call on
+ * a device looks up that array's device address (with that device current) and caches it with
+ * the id of the current context; a call in a new context (after a device reset, say) looks it up
+ * again. Make the first call on each device, and the first after a reset, before any stream
+ * capture. All calls share the one array: calls that overlap on the GPU race and must be
+ * serialised by the caller (e.g. one stream). Every scratch slot a call reads is written earlier
+ * in the same call, so nothing needs clearing between calls. Sizes whose partial sums would not
+ * fit return EVP_ERR_ARG. */
 int evp_stress_residual_noalloc(int n, int precision, const void *sig_dev, void *spec_dev, double *out_dev,
                                 void *cuda_stream);
 

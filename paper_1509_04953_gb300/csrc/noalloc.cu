@@ -1,9 +1,10 @@
 // Allocation-free variant of evp_stress_residual, for callers that cannot allocate device
-// memory themselves: code running where cudaMalloc is unavailable or forbidden (for instance
-// inside a host callback, a signal-safe or real-time section, or a plug-in whose host
-// application owns every device allocation), or a caller with no allocator of its own at hand.
-// evp_stress_residual needs a small caller-owned scratch buffer for its per-block partial sums;
-// this entry point uses a fixed array that lives in the library's own device memory instead.
+// memory themselves: typically a plug-in or library component whose host application owns
+// every device allocation (its own pool, its own accounting) and does not let components call
+// cudaMalloc, or a caller with no allocator of its own at hand. evp_stress_residual needs a
+// small caller-owned scratch buffer for its per-block partial sums; this entry point uses a
+// fixed array that lives in the library's own device memory instead.
+#include <cuda.h>
 #include <mutex>
 
 #include "../../include/evp.h"
@@ -17,21 +18,61 @@ constexpr int kMaxPartials = 8192;
 static __device__ __align__(256) double g_resid_partials[kMaxPartials];
 
 // Host code cannot use g_resid_partials as a device address: the name is only a host-side
-// stand-in. The device address is looked up once per device, with that device current.
+// stand-in. The device address is looked up once per device, with that device current, and
+// cached together with the id of the context it belongs to. A device reset (or any other way
+// the context is destroyed and re-created) gives the new context a new id, so the next call
+// looks the address up again instead of using a stale one.
 constexpr int kMaxDevices = 64;
-double *g_dev_ptr[kMaxDevices] = {};
+struct Slot {
+    unsigned long long ctx_id;   // 0: no context id known (the address is looked up on every call)
+    double *ptr;
+};
+Slot g_slot[kMaxDevices] = {};
 std::mutex g_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the context current on this thread, through the driver entry points the runtime hands
+// out (the library does not link libcuda itself); 0 when there is none or the driver lacks them.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 int partials_for_current_device(double **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return EVP_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
+    unsigned long long id = current_context_id();
+    Slot &s = g_slot[dev];
+    if (id == 0 || s.ptr == nullptr || s.ctx_id != id) {
         void *p = nullptr;
+        // also makes the device's primary context current on this thread if none was
         if (cudaGetSymbolAddress(&p, g_resid_partials) != cudaSuccess || p == nullptr) return EVP_ERR_CUDA;
-        g_dev_ptr[dev] = static_cast<double *>(p);
+        s.ptr = static_cast<double *>(p);
+        s.ctx_id = current_context_id();
     }
-    *out = g_dev_ptr[dev];
+    *out = s.ptr;
     return EVP_OK;
 }
 

@@ -144,3 +144,18 @@ def test_product_path_fails_loudly_without_a_gpu():
                  lambda: evp.voronoi(n, synth.voronoi_seeds(n, G, 0))):
         with pytest.raises(evp.EVPError, match="no CUDA device"):
             call()
+
+
+def test_residual_partials_fit_the_allocation_free_array_at_every_size(lib):
+    """evp_stress_residual_noalloc keeps the z pass's per-block partial sums in a fixed array of 8192 doubles.
+    The scratch that evp_stress_residual asks of its caller holds exactly those partial sums, so it must fit in
+    the fixed array for every size the allocation-free entry point accepts (n <= 256, every precision); the
+    largest, n = 256 in FP64, fills it exactly."""
+    nb = C.c_size_t(0)
+    sizes = {}
+    for prec in (0, 1, 2):
+        for n in (4, 8, 16, 32, 64, 128, 256):
+            assert lib.evp_residual_scratch_bytes(n, prec, C.byref(nb)) == 0
+            assert 0 < nb.value <= 8192 * 8, (n, prec, nb.value)
+            sizes[(n, prec)] = nb.value
+    assert max(sizes.values()) == 8192 * 8
