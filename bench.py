@@ -303,11 +303,30 @@ def native(args, ws, rank, local):
     return res
 
 
-ALG_BYTES_WORDS = None   # see hbm_bytes_per_voxel
-# measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one local-solve launch, per workload
-# (ncu, dram__bytes_read.sum + dram__bytes_write.sum averaged over 214 iterations of the second and third increments;
-# profiles/launches_cu128_mixed.md): pass 1 326.8 MB + pass 2 15.0 MB; re-measure after a change of these kernels
-NEWTON_TRAFFIC = {(128, "mixed", True): 341.8e6}
+# Measured DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum, averaged over 214 iterations of the
+# second and third increments) of one local-solve iteration (pass 1 326.8 MB + pass 2 15.0 MB), per workload,
+# with the SHA-256 prefix of the local-solve sources it was taken on. A figure taken on other sources is stale
+# and reported as null.
+NEWTON_TRAFFIC = {(128, "mixed", True): (341.8e6, "e086464008509734")}
+NEWTON_SOURCES = ("paper_1509_04953_gb300/csrc/newton.cu", "paper_1509_04953_gb300/csrc/local.cuh")
+
+
+def sources_sha(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(table, key, paths):
+    """The stored ncu traffic for `key` if it was taken on the current sources, else None."""
+    entry = table.get(key)
+    if entry is None:
+        return None
+    value, sha = entry
+    return value if sha == sources_sha(paths) else None
 
 
 def hbm_bytes_per_voxel(kernel, n, T):
@@ -345,21 +364,29 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
         t64, t32 = f64 / FP64_PEAK_TFLOPS, f32 / FP32_PEAK_TFLOPS
         flops, peak, pipe = (f64, FP64_PEAK_TFLOPS, "fp64") if t64 >= t32 else (f32, FP32_PEAK_TFLOPS, "fp32")
         alu = flops / (ms / 1e3) / 1e12
-        # algorithmic HBM bytes per launch: every voxel reads its trial strain, stress, tau_c and grain id
-        # (and with tangent reuse its 21 stored factor words) and writes its stress
-        words = 6 + 6 + 1 + (21 if reuse else 0) + 6
+        # algorithmic HBM bytes per launch, the method's operands of the local update (Eqs. HookeLaw and
+        # PlasticRate): total strain 6, plastic strain 6, the 12 critical resolved shear stresses, the grain id and
+        # the stress warm start 6 read, the stress 6 written. Stored tangent factors are this implementation's
+        # cache, not the method's work, and are not counted; the formulation's minimal operands (trial strain 6,
+        # stress 6, one tau_c, grain id -> stress 6) and the bytes with the factor cache are given as context.
+        words = 6 + 6 + 12 + 6 + 6
         bytes_launch = (words * T + 4) * N3
+        minimal_launch = ((6 + 6 + 1 + 6) * T + 4) * N3
+        with_cache_launch = ((6 + 6 + 1 + (21 if reuse else 0) + 6) * T + 4) * N3
         hbm = bytes_launch / avg_s / 1e9
         hpk = pk.get("hbm_gbs", 6800.0)
         alu_frac, hbm_frac = alu / peak, hbm / hpk
         detail = {"alu": {"pipe": pipe, "achieved": alu, "peak": peak, "unit": "TFLOP/s", "frac": alu_frac,
                           "flops_fp32": f32, "flops_fp64": f64},
                   "hbm": {"achieved": hbm, "peak": hpk, "unit": "GB/s", "frac": hbm_frac,
-                          "bytes_per_launch": bytes_launch, "peak_source": pk_kind}}
+                          "bytes_per_launch": bytes_launch, "peak_source": pk_kind,
+                          "minimal_operand_bytes_per_launch": minimal_launch,
+                          "frac_by_minimal_operands": minimal_launch / avg_s / 1e9 / hpk,
+                          "bytes_per_launch_with_factor_cache": with_cache_launch}}
         top = detail["hbm"] if hbm_frac >= alu_frac else detail["alu"]
-        # DRAM bytes of one local-solve launch (both passes) from an ncu capture of the current build at this
-        # workload (profiles/iteration_kernels_cu128_mixed.md), when one has been taken
-        traffic = NEWTON_TRAFFIC.get((wl.n, precision, reuse))
+        # DRAM bytes of one local-solve iteration (both passes) from an ncu capture at this workload, when one was
+        # taken on the current sources
+        traffic = measured_traffic(NEWTON_TRAFFIC, (wl.n, precision, reuse), NEWTON_SOURCES)
         return {"bound": "hbm" if hbm_frac >= alu_frac else "alu", "kernel": "newton",
                 "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"], "frac": top["frac"],
                 "traffic": traffic, "traffic_unit": "bytes per launch", "resources": detail,
@@ -367,7 +394,8 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
                         "Algorithmic flops: 1140 per residual+tangent evaluation, 544 per residual-only "
                         "evaluation, 80 per 6x6 LDL^T factorisation, 72 per pair of triangular solves, counted "
                         "by pipe, peak from unit counts and the maximum SM clock; algorithmic bytes: the "
-                        "per-voxel words read and written once per launch"}
+                        "method's per-voxel operands (strain, plastic strain, 12 critical stresses, grain id, "
+                        "stress warm start -> stress: 148 B FP32), read and written once per launch"}
     if hbm_bytes_per_voxel(dom, wl.n, T) is None:
         return {"bound": "unknown", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
@@ -638,14 +666,18 @@ def e2e(solver, wl, torch, evp):
     for s in range(steps):
         for k in names:
             t = host[k]
-            L.set_fields(solver.h, evp.FIELDS[k], t.data_ptr(), t.numel() * t.element_size(), 0)
+            rc = L.set_fields(solver.h, evp.FIELDS[k], t.data_ptr(), t.numel() * t.element_size(), 0)
+            if rc != 0:
+                raise evp.EVPError(f"set_fields({k}): {evp.EVP_ERR.get(rc, rc)}: {solver.last_error()}")
         _, es = solver.increment(wl.dE33, wl.dt)
         iters += es.iterations
         solver.nucleate(100 + s)
         solver.pf_step(wl.pf_steps)
         for k in names:
             t = host[k]
-            L.get_fields(solver.h, evp.FIELDS[k], t.data_ptr(), t.numel() * t.element_size(), 0)
+            rc = L.get_fields(solver.h, evp.FIELDS[k], t.data_ptr(), t.numel() * t.element_size(), 0)
+            if rc != 0:
+                raise evp.EVPError(f"get_fields({k}): {evp.EVP_ERR.get(rc, rc)}: {solver.last_error()}")
     e1.record(st)
     e1.synchronize()
     secs = e0.elapsed_time(e1) / 1e3

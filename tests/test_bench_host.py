@@ -8,7 +8,7 @@ import types
 import pytest
 
 
-def test_local_solve_roofline_counts_164_bytes_per_voxel_with_stored_factors():
+def test_local_solve_roofline_counts_the_methods_148_bytes_per_voxel():
     import bench
     n = 128
     N3 = n ** 3
@@ -18,19 +18,34 @@ def test_local_solve_roofline_counts_164_bytes_per_voxel_with_stored_factors():
                          evals=N3 * 100, pk={"hbm_gbs": 6000.0}, pk_kind="measured", precision="mixed",
                          facs=0, reuse=True)
     hbm = out["resources"]["hbm"]
-    assert hbm["bytes_per_launch"] == 164 * N3      # eps_tr 6, sigma 6, tau_c 1, factors 21, sigma out 6; g0
-    assert hbm["achieved"] == pytest.approx(164 * N3 / 1e-4 / 1e9)
+    # eps 6, eps_p 6, tau_c 12, sigma warm start 6 in, sigma 6 out; g0: the method's operands, no factor cache
+    assert hbm["bytes_per_launch"] == 148 * N3
+    assert hbm["minimal_operand_bytes_per_launch"] == 80 * N3          # eps_tr 6, sigma 6, tau_c 1, sigma 6; g0
+    assert hbm["bytes_per_launch_with_factor_cache"] == 164 * N3       # + 21 stored factor words
+    assert hbm["achieved"] == pytest.approx(148 * N3 / 1e-4 / 1e9)
     assert hbm["frac"] == pytest.approx(hbm["achieved"] / 6000.0)
     assert out["bound"] == "hbm" and out["frac"] == pytest.approx(hbm["frac"])
-    assert out["traffic"] == bench.NEWTON_TRAFFIC[(128, "mixed", True)]
     # FP32 pipe: residual-only evaluations with tangent reuse, FP32 triangular solves
     alu = out["resources"]["alu"]
     assert alu["pipe"] == "fp32"
     assert alu["flops_fp32"] == bench.NEWTON_FLOPS_RESID * N3 * 100 + bench.NEWTON_FLOPS_SOLVE * N3 * 100
-    # without stored factors the exact Newton reads 19 words
+    # the exact Newton has the same algorithmic operands
     ex = bench.roofline("newton", {"newton": (ms, launches)}, wl, N3, 100, N3 * 100, N3 * 100, {"hbm_gbs": 6000.0},
                         "measured", "mixed", reuse=False)
-    assert ex["resources"]["hbm"]["bytes_per_launch"] == (19 * 4 + 4) * N3
+    assert ex["resources"]["hbm"]["bytes_per_launch"] == 148 * N3
+
+
+def test_stored_traffic_is_dropped_once_its_sources_change(tmp_path, monkeypatch):
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.sources_sha(["k.cu"])
+    table = {(1, "mixed", True): (123.0, sha)}
+    assert bench.measured_traffic(table, (1, "mixed", True), ["k.cu"]) == 123.0
+    src.write_text("kernel v2")
+    assert bench.measured_traffic(table, (1, "mixed", True), ["k.cu"]) is None
+    assert bench.measured_traffic(table, (2, "mixed", True), ["k.cu"]) is None
 
 
 def test_fft_pass_bytes_follow_the_half_spectrum():
