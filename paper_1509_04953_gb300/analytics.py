@@ -57,9 +57,30 @@ def avrami_fit(t, X, x_lo=0.05, x_hi=0.95, t0=None):
     return float(m), float(math.exp(c))
 
 
+def grain_components(grain_id, n):
+    """Label grains as connected components: two voxels belong to the same grain when a chain of face
+    neighbours (6-neighbour, periodic) with their grain id joins them. One id can form several grains (a
+    recrystallised id that two growth fronts split, a deformed grain cut by a new one). Returns
+    (number of grains, label per voxel in 0..number-1)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    g = np.asarray(grain_id).reshape(n, n, n)
+    N3 = g.size
+    idx = np.arange(N3, dtype=np.int64).reshape(n, n, n)
+    rows, cols = [], []
+    for ax in range(3):
+        same = g == np.roll(g, -1, axis=ax)
+        rows.append(idx[same])
+        cols.append(np.roll(idx, -1, axis=ax)[same])
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    adj = coo_matrix((np.ones(r.size, dtype=np.int8), (r, c)), shape=(N3, N3))
+    ncomp, labels = connected_components(adj, directed=False)
+    return int(ncomp), labels
+
+
 def grain_statistics(grain_id, n, dx=1.0):
-    """Number of distinct grains and the mean equivalent-sphere diameter (same length unit as dx)."""
-    g = np.asarray(grain_id).reshape(-1)
-    ng = len(np.unique(g))
-    vol = g.size / ng * dx ** 3
-    return ng, float((6.0 * vol / math.pi) ** (1.0 / 3.0))
+    """Number of grains (connected components, see grain_components) and their mean equivalent-sphere
+    diameter (the mean over grains of (6 V / pi)^(1/3), same length unit as dx)."""
+    ng, labels = grain_components(grain_id, n)
+    vol = np.bincount(labels, minlength=ng).astype(np.float64) * dx ** 3
+    return ng, float(np.mean((6.0 * vol / math.pi) ** (1.0 / 3.0)))

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 import oracle as O
 from paper_1509_04953_gb300 import analytics as A
@@ -41,3 +42,58 @@ def test_grain_statistics():
     g = np.repeat(np.arange(8), 64)
     ng, d = A.grain_statistics(g, 8, dx=2.0)
     assert ng == 8 and abs(d - (6 * 64 * 8 / math.pi) ** (1 / 3)) < 1e-12
+
+
+def _flood_fill_count(g, n):
+    """Brute force: count 6-connected periodic same-id components by breadth-first search."""
+    g = np.asarray(g).reshape(n, n, n)
+    seen = np.zeros_like(g, dtype=bool)
+    count = 0
+    for start in np.ndindex(n, n, n):
+        if seen[start]:
+            continue
+        count += 1
+        stack = [start]
+        seen[start] = True
+        while stack:
+            z, y, x = stack.pop()
+            for dz, dy, dx in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                w = ((z + dz) % n, (y + dy) % n, (x + dx) % n)
+                if not seen[w] and g[w] == g[z, y, x]:
+                    seen[w] = True
+                    stack.append(w)
+    return count
+
+
+def test_grain_components_are_periodic_six_neighbour_regions():
+    n = 8
+    g = np.zeros((n, n, n), dtype=np.int32)
+    g[:, :, 0:2] = 1          # a slab at x = 0, 1 ...
+    g[:, :, 7] = 1            # ... continues across the periodic wrap: one grain
+    g[2:4, 2:4, 4:6] = 2      # two separate blocks of id 2: two grains
+    g[5:7, 5:7, 4:6] = 2
+    g[0, 4, 3] = 3            # id 3 at two voxels touching only along an edge: two grains (6-neighbour)
+    g[1, 5, 3] = 3
+    ng, labels = A.grain_components(g.reshape(-1), n)
+    assert ng == 1 + 1 + 2 + 2              # id 0 (the rest, one region), slab, two blocks, two single voxels
+    assert ng == _flood_fill_count(g, n)
+    lab = labels.reshape(n, n, n)
+    assert lab[0, 0, 0] == lab[0, 0, 7] and lab[2, 2, 4] != lab[5, 5, 4] and lab[0, 4, 3] != lab[1, 5, 3]
+
+
+def test_grain_components_match_brute_force_on_random_voronoi():
+    for seed, (n, G) in enumerate([(6, 5), (8, 12), (10, 30)]):
+        g = O.voronoi(n, synth.voronoi_seeds(n, G, 40 + seed))
+        rng = np.random.default_rng(seed)
+        g = np.where(rng.random(g.size) < 0.1, G + rng.integers(0, 3, g.size), g)   # scattered "nuclei"
+        assert A.grain_components(g, n)[0] == _flood_fill_count(g, n)
+
+
+def test_grain_statistics_mean_equivalent_diameter():
+    n = 4
+    g = np.zeros((n, n, n), dtype=np.int32)
+    g[:, :, 2:] = 1                          # two grains of 32 voxels
+    g[0, 0, 0] = 2                           # and one of 1 voxel
+    ng, d = A.grain_statistics(g.reshape(-1), n, dx=0.5)
+    vols = np.array([31.0, 32.0, 1.0]) * 0.125
+    assert ng == 3 and d == pytest.approx(np.mean((6 * vols / math.pi) ** (1 / 3)), rel=1e-14)
