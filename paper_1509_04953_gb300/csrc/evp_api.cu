@@ -35,6 +35,8 @@ struct evp_handle {
     int r, npf;      // phase-field grid: r = 1 (the mechanics grid) or 2 (refined), npf = r n points per edge
     long N3pf;
     int32_t *gpf;    // argmax id per PF point (= g when r = 1)
+    uint8_t *rmax, *rmax2;   // per-row slot bounds of (ids, eta) and (ids2, eta2), for the tiled PF step
+    long rmax_bytes;
     double *kpf;     // rho_tot on the PF grid (= k when r = 1)
     int fac_valid;   // stored tangent factors hold a factorisation (of some earlier state) for every voxel
     uint32_t *bitmap;
@@ -212,6 +214,8 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
     char *g0 = take(N3 * 4), *g = take(N3 * 4), *gprev = take(N3 * 4), *draws = take(N3 * 4);
     char *ids = take(K * M3 * 4), *ids2 = take(K * M3 * 4);
     char *gpf = take(r == 2 ? M3 * 4 : 0), *kpf = take(r == 2 ? M3 * 8 : 0);
+    const long rb = pf_row_bounds_bytes(r * (int)n);
+    char *rmax = take(rb), *rmax2 = take(rb);
     char *partials = take(sizeof(double) * npart), *scal = take(sizeof(double) * 64);
     char *flags = take(sizeof(int32_t) * 16);
     char *ctl = take(256);   // FpCtl
@@ -248,6 +252,9 @@ size_t layout(const evp_config *c, evp_handle *h, char *base) {
         h->npf = r * (int)n;
         h->N3pf = M3;
         h->gpf = r == 2 ? (int32_t *)gpf : h->g;
+        h->rmax = (uint8_t *)rmax;
+        h->rmax2 = (uint8_t *)rmax2;
+        h->rmax_bytes = rb;
         h->kpf = r == 2 ? (double *)kpf : h->k;
     }
     return (off + 255) & ~(size_t)255;
@@ -709,6 +716,10 @@ int evp_init(evp_handle **out, const evp_config *cfg, const evp_params *p, const
         CK(mr_refresh_k(h));
     }
     CK(pf_init(h->n, h->r, h->K, h->g0, h->ids, h->eta, h->ids2, h->eta2, h->dbl, h->gpf, h->st));
+    if (h->rmax_bytes) {   // one entry per point in (ids, eta), none in (ids2, eta2)
+        CK(cudaMemsetAsync(h->rmax, 1, h->rmax_bytes, h->st));
+        CK(cudaMemsetAsync(h->rmax2, 0, h->rmax_bytes, h->st));
+    }
     if (h->r == 2) CK(pf_interp(h->n, h->k, h->kpf, h->st));
     CK(cudaStreamSynchronize(h->st));
     return EVP_OK;
@@ -1034,12 +1045,13 @@ int pf_step(evp_handle *h, int nsteps, pf_stats *out) {
         PROF(10, 1);
         if (h->dbl)
             CK(pf_one_step<double>(h->npf, h->ids, (double *)h->eta, h->ids2, (double *)h->eta2, h->gpf, h->kpf,
-                                   h->pc, h->flags + 2, h->st));
+                                   h->pc, h->flags + 2, h->rmax, h->rmax2, h->st));
         else
             CK(pf_one_step<float>(h->npf, h->ids, (float *)h->eta, h->ids2, (float *)h->eta2, h->gpf, h->kpf, h->pc,
-                                  h->flags + 2, h->st));
+                                  h->flags + 2, h->rmax, h->rmax2, h->st));
         int32_t *ti = h->ids; h->ids = h->ids2; h->ids2 = ti;
         void *te = h->eta; h->eta = h->eta2; h->eta2 = te;
+        uint8_t *tr = h->rmax; h->rmax = h->rmax2; h->rmax2 = tr;
     }
     if (h->r == 2 && nsteps > 0) {   // grain ids of the mechanics grid from the PF children
         PROF(11, 1);
@@ -1133,6 +1145,8 @@ int set_fields(evp_handle *h, uint32_t mask, const void *src, size_t bytes, int 
         CK(cudaMemcpyAsync(field_ptr(h, bit), (const char *)src + off, fb, kind, h->st));
         off += fb;
     }
+    if ((mask & EVP_F_IDS) && h->rmax_bytes)   // arbitrary active sets: every slot may be in use
+        CK(cudaMemsetAsync(h->rmax, h->K, h->rmax_bytes, h->st));
     if (mask & (EVP_F_RHO | EVP_F_GND)) {
         if (h->mr) CK(mr_refresh_k(h));
         else if (h->dbl) CK(refresh_k<double>(h->N3, (double *)h->rho, h->k, h->st));

@@ -153,9 +153,14 @@ struct PFConst {
     float m_f, kappa_f, gam_f, L_dt_f, drop_f;   // FP32 copies for the FP32 path
     void set_fp32() { m_f = (float)m; kappa_f = (float)kappa; gam_f = (float)gam; L_dt_f = (float)L_dt; drop_f = (float)drop; }
 };
+// One explicit Allen-Cahn step of the active sets (ids, eta) -> (ids2, eta2), argmax ids into g. Grids of 32 points
+// per edge and more take the tiled kernel, which reads the per-row slot bounds rcur of (ids, eta) and rewrites
+// rdst, the bounds of (ids2, eta2) (pf_row_bounds_bytes(n) bytes each; see pf.cu); smaller grids ignore them.
+long pf_row_bounds_bytes(int n);
 template <typename T>
 cudaError_t pf_one_step(int n, const int32_t *ids, const T *eta, int32_t *ids2, T *eta2, int32_t *g,
-                        const double *k, PFConst pc, int32_t *overflow, cudaStream_t s);
+                        const double *k, PFConst pc, int32_t *overflow, const uint8_t *rcur, uint8_t *rdst,
+                        cudaStream_t s);
 template <typename T>
 cudaError_t pf_soften(long N3, const int32_t *gprev, const int32_t *g, T *rho, double *k, int G, double s_soften,
                       cudaStream_t s);

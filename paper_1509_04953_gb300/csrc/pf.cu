@@ -46,6 +46,13 @@ __device__ __forceinline__ Nbr neighbours(int n, long v) {
 
 constexpr int kEmpty = 0x7fffffff;
 
+// Asynchronous global -> shared copy of B bytes (cp.async; completion by commit / wait groups).
+template <int B> __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (B == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
 
 template <typename T>
 __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta,
@@ -163,6 +170,239 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
         eta2[j * N3 + v] = (T)0;
     }
     if (ovf) atomicAdd(overflow, 1);
+}
+
+// ---- tiled PF step (grids of 32 points per edge and more) ----
+// The same update as k_pf, voxel by voxel and in the same arithmetic order (so FP64 results are bitwise the
+// same), organised for bandwidth. A CTA owns a 32 x 8 column tile and marches through kZC planes of z. The
+// active sets of the planes z-1, z, z+1 (interior) and the x/y halo of plane z are staged in shared memory by
+// cp.async, one plane ahead of the compute, so the seven-list merge reads shared memory instead of issuing
+// chains of dependent global loads. Which slots to stage comes from a per-row bound: rmax[s] >= the number of
+// entries of every point of the 32-point row segment s = (z n + y) (n / 32) + x / 32, so every staged load is
+// independent of the others. Each step writes the exact bound of the rows it produced and clears, in the
+// destination, the slots between a point's new count and the destination's previous bound, which keeps every
+// list -1 / 0 terminated over all K slots (the layout every other reader of the active sets assumes).
+constexpr int kTX = 32, kTY = 8, kZC = 16;
+constexpr int kPlane = kTX * kTY;             // interior points of one plane tile
+constexpr int kHalo = 2 * kTX + 2 * kTY;      // rows y0-1, y0+8 and columns x0-1, x0+32 of the centre plane
+constexpr int kTileThreads = kTX * kTY;
+
+template <typename T>
+struct PFTile {
+    // element index space shared by id[] and e[]: 4 interior plane buffers [buf][slot][point], then two halo
+    // buffers [hbuf][slot][halo point]
+    int32_t id[4 * KM * kPlane + 2 * KM * kHalo];
+    T e[4 * KM * kPlane + 2 * KM * kHalo];
+    uint8_t rin[(kZC + 2) * (kTY + 2)];   // bounds of the current buffer: planes z0-1..z0+kZC, rows y0-1..y0+8
+    uint8_t rxl[kZC * kTY], rxr[kZC * kTY];   // bounds of the left / right neighbour segments, planes z0.., rows y0..
+    uint8_t rdst[kZC * kTY];              // previous bounds of the destination rows
+};
+
+__device__ __forceinline__ int tile_int_index(int buf, int j, int p) { return (buf * KM + j) * kPlane + p; }
+__device__ __forceinline__ int tile_halo_index(int hb, int j, int hp) {
+    return 4 * KM * kPlane + (hb * KM + j) * kHalo + hp;
+}
+
+// Issue the asynchronous copies of one point's slots [0, R) into the tile (element index base, stride), and
+// terminate its list at slot R in shared memory when R < K (the slot that global memory also holds -1 at).
+template <typename T>
+__device__ __forceinline__ void stage_point(PFTile<T> &tb, int base, int stride, int R, int K,
+                                            const int32_t *__restrict__ ids, const T *__restrict__ eta, long N3,
+                                            long v) {
+    R = min(R, K);   // a bound never exceeds K; the clamp keeps every access inside the K slot planes regardless
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+        if (j < R) {
+            cp_async<4>(&tb.id[base + j * stride], ids + j * N3 + v);
+            cp_async<sizeof(T)>(&tb.e[base + j * stride], eta + j * N3 + v);
+        }
+    if (R < K) tb.id[base + R * stride] = -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads, 2)
+k_pf_tile(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta, int32_t *__restrict__ ids2,
+          T *__restrict__ eta2, int32_t *__restrict__ gout, const double *__restrict__ kf, PFConst pc,
+          int32_t *__restrict__ overflow, const uint8_t *__restrict__ rcur, uint8_t *__restrict__ rdst) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PFTile<T> &tb = *reinterpret_cast<PFTile<T> *>(smem_raw);
+    const long N3 = (long)n * n * n;
+    const int msk = n - 1, nseg = n / kTX;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int xs = blockIdx.x, x0 = xs * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * kZC;
+    const int K = pc.K, G = pc.G;
+    auto seg = [&](int z, int y, int s) { return ((long)z * n + y) * nseg + s; };
+    // row bounds of the chunk
+    for (int t = threadIdx.x; t < (kZC + 2) * (kTY + 2); t += kTileThreads) {
+        const int pz = t / (kTY + 2), ry = t % (kTY + 2);
+        tb.rin[t] = rcur[seg((z0 - 1 + pz) & msk, (y0 - 1 + ry) & msk, xs)];
+    }
+    for (int t = threadIdx.x; t < kZC * kTY; t += kTileThreads) {
+        const int pz = t / kTY, ry = t % kTY;
+        tb.rxl[t] = rcur[seg(z0 + pz, y0 + ry, (xs + nseg - 1) % nseg)];
+        tb.rxr[t] = rcur[seg(z0 + pz, y0 + ry, (xs + 1) % nseg)];
+        tb.rdst[t] = rdst[seg(z0 + pz, y0 + ry, xs)];
+    }
+    __syncthreads();
+    const int p = ty * kTX + tx;
+    // plane index pp = 0 .. kZC+1 holds z = z0 - 1 + pp in interior buffer pp % 4
+    auto stage_plane = [&](int pp) {
+        const int z = (z0 - 1 + pp) & msk;
+        const long v = ((long)z * n + (y0 + ty)) * n + x0 + tx;
+        stage_point(tb, tile_int_index(pp & 3, 0, p), kPlane, tb.rin[pp * (kTY + 2) + ty + 1], K, ids, eta, N3, v);
+    };
+    // halo of centre plane i (z = z0 + i) into halo buffer i % 2
+    auto stage_halo = [&](int i) {
+        const int t = threadIdx.x;
+        if (t >= kHalo) return;
+        const int z = z0 + i;
+        int x, y, R;
+        if (t < kTX) { x = x0 + t; y = (y0 - 1) & msk; R = tb.rin[(i + 1) * (kTY + 2)]; }
+        else if (t < 2 * kTX) { x = x0 + t - kTX; y = (y0 + kTY) & msk; R = tb.rin[(i + 1) * (kTY + 2) + kTY + 1]; }
+        else if (t < 2 * kTX + kTY) { x = (x0 - 1) & msk; y = y0 + t - 2 * kTX; R = tb.rxl[i * kTY + t - 2 * kTX]; }
+        else { x = (x0 + kTX) & msk; y = y0 + t - 2 * kTX - kTY; R = tb.rxr[i * kTY + t - 2 * kTX - kTY]; }
+        const long v = ((long)z * n + y) * n + x;
+        stage_point(tb, tile_halo_index(i & 1, 0, t), kHalo, R, K, ids, eta, N3, v);
+    };
+    stage_plane(0);
+    stage_plane(1);
+    stage_plane(2);
+    stage_halo(0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+
+    T m, kap, gam, Ldt, drop;   // in the field precision (no FP64 conversions on the FP32 path)
+    if constexpr (sizeof(T) == 4) { m = pc.m_f; kap = pc.kappa_f; gam = pc.gam_f; Ldt = pc.L_dt_f; drop = pc.drop_f; }
+    else { m = pc.m; kap = pc.kappa; gam = pc.gam; Ldt = pc.L_dt; drop = pc.drop; }
+
+    for (int i = 0; i < kZC; ++i) {
+        const int z = z0 + i;
+        const long v = ((long)z * n + (y0 + ty)) * n + x0 + tx;
+        if (i + 1 < kZC) {   // the next plane's data, under this plane's compute
+            stage_plane(i + 3);
+            stage_halo(i + 1);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+        const double kv = kf[v];
+        // the seven lists: self, x-, x+, y-, y+, z-, z+ (element index of slot 0, slot stride)
+        const int c = (i + 1) & 3, hb = i & 1;
+        int base[7], str[7];
+        base[0] = tile_int_index(c, 0, p); str[0] = kPlane;
+        if (tx > 0) { base[1] = base[0] - 1; str[1] = kPlane; } else { base[1] = tile_halo_index(hb, 0, 2 * kTX + ty); str[1] = kHalo; }
+        if (tx < kTX - 1) { base[2] = base[0] + 1; str[2] = kPlane; }
+        else { base[2] = tile_halo_index(hb, 0, 2 * kTX + kTY + ty); str[2] = kHalo; }
+        if (ty > 0) { base[3] = base[0] - kTX; str[3] = kPlane; } else { base[3] = tile_halo_index(hb, 0, tx); str[3] = kHalo; }
+        if (ty < kTY - 1) { base[4] = base[0] + kTX; str[4] = kPlane; } else { base[4] = tile_halo_index(hb, 0, kTX + tx); str[4] = kHalo; }
+        base[5] = tile_int_index(i & 3, 0, p); str[5] = kPlane;
+        base[6] = tile_int_index((i + 2) & 3, 0, p); str[6] = kPlane;
+
+        // local sums over the voxel's own list, ascending id
+        T S2 = (T)0, D = (T)0, R = (T)0;
+        for (int j = 0; j < K; ++j) {
+            const int id = tb.id[base[0] + j * kPlane];
+            if (id < 0) break;
+            const T e = tb.e[base[0] + j * kPlane];
+            S2 += e * e;
+            if (id < G) D += e * e;
+            else R += e * e;
+        }
+        const T Ep = (T)(pc.Escale * kv);
+        const T Ssum = D + R;
+        int head[7], pos[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            pos[q] = 0;
+            const int id = tb.id[base[q]];
+            head[q] = id < 0 ? kEmpty : id;
+        }
+        int kid[KM + 1];
+        T ke[KM + 1];
+#pragma unroll
+        for (int j = 0; j <= KM; ++j) {
+            kid[j] = kEmpty;
+            ke[j] = (T)0;
+        }
+        int cnt = 0;
+        int best_id = kEmpty, kbest_id = kEmpty;
+        T best = (T)-INFINITY, kbest = (T)-INFINITY;
+        bool ovf = false;
+        for (int guard = 0; guard < 7 * KM; ++guard) {
+            int cid = head[0];
+#pragma unroll
+            for (int q = 1; q < 7; ++q) cid = min(cid, head[q]);
+            if (cid == kEmpty) break;
+            T e[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                e[q] = (T)0;
+                if (head[q] == cid) {
+                    e[q] = tb.e[base[q] + pos[q] * str[q]];
+                    ++pos[q];
+                    int nx = kEmpty;
+                    if (pos[q] < K) {
+                        const int id = tb.id[base[q] + pos[q] * str[q]];
+                        nx = id < 0 ? kEmpty : id;
+                    }
+                    head[q] = nx;
+                }
+            }
+            const T e0 = e[0];
+            const T lap = e[1] + e[2] + e[3] + e[4] + e[5] + e[6] - (T)6 * e0;
+            const T df0 = m * (e0 * e0 * e0 - e0 + (T)2 * gam * e0 * (S2 - e0 * e0));
+            T ddef = (T)0;
+            if (Ssum > (T)1e-12)
+                ddef = (cid < G) ? (T)2 * Ep * e0 * R / (Ssum * Ssum) : -(T)2 * Ep * e0 * D / (Ssum * Ssum);
+            const T en = e0 - Ldt * (df0 - kap * lap + ddef);
+            if (en > best) { best = en; best_id = cid; }
+            if (en >= drop) {
+                if (en > kbest) { kbest = en; kbest_id = cid; }   // ascending ids: a tie keeps the smaller id
+#pragma unroll
+                for (int j = 0; j <= KM; ++j)
+                    if (j == cnt) { kid[j] = cid; ke[j] = en; }
+                ++cnt;
+                if (cnt > K) {   // over capacity: remove the worst entry (smallest value, larger id among equals)
+                    ovf = true;
+                    int wj = 0, wid = kid[0];
+                    T wv = ke[0];
+#pragma unroll
+                    for (int j = 1; j <= KM; ++j)
+                        if (j < cnt && (ke[j] < wv || (ke[j] == wv && kid[j] > wid))) { wj = j; wv = ke[j]; wid = kid[j]; }
+#pragma unroll
+                    for (int j = 0; j < KM; ++j)
+                        if (j >= wj) { kid[j] = kid[j + 1]; ke[j] = ke[j + 1]; }
+                    kid[KM] = kEmpty;
+                    ke[KM] = (T)0;
+                    cnt = K;
+                }
+            }
+        }
+        if (cnt == 0 && best_id != kEmpty) {   // nothing above the drop threshold: keep the largest
+            kid[0] = best_id;
+            ke[0] = best;
+            cnt = 1;
+            kbest_id = best_id;
+        }
+        gout[v] = kbest_id;
+        // kept entries, then the slots up to the destination's previous bound cleared (beyond it they are empty)
+        const int rd = min((int)tb.rdst[i * kTY + ty], K);
+#pragma unroll
+        for (int j = 0; j < KM; ++j) {
+            if (j < cnt) {
+                ids2[j * N3 + v] = kid[j];
+                eta2[j * N3 + v] = ke[j];
+            } else if (j < rd) {
+                ids2[j * N3 + v] = -1;
+                eta2[j * N3 + v] = (T)0;
+            }
+        }
+        const int rowmax = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+        if (tx == 0) rdst[seg(z, y0 + ty, xs)] = (uint8_t)rowmax;
+        const unsigned ob = __ballot_sync(0xffffffffu, ovf);
+        if (tx == 0 && ob) atomicAdd(overflow, __popc(ob));
+        if (i + 1 < kZC) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+    }
 }
 
 template <typename T>
@@ -374,12 +614,26 @@ __global__ void k_pf_init(int n, int r, int K, const int32_t *__restrict__ g0, i
 
 }  // namespace
 
+long pf_row_bounds_bytes(int n) { return n >= kTX ? (long)n * n * (n / kTX) : 0; }
+
 template <typename T>
 cudaError_t pf_one_step(int n, const int32_t *ids, const T *eta, int32_t *ids2, T *eta2, int32_t *g, const double *k,
-                        PFConst pc, int32_t *overflow, cudaStream_t s) {
+                        PFConst pc, int32_t *overflow, const uint8_t *rcur, uint8_t *rdst, cudaStream_t s) {
     const long N3 = (long)n * n * n;
     if (pc.K > KM || pc.K < 1) return cudaErrorInvalidValue;
-    k_pf<T><<<(int)((N3 + kPF - 1) / kPF), kPF, 0, s>>>(n, ids, eta, ids2, eta2, g, k, pc, overflow);
+    if (n >= kTX && rcur != nullptr && rdst != nullptr) {
+        static bool attr_set = false;   // per instantiation
+        const int sm = (int)sizeof(PFTile<T>);
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(k_pf_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        const dim3 grid(n / kTX, n / kTY, n / kZC);
+        k_pf_tile<T><<<grid, kTileThreads, sm, s>>>(n, ids, eta, ids2, eta2, g, k, pc, overflow, rcur, rdst);
+    } else {
+        k_pf<T><<<(int)((N3 + kPF - 1) / kPF), kPF, 0, s>>>(n, ids, eta, ids2, eta2, g, k, pc, overflow);
+    }
     return cudaGetLastError();
 }
 
@@ -435,9 +689,9 @@ cudaError_t pf_init(int n, int r, int K, const int32_t *g0, int32_t *ids, void *
 template cudaError_t pf_restrict<float>(int, int, const int32_t *, const float *, int32_t *, cudaStream_t);
 template cudaError_t pf_restrict<double>(int, int, const int32_t *, const double *, int32_t *, cudaStream_t);
 template cudaError_t pf_one_step<float>(int, const int32_t *, const float *, int32_t *, float *, int32_t *,
-                                        const double *, PFConst, int32_t *, cudaStream_t);
+                                        const double *, PFConst, int32_t *, const uint8_t *, uint8_t *, cudaStream_t);
 template cudaError_t pf_one_step<double>(int, const int32_t *, const double *, int32_t *, double *, int32_t *,
-                                         const double *, PFConst, int32_t *, cudaStream_t);
+                                         const double *, PFConst, int32_t *, const uint8_t *, uint8_t *, cudaStream_t);
 template cudaError_t pf_soften<float>(long, const int32_t *, const int32_t *, float *, double *, int, double, cudaStream_t);
 template cudaError_t pf_soften<double>(long, const int32_t *, const int32_t *, double *, double *, int, double, cudaStream_t);
 template cudaError_t pf_stats_launch<float>(int, const int32_t *, const float *, const int32_t *, const double *, PFConst,

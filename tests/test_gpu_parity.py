@@ -81,6 +81,27 @@ def test_rfft3d_matches_oracle_fft(ev, n, prec):
     assert rel(back, x) < (1e-14 if prec == "fp64" else 2e-6)
 
 
+@pytest.mark.parametrize("n,prec,nf", [(128, "fp64", 2), (128, "fp32", 6), (256, "fp32", 1)])
+def test_rfft3d_matches_oracle_fft_at_the_bench_sizes(ev, n, prec, nf):
+    """The 128^3 and 256^3 instantiations (radix 16 x 8 and 16 x 16 line transforms) that the headline and the
+    large workload run, element by element against the oracle's radix-2 FFT, forward and inverse. At 128^3 FP32
+    all six fields go through in one call, as in the fixed point."""
+    import torch
+    rng = np.random.default_rng(n + nf)
+    x = rng.standard_normal((nf, n, n, n))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    spec_d = ev.rfft3d(torch.tensor(x, dtype=dt, device="cuda"))
+    spec = spec_d.cpu().numpy()
+    # FP32: a few units of rounding per radix pass, relative to the largest coefficient
+    tol = 1e-13 if prec == "fp64" else 3e-6
+    for f in range(min(nf, 2)):
+        full = O.fft3d(x[f].astype(np.complex128), -1)
+        assert rel(spec[f], full[:, :, : n // 2 + 1]) < tol
+        del full
+    back = ev.irfft3d(spec_d).cpu().numpy() / n ** 3
+    assert rel(back, x) < (1e-14 if prec == "fp64" else 3e-6)
+
+
 @pytest.mark.parametrize("n,prec", [(8, "fp64"), (16, "fp64"), (32, "fp64"), (16, "fp32"), (64, "fp32")])
 def test_stress_residual_matches_oracle(ev, n, prec):
     import torch
@@ -175,6 +196,69 @@ def test_full_size_headline_increment_against_oracle_checks(ev, mat):
     fields["k"] = gpu.get("k")[0]
     sample = np.random.default_rng(5).choice(n ** 3, 400, replace=False)
     check_first_increment(mat, quat, g0, n, wl.dt, tol, fields, st.sig_mean, sample, loc_tol=2e-4, state_tol=2e-3)
+
+
+def test_full_size_large_workload_increment_against_oracle_checks(ev, mat):
+    """The large workload: 256^3 voxels, 1024 grains, mixed precision, its strain increment and time step. After
+    the first converged increment the FP64 oracle confirms equilibrium (its FFT of the GPU's stress), the boundary
+    conditions and, at 200 sampled voxels, the local and state updates, with the tolerances of the 128^3 check."""
+    from increment_checks import check_first_increment
+    wl = synth.WORKLOADS["cu256"]
+    n, G, seed, tol = wl.n, wl.grains, wl.seed, 1e-6
+    seeds = synth.voronoi_seeds(n, G, seed)
+    quat = synth.orientations(G, seed)
+    g0 = ev.voronoi(n, seeds).cpu().numpy()
+    gpu = ev.Solver(n, G, g0, quat, mat, seed, precision="mixed", tol=tol, max_iter=5000)
+    rc, st = gpu.increment(wl.dE33, wl.dt)
+    assert rc == 0 and st.iterations > 1
+    fields = {f: gpu.get(f) for f in ("sig", "eps", "epsp", "rho")}
+    fields["k"] = gpu.get("k")[0]
+    gpu.close()
+    sample = np.random.default_rng(6).choice(n ** 3, 200, replace=False)
+    check_first_increment(mat, quat, g0, n, wl.dt, tol, fields, st.sig_mean, sample, loc_tol=2e-4, state_tol=2e-3)
+
+
+def test_coupled_window_at_64_cubed_with_nucleation_matches_oracle(ev, mat):
+    """The 64^3 / 64-grain coupled workload over a window of increments in which nuclei form (densities raised to
+    k between 0.1 and 0.45 k_c, so that about 1 % of the boundary voxels nucleate from the first increment on): each increment a fixed number
+    of fixed-point iterations, nucleation and five PF steps, the same on both sides. Grain ids, nucleation sites,
+    fresh ids, draw counters and active-set ids bit-exact every increment; stress, strain and densities within
+    1e-10 (fixed iterations, FP64); no near-threshold flips."""
+    wl = synth.WORKLOADS["cu64"]
+    n, G, seed = wl.n, wl.grains, wl.seed
+    kw = dict(tol=1e-14, max_iter=12, allow_unconverged=1)
+    gpu, ref, _ = make_pair(ev, mat, n, G, seed, **kw)
+    rng = np.random.default_rng(11)
+    rho = np.repeat(rng.uniform(0.1, 0.45, size=(1, n ** 3)) * mat.kc / 12.0, 12, axis=0)
+    gpu.set("rho", rho)
+    ref.field("rho")[:] = rho
+    ref.refresh_derived()
+    assert rel(gpu.get("k")[0], ref.field("k")[0]) == 0.0
+    total = 0
+    for inc in range(3):
+        rc, st = gpu.increment(wl.dE33, wl.dt)
+        rco, sto = ref.increment(wl.dE33, wl.dt)
+        assert rc == 1 and rco == 1 and st.iterations == sto.iterations == 12
+        assert rel(gpu.get("sig"), ref.field("sig")) < FP64_TOL
+        assert rel(gpu.get("rho"), ref.field("rho")) < FP64_TOL
+        assert rel(gpu.get("k")[0], ref.field("k")[0]) < FP64_TOL
+        _, nn = gpu.nucleate(inc)
+        _, nno = ref.nucleate(inc)
+        assert nn == nno and nn > 0
+        total += nn
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))        # nucleation sites and fresh ids
+        assert np.array_equal(gpu.get("draws")[0], ref.ifield("draws"))
+        assert gpu.next_id == ref.next_id
+        _, ps = gpu.pf_step(wl.pf_steps)
+        _, pso = ref.pf_step(wl.pf_steps)
+        assert np.array_equal(gpu.get("ids"), ref.ifield("ids"))        # active sets
+        assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))         # argmax ids after the sweep: no flips
+        assert rel(gpu.get("eta"), ref.field("eta")) < FP64_TOL
+        assert ps.n_grains == pso.n_grains and ps.X_rex == pso.X_rex and ps.overflow == pso.overflow
+        assert abs(ps.F_tot / pso.F_tot - 1) < 1e-9
+        assert rel(gpu.get("rho"), ref.field("rho")) < FP64_TOL     # sweep softening at the same voxels
+    assert total > 100
+    assert ps.X_rex > 0.0
 
 
 def test_converged_increments_match_oracle_fp64(ev, mat):
@@ -273,8 +357,11 @@ def pf_setup(ev, mat, n, G, seed, kmax=8, nuclei=(5, 400, 1000, 1500)):
 
 
 @pytest.mark.parametrize("kmax", [8, 2])
-def test_pf_steps_bit_exact_fp64(ev, mat, kmax):
-    n, G = 16, 8
+@pytest.mark.parametrize("n,G", [(16, 8), (32, 27), (64, 64)])
+def test_pf_steps_bit_exact_fp64(ev, mat, kmax, n, G):
+    """Grids of 32 points per edge and more run the tiled PF kernel (shared-memory staging, per-row slot bounds),
+    smaller ones the one-thread-per-point kernel: both bitwise equal to the oracle, with few (K = 2, overflows) and
+    many active-set slots, starting from bounds made conservative by set_fields."""
     gpu, ref = pf_setup(ev, mat, n, G, 3, kmax=kmax)
     for call in range(3):
         rc, st = gpu.pf_step(5)
@@ -288,8 +375,8 @@ def test_pf_steps_bit_exact_fp64(ev, mat, kmax):
         assert rel(gpu.get("rho"), ref.field("rho")) == 0.0
 
 
-def test_pf_mixed_close_to_fp64(ev, mat):
-    n, G = 16, 8
+@pytest.mark.parametrize("n,G", [(16, 8), (64, 64)])
+def test_pf_mixed_close_to_fp64(ev, mat, n, G):
     a, _ = pf_setup(ev, mat, n, G, 4)
     seeds = synth.voronoi_seeds(n, G, 4)
     b = ev.Solver(n, G, O.voronoi(n, seeds), synth.orientations(G, 4), mat, 4, precision="mixed")
