@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--mr-fp64-steps", type=int, default=2, help="FP64 Ma-Roters comparison increments (0 = skip)")
     ap.add_argument("--fft-reps", type=int, default=20,
                     help="repetitions of the FFT comparison against cuFFT (torch.fft; 0 = skip)")
+    ap.add_argument("--trajectory", type=int, default=500,
+                    help="increments of the full-run mixed vs FP64 comparison and DRX window (0 = skip)")
+    ap.add_argument("--trajectory-fp64-scheme", default="al", choices=["basic", "al"],
+                    help="fixed-point scheme of the FP64 reference run (both reach the same solution)")
+    ap.add_argument("--drx-window", type=int, default=10, help="timed increments of the DRX-regime window")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
@@ -293,8 +298,10 @@ def native(args, ws, rank, local):
         res["ma_roters"] = mr_companion(args, wl, g0, quat, torch, evp, pk)
     if args.fft_reps > 0:
         res["fft_vs_cufft"] = fft_comparator(wl, torch, evp, args.fft_reps, pk)
-    # FP64 companion run on the same seeded input
-    n64 = args.warmup + args.steps if args.fp64_steps < 0 else args.fp64_steps
+    if args.trajectory > 0:
+        res["trajectory"] = trajectory_companion(args, wl, g0, quat, mat, torch, evp)
+    # FP64 companion run on the same seeded input (the full-run comparison above supersedes it by default)
+    n64 = (0 if args.trajectory > 0 else args.warmup + args.steps) if args.fp64_steps < 0 else args.fp64_steps
     if n64 > 0:
         res["fp64"] = fp64_companion(args, wl, g0, quat, mat, n64, warm + timed, torch, evp)
     if not args.no_e2e:
@@ -646,6 +653,142 @@ def fp64_companion(args, wl, g0, quat, mat, nsteps, mixed_hist, torch, evp):
            "fixed_point_iterations": [r["it"] for r in h], "tol": args.tol64,
            "mixed_vs_fp64_macro_stress_rel_err_max": max(errs),
            "X_rex_abs_diff_max": max(abs(a["X_rex"] - b["X_rex"]) for a, b in zip(m, h))}
+    return out
+
+
+def one_increment(solver, step, dE33, dt, pf_steps, torch):
+    """One DRX increment (solve, nucleation, PF steps) bracketed by CUDA events on the solver's stream."""
+    st = solver.stream
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(st)
+    rc, es = solver.increment(dE33, dt)
+    e1.record(st)
+    _, nn = solver.nucleate(step)
+    _, ps = solver.pf_step(pf_steps)
+    e2.record(st)
+    e2.synchronize()
+    return dict(evp_ms=e0.elapsed_time(e1), step_ms=e0.elapsed_time(e2), it=es.iterations, sig33=es.sig_mean[2],
+                nuclei=nn, X_rex=ps.X_rex, F=ps.F_tot, n_grains=ps.n_grains, overflow=ps.overflow, rc=rc)
+
+
+def field_errors(mixed, fp64):
+    """The mixed path's voxel stress field against the FP64 path's: max and RMS difference, relative to the
+    largest mean-stress component and to the FP64 field's RMS, over all voxels and over the voxels whose grain id
+    agrees (DRX events can differ near a nucleation threshold: k differs between precisions in its last bits)."""
+    sm = mixed.get("sig").astype(np.float64)
+    sd = fp64.get("sig")
+    d = sm - sd
+    den = float(np.abs(sd.mean(axis=1)).max())
+    same = mixed.get("g")[0] == fp64.get("g")[0]
+    dsame = d[:, same]
+    return {"max_rel_to_mean": float(np.abs(d).max() / den), "rms_rel_to_mean": float(np.sqrt((d ** 2).mean()) / den),
+            "rms_rel": float(np.sqrt((d ** 2).sum() / (sd ** 2).sum())),
+            "rms_rel_same_grain": float(np.sqrt((dsame ** 2).sum() / (sd[:, same] ** 2).sum())),
+            "max_rel_to_mean_same_grain": float(np.abs(dsame).max() / den),
+            "same_grain_fraction": float(same.mean())}
+
+
+def trajectory_companion(args, wl, g0, quat, mat, torch, evp):
+    """The whole workload (wl.increments increments, to strain |dE33| x increments), FP32-mixed and FP64 on the same
+    seeded input in lockstep: the mixed path's error against FP64 on the macroscopic stress-strain curve, the voxel
+    stress field (every `every` increments) and the recrystallised fraction; the mixed path's throughput over the
+    whole run and over a window taken in the DRX regime; the DRX analytics (critical strain, Avrami fit, grains as
+    connected components) of both runs."""
+    from paper_1509_04953_gb300 import analytics as A
+    T = args.trajectory
+    N3 = wl.n ** 3
+    # every boundary voxel can nucleate again in every increment once k exceeds the redrawn strengths (reading
+    # C17): the grain-id space is sized for the whole run
+    ids = min(wl.grains + 64 * N3, 2 ** 31 - 1)
+    kw = dict(precision=args.precision, tol=args.tol, max_iter=5000, newton_adapt=args.newton_adapt,
+              newton_tol=args.newton_tol, ref_scale=args.ref_scale, max_ids=ids)
+    mx = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, **kw)
+    f64 = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="fp64", tol=args.tol64, max_iter=20000,
+                     scheme=args.trajectory_fp64_scheme, max_ids=ids)
+    # the mixed path restarted from the FP64 state at each checkpoint: the error of one increment from a common
+    # state, free of the divergence of the two runs' discrete DRX histories
+    scratch = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, **kw)
+    state_fields = ("sig", "epse", "epsp", "deps", "rho")
+    hm, hd, fields, common = [], [], [], []
+    every = max(T // 10, 1)
+    synced = False
+    for t in range(T):
+        hm.append(one_increment(mx, t, wl.dE33, wl.dt, wl.pf_steps, torch))
+        if synced:
+            _, sc = scratch.increment(wl.dE33, wl.dt)
+        hd.append(one_increment(f64, t, wl.dE33, wl.dt, wl.pf_steps, torch))
+        if synced:
+            sd = f64.get("sig")
+            d = scratch.get("sig").astype(np.float64) - sd
+            common.append({"increment": t + 1, "macro_rel": abs(sc.sig_mean[2] - hd[-1]["sig33"]) / abs(hd[-1]["sig33"]),
+                           "voxel_sigma_rms_rel": float(np.sqrt((d ** 2).sum() / (sd ** 2).sum())),
+                           "voxel_sigma_max_rel_to_mean": float(np.abs(d).max() / np.abs(sd.mean(axis=1)).max())})
+            synced = False
+        if (t + 1) % every == 0 or t + 1 == T:
+            fe = field_errors(mx, f64)
+            fe["increment"] = t + 1
+            fe["strain"] = (t + 1) * abs(wl.dE33)
+            fields.append(fe)
+            if t + 1 < T:
+                for f in state_fields:
+                    scratch.set(f, f64.get(f))
+                sc64 = f64.scalars()
+                scratch.set_scalars(sc64["E"], sc64["dE_prev"], sc64["have_prev"], sc64["next_id"])
+                synced = True
+    strain = [(t + 1) * abs(wl.dE33) for t in range(T)]
+    curve_err = [abs(a["sig33"] - b["sig33"]) / abs(b["sig33"]) for a, b in zip(hm, hd)]
+    xr_err = [abs(a["X_rex"] - b["X_rex"]) for a, b in zip(hm, hd)]
+    # DRX window: the mixed path's increments from the first one at or past X_rex = 0.1, or the last quarter
+    w0 = next((i for i, r in enumerate(hm) if r["X_rex"] >= 0.1), 3 * T // 4)
+    w0 = min(w0, max(T - args.drx_window, 0))
+    win = hm[w0:w0 + args.drx_window]
+    wstep = sum(r["step_ms"] for r in win) / 1e3
+    wevp = sum(r["evp_ms"] for r in win) / 1e3
+
+    def analytics(h, solver):
+        out = {"critical_strain": A.critical_strain(strain, [r["nuclei"] for r in h])}
+        tt = np.array(strain) / abs(wl.dE33) * wl.dt
+        X = np.array([r["X_rex"] for r in h])
+        try:
+            m, K = A.avrami_fit(tt, X)
+            out["avrami"] = {"m": m, "K": K}
+        except ValueError as e:
+            out["avrami"] = str(e)
+        ng, d = A.grain_statistics(solver.get("g")[0], wl.n, dx=mat.dx)
+        out["grains_connected"] = ng
+        out["mean_diameter_um"] = d * 1e6
+        out["n_grains_ids"] = h[-1]["n_grains"]
+        return out
+
+    out = {"increments": T, "strain_final": strain[-1], "fp64_scheme": args.trajectory_fp64_scheme,
+           "fp64_tol": args.tol64, "mixed_tol": args.tol,
+           "mixed_vs_fp64": {"curve_rel_err_max": max(curve_err), "curve_rel_err_final": curve_err[-1],
+                             "voxel_sigma": fields, "voxel_sigma_rms_rel_max": max(f["rms_rel"] for f in fields),
+                             "voxel_sigma_rms_rel_same_grain_max": max(f["rms_rel_same_grain"] for f in fields),
+                             "X_rex_abs_diff_max": max(xr_err), "X_rex_final": [hm[-1]["X_rex"], hd[-1]["X_rex"]],
+                             "one_increment_from_common_state": common,
+                             "one_increment_voxel_sigma_rms_rel_max": max((c["voxel_sigma_rms_rel"] for c in common),
+                                                                          default=None),
+                             "one_increment_macro_rel_max": max((c["macro_rel"] for c in common), default=None)},
+           "mixed_full_run": {"voxel_iters_per_s": N3 * sum(r["it"] for r in hm) / (sum(r["evp_ms"] for r in hm) / 1e3),
+                              "drx_increments_per_s": T / (sum(r["step_ms"] for r in hm) / 1e3),
+                              "fixed_point_iterations_total": sum(r["it"] for r in hm),
+                              "nuclei_total": sum(r["nuclei"] for r in hm)},
+           "drx_window": {"first_increment": w0 + 1, "increments": len(win), "strain": strain[w0],
+                          "X_rex": [win[0]["X_rex"], win[-1]["X_rex"]], "nuclei": sum(r["nuclei"] for r in win),
+                          "n_grains": win[-1]["n_grains"], "drx_increments_per_s": len(win) / wstep,
+                          "voxel_iters_per_s": N3 * sum(r["it"] for r in win) / wevp,
+                          "ms_per_step": 1e3 * wstep / len(win),
+                          "pf_ms_per_increment": 1e3 * (wstep - wevp) / len(win)},
+           "fp64_full_run": {"voxel_iters_per_s": N3 * sum(r["it"] for r in hd) / (sum(r["evp_ms"] for r in hd) / 1e3),
+                             "drx_increments_per_s": T / (sum(r["step_ms"] for r in hd) / 1e3)},
+           "analytics": {"mixed": analytics(hm, mx), "fp64": analytics(hd, f64)},
+           "curve": {"every": every, "strain": strain[every - 1::every],
+                     "sig33_mixed": [round(r["sig33"], 4) for r in hm[every - 1::every]],
+                     "X_rex_mixed": [r["X_rex"] for r in hm[every - 1::every]],
+                     "X_rex_fp64": [r["X_rex"] for r in hd[every - 1::every]],
+                     "iterations_mixed": [r["it"] for r in hm[every - 1::every]]}}
+    del mx, f64, scratch
     return out
 
 
