@@ -36,8 +36,10 @@ NEWTON_FLOPS_EVAL = 1140      # one residual + tangent + potential evaluation (1
 NEWTON_FLOPS_RESID = 544      # one residual + potential evaluation without the tangent
 NEWTON_FLOPS_FACTOR = 80      # one 6x6 LDL^T factorisation
 NEWTON_FLOPS_SOLVE = 72       # the two triangular solves of one Newton step
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 1.25                             # nominal (1.203 measured with an FMA-chain probe)
+# Nominal FMA-pipe peaks (SMs x lanes x 2 x maximum SM clock for FP32; the data-sheet FP64 rate), used only if the
+# library's FMA-chain measurement (evp_fma_throughput) fails; bench.py measures both in the same run.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -283,8 +285,10 @@ def native(args, ws, rank, local):
     res["newton"] = {"mode": "reuse" if mixed.cfg.newton_mode == 1 else "exact", "solves": solves, "evals": evals, "factorisations": n1[2] - n0[2],
                      "solves_per_voxel_iter": solves / (N3 * iters), "evals_per_voxel_iter": evals / (N3 * iters),
                      "factorisations_per_voxel_iter": (n1[2] - n0[2]) / (N3 * iters)}
+    pipes = pipe_peaks(evp)
+    res["pipe_peaks_tflops"] = pipes
     res["roofline"] = roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision=args.precision,
-                               facs=n1[2] - n0[2], reuse=mixed.cfg.newton_mode == 1)
+                               facs=n1[2] - n0[2], reuse=mixed.cfg.newton_mode == 1, pipes=pipes)
     res["memory_bound_kernels"] = memory_kernels(ksplit, wl, N3, args.precision, pk)
     if args.fast_steps > 0:
         res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
@@ -346,7 +350,21 @@ def hbm_bytes_per_voxel(kernel, n, T):
             "pf_step": 2 * 8 * (4 + T) + 8}.get(kernel)
 
 
-def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, facs=0, reuse=False):
+def pipe_peaks(evp):
+    """FP32 and FP64 FMA-pipe throughput of this GPU, measured by the library's own FMA-chain kernel (best of
+    three runs each), with the nominal figures as the fallback."""
+    out = {}
+    for name, nominal in (("fp32", FP32_PEAK_TFLOPS), ("fp64", FP64_PEAK_TFLOPS)):
+        try:
+            out[name] = max(evp.fma_throughput(name) for _ in range(3))
+            out[name + "_source"] = "measured (evp_fma_throughput)"
+        except Exception as e:   # noqa: BLE001 -- report the nominal figure and why
+            out[name] = nominal
+            out[name + "_source"] = f"nominal ({e})"
+    return out
+
+
+def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, facs=0, reuse=False, pipes=None):
     ms, n = ktimes[dom]
     avg_s = ms / 1e3 / max(n, 1)
     T = 4 if precision != "fp64" else 8
@@ -368,8 +386,10 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
             f64 += ev
         else:
             f32 += ev
-        t64, t32 = f64 / FP64_PEAK_TFLOPS, f32 / FP32_PEAK_TFLOPS
-        flops, peak, pipe = (f64, FP64_PEAK_TFLOPS, "fp64") if t64 >= t32 else (f32, FP32_PEAK_TFLOPS, "fp32")
+        p32 = (pipes or {}).get("fp32", FP32_PEAK_TFLOPS)
+        p64 = (pipes or {}).get("fp64", FP64_PEAK_TFLOPS)
+        t64, t32 = f64 / p64, f32 / p32
+        flops, peak, pipe = (f64, p64, "fp64") if t64 >= t32 else (f32, p32, "fp32")
         alu = flops / (ms / 1e3) / 1e12
         # algorithmic HBM bytes per launch, the method's operands of the local update (Eqs. HookeLaw and
         # PlasticRate): total strain 6, plastic strain 6, the 12 critical resolved shear stresses, the grain id and
@@ -400,7 +420,7 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
                 "note": "the local solve is reported against the resource it uses the larger fraction of. "
                         "Algorithmic flops: 1140 per residual+tangent evaluation, 544 per residual-only "
                         "evaluation, 80 per 6x6 LDL^T factorisation, 72 per pair of triangular solves, counted "
-                        "by pipe, peak from unit counts and the maximum SM clock; algorithmic bytes: the "
+                        "by pipe, pipe peaks measured in the same run (evp_fma_throughput); algorithmic bytes: the "
                         "method's per-voxel operands (strain, plastic strain, 12 critical stresses, grain id, "
                         "stress warm start -> stress: 148 B FP32), read and written once per launch"}
     if hbm_bytes_per_voxel(dom, wl.n, T) is None:
@@ -728,6 +748,7 @@ def trajectory_companion(args, wl, g0, quat, mat, torch, evp):
             fe = field_errors(mx, f64)
             fe["increment"] = t + 1
             fe["strain"] = (t + 1) * abs(wl.dE33)
+            fe["curve_rel"] = abs(hm[-1]["sig33"] - hd[-1]["sig33"]) / abs(hd[-1]["sig33"])
             fields.append(fe)
             if t + 1 < T:
                 for f in state_fields:

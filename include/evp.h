@@ -267,6 +267,16 @@ int evp_newton_counts(const evp_handle *h, int64_t *solves, int64_t *evals);
 /* Running total of tangent factorisations (EVP_NEWTON_REUSE; equals solves with EVP_NEWTON_EXACT). */
 int evp_newton_refreshes(const evp_handle *h, int64_t *refreshes);
 
+/* Measured throughput of this GPU's fused multiply-add pipe (the paper has no counterpart: a measurement
+ * service of this library, the denominator of the local solve's pipe utilisation). precision: EVP_FP64 measures
+ * FP64, the other codes FP32. Runs the library's own kernel -- 8 independent FMA chains per thread, `iters`
+ * steps each, 8 CTAs of 256 threads per SM -- on cuda_stream, times it with CUDA events, synchronises, and
+ * writes *tflops = 2 x FMAs / time in TFLOP/s. sink_dev: caller-owned device buffer of at least 8 bytes that the
+ * kernel may write (it keeps the chains from being optimised away; its content is meaningless). Choose iters so
+ * that the kernel runs for tens of milliseconds (about 3e5 for FP32, 5e3 for FP64 on a GB300). Errors:
+ * EVP_ERR_ARG for a NULL pointer, iters < 1 or an unknown precision; EVP_ERR_CUDA if a CUDA call fails. */
+int evp_fma_throughput(int precision, int iters, void *sink_dev, double *tflops, void *cuda_stream);
+
 /* Frees the handle and its CUDA events. The workspace stays the caller's (the library never owns device memory);
  * work still queued on the stream must finish before the caller frees the workspace. NULL is a no-op. */
 void evp_destroy(evp_handle *h);

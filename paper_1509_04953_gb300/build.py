@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libevp_gb300.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["fft.cu", "newton.cu", "mr.cu", "drx.cu", "pf.cu", "adjoint.cu", "evp_api.cu", "noalloc.cu"]
+SOURCES = ["fft.cu", "newton.cu", "mr.cu", "drx.cu", "pf.cu", "adjoint.cu", "evp_api.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 EXTRA = {"pf.cu": ["-fmad=false"]}

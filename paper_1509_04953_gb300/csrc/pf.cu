@@ -174,37 +174,41 @@ __global__ void __launch_bounds__(kPF) k_pf(int n, const int32_t *__restrict__ i
 
 // ---- tiled PF step (grids of 32 points per edge and more) ----
 // The same update as k_pf, voxel by voxel and in the same arithmetic order (so FP64 results are bitwise the
-// same), organised for bandwidth. A CTA owns a 32 x 8 column tile and marches through kZC planes of z. The
-// active sets of the planes z-1, z, z+1 (interior) and the x/y halo of plane z are staged in shared memory by
-// cp.async, one plane ahead of the compute, so the seven-list merge reads shared memory instead of issuing
-// chains of dependent global loads. Which slots to stage comes from a per-row bound: rmax[s] >= the number of
+// same), organised for the SM. A CTA owns a 32 x 8 column tile and marches through kZC planes of z. The active
+// sets of the planes z-1, z, z+1 (interior) and the x/y halo of plane z are staged in shared memory by cp.async,
+// as (id, eta) pairs with a -1 id after each list's last staged slot, so the seven-list merge reads one pair per
+// step and needs no slot-count checks. Which slots to stage comes from a per-row bound: rmax[s] >= the number of
 // entries of every point of the 32-point row segment s = (z n + y) (n / 32) + x / 32, so every staged load is
 // independent of the others. Each step writes the exact bound of the rows it produced and clears, in the
 // destination, the slots between a point's new count and the destination's previous bound, which keeps every
 // list -1 / 0 terminated over all K slots (the layout every other reader of the active sets assumes).
+// Three plane buffers and one halo buffer keep the FP32 tile at 61 KB, so three CTAs share an SM and cover each
+// other's staging waits.
 constexpr int kTX = 32, kTY = 8, kZC = 16;
 constexpr int kPlane = kTX * kTY;             // interior points of one plane tile
 constexpr int kHalo = 2 * kTX + 2 * kTY;      // rows y0-1, y0+8 and columns x0-1, x0+32 of the centre plane
 constexpr int kTileThreads = kTX * kTY;
+constexpr int kSlots = KM + 1;                // KM slots and the terminating -1
+
+template <typename T> struct alignas(2 * sizeof(T) > 8 ? 16 : 8) PFPair {
+    int32_t id;
+    T e;
+};
 
 template <typename T>
 struct PFTile {
-    // element index space shared by id[] and e[]: 4 interior plane buffers [buf][slot][point], then two halo
-    // buffers [hbuf][slot][halo point]
-    int32_t id[4 * KM * kPlane + 2 * KM * kHalo];
-    T e[4 * KM * kPlane + 2 * KM * kHalo];
+    // element index space: 3 interior plane buffers [buf][slot][point], then the halo [slot][halo point]
+    PFPair<T> pr[3 * kSlots * kPlane + kSlots * kHalo];
     uint8_t rin[(kZC + 2) * (kTY + 2)];   // bounds of the current buffer: planes z0-1..z0+kZC, rows y0-1..y0+8
     uint8_t rxl[kZC * kTY], rxr[kZC * kTY];   // bounds of the left / right neighbour segments, planes z0.., rows y0..
     uint8_t rdst[kZC * kTY];              // previous bounds of the destination rows
 };
 
-__device__ __forceinline__ int tile_int_index(int buf, int j, int p) { return (buf * KM + j) * kPlane + p; }
-__device__ __forceinline__ int tile_halo_index(int hb, int j, int hp) {
-    return 4 * KM * kPlane + (hb * KM + j) * kHalo + hp;
-}
+__device__ __forceinline__ int tile_int_index(int buf, int j, int p) { return (buf * kSlots + j) * kPlane + p; }
+__device__ __forceinline__ int tile_halo_index(int j, int hp) { return 3 * kSlots * kPlane + j * kHalo + hp; }
 
-// Issue the asynchronous copies of one point's slots [0, R) into the tile (element index base, stride), and
-// terminate its list at slot R in shared memory when R < K (the slot that global memory also holds -1 at).
+// Issue the asynchronous copies of one point's slots [0, R) into the tile (element index base, slot stride) and
+// write the terminating -1 at slot R (R <= K <= KM: global memory also holds -1 there when R < K).
 template <typename T>
 __device__ __forceinline__ void stage_point(PFTile<T> &tb, int base, int stride, int R, int K,
                                             const int32_t *__restrict__ ids, const T *__restrict__ eta, long N3,
@@ -213,14 +217,14 @@ __device__ __forceinline__ void stage_point(PFTile<T> &tb, int base, int stride,
 #pragma unroll
     for (int j = 0; j < KM; ++j)
         if (j < R) {
-            cp_async<4>(&tb.id[base + j * stride], ids + j * N3 + v);
-            cp_async<sizeof(T)>(&tb.e[base + j * stride], eta + j * N3 + v);
+            cp_async<4>(&tb.pr[base + j * stride].id, ids + j * N3 + v);
+            cp_async<sizeof(T)>(&tb.pr[base + j * stride].e, eta + j * N3 + v);
         }
-    if (R < K) tb.id[base + R * stride] = -1;
+    tb.pr[base + R * stride].id = -1;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads, 2)
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 1)
 k_pf_tile(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta, int32_t *__restrict__ ids2,
           T *__restrict__ eta2, int32_t *__restrict__ gout, const double *__restrict__ kf, PFConst pc,
           int32_t *__restrict__ overflow, const uint8_t *__restrict__ rcur, uint8_t *__restrict__ rdst) {
@@ -245,13 +249,13 @@ k_pf_tile(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta, int
     }
     __syncthreads();
     const int p = ty * kTX + tx;
-    // plane index pp = 0 .. kZC+1 holds z = z0 - 1 + pp in interior buffer pp % 4
+    // plane index pp = 0 .. kZC+1 holds z = z0 - 1 + pp in interior buffer pp % 3
     auto stage_plane = [&](int pp) {
         const int z = (z0 - 1 + pp) & msk;
         const long v = ((long)z * n + (y0 + ty)) * n + x0 + tx;
-        stage_point(tb, tile_int_index(pp & 3, 0, p), kPlane, tb.rin[pp * (kTY + 2) + ty + 1], K, ids, eta, N3, v);
+        stage_point(tb, tile_int_index(pp % 3, 0, p), kPlane, tb.rin[pp * (kTY + 2) + ty + 1], K, ids, eta, N3, v);
     };
-    // halo of centre plane i (z = z0 + i) into halo buffer i % 2
+    // halo of centre plane i (z = z0 + i)
     auto stage_halo = [&](int i) {
         const int t = threadIdx.x;
         if (t >= kHalo) return;
@@ -262,7 +266,7 @@ k_pf_tile(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta, int
         else if (t < 2 * kTX + kTY) { x = (x0 - 1) & msk; y = y0 + t - 2 * kTX; R = tb.rxl[i * kTY + t - 2 * kTX]; }
         else { x = (x0 + kTX) & msk; y = y0 + t - 2 * kTX - kTY; R = tb.rxr[i * kTY + t - 2 * kTX - kTY]; }
         const long v = ((long)z * n + y) * n + x;
-        stage_point(tb, tile_halo_index(i & 1, 0, t), kHalo, R, K, ids, eta, N3, v);
+        stage_point(tb, tile_halo_index(0, t), kHalo, R, K, ids, eta, N3, v);
     };
     stage_plane(0);
     stage_plane(1);
@@ -279,42 +283,38 @@ k_pf_tile(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta, int
     for (int i = 0; i < kZC; ++i) {
         const int z = z0 + i;
         const long v = ((long)z * n + (y0 + ty)) * n + x0 + tx;
-        if (i + 1 < kZC) {   // the next plane's data, under this plane's compute
-            stage_plane(i + 3);
-            stage_halo(i + 1);
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-        }
         const double kv = kf[v];
-        // the seven lists: self, x-, x+, y-, y+, z-, z+ (element index of slot 0, slot stride)
-        const int c = (i + 1) & 3, hb = i & 1;
-        int base[7], str[7];
-        base[0] = tile_int_index(c, 0, p); str[0] = kPlane;
-        if (tx > 0) { base[1] = base[0] - 1; str[1] = kPlane; } else { base[1] = tile_halo_index(hb, 0, 2 * kTX + ty); str[1] = kHalo; }
-        if (tx < kTX - 1) { base[2] = base[0] + 1; str[2] = kPlane; }
-        else { base[2] = tile_halo_index(hb, 0, 2 * kTX + kTY + ty); str[2] = kHalo; }
-        if (ty > 0) { base[3] = base[0] - kTX; str[3] = kPlane; } else { base[3] = tile_halo_index(hb, 0, tx); str[3] = kHalo; }
-        if (ty < kTY - 1) { base[4] = base[0] + kTX; str[4] = kPlane; } else { base[4] = tile_halo_index(hb, 0, kTX + tx); str[4] = kHalo; }
-        base[5] = tile_int_index(i & 3, 0, p); str[5] = kPlane;
-        base[6] = tile_int_index((i + 2) & 3, 0, p); str[6] = kPlane;
+        // the seven lists: self, x-, x+, y-, y+, z-, z+ -- element index of the current slot, slot stride
+        // (kPlane, or kHalo where the bit of `halo` is set)
+        const int c = (i + 1) % 3;
+        int at[7];
+        at[0] = tile_int_index(c, 0, p);
+        unsigned halo = 0;
+        if (tx > 0) at[1] = at[0] - 1; else { at[1] = tile_halo_index(0, 2 * kTX + ty); halo |= 2u; }
+        if (tx < kTX - 1) at[2] = at[0] + 1; else { at[2] = tile_halo_index(0, 2 * kTX + kTY + ty); halo |= 4u; }
+        if (ty > 0) at[3] = at[0] - kTX; else { at[3] = tile_halo_index(0, tx); halo |= 8u; }
+        if (ty < kTY - 1) at[4] = at[0] + kTX; else { at[4] = tile_halo_index(0, kTX + tx); halo |= 16u; }
+        at[5] = tile_int_index(i % 3, 0, p);
+        at[6] = tile_int_index((i + 2) % 3, 0, p);
 
-        // local sums over the voxel's own list, ascending id
+        // local sums over the voxel's own list, ascending id (the list ends at a -1)
         T S2 = (T)0, D = (T)0, R = (T)0;
-        for (int j = 0; j < K; ++j) {
-            const int id = tb.id[base[0] + j * kPlane];
-            if (id < 0) break;
-            const T e = tb.e[base[0] + j * kPlane];
-            S2 += e * e;
-            if (id < G) D += e * e;
-            else R += e * e;
+        for (int j = 0; j < kSlots; ++j) {
+            const PFPair<T> pj = tb.pr[at[0] + j * kPlane];
+            if (pj.id < 0) break;
+            S2 += pj.e * pj.e;
+            if (pj.id < G) D += pj.e * pj.e;
+            else R += pj.e * pj.e;
         }
         const T Ep = (T)(pc.Escale * kv);
         const T Ssum = D + R;
-        int head[7], pos[7];
+        int head[7];
+        T cur[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            pos[q] = 0;
-            const int id = tb.id[base[q]];
-            head[q] = id < 0 ? kEmpty : id;
+            const PFPair<T> pq = tb.pr[at[q]];
+            head[q] = pq.id < 0 ? kEmpty : pq.id;
+            cur[q] = pq.e;
         }
         int kid[KM + 1];
         T ke[KM + 1];
@@ -335,16 +335,13 @@ k_pf_tile(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta, int
             T e[7];
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
-                e[q] = (T)0;
-                if (head[q] == cid) {
-                    e[q] = tb.e[base[q] + pos[q] * str[q]];
-                    ++pos[q];
-                    int nx = kEmpty;
-                    if (pos[q] < K) {
-                        const int id = tb.id[base[q] + pos[q] * str[q]];
-                        nx = id < 0 ? kEmpty : id;
-                    }
-                    head[q] = nx;
+                const bool hit = head[q] == cid;
+                e[q] = hit ? cur[q] : (T)0;
+                if (hit) {   // advance list q to its next pair (a -1 id ends it)
+                    at[q] += (halo >> q) & 1u ? kHalo : kPlane;
+                    const PFPair<T> pq = tb.pr[at[q]];
+                    head[q] = pq.id < 0 ? kEmpty : pq.id;
+                    cur[q] = pq.e;
                 }
             }
             const T e0 = e[0];
@@ -400,8 +397,14 @@ k_pf_tile(int n, const int32_t *__restrict__ ids, const T *__restrict__ eta, int
         if (tx == 0) rdst[seg(z, y0 + ty, xs)] = (uint8_t)rowmax;
         const unsigned ob = __ballot_sync(0xffffffffu, ovf);
         if (tx == 0 && ob) atomicAdd(overflow, __popc(ob));
-        if (i + 1 < kZC) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        __syncthreads();
+        __syncthreads();   // every thread is done with plane z - 1 and with this halo
+        if (i + 1 < kZC) {
+            stage_plane(i + 3);   // into the buffer plane z - 1 held
+            stage_halo(i + 1);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            __syncthreads();
+        }
     }
 }
 

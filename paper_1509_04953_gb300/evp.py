@@ -106,13 +106,15 @@ def load():
     L.evp_residual_scratch_bytes.argtypes = [i, i, C.POINTER(sz)]
     L.evp_stress_residual.argtypes = [i, i, vp, vp, vp, vp, vp]
     L.evp_stress_residual_noalloc.argtypes = [i, i, vp, vp, vp, vp]
+    L.evp_fma_throughput.argtypes = [i, i, vp, C.POINTER(d), vp]
     for f in ("evp_workspace_bytes", "evp_init", "evp_increment", "drx_nucleate", "pf_step", "get_fields",
               "set_fields", "evp_fields_bytes", "evp_get_scalars", "evp_set_scalars", "evp_set_solver",
               "evp_voronoi", "evp_rfft3d", "evp_irfft3d", "evp_set_profiling", "evp_set_profiling_mask",
               "evp_kernel_times",
               "evp_launch_count", "evp_newton_counts", "evp_residual_scratch_bytes", "evp_stress_residual",
               "evp_adjoint_workspace_bytes", "evp_adjoint_begin", "evp_adjoint_step", "evp_adjoint_end",
-              "evp_newton_refreshes", "evp_get_leff", "evp_set_leff", "evp_stress_residual_noalloc"):
+              "evp_newton_refreshes", "evp_get_leff", "evp_set_leff", "evp_stress_residual_noalloc",
+              "evp_fma_throughput"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -407,6 +409,22 @@ def irfft3d(spec):
     if rc != 0:
         raise EVPError(f"evp_irfft3d: {EVP_ERR.get(rc, rc)}")
     return out
+
+
+def fma_throughput(precision, iters=None):
+    """Measured FMA-pipe throughput of the current GPU in TFLOP/s ("fp32" or "fp64"), from the library's own
+    FMA-chain kernel on the current stream."""
+    torch = _torch()
+    code = PRECISION["fp64"] if precision == "fp64" else PRECISION["mixed"]
+    if iters is None:
+        iters = 5000 if precision == "fp64" else 300000
+    sink = torch.empty(2, dtype=torch.float64, device="cuda")
+    tf = C.c_double(0.0)
+    rc = load().evp_fma_throughput(code, int(iters), sink.data_ptr(), C.byref(tf),
+                                   torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise EVPError(f"evp_fma_throughput: {EVP_ERR.get(rc, rc)}")
+    return tf.value
 
 
 def stress_residual(sig):

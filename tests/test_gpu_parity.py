@@ -593,3 +593,14 @@ def test_faults_injected_on_the_host_return_a_status_and_leave_the_handle_usable
         s.increment(-1e-3, float("nan"))
     rc, st = s.increment(-1e-3, 1.0)
     assert rc == 0 and np.isfinite(st.sig_mean[2]) and st.sig_mean[2] < 0
+
+
+def test_fma_throughput_measures_both_pipes(ev):
+    """The pipe peaks bench.py divides by: the library's FMA-chain kernel gives the FP32 rate within a factor of
+    two of the unit-count figure (152 SMs x 128 lanes x 2 flops x clock) and an FP64 rate far below it, as
+    GB300's FP64 units are few."""
+    f32 = ev.fma_throughput("fp32")
+    f64 = ev.fma_throughput("fp64")
+    nominal32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    assert 0.5 * nominal32 < f32 < 1.05 * nominal32
+    assert 0.05 < f64 < f32 / 10
