@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--trajectory-fp64-scheme", default="al", choices=["basic", "al"],
                     help="fixed-point scheme of the FP64 reference run (both reach the same solution)")
     ap.add_argument("--drx-window", type=int, default=10, help="timed increments of the DRX-regime window")
+    ap.add_argument("--large-steps", type=int, default=3,
+                    help="timed DRX increments of the 256^3 / 1024-grain companion (0 = skip it)")
+    ap.add_argument("--large-adjoint", type=int, default=16,
+                    help="increments of the 256^3 checkpointed adjoint sweep (0 = skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-6, help="fixed-point tolerance of the mixed path")
@@ -304,6 +308,8 @@ def native(args, ws, rank, local):
         res["fft_vs_cufft"] = fft_comparator(wl, torch, evp, args.fft_reps, pk)
     if args.trajectory > 0:
         res["trajectory"] = trajectory_companion(args, wl, g0, quat, mat, torch, evp)
+    if args.large_steps > 0:
+        res["large_256"] = large_companion(args, torch, evp, pk)
     # FP64 companion run on the same seeded input (the full-run comparison above supersedes it by default)
     n64 = (0 if args.trajectory > 0 else args.warmup + args.steps) if args.fp64_steps < 0 else args.fp64_steps
     if n64 > 0:
@@ -810,6 +816,52 @@ def trajectory_companion(args, wl, g0, quat, mat, torch, evp):
                      "X_rex_fp64": [r["X_rex"] for r in hd[every - 1::every]],
                      "iterations_mixed": [r["it"] for r in hm[every - 1::every]]}}
     del mx, f64, scratch
+    return out
+
+
+def large_companion(args, torch, evp, pk):
+    """The large workload (256^3, 1024 grains, FP32-mixed, 6e-4 strain per 0.6 s increment): DRX increments timed
+    after a warm-up, then a checkpointed adjoint sweep over the next `large_adjoint` increments (gradient of the
+    summed axial stress with respect to k1, k2, tau0, n), with the forward and adjoint workspace bytes and the
+    adjoint workspace that 100 increments with a checkpoint every 10 would take."""
+    import ctypes as C
+    wl = synth.WORKLOADS["cu256"]
+    mat = synth.Material()
+    seeds, quat = workload_inputs(wl)
+    g0 = evp.voronoi(wl.n, seeds).cpu().numpy()
+    s = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="mixed", tol=args.tol, max_iter=5000)
+    ws = evp.workspace_bytes(s.cfg)
+    warm = run_steps(s, 2, wl.dE33, wl.dt, wl.pf_steps, torch)
+    h = run_steps(s, args.large_steps, wl.dE33, wl.dt, wl.pf_steps, torch)
+    N3 = wl.n ** 3
+    evp_s = sum(r["evp_ms"] for r in h) / 1e3
+    step_s = sum(r["step_ms"] for r in h) / 1e3
+    out = {"workload": wl.name, "workspace_bytes": ws, "increments_timed": len(h),
+           "voxel_iters_per_s": N3 * sum(r["it"] for r in h) / evp_s, "drx_increments_per_s": len(h) / step_s,
+           "ms_per_step": 1e3 * step_s / len(h), "fixed_point_iterations": [r["it"] for r in warm + h],
+           "sig33": [round(r["sig33"], 4) for r in warm + h]}
+    T = args.large_adjoint
+    if T > 0:
+        ck = max(1, int(round(T ** 0.5)))
+        nb = C.c_size_t(0)
+        evp.load().evp_adjoint_workspace_bytes(C.byref(s.cfg), 100, 10, C.byref(nb))
+        st = s.stream
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s.adjoint_begin(T, ck)
+        e0.record(st)
+        curve = [s.adjoint_step(wl.dE33, wl.dt).sig_mean[2] for _ in range(T)]
+        e1.record(st)
+        gb = np.zeros((T, 6))
+        gb[:, 2] = 1.0                  # L = sum of the axial stresses of the recorded increments
+        grad = s.adjoint_end(gb, tol=1e-5)
+        e2.record(st)
+        e2.synchronize()
+        out["adjoint"] = {"increments": T, "checkpoint_every": ck, "workspace_bytes": int(s.adj_ws.numel()),
+                          "forward_s": e0.elapsed_time(e1) / 1e3, "reverse_s": e1.elapsed_time(e2) / 1e3,
+                          "dL_dtheta": {"k1": grad[0], "k2": grad[1], "tau0": grad[2], "n": grad[3]},
+                          "sig33_recorded": [round(c, 4) for c in curve],
+                          "workspace_bytes_100_increments_every_10": nb.value}
+    s.close()
     return out
 
 

@@ -105,7 +105,8 @@ def test_state_is_restored_after_the_reverse_sweep(ev, mat, target):
 def test_mixed_adjoint_close_to_fp64(ev, mat, target):
     m1 = perturbed(mat)
     _, g64, _, _ = gpu_loss_grad(ev, m1, target)
-    _, g32, _, _ = gpu_loss_grad(ev, m1, target, precision="mixed", tol=1e-6, adj_tol=1e-5)
+    # the adjoint fixed point solved to 1e-6 (FP32 fields reach it); at 1e-5 the gradient is within 1.1e-4
+    _, g32, _, _ = gpu_loss_grad(ev, m1, target, precision="mixed", tol=1e-6, adj_tol=1e-6)
     assert np.abs(g32 / g64 - 1).max() < 3e-5, (g32, g64)      # measured 1.0e-5 (the n component)
 
 
@@ -117,7 +118,7 @@ def test_mixed_adjoint_against_central_differences(ev, mat, target):
     same value) and at h <= 1e-4 it is off by percents; h = 1e-2 balances noise against truncation and agrees to
     1e-3 (measured 4.4e-4, on k2, the smallest component)."""
     m1 = perturbed(mat)
-    _, g32, _, _ = gpu_loss_grad(ev, m1, target, precision="mixed", tol=1e-6, adj_tol=1e-5)
+    _, g32, _, _ = gpu_loss_grad(ev, m1, target, precision="mixed", tol=1e-6, adj_tol=1e-6)
     for i, k in enumerate(("k1", "k2", "tau0", "n")):
         v = getattr(m1, k)
         h = 1e-6 * v
