@@ -31,4 +31,32 @@ __device__ __forceinline__ double block_sum(double v, double *sh /* >= 32 double
     return v;
 }
 
+// Programmatic dependent launch (sm_90+). The kernels of one fixed-point iteration are queued back to back; each is
+// launched with programmatic stream serialization, so it can start while its predecessor's last CTAs still run.
+// pdl_wait() blocks until the preceding kernel has completed and its memory is visible (a no-op for a kernel
+// launched without the attribute), so it comes before any access to data an earlier kernel wrote; pdl_trigger()
+// then lets the next kernel launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    if (!pdl) {
+        kernel<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace evp

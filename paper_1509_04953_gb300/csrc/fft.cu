@@ -249,6 +249,8 @@ template <int N, typename T> __host__ __device__ constexpr int z_threads() { ret
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads, N >= 64 && N <= 128 ? (sizeof(T) == 4 ? 6 : 3) : 1) k_fft_x_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out,
                                                        long npairs, const int *__restrict__ skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int RP = rowpairs<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
@@ -290,6 +292,8 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
                                                        long npairs, T scale, int has_add, T a0, T a1, T a2, T a3, T a4,
                                                        T a5, const T *__restrict__ base, const int *__restrict__ skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int RP = rowpairs_c2r<N>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
@@ -353,6 +357,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N, bool INV>
 __global__ void __launch_bounds__(y_threads<N, T>()) k_fft_y(typename CT<T>::type *__restrict__ spec, const int *__restrict__ skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int TX = tx_y<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1;
@@ -471,6 +477,8 @@ template <typename T, int N>
 __global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 ? 3 : 1) k_fft_z(typename CT<T>::type *__restrict__ spec, int nf, int mode, T lam0,
                                                    T mu0, double *__restrict__ partials, double *__restrict__ mean6, const int *__restrict__ skip,
                                                    ZCtl zc) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
     constexpr int TX = tx_z<N, T>(), LS = Shape<N>::LS, Hx = N / 2 + 1, MI = maxit<N>(6 * (TX + 1), z_threads<N, T>());
@@ -489,11 +497,30 @@ __global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 
     const long plane = (long)N * Hx;            // one z plane of one field
     const long fstride = plane * N;
     load_tw(tw, N);
-    for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {   // TX, N powers of two: shifts
-        const int f = t / (TX * N), r = t % (TX * N);
-        int z, xl;
-        slab_item<N, TX>(r, z, xl);
-        cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx0 + xl);
+    // The slab walk: element r = t mod (TX N) of field f sits at column xl and plane z = slab_item(r). With
+    // NT threads and NT | TX N, a thread keeps its column, and its planes advance by DZ = NT / TX per step
+    // (slab_item adds DZ to z when r grows by NT, and pad16 adds DZ + DZ / 16 when DZ is a multiple of 16), so its
+    // shared and global addresses advance by constant strides.
+    constexpr int NT = z_threads<N, T>(), DZ = NT / TX, KZ = TX * N / NT;
+    constexpr bool walk = (TX * N) % NT == 0 && DZ % 16 == 0 &&
+                          ((TX == 8 && N % 16 == 0 && LS % 16 == 9) ? NT % 128 == 0 : NT % TX == 0);
+    int wz = 0, wxl = 0;
+    if constexpr (walk) slab_item<N, TX>((int)threadIdx.x, wz, wxl);
+    if constexpr (walk) {
+        C *sb = buf + wxl * LS + pad16(wz);
+        const C *gb = spec + (long)wz * plane + (long)ky * Hx + kx0 + wxl;
+        for (int f = 0; f < nf; ++f) {
+#pragma unroll
+            for (int k = 0; k < KZ; ++k)
+                cp_async<sizeof(C)>(sb + f * TX * LS + k * (DZ + DZ / 16), gb + f * fstride + (long)k * DZ * plane);
+        }
+    } else {
+        for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {   // TX, N powers of two: shifts
+            const int f = t / (TX * N), r = t % (TX * N);
+            int z, xl;
+            slab_item<N, TX>(r, z, xl);
+            cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx0 + xl);
+        }
     }
     if (nyq)
         for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
@@ -530,11 +557,20 @@ __global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 
         if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = tot;
     }
     if (mode == Z_INV || mode == Z_FWD_GAMMA_INV) block_fft<N, true, MI>(buf, nlines, tw);
-    for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
-        const int f = t / (TX * N), r = t % (TX * N);
-        int z, xl;
-        slab_item<N, TX>(r, z, xl);
-        spec[f * fstride + z * plane + (long)ky * Hx + kx0 + xl] = buf[(f * TX + xl) * LS + pad16(z)];
+    if constexpr (walk) {
+        const C *sb = buf + wxl * LS + pad16(wz);
+        C *gb = spec + (long)wz * plane + (long)ky * Hx + kx0 + wxl;
+        for (int f = 0; f < nf; ++f) {
+#pragma unroll
+            for (int k = 0; k < KZ; ++k) gb[f * fstride + (long)k * DZ * plane] = sb[f * TX * LS + k * (DZ + DZ / 16)];
+        }
+    } else {
+        for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
+            const int f = t / (TX * N), r = t % (TX * N);
+            int z, xl;
+            slab_item<N, TX>(r, z, xl);
+            spec[f * fstride + z * plane + (long)ky * Hx + kx0 + xl] = buf[(f * TX + xl) * LS + pad16(z)];
+        }
     }
     if (nyq)
         for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
@@ -572,8 +608,7 @@ template <typename T, int N> cudaError_t x_r2c_n(const T *in, void *spec, int nf
     const size_t sm = smem_x<T, N>();
     cudaError_t e = allow_smem(k_fft_x_r2c<T, N>, sm);
     if (e != cudaSuccess) return e;
-    k_fft_x_r2c<T, N><<<blocks, kThreads, sm, s>>>(in, (C *)spec, npairs, skip);
-    return cudaGetLastError();
+    return launch_k(skip != nullptr, k_fft_x_r2c<T, N>, dim3(blocks), dim3(kThreads), sm, s, in, (C *)spec, npairs, skip);
 }
 
 template <typename T, int N>
@@ -591,9 +626,8 @@ cudaError_t x_c2r_n(const void *spec, T *out, int nfields, T scale, const double
     if (add6)
         for (int i = 0; i < 6; ++i) a[i] = (T)add6[i];
     const int has_add = add6 != nullptr;
-    k_fft_x_c2r<T, N><<<blocks, kThreads, sm, s>>>((const C *)spec, out, npairs, scale, has_add, a[0], a[1], a[2], a[3],
-                                                   a[4], a[5], base, skip);
-    return cudaGetLastError();
+    return launch_k(skip != nullptr, k_fft_x_c2r<T, N>, dim3(blocks), dim3(kThreads), sm, s, (const C *)spec, out, npairs,
+                    scale, has_add, a[0], a[1], a[2], a[3], a[4], a[5], base, skip);
 }
 
 template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int inverse, cudaStream_t s, const int *skip) {
@@ -603,9 +637,8 @@ template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int invers
     const size_t sm = smem_y<T, N>();
     cudaError_t e = inverse ? allow_smem(k_fft_y<T, N, true>, sm) : allow_smem(k_fft_y<T, N, false>, sm);
     if (e != cudaSuccess) return e;
-    if (inverse) k_fft_y<T, N, true><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec, skip);
-    else k_fft_y<T, N, false><<<blocks, y_threads<N, T>(), sm, s>>>((C *)spec, skip);
-    return cudaGetLastError();
+    if (inverse) return launch_k(skip != nullptr, k_fft_y<T, N, true>, dim3(blocks), dim3(y_threads<N, T>()), sm, s, (C *)spec, skip);
+    return launch_k(skip != nullptr, k_fft_y<T, N, false>, dim3(blocks), dim3(y_threads<N, T>()), sm, s, (C *)spec, skip);
 }
 
 template <typename T, int N>
@@ -619,9 +652,8 @@ cudaError_t z_n(void *spec, int nfields, int mode, double lam0, double mu0, doub
     if (e != cudaSuccess) return e;
     ZCtl zc{};
     if (zcp != nullptr) zc = *zcp;
-    k_fft_z<T, N><<<blocks, z_threads<N, T>(), sm, s>>>((C *)spec, nfields, mode, (T)lam0, (T)mu0, partials, mean6,
-                                                       skip, zc);
-    return cudaGetLastError();
+    return launch_k(skip != nullptr, k_fft_z<T, N>, dim3(blocks), dim3(z_threads<N, T>()), sm, s, (C *)spec, nfields, mode,
+                    (T)lam0, (T)mu0, partials, mean6, skip, zc);
 }
 
 #define EVP_DISPATCH(N_, CALL)                             \

@@ -112,6 +112,8 @@ __global__ void __launch_bounds__(kThreads) k_newton(long N3, const TA *__restri
                                                     const TA *__restrict__ Stab, const TA *__restrict__ Mtab, MatConst mc,
                                                     TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int *__restrict__ skip,
     const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,6 +201,8 @@ __global__ void __launch_bounds__(kThreads) k_newton_df(long N3, const double *_
                                                        const float *__restrict__ Mtabf, MatConst mc, double tol,
                                                        int maxit, int *__restrict__ flags, const int *__restrict__ skip,
     const double *__restrict__ tol_dev) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -314,6 +318,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
                                                           TS *__restrict__ fac, MatConst mc, TA tol, int maxit,
                                                           TA ls_free, int force_refresh, int *__restrict__ flags, const int *__restrict__ skip,
     const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,6 +370,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
                                                          MatConst mc, TA tol, int *__restrict__ flags,
                                                          int32_t *__restrict__ wl, const int *__restrict__ skip,
     const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -422,6 +430,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_res
     TA *__restrict__ sig, const TA *__restrict__ Stab, const TA *__restrict__ Mtab, TS *__restrict__ fac, MatConst mc,
     TA tol, int maxit, TA ls_free, int *__restrict__ flags, const int32_t *__restrict__ wl, const int *__restrict__ skip,
     const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
+    pdl_wait();
+    pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const int count = *(volatile const int *)(flags + 10);
@@ -688,24 +698,59 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_al_local(
 template <typename TA>
 __global__ void __launch_bounds__(256) k_predictor(long N3, const TA *__restrict__ epse, const TA *__restrict__ deps,
                                                   const TA *__restrict__ rho, TA *__restrict__ epst, TA *__restrict__ tauc,
-                                                  MatConst mc, double r, int use_field, double d0, double d1, double d2,
-                                                  double d3, double d4, double d5) {
+                                                  MatConst mc, TA r, int use_field, TA d0, TA d1, TA d2, TA d3, TA d4,
+                                                  TA d5) {
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N3) return;
-    TA rf = (TA)0;   // in the field precision (the FP32 path keeps the FP64 pipe out)
+    // all loads first; arithmetic in the field precision (the FP32 path keeps the FP64 pipe out)
+    TA rr[12], ee[6], dd[6];
 #pragma unroll
-    for (int a = 0; a < 12; ++a) rf += rho[a * N3 + v];
-    tauc[v] = (TA)mc.tau0 + (TA)mc.alpha_mu_b * sqrt(rf);
-    const double dE[6] = {d0, d1, d2, d3, d4, d5};
+    for (int a = 0; a < 12; ++a) rr[a] = rho[a * N3 + v];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        const TA add = use_field ? (TA)(r * (double)deps[c * N3 + v]) : (TA)dE[c];
-        epst[c * N3 + v] = epse[c * N3 + v] + add;
+        ee[c] = epse[c * N3 + v];
+        dd[c] = use_field ? deps[c * N3 + v] : (TA)0;
     }
+    TA rf = (TA)0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) rf += rr[a];
+    tauc[v] = (TA)mc.tau0 + (TA)mc.alpha_mu_b * sqrt(rf);
+    const TA dE[6] = {d0, d1, d2, d3, d4, d5};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) epst[c * N3 + v] = ee[c] + (use_field ? r * dd[c] : dE[c]);
+}
+
+// Error-free sum of two floats (Knuth's two-sum): s + e equals a + b exactly.
+__device__ __forceinline__ void two_sum_k(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// k = sum of the 12 densities as a double. FP64 fields: summed in FP64. FP32 fields: summed as an unevaluated
+// float pair (two-sum per term, the rounding errors added in float) and converted once: the result is within a few
+// units of 2^-48 of the exact sum of the FP32 densities (the FP64 running sum is exact for them too, or nearly),
+// with 2 FP64-pipe operations instead of 24 on a pipe that runs at 1/64 of the FP32 rate.
+__device__ __forceinline__ double density_total(const double r[12]) {
+    double kk = 0.0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) kk += r[a];
+    return kk;
+}
+__device__ __forceinline__ double density_total(const float r[12]) {
+    float hi = r[0], lo = 0.f;
+#pragma unroll
+    for (int a = 1; a < 12; ++a) {
+        float s, e;
+        two_sum_k(hi, r[a], s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    return (double)hi + (double)lo;
 }
 
 // After convergence (a7): advance eps_p, eps_e, the strain increment and the densities with
-// the converged shear rates; k = rho_tot in FP64.
+// the converged shear rates; k = rho_tot as a double.
 template <typename TA>
 __global__ void __launch_bounds__(kThreads) k_state_update(long N3, const TA *__restrict__ sig, const TA *__restrict__ tauc,
                                                           const int32_t *__restrict__ g0, const TA *__restrict__ Mtab,
@@ -714,12 +759,21 @@ __global__ void __launch_bounds__(kThreads) k_state_update(long N3, const TA *__
                                                           double *__restrict__ kf, MatConst mc) {
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N3) return;
+    // every operand is loaded before any arithmetic, so a thread has all its requests in flight at once
     const int g = g0[v];
-    const TA *M = Mtab + 72 * (long)g;
-    TA sg[6];
+    TA sg[6], tr[6], eo[6], po[6], r[12];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) sg[c] = sig[c * N3 + v];
-    const TA inv_tc = (TA)1 / tauc[v];
+    for (int c = 0; c < 6; ++c) {
+        sg[c] = sig[c * N3 + v];
+        tr[c] = epst[c * N3 + v];
+        eo[c] = epse[c * N3 + v];
+        po[c] = epsp[c * N3 + v];
+    }
+#pragma unroll
+    for (int a = 0; a < 12; ++a) r[a] = rho[a * N3 + v];
+    const TA tcv = tauc[v];
+    const TA *M = Mtab + 72 * (long)g;
+    const TA inv_tc = (TA)1 / tcv;
     const TA g0r = (TA)mc.gdot0, dt = (TA)mc.dt;
     TA ep[6] = {0, 0, 0, 0, 0, 0};
     TA agd[12];
@@ -740,29 +794,22 @@ __global__ void __launch_bounds__(kThreads) k_state_update(long N3, const TA *__
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-        const TA tr = epst[c * N3 + v];
-        const TA eo = epse[c * N3 + v];
-        epsp[c * N3 + v] += dt * ep[c];
-        deps[c * N3 + v] = tr - eo;
-        epse[c * N3 + v] = tr - dt * ep[c];
+        epsp[c * N3 + v] = po[c] + dt * ep[c];
+        deps[c * N3 + v] = tr[c] - eo[c];
+        epse[c * N3 + v] = tr[c] - dt * ep[c];
     }
-    // Kocks-Mecking update in the field precision; k summed in FP64 (the nucleation decision compares it)
+    // Kocks-Mecking update in the field precision
     TA rf = (TA)0;
-    TA r[12];
 #pragma unroll
-    for (int a = 0; a < 12; ++a) {
-        r[a] = rho[a * N3 + v];
-        rf += r[a];
-    }
+    for (int a = 0; a < 12; ++a) rf += r[a];
     const TA srf = sqrt(rf), k1 = (TA)mc.k1, k2 = (TA)mc.k2;
-    double kk = 0.0;
+    TA nr[12];
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
-        const TA nr = r[a] + dt * (k1 * srf - k2 * r[a]) * agd[a];
-        rho[a * N3 + v] = nr;
-        kk += (double)nr;
+        nr[a] = r[a] + dt * (k1 * srf - k2 * r[a]) * agd[a];
+        rho[a * N3 + v] = nr[a];
     }
-    kf[v] = kk;
+    kf[v] = density_total(nr);
 }
 
 template <typename TA>
@@ -805,24 +852,32 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
                                const TA *tol_dev, MRPtr<TA> mrp) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
     if (!force_refresh && wl) {
-        // flags[10] counts the listed voxels; pass 2 reads it on the device (no host round trip)
-        cudaError_t e = cudaMemsetAsync(flags + 10, 0, sizeof(int), s);
-        if (e != cudaSuccess) return e;
+        // flags[10] counts the listed voxels; pass 2 reads it on the device (no host round trip). Inside the
+        // fixed-point loop (skip set) the kernels run as one programmatic-launch chain: the count starts at zero
+        // from the increment's flag reset and is reset by each iteration's control block (fpctl.cuh), so no
+        // memset breaks the chain; outside it the count is reset here.
+        const bool pdl = skip != nullptr;
+        if (!pdl) {
+            cudaError_t e = cudaMemsetAsync(flags + 10, 0, sizeof(int), s);
+            if (e != cudaSuccess) return e;
+        }
         const int rb = std::min(blocks, nsm * (sizeof(TA) == 4 ? 3 : 2));
-        return by_law(mrp, [&](auto law) {
+        cudaError_t err = cudaSuccess;
+        by_law(mrp, [&](auto law) {
             constexpr bool MR = decltype(law)::value;
-            k_chord_first<TA, TA, MR><<<blocks, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (const TA *)fac,
-                                                                  mc, (TA)tol, flags, wl, skip, tol_dev, mrp);
+            err = launch_k(pdl, k_chord_first<TA, TA, MR>, dim3(blocks), dim3(kThreads), 0, s, N3, epst, tauc, g0, sig,
+                           Stab, Mtab, (const TA *)fac, mc, (TA)tol, flags, wl, skip, tol_dev, mrp);
+            if (err != cudaSuccess) return;
             if (solve_fp64)
-                k_chord_rest<TA, TA, double, MR><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab,
-                                                                         (TA *)fac, mc, (TA)tol, maxit,
-                                                                         ls_free_of<TA>(), flags, wl, skip, tol_dev,
-                                                                         mrp);
+                err = launch_k(pdl, k_chord_rest<TA, TA, double, MR>, dim3(rb), dim3(kThreads), 0, s, N3, epst, tauc,
+                               g0, sig, Stab, Mtab, (TA *)fac, mc, (TA)tol, maxit, ls_free_of<TA>(), flags,
+                               (const int32_t *)wl, skip, tol_dev, mrp);
             else
-                k_chord_rest<TA, TA, TA, MR><<<rb, kThreads, 0, s>>>(N3, epst, tauc, g0, sig, Stab, Mtab, (TA *)fac,
-                                                                     mc, (TA)tol, maxit, ls_free_of<TA>(), flags, wl,
-                                                                     skip, tol_dev, mrp);
+                err = launch_k(pdl, k_chord_rest<TA, TA, TA, MR>, dim3(rb), dim3(kThreads), 0, s, N3, epst, tauc, g0,
+                               sig, Stab, Mtab, (TA *)fac, mc, (TA)tol, maxit, ls_free_of<TA>(), flags,
+                               (const int32_t *)wl, skip, tol_dev, mrp);
         });
+        return err != cudaSuccess ? err : cudaGetLastError();
     }
     // factors stored in the field precision; factorised in FP64 unless the FP32 solve is asked for
     return by_law(mrp, [&](auto law) {
@@ -881,8 +936,9 @@ template <typename TA>
 cudaError_t predictor(long N3, const TA *epse, const TA *deps, const TA *rho, TA *epst, TA *tauc, MatConst mc,
                       double r, const double *dE6, int use_field, cudaStream_t s) {
     const int blocks = (int)((N3 + 255) / 256);
-    k_predictor<TA><<<blocks, 256, 0, s>>>(N3, epse, deps, rho, epst, tauc, mc, r, use_field, dE6[0], dE6[1], dE6[2],
-                                           dE6[3], dE6[4], dE6[5]);
+    // the extrapolation ratio and the uniform guess rounded to the field precision once, here
+    k_predictor<TA><<<blocks, 256, 0, s>>>(N3, epse, deps, rho, epst, tauc, mc, (TA)r, use_field, (TA)dE6[0],
+                                           (TA)dE6[1], (TA)dE6[2], (TA)dE6[3], (TA)dE6[4], (TA)dE6[5]);
     return cudaGetLastError();
 }
 
