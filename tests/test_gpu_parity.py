@@ -235,6 +235,7 @@ def test_coupled_window_at_64_cubed_with_nucleation_matches_oracle(ev, mat):
     ref.refresh_derived()
     assert rel(gpu.get("k")[0], ref.field("k")[0]) == 0.0
     total = 0
+    hist_gpu, hist_ref = [], []
     for inc in range(3):
         rc, st = gpu.increment(wl.dE33, wl.dt)
         rco, sto = ref.increment(wl.dE33, wl.dt)
@@ -251,6 +252,8 @@ def test_coupled_window_at_64_cubed_with_nucleation_matches_oracle(ev, mat):
         assert gpu.next_id == ref.next_id
         _, ps = gpu.pf_step(wl.pf_steps)
         _, pso = ref.pf_step(wl.pf_steps)
+        hist_gpu.append((nn, ps.X_rex))
+        hist_ref.append((nno, pso.X_rex))
         assert np.array_equal(gpu.get("ids"), ref.ifield("ids"))        # active sets
         assert np.array_equal(gpu.get("g")[0], ref.ifield("g"))         # argmax ids after the sweep: no flips
         assert rel(gpu.get("eta"), ref.field("eta")) < FP64_TOL
@@ -259,6 +262,15 @@ def test_coupled_window_at_64_cubed_with_nucleation_matches_oracle(ev, mat):
         assert rel(gpu.get("rho"), ref.field("rho")) < FP64_TOL     # sweep softening at the same voxels
     assert total > 100
     assert ps.X_rex > 0.0
+    # the DRX analytics of the two runs (Table CriticalStrainDRX, Eq. NumCrt, Fig. Statistics)
+    from paper_1509_04953_gb300 import analytics as A
+    strain = [abs(wl.dE33) * (i + 1) for i in range(3)]
+    assert A.critical_strain(strain, [h[0] for h in hist_gpu]) == A.critical_strain(strain, [h[0] for h in hist_ref])
+    g_gpu, g_ref = gpu.get("g")[0], ref.ifield("g")
+    assert A.grain_statistics(g_gpu, n, dx=mat.dx) == A.grain_statistics(g_ref, n, dx=mat.dx)
+    e_gpu = A.expected_nuclei(gpu.get("k")[0], g_gpu, n, mat.kc, mat.q)
+    e_ref = A.expected_nuclei(ref.field("k")[0], g_ref, n, mat.kc, mat.q)
+    assert abs(e_gpu / e_ref - 1) < 1e-9
 
 
 def test_converged_increments_match_oracle_fp64(ev, mat):
