@@ -293,7 +293,7 @@ def native(args, ws, rank, local):
     res["pipe_peaks_tflops"] = pipes
     res["roofline"] = roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision=args.precision,
                                facs=n1[2] - n0[2], reuse=mixed.cfg.newton_mode == 1, pipes=pipes)
-    res["memory_bound_kernels"] = memory_kernels(ksplit, wl, N3, args.precision, pk)
+    res["memory_bound_kernels"] = memory_kernels(ksplit, wl, N3, args.precision, pk, iterations=split_steps[0]["it"])
     if args.fast_steps > 0:
         res["mixed_fast"] = fast_companion(args, wl, g0, quat, mat, torch, evp)
     if args.soft_ref_steps > 0:
@@ -320,11 +320,11 @@ def native(args, ws, rank, local):
     return res
 
 
-# Measured DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum, averaged over 214 iterations of the
-# second and third increments) of one local-solve iteration (pass 1 326.8 MB + pass 2 15.0 MB), per workload,
-# with the SHA-256 prefix of the local-solve sources it was taken on. A figure taken on other sources is stale
-# and reported as null.
-NEWTON_TRAFFIC = {(128, "mixed", True): (341.8e6, "e086464008509734")}
+# Measured DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum, averaged over 20 iterations of the
+# second increment) of one local-solve iteration (pass 1 326.8 MB + pass 2 0.1 MB), per workload, with the
+# SHA-256 prefix of the local-solve sources it was taken on. A figure taken on other sources is stale and
+# reported as null.
+NEWTON_TRAFFIC = {(128, "mixed", True): (326.9e6, "bc0e6195a9e87630")}
 NEWTON_SOURCES = ("paper_1509_04953_gb300/csrc/newton.cu", "paper_1509_04953_gb300/csrc/local.cuh")
 
 
@@ -372,7 +372,7 @@ def pipe_peaks(evp):
 
 def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, facs=0, reuse=False, pipes=None):
     ms, n = ktimes[dom]
-    avg_s = ms / 1e3 / max(n, 1)
+    avg_s = per_unit(dom, ms, n, iters)
     T = 4 if precision != "fp64" else 8
     if dom == "newton":
         # Count the algorithmic flops by pipe and report the pipe they bind. Tangent reuse (chord)
@@ -439,15 +439,28 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
             "frac": achieved / peak, "traffic": None, "peak_source": pk_kind}
 
 
-def memory_kernels(ktimes, wl, N3, precision, pk):
+# Kernel classes launched once per fixed-point iteration. Iterations are queued in batches and the ones queued after
+# convergence return at once, so these classes are averaged over the iterations that ran, not over their launches.
+ITERATION_CLASSES = ("newton", "fft_x_r2c", "fft_y_fwd", "fft_z_gamma", "fft_y_inv", "fft_x_c2r_update")
+
+
+def per_unit(kernel, ms, launches, iterations):
+    """Average time of one unit of work of a kernel class, in seconds: one iteration for the iteration classes (the
+    time of the brackets that returned at once counts against the iterations that ran), one launch otherwise."""
+    units = iterations if (kernel in ITERATION_CLASSES and iterations) else launches
+    return ms / 1e3 / max(units, 1)
+
+
+def memory_kernels(ktimes, wl, N3, precision, pk, iterations=None):
     T = 4 if precision != "fp64" else 8
     out = {}
     for k, (ms, n) in ktimes.items():
         bpv = hbm_bytes_per_voxel(k, wl.n, T)
         if bpv is None or n == 0:
             continue
-        gbs = bpv * N3 / (ms / 1e3 / n) / 1e9
-        out[k] = {"avg_us": round(1e3 * ms / n, 2), "GB/s": round(gbs, 1), "frac": round(gbs / pk.get("hbm_gbs", 6800.0), 3)}
+        avg = per_unit(k, ms, n, iterations)
+        gbs = bpv * N3 / avg / 1e9
+        out[k] = {"avg_us": round(1e6 * avg, 2), "GB/s": round(gbs, 1), "frac": round(gbs / pk.get("hbm_gbs", 6800.0), 3)}
     return out
 
 
@@ -606,12 +619,12 @@ def mr_companion(args, wl, g0, quat, torch, evp, pk):
                                "frac": round(b / per / 1e9 / hpk, 3), "bytes_per_increment": b}
     ms, nl = kt.get("newton", (0.0, 0))
     if nl:
-        per = ms / nl / 1e3
+        per = per_unit("newton", ms, nl, iters)
         # AL local step, per voxel: reads trial and elastic strain, multiplier, stress (24), tau_ref (1), tau_pass
         # and 1/tau_cut (24), stored factors (24 planes' words) and the grain id; writes stress, multiplier,
         # polarisation (18) and, on a refresh, the factors
         b = ((6 + 6 + 6 + 6 + 1 + 24 + 24 + 18) * T + 4) * N3
-        out["local_solve"] = {"us_per_launch": round(1e6 * per, 1), "GB/s": round(b / per / 1e9, 1),
+        out["local_solve"] = {"us_per_iteration": round(1e6 * per, 1), "GB/s": round(b / per / 1e9, 1),
                               "frac": round(b / per / 1e9 / hpk, 3)}
     if args.mr_fp64_steps > 0 and prec != "fp64":
         s64 = evp.Solver(wl.n, wl.grains, g0, quat, mat, wl.seed, precision="fp64", law="mr", scheme="al",

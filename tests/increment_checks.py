@@ -52,3 +52,43 @@ def check_first_increment(mat, quat, g0, n, dt, tol, fields, sig_mean_reported, 
     assert np.abs(want_r - rho[:, sample]).max() <= state_tol * np.abs(want_r).max()
     assert np.abs(want_r.sum(axis=0) - k[sample]).max() <= state_tol * np.abs(want_r.sum(axis=0)).max()
     return err_eq
+
+
+def check_increment(mat, quat, g0, n, dt, tol, before, after, sig_mean_reported, sample, loc_tol, state_tol,
+                    eq_factor=3.0):
+    """The same checks for any increment of the power-law workload, from the state before it (plastic strain and
+    densities) and after it (stress, total strain, plastic strain, densities, k): equilibrium and boundary
+    conditions of the new stress; at sampled voxels the local implicit update from the trial strain (total strain
+    after minus plastic strain before) with tau_c frozen at the densities before (reading C7), the plastic strain
+    and Kocks-Mecking densities it advances, and k, their sum."""
+    sig = np.asarray(after["sig"], dtype=np.float64)
+    out = O.stress_residual(n, sig)
+    mean = out[:6]
+    den = max(np.linalg.norm(mean), mat.tau0)
+    err_eq = np.sqrt(out[6]) / (n ** 3 * den)
+    assert err_eq <= eq_factor * tol, f"equilibrium residual {err_eq:.3e}"
+    assert np.linalg.norm(mean[STRESS_CONTROLLED]) / den <= 10 * tol
+    assert np.abs(mean - np.asarray(sig_mean_reported)).max() / den <= 10 * tol
+    _, S, M = O.grain_tables(mat, quat)
+    mu = (mat.C11 - mat.C12 + 3.0 * mat.C44) / 5.0
+    eps = np.asarray(after["eps"], dtype=np.float64)
+    p0 = np.asarray(before["epsp"], dtype=np.float64)
+    r0 = np.asarray(before["rho"], dtype=np.float64)
+    p1 = np.asarray(after["epsp"], dtype=np.float64)
+    r1 = np.asarray(after["rho"], dtype=np.float64)
+    k1 = np.asarray(after["k"], dtype=np.float64)
+    ws, wp, wr = [], [], []
+    for v in sample:
+        g = int(g0[v])
+        tauc = mat.tau0 + mat.alpha * mu * mat.b * np.sqrt(r0[:, v].sum())
+        rc, s, gd, _ = O.newton(mat, S[g], M[g], eps[:, v] - p0[:, v], tauc, dt, sig[:, v])
+        assert rc >= 0, f"oracle local Newton failed at voxel {v}"
+        ws.append(s)
+        wp.append(p0[:, v] + dt * M[g].T @ gd)
+        wr.append(O.km_update(mat, r0[:, v], gd, dt))
+    ws, wp, wr = np.array(ws).T, np.array(wp).T, np.array(wr).T
+    assert np.abs(ws - sig[:, sample]).max() <= loc_tol * np.abs(sig).max()
+    assert np.abs(wp - p1[:, sample]).max() <= state_tol * np.abs(wp - p0[:, sample]).max()
+    assert np.abs(wr - r1[:, sample]).max() <= state_tol * np.abs(wr - r0[:, sample]).max()
+    assert np.abs(r1[:, sample].sum(axis=0) - k1[sample]).max() <= 1e-6 * np.abs(k1[sample]).max()
+    return err_eq

@@ -48,6 +48,19 @@ def test_stored_traffic_is_dropped_once_its_sources_change(tmp_path, monkeypatch
     assert bench.measured_traffic(table, (2, "mixed", True), ["k.cu"]) is None
 
 
+def test_iteration_classes_are_averaged_over_the_iterations_that_ran():
+    """Iterations queued after convergence return at once: an iteration class is averaged over the iterations that
+    ran (its brackets' total time over them), a per-increment class over its launches."""
+    import bench
+    assert bench.per_unit("fft_z_gamma", 128.0, 128, 113) == pytest.approx(128.0 / 1e3 / 113)
+    assert bench.per_unit("newton", 10.0, 128, 113) == pytest.approx(10.0 / 1e3 / 113)
+    assert bench.per_unit("state_update", 0.15, 1, 113) == pytest.approx(0.15 / 1e3)
+    assert bench.per_unit("fft_z_gamma", 1.0, 16, None) == pytest.approx(1.0 / 1e3 / 16)
+    m = bench.memory_kernels({"fft_y_fwd": (2.0, 128)}, types.SimpleNamespace(n=128), 128 ** 3, "mixed",
+                             {"hbm_gbs": 5000.0}, iterations=100)
+    assert m["fft_y_fwd"]["avg_us"] == 20.0
+
+
 def test_fft_pass_bytes_follow_the_half_spectrum():
     import bench
     n, T = 128, 4

@@ -324,6 +324,35 @@ def test_converged_increment_checks_hold_for_the_oracle(mat, n, G):
         check_first_increment(mat, quat, g0, n, 2.0, 1e-6, fields, s.sig_mean, sample, 1e-9, 1e-9)
 
 
+def test_any_increment_checks_hold_for_the_oracle_in_the_drx_regime(mat):
+    """The any-increment checks (tests/increment_checks.py check_increment) that the GPU's full-size run in the DRX
+    regime is held to hold for the oracle's own run to round-off: densities raised so that nucleation and sweep
+    softening act, two coupled increments, then the third increment checked from the state before it."""
+    from increment_checks import check_increment
+    n, G, seed = 16, 8, synth.BASE_SEED
+    quat = synth.orientations(G, seed)
+    g0 = O.voronoi(n, synth.voronoi_seeds(n, G, seed))
+    st = O.State(n, G, g0, quat, mat, seed=seed, tol=1e-6, max_iter=5000)
+    st.field("rho")[:] = np.repeat(np.random.default_rng(1).uniform(2e13, 6e13, size=(1, n ** 3)), 12, axis=0)
+    st.refresh_derived()
+    nuclei = 0
+    for inc in range(2):
+        assert st.increment(-1e-3, 1.0)[0] == 0
+        nuclei += st.nucleate(inc)[1]
+        st.pf_step(5)
+    assert nuclei > 0
+    before = {f: st.field(f).copy() for f in ("epsp", "rho")}
+    rc, s = st.increment(-1e-3, 1.0)
+    assert rc == 0
+    after = {f: st.field(f) for f in ("sig", "eps", "epsp", "rho")}
+    after["k"] = st.field("k")[0]
+    sample = np.random.default_rng(4).choice(n ** 3, 200, replace=False)
+    check_increment(mat, quat, g0, n, 1.0, 1e-6, before, after, s.sig_mean, sample, 1e-9, 1e-9, eq_factor=1.0)
+    with pytest.raises(AssertionError):      # the densities before the increment, not after, freeze tau_c
+        check_increment(mat, quat, g0, n, 1.0, 1e-6, {"epsp": before["epsp"], "rho": after["rho"]}, after,
+                        s.sig_mean, sample, 1e-9, 1e-9)
+
+
 @pytest.mark.parametrize("scheme,ref_scale", [(0, 1.0), (1, 1.0), (0, 1.3)],
                          ids=["basic", "augmented_lagrangian", "basic_softer_reference"])
 def test_elastic_laminate_closed_form(mat, scheme, ref_scale):
