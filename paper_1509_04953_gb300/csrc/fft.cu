@@ -152,7 +152,10 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
         __syncthreads();
     } else {
         // pass 1: radix R1, Ns = 1: item (l, j < M1) reads slots j + M1 r and writes j R1 + r, so
-        // every read completes before any write (held in registers across a barrier)
+        // every read completes before any write (held in registers across a barrier). With j < M1 and M1 | 16
+        // the padded slots are pad16(j + M1 r) = j + pad16(M1 r) and pad16(16 j + r) = 17 j + r (r < 16): one base
+        // address per item and compile-time offsets.
+        static_assert(16 % M1 == 0 || M1 % 16 == 0, "pass-1 stride");
         const int items = nlines * M1;
         C v[MAXIT][R1];
 #pragma unroll
@@ -161,8 +164,9 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
             if (t < items) {
                 int l, j;
                 pass1_item<N>(t, nlines, l, j);
+                const C *src = buf + l * LS + (M1 <= 16 ? j : pad16(j));
 #pragma unroll
-                for (int r = 0; r < R1; ++r) v[it][r] = buf[l * LS + pad16(j + r * M1)];
+                for (int r = 0; r < R1; ++r) v[it][r] = src[M1 <= 16 ? pad16(r * M1) : r * (M1 + M1 / 16)];
             }
         }
         __syncthreads();
@@ -173,18 +177,21 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
                 int l, j;
                 pass1_item<N>(t, nlines, l, j);
                 dft_reg<R1, INV>(v[it]);
+                C *dst = buf + l * LS + 17 * j;
 #pragma unroll
-                for (int r = 0; r < R1; ++r) buf[l * LS + pad16(j * R1 + r)] = v[it][r];
+                for (int r = 0; r < R1; ++r) dst[r] = v[it][r];
             }
         }
         __syncthreads();
-        // pass 2: radix R2, Ns = R1 = 16: item (l, j < 16) reads and writes slots j + 16 r only
+        // pass 2: radix R2, Ns = R1 = 16: item (l, j < 16) reads and writes slots j + 16 r only, which are
+        // pad16(j + 16 r) = j + 17 r
         for (int t = threadIdx.x; t < nlines * 16; t += blockDim.x) {
             const int l = t >> 4, j = t & 15;
+            C *line = buf + l * LS + j;
             C u[R2];
 #pragma unroll
             for (int r = 0; r < R2; ++r) {
-                C a = buf[l * LS + pad16(j + 16 * r)];
+                C a = line[17 * r];
                 if (r > 0) {
                     C w = tw[16 * r + j];   // = exp(-2 pi i r j / N), r-major: a half-warp reads 16 in a row
                     if (INV) w.y = -w.y;
@@ -194,7 +201,7 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
             }
             dft_reg<R2, INV>(u);
 #pragma unroll
-            for (int r = 0; r < R2; ++r) buf[l * LS + pad16(j + 16 * r)] = u[r];
+            for (int r = 0; r < R2; ++r) line[17 * r] = u[r];
         }
         __syncthreads();
     }
@@ -533,16 +540,10 @@ __global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 
     if (mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) {
         const bool apply = mode == Z_FWD_GAMMA_INV;
         T acc = (T)0;   // per-thread sum in the field precision; block and global sums in FP64
-        const int npts = (TX + (nyq ? 1 : 0)) * N;
-        for (int t = threadIdx.x; t < npts; t += blockDim.x) {
-            const bool reg = t < TX * N;
-            int zr = 0, xr = 0;
-            if (reg) slab_item<N, TX>(t, zr, xr);
-            const int kz = reg ? zr : t - TX * N;
-            const int kx = reg ? kx0 + xr : N / 2;
-            const int l0 = reg ? xr : nf * TX, ls = reg ? TX : 1;   // line of field f: l0 + f*ls
+        // one frequency: its six field values at p0 + f * fstep in the slab
+        auto point = [&](int kz, int kx, C *p0, int fstep) {
             C s6[6];
-            for (int f = 0; f < 6; ++f) s6[f] = buf[(l0 + f * ls) * LS + pad16(kz)];
+            for (int f = 0; f < 6; ++f) s6[f] = p0[f * fstep];
             if (kx == 0 && ky == 0 && kz == 0 && mean6 != nullptr) {
                 const double inv = 1.0 / ((double)N * N * N);
                 for (int f = 0; f < 6; ++f) mean6[f] = (double)s6[f].x * inv;
@@ -550,7 +551,25 @@ __global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 
             const bool partner = !(kx == 0 || kx == (N >> 1));
             gamma_point<C, T>(s6, kx, ky, kz, N, lam0, mu0, acc, partner, apply);
             if (apply)
-                for (int f = 0; f < 6; ++f) buf[(l0 + f * ls) * LS + pad16(kz)] = s6[f];
+                for (int f = 0; f < 6; ++f) p0[f * fstep] = s6[f];
+        };
+        if constexpr (walk) {   // the same points per thread, in the same order, as the loop below
+            C *pb = buf + wxl * LS + pad16(wz);
+#pragma unroll
+            for (int k = 0; k < KZ; ++k) point(wz + k * DZ, kx0 + wxl, pb + k * (DZ + DZ / 16), TX * LS);
+            if (nyq)
+                for (int t = threadIdx.x; t < N; t += blockDim.x) point(t, N / 2, buf + nf * TX * LS + pad16(t), LS);
+        } else {
+            const int npts = (TX + (nyq ? 1 : 0)) * N;
+            for (int t = threadIdx.x; t < npts; t += blockDim.x) {
+                const bool reg = t < TX * N;
+                int zr = 0, xr = 0;
+                if (reg) slab_item<N, TX>(t, zr, xr);
+                const int kz = reg ? zr : t - TX * N;
+                const int kx = reg ? kx0 + xr : N / 2;
+                const int l0 = reg ? xr : nf * TX, ls = reg ? TX : 1;   // line of field f: l0 + f*ls
+                point(kz, kx, buf + l0 * LS + pad16(kz), ls * LS);
+            }
         }
         __syncthreads();
         const double tot = block_sum((double)acc, red);
