@@ -185,18 +185,23 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
         __syncthreads();
         // pass 2: radix R2, Ns = R1 = 16: item (l, j < 16) reads and writes slots j + 16 r only, which are
         // pad16(j + 16 r) = j + 17 r
+        // Every CTA has a multiple of 16 threads, so a thread's items share one j = threadIdx.x mod 16 and its
+        // twiddles tw[16 r + j] = exp(-2 pi i r j / N) are loaded once, into registers.
+        const int jt = threadIdx.x & 15;
+        C wr[R2];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) {
+            wr[r] = tw[16 * r + jt];   // r-major: a half-warp reads 16 in a row
+            if (INV) wr[r].y = -wr[r].y;
+        }
         for (int t = threadIdx.x; t < nlines * 16; t += blockDim.x) {
-            const int l = t >> 4, j = t & 15;
-            C *line = buf + l * LS + j;
+            const int l = t >> 4;
+            C *line = buf + l * LS + jt;
             C u[R2];
 #pragma unroll
             for (int r = 0; r < R2; ++r) {
                 C a = line[17 * r];
-                if (r > 0) {
-                    C w = tw[16 * r + j];   // = exp(-2 pi i r j / N), r-major: a half-warp reads 16 in a row
-                    if (INV) w.y = -w.y;
-                    a = cmul(a, w);
-                }
+                if (r > 0) a = cmul(a, wr[r]);
                 u[r] = a;
             }
             dft_reg<R2, INV>(u);
@@ -363,7 +368,8 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_c2r(const typename CT<T>::ty
 // y pass: CTA = (field, z, kx tile of TX columns); lines along y.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(y_threads<N, T>()) k_fft_y(typename CT<T>::type *__restrict__ spec, const int *__restrict__ skip) {
+__global__ void __launch_bounds__(y_threads<N, T>(), sizeof(T) == 4 && N >= 64 && N <= 128 ? 5 : 1)
+k_fft_y(typename CT<T>::type *__restrict__ spec, const int *__restrict__ skip) {
     pdl_wait();
     pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
