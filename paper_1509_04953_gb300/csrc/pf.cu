@@ -625,13 +625,11 @@ cudaError_t pf_one_step(int n, const int32_t *ids, const T *eta, int32_t *ids2, 
     const long N3 = (long)n * n * n;
     if (pc.K > KM || pc.K < 1) return cudaErrorInvalidValue;
     if (n >= kTX && rcur != nullptr && rdst != nullptr) {
-        static bool attr_set = false;   // per instantiation
+        // set on every launch (a host-side call of about a microsecond): the attribute belongs to the current
+        // device, so a process that drives several GPUs needs it on each
         const int sm = (int)sizeof(PFTile<T>);
-        if (!attr_set) {
-            const cudaError_t e = cudaFuncSetAttribute(k_pf_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        const cudaError_t e = cudaFuncSetAttribute(k_pf_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
         const dim3 grid(n / kTX, n / kTY, n / kZC);
         k_pf_tile<T><<<grid, kTileThreads, sm, s>>>(n, ids, eta, ids2, eta2, g, k, pc, overflow, rcur, rdst);
     } else {
