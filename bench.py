@@ -857,7 +857,8 @@ def large_companion(args, torch, evp, pk):
     if T > 0:
         ck = max(1, int(round(T ** 0.5)))
         nb = C.c_size_t(0)
-        evp.load().evp_adjoint_workspace_bytes(C.byref(s.cfg), 100, 10, C.byref(nb))
+        if evp.load().evp_adjoint_workspace_bytes(C.byref(s.cfg), 100, 10, C.byref(nb)) != 0:
+            raise evp.EVPError("evp_adjoint_workspace_bytes refused the 100-increment sweep")
         st = s.stream
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         s.adjoint_begin(T, ck)
