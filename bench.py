@@ -350,8 +350,8 @@ def hbm_bytes_per_voxel(kernel, n, T):
     """Algorithmic HBM bytes per voxel for one launch of a memory-bound kernel (each field word read
     and written once; half spectra have (n/2+1)/n complex words per real word)."""
     Hw = (n // 2 + 1) / n
-    return {"fft_x_r2c": (6 + 12 * Hw) * T, "fft_y_fwd": 24 * Hw * T, "fft_z_gamma": 24 * Hw * T,
-            "fft_y_inv": 24 * Hw * T, "fft_x_c2r_update": (12 * Hw + 12) * T,
+    return {"fft_xy_r2c": (6 + 12 * Hw) * T, "fft_y_fwd": 24 * Hw * T, "fft_z_gamma": 24 * Hw * T,
+            "fft_y_inv": 24 * Hw * T, "fft_xy_c2r_update": (12 * Hw + 12) * T,
             "predictor": (12 + 6 + 6 + 6 + 1) * T, "state_update": (6 + 1 + 6 + 4 * 6 + 24) * T + 4 + 8,
             "pf_step": 2 * 8 * (4 + T) + 8}.get(kernel)
 
@@ -441,7 +441,7 @@ def roofline(dom, ktimes, wl, N3, iters, solves, evals, pk, pk_kind, precision, 
 
 # Kernel classes launched once per fixed-point iteration. Iterations are queued in batches and the ones queued after
 # convergence return at once, so these classes are averaged over the iterations that ran, not over their launches.
-ITERATION_CLASSES = ("newton", "fft_x_r2c", "fft_y_fwd", "fft_z_gamma", "fft_y_inv", "fft_x_c2r_update")
+ITERATION_CLASSES = ("newton", "fft_xy_r2c", "fft_y_fwd", "fft_z_gamma", "fft_y_inv", "fft_xy_c2r_update")
 
 
 def per_unit(kernel, ms, launches, iterations):

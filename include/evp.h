@@ -246,9 +246,12 @@ int evp_adjoint_end(evp_handle *h, const double *gbar, double *grad, double tol,
 
 /* Instrumentation. Kernel launches are always counted. With profiling on (evp_set_profiling
  * (h, 1)) every kernel launch is bracketed by CUDA events on the handle's stream and its device
- * time is accumulated per kernel class. Classes: 0 newton, 1 fft_x_r2c, 2 fft_y_fwd,
- * 3 fft_z_gamma, 4 fft_y_inv, 5 fft_x_c2r_update, 6 reduce, 7 predictor, 8 state_update,
- * 9 nucleate, 10 pf_step, 11 pf_soften, 12 pf_stats. ms and launches hold EVP_NCLASS entries. */
+ * time is accumulated per kernel class. Classes: 0 newton, 1 fft_xy_r2c, 2 fft_y_fwd,
+ * 3 fft_z_gamma, 4 fft_y_inv, 5 fft_xy_c2r_update, 6 reduce, 7 predictor, 8 state_update,
+ * 9 nucleate, 10 pf_step, 11 pf_soften, 12 pf_stats. Classes 1 and 5 are the x passes of the forward and
+ * inverse transforms; where a (field, z) plane fits one SM's shared memory (FP32 up to n = 128, FP64 up to
+ * n = 64, n >= 32) the y pass runs inside them and classes 2 and 4 stay empty. ms and launches hold
+ * EVP_NCLASS entries. */
 #define EVP_NCLASS 13
 int evp_set_profiling(evp_handle *h, int on);
 /* Profile only the classes whose bits are set in mask (bit c = class c; 0 = off). The events cost a few

@@ -478,6 +478,37 @@ static_assert(sizeof(FpCtl) <= 256, "FpCtl must fit its workspace slot");
 constexpr int kFpBatch = 16;   // iterations queued between host reads of the control block
 const double kZero6[6] = {0, 0, 0, 0, 0, 0};
 
+// The x and y passes of the fixed point's transforms, forward and inverse: one launch each where the (field, z)
+// plane fits shared memory (timed as classes 1 and 5), else the two passes (classes 1, 2 and 4, 5).
+int xy_launches(const evp_handle *h) { return fft_xy_fused(h->n, h->dbl) ? 1 : 2; }
+template <typename T> cudaError_t fwd_xy(evp_handle *h, const T *in, const int *skip = nullptr) {
+    if (fft_xy_fused(h->n, h->dbl)) {
+        PROF(1, 1);
+        return fft_xy_r2c<T>(in, h->spec, h->n, 6, h->st, skip);
+    }
+    {
+        PROF(1, 1);
+        const cudaError_t e = fft_x_r2c<T>(in, h->spec, h->n, 6, h->st, skip);
+        if (e != cudaSuccess) return e;
+    }
+    PROF(2, 1);
+    return fft_y<T>(h->spec, h->n, 6, 0, h->st, skip);
+}
+template <typename T>
+cudaError_t inv_xy(evp_handle *h, T *out, T scale, const double *add6, const T *base, const int *skip = nullptr) {
+    if (fft_xy_fused(h->n, h->dbl)) {
+        PROF(5, 1);
+        return fft_xy_c2r<T>(h->spec, out, h->n, 6, scale, add6, h->st, base, skip);
+    }
+    {
+        PROF(4, 1);
+        const cudaError_t e = fft_y<T>(h->spec, h->n, 6, 1, h->st, skip);
+        if (e != cudaSuccess) return e;
+    }
+    PROF(5, 1);
+    return fft_x_c2r<T>(h->spec, out, h->n, 6, scale, add6, h->st, base, skip);
+}
+
 template <typename TA>
 int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, int *nmax_out, double *err_eq,
             double *err_bc, double *mean_sig) {
@@ -524,12 +555,9 @@ int al_loop(evp_handle *h, MatConst mc, double *dE, int *it_out, int *conv_out, 
         for (int i = 3; i < 6; ++i) dEk[i] = -(hs[2 + i] / (double)N3) / (2.0 * mu0);
         for (int i = 0; i < 6; ++i) dE[i] += dEk[i];
         // compatibility: eps_tr = eps_e^t + dE + Gamma0 * (C0 de - lam)
-        { PROF(1, 1); CK(fft_x_r2c<TA>((const TA *)h->pal, h->spec, n, 6, h->st)); }
-        { PROF(2, 1); CK(fft_y<TA>(h->spec, n, 6, 0, h->st)); }
+        CK(fwd_xy<TA>(h, (const TA *)h->pal));
         { PROF(3, 1); CK(fft_z<TA>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, nullptr, nullptr, h->st)); }
-        { PROF(4, 1); CK(fft_y<TA>(h->spec, n, 6, 1, h->st)); }
-        { PROF(5, 1);
-          CK(fft_x_c2r<TA>(h->spec, (TA *)h->epst, n, 6, (TA)(1.0 / (double)N3), dE, h->st, (const TA *)h->epse)); }
+        CK(inv_xy<TA>(h, (TA *)h->epst, (TA)(1.0 / (double)N3), dE, (const TA *)h->epse));
         rc = local(0, it == 1);
         if (rc) break;
         double En = 0.0, mn = 0.0, mu_n = 0.0;
@@ -881,8 +909,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                                 (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
                                                 h->flags, h->st, skip, tl64, mr_ptr<double>(h))); }
-                  { PROF(1, 1); CK(fft_x_r2c<double>((double *)h->sigk, h->spec, n, 6, h->st, skip)); }
-                  { PROF(2, 1); CK(fft_y<double>(h->spec, n, 6, 0, h->st, skip)); }
+                  CK(fwd_xy<double>(h, (const double *)h->sigk, skip));
                   { PROF(3, 1);
                     CK(fft_z<double>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0r, mu0r, h->partials, h->scal, h->st, skip,
                                      &zc)); }
@@ -897,21 +924,16 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                                (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,
                                                h->flags, h->st, skip, tl32, mr_ptr<float>(h))); }
-                  { PROF(1, 1); CK(fft_x_r2c<float>((float *)h->sigk, h->spec, n, 6, h->st, skip)); }
-                  { PROF(2, 1); CK(fft_y<float>(h->spec, n, 6, 0, h->st, skip)); }
+                  CK(fwd_xy<float>(h, (const float *)h->sigk, skip));
                   { PROF(3, 1);
                     CK(fft_z<float>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0r, mu0r, h->partials, h->scal, h->st, skip,
                                     &zc)); }
                 }
                 // the strain correction arrives through the zero-frequency term: no offsets here
                 if (h->dbl) {
-                    { PROF(4, 1); CK(fft_y<double>(h->spec, n, 6, 1, h->st, skip)); }
-                    { PROF(5, 1);
-                      CK(fft_x_c2r<double>(h->spec, (double *)h->epst, n, 6, inv, kZero6, h->st, nullptr, skip)); }
+                    CK(inv_xy<double>(h, (double *)h->epst, inv, kZero6, nullptr, skip));
                 } else {
-                    { PROF(4, 1); CK(fft_y<float>(h->spec, n, 6, 1, h->st, skip)); }
-                    { PROF(5, 1);
-                      CK(fft_x_c2r<float>(h->spec, (float *)h->epst, n, 6, (float)inv, kZero6, h->st, nullptr, skip)); }
+                    CK(inv_xy<float>(h, (float *)h->epst, (float)inv, kZero6, nullptr, skip));
                 }
             }
             queued += nb;
@@ -1202,12 +1224,10 @@ int evp_rfft3d(int n, int precision, int nfields, const void *in_dev, void *out_
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e;
     if (precision == EVP_FP64) {
-        e = fft_x_r2c<double>((const double *)in_dev, out_dev, n, nfields, s);
-        if (e == cudaSuccess) e = fft_y<double>(out_dev, n, nfields, 0, s);
+        e = fft_xy_r2c<double>((const double *)in_dev, out_dev, n, nfields, s);
         if (e == cudaSuccess) e = fft_z<double>(out_dev, n, nfields, Z_FWD, 0, 0, nullptr, nullptr, s);
     } else {
-        e = fft_x_r2c<float>((const float *)in_dev, out_dev, n, nfields, s);
-        if (e == cudaSuccess) e = fft_y<float>(out_dev, n, nfields, 0, s);
+        e = fft_xy_r2c<float>((const float *)in_dev, out_dev, n, nfields, s);
         if (e == cudaSuccess) e = fft_z<float>(out_dev, n, nfields, Z_FWD, 0, 0, nullptr, nullptr, s);
     }
     return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
@@ -1220,12 +1240,10 @@ int evp_irfft3d(int n, int precision, int nfields, void *in_dev, void *out_dev, 
     cudaError_t e;
     if (precision == EVP_FP64) {
         e = fft_z<double>(in_dev, n, nfields, Z_INV, 0, 0, nullptr, nullptr, s);
-        if (e == cudaSuccess) e = fft_y<double>(in_dev, n, nfields, 1, s);
-        if (e == cudaSuccess) e = fft_x_c2r<double>(in_dev, (double *)out_dev, n, nfields, 1.0, nullptr, s);
+        if (e == cudaSuccess) e = fft_xy_c2r<double>(in_dev, (double *)out_dev, n, nfields, 1.0, nullptr, s);
     } else {
         e = fft_z<float>(in_dev, n, nfields, Z_INV, 0, 0, nullptr, nullptr, s);
-        if (e == cudaSuccess) e = fft_y<float>(in_dev, n, nfields, 1, s);
-        if (e == cudaSuccess) e = fft_x_c2r<float>(in_dev, (float *)out_dev, n, nfields, 1.0f, nullptr, s);
+        if (e == cudaSuccess) e = fft_xy_c2r<float>(in_dev, (float *)out_dev, n, nfields, 1.0f, nullptr, s);
     }
     return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
@@ -1349,14 +1367,13 @@ int adjoint_sweep(evp_handle *h, const AdjLayout &L, const double *gbar, double 
                 double err = 0.0;
                 for (it = 1; it <= max_iter; ++it) {
                     CK(adj_tau<TA>(N3, Ct, eb, aa, (TA *)h->sigk, h->st));
-                    CK(fft_x_r2c<TA>((const TA *)h->sigk, h->spec, n, 6, h->st));
-                    CK(fft_y<TA>(h->spec, n, 6, 0, h->st));
+                    CK(fft_xy_r2c<TA>((const TA *)h->sigk, h->spec, n, 6, h->st));
                     CK(fft_z<TA>(h->spec, n, 6, Z_FWD_GAMMA_INV, lam0, mu0, h->partials, h->scal, h->st));
                     CK(reduce_partials(h->partials, zb, 1, h->scal + 6, h->st));
                     double hs[7];
                     CK(cudaMemcpyAsync(hs, h->scal, sizeof hs, cudaMemcpyDeviceToHost, h->st));
                     CK(cudaStreamSynchronize(h->st));
-                    h->launches += 5;
+                    h->launches += 3 + xy_launches(h);
                     double mu_n = 0.0;
                     for (int i = 0; i < 6; ++i)
                         if (i != 2) mu_n += hs[i] * hs[i];
@@ -1367,9 +1384,8 @@ int adjoint_sweep(evp_handle *h, const AdjLayout &L, const double *gbar, double 
                     dEk[0] = (aa_ * (-hs[0]) - bb_ * (-hs[1])) / det;
                     dEk[1] = (-bb_ * (-hs[0]) + aa_ * (-hs[1])) / det;
                     for (int i = 3; i < 6; ++i) dEk[i] = -hs[i] / (2.0 * mu0);
-                    CK(fft_y<TA>(h->spec, n, 6, 1, h->st));
-                    CK(fft_x_c2r<TA>(h->spec, eb, n, 6, (TA)(1.0 / (double)N3), dEk, h->st));
-                    h->launches += 2;
+                    CK(fft_xy_c2r<TA>(h->spec, eb, n, 6, (TA)(1.0 / (double)N3), dEk, h->st));
+                    h->launches += xy_launches(h);
                 }
                 if (it > max_iter)
                     return fail(h, EVP_ERR_FIXEDPOINT, "adjoint fixed point not converged at increment %d (err %.3e)", t,
@@ -1476,12 +1492,10 @@ int evp_stress_residual(int n, int precision, const void *sig_dev, void *spec_de
     double *part = (double *)scratch_dev;
     cudaError_t e;
     if (dbl) {
-        e = fft_x_r2c<double>((const double *)sig_dev, spec_dev, n, 6, s);
-        if (e == cudaSuccess) e = fft_y<double>(spec_dev, n, 6, 0, s);
+        e = fft_xy_r2c<double>((const double *)sig_dev, spec_dev, n, 6, s);
         if (e == cudaSuccess) e = fft_z<double>(spec_dev, n, 6, Z_FWD_RESID, 0, 0, part, out_dev, s);
     } else {
-        e = fft_x_r2c<float>((const float *)sig_dev, spec_dev, n, 6, s);
-        if (e == cudaSuccess) e = fft_y<float>(spec_dev, n, 6, 0, s);
+        e = fft_xy_r2c<float>((const float *)sig_dev, spec_dev, n, 6, s);
         if (e == cudaSuccess) e = fft_z<float>(spec_dev, n, 6, Z_FWD_RESID, 0, 0, part, out_dev, s);
     }
     if (e == cudaSuccess) e = reduce_partials(part, fft_z_blocks(n, dbl), 1, out_dev + 6, s);

@@ -5,7 +5,10 @@
 //   z pass : complex, the six stress components of a [kx tile] x z slab of one ky; the forward
 //            transform, the equilibrium residual, the Green-operator contraction and the inverse
 //            transform run on the slab while it sits in shared memory
+//   y pass : inverse
 //   x pass : half spectrum -> real, fused with the strain update eps += field/N^3 + dE
+// Where a (field, z) plane fits in shared memory next to two others, the x and y passes run as one launch
+// per direction over whole planes (k_fft_xy_r2c, k_fft_xy_c2r), so an iteration crosses HBM three times.
 // Spectra are [field][z|kz][ky][kx] with kx = 0..N/2 (row length N/2+1).
 //
 // Line transforms: Stockham auto-sort with register butterflies. N = R1 * R2 with R1 = min(N, 16)
@@ -403,6 +406,222 @@ k_fft_y(typename CT<T>::type *__restrict__ spec, const int *__restrict__ skip) {
         for (int y = threadIdx.x; y < N; y += blockDim.x) base[(long)y * Hx + N / 2] = buf[TX * LS + pad16(y)];
 }
 
+// ---------------------------------------------------------------------------------------------
+// x and y passes fused: CTA = one (field, z) plane held in shared memory. The x transform runs on
+// N/2 packed row pairs (line p = rows 2p, 2p+1, as in the x pass); the half-spectrum rows then replace
+// their line in place (row 2p at slots 0..N/2 of line p, row 2p+1 at slots N/2+1..N+1), and the y
+// transform runs down the N/2+1 columns of that row-major plane. Every value goes through the same
+// operations, in the same order, as in the separate x and y passes, so the spectra are bitwise the same;
+// the plane crosses HBM once instead of twice. Used where the plane fits (xy_fused).
+// ---------------------------------------------------------------------------------------------
+// One thread per pass-1 item of the N/2 row-pair lines (x) and of the N/2 regular columns (y); the Nyquist
+// column's few pass-1 items run on lanes of warp 0 (col_fft).
+template <int N> __host__ __device__ constexpr int xy_threads() {
+    return (((N / 2) * (N / Shape<N>::R1) + 31) / 32) * 32;
+}
+template <typename T, int N> __host__ __device__ constexpr size_t smem_xy() {
+    return sizeof(typename CT<T>::type) * (N + (size_t)(N / 2) * Shape<N>::LS);
+}
+// The plane fits next to two others on one SM (FP32 up to N = 128, FP64 up to N = 64), the row pair of the
+// half spectrum fits in a padded line (2 (N/2+1) <= LS), and both passes are two-radix Stockham passes.
+template <typename T, int N> __host__ __device__ constexpr bool xy_fused() {
+    return N >= 32 && Shape<N>::R2 > 1 && 2 * (N / 2 + 1) <= Shape<N>::LS && smem_xy<T, N>() <= 72 * 1024;
+}
+template <typename T, int N> __host__ __device__ constexpr int xy_ctas() {
+    return sizeof(T) == 4 ? (N >= 128 ? 3 : N == 64 ? 8 : 1) : 1;
+}
+
+// Slot of half-spectrum row y, column kx in the row-major plane (rows 2p and 2p+1 share line p).
+template <int N> __device__ __forceinline__ int xy_at(int y, int kx) {
+    return (y >> 1) * Shape<N>::LS + (y & 1) * (N / 2 + 1) + kx;
+}
+
+// The y transform of the N/2+1 columns of a row-major plane: the two passes of block_fft with the same
+// items, operands and twiddles, addressed through xy_at. Items run kx-fastest, so a warp reads and writes
+// consecutive slots. Needs blockDim.x >= (N/2) N/R1. Starts after and ends with a barrier.
+template <int N, bool INV, typename C> __device__ void col_fft(C *buf, const C *tw) {
+    constexpr int R1 = Shape<N>::R1, R2 = Shape<N>::R2, M1 = N / R1, Hx = N / 2 + 1, LS = Shape<N>::LS;
+    static_assert(M1 % 2 == 0 && R1 % 2 == 0 && M1 <= 32, "row pairs");
+    // pass 1: item (kx, j < M1) reads rows j + M1 r (line (j >> 1) + r M1 / 2, half j & 1) and writes rows R1 j + r
+    // (line R1 j / 2 + r / 2, half r & 1); in a column every read comes before any write
+    auto pass1 = [&](int j, int kx, C (&v)[R1], bool write) {
+        if (!write) {
+            const C *src = buf + xy_at<N>(j, kx);
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[r] = src[r * (M1 / 2) * LS];
+        } else {
+            dft_reg<R1, INV>(v);
+            C *dst = buf + (R1 / 2) * j * LS + kx;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) dst[(r >> 1) * LS + (r & 1) * Hx] = v[r];
+        }
+    };
+    {
+        const int t = threadIdx.x;
+        const bool on = t < (N / 2) * M1;   // the regular columns kx < N/2
+        const int j = t / (N / 2), kx = t % (N / 2);
+        C v[R1];
+        if (on) pass1(j, kx, v, false);
+        __syncthreads();
+        if (on) pass1(j, kx, v, true);
+        if (t < M1) {   // the Nyquist column kx = N/2, lanes 0..M1-1 of warp 0 (no other item touches it)
+            pass1(t, N / 2, v, false);
+            __syncwarp((1u << M1) - 1u);
+            pass1(t, N / 2, v, true);
+        }
+        __syncthreads();
+    }
+    // pass 2: item (kx, j < R1) reads and writes rows j + R1 r, twiddles tw[16 r + j]
+    for (int t = threadIdx.x; t < Hx * R1; t += blockDim.x) {
+        const int j = t / Hx, kx = t - j * Hx;
+        C *line = buf + xy_at<N>(j, kx);   // rows j + 16 r: line (j >> 1) + 8 r, same half
+        C u[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            C a = line[r * (R1 / 2) * LS];
+            if (r > 0) {
+                C w = tw[16 * r + j];
+                if (INV) w.y = -w.y;
+                a = cmul(a, w);
+            }
+            u[r] = a;
+        }
+        dft_reg<R2, INV>(u);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) line[r * (R1 / 2) * LS] = u[r];
+    }
+    __syncthreads();
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(xy_threads<N>(), xy_ctas<T, N>())
+k_fft_xy_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out, const int *__restrict__ skip) {
+    pdl_wait();
+    pdl_trigger();
+    if (skip != nullptr && *skip) return;   // the fixed point has converged
+    using C = typename CT<T>::type;
+    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, KU = (Hx + 31) / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *buf = tw + N;
+    const T *src = in + (long)blockIdx.x * N * N;   // plane = field * N + z
+    C *dst = out + (long)blockIdx.x * N * Hx;
+    load_tw(tw, N);
+    for (int t = threadIdx.x; t < NP * N; t += blockDim.x) {
+        const int p = t / N, j = t - p * N;
+        T *slot = reinterpret_cast<T *>(buf + p * LS + pad16(j));
+        cp_async<sizeof(T)>(slot, src + (2 * p) * N + j);
+        cp_async<sizeof(T)>(slot + 1, src + (2 * p + 1) * N + j);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    block_fft<N, false, 1>(buf, NP, tw);
+    {   // unpack one line per warp: read the line's values, then write its two half-spectrum rows in place
+        const int lane = threadIdx.x & 31;
+        const T h = (T)0.5;
+        for (int p = threadIdx.x >> 5; p < NP; p += blockDim.x >> 5) {
+            C *line = buf + p * LS;
+            C a[KU], b[KU];
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const int k = lane + 32 * u;
+                if (k < Hx) {
+                    const C zk = line[pad16(k & (N - 1))];
+                    const C zc = cconj(line[pad16((N - k) & (N - 1))]);
+                    a[u] = cmk<C>(h * (zk.x + zc.x), h * (zk.y + zc.y));
+                    b[u] = cmk<C>(h * (zk.y - zc.y), -h * (zk.x - zc.x));   // (zk - zc) / 2i
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const int k = lane + 32 * u;
+                if (k < Hx) {
+                    line[k] = a[u];
+                    line[Hx + k] = b[u];
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    col_fft<N, false>(buf, tw);
+    for (int t = threadIdx.x; t < N * Hx; t += blockDim.x) {
+        const int ky = t / Hx, kx = t - ky * Hx;
+        dst[t] = buf[xy_at<N>(ky, kx)];
+    }
+}
+
+// The inverse: y transform down the columns, the row pairs packed as one complex line (A + iB), the x
+// transform, and the strain update of the x pass's epilogue.
+template <typename T, int N>
+__global__ void __launch_bounds__(xy_threads<N>(), xy_ctas<T, N>())
+k_fft_xy_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out, T scale, int has_add, T a0, T a1, T a2,
+             T a3, T a4, T a5, const T *__restrict__ base, const int *__restrict__ skip) {
+    pdl_wait();
+    pdl_trigger();
+    if (skip != nullptr && *skip) return;   // the fixed point has converged
+    using C = typename CT<T>::type;
+    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, KV = N / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *buf = tw + N;
+    const C *src = spec + (long)blockIdx.x * N * Hx;
+    for (int t = threadIdx.x; t < N * Hx; t += blockDim.x) {
+        const int ky = t / Hx, kx = t - ky * Hx;
+        cp_async<sizeof(C)>(buf + xy_at<N>(ky, kx), src + t);
+    }
+    load_tw(tw, N);
+    cp_async_wait_all();
+    __syncthreads();
+    col_fft<N, true>(buf, tw);
+    {   // pack one line per warp: read rows 2p and 2p+1, then write A + iB over them
+        const int lane = threadIdx.x & 31;
+        for (int p = threadIdx.x >> 5; p < NP; p += blockDim.x >> 5) {
+            C *line = buf + p * LS;
+            C zv[KV];
+#pragma unroll
+            for (int u = 0; u < KV; ++u) {
+                const int k = lane + 32 * u;
+                C A, B;
+                if (k <= (N >> 1)) {
+                    A = line[k];
+                    B = line[Hx + k];
+                } else {
+                    A = cconj(line[N - k]);
+                    B = cconj(line[Hx + N - k]);
+                }
+                zv[u] = cmk<C>(A.x - B.y, A.y + B.x);   // A + iB
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < KV; ++u) line[pad16(lane + 32 * u)] = zv[u];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    block_fft<N, true, 1>(buf, NP, tw);
+    const long r0 = (long)blockIdx.x * N;   // first row: (field * N + z) * N
+    T add = (T)0;
+    if (has_add) {
+        const int f = (int)(blockIdx.x / N);
+        add = f == 0 ? a0 : f == 1 ? a1 : f == 2 ? a2 : f == 3 ? a3 : f == 4 ? a4 : a5;
+    }
+    const T *bsrc = base ? base : out;
+    for (int t = threadIdx.x; t < NP * N; t += blockDim.x) {
+        const int p = t / N, j = t - p * N;
+        const C z = buf[p * LS + pad16(j)];
+        const long o0 = (r0 + 2 * p) * N + j, o1 = o0 + N;
+        if (has_add) {
+            out[o0] = bsrc[o0] + (z.x * scale + add);
+            out[o1] = bsrc[o1] + (z.y * scale + add);
+        } else {
+            out[o0] = z.x;
+            out[o1] = z.y;
+        }
+    }
+}
+
 // Green operator of the isotropic reference medium applied to one spectral stress (Mandel):
 // eps_kh = (n_h v_k + n_k v_h)/(2 mu0) - c n_k n_h (n.v), v = sigma.n, n = xi/|xi|,
 // c = (lam0+mu0)/(mu0 (lam0+2 mu0)). At frequencies with a Nyquist component the compliance of
@@ -666,6 +885,43 @@ template <typename T, int N> cudaError_t y_n(void *spec, int nfields, int invers
     return launch_k(skip != nullptr, k_fft_y<T, N, false>, dim3(blocks), dim3(y_threads<N, T>()), sm, s, (C *)spec, skip);
 }
 
+// x and y passes of the forward transform: one fused launch where the plane fits (xy_fused), else the two passes
+template <typename T, int N> cudaError_t xy_r2c_n(const T *in, void *spec, int nfields, cudaStream_t s, const int *skip) {
+    if constexpr (xy_fused<T, N>()) {
+        using C = typename CT<T>::type;
+        constexpr size_t sm = smem_xy<T, N>();
+        cudaError_t e = allow_smem(k_fft_xy_r2c<T, N>, sm);
+        if (e != cudaSuccess) return e;
+        return launch_k(skip != nullptr, k_fft_xy_r2c<T, N>, dim3(nfields * N), dim3(xy_threads<N>()), sm, s, in,
+                        (C *)spec, skip);
+    } else {
+        cudaError_t e = x_r2c_n<T, N>(in, spec, nfields, s, skip);
+        if (e != cudaSuccess) return e;
+        return y_n<T, N>(spec, nfields, 0, s, skip);
+    }
+}
+
+template <typename T, int N>
+cudaError_t xy_c2r_n(const void *spec, T *out, int nfields, T scale, const double *add6, cudaStream_t s, const T *base,
+                     const int *skip) {
+    if constexpr (xy_fused<T, N>()) {
+        using C = typename CT<T>::type;
+        constexpr size_t sm = smem_xy<T, N>();
+        cudaError_t e = allow_smem(k_fft_xy_c2r<T, N>, sm);
+        if (e != cudaSuccess) return e;
+        T a[6] = {0, 0, 0, 0, 0, 0};   // rounded to the field precision here, as in the x pass
+        if (add6)
+            for (int i = 0; i < 6; ++i) a[i] = (T)add6[i];
+        const int has_add = add6 != nullptr;
+        return launch_k(skip != nullptr, k_fft_xy_c2r<T, N>, dim3(nfields * N), dim3(xy_threads<N>()), sm, s,
+                        (const C *)spec, out, scale, has_add, a[0], a[1], a[2], a[3], a[4], a[5], base, skip);
+    } else {
+        cudaError_t e = y_n<T, N>(const_cast<void *>(spec), nfields, 1, s, skip);
+        if (e != cudaSuccess) return e;
+        return x_c2r_n<T, N>(spec, out, nfields, scale, add6, s, base, skip);
+    }
+}
+
 template <typename T, int N>
 cudaError_t z_n(void *spec, int nfields, int mode, double lam0, double mu0, double *partials, double *mean6,
                 cudaStream_t s, const int *skip, const ZCtl *zcp) {
@@ -701,6 +957,26 @@ int fft_z_blocks(int n, int is_double) {
     return n * ((n / 2) / TX);
 }
 
+int fft_xy_fused(int n, int is_double) {
+    if (is_double) {
+        EVP_DISPATCH(n, (int)(xy_fused<double, NN>()))
+    }
+    EVP_DISPATCH(n, (int)(xy_fused<float, NN>()))
+}
+
+template <typename T>
+cudaError_t fft_xy_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s, const int *skip) {
+    EVP_DISPATCH(n, (xy_r2c_n<T, NN>(in, spec, nfields, s, skip)))
+}
+
+template <typename T>
+cudaError_t fft_xy_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6, cudaStream_t s,
+                       const T *base, const int *skip) {
+    // the same contract as the x pass (whole rows in 16-byte chunks where the passes run separately)
+    if (((uintptr_t)spec | (uintptr_t)out | (uintptr_t)base) & 15) return cudaErrorInvalidValue;
+    EVP_DISPATCH(n, (xy_c2r_n<T, NN>(spec, out, nfields, scale, add6, s, base, skip)))
+}
+
 template <typename T>
 cudaError_t fft_x_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s, const int *skip) {
     EVP_DISPATCH(n, (x_r2c_n<T, NN>(in, spec, nfields, s, skip)))
@@ -731,6 +1007,9 @@ cudaError_t fft_z(void *spec, int n, int nfields, int mode, double lam0, double 
     template cudaError_t fft_x_c2r<T>(const void *, T *, int, int, T, const double *, cudaStream_t, const T *,     \
                                       const int *);                                                                \
     template cudaError_t fft_y<T>(void *, int, int, int, cudaStream_t, const int *);                               \
+    template cudaError_t fft_xy_r2c<T>(const T *, void *, int, int, cudaStream_t, const int *);                    \
+    template cudaError_t fft_xy_c2r<T>(const void *, T *, int, int, T, const double *, cudaStream_t, const T *,    \
+                                       const int *);                                                               \
     template cudaError_t fft_z<T>(void *, int, int, int, double, double, double *, double *, cudaStream_t,         \
                                   const int *, const ZCtl *);
 EVP_FFT_INST(float)

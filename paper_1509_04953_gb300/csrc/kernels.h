@@ -56,6 +56,15 @@ template <typename T>
 cudaError_t fft_x_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6,
                       cudaStream_t s, const T *base = nullptr, const int *skip = nullptr);
 int fft_z_blocks(int n, int is_double);
+// The x and y passes together: forward = fft_x_r2c then the forward y pass, inverse = the inverse y pass then
+// fft_x_c2r (same contract), with bitwise the same results. Where fft_xy_fused(n, is_double) is 1 each is one
+// launch over (field, z) planes held in shared memory; otherwise the two passes are launched.
+int fft_xy_fused(int n, int is_double);
+template <typename T>
+cudaError_t fft_xy_r2c(const T *in, void *spec, int n, int nfields, cudaStream_t s, const int *skip = nullptr);
+template <typename T>
+cudaError_t fft_xy_c2r(const void *spec, T *out, int n, int nfields, T scale, const double *add6,
+                       cudaStream_t s, const T *base = nullptr, const int *skip = nullptr);
 
 // ---- newton.cu ----
 // solve_fp64: 1 -> the 6x6 Newton system is solved in FP64 even when TA = float.

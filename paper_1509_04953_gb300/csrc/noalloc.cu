@@ -94,12 +94,10 @@ extern "C" int evp_stress_residual_noalloc(int n, int precision, const void *sig
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e;
     if (dbl) {
-        e = evp::fft_x_r2c<double>((const double *)sig_dev, spec_dev, n, 6, s);
-        if (e == cudaSuccess) e = evp::fft_y<double>(spec_dev, n, 6, 0, s);
+        e = evp::fft_xy_r2c<double>((const double *)sig_dev, spec_dev, n, 6, s);
         if (e == cudaSuccess) e = evp::fft_z<double>(spec_dev, n, 6, evp::Z_FWD_RESID, 0, 0, part, out_dev, s);
     } else {
-        e = evp::fft_x_r2c<float>((const float *)sig_dev, spec_dev, n, 6, s);
-        if (e == cudaSuccess) e = evp::fft_y<float>(spec_dev, n, 6, 0, s);
+        e = evp::fft_xy_r2c<float>((const float *)sig_dev, spec_dev, n, 6, s);
         if (e == cudaSuccess) e = evp::fft_z<float>(spec_dev, n, 6, evp::Z_FWD_RESID, 0, 0, part, out_dev, s);
     }
     if (e == cudaSuccess) e = evp::reduce_partials(part, nparts, 1, out_dev + 6, s);

@@ -333,7 +333,7 @@ class Solver:
         return grad
 
     # ---- instrumentation ----
-    KERNEL_CLASSES = ("newton", "fft_x_r2c", "fft_y_fwd", "fft_z_gamma", "fft_y_inv", "fft_x_c2r_update", "reduce",
+    KERNEL_CLASSES = ("newton", "fft_xy_r2c", "fft_y_fwd", "fft_z_gamma", "fft_y_inv", "fft_xy_c2r_update", "reduce",
                       "predictor", "state_update", "nucleate", "pf_step", "pf_soften", "pf_stats")
 
     def set_profiling(self, on=True):

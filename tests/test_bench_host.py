@@ -65,10 +65,10 @@ def test_fft_pass_bytes_follow_the_half_spectrum():
     import bench
     n, T = 128, 4
     H = (n // 2 + 1) / n
-    assert bench.hbm_bytes_per_voxel("fft_x_r2c", n, T) == pytest.approx((6 + 12 * H) * T)
+    assert bench.hbm_bytes_per_voxel("fft_xy_r2c", n, T) == pytest.approx((6 + 12 * H) * T)
     for k in ("fft_y_fwd", "fft_z_gamma", "fft_y_inv"):
         assert bench.hbm_bytes_per_voxel(k, n, T) == pytest.approx(24 * H * T)
-    assert bench.hbm_bytes_per_voxel("fft_x_c2r_update", n, T) == pytest.approx((12 * H + 12) * T)
+    assert bench.hbm_bytes_per_voxel("fft_xy_c2r_update", n, T) == pytest.approx((12 * H + 12) * T)
     m = bench.memory_kernels({"fft_y_fwd": (2.0, 100)}, types.SimpleNamespace(n=n), n ** 3, "mixed",
                              {"hbm_gbs": 5000.0})
     gbs = 24 * H * T * n ** 3 / 20e-6 / 1e9
