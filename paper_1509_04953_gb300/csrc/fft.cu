@@ -137,12 +137,79 @@ template <int N, int TX> __device__ __forceinline__ void slab_item(int r, int &z
     }
 }
 
+// The two passes of block_fft (R2 > 1), also called on their own by the z pass.
+// pass 1: radix R1, Ns = 1: item (l, j < M1) reads slots j + M1 r and writes j R1 + r, so
+// every read completes before any write (held in registers across a barrier). With j < M1 and M1 | 16
+// the padded slots are pad16(j + M1 r) = j + pad16(M1 r) and pad16(16 j + r) = 17 j + r (r < 16): one base
+// address per item and compile-time offsets. Ends with a barrier.
+template <int N, bool INV, int MAXIT, typename C> __device__ void bfft_pass1(C *buf, int nlines) {
+    constexpr int R1 = Shape<N>::R1, LS = Shape<N>::LS;
+    constexpr int M1 = N / R1;
+    static_assert(16 % M1 == 0 || M1 % 16 == 0, "pass-1 stride");
+    const int items = nlines * M1;
+    C v[MAXIT][R1];
+#pragma unroll
+    for (int it = 0; it < MAXIT; ++it) {
+        const int t = threadIdx.x + it * blockDim.x;
+        if (t < items) {
+            int l, j;
+            pass1_item<N>(t, nlines, l, j);
+            const C *src = buf + l * LS + (M1 <= 16 ? j : pad16(j));
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[it][r] = src[M1 <= 16 ? pad16(r * M1) : r * (M1 + M1 / 16)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < MAXIT; ++it) {
+        const int t = threadIdx.x + it * blockDim.x;
+        if (t < items) {
+            int l, j;
+            pass1_item<N>(t, nlines, l, j);
+            dft_reg<R1, INV>(v[it]);
+            C *dst = buf + l * LS + 17 * j;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) dst[r] = v[it][r];
+        }
+    }
+    __syncthreads();
+}
+
+// pass 2: radix R2, Ns = R1 = 16: item (l, j < 16) reads and writes slots j + 16 r only, which are
+// pad16(j + 16 r) = j + 17 r
+// Every CTA has a multiple of 16 threads, so a thread's items share one j = threadIdx.x mod 16 and its
+// twiddles tw[16 r + j] = exp(-2 pi i r j / N) are loaded once, into registers. Ends with a barrier.
+template <int N, bool INV, typename C> __device__ void bfft_pass2(C *buf, int nlines, const C *tw) {
+    constexpr int R2 = Shape<N>::R2, LS = Shape<N>::LS;
+    const int jt = threadIdx.x & 15;
+    C wr[R2];
+#pragma unroll
+    for (int r = 1; r < R2; ++r) {
+        wr[r] = tw[16 * r + jt];   // r-major: a half-warp reads 16 in a row
+        if (INV) wr[r].y = -wr[r].y;
+    }
+    for (int t = threadIdx.x; t < nlines * 16; t += blockDim.x) {
+        const int l = t >> 4;
+        C *line = buf + l * LS + jt;
+        C u[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            C a = line[17 * r];
+            if (r > 0) a = cmul(a, wr[r]);
+            u[r] = a;
+        }
+        dft_reg<R2, INV>(u);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) line[17 * r] = u[r];
+    }
+    __syncthreads();
+}
+
 // In-place transform of nlines padded lines (line l at buf + l*LS). tw[16 r + j] = exp(-2 pi i r j / N)
 // (see load_tw),
 // m < N. Starts after and ends with a barrier. MAXIT >= ceil(nlines * (N/R1) / blockDim).
 template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *buf, int nlines, const C *tw) {
     constexpr int R1 = Shape<N>::R1, R2 = Shape<N>::R2, LS = Shape<N>::LS;
-    constexpr int M1 = N / R1;
     if constexpr (R2 == 1) {   // a single radix-N pass; every line is owned by one thread
         for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
             C v[R1];
@@ -154,64 +221,8 @@ template <int N, bool INV, int MAXIT, typename C> __device__ void block_fft(C *b
         }
         __syncthreads();
     } else {
-        // pass 1: radix R1, Ns = 1: item (l, j < M1) reads slots j + M1 r and writes j R1 + r, so
-        // every read completes before any write (held in registers across a barrier). With j < M1 and M1 | 16
-        // the padded slots are pad16(j + M1 r) = j + pad16(M1 r) and pad16(16 j + r) = 17 j + r (r < 16): one base
-        // address per item and compile-time offsets.
-        static_assert(16 % M1 == 0 || M1 % 16 == 0, "pass-1 stride");
-        const int items = nlines * M1;
-        C v[MAXIT][R1];
-#pragma unroll
-        for (int it = 0; it < MAXIT; ++it) {
-            const int t = threadIdx.x + it * blockDim.x;
-            if (t < items) {
-                int l, j;
-                pass1_item<N>(t, nlines, l, j);
-                const C *src = buf + l * LS + (M1 <= 16 ? j : pad16(j));
-#pragma unroll
-                for (int r = 0; r < R1; ++r) v[it][r] = src[M1 <= 16 ? pad16(r * M1) : r * (M1 + M1 / 16)];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < MAXIT; ++it) {
-            const int t = threadIdx.x + it * blockDim.x;
-            if (t < items) {
-                int l, j;
-                pass1_item<N>(t, nlines, l, j);
-                dft_reg<R1, INV>(v[it]);
-                C *dst = buf + l * LS + 17 * j;
-#pragma unroll
-                for (int r = 0; r < R1; ++r) dst[r] = v[it][r];
-            }
-        }
-        __syncthreads();
-        // pass 2: radix R2, Ns = R1 = 16: item (l, j < 16) reads and writes slots j + 16 r only, which are
-        // pad16(j + 16 r) = j + 17 r
-        // Every CTA has a multiple of 16 threads, so a thread's items share one j = threadIdx.x mod 16 and its
-        // twiddles tw[16 r + j] = exp(-2 pi i r j / N) are loaded once, into registers.
-        const int jt = threadIdx.x & 15;
-        C wr[R2];
-#pragma unroll
-        for (int r = 1; r < R2; ++r) {
-            wr[r] = tw[16 * r + jt];   // r-major: a half-warp reads 16 in a row
-            if (INV) wr[r].y = -wr[r].y;
-        }
-        for (int t = threadIdx.x; t < nlines * 16; t += blockDim.x) {
-            const int l = t >> 4;
-            C *line = buf + l * LS + jt;
-            C u[R2];
-#pragma unroll
-            for (int r = 0; r < R2; ++r) {
-                C a = line[17 * r];
-                if (r > 0) a = cmul(a, wr[r]);
-                u[r] = a;
-            }
-            dft_reg<R2, INV>(u);
-#pragma unroll
-            for (int r = 0; r < R2; ++r) line[17 * r] = u[r];
-        }
-        __syncthreads();
+        bfft_pass1<N, INV, MAXIT>(buf, nlines);
+        bfft_pass2<N, INV>(buf, nlines, tw);
     }
 }
 
@@ -415,7 +426,7 @@ k_fft_y(typename CT<T>::type *__restrict__ spec, const int *__restrict__ skip) {
 // the plane crosses HBM once instead of twice. Used where the plane fits (xy_fused).
 // ---------------------------------------------------------------------------------------------
 // One thread per pass-1 item of the N/2 row-pair lines (x) and of the N/2 regular columns (y); the Nyquist
-// column's few pass-1 items run on lanes of warp 0 (col_fft).
+// column's few pass-1 items run on lanes of warp 0 (col_pass1).
 template <int N> __host__ __device__ constexpr int xy_threads() {
     return (((N / 2) * (N / Shape<N>::R1) + 31) / 32) * 32;
 }
@@ -436,45 +447,78 @@ template <int N> __device__ __forceinline__ int xy_at(int y, int kx) {
     return (y >> 1) * Shape<N>::LS + (y & 1) * (N / 2 + 1) + kx;
 }
 
-// The y transform of the N/2+1 columns of a row-major plane: the two passes of block_fft with the same
-// items, operands and twiddles, addressed through xy_at. Items run kx-fastest, so a warp reads and writes
-// consecutive slots. Needs blockDim.x >= (N/2) N/R1. Starts after and ends with a barrier.
-template <int N, bool INV, typename C> __device__ void col_fft(C *buf, const C *tw) {
-    constexpr int R1 = Shape<N>::R1, R2 = Shape<N>::R2, M1 = N / R1, Hx = N / 2 + 1, LS = Shape<N>::LS;
+// The passes of the plane transforms, one pass-1 item per thread (blockDim.x >= items). Each has the items,
+// operands and twiddles of block_fft's passes (x: lines of the packed row pairs) or of the y pass (columns,
+// addressed through xy_at, kx-fastest so a warp touches consecutive slots); only where the values come from
+// or go to differs: the first pass of the forward kernel reads HBM straight into registers, and so do the
+// inverse kernel's first pass and the forward kernel's last pass store, so none of them round-trips through
+// shared memory.
+
+// x pass 1 (bfft_pass1's items) with element e of line l read through ld(l, e): no in-place hazard, so no barrier
+// between reads and writes. Ends with a barrier.
+template <int N, bool INV, typename C, typename Ld> __device__ void x_pass1_ld(C *buf, int nlines, Ld ld) {
+    constexpr int R1 = Shape<N>::R1, LS = Shape<N>::LS, M1 = N / R1;
+    static_assert(M1 <= 16 && 16 % M1 == 0, "pass-1 stride");
+    const int t = threadIdx.x;
+    if (t < nlines * M1) {
+        int l, j;
+        pass1_item<N>(t, nlines, l, j);
+        C v[R1];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[r] = ld(l, j + M1 * r);
+        dft_reg<R1, INV>(v);
+        C *dst = buf + l * LS + 17 * j;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) dst[r] = v[r];
+    }
+    __syncthreads();
+}
+
+// y pass 1: item (kx, j < M1) takes rows j + M1 r of column kx, from ld(y, kx) or from the plane, and writes
+// rows R1 j + r (line R1 j / 2 + r / 2, half r & 1). The regular columns kx < N/2 take one item per thread; the
+// Nyquist column's M1 items run on lanes 0..M1-1 of warp 0 afterwards (no other item touches that column).
+// Ends with a barrier.
+template <int N, bool INV, bool FROM_BUF, typename C, typename Ld> __device__ void col_pass1(C *buf, Ld ld) {
+    constexpr int R1 = Shape<N>::R1, M1 = N / R1, Hx = N / 2 + 1, LS = Shape<N>::LS;
     static_assert(M1 % 2 == 0 && R1 % 2 == 0 && M1 <= 32, "row pairs");
-    // pass 1: item (kx, j < M1) reads rows j + M1 r (line (j >> 1) + r M1 / 2, half j & 1) and writes rows R1 j + r
-    // (line R1 j / 2 + r / 2, half r & 1); in a column every read comes before any write
-    auto pass1 = [&](int j, int kx, C (&v)[R1], bool write) {
-        if (!write) {
-            const C *src = buf + xy_at<N>(j, kx);
+    auto load = [&](int j, int kx, C (&v)[R1]) {
+        if constexpr (FROM_BUF) {
+            const C *src = buf + xy_at<N>(j, kx);   // rows j + M1 r: line (j >> 1) + r M1 / 2, half j & 1
 #pragma unroll
             for (int r = 0; r < R1; ++r) v[r] = src[r * (M1 / 2) * LS];
         } else {
-            dft_reg<R1, INV>(v);
-            C *dst = buf + (R1 / 2) * j * LS + kx;
 #pragma unroll
-            for (int r = 0; r < R1; ++r) dst[(r >> 1) * LS + (r & 1) * Hx] = v[r];
+            for (int r = 0; r < R1; ++r) v[r] = ld(j + M1 * r, kx);
         }
     };
-    {
-        const int t = threadIdx.x;
-        const bool on = t < (N / 2) * M1;   // the regular columns kx < N/2
-        const int j = t / (N / 2), kx = t % (N / 2);
-        C v[R1];
-        if (on) pass1(j, kx, v, false);
-        __syncthreads();
-        if (on) pass1(j, kx, v, true);
-        if (t < M1) {   // the Nyquist column kx = N/2, lanes 0..M1-1 of warp 0 (no other item touches it)
-            pass1(t, N / 2, v, false);
-            __syncwarp((1u << M1) - 1u);
-            pass1(t, N / 2, v, true);
-        }
-        __syncthreads();
+    auto transform = [&](int j, int kx, C (&v)[R1]) {
+        dft_reg<R1, INV>(v);
+        C *dst = buf + (R1 / 2) * j * LS + kx;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) dst[(r >> 1) * LS + (r & 1) * Hx] = v[r];
+    };
+    const int t = threadIdx.x;
+    const bool on = t < (N / 2) * M1;
+    const int j = t / (N / 2), kx = t % (N / 2);
+    C v[R1];
+    if (on) load(j, kx, v);
+    if constexpr (FROM_BUF) __syncthreads();
+    if (on) transform(j, kx, v);
+    if (t < M1) {
+        load(t, N / 2, v);
+        __syncwarp((1u << M1) - 1u);
+        transform(t, N / 2, v);
     }
-    // pass 2: item (kx, j < R1) reads and writes rows j + R1 r, twiddles tw[16 r + j]
+    __syncthreads();
+}
+
+// y pass 2: item (kx, j < 16) transforms rows j + 16 r (line (j >> 1) + 8 r, half j & 1) and hands its outputs
+// (row j + 16 r in u[r]) to st(j, kx, slot of row j, u). Ends with a barrier.
+template <int N, bool INV, typename C, typename St> __device__ void col_pass2(C *buf, const C *tw, St st) {
+    constexpr int R1 = Shape<N>::R1, R2 = Shape<N>::R2, Hx = N / 2 + 1, LS = Shape<N>::LS;
     for (int t = threadIdx.x; t < Hx * R1; t += blockDim.x) {
         const int j = t / Hx, kx = t - j * Hx;
-        C *line = buf + xy_at<N>(j, kx);   // rows j + 16 r: line (j >> 1) + 8 r, same half
+        C *line = buf + xy_at<N>(j, kx);
         C u[R2];
 #pragma unroll
         for (int r = 0; r < R2; ++r) {
@@ -487,8 +531,7 @@ template <int N, bool INV, typename C> __device__ void col_fft(C *buf, const C *
             u[r] = a;
         }
         dft_reg<R2, INV>(u);
-#pragma unroll
-        for (int r = 0; r < R2; ++r) line[r * (R1 / 2) * LS] = u[r];
+        st(j, kx, line, u);
     }
     __syncthreads();
 }
@@ -500,22 +543,16 @@ k_fft_xy_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out, c
     pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
-    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, KU = (Hx + 31) / 32;
+    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, KU = (Hx + 31) / 32, R2 = Shape<N>::R2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *buf = tw + N;
     const T *src = in + (long)blockIdx.x * N * N;   // plane = field * N + z
     C *dst = out + (long)blockIdx.x * N * Hx;
     load_tw(tw, N);
-    for (int t = threadIdx.x; t < NP * N; t += blockDim.x) {
-        const int p = t / N, j = t - p * N;
-        T *slot = reinterpret_cast<T *>(buf + p * LS + pad16(j));
-        cp_async<sizeof(T)>(slot, src + (2 * p) * N + j);
-        cp_async<sizeof(T)>(slot + 1, src + (2 * p + 1) * N + j);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    block_fft<N, false, 1>(buf, NP, tw);
+    // x: line p packs rows 2p and 2p+1 as one complex row; pass 1 reads them from HBM
+    x_pass1_ld<N, false>(buf, NP, [&](int p, int e) { return cmk<C>(src[(2 * p) * N + e], src[(2 * p + 1) * N + e]); });
+    bfft_pass2<N, false>(buf, NP, tw);
     {   // unpack one line per warp: read the line's values, then write its two half-spectrum rows in place
         const int lane = threadIdx.x & 31;
         const T h = (T)0.5;
@@ -545,11 +582,12 @@ k_fft_xy_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out, c
         }
     }
     __syncthreads();
-    col_fft<N, false>(buf, tw);
-    for (int t = threadIdx.x; t < N * Hx; t += blockDim.x) {
-        const int ky = t / Hx, kx = t - ky * Hx;
-        dst[t] = buf[xy_at<N>(ky, kx)];
-    }
+    // y: down the columns of the row-major plane; pass 2 stores rows j + 16 r to HBM
+    col_pass1<N, false, true>(buf, 0);
+    col_pass2<N, false>(buf, tw, [&](int j, int kx, C *, const C (&u)[R2]) {
+#pragma unroll
+        for (int r = 0; r < R2; ++r) dst[(j + 16 * r) * Hx + kx] = u[r];
+    });
 }
 
 // The inverse: y transform down the columns, the row pairs packed as one complex line (A + iB), the x
@@ -562,19 +600,18 @@ k_fft_xy_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
     pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
-    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, KV = N / 32;
+    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, KV = N / 32, R2 = Shape<N>::R2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *buf = tw + N;
     const C *src = spec + (long)blockIdx.x * N * Hx;
-    for (int t = threadIdx.x; t < N * Hx; t += blockDim.x) {
-        const int ky = t / Hx, kx = t - ky * Hx;
-        cp_async<sizeof(C)>(buf + xy_at<N>(ky, kx), src + t);
-    }
     load_tw(tw, N);
-    cp_async_wait_all();
-    __syncthreads();
-    col_fft<N, true>(buf, tw);
+    // y: pass 1 reads the columns from HBM
+    col_pass1<N, true, false>(buf, [&](int y, int kx) { return src[y * Hx + kx]; });
+    col_pass2<N, true>(buf, tw, [](int, int, C *line, const C (&u)[R2]) {
+#pragma unroll
+        for (int r = 0; r < R2; ++r) line[r * 8 * LS] = u[r];
+    });
     {   // pack one line per warp: read rows 2p and 2p+1, then write A + iB over them
         const int lane = threadIdx.x & 31;
         for (int p = threadIdx.x >> 5; p < NP; p += blockDim.x >> 5) {
@@ -600,7 +637,9 @@ k_fft_xy_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
         }
     }
     __syncthreads();
-    block_fft<N, true, 1>(buf, NP, tw);
+    // x, then the strain update row by row (row-contiguous loads of the base strain and stores)
+    bfft_pass1<N, true, 1>(buf, NP);
+    bfft_pass2<N, true>(buf, NP, tw);
     const long r0 = (long)blockIdx.x * N;   // first row: (field * N + z) * N
     T add = (T)0;
     if (has_add) {
@@ -738,30 +777,65 @@ __global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 
                           ((TX == 8 && N % 16 == 0 && LS % 16 == 9) ? NT % 128 == 0 : NT % TX == 0);
     int wz = 0, wxl = 0;
     if constexpr (walk) slab_item<N, TX>((int)threadIdx.x, wz, wxl);
-    if constexpr (walk) {
-        C *sb = buf + wxl * LS + pad16(wz);
-        const C *gb = spec + (long)wz * plane + (long)ky * Hx + kx0 + wxl;
-        for (int f = 0; f < nf; ++f) {
+    // Item it of an HBM-side step over the slab's lines with L items per line: regular lines (field f, column
+    // xl) take it = (f L + i) TX + xl, xl fastest, so 8 lanes touch 8 consecutive columns of one plane; the Nyquist
+    // lines (tile 0) follow. Gives the line, the item's index i < L and the column's first element in HBM.
+    auto hbm_item = [&](int it, int L, int &l, int &i) -> C * {
+        const int nreg = nf * TX * L;
+        if (it < nreg) {
+            const int xl = it % TX, f = it / (TX * L);
+            i = (it / TX) % L;
+            l = f * TX + xl;
+            return spec + f * fstride + (long)ky * Hx + kx0 + xl;
+        }
+        const int q = it - nreg, f = q / L;
+        i = q - f * L;
+        l = nf * TX + f;
+        return spec + f * fstride + (long)ky * Hx + N / 2;
+    };
+    if (mode != Z_INV) {
+        // the forward transform's pass 1 (the whole transform when R2 = 1) straight from HBM: item (line, j < M1)
+        // reads elements j + M1 r and writes slots 16 j + r (slot r when R2 = 1), as bfft_pass1
+        constexpr int R1 = Shape<N>::R1, M1 = N / R1;
+        const int nit = nlines * M1;
+        for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+            int l, j;
+            const C *g = hbm_item(it, M1, l, j);
+            C v[R1];
 #pragma unroll
-            for (int k = 0; k < KZ; ++k)
-                cp_async<sizeof(C)>(sb + f * TX * LS + k * (DZ + DZ / 16), gb + f * fstride + (long)k * DZ * plane);
+            for (int r = 0; r < R1; ++r) v[r] = g[(long)(j + M1 * r) * plane];
+            dft_reg<R1, false>(v);
+            C *dst = buf + l * LS + 17 * j;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) dst[r] = v[r];
         }
+        __syncthreads();
+        if constexpr (Shape<N>::R2 > 1) bfft_pass2<N, false>(buf, nlines, tw);
     } else {
-        for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {   // TX, N powers of two: shifts
-            const int f = t / (TX * N), r = t % (TX * N);
-            int z, xl;
-            slab_item<N, TX>(r, z, xl);
-            cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx0 + xl);
+        if constexpr (walk) {
+            C *sb = buf + wxl * LS + pad16(wz);
+            const C *gb = spec + (long)wz * plane + (long)ky * Hx + kx0 + wxl;
+            for (int f = 0; f < nf; ++f) {
+#pragma unroll
+                for (int k = 0; k < KZ; ++k)
+                    cp_async<sizeof(C)>(sb + f * TX * LS + k * (DZ + DZ / 16), gb + f * fstride + (long)k * DZ * plane);
+            }
+        } else {
+            for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {   // TX, N powers of two: shifts
+                const int f = t / (TX * N), r = t % (TX * N);
+                int z, xl;
+                slab_item<N, TX>(r, z, xl);
+                cp_async<sizeof(C)>(buf + (f * TX + xl) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + kx0 + xl);
+            }
         }
+        if (nyq)
+            for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
+                const int f = t / N, z = t % N;
+                cp_async<sizeof(C)>(buf + (nf * TX + f) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + N / 2);
+            }
+        cp_async_wait_all();
+        __syncthreads();
     }
-    if (nyq)
-        for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
-            const int f = t / N, z = t % N;
-            cp_async<sizeof(C)>(buf + (nf * TX + f) * LS + pad16(z), spec + f * fstride + z * plane + (long)ky * Hx + N / 2);
-        }
-    cp_async_wait_all();
-    __syncthreads();
-    if (mode != Z_INV) block_fft<N, false, MI>(buf, nlines, tw);
     if (mode == Z_FWD_GAMMA_INV || mode == Z_FWD_RESID) {
         const bool apply = mode == Z_FWD_GAMMA_INV;
         T acc = (T)0;   // per-thread sum in the field precision; block and global sums in FP64
@@ -800,27 +874,59 @@ __global__ void __launch_bounds__(z_threads<N, T>(), sizeof(T) == 4 && N <= 128 
         const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = tot;
     }
-    if (mode == Z_INV || mode == Z_FWD_GAMMA_INV) block_fft<N, true, MI>(buf, nlines, tw);
-    if constexpr (walk) {
-        const C *sb = buf + wxl * LS + pad16(wz);
-        C *gb = spec + (long)wz * plane + (long)ky * Hx + kx0 + wxl;
-        for (int f = 0; f < nf; ++f) {
+    const bool inv = mode == Z_INV || mode == Z_FWD_GAMMA_INV;
+    if constexpr (Shape<N>::R2 > 1) {
+        if (inv) {
+            bfft_pass1<N, true, MI>(buf, nlines);
+            // the inverse transform's pass 2 stored straight to HBM: item (line, j < 16) transforms slots j + 16 r
+            // as bfft_pass2 and stores elements j + 16 r
+            constexpr int R2 = Shape<N>::R2;
+            const int nit = nlines * 16;
+            for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+                int l, j;
+                C *g = hbm_item(it, 16, l, j);
+                const C *line = buf + l * LS + j;
+                C u[R2];
 #pragma unroll
-            for (int k = 0; k < KZ; ++k) gb[f * fstride + (long)k * DZ * plane] = sb[f * TX * LS + k * (DZ + DZ / 16)];
+                for (int r = 0; r < R2; ++r) {
+                    C a = line[17 * r];
+                    if (r > 0) {
+                        C w = tw[16 * r + j];
+                        w.y = -w.y;
+                        a = cmul(a, w);
+                    }
+                    u[r] = a;
+                }
+                dft_reg<R2, true>(u);
+#pragma unroll
+                for (int r = 0; r < R2; ++r) g[(long)(j + 16 * r) * plane] = u[r];
+            }
         }
-    } else {
-        for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
-            const int f = t / (TX * N), r = t % (TX * N);
-            int z, xl;
-            slab_item<N, TX>(r, z, xl);
-            spec[f * fstride + z * plane + (long)ky * Hx + kx0 + xl] = buf[(f * TX + xl) * LS + pad16(z)];
-        }
+    } else if (inv) {
+        block_fft<N, true, MI>(buf, nlines, tw);
     }
-    if (nyq)
-        for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
-            const int f = t / N, z = t % N;
-            spec[f * fstride + z * plane + (long)ky * Hx + N / 2] = buf[(nf * TX + f) * LS + pad16(z)];
+    if (!inv || Shape<N>::R2 == 1) {   // the slab from shared memory
+        if constexpr (walk) {
+            const C *sb = buf + wxl * LS + pad16(wz);
+            C *gb = spec + (long)wz * plane + (long)ky * Hx + kx0 + wxl;
+            for (int f = 0; f < nf; ++f) {
+#pragma unroll
+                for (int k = 0; k < KZ; ++k) gb[f * fstride + (long)k * DZ * plane] = sb[f * TX * LS + k * (DZ + DZ / 16)];
+            }
+        } else {
+            for (int t = threadIdx.x; t < nf * TX * N; t += blockDim.x) {
+                const int f = t / (TX * N), r = t % (TX * N);
+                int z, xl;
+                slab_item<N, TX>(r, z, xl);
+                spec[f * fstride + z * plane + (long)ky * Hx + kx0 + xl] = buf[(f * TX + xl) * LS + pad16(z)];
+            }
         }
+        if (nyq)
+            for (int t = threadIdx.x; t < nf * N; t += blockDim.x) {
+                const int f = t / N, z = t % N;
+                spec[f * fstride + z * plane + (long)ky * Hx + N / 2] = buf[(nf * TX + f) * LS + pad16(z)];
+            }
+    }
     if (zc.ctl != nullptr) {   // the last block to finish runs the fixed-point control (fpctl.cuh)
         __shared__ int last;
         __threadfence();       // this block's partial sum and spectrum are visible to the others
