@@ -454,18 +454,22 @@ template <int N> __device__ __forceinline__ int xy_at(int y, int kx) {
 // inverse kernel's first pass and the forward kernel's last pass store, so none of them round-trips through
 // shared memory.
 
-// x pass 1 (bfft_pass1's items) with element e of line l read through ld(l, e): no in-place hazard, so no barrier
-// between reads and writes. Ends with a barrier.
-template <int N, bool INV, typename C, typename Ld> __device__ void x_pass1_ld(C *buf, int nlines, Ld ld) {
+// x pass 1 (bfft_pass1's items) with element e of line l read through ld(l, e). IN_PLACE: ld reads the lines the
+// pass writes, so every read comes before any write (a barrier between); otherwise it reads HBM. Ends with a barrier.
+template <int N, bool INV, bool IN_PLACE, typename C, typename Ld> __device__ void x_pass1_ld(C *buf, int nlines, Ld ld) {
     constexpr int R1 = Shape<N>::R1, LS = Shape<N>::LS, M1 = N / R1;
     static_assert(M1 <= 16 && 16 % M1 == 0, "pass-1 stride");
     const int t = threadIdx.x;
-    if (t < nlines * M1) {
-        int l, j;
-        pass1_item<N>(t, nlines, l, j);
-        C v[R1];
+    const bool on = t < nlines * M1;
+    int l = 0, j = 0;
+    if (on) pass1_item<N>(t, nlines, l, j);
+    C v[R1];
+    if (on) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = ld(l, j + M1 * r);
+    }
+    if constexpr (IN_PLACE) __syncthreads();
+    if (on) {
         dft_reg<R1, INV>(v);
         C *dst = buf + l * LS + 17 * j;
 #pragma unroll
@@ -474,23 +478,16 @@ template <int N, bool INV, typename C, typename Ld> __device__ void x_pass1_ld(C
     __syncthreads();
 }
 
-// y pass 1: item (kx, j < M1) takes rows j + M1 r of column kx, from ld(y, kx) or from the plane, and writes
-// rows R1 j + r (line R1 j / 2 + r / 2, half r & 1). The regular columns kx < N/2 take one item per thread; the
-// Nyquist column's M1 items run on lanes 0..M1-1 of warp 0 afterwards (no other item touches that column).
-// Ends with a barrier.
-template <int N, bool INV, bool FROM_BUF, typename C, typename Ld> __device__ void col_pass1(C *buf, Ld ld) {
+// y pass 1: item (kx, j < M1) takes rows j + M1 r of column kx through ld(y, kx) and writes rows R1 j + r (line
+// R1 j / 2 + r / 2, half r & 1). IN_PLACE: ld reads the buffer the pass writes, so every read comes before any write
+// (a barrier between). The regular columns kx < N/2 take one item per thread; the Nyquist column's M1 items then run
+// on lanes 0..M1-1 of warp 0 (no other item writes that column), reading its rows through ldn(y), which must not
+// read what the regular items write (pre(), run by every thread in the read phase, could copy them aside). Ends
+// with a barrier.
+template <int N, bool INV, bool IN_PLACE, typename C, typename Ld, typename Pre, typename LdN>
+__device__ void col_pass1(C *buf, Ld ld, Pre pre, LdN ldn) {
     constexpr int R1 = Shape<N>::R1, M1 = N / R1, Hx = N / 2 + 1, LS = Shape<N>::LS;
     static_assert(M1 % 2 == 0 && R1 % 2 == 0 && M1 <= 32, "row pairs");
-    auto load = [&](int j, int kx, C (&v)[R1]) {
-        if constexpr (FROM_BUF) {
-            const C *src = buf + xy_at<N>(j, kx);   // rows j + M1 r: line (j >> 1) + r M1 / 2, half j & 1
-#pragma unroll
-            for (int r = 0; r < R1; ++r) v[r] = src[r * (M1 / 2) * LS];
-        } else {
-#pragma unroll
-            for (int r = 0; r < R1; ++r) v[r] = ld(j + M1 * r, kx);
-        }
-    };
     auto transform = [&](int j, int kx, C (&v)[R1]) {
         dft_reg<R1, INV>(v);
         C *dst = buf + (R1 / 2) * j * LS + kx;
@@ -501,12 +498,16 @@ template <int N, bool INV, bool FROM_BUF, typename C, typename Ld> __device__ vo
     const bool on = t < (N / 2) * M1;
     const int j = t / (N / 2), kx = t % (N / 2);
     C v[R1];
-    if (on) load(j, kx, v);
-    if constexpr (FROM_BUF) __syncthreads();
+    if (on) {
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[r] = ld(j + M1 * r, kx);
+    }
+    pre();
+    if constexpr (IN_PLACE) __syncthreads();
     if (on) transform(j, kx, v);
     if (t < M1) {
-        load(t, N / 2, v);
-        __syncwarp((1u << M1) - 1u);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[r] = ldn(t + M1 * r);
         transform(t, N / 2, v);
     }
     __syncthreads();
@@ -551,7 +552,7 @@ k_fft_xy_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out, c
     C *dst = out + (long)blockIdx.x * N * Hx;
     load_tw(tw, N);
     // x: line p packs rows 2p and 2p+1 as one complex row; pass 1 reads them from HBM
-    x_pass1_ld<N, false>(buf, NP, [&](int p, int e) { return cmk<C>(src[(2 * p) * N + e], src[(2 * p + 1) * N + e]); });
+    x_pass1_ld<N, false, false>(buf, NP, [&](int p, int e) { return cmk<C>(src[(2 * p) * N + e], src[(2 * p + 1) * N + e]); });
     bfft_pass2<N, false>(buf, NP, tw);
     {   // unpack one line per warp: read the line's values, then write its two half-spectrum rows in place
         const int lane = threadIdx.x & 31;
@@ -583,7 +584,9 @@ k_fft_xy_r2c(const T *__restrict__ in, typename CT<T>::type *__restrict__ out, c
     }
     __syncthreads();
     // y: down the columns of the row-major plane; pass 2 stores rows j + 16 r to HBM
-    col_pass1<N, false, true>(buf, 0);
+    // y: down the columns of the row-major plane; pass 2 stores rows j + 16 r to HBM
+    col_pass1<N, false, true>(
+        buf, [&](int y, int kx) { return buf[xy_at<N>(y, kx)]; }, [] {}, [&](int y) { return buf[xy_at<N>(y, N / 2)]; });
     col_pass2<N, false>(buf, tw, [&](int j, int kx, C *, const C (&u)[R2]) {
 #pragma unroll
         for (int r = 0; r < R2; ++r) dst[(j + 16 * r) * Hx + kx] = u[r];
@@ -600,45 +603,33 @@ k_fft_xy_c2r(const typename CT<T>::type *__restrict__ spec, T *__restrict__ out,
     pdl_trigger();
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     using C = typename CT<T>::type;
-    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, KV = N / 32, R2 = Shape<N>::R2;
+    constexpr int LS = Shape<N>::LS, Hx = N / 2 + 1, NP = N / 2, R2 = Shape<N>::R2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *buf = tw + N;
     const C *src = spec + (long)blockIdx.x * N * Hx;
     load_tw(tw, N);
     // y: pass 1 reads the columns from HBM
-    col_pass1<N, true, false>(buf, [&](int y, int kx) { return src[y * Hx + kx]; });
+    col_pass1<N, true, false>(
+        buf, [&](int y, int kx) { return src[y * Hx + kx]; }, [] {}, [&](int y) { return src[y * Hx + N / 2]; });
     col_pass2<N, true>(buf, tw, [](int, int, C *line, const C (&u)[R2]) {
 #pragma unroll
         for (int r = 0; r < R2; ++r) line[r * 8 * LS] = u[r];
     });
-    {   // pack one line per warp: read rows 2p and 2p+1, then write A + iB over them
-        const int lane = threadIdx.x & 31;
-        for (int p = threadIdx.x >> 5; p < NP; p += blockDim.x >> 5) {
-            C *line = buf + p * LS;
-            C zv[KV];
-#pragma unroll
-            for (int u = 0; u < KV; ++u) {
-                const int k = lane + 32 * u;
-                C A, B;
-                if (k <= (N >> 1)) {
-                    A = line[k];
-                    B = line[Hx + k];
-                } else {
-                    A = cconj(line[N - k]);
-                    B = cconj(line[Hx + N - k]);
-                }
-                zv[u] = cmk<C>(A.x - B.y, A.y + B.x);   // A + iB
-            }
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < KV; ++u) line[pad16(lane + 32 * u)] = zv[u];
-            __syncwarp();
+    // x: pass 1 packs rows 2p and 2p+1 as it reads them (Z[k] = A[k] + i B[k], with A[N-k] = conj A[k] past N/2)
+    // and writes the lines in place
+    x_pass1_ld<N, true, true>(buf, NP, [&](int p, int k) {
+        const C *line = buf + p * LS;
+        C A, B;
+        if (k <= (N >> 1)) {
+            A = line[k];
+            B = line[Hx + k];
+        } else {
+            A = cconj(line[N - k]);
+            B = cconj(line[Hx + N - k]);
         }
-    }
-    __syncthreads();
-    // x, then the strain update row by row (row-contiguous loads of the base strain and stores)
-    bfft_pass1<N, true, 1>(buf, NP);
+        return cmk<C>(A.x - B.y, A.y + B.x);
+    });
     bfft_pass2<N, true>(buf, NP, tw);
     const long r0 = (long)blockIdx.x * N;   // first row: (field * N + z) * N
     T add = (T)0;
