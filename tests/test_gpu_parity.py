@@ -64,9 +64,12 @@ def test_voronoi_ties_go_to_the_smaller_index(ev):
         assert np.array_equal(got, O.voronoi(n, tied))
 
 
-@pytest.mark.parametrize("n", [4, 8, 16, 32])
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_rfft3d_matches_oracle_fft(ev, n, prec):
+    """Forward and inverse against the oracle's radix-2 FFT. From 32^3 (FP32 up to 128^3, FP64 up to 64^3) the x and
+    y transforms run as one launch over whole planes; below, and at the sizes of the next test that do not fit, as
+    separate passes."""
     import torch
     rng = np.random.default_rng(n)
     nf = 6 if n <= 16 else 3
