@@ -34,7 +34,8 @@ struct FpCtlParams {
 struct ZCtl {
     FpCtl *ctl;
     int32_t *flags;         // flags[0] failed local solves, flags[1] max local iterations, flags[10] the local
-                            // solve's work-list count (reset here for the next iteration)
+                            // solve's work-list count, flags[11] its pass 1's two-step count (both reset here for
+                            // the next iteration)
     double *scal;           // scal[0..5] mean stress (written by the z pass), scal[6] residual sum
     FpCtlParams p;
 };
@@ -62,7 +63,8 @@ __device__ __forceinline__ void fp_control_block(const ZCtl &z, const double *__
     if (threadIdx.x == 0) {
         go = 0;
         z.scal[6] = s;
-        z.flags[10] = 0;   // the next iteration's first local-solve pass counts its work list from zero
+        z.flags[10] = 0;   // the next iteration's first local-solve pass counts its work list from zero,
+        z.flags[11] = 0;   // and its voxels accepted after two steps
         const int it = iv[0] + 1;
         c->it = it;
         c->nmax = max(iv[1], iv[3]);

@@ -363,11 +363,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
 // full chord iteration on the listed voxels only, from their unchanged state, so every result is
 // bitwise the one the single-kernel iteration gives.
 template <typename TA, typename TS, bool MR = false>
-__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_first(long N3, const TA *__restrict__ epst,
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 7 : 1) k_chord_first(long N3, const TA *__restrict__ epst,
                                                          const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
                                                          TA *__restrict__ sig, const TA *__restrict__ Stab,
                                                          const TA *__restrict__ Mtab, const TS *__restrict__ fac,
-                                                         MatConst mc, TA tol, int *__restrict__ flags,
+                                                         MatConst mc, TA tol, TA ls_free, int *__restrict__ flags,
                                                          int32_t *__restrict__ wl, const int *__restrict__ skip,
     const TA *__restrict__ tol_dev, MRPtr<TA> mrp) {
     pdl_wait();
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = v < N3;
-    bool done = false;
+    bool done = false, two = false;
     // the stored factors are needed only after the residual: their copies start first, into this thread's slots
     // of shared memory, and run under the other loads and the evaluation
     __shared__ __align__(16) TS fsh[factor_words<TS>() * kThreads];
@@ -409,19 +409,59 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 8 : 1) k_chord_fir
             sn += sg[i] * sg[i];
         }
         dn = dsqrt(dn);
-        if (dn <= tol * (dsqrt(sn) + tc) && rd >= (TA)0) {   // the acceptance test of chord_voxel
+        const TA scale = dsqrt(sn) + tc;
+        if (dn <= tol * scale && rd >= (TA)0) {   // the acceptance test of chord_voxel
 #pragma unroll
             for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c] - d[c];
             done = true;
+        } else if (rd > (TA)0) {
+            // chord_voxel's next moves while they stay on its common path, with its operations in its order: the
+            // full step of the line search (s = 1) passes the sufficient-decrease test, and the chord step from
+            // there passes the acceptance test. Anything else goes to pass 2, which starts over from the
+            // unchanged state, so every voxel still ends bitwise where the single-kernel iteration puts it.
+            // The grain's compliance and the factors are fetched again (from L1 and shared memory) rather than held
+            // in registers through the first step.
+            const TA s1 = (TA)1, phi0 = e.phi;
+            TA st[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) st[i] = sg[i] - s1 * d[i];
+            asm volatile("" ::: "memory");
+            TA Sp2[21];
+            load_compliance(Stab + 36 * (long)g, Sp2);
+            if constexpr (MR)
+                evaluate_r<TA>(Sp2, Mtab + 72 * (long)g, etr, FlowMR<TA>{mrp.tpi, N3, v, tc}, (TA)0, st, mc, e);
+            else
+                evaluate_r<TA>(Sp2, Mtab + 72 * (long)g, etr, tc, drcp(tc), st, mc, e);
+            if (e.phi <= phi0 - (TA)1e-4 * s1 * rd || s1 * dn <= ls_free * scale) {
+                prefetched_factors(fsh, F);
+                ldl_apply<TS, TA>(F, e.r, d);
+                TA rd2 = (TA)0, dn2 = (TA)0, sn2 = (TA)0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    rd2 += e.r[i] * d[i];
+                    dn2 += d[i] * d[i];
+                    sn2 += st[i] * st[i];
+                }
+                dn2 = dsqrt(dn2);
+                if (dn2 <= tol * (dsqrt(sn2) + tc) && rd2 >= (TA)0) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) sig[c * N3 + v] = st[c] - d[c];
+                    done = true;
+                    two = true;
+                }
+            }
         }
     }
     const unsigned todo = __ballot_sync(0xffffffffu, valid && !done);
+    const unsigned twos = __ballot_sync(0xffffffffu, two);
     const int lane = threadIdx.x & 31;
     int base = 0;
     if (lane == 0 && todo) base = atomicAdd(flags + 10, __popc(todo));
+    if (lane == 0 && twos) atomicAdd(flags + 11, __popc(twos));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (valid && !done) wl[base + __popc(todo & ((1u << lane) - 1u))] = (int32_t)v;
-    // the accepted voxels (one evaluation and one solve each) are counted by pass 2 as N3 - listed
+    // the accepted voxels are counted by pass 2: N3 - listed with one evaluation and one solve each, plus one more
+    // of each for the flags[11] voxels accepted after two steps
 }
 
 template <typename TA, typename TS, typename TF, bool MR = false>
@@ -435,10 +475,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_chord_res
     if (skip != nullptr && *skip) return;   // the fixed point has converged
     if (tol_dev != nullptr) tol = *tol_dev;   // local tolerance set on the device for this iteration
     const int count = *(volatile const int *)(flags + 10);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && N3 - count > 0) {   // pass 1 accepted the others in one step
-        atomicMax(flags + 1, 1);
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)(N3 - count));
-        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)(N3 - count));
+    if (blockIdx.x == 0 && threadIdx.x == 0 && N3 - count > 0) {   // pass 1 accepted the others in one or two steps
+        const int twos = *(volatile const int *)(flags + 11);
+        atomicMax(flags + 1, twos > 0 ? 2 : 1);
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 4), (unsigned long long)(N3 - count + twos));
+        atomicAdd(reinterpret_cast<unsigned long long *>(flags + 6), (unsigned long long)(N3 - count + twos));
     }
     const long stride = (long)gridDim.x * blockDim.x;
     int t_fail = 0, t_mx = 0, t_it = 0, t_ev = 0, t_rf = 0;
@@ -858,7 +899,7 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
         // memset breaks the chain; outside it the count is reset here.
         const bool pdl = skip != nullptr;
         if (!pdl) {
-            cudaError_t e = cudaMemsetAsync(flags + 10, 0, sizeof(int), s);
+            cudaError_t e = cudaMemsetAsync(flags + 10, 0, 2 * sizeof(int), s);
             if (e != cudaSuccess) return e;
         }
         const int rb = std::min(blocks, nsm * (sizeof(TA) == 4 ? 3 : 2));
@@ -866,7 +907,7 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
         by_law(mrp, [&](auto law) {
             constexpr bool MR = decltype(law)::value;
             err = launch_k(pdl, k_chord_first<TA, TA, MR>, dim3(blocks), dim3(kThreads), 0, s, N3, epst, tauc, g0, sig,
-                           Stab, Mtab, (const TA *)fac, mc, (TA)tol, flags, wl, skip, tol_dev, mrp);
+                           Stab, Mtab, (const TA *)fac, mc, (TA)tol, ls_free_of<TA>(), flags, wl, skip, tol_dev, mrp);
             if (err != cudaSuccess) return;
             if (solve_fp64)
                 err = launch_k(pdl, k_chord_rest<TA, TA, double, MR>, dim3(rb), dim3(kThreads), 0, s, N3, epst, tauc,
