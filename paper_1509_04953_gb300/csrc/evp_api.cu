@@ -476,6 +476,7 @@ double vm_strain(const double e[6]) {
 // Returns a status; fills the iteration count, residuals, mean stress and the macro strain increment.
 static_assert(sizeof(FpCtl) <= 256, "FpCtl must fit its workspace slot");
 constexpr int kFpBatch = 16;   // iterations queued between host reads of the control block
+constexpr int kTwoStepIters = 40;   // iterations of an increment whose first local-solve pass takes two chord steps
 const double kZero6[6] = {0, 0, 0, 0, 0, 0};
 
 // The x and y passes of the fixed point's transforms, forward and inverse: one launch each where the (field, z)
@@ -894,6 +895,9 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
             const int nb = std::min(kFpBatch, h->cfg.max_iter - queued);
             for (int q = 0; q < nb; ++q) {
                 const int first = queued + q == 0 && fresh;
+                // the first pass takes two chord steps in the early iterations of an increment, where many voxels
+                // need them; later a single step keeps it at one more CTA per SM
+                const int two = queued + q < kTwoStepIters;
                 if (h->dbl) {
                   { PROF(0, 1);
                     if (h->cfg.newton_mode == EVP_NEWTON_F32_TANGENT)
@@ -904,7 +908,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         CK(newton_chord_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                                       (double *)h->Stab, (double *)h->Mtab, h->fac, mc, ntol,
                                                       h->cfg.newton_max, 1, first, h->flags, h->wlist, h->nsm, h->st,
-                                                      skip, tl64, mr_ptr<double>(h)));
+                                                      skip, tl64, mr_ptr<double>(h), two));
                     else
                         CK(newton_field<double>(N3, (double *)h->epst, (double *)h->tauc, h->g0, (double *)h->sigk,
                                                 (double *)h->Stab, (double *)h->Mtab, mc, ntol, h->cfg.newton_max, 1,
@@ -919,7 +923,7 @@ int evp_increment(evp_handle *h, double dE33, double dt, evp_stats *out) {
                         CK(newton_chord_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                                      (float *)h->Stab, (float *)h->Mtab, h->fac, mc, ntol,
                                                      h->cfg.newton_max, solve64, first, h->flags, h->wlist, h->nsm,
-                                                     h->st, skip, tl32, mr_ptr<float>(h)));
+                                                     h->st, skip, tl32, mr_ptr<float>(h), two));
                     else
                         CK(newton_field<float>(N3, (float *)h->epst, (float *)h->tauc, h->g0, (float *)h->sigk,
                                                (float *)h->Stab, (float *)h->Mtab, mc, ntol, h->cfg.newton_max, solve64,

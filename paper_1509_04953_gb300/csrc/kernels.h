@@ -76,13 +76,14 @@ cudaError_t newton_field(long N3, const TA *epst, const TA *tauc, const int32_t 
                          const int *skip = nullptr, const TA *tol_dev = nullptr, MRPtr<TA> mrp = MRPtr<TA>{});
 // Jacobian-reuse variant: fac holds 21 factor words per voxel in TA (factorised in FP64 if solve_fp64).
 // Unless force_refresh, runs in two passes with the work list wl (N3 entries, count in flags[10]);
-// nsm = multiprocessors, for the grid of the second pass.
+// nsm = multiprocessors, for the grid of the second pass. two_step: the first pass also takes the chord
+// iteration's next two moves where they stay on its common path (same results, fewer listed voxels).
 template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s,
                                const int *skip = nullptr,
-                               const TA *tol_dev = nullptr, MRPtr<TA> mrp = MRPtr<TA>{});
+                               const TA *tol_dev = nullptr, MRPtr<TA> mrp = MRPtr<TA>{}, int two_step = 1);
 // FP64 residual / FP32 tangent Newton (FP64 path); Stabf / Mtabf are FP32 copies of the tables.
 cudaError_t newton_field_df(long N3, const double *epst, const double *tauc, const int32_t *g0, double *sig,
                             const double *Stab, const double *Mtab, const float *Stabf, const float *Mtabf,

@@ -362,8 +362,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 3 : 2) k_newton_ch
 // order immaterial: each voxel's computation is independent and deterministic). Pass 2 runs the
 // full chord iteration on the listed voxels only, from their unchanged state, so every result is
 // bitwise the one the single-kernel iteration gives.
-template <typename TA, typename TS, bool MR = false>
-__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 7 : 1) k_chord_first(long N3, const TA *__restrict__ epst,
+// TWO: also the chord iteration's next two moves (below); its registers cost one CTA per SM on the FP32 path.
+template <typename TA, typename TS, bool MR = false, bool TWO = true>
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? (TWO ? 7 : 8) : 1) k_chord_first(long N3, const TA *__restrict__ epst,
                                                          const TA *__restrict__ tauc, const int32_t *__restrict__ g0,
                                                          TA *__restrict__ sig, const TA *__restrict__ Stab,
                                                          const TA *__restrict__ Mtab, const TS *__restrict__ fac,
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 4 ? 7 : 1) k_chord_fir
 #pragma unroll
             for (int c = 0; c < 6; ++c) sig[c * N3 + v] = sg[c] - d[c];
             done = true;
-        } else if (rd > (TA)0) {
+        } else if (TWO && rd > (TA)0) {
             // chord_voxel's next moves while they stay on its common path, with its operations in its order: the
             // full step of the line search (s = 1) passes the sufficient-decrease test, and the chord step from
             // there passes the acceptance test. Anything else goes to pass 2, which starts over from the
@@ -890,7 +891,7 @@ template <typename TA>
 cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const int32_t *g0, TA *sig, const TA *Stab,
                                const TA *Mtab, void *fac, MatConst mc, double tol, int maxit, int solve_fp64,
                                int force_refresh, int *flags, int32_t *wl, int nsm, cudaStream_t s, const int *skip,
-                               const TA *tol_dev, MRPtr<TA> mrp) {
+                               const TA *tol_dev, MRPtr<TA> mrp, int two_step) {
     const int blocks = (int)((N3 + kThreads - 1) / kThreads);
     if (!force_refresh && wl) {
         // flags[10] counts the listed voxels; pass 2 reads it on the device (no host round trip). Inside the
@@ -906,8 +907,14 @@ cudaError_t newton_chord_field(long N3, const TA *epst, const TA *tauc, const in
         cudaError_t err = cudaSuccess;
         by_law(mrp, [&](auto law) {
             constexpr bool MR = decltype(law)::value;
-            err = launch_k(pdl, k_chord_first<TA, TA, MR>, dim3(blocks), dim3(kThreads), 0, s, N3, epst, tauc, g0, sig,
-                           Stab, Mtab, (const TA *)fac, mc, (TA)tol, ls_free_of<TA>(), flags, wl, skip, tol_dev, mrp);
+            if (two_step)
+                err = launch_k(pdl, k_chord_first<TA, TA, MR, true>, dim3(blocks), dim3(kThreads), 0, s, N3, epst, tauc,
+                               g0, sig, Stab, Mtab, (const TA *)fac, mc, (TA)tol, ls_free_of<TA>(), flags, wl, skip,
+                               tol_dev, mrp);
+            else
+                err = launch_k(pdl, k_chord_first<TA, TA, MR, false>, dim3(blocks), dim3(kThreads), 0, s, N3, epst,
+                               tauc, g0, sig, Stab, Mtab, (const TA *)fac, mc, (TA)tol, ls_free_of<TA>(), flags, wl,
+                               skip, tol_dev, mrp);
             if (err != cudaSuccess) return;
             if (solve_fp64)
                 err = launch_k(pdl, k_chord_rest<TA, TA, double, MR>, dim3(rb), dim3(kThreads), 0, s, N3, epst, tauc,
@@ -1003,7 +1010,7 @@ template <typename TA> cudaError_t total_strain(long N3, const TA *epse, const T
                                           const int *, const TA *, MRPtr<TA>);                                   \
     template cudaError_t newton_chord_field<TA>(long, const TA *, const TA *, const int32_t *, TA *, const TA *,  \
                                                 const TA *, void *, MatConst, double, int, int, int, int *,       \
-                                                int32_t *, int, cudaStream_t, const int *, const TA *, MRPtr<TA>); \
+                                                int32_t *, int, cudaStream_t, const int *, const TA *, MRPtr<TA>, int); \
     template cudaError_t al_local<TA>(long, const TA *, const TA *, const TA *, const int32_t *, TA *, TA *, TA *, \
                                       const TA *, const TA *, const TA *, MatConst, double, double, double, int, int, \
                                       int, int *, double *, void *, int, cudaStream_t, int, MRPtr<TA>);           \
