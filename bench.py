@@ -321,10 +321,10 @@ def native(args, ws, rank, local):
 
 
 # Measured DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum, averaged over 20 iterations of the
-# second increment) of one local-solve iteration (pass 1 326.8 MB + pass 2 0.06 MB), per workload, with the
-# SHA-256 prefix of the local-solve sources it was taken on. A figure taken on other sources is stale and
-# reported as null.
-NEWTON_TRAFFIC = {(128, "mixed", True): (326.8e6, "409e9034b89ab28e")}
+# second increment, where pass 1 takes one step) of one local-solve iteration (pass 1 326.8 MB + pass 2 0.06 MB;
+# the two-step pass 1 of an increment's first iterations moves 327.9 MB), per workload, with the SHA-256 prefix of
+# the local-solve sources it was taken on. A figure taken on other sources is stale and reported as null.
+NEWTON_TRAFFIC = {(128, "mixed", True): (326.8e6, "e2768457d0fe49dd")}
 NEWTON_SOURCES = ("paper_1509_04953_gb300/csrc/newton.cu", "paper_1509_04953_gb300/csrc/local.cuh")
 
 
