@@ -482,8 +482,8 @@ template <int N, bool INV, bool IN_PLACE, typename C, typename Ld> __device__ vo
 // R1 j / 2 + r / 2, half r & 1). IN_PLACE: ld reads the buffer the pass writes, so every read comes before any write
 // (a barrier between). The regular columns kx < N/2 take one item per thread; the Nyquist column's M1 items then run
 // on lanes 0..M1-1 of warp 0 (no other item writes that column), reading its rows through ldn(y), which must not
-// read what the regular items write (pre(), run by every thread in the read phase, could copy them aside). Ends
-// with a barrier.
+// read what the regular items write (pre(), run by every thread in the read phase, could copy them aside); a warp
+// barrier orders those lanes' reads before their in-place writes. Ends with a barrier.
 template <int N, bool INV, bool IN_PLACE, typename C, typename Ld, typename Pre, typename LdN>
 __device__ void col_pass1(C *buf, Ld ld, Pre pre, LdN ldn) {
     constexpr int R1 = Shape<N>::R1, M1 = N / R1, Hx = N / 2 + 1, LS = Shape<N>::LS;
@@ -508,6 +508,7 @@ __device__ void col_pass1(C *buf, Ld ld, Pre pre, LdN ldn) {
     if (t < M1) {
 #pragma unroll
         for (int r = 0; r < R1; ++r) v[r] = ldn(t + M1 * r);
+        __syncwarp((1u << M1) - 1u);   // ldn may read the column these lanes write
         transform(t, N / 2, v);
     }
     __syncthreads();
